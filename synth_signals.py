@@ -1,0 +1,121 @@
+"""Seeded synthetic audio generators shared by the tests, the benchmark and the oracle checks.
+
+This module holds no arithmetic of the scattering transform: it only draws signals.
+The paper's recordings (bird calls, Medley-solos-DB, dizi glissandi) are not available,
+so these generators stand in for them with the same lengths and the same kinds of
+content (AM/FM tones, chirps, click trains).
+
+Seeding: workload ``c`` uses base seed ``20220408 + c`` and one child stream per
+signal from ``numpy.random.SeedSequence(base).spawn(B)``.  Every generator works in
+float64 and returns float32 arrays (the transform's input type).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BASE_SEED = 20220408
+SR = 22050.0
+
+
+def _streams(seed: int, count: int):
+    return [np.random.default_rng(s) for s in np.random.SeedSequence(seed).spawn(count)]
+
+
+def noise_plus_chirp(N: int, seed: int, f0: float = 0.01, f1: float = 0.4, amp: float = 0.5):
+    """Unit-variance white noise plus a linear chirp sweeping f0 -> f1 cycles/sample."""
+    rng = _streams(seed, 1)[0]
+    n = np.arange(N, dtype=np.float64)
+    phase = 2.0 * np.pi * (f0 * n + (f1 - f0) * n * n / (2.0 * N))
+    x = rng.standard_normal(N) + amp * np.sin(phase)
+    return x.astype(np.float32)
+
+
+def amfm_batch(B: int, N: int, seed: int, sr: float = SR, noise_db: float = -30.0):
+    """AM/FM tones: (1 + 0.5 sin(2 pi f_am t + p1)) * sin(phi(t)),
+    phi'(t) = 2 pi f_c 2^{(e/12) sin(2 pi f_fm t + p2)}, plus white noise at
+    ``noise_db`` re the tone's RMS.  f_c log-uniform in [100, 4000] Hz, f_am uniform
+    in [1, 16] Hz, f_fm uniform in [1, 8] Hz, excursion e uniform in [1, 6] semitones."""
+    out = np.empty((B, N), dtype=np.float32)
+    t = np.arange(N, dtype=np.float64) / sr
+    for b, rng in enumerate(_streams(seed, B)):
+        fc = np.exp(rng.uniform(np.log(100.0), np.log(4000.0)))
+        fam = rng.uniform(1.0, 16.0)
+        ffm = rng.uniform(1.0, 8.0)
+        e = rng.uniform(1.0, 6.0)
+        p1, p2 = rng.uniform(0.0, 2.0 * np.pi, size=2)
+        inst = 2.0 * np.pi * fc * 2.0 ** ((e / 12.0) * np.sin(2.0 * np.pi * ffm * t + p2))
+        phi = np.cumsum(inst) / sr
+        tone = (1.0 + 0.5 * np.sin(2.0 * np.pi * fam * t + p1)) * np.sin(phi)
+        rms = np.sqrt(np.mean(tone * tone))
+        noise = rng.standard_normal(N) * rms * 10.0 ** (noise_db / 20.0)
+        out[b] = tone + noise
+    return out
+
+
+def _biquad_bandpass(x, fc, q, sr):
+    """Second-order resonator (constant 0 dB peak gain band-pass)."""
+    from scipy.signal import lfilter
+    w0 = 2.0 * np.pi * fc / sr
+    alpha = np.sin(w0) / (2.0 * q)
+    b = np.array([alpha, 0.0, -alpha])
+    a = np.array([1.0 + alpha, -2.0 * np.cos(w0), 1.0 - alpha])
+    return lfilter(b, a, x)
+
+
+def click_train_batch(B: int, N: int, seed: int, sr: float = SR):
+    """Poisson click trains (rate uniform in [5, 40] Hz); every click is an impulse
+    through its own random resonator (centre uniform in [200, 6000] Hz, Q log-uniform
+    in [5, 30]).  Normalised to unit RMS."""
+    out = np.empty((B, N), dtype=np.float32)
+    for b, rng in enumerate(_streams(seed, B)):
+        rate = rng.uniform(5.0, 40.0)
+        n_clicks = rng.poisson(rate * N / sr)
+        pos = np.sort(rng.integers(0, N, size=max(n_clicks, 1)))
+        y = np.zeros(N)
+        for p in pos:
+            fc = rng.uniform(200.0, 6000.0)
+            q = np.exp(rng.uniform(np.log(5.0), np.log(30.0)))
+            # the response decays as exp(-pi fc t / q): keep it until ~1e-9 of its start
+            span = int(min(N - p, np.ceil(21.0 * q * sr / (np.pi * fc))))
+            imp = np.zeros(span)
+            imp[0] = rng.uniform(0.5, 1.0) * (1.0 if rng.random() < 0.5 else -1.0)
+            y[p:p + span] += _biquad_bandpass(imp, fc, q, sr)
+        rms = np.sqrt(np.mean(y * y))
+        out[b] = y / (rms if rms > 0 else 1.0)
+    return out
+
+
+def white_noise_batch(B: int, N: int, seed: int, std: float = 1.0):
+    out = np.empty((B, N), dtype=np.float32)
+    for b, rng in enumerate(_streams(seed, B)):
+        out[b] = rng.standard_normal(N) * std
+    return out
+
+
+def chirp_eq5(N: int, fc: float, fm: float, gamma: float, sr: float = SR, w: float = 2.0):
+    """The paper's AM/FM exponential chirp (Sec. 3.2, Eq. 5): a Gaussian window of
+    characteristic width w (octaves) in gamma*t, times sin(2 pi f_m t), times
+    sin(2 pi f_c 2^{gamma t} / (gamma ln 2)), centred in the frame."""
+    t = (np.arange(N, dtype=np.float64) - N / 2) / sr
+    window = np.exp(-0.5 * (gamma * t / (w / 2.0)) ** 2)
+    x = window * np.sin(2.0 * np.pi * fm * t) * np.sin(
+        2.0 * np.pi * fc / (gamma * np.log(2.0)) * 2.0 ** (gamma * t))
+    return x.astype(np.float32)
+
+
+def varlen_lengths(count: int, seed: int, lo_log2: float = 13.0, hi_log2: float = 17.0):
+    """Signal lengths drawn log-uniform in [2^lo, 2^hi]."""
+    rng = _streams(seed, 1)[0]
+    return np.floor(2.0 ** rng.uniform(lo_log2, hi_log2, size=count)).astype(np.int64)
+
+
+def workload_signals(config: int, B: int, N: int):
+    """Inputs for the named workloads (1: noise + chirp, 2/4: AM/FM, 3: click trains)."""
+    seed = BASE_SEED + config
+    if config == 1:
+        return np.stack([noise_plus_chirp(N, seed + 1000 * b) for b in range(B)])
+    if config in (2, 4):
+        return amfm_batch(B, N, seed)
+    if config == 3:
+        return click_train_batch(B, N, seed)
+    raise ValueError(f"no generator for workload {config}")
