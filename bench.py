@@ -1,0 +1,317 @@
+"""Throughput benchmark: JTFS forward + backward signals/sec on the B = 64, N = 2^16, Q = 16
+workload (J = 12, J_fr = 4, Q_fr = 2, T = 2^12, F = 16; seeded synthetic AM/FM tones).
+
+One step = forward of the whole batch (inputs resident in HBM) + backward with fixed
+cotangents.  Prints one JSON line.  Under torchrun each rank runs the same per-GPU batch
+(weak scaling, no data-path collective); the time is the max over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|tf32|bf16|fp32_simt]
+  python bench.py --impl reference ...   # the FP64 oracle on the host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(N=2 ** 16, J=12, Q=16, J_fr=4, Q_fr=2, T=2 ** 12, F=16)
+BATCH = 64
+METRIC = "JTFS fwd+bwd signals/sec (B=64, N=2^16, Q=16) at rel err <=1e-4; % HBM roofline"
+WORKLOAD_NAME = ("jtfs fwd+bwd, B=64 AM/FM tones, N=2^16 at 22050 Hz, J=12, Q=16, Q2=1, "
+                 "J_fr=4, Q_fr=2, T=2^12, F=16, oversampling 0")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                  "sm_max_mhz": 2070.0}
+SMS = 152
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return FALLBACK_PEAKS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def contraction_flops(plan_shapes, schedule, B):
+    """Algorithmic FLOPs of the log-frequency contractions in one forward + backward step:
+    the forward Z = W_c Y_alpha, the backward's recomputation of Z and gY = W_c^H gZ; each is
+    C * n1 * K_alpha * L_alpha complex multiply-adds (8 real flops) per signal."""
+    s1, s2, lm = schedule
+    n1, C, N = plan_shapes.n1, plan_shapes.C, plan_shapes.N
+    per = 0
+    for a in range(len(s2)):
+        if s2[a] == 0:
+            continue
+        per += C * n1 * (n1 - int(lm[a])) * (N // int(s2[a]))
+    return 8 * per * B
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import synth_signals as SS
+    from paper_2204_08269_gb300 import JTFSPlan, build
+
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    plan = JTFSPlan(**WORKLOAD, precision=args.precision)
+    sh = plan.shapes
+    x = torch.from_numpy(SS.workload_signals(2, BATCH, WORKLOAD["N"])).cuda()
+    gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
+    g0 = torch.randn(sh.s0(BATCH), device="cuda", generator=gen)
+    g1 = torch.randn(sh.s1(BATCH), device="cuda", generator=gen)
+    g2 = torch.randn(sh.s2(BATCH), device="cuda", generator=gen)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        s0, s1, s2, u1 = plan.forward(x)
+        gx = plan.backward(x, u1, g0, g1, g2)
+        return gx
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.profile_read()  # reset counters
+    plan.profile(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))          # evict L2 between timed steps (outside the events)
+            starts[i].record()
+            step()
+            ends[i].record()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    stages, launches = plan.profile_read()
+    plan.profile(False)
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = BATCH * world / (ms_max / 1e3)
+
+    # end to end through the host-buffer entry point (H2D, fwd, bwd, D2H in one call)
+    xh = torch.from_numpy(SS.workload_signals(2, BATCH, WORKLOAD["N"])).pin_memory()
+    gh = [g.cpu().pin_memory() for g in (g0, g1, g2)]
+    for _ in range(max(1, min(args.warmup, 2))):
+        plan.forward_backward_host(xh, *gh)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        o = plan.forward_backward_host(xh, *gh)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = xh.numel() * 4 + sum(g.numel() * 4 for g in gh)
+    d2h = sum(t.numel() * 4 for t in o)
+
+    peaks, peaks_kind = _peaks()
+    sched = plan.schedule()
+    flops = contraction_flops(sh, sched, BATCH)
+    joint_ms = (stages["joint_fwd"] + stages["joint_bwd"]) / args.steps
+    clocks = clk.summary()
+    if args.precision == "fp32_simt":
+        # plain FP32 on CUDA cores: 128 FMA lanes per SM at the maximum SM clock
+        peak = SMS * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": "joint_fwd+joint_bwd (contraction, CUDA cores)",
+                "achieved": flops / (joint_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                "traffic": None}
+    else:
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        if args.precision == "tf32":
+            peak = peak / 2.0
+        roof = {"bound": "tensor", "kernel": "joint_fwd+joint_bwd (tcgen05 contraction)",
+                "achieved": flops / (joint_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"{peaks_kind} bf16 sustained" + (" / 2 (tf32)" if args.precision == "tf32" else ""),
+                "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["launch_ms"] = joint_ms
+    roof["flops_per_step"] = flops
+    out = None
+    if rank == 0:
+        cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
+        out = {
+            "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision in ("fp32", "fp32_simt") else args.precision,
+            "data": "synthetic (seeded AM/FM tones + -30 dB noise)",
+            "config": {"workload": WORKLOAD_NAME, "global_batch": BATCH * world,
+                       "batch_per_gpu": BATCH, "N": WORKLOAD["N"], "precision": args.precision,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "flushed by a 256 MiB write before every timed step"},
+            "roofline": roof,
+            "stage_ms_per_step": {k: v / args.steps for k, v in stages.items()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": BATCH / e2e_s, "unit": "signals/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "how": "jtfs_forward_backward_host on pinned host buffers, wall clock"},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "peaks": peaks_kind,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def _oracle_sample(n_signals):
+    """FP64 oracle forward + backward of ``n_signals`` signals of the workload; seconds."""
+    import synth_signals as SS
+    from oracle import jtfs_oracle as O
+    cfg = O.Config(**{k: WORKLOAD[k] for k in ("J", "Q", "J_fr", "Q_fr", "T", "F", "N")})
+    p = O.Plan(cfg)
+    s = O.Schedule(p, 0)
+    x = SS.workload_signals(2, n_signals, cfg.N).astype(np.float64)
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    for b in range(n_signals):
+        out = O.forward_one(x[b], p, s)
+        g = {k: rng.standard_normal(v.shape) for k, v in out.items()}
+        O.backward_one(x[b], g["S0"], g["S1"], g["S2"], p, s)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args, n_signals=3):
+    secs = _oracle_sample(n_signals)
+    return {"value": n_signals / secs, "unit": "signals/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{n_signals} of the 64 signals, FP64 NumPy oracle forward + backward "
+                      "(SCHEDULED mode), one signal at a time; BLAS threads = all cores"}
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return None
+    # warm-up: one untimed signal at most (each is seconds of CPU work)
+    for _ in range(min(args.warmup, 1)):
+        _oracle_sample(1)
+    secs = 0.0
+    for _ in range(args.steps):
+        secs += _oracle_sample(1)
+    value = args.steps / secs
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "signals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded AM/FM tones)",
+        "config": {"workload": WORKLOAD_NAME, "global_batch": BATCH, "N": WORKLOAD["N"]},
+        "cpu_baseline": {"value": value, "unit": "signals/s", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": "1 signal of the 64 per step, FP64 oracle forward + backward"},
+        "e2e": {"value": value, "unit": "signals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "fp32_simt"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,146 @@
+/*
+ * jtfs.h -- C ABI of libjtfs: joint time-frequency scattering (JTFS) forward and backward
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * The operation is the transform of "Differentiable time-frequency scattering on GPU"
+ * (Muradeli et al., DAFx 2022):
+ *   Sec. 2     first-order scalogram X(t, lambda) = |x * psi_lambda|(t), analytic Morlet filters;
+ *              S0 = x * phi_T and S1 = X * phi_T, subsampled every T samples (no frequential
+ *              averaging on S1, Sec. 4.2).
+ *   Eq. 1      psi_alpha(t) = 2^alpha psi(2^alpha t); psi_{beta,theta}(lambda) = 2^beta psi(theta 2^beta lambda).
+ *   Eq. 2      joint wavelet Psi_{alpha,beta,theta}(t, lambda) = psi_alpha(t) psi_{beta,theta}(lambda).
+ *   Eq. 3      S2 = (|X *_{t,lambda} Psi| *_{t,lambda} Phi_{T,F}), sampled every (T, 2^floor(log2 F)).
+ *   Eq. 4      the same with time-only averaging (average_fr = 0).
+ *   Sec. 5     the gradient with respect to x by reverse-ordered adjoints.
+ * The discretisation (filterbank rule, critical-subsampling schedule) is documented in the
+ * repository's design notes; the library and its FP64 test oracle implement the same rules
+ * independently.
+ *
+ * Conventions for every call:
+ *   - Device pointers point to memory of the plan's device; "host" pointers to host memory.
+ *   - Buffers are owned by the caller; the plan owns only its filter tables.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).  They validate their arguments on the host and return
+ *     a status; nothing throws across the ABI.  Kernel faults surface as JTFS_ERR_CUDA from
+ *     the call that observes them (or from jtfs_sync_status).
+ *   - jtfs_last_error() returns a per-thread message describing the last non-OK status.
+ *   - All float buffers are contiguous, C order, float32.
+ */
+#ifndef JTFS_H
+#define JTFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  JTFS_OK = 0,
+  JTFS_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad configuration value */
+  JTFS_ERR_UNSUPPORTED = 2,   /* valid configuration outside what the kernels handle */
+  JTFS_ERR_WORKSPACE = 3,     /* workspace missing or smaller than jtfs_workspace_bytes */
+  JTFS_ERR_CUDA = 4,          /* a CUDA runtime call or kernel failed */
+  JTFS_ERR_TIMEOUT = 5,       /* a bounded device wait gave up */
+  JTFS_ERR_NUMERIC = 6        /* non-finite values where finite ones are required */
+} jtfs_status;
+
+/* Arithmetic of the log-frequency contraction (the dense lambda-contraction of Eq. 2-3).
+ * Every other step (FFTs, filter products, modulus, pooling) is FP32 on CUDA cores. */
+typedef enum {
+  JTFS_PREC_FP32 = 0,       /* tensor cores, bf16 hi/lo split in three passes, FP32 accumulate */
+  JTFS_PREC_TF32 = 1,       /* tensor cores, one TF32 pass, FP32 accumulate */
+  JTFS_PREC_BF16 = 2,       /* tensor cores, one BF16 pass, FP32 accumulate */
+  JTFS_PREC_FP32_SIMT = 3   /* CUDA cores, plain FP32 (the comparison form) */
+} jtfs_precision;
+
+/* Sec. 4.2 parameters.  T and F must be >= 1; T a power of two <= N.  Q2 is the number of
+ * second-order time wavelets per octave (1 in the paper).  oversampling o >= 0 divides every
+ * subsampling stride by 2^o. */
+typedef struct {
+  int32_t J, Q, Q2, J_fr, Q_fr;
+  int64_t T, F;
+  int32_t average_fr;    /* 1: Eq. 3 (phi_F pooling, lambda stride 2^floor(log2 F)); 0: Eq. 4 */
+  int32_t oversampling;
+  int32_t precision;     /* jtfs_precision */
+  int32_t reserved[5];   /* must be 0 */
+} jtfs_config;
+
+/* Output sizes.  S0 [B, n_t]; S1 [B, n1, n_t]; S2 [B, n2, C, n_lam_out, n_t] with channel
+ * c < n_fr = (beta = c, theta = +1), n_fr <= c < 2 n_fr = (beta = c - n_fr, theta = -1),
+ * c = 2 n_fr = the psi_t x phi_F branch.  lambda increases with frequency (theta = -1 is an
+ * upward slope, Sec. 2).  u1_len is the checkpointed scalogram's length per signal (rows
+ * packed at their own strides). */
+typedef struct {
+  int64_t N, n1, n2, n_fr, C, n_t, n_lam_out, N_fr, s_F;
+  int64_t s0_len, s1_len, s2_len, u1_len;
+} jtfs_shapes;
+
+typedef struct jtfs_plan jtfs_plan;
+
+/* Builds the filterbanks (FP64 on the current CUDA device, Sec. 2 / Eq. 1 with the
+ * Littlewood-Paley normalisation) and the subsampling schedule for signals of length N
+ * (a power of two).  Synchronous.  On success *out owns device memory until
+ * jtfs_plan_destroy.  Errors: INVALID_ARG (bad values), UNSUPPORTED (e.g. a row longer
+ * than the shared-memory FFT), CUDA. */
+jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out);
+void jtfs_plan_destroy(jtfs_plan* plan);
+
+jtfs_status jtfs_plan_shapes(const jtfs_plan* plan, jtfs_shapes* out);
+
+/* The schedule, for inspection: s1[n1] first-order strides, s2[n2] second-order strides
+ * (0 for a skipped rate), lam_min[n2] first row used by each rate.  Host arrays. */
+jtfs_status jtfs_plan_schedule(const jtfs_plan* plan, int32_t* s1, int32_t* s2,
+                               int32_t* lam_min);
+
+/* Device workspace bytes for a batch of B signals; with_grad != 0 also covers
+ * jtfs_backward. */
+jtfs_status jtfs_workspace_bytes(const jtfs_plan* plan, int64_t B, int32_t with_grad,
+                                 size_t* out);
+
+/* Forward transform of x [B, N] (device).  Writes s0, s1, s2 (device, sizes from
+ * jtfs_plan_shapes).  u1_ckpt (device, [B, u1_len]) receives the first-order scalogram
+ * checkpoint when not NULL; jtfs_backward needs it.  B = 0 is a no-op. */
+jtfs_status jtfs_forward(const jtfs_plan* plan, const float* x, int64_t B, float* s0, float* s1,
+                         float* s2, float* u1_ckpt, void* ws, size_t ws_bytes, void* stream);
+
+/* Backward: g_x [B, N] = d<g, S(x)>/dx for cotangents g_s0, g_s1, g_s2 (device, same shapes
+ * as the outputs; any may be NULL for zero).  Needs the forward's u1_ckpt for the same x.
+ * The modulus Jacobian d|z| = Re(conj(z) dz) / |z| is taken as 0 at z = 0. */
+jtfs_status jtfs_backward(const jtfs_plan* plan, const float* x, const float* u1_ckpt,
+                          int64_t B, const float* g_s0, const float* g_s1, const float* g_s2,
+                          float* g_x, void* ws, size_t ws_bytes, void* stream);
+
+/* End-to-end forward + backward from HOST buffers: copies x (host, [B, N]) and the
+ * cotangents (host; NULL = zero) to the device, runs jtfs_forward and jtfs_backward, and
+ * copies s0, s1, s2 (host, may be NULL) and g_x (host) back.  dev_buf must hold
+ * jtfs_host_step_bytes(plan, B) bytes of device memory; ws as for with_grad = 1.
+ * Synchronous on return. */
+jtfs_status jtfs_host_step_bytes(const jtfs_plan* plan, int64_t B, size_t* out);
+jtfs_status jtfs_forward_backward_host(const jtfs_plan* plan, const float* x_host, int64_t B,
+                                       const float* g_s0_host, const float* g_s1_host,
+                                       const float* g_s2_host, float* s0_host, float* s1_host,
+                                       float* s2_host, float* g_x_host, void* dev_buf,
+                                       size_t dev_buf_bytes, void* ws, size_t ws_bytes,
+                                       void* stream);
+
+/* Tracing: when enabled, forward/backward record a CUDA event pair around each stage on
+ * the launching stream.  jtfs_profile_read waits for the recorded events, writes the
+ * milliseconds accumulated per stage into ms[0..n_ms) (stage i is named by
+ * jtfs_profile_stage_name(i), NULL past the last stage), writes the number of kernels
+ * launched since the previous read (counted whether or not tracing is on), and resets both. */
+jtfs_status jtfs_profile_enable(const jtfs_plan* plan, int32_t on);
+jtfs_status jtfs_profile_read(const jtfs_plan* plan, double* ms, int32_t n_ms, int64_t* launches);
+const char* jtfs_profile_stage_name(int32_t i);
+
+/* Waits for the stream and reports any pending device error. */
+jtfs_status jtfs_sync_status(const jtfs_plan* plan, void* stream);
+
+const char* jtfs_status_string(jtfs_status s);
+const char* jtfs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JTFS_H */

@@ -1,0 +1,518 @@
+// C ABI of libjtfs (include/jtfs.h): plan construction on the host (filterbank rule,
+// subsampling schedule, table layout), argument validation and launch sequencing.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace jtfs {
+
+thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+jtfs_status cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return JTFS_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return JTFS_ERR_CUDA;
+}
+
+namespace {
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(long long v) {
+  int l = 0;
+  while ((1LL << l) < v) ++l;
+  return l;
+}
+
+// Morlet bank of Sec. 2 / Eq. 1 under the repository's filterbank rule: constant-Q centre
+// frequencies xi_0 2^{-k/Q} with widths rho xi (neighbours cross at half maximum) while the
+// width stays >= sigma_min = 0.1 2^-J, then a linearly spaced tail of width sigma_min spaced
+// one full width at half maximum apart.  Highest frequency first.
+bool morlet_bank(int J, int Q, std::vector<double>& xi, std::vector<double>& sg) {
+  const double fwhm = 2.0 * std::sqrt(2.0 * std::log(2.0));
+  const double rho = (1.0 - std::pow(2.0, -1.0 / Q)) / fwhm;
+  const double xi0 = std::min(0.35, 0.5 / (1.0 + 4.0 * rho));
+  const double smin = 0.1 * std::pow(2.0, -(double)J);
+  xi.clear();
+  sg.clear();
+  for (int k = 0; k < 100000; ++k) {
+    const double x = xi0 * std::pow(2.0, -(double)k / Q);
+    if (rho * x < smin) break;
+    xi.push_back(x);
+    sg.push_back(rho * x);
+  }
+  if (xi.empty()) return false;
+  const double delta = fwhm * smin;
+  const double xl = xi.back();
+  for (int m = 1; m < 100000; ++m) {
+    const double x = xl - m * delta;
+    if (x < delta) break;
+    xi.push_back(x);
+    sg.push_back(smin);
+  }
+  return true;
+}
+
+int pow2_stride(double v, int o, long long cap) {
+  const int e = v > 0 ? (int)std::floor(std::log2(v)) : 0;
+  const long long s = 1LL << std::max(0, e - o);
+  return (int)std::min(cap, s);
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+jtfs_status validate_cfg(const jtfs_config* c, int64_t N) {
+  if (!c) { set_error("cfg is NULL"); return JTFS_ERR_INVALID_ARG; }
+  if (!is_pow2(N) || N < 16 || N > (1LL << 20)) {
+    set_error("N must be a power of two in [16, 2^20]");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  if (c->J < 1 || c->J > 24 || c->Q < 1 || c->Q > 64 || c->Q2 < 1 || c->Q2 > 64 ||
+      c->J_fr < 1 || c->J_fr > 16 || c->Q_fr < 1 || c->Q_fr > 64) {
+    set_error("J, Q, Q2, J_fr, Q_fr out of range");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  if (!is_pow2(c->T) || c->T > N) { set_error("T must be a power of two <= N"); return JTFS_ERR_INVALID_ARG; }
+  if (c->F < 1 || c->F > (1 << 16)) { set_error("F must be in [1, 65536]"); return JTFS_ERR_INVALID_ARG; }
+  if (c->average_fr != 0 && c->average_fr != 1) { set_error("average_fr must be 0 or 1"); return JTFS_ERR_INVALID_ARG; }
+  if (c->oversampling < 0 || c->oversampling > 16) { set_error("oversampling must be in [0, 16]"); return JTFS_ERR_INVALID_ARG; }
+  if (c->precision < 0 || c->precision > 3) { set_error("unknown precision"); return JTFS_ERR_INVALID_ARG; }
+  for (int i = 0; i < 5; ++i)
+    if (c->reserved[i] != 0) { set_error("reserved fields must be 0"); return JTFS_ERR_INVALID_ARG; }
+  return JTFS_OK;
+}
+
+}  // namespace
+
+bool joint_simt_supported(const jtfs_plan* p);
+size_t joint_fwd_smem(const jtfs_plan* p);
+size_t joint_bwd_smem(const jtfs_plan* p);
+
+static cudaEvent_t take_event(Profiler& pr) {
+  if (!pr.pool.empty()) {
+    cudaEvent_t e = pr.pool.back();
+    pr.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+StageScope::StageScope(const jtfs_plan* p_, int stage_, cudaStream_t st_, int n_launch)
+    : p(p_), stage(stage_), st(st_) {
+  p->prof.launches += n_launch;
+  if (p->prof.on) {
+    a = take_event(p->prof);
+    if (a) cudaEventRecord(a, st);
+  }
+}
+
+StageScope::~StageScope() {
+  if (!a) return;
+  cudaEvent_t b = take_event(p->prof);
+  if (!b) return;
+  cudaEventRecord(b, st);
+  p->prof.recs.push_back(ProfRec{stage, a, b});
+}
+
+size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* base, Workspace* w) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* ptr = base ? base + off : nullptr;
+    off += align256(bytes);
+    return ptr;
+  };
+  const size_t Bz = (size_t)B;
+  Workspace tmp;
+  Workspace& W = w ? *w : tmp;
+  W.xh = (float2*)take(Bz * (p->N / 2) * 8);
+  W.xsub = (float2*)take(Bz * p->N * 8);
+  W.u1 = (float*)take(Bz * p->u1_len * 4);
+  W.uh = (float2*)take(Bz * p->uh_len * 8);
+  W.y = (float2*)take(Bz * p->y_len * 8);
+  W.gy = nullptr;
+  W.gu1 = nullptr;
+  W.gf = nullptr;
+  W.gxh = nullptr;
+  if (with_grad) {
+    W.gy = (float2*)take(Bz * p->y_len * 8);
+    W.gu1 = (float*)take(Bz * p->u1_len * 4);
+    W.gf = (float2*)take(Bz * p->u1_len * 8);
+    W.gxh = (float2*)take(Bz * (p->N / 2) * 8);
+  }
+  return off;
+}
+
+}  // namespace jtfs
+
+using namespace jtfs;
+
+extern "C" {
+
+const char* jtfs_status_string(jtfs_status s) {
+  switch (s) {
+    case JTFS_OK: return "ok";
+    case JTFS_ERR_INVALID_ARG: return "invalid argument";
+    case JTFS_ERR_UNSUPPORTED: return "unsupported configuration";
+    case JTFS_ERR_WORKSPACE: return "workspace too small";
+    case JTFS_ERR_CUDA: return "CUDA error";
+    case JTFS_ERR_TIMEOUT: return "device wait timed out";
+    case JTFS_ERR_NUMERIC: return "non-finite values";
+  }
+  return "unknown status";
+}
+
+const char* jtfs_last_error(void) { return g_last_error.c_str(); }
+
+void jtfs_plan_destroy(jtfs_plan* p) {
+  if (!p) return;
+  for (auto& r : p->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : p->prof.pool) cudaEventDestroy(e);
+  if (p->d_mem) cudaFree(p->d_mem);
+  delete p;
+}
+
+jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out) {
+  if (!out) { set_error("out is NULL"); return JTFS_ERR_INVALID_ARG; }
+  *out = nullptr;
+  jtfs_status st = validate_cfg(cfg, N);
+  if (st != JTFS_OK) return st;
+  jtfs_plan* p = new (std::nothrow) jtfs_plan();
+  if (!p) { set_error("out of host memory"); return JTFS_ERR_INVALID_ARG; }
+  p->cfg = *cfg;
+  p->N = N;
+  p->d_mem = nullptr;
+  if ((st = cuda_check(cudaGetDevice(&p->device), "cudaGetDevice")) != JTFS_OK) {
+    delete p;
+    return st;
+  }
+  auto fail = [&](jtfs_status s, const std::string& m) {
+    if (!m.empty()) set_error(m);
+    jtfs_plan_destroy(p);
+    return s;
+  };
+  // --- filterbanks (lambda ascending in frequency; alpha and beta highest first) ---
+  std::vector<double> xi, sg;
+  if (!morlet_bank(cfg->J, cfg->Q, xi, sg)) return fail(JTFS_ERR_INVALID_ARG, "first-order bank is empty");
+  p->xi1.assign(xi.rbegin(), xi.rend());
+  p->sg1.assign(sg.rbegin(), sg.rend());
+  if (!morlet_bank(cfg->J, cfg->Q2, p->xi2, p->sg2)) return fail(JTFS_ERR_INVALID_ARG, "second-order bank is empty");
+  if (!morlet_bank(cfg->J_fr, cfg->Q_fr, p->xi_fr, p->sg_fr)) return fail(JTFS_ERR_INVALID_ARG, "frequential bank is empty");
+  p->n1 = (int)p->xi1.size();
+  p->n2 = (int)p->xi2.size();
+  p->n_fr = (int)p->xi_fr.size();
+  p->C = 2 * p->n_fr + 1;
+  p->n_t = (int)(N / cfg->T);
+  p->N_fr = 2 * (1 << ilog2(p->n1));
+  p->s_F = 1 << (int)std::floor(std::log2((double)cfg->F));
+  p->n_lo = cfg->average_fr ? (p->n1 + p->s_F - 1) / p->s_F : p->n1;
+  // --- schedule (first order: envelope bandwidth 8 sigma per row) ---
+  const int o = cfg->oversampling;
+  p->rows1.resize(p->n1);
+  long long off_u = 0, off_uh = 0, off_v = 0;
+  int smin = (int)cfg->T;
+  p->L1max = 0;
+  for (int l = 0; l < p->n1; ++l) {
+    Row1& r = p->rows1[l];
+    r.s = pow2_stride(1.0 / (16.0 * p->sg1[l]), o, cfg->T);
+    r.L = (int)(N / r.s);
+    r.logL = ilog2(r.L);
+    if (r.logL > kMaxLogL)
+      return fail(JTFS_ERR_UNSUPPORTED, "a first-order row is longer than 2^14 samples (lower the oversampling)");
+    r.off_u = (int)off_u;
+    r.off_uh = (int)off_uh;
+    off_u += r.L;
+    off_uh += std::max(1, r.L / 2);
+    const double lo = (p->xi1[l] - kSupportSigmas * p->sg1[l]) * (double)N;
+    const double hi = (p->xi1[l] + kSupportSigmas * p->sg1[l]) * (double)N;
+    r.ks = std::max(1, (int)std::ceil(lo));
+    const int ke = std::min((int)(N / 2 - 1), (int)std::floor(hi));
+    r.kl = std::max(0, ke - r.ks + 1);
+    r.off_v = (int)off_v;
+    off_v += r.kl;
+    smin = std::min(smin, r.s);
+    p->L1max = std::max(p->L1max, r.L);
+  }
+  p->u1_len = off_u;
+  p->uh_len = off_uh;
+  const double nyq = 0.5 / (double)smin;
+  p->rates2.resize(p->n2);
+  long long off_y = 0;
+  p->L2max = 1;
+  p->pairs.clear();
+  p->items.clear();
+  for (int a = 0; a < p->n2; ++a) {
+    Rate2& A = p->rates2[a];
+    const double lo = std::max(0.0, p->xi2[a] - kBandSigmas * p->sg2[a]);
+    const double hi = std::min(p->xi2[a] + kBandSigmas * p->sg2[a], nyq);
+    A.off_y = off_y;
+    if (lo >= hi) {
+      A.s = 0; A.L = 0; A.logL = 0; A.lam_min = p->n1; A.K = 0;
+      continue;
+    }
+    A.s = pow2_stride(1.0 / (2.0 * (hi - lo)), o, cfg->T);
+    A.L = (int)(N / A.s);
+    A.logL = ilog2(A.L);
+    if (A.logL > kMaxLogL)
+      return fail(JTFS_ERR_UNSUPPORTED, "a second-order row is longer than 2^14 samples (lower the oversampling)");
+    int lm = p->n1;
+    for (int l = 0; l < p->n1; ++l)
+      if (0.5 / (double)p->rows1[l].s > lo) { lm = l; break; }
+    A.lam_min = lm;
+    A.K = p->n1 - lm;
+    off_y += (long long)A.K * A.L;
+    p->L2max = std::max(p->L2max, A.L);
+    for (int l = lm; l < p->n1; ++l) { p->pairs.push_back(a); p->pairs.push_back(l); }
+    for (int n0 = 0; n0 < A.L; n0 += 32) { p->items.push_back(a); p->items.push_back(n0); }
+  }
+  p->y_len = off_y;
+  if (!joint_simt_supported(p)) return fail(JTFS_ERR_UNSUPPORTED, "n1 or n1 * n_t too large for the joint-stage kernel");
+  // --- device tables ---
+  DevPlan& d = p->dp;
+  d.N = (int)N; d.logN = ilog2(N); d.T = (int)cfg->T; d.n_t = p->n_t; d.n1 = p->n1; d.n2 = p->n2;
+  d.n_fr = p->n_fr; d.C = p->C; d.N_fr = p->N_fr; d.s_F = p->s_F; d.n_lo = p->n_lo;
+  d.average_fr = cfg->average_fr;
+  d.TW = (int)N; d.logTW = d.logN;
+  d.M = (int)std::min<int64_t>(N, 8192); d.logM = ilog2(d.M); d.D = (int)(N / d.M);
+  d.K2max = std::max(1, p->L1max / 2);
+  d.u1_len = p->u1_len; d.uh_len = p->uh_len; d.y_len = p->y_len;
+  // lambda range per 256-bin block of x-hat (for the gradient gather)
+  const int nblk = (int)((N / 2 + 255) / 256);
+  std::vector<int2> gxl(nblk);
+  for (int bl = 0; bl < nblk; ++bl) {
+    int lo = p->n1, hi = 0;
+    const int k0 = bl * 256, k1 = k0 + 256;
+    for (int l = 0; l < p->n1; ++l) {
+      const Row1& r = p->rows1[l];
+      if (r.kl > 0 && r.ks < k1 && r.ks + r.kl > k0) { lo = std::min(lo, l); hi = std::max(hi, l + 1); }
+    }
+    gxl[bl] = make_int2(lo < hi ? lo : 0, lo < hi ? hi : 0);
+  }
+  std::vector<float2> tw(N);
+  for (long long j = 0; j < N; ++j) {
+    const double ang = 2.0 * M_PI * (double)j / (double)N;
+    tw[j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+  }
+  // layout of one device allocation
+  size_t off = 0;
+  auto place = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
+  const size_t o_rows = place(sizeof(Row1) * p->n1);
+  const size_t o_rates = place(sizeof(Rate2) * p->n2);
+  const size_t o_psi1 = place(sizeof(float) * std::max<long long>(1, off_v));
+  const size_t o_psi2 = place(sizeof(float) * (size_t)p->n2 * d.K2max);
+  const size_t o_phiT = place(sizeof(float) * N);
+  const size_t o_phiF = place(sizeof(float) * p->N_fr);
+  const size_t o_h = place(sizeof(float2) * (size_t)p->C * p->N_fr);
+  const size_t o_tw = place(sizeof(float2) * N);
+  const size_t o_gx = place(sizeof(int2) * nblk);
+  const size_t o_pairs = place(sizeof(int) * std::max<size_t>(2, p->pairs.size()));
+  const size_t o_items = place(sizeof(int) * std::max<size_t>(2, p->items.size()));
+  p->d_bytes = off;
+  if ((st = cuda_check(cudaMalloc(&p->d_mem, off), "plan tables")) != JTFS_OK) return fail(st, "");
+  char* base = (char*)p->d_mem;
+  d.rows1 = (const Row1*)(base + o_rows);
+  d.rates2 = (const Rate2*)(base + o_rates);
+  d.psi1 = (const float*)(base + o_psi1);
+  d.psi2 = (const float*)(base + o_psi2);
+  d.phiT = (const float*)(base + o_phiT);
+  d.phiF = (const float*)(base + o_phiF);
+  d.h = (const float2*)(base + o_h);
+  d.tw = (const float2*)(base + o_tw);
+  d.gx_lam = (const int2*)(base + o_gx);
+  p->d_pairs = (int*)(base + o_pairs);
+  p->d_items = (int*)(base + o_items);
+  struct Up { size_t at; const void* src; size_t bytes; } ups[] = {
+      {o_rows, p->rows1.data(), sizeof(Row1) * p->n1},
+      {o_rates, p->rates2.data(), sizeof(Rate2) * p->n2},
+      {o_tw, tw.data(), sizeof(float2) * N},
+      {o_gx, gxl.data(), sizeof(int2) * nblk},
+      {o_pairs, p->pairs.data(), sizeof(int) * p->pairs.size()},
+      {o_items, p->items.data(), sizeof(int) * p->items.size()},
+  };
+  for (const Up& u : ups)
+    if (u.bytes && (st = cuda_check(cudaMemcpy(base + u.at, u.src, u.bytes, cudaMemcpyHostToDevice),
+                                    "plan upload")) != JTFS_OK)
+      return fail(st, "");
+  if ((st = build_tables(p)) != JTFS_OK) return fail(st, "");
+  *out = p;
+  return JTFS_OK;
+}
+
+jtfs_status jtfs_plan_shapes(const jtfs_plan* p, jtfs_shapes* s) {
+  if (!p || !s) { set_error("NULL argument"); return JTFS_ERR_INVALID_ARG; }
+  s->N = p->N; s->n1 = p->n1; s->n2 = p->n2; s->n_fr = p->n_fr; s->C = p->C; s->n_t = p->n_t;
+  s->n_lam_out = p->n_lo; s->N_fr = p->N_fr; s->s_F = p->s_F;
+  s->s0_len = p->n_t;
+  s->s1_len = (int64_t)p->n1 * p->n_t;
+  s->s2_len = (int64_t)p->n2 * p->C * p->n_lo * p->n_t;
+  s->u1_len = p->u1_len;
+  return JTFS_OK;
+}
+
+jtfs_status jtfs_plan_schedule(const jtfs_plan* p, int32_t* s1, int32_t* s2, int32_t* lam_min) {
+  if (!p) { set_error("NULL plan"); return JTFS_ERR_INVALID_ARG; }
+  for (int l = 0; l < p->n1 && s1; ++l) s1[l] = p->rows1[l].s;
+  for (int a = 0; a < p->n2; ++a) {
+    if (s2) s2[a] = p->rates2[a].s;
+    if (lam_min) lam_min[a] = p->rates2[a].lam_min;
+  }
+  return JTFS_OK;
+}
+
+jtfs_status jtfs_workspace_bytes(const jtfs_plan* p, int64_t B, int32_t with_grad, size_t* out) {
+  if (!p || !out || B < 0) { set_error("bad argument"); return JTFS_ERR_INVALID_ARG; }
+  *out = workspace_layout(p, B, with_grad != 0, nullptr, nullptr);
+  return JTFS_OK;
+}
+
+static jtfs_status check_device(const jtfs_plan* p) {
+  int dev = -1;
+  jtfs_status st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (st != JTFS_OK) return st;
+  if (dev != p->device) { set_error("current device differs from the plan's device"); return JTFS_ERR_INVALID_ARG; }
+  return JTFS_OK;
+}
+
+jtfs_status jtfs_forward(const jtfs_plan* p, const float* x, int64_t B, float* s0, float* s1,
+                         float* s2, float* u1_ckpt, void* ws, size_t ws_bytes, void* stream) {
+  if (!p || B < 0 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
+  if (B == 0) return JTFS_OK;
+  if (!x || !s0 || !s1 || !s2) { set_error("NULL input or output"); return JTFS_ERR_INVALID_ARG; }
+  jtfs_status st = check_device(p);
+  if (st != JTFS_OK) return st;
+  const size_t need = workspace_layout(p, B, false, nullptr, nullptr);
+  if (!ws || ws_bytes < need) {
+    set_error("workspace needs " + std::to_string(need) + " bytes");
+    return JTFS_ERR_WORKSPACE;
+  }
+  Workspace w;
+  workspace_layout(p, B, false, (char*)ws, &w);
+  return launch_forward(p, x, (int)B, s0, s1, s2, u1_ckpt ? u1_ckpt : w.u1, w,
+                        (cudaStream_t)stream);
+}
+
+jtfs_status jtfs_backward(const jtfs_plan* p, const float* x, const float* u1_ckpt, int64_t B,
+                          const float* g_s0, const float* g_s1, const float* g_s2, float* g_x,
+                          void* ws, size_t ws_bytes, void* stream) {
+  if (!p || B < 0 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
+  if (B == 0) return JTFS_OK;
+  if (!x || !u1_ckpt || !g_x) { set_error("NULL x, u1_ckpt or g_x"); return JTFS_ERR_INVALID_ARG; }
+  jtfs_status st = check_device(p);
+  if (st != JTFS_OK) return st;
+  const size_t need = workspace_layout(p, B, true, nullptr, nullptr);
+  if (!ws || ws_bytes < need) {
+    set_error("workspace needs " + std::to_string(need) + " bytes");
+    return JTFS_ERR_WORKSPACE;
+  }
+  Workspace w;
+  workspace_layout(p, B, true, (char*)ws, &w);
+  return launch_backward(p, x, u1_ckpt, (int)B, g_s0, g_s1, g_s2, g_x, w, (cudaStream_t)stream);
+}
+
+jtfs_status jtfs_host_step_bytes(const jtfs_plan* p, int64_t B, size_t* out) {
+  if (!p || !out || B < 0) { set_error("bad argument"); return JTFS_ERR_INVALID_ARG; }
+  const size_t Bz = (size_t)B;
+  size_t n = 0;
+  n += align256(Bz * p->N * 4) * 2;                             // x, g_x
+  n += align256(Bz * p->n_t * 4) * 2;                           // s0, g_s0
+  n += align256(Bz * (size_t)p->n1 * p->n_t * 4) * 2;           // s1, g_s1
+  n += align256(Bz * (size_t)p->n2 * p->C * p->n_lo * p->n_t * 4) * 2;  // s2, g_s2
+  n += align256(Bz * p->u1_len * 4);                            // checkpoint
+  *out = n;
+  return JTFS_OK;
+}
+
+jtfs_status jtfs_forward_backward_host(const jtfs_plan* p, const float* x_host, int64_t B,
+                                       const float* g_s0_host, const float* g_s1_host,
+                                       const float* g_s2_host, float* s0_host, float* s1_host,
+                                       float* s2_host, float* g_x_host, void* dev_buf,
+                                       size_t dev_buf_bytes, void* ws, size_t ws_bytes,
+                                       void* stream) {
+  if (!p || B < 0) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
+  if (B == 0) return JTFS_OK;
+  if (!x_host || !g_x_host) { set_error("NULL x or g_x"); return JTFS_ERR_INVALID_ARG; }
+  size_t need = 0;
+  jtfs_host_step_bytes(p, B, &need);
+  if (!dev_buf || dev_buf_bytes < need) { set_error("dev_buf too small"); return JTFS_ERR_WORKSPACE; }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t Bz = (size_t)B;
+  char* base = (char*)dev_buf;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* q = base + off; off += align256(bytes); return q; };
+  const size_t bx = Bz * p->N * 4, b0 = Bz * p->n_t * 4, b1 = Bz * (size_t)p->n1 * p->n_t * 4;
+  const size_t b2 = Bz * (size_t)p->n2 * p->C * p->n_lo * p->n_t * 4;
+  float* dx = (float*)take(bx);
+  float* dgx = (float*)take(bx);
+  float* ds0 = (float*)take(b0);
+  float* dg0 = (float*)take(b0);
+  float* ds1 = (float*)take(b1);
+  float* dg1 = (float*)take(b1);
+  float* ds2 = (float*)take(b2);
+  float* dg2 = (float*)take(b2);
+  float* du1 = (float*)take(Bz * p->u1_len * 4);
+  jtfs_status rc;
+  if ((rc = cuda_check(cudaMemcpyAsync(dx, x_host, bx, cudaMemcpyHostToDevice, st), "H2D x")) != JTFS_OK) return rc;
+  if (g_s0_host && (rc = cuda_check(cudaMemcpyAsync(dg0, g_s0_host, b0, cudaMemcpyHostToDevice, st), "H2D g_s0")) != JTFS_OK) return rc;
+  if (g_s1_host && (rc = cuda_check(cudaMemcpyAsync(dg1, g_s1_host, b1, cudaMemcpyHostToDevice, st), "H2D g_s1")) != JTFS_OK) return rc;
+  if (g_s2_host && (rc = cuda_check(cudaMemcpyAsync(dg2, g_s2_host, b2, cudaMemcpyHostToDevice, st), "H2D g_s2")) != JTFS_OK) return rc;
+  if ((rc = jtfs_forward(p, dx, B, ds0, ds1, ds2, du1, ws, ws_bytes, stream)) != JTFS_OK) return rc;
+  if ((rc = jtfs_backward(p, dx, du1, B, g_s0_host ? dg0 : nullptr, g_s1_host ? dg1 : nullptr,
+                          g_s2_host ? dg2 : nullptr, dgx, ws, ws_bytes, stream)) != JTFS_OK)
+    return rc;
+  if (s0_host && (rc = cuda_check(cudaMemcpyAsync(s0_host, ds0, b0, cudaMemcpyDeviceToHost, st), "D2H s0")) != JTFS_OK) return rc;
+  if (s1_host && (rc = cuda_check(cudaMemcpyAsync(s1_host, ds1, b1, cudaMemcpyDeviceToHost, st), "D2H s1")) != JTFS_OK) return rc;
+  if (s2_host && (rc = cuda_check(cudaMemcpyAsync(s2_host, ds2, b2, cudaMemcpyDeviceToHost, st), "D2H s2")) != JTFS_OK) return rc;
+  if ((rc = cuda_check(cudaMemcpyAsync(g_x_host, dgx, bx, cudaMemcpyDeviceToHost, st), "D2H g_x")) != JTFS_OK) return rc;
+  return cuda_check(cudaStreamSynchronize(st), "host step sync");
+}
+
+static const char* kStageNames[kNumStages] = {
+    "x_fft", "s0", "scalogram", "second_order", "joint_fwd", "uh_from_u1", "joint_bwd",
+    "second_order_bwd", "stage1_bwd", "gx"};
+
+jtfs_status jtfs_profile_enable(const jtfs_plan* p, int32_t on) {
+  if (!p) { set_error("NULL plan"); return JTFS_ERR_INVALID_ARG; }
+  p->prof.on = on != 0;
+  return JTFS_OK;
+}
+
+jtfs_status jtfs_profile_read(const jtfs_plan* p, double* ms, int32_t n_ms,
+                              int64_t* launches) {
+  if (!p || (n_ms > 0 && !ms)) { set_error("bad argument"); return JTFS_ERR_INVALID_ARG; }
+  for (int i = 0; i < n_ms; ++i) ms[i] = 0.0;
+  jtfs_status st = JTFS_OK;
+  for (auto& r : p->prof.recs) {
+    if (st == JTFS_OK) st = cuda_check(cudaEventSynchronize(r.b), "profile sync");
+    float t = 0.f;
+    if (st == JTFS_OK) st = cuda_check(cudaEventElapsedTime(&t, r.a, r.b), "profile elapsed");
+    if (st == JTFS_OK && r.stage < n_ms) ms[r.stage] += t;
+    p->prof.pool.push_back(r.a);
+    p->prof.pool.push_back(r.b);
+  }
+  p->prof.recs.clear();
+  if (launches) *launches = p->prof.launches;
+  p->prof.launches = 0;
+  return st;
+}
+
+const char* jtfs_profile_stage_name(int32_t i) {
+  return (i >= 0 && i < kNumStages) ? kStageNames[i] : nullptr;
+}
+
+jtfs_status jtfs_sync_status(const jtfs_plan* p, void* stream) {
+  if (!p) { set_error("NULL plan"); return JTFS_ERR_INVALID_ARG; }
+  jtfs_status st = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "stream sync");
+  if (st != JTFS_OK) return st;
+  return cuda_check(cudaGetLastError(), "pending error");
+}
+
+}  // extern "C"

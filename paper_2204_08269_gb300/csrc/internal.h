@@ -1,0 +1,134 @@
+// Internal declarations of libjtfs: the plan, per-row schedule records and kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/jtfs.h"
+
+namespace jtfs {
+
+constexpr int kMaxLogL = 14;          // longest row FFT kept in shared memory: 2^14 complex
+constexpr int kSupportSigmas = 8;     // band-pass filters are stored on xi +- 8 sigma (e^-32)
+constexpr int kBandSigmas = 4;        // band edges used by the subsampling schedule
+
+// One first-order row lambda (Sec. 2): stride, length, offsets and filter support.
+struct Row1 {
+  int s;        // stride s_lambda
+  int L;        // N / s
+  int logL;
+  int off_u;    // offset of the row in a packed [u1_len] float array
+  int off_uh;   // offset of the row's half spectrum (L/2 complex) in a packed array
+  int ks;       // first bin of the filter support on the N grid (>= 1)
+  int kl;       // number of support bins
+  int off_v;    // offset of the support values in the psi1 table
+};
+
+// One second-order time rate alpha (Eq. 1, Eq. 3): stride, length and contraction rows.
+struct Rate2 {
+  int s;        // stride s_alpha (0 when the rate is skipped)
+  int L;        // N / s
+  int logL;
+  int lam_min;  // first lambda' row with a non-zero Y_alpha row
+  int K;        // n1 - lam_min rows of Y_alpha
+  long long off_y;  // offset of Y_alpha (K x L complex) in a packed per-signal array
+};
+
+// Device-side constants of a plan (passed by value to kernels).
+struct DevPlan {
+  int N, logN, T, n_t, n1, n2, n_fr, C, N_fr, s_F, n_lo, average_fr;
+  int TW, logTW;          // twiddle table length (>= every FFT length and N)
+  int D, M, logM;         // decimation of the length-N FFT: N = D * M, M <= 2^kMaxLogL
+  int K2max;              // width of the psi2 table (bins 0..K2max-1 on the N grid)
+  long long u1_len, uh_len, y_len;
+  const Row1* rows1;      // [n1]
+  const Rate2* rates2;    // [n2]
+  const float* psi1;      // packed support values of psi1
+  const float* psi2;      // [n2][K2max]
+  const float* phiT;      // [N] time-domain lowpass phi_T[n]
+  const float* phiF;      // [N_fr] phi_F[m]
+  const float2* h;        // [C][N_fr] log-frequency filters h_c[m]
+  const float2* tw;       // [TW] exp(-2 pi i j / TW)
+  const int2* gx_lam;     // [N/2 / 256] lambda range touching each 256-bin block of x-hat
+};
+
+}  // namespace jtfs
+
+namespace jtfs {
+// Stages timed by the optional profiler (CUDA events on the launching stream).
+enum Stage {
+  kStXfft = 0, kStS0, kStScalogram, kStSecondOrder, kStJointFwd, kStUhFromU1, kStJointBwd,
+  kStSecondOrderBwd, kStStage1Bwd, kStGx, kNumStages
+};
+struct ProfRec { int stage; cudaEvent_t a, b; };
+struct Profiler {
+  bool on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  long long launches = 0;   // kernels launched by forward/backward calls
+};
+}  // namespace jtfs
+
+struct jtfs_plan {
+  jtfs_config cfg;
+  int64_t N;
+  int device;
+  int n1, n2, n_fr, C, n_t, N_fr, s_F, n_lo;
+  std::vector<double> xi1, sg1, xi2, sg2, xi_fr, sg_fr;  // lambda ascending; alpha, beta descending
+  double c1, c2, c_fr;
+  std::vector<jtfs::Row1> rows1;
+  std::vector<jtfs::Rate2> rates2;
+  std::vector<int> pairs;  // (alpha, lambda') work items of the second-order kernels
+  std::vector<int> items;  // (alpha, first column) work items of the joint backward
+  long long u1_len, uh_len, y_len;
+  int L1max, L2max;
+  jtfs::DevPlan dp;
+  // device allocations
+  void* d_mem;
+  size_t d_bytes;
+  int* d_pairs;
+  int* d_items;
+  mutable jtfs::Profiler prof;
+};
+
+namespace jtfs {
+
+void set_error(const std::string& msg);
+jtfs_status cuda_check(cudaError_t e, const char* what);
+
+// plan construction (kernels_plan.cu)
+jtfs_status build_tables(jtfs_plan* p);
+
+// forward / backward launchers (kernels_fwd.cu, kernels_bwd.cu)
+struct Workspace {
+  float2* xh;      // [B][N/2]
+  float2* xsub;    // [B][N]  (D sub-spectra of length M)
+  float* u1;       // [B][u1_len]
+  float2* uh;      // [B][uh_len]
+  float2* y;       // [B][y_len]
+  float2* gy;      // [B][y_len]
+  float* gu1;      // [B][u1_len]
+  float2* gf;      // [B][u1_len]  (per row L complex)
+  float2* gxh;     // [B][N/2]
+};
+size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* base, Workspace* w);
+
+// Records an event pair around a stage when profiling is on; counts launches always.
+struct StageScope {
+  const jtfs_plan* p;
+  int stage;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  StageScope(const jtfs_plan* p_, int stage_, cudaStream_t st_, int n_launch);
+  ~StageScope();
+};
+
+jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0, float* s1,
+                           float* s2, float* u1, const Workspace& w, cudaStream_t st);
+jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1, int B,
+                            const float* gs0, const float* gs1, const float* gs2, float* gx,
+                            const Workspace& w, cudaStream_t st);
+
+}  // namespace jtfs

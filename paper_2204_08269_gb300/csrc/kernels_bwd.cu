@@ -1,0 +1,361 @@
+// Backward JTFS kernels (Sec. 5: reverse-ordered adjoints of the forward operators), FP32
+// on CUDA cores.  Only the first-order scalogram U1 is checkpointed by the forward; the
+// backward recomputes x-hat, U1-hat, Y_alpha and Z, and the first-order coefficients z.
+//
+//   k_uh_from_u1       : U1-hat = FFT of every checkpointed U1 row
+//   k_joint_bwd_simt   : per (alpha, 32-column chunk, signal): for every channel c,
+//                        Z = W_c Y, g|Z| = adjoint of phi_T x phi_F pooling applied to g_S2,
+//                        gZ = g|Z| Z / |Z| (0 at Z = 0), gY += W_c^H gZ
+//   k_second_order_bwd : per (lambda', signal): sum over alpha of the adjoint of the
+//                        fold / inverse FFT / psi_alpha product, real part of the inverse of
+//                        the row FFT, plus the adjoint of S1's pooling -> g_U1 row
+//   k_stage1_bwd       : per (lambda, signal): recompute z, gz = g_U1 z / |z|, FFT -> gF
+//   k_gxh              : g_x-hat[k] = sum_lambda psi_lambda[k] gF_lambda[k mod L_lambda]
+//   k_gx               : g_x = Re(inverse DFT of g_x-hat) + adjoint of S0's pooling
+#include "stages.cuh"
+
+namespace jtfs {
+namespace {
+
+__global__ void __launch_bounds__(kFftThreads)
+k_uh_from_u1(DevPlan P, const float* __restrict__ u1, float2* __restrict__ uh) {
+  extern __shared__ float2 sm[];
+  const int lam = blockIdx.x, b = blockIdx.y;
+  const Row1 R = P.rows1[lam];
+  const float* ub = u1 + (size_t)b * P.u1_len + R.off_u;
+  for (int m = threadIdx.x; m < R.L; m += blockDim.x) sm[m] = make_float2(ub[m], 0.f);
+  __syncthreads();
+  fft_dif<-1>(sm, R.logL, P.tw, P.logTW);
+  float2* hb = uh + (size_t)b * P.uh_len + R.off_uh;
+  for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[bitrev(k, R.logL)];
+}
+
+// ---------------------------------------------------------------------------------------
+constexpr int kJT = 256;
+constexpr int kNC = 32;
+constexpr int kRPT = 8;
+
+__global__ void __launch_bounds__(kJT)
+k_joint_bwd_simt(DevPlan P, const int2* __restrict__ items, const float2* __restrict__ y,
+                 const float* __restrict__ gs2, float2* __restrict__ gy) {
+  extern __shared__ float4 smraw[];
+  const int2 it = items[blockIdx.x];
+  const int a = it.x, n0 = it.y, b = blockIdx.y;
+  const Rate2 A = P.rates2[a];
+  const int n1 = P.n1, nt = P.n_t, K = A.K, l0 = A.lam_min, nfm = P.N_fr - 1;
+  float2* sh = reinterpret_cast<float2*>(smraw);        // [N_fr]
+  float2* yt = sh + P.N_fr;                              // [K][kNC]
+  float2* gz = yt + (size_t)n1 * kNC;                    // [n1][kNC]
+  float* g1 = reinterpret_cast<float*>(gz + (size_t)n1 * kNC);  // [n1][n_t]
+  float* wt = g1 + (size_t)n1 * nt;                      // [n_t][kNC]
+  const float2* ya = y + (size_t)b * P.y_len + A.off_y;
+  for (int i = threadIdx.x; i < K * kNC; i += blockDim.x) {
+    const int k = i / kNC, col = i % kNC;
+    yt[i] = (n0 + col < A.L) ? ya[(size_t)k * A.L + n0 + col] : make_float2(0.f, 0.f);
+  }
+  for (int i = threadIdx.x; i < nt * kNC; i += blockDim.x) {
+    const int t = i / kNC, col = i % kNC;
+    const int n = n0 + col;
+    wt[i] = (n < A.L) ? __ldg(&P.phiT[(t * P.T - n * A.s) & (P.N - 1)]) * (float)A.s : 0.f;
+  }
+  const int ty = threadIdx.x >> 3, tx = threadIdx.x & 7;
+  float2 gacc[kRPT][4];
+#pragma unroll
+  for (int i = 0; i < kRPT; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) gacc[i][j] = make_float2(0.f, 0.f);
+
+  for (int c = 0; c < P.C; ++c) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < P.N_fr; i += blockDim.x) sh[i] = P.h[(size_t)c * P.N_fr + i];
+    const float* g = gs2 + (((size_t)b * P.n2 + a) * P.C + c) * (size_t)P.n_lo * nt;
+    for (int i = threadIdx.x; i < n1 * nt; i += blockDim.x) {
+      if (P.average_fr) {
+        const int r = i / nt, t = i % nt;
+        float s = 0.f;
+        for (int lo = 0; lo < P.n_lo; ++lo)
+          s += __ldg(&P.phiF[(lo * P.s_F - r) & nfm]) * g[lo * nt + t];
+        g1[i] = s;
+      } else {
+        g1[i] = g[i];
+      }
+    }
+    __syncthreads();
+    // Z = W_c Y for the thread's (row, column) outputs
+    float2 acc[kRPT][4];
+#pragma unroll
+    for (int i = 0; i < kRPT; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k = 0; k < K; ++k) {
+      const float4 y01 = reinterpret_cast<const float4*>(yt + k * kNC)[tx * 2];
+      const float4 y23 = reinterpret_cast<const float4*>(yt + k * kNC)[tx * 2 + 1];
+      const float2 yv[4] = {make_float2(y01.x, y01.y), make_float2(y01.z, y01.w),
+                            make_float2(y23.x, y23.y), make_float2(y23.z, y23.w)};
+      const int kk = k + l0;
+#pragma unroll
+      for (int i = 0; i < kRPT; ++i) {
+        const int r = ty + 32 * i;
+        if (r < n1) {
+          const float2 hv = sh[(r - kk) & nfm];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j].x += hv.x * yv[j].x - hv.y * yv[j].y;
+            acc[i][j].y += hv.x * yv[j].y + hv.y * yv[j].x;
+          }
+        }
+      }
+    }
+    // g|Z| = sum_t g1[r][t] w[t][col];  gZ = g|Z| Z / |Z|
+#pragma unroll
+    for (int i = 0; i < kRPT; ++i) {
+      const int r = ty + 32 * i;
+      if (r < n1) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int col = tx * 4 + j;
+          float ga = 0.f;
+          for (int t = 0; t < nt; ++t) ga += g1[r * nt + t] * wt[t * kNC + col];
+          const float2 z = acc[i][j];
+          const float m = sqrtf(z.x * z.x + z.y * z.y);
+          const float f = (m > 0.f) ? ga / m : 0.f;
+          gz[r * kNC + col] = make_float2(z.x * f, z.y * f);
+        }
+      }
+    }
+    __syncthreads();
+    // gY[k][col] += sum_r conj(h_c[(r - k) mod N_fr]) gZ[r][col]
+    for (int r = 0; r < n1; ++r) {
+      const float4 g01 = reinterpret_cast<const float4*>(gz + r * kNC)[tx * 2];
+      const float4 g23 = reinterpret_cast<const float4*>(gz + r * kNC)[tx * 2 + 1];
+      const float2 gv[4] = {make_float2(g01.x, g01.y), make_float2(g01.z, g01.w),
+                            make_float2(g23.x, g23.y), make_float2(g23.z, g23.w)};
+#pragma unroll
+      for (int i = 0; i < kRPT; ++i) {
+        const int k = ty + 32 * i;
+        if (k < K) {
+          const float2 hv = sh[(r - k - l0) & nfm];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            gacc[i][j].x += hv.x * gv[j].x + hv.y * gv[j].y;
+            gacc[i][j].y += hv.x * gv[j].y - hv.y * gv[j].x;
+          }
+        }
+      }
+    }
+  }
+  float2* go = gy + (size_t)b * P.y_len + A.off_y;
+#pragma unroll
+  for (int i = 0; i < kRPT; ++i) {
+    const int k = ty + 32 * i;
+    if (k < K)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int col = tx * 4 + j;
+        if (n0 + col < A.L) go[(size_t)k * A.L + n0 + col] = gacc[i][j];
+      }
+  }
+}
+
+// g_U1 row lambda': sum over rates alpha of the adjoint of psi2 (DFT of gY / Lr, times
+// psi-hat_alpha on the row's positive bins), then Re of the inverse row DFT, plus S1's adjoint.
+__global__ void __launch_bounds__(kFftThreads)
+k_second_order_bwd(DevPlan P, const float2* __restrict__ gy, const float* __restrict__ gs1,
+                   float* __restrict__ gu1) {
+  extern __shared__ float2 sm[];
+  const int lam = blockIdx.x, b = blockIdx.y;
+  const Row1 R = P.rows1[lam];
+  const int half = R.L >> 1;
+  float2* guh = sm;                // [L/2]
+  float2* tmp = sm + (half > 0 ? half : 1);  // [max(L_alpha, L)]
+  for (int k = threadIdx.x; k < half; k += blockDim.x) guh[k] = make_float2(0.f, 0.f);
+  const float invLr = 1.f / (float)R.L;
+  for (int a = 0; a < P.n2; ++a) {
+    const Rate2 A = P.rates2[a];
+    if (A.s == 0 || lam < A.lam_min) continue;
+    __syncthreads();
+    const float2* g = gy + (size_t)b * P.y_len + A.off_y + (size_t)(lam - A.lam_min) * A.L;
+    for (int m = threadIdx.x; m < A.L; m += blockDim.x) tmp[m] = g[m];
+    __syncthreads();
+    fft_dif<-1>(tmp, A.logL, P.tw, P.logTW);
+    const float* psi = P.psi2 + (size_t)a * P.K2max;
+    for (int k = 1 + threadIdx.x; k < half; k += blockDim.x) {
+      const float2 v = tmp[bitrev(k & (A.L - 1), A.logL)];
+      const float f = __ldg(&psi[k]) * invLr;
+      guh[k].x += v.x * f;
+      guh[k].y += v.y * f;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < R.L; k += blockDim.x)
+    tmp[bitrev(k, R.logL)] = (k < half) ? guh[k] : make_float2(0.f, 0.f);
+  __syncthreads();
+  fft_dit<+1>(tmp, R.logL, P.tw, P.logTW);
+  const float* g1 = gs1 ? gs1 + ((size_t)b * P.n1 + lam) * P.n_t : nullptr;
+  float* out = gu1 + (size_t)b * P.u1_len + R.off_u;
+  for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
+    float v = tmp[m].x;
+    if (g1) {
+      float s = 0.f;
+      for (int t = 0; t < P.n_t; ++t) s += __ldg(&P.phiT[(t * P.T - m * R.s) & (P.N - 1)]) * g1[t];
+      v += s * (float)R.s;
+    }
+    out[m] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kFftThreads)
+k_stage1_bwd(DevPlan P, const float2* __restrict__ xh, const float* __restrict__ gu1,
+             float2* __restrict__ gf) {
+  extern __shared__ float2 sm[];
+  const int lam = blockIdx.x, b = blockIdx.y;
+  const Row1 R = P.rows1[lam];
+  fold_first_order(P, R, xh + (size_t)b * (P.N >> 1), sm);
+  __syncthreads();
+  fft_dit<+1>(sm, R.logL, P.tw, P.logTW);
+  const float* g = gu1 + (size_t)b * P.u1_len + R.off_u;
+  for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
+    const float2 z = sm[m];  // N * z
+    const float mag = hypotf(z.x, z.y);
+    const float f = (mag > 0.f) ? g[m] / mag : 0.f;
+    sm[m] = make_float2(z.x * f, z.y * f);
+  }
+  __syncthreads();
+  fft_dif<-1>(sm, R.logL, P.tw, P.logTW);
+  const float invN = 1.f / (float)P.N;
+  float2* out = gf + (size_t)b * P.u1_len + R.off_u;
+  for (int k = threadIdx.x; k < R.L; k += blockDim.x) {
+    const float2 v = sm[bitrev(k, R.logL)];
+    out[k] = make_float2(v.x * invN, v.y * invN);
+  }
+}
+
+__global__ void k_gxh(DevPlan P, const float2* __restrict__ gf, float2* __restrict__ gxh) {
+  const int b = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int half = P.N >> 1;
+  const int2 rng = P.gx_lam[blockIdx.x];
+  float2 acc = make_float2(0.f, 0.f);
+  if (k < half) {
+    const float2* gb = gf + (size_t)b * P.u1_len;
+    for (int lam = rng.x; lam < rng.y; ++lam) {
+      const Row1 R = P.rows1[lam];
+      const int i = k - R.ks;
+      if (i >= 0 && i < R.kl) {
+        const float f = __ldg(&P.psi1[R.off_v + i]);
+        const float2 v = gb[R.off_u + (k & (R.L - 1))];
+        acc.x += f * v.x;
+        acc.y += f * v.y;
+      }
+    }
+    gxh[(size_t)b * half + k] = acc;
+  }
+}
+
+// g_x[r + D m] = Re(sum_k' e^{2 pi i k' m / M} sum_q H[k' + q M] e^{2 pi i (k' + q M) r / N})
+//              + sum_t phi_T[(tT - n) mod N] g_S0[t]
+__global__ void __launch_bounds__(kFftThreads)
+k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, float* __restrict__ gx) {
+  extern __shared__ float2 sm[];
+  const int r = blockIdx.x, b = blockIdx.y;
+  const int half = P.N >> 1;
+  const int step = P.TW / P.N;
+  const float2* H = gxh + (size_t)b * half;
+  for (int kp = threadIdx.x; kp < P.M; kp += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = kp; k < half; k += P.M) {
+      const float2 v = H[k];
+      const int idx = (int)(((long long)k * r) & (P.N - 1)) * step;
+      float2 w = __ldg(&P.tw[idx]);
+      w.y = -w.y;
+      acc.x += v.x * w.x - v.y * w.y;
+      acc.y += v.x * w.y + v.y * w.x;
+    }
+    sm[bitrev(kp, P.logM)] = acc;
+  }
+  __syncthreads();
+  fft_dit<+1>(sm, P.logM, P.tw, P.logTW);
+  const float* g0 = gs0 ? gs0 + (size_t)b * P.n_t : nullptr;
+  float* out = gx + (size_t)b * P.N;
+  for (int m = threadIdx.x; m < P.M; m += blockDim.x) {
+    const int n = r + P.D * m;
+    float v = sm[m].x;
+    if (g0)
+      for (int t = 0; t < P.n_t; ++t) v += __ldg(&P.phiT[(t * P.T - n) & (P.N - 1)]) * g0[t];
+    out[n] = v;
+  }
+}
+
+bool g_attrs_set = false;
+
+jtfs_status set_attrs() {
+  if (g_attrs_set) return JTFS_OK;
+  const int big = 227 * 1024;
+  const void* fns[] = {(const void*)k_uh_from_u1, (const void*)k_joint_bwd_simt,
+                       (const void*)k_second_order_bwd, (const void*)k_stage1_bwd,
+                       (const void*)k_gx, (const void*)k_xfft_sub, (const void*)k_second_order};
+  for (const void* f : fns) {
+    jtfs_status st = cuda_check(
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr");
+    if (st != JTFS_OK) return st;
+  }
+  g_attrs_set = true;
+  return JTFS_OK;
+}
+
+}  // namespace
+
+size_t joint_bwd_smem(const jtfs_plan* p) {
+  return (size_t)p->N_fr * 8 + 2 * (size_t)p->n1 * kNC * 8 + (size_t)p->n1 * p->n_t * 4 +
+         (size_t)p->n_t * kNC * 4;
+}
+
+jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1, int B,
+                            const float* gs0, const float* gs1, const float* gs2, float* gx,
+                            const Workspace& w, cudaStream_t st) {
+  jtfs_status rc = set_attrs();
+  if (rc != JTFS_OK) return rc;
+  const DevPlan& d = p->dp;
+  // recompute x-hat, U1-hat and Y from x and the checkpoint
+  {
+    StageScope sc(p, kStXfft, st, 2);
+    k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 8, st>>>(d, x, w.xsub);
+    k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.xsub, w.xh);
+  }
+  {
+    StageScope sc(p, kStUhFromU1, st, 1);
+    k_uh_from_u1<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 8, st>>>(d, u1, w.uh);
+  }
+  const size_t n_items = p->items.size() / 2;
+  if (gs2 && n_items > 0) {
+    {
+      StageScope sc(p, kStSecondOrder, st, 1);
+      k_second_order<<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
+                       (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
+                                                   w.uh, w.y);
+    }
+    StageScope sc(p, kStJointBwd, st, 1);
+    k_joint_bwd_simt<<<dim3((unsigned)n_items, B), kJT, joint_bwd_smem(p), st>>>(
+        d, reinterpret_cast<const int2*>(p->d_items), w.y, gs2, w.gy);
+  } else if (p->y_len > 0) {
+    cudaMemsetAsync(w.gy, 0, (size_t)B * p->y_len * sizeof(float2), st);
+  }
+  const size_t sob = ((size_t)(p->L1max / 2 > 0 ? p->L1max / 2 : 1) +
+                      (size_t)(p->L2max > p->L1max ? p->L2max : p->L1max)) * 8;
+  {
+    StageScope sc(p, kStSecondOrderBwd, st, 1);
+    k_second_order_bwd<<<dim3(p->n1, B), kFftThreads, sob, st>>>(d, w.gy, gs1, w.gu1);
+  }
+  {
+    StageScope sc(p, kStStage1Bwd, st, 1);
+    k_stage1_bwd<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 8, st>>>(d, w.xh, w.gu1, w.gf);
+  }
+  {
+    StageScope sc(p, kStGx, st, 2);
+    k_gxh<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.gf, w.gxh);
+    k_gx<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 8, st>>>(d, w.gxh, gs0, gx);
+  }
+  return cuda_check(cudaGetLastError(), "backward launch");
+}
+
+}  // namespace jtfs

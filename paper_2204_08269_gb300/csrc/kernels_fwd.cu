@@ -1,0 +1,254 @@
+// Forward JTFS kernels (Sec. 2, Eq. 2-4) on CUDA cores, FP32.
+//
+//   k_xfft_sub / k_xfft_combine : x-hat[k] for 0 <= k < N/2 (decimated length-N FFT)
+//   k_s0                        : S0[t] = sum_n phi_T[(tT - n) mod N] x[n]
+//   k_scalogram                 : per (lambda, signal): periodise x-hat * psi-hat_lambda to
+//                                 L_lambda bins, inverse FFT, modulus -> U1 row (checkpoint),
+//                                 S1 row (Riemann sum of phi_T), FFT of the row -> U1-hat
+//   k_second_order              : per (alpha, lambda', signal): U1-hat * psi-hat_alpha folded to
+//                                 L_alpha bins, inverse FFT -> Y_alpha row
+//   k_joint_fwd_simt            : per (c, alpha, signal): Z = W_c Y_alpha (zero-padded
+//                                 convolution along lambda), |Z|, phi_T then phi_F pooling -> S2
+#include "stages.cuh"
+
+namespace jtfs {
+namespace {
+
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;
+}
+
+__global__ void k_s0(DevPlan P, const float* __restrict__ x, float* __restrict__ s0) {
+  __shared__ float red[32];
+  const int t = blockIdx.x, b = blockIdx.y;
+  const float* xb = x + (size_t)b * P.N;
+  const int tT = t * P.T;
+  float acc = 0.f;
+  for (int n = threadIdx.x; n < P.N; n += blockDim.x)
+    acc += __ldg(&P.phiT[(tT - n) & (P.N - 1)]) * xb[n];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) s0[(size_t)b * P.n_t + t] = acc;
+}
+
+__global__ void __launch_bounds__(kFftThreads)
+k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
+            float2* __restrict__ uh, float* __restrict__ s1) {
+  extern __shared__ float2 sm[];
+  const int lam = blockIdx.x, b = blockIdx.y;
+  const Row1 R = P.rows1[lam];
+  float* su = reinterpret_cast<float*>(sm + R.L);
+  fold_first_order(P, R, xh + (size_t)b * (P.N >> 1), sm);
+  __syncthreads();
+  fft_dit<+1>(sm, R.logL, P.tw, P.logTW);
+  const float invN = 1.f / (float)P.N;
+  float* ub = u1 + (size_t)b * P.u1_len + R.off_u;
+  for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
+    const float2 z = sm[m];
+    const float a = hypotf(z.x, z.y) * invN;
+    ub[m] = a;
+    su[m] = a;
+    sm[m] = make_float2(a, 0.f);
+  }
+  __syncthreads();
+  // S1[lambda, t] = sum_m s phi_T[(tT - m s) mod N] U1[m]   (one warp per frame)
+  {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int t = w; t < P.n_t; t += nw) {
+      float acc = 0.f;
+      const int tT = t * P.T;
+      for (int m = l; m < R.L; m += 32) acc += __ldg(&P.phiT[(tT - m * R.s) & (P.N - 1)]) * su[m];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (l == 0) s1[((size_t)b * P.n1 + lam) * P.n_t + t] = acc * (float)R.s;
+    }
+  }
+  fft_dif<-1>(sm, R.logL, P.tw, P.logTW);
+  float2* hb = uh + (size_t)b * P.uh_len + R.off_uh;
+  for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[bitrev(k, R.logL)];
+}
+
+// ---------------------------------------------------------------------------------------
+// Joint stage on CUDA cores (the plain FP32 comparison form).  One CTA per (c, alpha, b).
+// Tile: all n1 rows x 32 time columns.  Thread (ty, tx) owns rows ty + 32 i, columns 4 tx + j.
+// ---------------------------------------------------------------------------------------
+constexpr int kJT = 256;      // threads
+constexpr int kNC = 32;       // time columns per tile
+constexpr int kRPT = 8;       // rows per thread (n1 <= 256)
+constexpr int kPQ = 32;       // pooled (row, frame) accumulators per thread (n1 * n_t <= 8192)
+
+struct JointSmem {
+  float2* h;      // [N_fr]
+  float2* yt;     // [n1][kNC]
+  float* az;      // [n1][kNC + 1]
+  float* wt;      // [n_t][kNC]
+};
+
+__global__ void __launch_bounds__(kJT)
+k_joint_fwd_simt(DevPlan P, const float2* __restrict__ y, float* __restrict__ s2) {
+  extern __shared__ float4 smraw[];
+  const int c = blockIdx.x, a = blockIdx.y, b = blockIdx.z;
+  const Rate2 A = P.rates2[a];
+  float* out = s2 + (((size_t)b * P.n2 + a) * P.C + c) * (size_t)P.n_lo * P.n_t;
+  if (A.s == 0) {
+    for (int i = threadIdx.x; i < P.n_lo * P.n_t; i += blockDim.x) out[i] = 0.f;
+    return;
+  }
+  const int n1 = P.n1, nt = P.n_t, K = A.K, l0 = A.lam_min;
+  float2* sh = reinterpret_cast<float2*>(smraw);
+  float2* yt = sh + P.N_fr;
+  float* az = reinterpret_cast<float*>(yt + (size_t)n1 * kNC);
+  float* wt = az + (size_t)n1 * (nt > kNC + 1 ? nt : kNC + 1);
+  for (int i = threadIdx.x; i < P.N_fr; i += blockDim.x) sh[i] = P.h[(size_t)c * P.N_fr + i];
+  const int ty = threadIdx.x >> 3, tx = threadIdx.x & 7;
+  const int nfm = P.N_fr - 1;
+  float pacc[kPQ];
+#pragma unroll
+  for (int q = 0; q < kPQ; ++q) pacc[q] = 0.f;
+  const float2* ya = y + (size_t)b * P.y_len + A.off_y;
+  for (int n0 = 0; n0 < A.L; n0 += kNC) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < K * kNC; i += blockDim.x) {
+      const int k = i / kNC, col = i % kNC;
+      yt[i] = (n0 + col < A.L) ? ya[(size_t)k * A.L + n0 + col] : make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < nt * kNC; i += blockDim.x) {
+      const int t = i / kNC, col = i % kNC;
+      const int n = n0 + col;
+      wt[i] = (n < A.L) ? __ldg(&P.phiT[(t * P.T - n * A.s) & (P.N - 1)]) * (float)A.s : 0.f;
+    }
+    __syncthreads();
+    float2 acc[kRPT][4];
+#pragma unroll
+    for (int i = 0; i < kRPT; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+    for (int k = 0; k < K; ++k) {
+      const float4 y01 = reinterpret_cast<const float4*>(yt + k * kNC)[tx * 2];
+      const float4 y23 = reinterpret_cast<const float4*>(yt + k * kNC)[tx * 2 + 1];
+      const float2 yv[4] = {make_float2(y01.x, y01.y), make_float2(y01.z, y01.w),
+                            make_float2(y23.x, y23.y), make_float2(y23.z, y23.w)};
+      const int kk = k + l0;
+#pragma unroll
+      for (int i = 0; i < kRPT; ++i) {
+        const int r = ty + 32 * i;
+        if (r < n1) {
+          const float2 hv = sh[(r - kk) & nfm];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j].x += hv.x * yv[j].x - hv.y * yv[j].y;
+            acc[i][j].y += hv.x * yv[j].y + hv.y * yv[j].x;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kRPT; ++i) {
+      const int r = ty + 32 * i;
+      if (r < n1)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          az[r * (kNC + 1) + tx * 4 + j] = sqrtf(acc[i][j].x * acc[i][j].x + acc[i][j].y * acc[i][j].y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kPQ; ++q) {
+      const int p = threadIdx.x + q * kJT;
+      if (p < n1 * nt) {
+        const int r = p / nt, t = p % nt;
+        const float* zr = az + r * (kNC + 1);
+        const float* wr = wt + t * kNC;
+        float s = 0.f;
+#pragma unroll 8
+        for (int col = 0; col < kNC; ++col) s += zr[col] * wr[col];
+        pacc[q] += s;
+      }
+    }
+  }
+  __syncthreads();
+  // time-pooled rows -> shared, then phi_F pooling along lambda (or none for Eq. 4)
+  float* pm = az;  // [n1][n_t]
+#pragma unroll
+  for (int q = 0; q < kPQ; ++q) {
+    const int p = threadIdx.x + q * kJT;
+    if (p < n1 * nt) pm[p] = pacc[q];
+  }
+  __syncthreads();
+  if (P.average_fr) {
+    for (int i = threadIdx.x; i < P.n_lo * nt; i += blockDim.x) {
+      const int lo = i / nt, t = i % nt;
+      float s = 0.f;
+      for (int r = 0; r < n1; ++r) s += __ldg(&P.phiF[(lo * P.s_F - r) & nfm]) * pm[r * nt + t];
+      out[i] = s;
+    }
+  } else {
+    for (int i = threadIdx.x; i < n1 * nt; i += blockDim.x) out[i] = pm[i];
+  }
+}
+
+bool g_attrs_set = false;
+
+jtfs_status set_attrs(const jtfs_plan* p) {
+  (void)p;
+  if (g_attrs_set) return JTFS_OK;
+  const int big = 227 * 1024;
+  jtfs_status st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_xfft_sub, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_scalogram, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_joint_fwd_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
+  g_attrs_set = true;
+  return JTFS_OK;
+}
+
+}  // namespace
+
+size_t joint_fwd_smem(const jtfs_plan* p) {
+  const size_t azw = (size_t)(p->n_t > kNC + 1 ? p->n_t : kNC + 1);
+  return (size_t)p->N_fr * 8 + (size_t)p->n1 * kNC * 8 + (size_t)p->n1 * azw * 4 +
+         (size_t)p->n_t * kNC * 4;
+}
+
+bool joint_simt_supported(const jtfs_plan* p) {
+  return p->n1 <= 32 * kRPT && (long long)p->n1 * p->n_t <= (long long)kPQ * kJT &&
+         joint_fwd_smem(p) <= 227 * 1024;
+}
+
+jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0, float* s1,
+                           float* s2, float* u1, const Workspace& w, cudaStream_t st) {
+  jtfs_status rc = set_attrs(p);
+  if (rc != JTFS_OK) return rc;
+  const DevPlan& d = p->dp;
+  {
+    StageScope sc(p, kStXfft, st, 2);
+    k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 8, st>>>(d, x, w.xsub);
+    k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.xsub, w.xh);
+  }
+  {
+    StageScope sc(p, kStS0, st, 1);
+    k_s0<<<dim3(p->n_t, B), 256, 0, st>>>(d, x, s0);
+  }
+  {
+    StageScope sc(p, kStScalogram, st, 1);
+    k_scalogram<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 12, st>>>(d, w.xh, u1, w.uh, s1);
+  }
+  if (!p->pairs.empty()) {
+    StageScope sc(p, kStSecondOrder, st, 1);
+    k_second_order<<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
+                     (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
+                                                 w.uh, w.y);
+  }
+  {
+    StageScope sc(p, kStJointFwd, st, 1);
+    k_joint_fwd_simt<<<dim3(p->C, p->n2, B), kJT, joint_fwd_smem(p), st>>>(d, w.y, s2);
+  }
+  return cuda_check(cudaGetLastError(), "forward launch");
+}
+
+}  // namespace jtfs

@@ -1,0 +1,291 @@
+"""Python binding of libjtfs (argument marshalling only; every step of the transform runs in
+the library's CUDA kernels).  PyTorch provides device memory and the current stream.
+
+The C ABI is declared in ``include/jtfs.h``; each Python function here calls the function
+of the same name.  There is no CPU path: if ``libjtfs.so`` is missing or fails to load,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjtfs.so")
+
+PRECISIONS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp32_simt": 3}
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_int32), ("Q", ctypes.c_int32), ("Q2", ctypes.c_int32),
+                ("J_fr", ctypes.c_int32), ("Q_fr", ctypes.c_int32), ("T", ctypes.c_int64),
+                ("F", ctypes.c_int64), ("average_fr", ctypes.c_int32),
+                ("oversampling", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class _Shapes(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "N", "n1", "n2", "n_fr", "C", "n_t", "n_lam_out", "N_fr", "s_F",
+        "s0_len", "s1_len", "s2_len", "u1_len")]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+
+def lib():
+    """The loaded libjtfs (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libjtfs.so not found at {LIB_PATH}; run "
+                           "`python -m paper_2204_08269_gb300.build` (needs nvcc)")
+    L = ctypes.CDLL(LIB_PATH)
+    sig = {
+        "jtfs_plan_create": ([ctypes.POINTER(_Config), _I64, ctypes.POINTER(_P)], _I32),
+        "jtfs_plan_destroy": ([_P], None),
+        "jtfs_plan_shapes": ([_P, ctypes.POINTER(_Shapes)], _I32),
+        "jtfs_plan_schedule": ([_P, _P, _P, _P], _I32),
+        "jtfs_workspace_bytes": ([_P, _I64, _I32, ctypes.POINTER(_SZ)], _I32),
+        "jtfs_forward": ([_P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P], _I32),
+        "jtfs_backward": ([_P, _P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P], _I32),
+        "jtfs_host_step_bytes": ([_P, _I64, ctypes.POINTER(_SZ)], _I32),
+        "jtfs_forward_backward_host": ([_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P,
+                                        _SZ, _P], _I32),
+        "jtfs_sync_status": ([_P, _P], _I32),
+        "jtfs_profile_enable": ([_P, _I32], _I32),
+        "jtfs_profile_read": ([_P, _P, _I32, ctypes.POINTER(_I64)], _I32),
+        "jtfs_profile_stage_name": ([_I32], ctypes.c_char_p),
+        "jtfs_status_string": ([_I32], ctypes.c_char_p),
+        "jtfs_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names the binding expects the library to export (one per declaration in jtfs.h)."""
+    return ["jtfs_plan_create", "jtfs_plan_destroy", "jtfs_plan_shapes", "jtfs_plan_schedule",
+            "jtfs_workspace_bytes", "jtfs_forward", "jtfs_backward", "jtfs_host_step_bytes",
+            "jtfs_forward_backward_host", "jtfs_sync_status", "jtfs_status_string",
+            "jtfs_last_error", "jtfs_profile_enable", "jtfs_profile_read",
+            "jtfs_profile_stage_name"]
+
+
+class JTFSError(RuntimeError):
+    def __init__(self, call, status):
+        L = lib()
+        msg = L.jtfs_status_string(status).decode()
+        detail = L.jtfs_last_error().decode()
+        super().__init__(f"{call}: {msg}: {detail}")
+        self.status = status
+
+
+def _check(call, status):
+    if status != 0:
+        raise JTFSError(call, status)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+@dataclass(frozen=True)
+class Shapes:
+    N: int
+    n1: int
+    n2: int
+    n_fr: int
+    C: int
+    n_t: int
+    n_lam_out: int
+    N_fr: int
+    s_F: int
+    u1_len: int
+
+    def s0(self, B):
+        return (B, self.n_t)
+
+    def s1(self, B):
+        return (B, self.n1, self.n_t)
+
+    def s2(self, B):
+        return (B, self.n2, self.C, self.n_lam_out, self.n_t)
+
+
+class JTFSPlan:
+    """Filterbanks and schedule for signals of length N (Sec. 4.2 parameters), on the
+    current CUDA device.  ``precision`` selects the arithmetic of the log-frequency
+    contraction: 'fp32' (tensor cores, bf16 hi/lo split), 'tf32', 'bf16' or 'fp32_simt'."""
+
+    def __init__(self, N, J, Q, J_fr, Q_fr, T, F, Q2=1, average_fr=True, oversampling=0,
+                 precision="fp32"):
+        L = lib()
+        cfg = _Config(J=J, Q=Q, Q2=Q2, J_fr=J_fr, Q_fr=Q_fr, T=T, F=F,
+                      average_fr=1 if average_fr else 0, oversampling=oversampling,
+                      precision=PRECISIONS[precision])
+        h = ctypes.c_void_p()
+        _check("jtfs_plan_create", L.jtfs_plan_create(ctypes.byref(cfg), N, ctypes.byref(h)))
+        self._h = h
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        sh = _Shapes()
+        _check("jtfs_plan_shapes", L.jtfs_plan_shapes(h, ctypes.byref(sh)))
+        self.shapes = Shapes(sh.N, sh.n1, sh.n2, sh.n_fr, sh.C, sh.n_t, sh.n_lam_out, sh.N_fr,
+                             sh.s_F, sh.u1_len)
+        self.config = dict(N=N, J=J, Q=Q, Q2=Q2, J_fr=J_fr, Q_fr=Q_fr, T=T, F=F,
+                           average_fr=average_fr, oversampling=oversampling, precision=precision)
+        self._ws = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.jtfs_plan_destroy(h)
+            self._h = None
+
+    def schedule(self):
+        import numpy as np
+        s1 = np.zeros(self.shapes.n1, dtype=np.int32)
+        s2 = np.zeros(self.shapes.n2, dtype=np.int32)
+        lm = np.zeros(self.shapes.n2, dtype=np.int32)
+        _check("jtfs_plan_schedule", lib().jtfs_plan_schedule(
+            self._h, s1.ctypes.data_as(_P), s2.ctypes.data_as(_P), lm.ctypes.data_as(_P)))
+        return s1, s2, lm
+
+    def workspace_bytes(self, B, with_grad):
+        n = ctypes.c_size_t()
+        _check("jtfs_workspace_bytes",
+               lib().jtfs_workspace_bytes(self._h, B, 1 if with_grad else 0, ctypes.byref(n)))
+        return n.value
+
+    def workspace(self, B, with_grad):
+        need = self.workspace_bytes(B, with_grad)
+        key = "ws"
+        buf = self._ws.get(key)
+        if buf is None or buf.numel() < need:
+            buf = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+            self._ws[key] = buf
+        return buf
+
+    def _check_x(self, x):
+        if not (x.is_cuda and x.dtype == torch.float32 and x.dim() == 2
+                and x.shape[1] == self.shapes.N and x.is_contiguous()):
+            raise ValueError(f"x must be a contiguous float32 CUDA tensor [B, {self.shapes.N}]")
+
+    def forward(self, x, keep_checkpoint=True):
+        """S0 [B, n_t], S1 [B, n1, n_t], S2 [B, n2, C, n_lam_out, n_t] and the U1 checkpoint."""
+        self._check_x(x)
+        B = x.shape[0]
+        sh = self.shapes
+        dev = x.device
+        s0 = torch.empty(sh.s0(B), dtype=torch.float32, device=dev)
+        s1 = torch.empty(sh.s1(B), dtype=torch.float32, device=dev)
+        s2 = torch.empty(sh.s2(B), dtype=torch.float32, device=dev)
+        u1 = torch.empty((B, sh.u1_len), dtype=torch.float32, device=dev) if keep_checkpoint else None
+        ws = self.workspace(B, True)
+        _check("jtfs_forward", lib().jtfs_forward(
+            self._h, _ptr(x), B, _ptr(s0), _ptr(s1), _ptr(s2), _ptr(u1), _ptr(ws), ws.numel(),
+            _stream()))
+        return s0, s1, s2, u1
+
+    def backward(self, x, u1, g_s0=None, g_s1=None, g_s2=None):
+        """g_x = d<g, S(x)>/dx (Sec. 5).  Cotangents may be None (zero)."""
+        self._check_x(x)
+        B = x.shape[0]
+        gx = torch.empty_like(x)
+        ws = self.workspace(B, True)
+        gs = [None if g is None else g.contiguous() for g in (g_s0, g_s1, g_s2)]
+        _check("jtfs_backward", lib().jtfs_backward(
+            self._h, _ptr(x), _ptr(u1), B, _ptr(gs[0]), _ptr(gs[1]), _ptr(gs[2]), _ptr(gx),
+            _ptr(ws), ws.numel(), _stream()))
+        return gx
+
+    def forward_backward_host(self, x_host, g_s0=None, g_s1=None, g_s2=None, outputs=True):
+        """End-to-end step from pinned (or pageable) host tensors: H2D, forward, backward,
+        D2H, all inside one library call.  Returns (s0, s1, s2, g_x) host tensors."""
+        B = x_host.shape[0]
+        sh = self.shapes
+        n = ctypes.c_size_t()
+        _check("jtfs_host_step_bytes", lib().jtfs_host_step_bytes(self._h, B, ctypes.byref(n)))
+        key = "host_dev"
+        dev_buf = self._ws.get(key)
+        if dev_buf is None or dev_buf.numel() < n.value:
+            dev_buf = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+            self._ws[key] = dev_buf
+        ws = self.workspace(B, True)
+        pin = x_host.is_pinned()
+        gx = torch.empty(x_host.shape, dtype=torch.float32, pin_memory=pin)
+        outs = [torch.empty(s, dtype=torch.float32, pin_memory=pin) if outputs else None
+                for s in (sh.s0(B), sh.s1(B), sh.s2(B))]
+        _check("jtfs_forward_backward_host", lib().jtfs_forward_backward_host(
+            self._h, _ptr(x_host), B, _ptr(g_s0), _ptr(g_s1), _ptr(g_s2), _ptr(outs[0]),
+            _ptr(outs[1]), _ptr(outs[2]), _ptr(gx), _ptr(dev_buf), dev_buf.numel(), _ptr(ws),
+            ws.numel(), _stream()))
+        return outs[0], outs[1], outs[2], gx
+
+    def profile(self, on=True):
+        _check("jtfs_profile_enable", lib().jtfs_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """({stage: milliseconds}, kernel launches) since the previous read."""
+        import numpy as np
+        L = lib()
+        names = []
+        while True:
+            n = L.jtfs_profile_stage_name(len(names))
+            if n is None:
+                break
+            names.append(n.decode())
+        ms = np.zeros(len(names), dtype=np.float64)
+        launches = ctypes.c_int64()
+        _check("jtfs_profile_read", L.jtfs_profile_read(self._h, ms.ctypes.data_as(_P), len(names),
+                                                        ctypes.byref(launches)))
+        return dict(zip(names, ms.tolist())), launches.value
+
+    def sync(self):
+        _check("jtfs_sync_status", lib().jtfs_sync_status(self._h, _stream()))
+
+
+class JTFSFunction(torch.autograd.Function):
+    """(S0, S1, S2) = JTFS(x) with the hand-written adjoint chain as backward; only the
+    first-order scalogram is kept between the passes."""
+
+    @staticmethod
+    def forward(ctx, x, plan):
+        x = x.contiguous()
+        s0, s1, s2, u1 = plan.forward(x)
+        ctx.plan = plan
+        ctx.save_for_backward(x, u1)
+        return s0, s1, s2
+
+    @staticmethod
+    def backward(ctx, g0, g1, g2):
+        x, u1 = ctx.saved_tensors
+        gx = ctx.plan.backward(x, u1, g0, g1, g2)
+        return gx, None
+
+
+class JTFS(torch.nn.Module):
+    """Joint time-frequency scattering as a module: x [B, N] -> (S0, S1, S2)."""
+
+    def __init__(self, N, J, Q, J_fr, Q_fr, T, F, **kw):
+        super().__init__()
+        self.plan = JTFSPlan(N, J, Q, J_fr, Q_fr, T, F, **kw)
+
+    def forward(self, x):
+        return JTFSFunction.apply(x, self.plan)
