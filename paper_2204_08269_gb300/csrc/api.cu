@@ -143,6 +143,13 @@ size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* bas
   W.gu1 = nullptr;
   W.gf = nullptr;
   W.gxh = nullptr;
+  W.ybh = W.ybl = nullptr;
+  W.pbuf = nullptr;
+  if (p->use_tc) {
+    W.ybh = take(Bz * p->y_len * 2 * 2);
+    if (p->cfg.precision == JTFS_PREC_FP32) W.ybl = take(Bz * p->y_len * 2 * 2);
+    W.pbuf = (float*)take(Bz * p->n2 * (size_t)p->C * p->n1 * p->n_t * 4);
+  }
   if (with_grad) {
     W.gy = (float2*)take(Bz * p->y_len * 8);
     W.gu1 = (float*)take(Bz * p->u1_len * 4);
@@ -178,6 +185,7 @@ void jtfs_plan_destroy(jtfs_plan* p) {
   for (auto& r : p->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : p->prof.pool) cudaEventDestroy(e);
   if (p->d_mem) cudaFree(p->d_mem);
+  if (p->d_tc_mem) cudaFree(p->d_tc_mem);
   delete p;
 }
 
@@ -191,6 +199,9 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   p->cfg = *cfg;
   p->N = N;
   p->d_mem = nullptr;
+  p->d_tc_mem = nullptr;
+  p->d_err = nullptr;
+  p->use_tc = false;
   if ((st = cuda_check(cudaGetDevice(&p->device), "cudaGetDevice")) != JTFS_OK) {
     delete p;
     return st;
@@ -343,6 +354,13 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
                                     "plan upload")) != JTFS_OK)
       return fail(st, "");
   if ((st = build_tables(p)) != JTFS_OK) return fail(st, "");
+  if (cfg->precision == JTFS_PREC_TF32)
+    return fail(JTFS_ERR_UNSUPPORTED, "TF32 contraction is not built; use FP32, BF16 or FP32_SIMT");
+  if (cfg->precision == JTFS_PREC_FP32 || cfg->precision == JTFS_PREC_BF16) {
+    if (!tc_supported(p)) return fail(JTFS_ERR_UNSUPPORTED, "configuration outside the tensor-core kernel");
+    p->use_tc = true;
+    if ((st = build_tc_tables(p)) != JTFS_OK) return fail(st, "");
+  }
   *out = p;
   return JTFS_OK;
 }
@@ -512,7 +530,18 @@ jtfs_status jtfs_sync_status(const jtfs_plan* p, void* stream) {
   if (!p) { set_error("NULL plan"); return JTFS_ERR_INVALID_ARG; }
   jtfs_status st = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "stream sync");
   if (st != JTFS_OK) return st;
-  return cuda_check(cudaGetLastError(), "pending error");
+  if ((st = cuda_check(cudaGetLastError(), "pending error")) != JTFS_OK) return st;
+  if (p->d_err) {
+    int code = 0;
+    if ((st = cuda_check(cudaMemcpy(&code, p->d_err, sizeof(int), cudaMemcpyDeviceToHost), "status word")) != JTFS_OK)
+      return st;
+    if (code != 0) {
+      cudaMemset(p->d_err, 0, sizeof(int));
+      set_error("a bounded device wait gave up (code " + std::to_string(code) + ")");
+      return JTFS_ERR_TIMEOUT;
+    }
+  }
+  return JTFS_OK;
 }
 
 }  // extern "C"

@@ -90,6 +90,16 @@ struct jtfs_plan {
   size_t d_bytes;
   int* d_pairs;
   int* d_items;
+  // tensor-core contraction (precisions FP32 / BF16)
+  bool use_tc;
+  int n1_pad;                  // lambda' columns of the W planes (multiple of 32)
+  void* d_wplanes[4];          // Wr_hi, Wi_hi, Wr_lo, Wi_lo: [C * n1][n1_pad] bf16
+  float* d_wt;                 // per alpha: [L_alpha rounded up to 128][NT] pooling weights
+  long long* d_wt_off;         // [n2]
+  std::vector<int> tc_items;   // (alpha, m0, n_tiles, 0) per signal, longest first
+  int* d_tc_items;
+  int* d_err;                  // device status word of the bounded waits
+  void* d_tc_mem;
   mutable jtfs::Profiler prof;
 };
 
@@ -112,6 +122,9 @@ struct Workspace {
   float* gu1;      // [B][u1_len]
   float2* gf;      // [B][u1_len]  (per row L complex)
   float2* gxh;     // [B][N/2]
+  void* ybh;       // [B * y_len * 2] bf16 (tensor-core path)
+  void* ybl;       // [B * y_len * 2] bf16 (three-pass split only)
+  float* pbuf;     // [B][n2][C * n1][n_t] time-pooled rows
 };
 size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* base, Workspace* w);
 
@@ -124,6 +137,13 @@ struct StageScope {
   StageScope(const jtfs_plan* p_, int stage_, cudaStream_t st_, int n_launch);
   ~StageScope();
 };
+
+// tensor-core contraction (kernels_tc.cu)
+bool tc_supported(const jtfs_plan* p);
+int tc_nt(int n_t);
+jtfs_status build_tc_tables(jtfs_plan* p);
+jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi, const void* ylo,
+                                float* Pbuf, float* s2, cudaStream_t st);
 
 jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0, float* s1,
                            float* s2, float* u1, const Workspace& w, cudaStream_t st);

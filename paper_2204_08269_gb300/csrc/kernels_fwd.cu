@@ -201,7 +201,8 @@ jtfs_status set_attrs(const jtfs_plan* p) {
   jtfs_status st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_xfft_sub, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_scalogram, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
-  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_joint_fwd_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
   g_attrs_set = true;
   return JTFS_OK;
@@ -238,13 +239,24 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
     StageScope sc(p, kStScalogram, st, 1);
     k_scalogram<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 12, st>>>(d, w.xh, u1, w.uh, s1);
   }
-  if (!p->pairs.empty()) {
-    StageScope sc(p, kStSecondOrder, st, 1);
-    k_second_order<<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
-                     (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
-                                                 w.uh, w.y);
-  }
-  {
+  if (p->use_tc) {
+    if (!p->pairs.empty()) {
+      StageScope sc(p, kStSecondOrder, st, 1);
+      k_second_order<1><<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
+                         (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
+                                                     w.uh, nullptr, (__nv_bfloat16*)w.ybh,
+                                                     (__nv_bfloat16*)w.ybl, B);
+    }
+    StageScope sc(p, kStJointFwd, st, 2);
+    jtfs_status r2 = launch_joint_fwd_tc(p, B, w.ybh, w.ybl, w.pbuf, s2, st);
+    if (r2 != JTFS_OK) return r2;
+  } else {
+    if (!p->pairs.empty()) {
+      StageScope sc(p, kStSecondOrder, st, 1);
+      k_second_order<0><<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
+                         (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
+                                                     w.uh, w.y, nullptr, nullptr, B);
+    }
     StageScope sc(p, kStJointFwd, st, 1);
     k_joint_fwd_simt<<<dim3(p->C, p->n2, B), kJT, joint_fwd_smem(p), st>>>(d, w.y, s2);
   }

@@ -1,0 +1,123 @@
+// Self-test of the tcgen05 / TMA building blocks (test infrastructure, built into its own
+// library libjtfs_selftest.so): one CTA computes D[128 x 128] = A[128 x K] B[K x 128] in
+// BF16 with FP32 accumulation, A K-major with a 32/64/128-byte swizzle, B either MN-major
+// (rows of 128 time samples, 128-byte swizzle) or K-major.  The test compares D with a
+// plain matrix product.
+#include <stdint.h>
+
+#include <string>
+
+#include "../tma_host.h"
+#include "../umma.cuh"
+
+using namespace jtfs;
+using namespace jtfs::umma;
+
+namespace {
+
+__global__ void k_umma_selftest(const __grid_constant__ CUtensorMap ta,
+                                const __grid_constant__ CUtensorMap tb, float* D, int K,
+                                int a_swz, int b_mn, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = sm;
+  uint8_t* sB = sA + 128 * K * 2;
+  __shared__ uint64_t bar_tma, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    mbar_init(&bar_tma, 1);
+    mbar_init(&bar_mma, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 128);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  if (threadIdx.x == 0) {
+    const int kb = a_swz / 2;
+    mbar_arrive_expect_tx(&bar_tma, (uint32_t)(128 * K * 2 * 2));
+    for (int k0 = 0; k0 < K; k0 += kb) tma_load_2d(sA + k0 * 256, &ta, k0, 0, &bar_tma);
+    if (b_mn) {
+      for (int n0 = 0; n0 < 128; n0 += 64) tma_load_2d(sB + (n0 / 64) * K * 128, &tb, n0, 0, &bar_tma);
+    } else {
+      for (int k0 = 0; k0 < K; k0 += 64) tma_load_2d(sB + k0 * 256, &tb, k0, 0, &bar_tma);
+    }
+    if (!mbar_wait(&bar_tma, 0, 2000000000ull)) {
+      failed = 1;
+    } else {
+      const uint32_t lay = a_swz == 128 ? kSw128 : (a_swz == 64 ? kSw64 : kSw32);
+      const uint32_t idesc = instr_desc(128, 128, 1, 1, 0, (uint32_t)b_mn, 0);
+      for (int j = 0; j < K / 16; ++j) {
+        const int box = (j * 16) / kb, off = ((j * 16) % kb) * 2;
+        const uint64_t ad = smem_desc(smem_u32(sA + box * 128 * a_swz + off), 16, 8 * a_swz, lay);
+        uint64_t bd;
+        if (b_mn) {
+          bd = smem_desc(smem_u32(sB + j * 16 * 128), (uint32_t)(K * 128), 1024, kSw128);
+        } else {
+          const int bb = (j * 16) / 64, bo = ((j * 16) % 64) * 2;
+          bd = smem_desc(smem_u32(sB + bb * 128 * 128 + bo), 16, 1024, kSw128);
+        }
+        mma_f16(tbase, ad, bd, idesc, j > 0 ? 1u : 0u);
+      }
+      mma_commit(&bar_mma);
+    }
+  }
+  __syncthreads();
+  if (!failed) {
+    if (!mbar_wait(&bar_mma, 0, 2000000000ull)) atomicExch(&failed, 1);
+  }
+  tc_fence_after();
+  if (!failed) {
+    const int row = warp * 32 + lane;
+    for (int c0 = 0; c0 < 128; c0 += 16) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) D[row * 128 + c0 + i] = v[i];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 128);
+  if (threadIdx.x == 0) *status = failed;
+}
+
+}  // namespace
+
+extern "C" int jtfs_selftest_umma(const void* A, const void* B, float* D, int K, int a_swz,
+                                  int b_mn, int* status_dev, void* stream) {
+  if (K < 16 || K > 128 || K % 16 || (a_swz != 32 && a_swz != 64 && a_swz != 128)) return 1;
+  if (K % (a_swz / 2)) return 1;
+  if (!b_mn && K % 64) return 1;
+  CUtensorMap ta, tb;
+  std::string err;
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)K, 128};
+    cuuint64_t str[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {(cuuint32_t)(a_swz / 2), 128};
+    if (!make_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, dims, str, box, a_swz, &err))
+      return 2;
+  }
+  if (b_mn) {
+    cuuint64_t dims[2] = {128, (cuuint64_t)K};
+    cuuint64_t str[1] = {128 * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)K};
+    if (!make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, dims, str, box, 128, &err)) return 2;
+  } else {
+    cuuint64_t dims[2] = {(cuuint64_t)K, 128};
+    cuuint64_t str[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {64, 128};
+    if (!make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, dims, str, box, 128, &err)) return 2;
+  }
+  const size_t smem = 1024 + (size_t)128 * K * 2 * 2;
+  cudaFuncSetAttribute(k_umma_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_umma_selftest<<<1, 128, smem, (cudaStream_t)stream>>>(ta, tb, D, K, a_swz, b_mn, status_dev);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}

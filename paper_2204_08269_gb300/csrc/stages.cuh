@@ -2,6 +2,8 @@
 // the periodisation of x-hat * psi-hat_lambda (Sec. 2) and the second-order time
 // wavelet producer Y_alpha (Eq. 3 along t).  Included by both translation units.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "fft.cuh"
 #include "internal.h"
 
@@ -65,9 +67,15 @@ __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R
 
 // Y_alpha row of lambda': the row spectrum U1-hat[k] (positive bins below the row's Nyquist)
 // times psi-hat_alpha(k / N), folded modulo L_alpha, inverse FFT, scaled by 1 / L_lambda'.
+// OUT_BF16 = 0: Y row written as complex FP32 at the per-signal offset of the rate.
+// OUT_BF16 = 1: Y row written as BF16 planes for the tensor-core contraction, layout
+// [alpha][2 b + part][lambda' - lam_min][n] (part 0 = Re, 1 = Im), value = hi + lo with
+// hi = bf16(v) and lo = bf16(v - hi).
+template <int OUT_BF16>
 __global__ void __launch_bounds__(kFftThreads)
 k_second_order(DevPlan P, const int2* __restrict__ pairs, const float2* __restrict__ uh,
-               float2* __restrict__ y) {
+               float2* __restrict__ y, __nv_bfloat16* __restrict__ yhi,
+               __nv_bfloat16* __restrict__ ylo, int B) {
   extern __shared__ float2 sm[];
   const int2 pr = pairs[blockIdx.x];
   const int a = pr.x, lam = pr.y, b = blockIdx.y;
@@ -89,10 +97,28 @@ k_second_order(DevPlan P, const int2* __restrict__ pairs, const float2* __restri
   __syncthreads();
   fft_dit<+1>(sm, A.logL, P.tw, P.logTW);
   const float inv = 1.f / (float)R.L;
-  float2* yr = y + (size_t)b * P.y_len + A.off_y + (size_t)(lam - A.lam_min) * A.L;
-  for (int m = threadIdx.x; m < A.L; m += blockDim.x) {
-    const float2 v = sm[m];
-    yr[m] = make_float2(v.x * inv, v.y * inv);
+  if (!OUT_BF16) {
+    float2* yr = y + (size_t)b * P.y_len + A.off_y + (size_t)(lam - A.lam_min) * A.L;
+    for (int m = threadIdx.x; m < A.L; m += blockDim.x) {
+      const float2 v = sm[m];
+      yr[m] = make_float2(v.x * inv, v.y * inv);
+    }
+  } else {
+    const size_t region = (size_t)B * 2 * A.off_y;
+    const size_t plane = (size_t)A.K * A.L;
+    const size_t off_re = region + (size_t)(2 * b) * plane + (size_t)(lam - A.lam_min) * A.L;
+    const size_t off_im = off_re + plane;
+    for (int m = threadIdx.x; m < A.L; m += blockDim.x) {
+      const float2 v = sm[m];
+      const float re = v.x * inv, im = v.y * inv;
+      const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi_ = __float2bfloat16_rn(im);
+      yhi[off_re + m] = hr;
+      yhi[off_im + m] = hi_;
+      if (ylo) {
+        ylo[off_re + m] = __float2bfloat16_rn(re - __bfloat162float(hr));
+        ylo[off_im + m] = __float2bfloat16_rn(im - __bfloat162float(hi_));
+      }
+    }
   }
 }
 

@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 
 TOL = {"fp32": 1e-4, "fp32_simt": 1e-4, "tf32": 1e-3, "bf16": 2e-2}
 GTOL = {"fp32": 1e-3, "fp32_simt": 1e-3, "tf32": 1e-2, "bf16": 5e-2}
-PRECS = ["fp32_simt"]
+PRECS = ["fp32_simt", "fp32", "bf16"]
 
 SMALL_CFGS = [
     dict(N=512, J=5, Q=4, J_fr=3, Q_fr=1, T=32, F=4),
@@ -169,6 +169,21 @@ def test_backward_workload2_sampled(prec):
     op, sc = _oracle(cfg)
     x = SS.workload_signals(2, 64, cfg["N"])
     _check_backward(plan, x, op, sc, GTOL[prec], idx=[11])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_tensor_core_matches_cuda_core_form(prec):
+    """The tcgen05 contraction and the CUDA-core FP32 form agree on the same input."""
+    cfg = _workload_cfg(2)
+    a = _plans(cfg, "fp32_simt")
+    b = _plans(cfg, prec)
+    x = torch.from_numpy(SS.workload_signals(2, 8, cfg["N"])).cuda()
+    ra = a.forward(x)
+    rb = b.forward(x)
+    for u, v in zip(ra[:3], rb[:3]):
+        e = float((u - v).norm() / u.norm())
+        assert e <= TOL[prec], e
+    b.sync()
 
 
 def test_partial_cotangents_and_zero_input():

@@ -1,0 +1,41 @@
+"""Unit test of the tcgen05 / TMA building blocks used by the tensor-core contraction:
+one 128 x 128 x K BF16 GEMM with the shared-memory layouts of the joint kernels,
+compared with a plain FP32 matrix product of the same BF16 values."""
+import ctypes
+import os
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def st():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_08269_gb300 import build
+    build.build()
+    L = ctypes.CDLL(build.SELFTEST_LIB)
+    f = L.jtfs_selftest_umma
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int] * 3 + [ctypes.c_void_p] * 2
+    f.restype = ctypes.c_int
+    return f
+
+
+@pytest.mark.parametrize("K,a_swz,b_mn", [(64, 128, 1), (32, 64, 1), (64, 64, 1), (128, 128, 1),
+                                          (32, 32, 1), (64, 128, 0), (128, 64, 0)])
+def test_umma_bf16_gemm(st, K, a_swz, b_mn):
+    g = torch.Generator(device="cuda").manual_seed(K + a_swz + b_mn)
+    A = torch.randn(128, K, device="cuda", generator=g).to(torch.bfloat16).contiguous()
+    Bkn = torch.randn(K, 128, device="cuda", generator=g).to(torch.bfloat16)
+    B = Bkn.contiguous() if b_mn else Bkn.t().contiguous()
+    D = torch.full((128, 128), float("nan"), device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = st(A.data_ptr(), B.data_ptr(), D.data_ptr(), K, a_swz, b_mn, status.data_ptr(), None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = A.float() @ Bkn.float()
+    err = (D - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 1e-5, err
