@@ -145,11 +145,13 @@ size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* bas
   W.gxh = nullptr;
   W.ybh = W.ybl = nullptr;
   W.pbuf = nullptr;
+  W.g1 = nullptr;
   if (p->use_tc) {
     W.ybh = take(Bz * p->y_len * 2 * 2);
     if (p->cfg.precision == JTFS_PREC_FP32) W.ybl = take(Bz * p->y_len * 2 * 2);
     W.pbuf = (float*)take(Bz * p->n2 * (size_t)p->C * p->n1 * p->n_t * 4);
   }
+  if (with_grad && p->use_tcb) W.g1 = take(tcb_g1_bytes(p, B));
   if (with_grad) {
     W.gy = (float2*)take(Bz * p->y_len * 8);
     W.gu1 = (float*)take(Bz * p->u1_len * 4);
@@ -186,6 +188,7 @@ void jtfs_plan_destroy(jtfs_plan* p) {
   for (auto e : p->prof.pool) cudaEventDestroy(e);
   if (p->d_mem) cudaFree(p->d_mem);
   if (p->d_tc_mem) cudaFree(p->d_tc_mem);
+  if (p->d_tcb_mem) cudaFree(p->d_tcb_mem);
   delete p;
 }
 
@@ -200,8 +203,10 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   p->N = N;
   p->d_mem = nullptr;
   p->d_tc_mem = nullptr;
+  p->d_tcb_mem = nullptr;
   p->d_err = nullptr;
   p->use_tc = false;
+  p->use_tcb = false;
   if ((st = cuda_check(cudaGetDevice(&p->device), "cudaGetDevice")) != JTFS_OK) {
     delete p;
     return st;
@@ -360,6 +365,10 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
     if (!tc_supported(p)) return fail(JTFS_ERR_UNSUPPORTED, "configuration outside the tensor-core kernel");
     p->use_tc = true;
     if ((st = build_tc_tables(p)) != JTFS_OK) return fail(st, "");
+    if (tcb_supported(p)) {
+      p->use_tcb = true;
+      if ((st = build_tcb_tables(p)) != JTFS_OK) return fail(st, "");
+    }
   }
   *out = p;
   return JTFS_OK;

@@ -100,6 +100,14 @@ struct jtfs_plan {
   int* d_tc_items;
   int* d_err;                  // device status word of the bounded waits
   void* d_tc_mem;
+  // tensor-core backward of the joint stage
+  bool use_tcb;
+  std::vector<int> tcb_items;  // (alpha, n0, lambda' start, K1) per signal, longest first
+  int* d_tcb_items;
+  void* d_wtb;                 // [rows][NT] bf16 pooling weights (time-major)
+  int* d_wtb_row0;             // [n2]
+  int tcb_wt_rows;
+  void* d_tcb_mem;
   mutable jtfs::Profiler prof;
 };
 
@@ -125,6 +133,7 @@ struct Workspace {
   void* ybh;       // [B * y_len * 2] bf16 (tensor-core path)
   void* ybl;       // [B * y_len * 2] bf16 (three-pass split only)
   float* pbuf;     // [B][n2][C * n1][n_t] time-pooled rows
+  void* g1;        // phi_F adjoint of g_S2 (tensor-core backward), bf16
 };
 size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* base, Workspace* w);
 
@@ -144,6 +153,12 @@ int tc_nt(int n_t);
 jtfs_status build_tc_tables(jtfs_plan* p);
 jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi, const void* ylo,
                                 float* Pbuf, float* s2, cudaStream_t st);
+
+bool tcb_supported(const jtfs_plan* p);
+jtfs_status build_tcb_tables(jtfs_plan* p);
+size_t tcb_g1_bytes(const jtfs_plan* p, int64_t B);
+jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi, const void* ylo,
+                                const float* gs2, void* g1buf, float2* gy, cudaStream_t st);
 
 jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0, float* s1,
                            float* s2, float* u1, const Workspace& w, cudaStream_t st);

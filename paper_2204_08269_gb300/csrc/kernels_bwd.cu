@@ -293,7 +293,8 @@ jtfs_status set_attrs() {
   const int big = 227 * 1024;
   const void* fns[] = {(const void*)k_uh_from_u1, (const void*)k_joint_bwd_simt,
                        (const void*)k_second_order_bwd, (const void*)k_stage1_bwd,
-                       (const void*)k_gx, (const void*)k_xfft_sub, (const void*)k_second_order<0>};
+                       (const void*)k_gx, (const void*)k_xfft_sub, (const void*)k_second_order<0>,
+                       (const void*)k_second_order<1>};
   for (const void* f : fns) {
     jtfs_status st = cuda_check(
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr");
@@ -327,12 +328,23 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
     k_uh_from_u1<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 8, st>>>(d, u1, w.uh);
   }
   const size_t n_items = p->items.size() / 2;
-  if (gs2 && n_items > 0) {
+  if (gs2 && n_items > 0 && p->use_tcb) {
+    {
+      StageScope sc(p, kStSecondOrder, st, 1);
+      k_second_order<1><<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
+                         (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
+                                                     w.uh, nullptr, (__nv_bfloat16*)w.ybh,
+                                                     (__nv_bfloat16*)w.ybl, B);
+    }
+    StageScope sc(p, kStJointBwd, st, 2);
+    jtfs_status r2 = launch_joint_bwd_tc(p, B, w.ybh, w.ybl, gs2, w.g1, w.gy, st);
+    if (r2 != JTFS_OK) return r2;
+  } else if (gs2 && n_items > 0) {
     {
       StageScope sc(p, kStSecondOrder, st, 1);
       k_second_order<0><<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
-                       (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
-                                                   w.uh, w.y, nullptr, nullptr, B);
+                         (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
+                                                     w.uh, w.y, nullptr, nullptr, B);
     }
     StageScope sc(p, kStJointBwd, st, 1);
     k_joint_bwd_simt<<<dim3((unsigned)n_items, B), kJT, joint_bwd_smem(p), st>>>(

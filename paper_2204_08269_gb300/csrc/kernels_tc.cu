@@ -339,7 +339,7 @@ bool tc_supported(const jtfs_plan* p) {
 
 jtfs_status build_tc_tables(jtfs_plan* p) {
   const int NT = tc_nt(p->n_t);
-  p->n1_pad = (p->n1 + kBK - 1) / kBK * kBK;
+  p->n1_pad = (p->n1 + 63) / 64 * 64;   // W plane rows hold whole 64-column boxes
   const size_t wplane = (size_t)p->C * p->n1 * p->n1_pad;
   std::vector<long long> wt_off(p->n2);
   long long wt_len = 0;

@@ -1,0 +1,898 @@
+// Tensor-core (tcgen05) backward of the joint stage (Sec. 5: reverse-ordered adjoints of
+// Eq. 3): for every rate alpha, signal b and tile of 128 time samples n,
+//     Z^T[n, r]   = sum_lambda' Y^T[n, lambda'] W^T[lambda', r]        (recomputed, complex)
+//     g|Z|^T[n,r] = sum_t w_alpha[n, t] G1[r, t]                        (phi_T adjoint; G1 = phi_F
+//                                                                      adjoint applied to g_S2)
+//     gZ^T[n, r]  = g|Z|^T[n, r] Z^T[n, r] / |Z^T[n, r]|  (0 at Z = 0)
+//     gY^T[n, l'] = sum_r gZ^T[n, r] conj(W[r, l'])
+// The rows r = c * n1 + lambda of W are visited in chunks of 32; the same W chunk in shared
+// memory is the K-major B operand of the first product and the MN-major B operand of the
+// last.  The time index n lives in the TMEM lanes, so each epilogue thread owns one sample.
+// One BF16 pass (gradients are held to 1e-3 relative).
+//
+// TMEM columns: Z^T Re [0,32) Im [32,64), g|Z|^T [64,96), gY^T Re [128,288) Im [288,448).
+// Roles (384 threads): warp 0 TMA producer, warp 1 MMA issuer / TMEM owner, warps 4..11
+// epilogue (two warps per lane quarter, each on half of the columns).  Waits are bounded.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "tma_host.h"
+#include "umma.cuh"
+
+namespace jtfs {
+
+using namespace umma;
+
+namespace {
+
+constexpr int kRC = 32;          // W rows per chunk
+constexpr int kK1Max = 160;      // lambda' rows of the resident Y^T tile
+constexpr int kThreads = 384;
+constexpr int kEpiWarp0 = 4;
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+constexpr uint32_t kA1Bytes = 2 * 2 * kK1Max * 128;       // Re/Im x two 64-sample halves
+constexpr uint32_t kWBufBytes = 2 * 3 * kRC * 128;        // Re/Im x three 64-lambda' blocks
+constexpr uint32_t kA2Bytes = 2 * 128 * kRC * 2;          // Re/Im x 128 n x 32 r bf16
+
+struct TbMaps {
+  CUtensorMap w[2];     // Wr, Wi hi planes [C*n1][n1_pad], box {64 lambda', 32 r}, 128-byte swizzle
+  CUtensorMap y[16];    // per alpha: Y hi planes [2B][K][L], box {64 n, 32 lambda', 1}
+  CUtensorMap g1;       // [rows][NT] bf16, box {NT, 32}
+  CUtensorMap wt;       // [rows][NT] bf16, box {NT, 128}
+};
+
+struct TbArgs {
+  const int4* items;    // (alpha, n0, lam_start, K1) per signal, longest first
+  int n_items;          // n_base * B
+  int B;
+  int n_rows;           // C * n1
+  int n_chunks;         // ceil(n_rows / 32)
+  int g1_rows;          // rows per (b, alpha) block of G1 = n_chunks * 32
+  const int* wt_row0;   // [n2] first row of each rate in the weight table
+  float2* gy;           // [B][y_len] complex FP32, rows (lambda' - lam_min) x L_alpha
+  int* err;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(kThreads, 1)
+k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr uint32_t kSw = NT * 2;                       // bytes per row of the NT-wide tiles
+  constexpr uint32_t kLayNT = kSw == 128 ? kSw128 : (kSw == 64 ? kSw64 : kSw32);
+  constexpr uint32_t kG1Bytes = ((kRC * NT * 2 + 1023) / 1024) * 1024;
+  constexpr uint32_t kA4Bytes = ((128 * NT * 2 + 1023) / 1024) * 1024;
+  uint8_t* sA1 = sm;
+  uint8_t* sW = sA1 + kA1Bytes;                          // 2 buffers
+  uint8_t* sG1 = sW + 2 * kWBufBytes;                    // 2 buffers
+  uint8_t* sA4 = sG1 + 2 * kG1Bytes;
+  uint8_t* sA2 = sA4 + kA4Bytes;                         // 2 buffers
+
+  __shared__ uint64_t a1_full, a1_free, w_full[2], w_empty[2], d1_full, d1_free, a2_full[2],
+      a2_free[2], d2_full, d2_free, mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(&a1_full, 1);
+    mbar_init(&a1_free, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&w_full[i], 1);
+      mbar_init(&w_empty[i], 1);
+      mbar_init(&a2_full[i], 8);
+      mbar_init(&a2_free[i], 1);
+    }
+    mbar_init(&d1_full, 1);
+    mbar_init(&d1_free, 8);
+    mbar_init(&d2_full, 1);
+    mbar_init(&d2_free, 8);
+    mbar_init(&mma_done, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  auto fail = [&](int code) {
+    if (!abort_flag) {
+      abort_flag = 1;
+      atomicCAS(args.err, 0, code);
+    }
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t a1_ph = 0;
+      int wst = 0;
+      uint32_t wph = 0;
+      int armed_w[2] = {-1, -1}, armed_a1 = -1;
+      for (int it = blockIdx.x; it < args.n_items && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it / args.B];
+        const int a = item.x, b = it % args.B, n0 = item.y, start = item.z, K1 = item.w;
+        const Rate2 A = P.rates2[a];
+        if (!mbar_wait(&a1_free, a1_ph ^ 1, kWaitNs)) { fail(21); break; }
+        const uint32_t a1_bytes = 2 * 2 * (K1 / 32) * 4096 + 128 * NT * 2;
+        mbar_arrive_expect_tx(&a1_full, a1_bytes);
+        armed_a1 = (int)a1_ph;
+        for (int p = 0; p < 2; ++p)
+          for (int h = 0; h < 2; ++h)
+            for (int kb = 0; kb < K1 / 32; ++kb)
+              tma_load_3d(sA1 + (p * 2 + h) * kK1Max * 128 + kb * 32 * 128, &maps.y[a],
+                          n0 + h * 64, start - A.lam_min + kb * 32, 2 * b + p, &a1_full);
+        tma_load_2d(sA4, &maps.wt, 0, args.wt_row0[a] + n0, &a1_full);
+        a1_ph ^= 1;
+        const int nblk = (K1 + 63) / 64;
+        const int g1row = (b * P.n2 + a) * args.g1_rows;
+        for (int j = 0; j < args.n_chunks; ++j) {
+          if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(22); break; }
+          mbar_arrive_expect_tx(&w_full[wst], 2 * nblk * 4096 + kRC * NT * 2);
+          armed_w[wst] = (int)wph;
+          uint8_t* wb = sW + wst * kWBufBytes;
+          for (int p = 0; p < 2; ++p)
+            for (int kb = 0; kb < nblk; ++kb)
+              tma_load_2d(wb + (p * 3 + kb) * 4096, &maps.w[p], start + kb * 64, j * kRC,
+                          &w_full[wst]);
+          tma_load_2d(sG1 + wst * kG1Bytes, &maps.g1, 0, g1row + j * kRC, &w_full[wst]);
+          if (++wst == 2) { wst = 0; wph ^= 1; }
+        }
+      }
+      for (int i = 0; i < 2; ++i)
+        if (armed_w[i] >= 0) mbar_wait(&w_full[i], (uint32_t)armed_w[i], kWaitNs);
+      if (armed_a1 >= 0) mbar_wait(&a1_full, (uint32_t)armed_a1, kWaitNs);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t t_d1r = tbase, t_d1i = tbase + 32, t_d4 = tbase + 64;
+      const uint32_t t_d2r = tbase + 128, t_d2i = tbase + 288;
+      uint32_t a1_ph = 0, d1f_ph = 0, d2f_ph = 0;
+      int wst = 0;
+      uint32_t wph = 0;
+      uint32_t a2_ph[2] = {0, 0};
+      for (int it = blockIdx.x; it < args.n_items && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it / args.B];
+        const int K1 = item.w;
+        const int N2 = K1;
+        const uint32_t id1 = instr_desc(128, kRC, 1, 1, 1, 0, 0);
+        const uint32_t id1n = instr_desc(128, kRC, 1, 1, 1, 0, 1);
+        const uint32_t id4 = instr_desc(128, kRC, 1, 1, 0, 0, 0);
+        const uint32_t id2 = instr_desc(128, N2, 1, 1, 0, 1, 0);
+        const uint32_t id2n = instr_desc(128, N2, 1, 1, 0, 1, 1);
+        if (!mbar_wait(&a1_full, a1_ph, kWaitNs)) { fail(23); break; }
+        a1_ph ^= 1;
+        const uint32_t a1 = smem_u32(sA1), a4 = smem_u32(sA4);
+        int prev_wst = -1;
+        bool first_d2 = true;
+        bool ok = true;
+        for (int j = 0; j <= args.n_chunks && ok; ++j) {
+          if (j < args.n_chunks) {
+            if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(24); ok = false; break; }
+            if (!mbar_wait(&d1_free, d1f_ph ^ 1, kWaitNs)) { fail(25); ok = false; break; }
+            d1f_ph ^= 1;
+            tc_fence_after();
+            const uint32_t wb = smem_u32(sW + wst * kWBufBytes);
+            for (int ks = 0; ks < K1 / 16; ++ks) {
+              const int kb = ks >> 2, ko = (ks & 3) * 32;
+              // A: Y^T (MN-major, n contiguous); B: W chunk (K-major)
+              const uint64_t ayr = smem_desc(a1 + 0 * 2 * kK1Max * 128 + ks * 2048, kK1Max * 128, 1024, kSw128);
+              const uint64_t ayi = smem_desc(a1 + 1 * 2 * kK1Max * 128 + ks * 2048, kK1Max * 128, 1024, kSw128);
+              const uint64_t bwr = smem_desc(wb + (0 * 3 + kb) * 4096 + ko, 16, 1024, kSw128);
+              const uint64_t bwi = smem_desc(wb + (1 * 3 + kb) * 4096 + ko, 16, 1024, kSw128);
+              const uint32_t f = ks > 0 ? 1u : 0u;
+              mma_f16(t_d1r, ayr, bwr, id1, f);      // Yr Wr
+              mma_f16(t_d1r, ayi, bwi, id1n, 1u);    // -Yi Wi
+              mma_f16(t_d1i, ayr, bwi, id1, f);      // Yr Wi
+              mma_f16(t_d1i, ayi, bwr, id1, 1u);     // Yi Wr
+            }
+            const uint32_t g1 = smem_u32(sG1 + wst * kG1Bytes);
+            for (int ks = 0; ks < NT / 16; ++ks)
+              mma_f16(t_d4, smem_desc(a4 + ks * 32, 16, 8 * kSw, kLayNT),
+                      smem_desc(g1 + ks * 32, 16, 8 * kSw, kLayNT), id4, ks > 0 ? 1u : 0u);
+            mma_commit(&d1_full);
+          }
+          if (j >= 1) {
+            // gY^T += gZ^T(chunk j-1) conj(W chunk j-1)
+            const int q = (j - 1) & 1;
+            if (!mbar_wait(&a2_full[q], a2_ph[q], kWaitNs)) { fail(26); ok = false; break; }
+            a2_ph[q] ^= 1;
+            if (first_d2) {
+              if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(27); ok = false; break; }
+              d2f_ph ^= 1;
+            }
+            tc_fence_after();
+            const uint32_t wb = smem_u32(sW + prev_wst * kWBufBytes);
+            const uint32_t a2 = smem_u32(sA2 + q * kA2Bytes);
+            for (int ks = 0; ks < kRC / 16; ++ks) {
+              const uint64_t agr = smem_desc(a2 + 0 * 128 * 64 + ks * 32, 16, 512, kSw64);
+              const uint64_t agi = smem_desc(a2 + 1 * 128 * 64 + ks * 32, 16, 512, kSw64);
+              const uint64_t bwr = smem_desc(wb + 0 * 3 * 4096 + ks * 2048, 4096, 1024, kSw128);
+              const uint64_t bwi = smem_desc(wb + 1 * 3 * 4096 + ks * 2048, 4096, 1024, kSw128);
+              const uint32_t f = (first_d2 && ks == 0) ? 0u : 1u;
+              mma_f16(t_d2r, agr, bwr, id2, f);      // gZr Wr
+              mma_f16(t_d2r, agi, bwi, id2, 1u);     // gZi Wi
+              mma_f16(t_d2i, agi, bwr, id2, f);      // gZi Wr
+              mma_f16(t_d2i, agr, bwi, id2n, 1u);    // -gZr Wi
+            }
+            first_d2 = false;
+            mma_commit(&a2_free[q]);
+            mma_commit(&w_empty[prev_wst]);
+          }
+          if (j < args.n_chunks) {
+            prev_wst = wst;
+            if (++wst == 2) { wst = 0; wph ^= 1; }
+          }
+        }
+        if (!ok) break;
+        mma_commit(&a1_free);
+        mma_commit(&d2_full);
+      }
+      mma_commit(&mma_done);
+      mbar_wait(&mma_done, 0, kWaitNs);
+    }
+  } else if (warp >= kEpiWarp0) {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - kEpiWarp0;
+    const int quarter = warp & 3;
+    const int half = ew >> 2;
+    const int row = quarter * 32 + lane;       // time sample within the tile
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    uint32_t d1_ph = 0, d2_ph = 0;
+    uint32_t a2f_ph[2] = {0, 0};
+    for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+      const int4 item = args.items[it / args.B];
+      const int a = item.x, b = it % args.B, n0 = item.y, start = item.z, K1 = item.w;
+      bool ok = !abort_flag;
+      for (int j = 0; j < args.n_chunks && ok; ++j) {
+        if (!mbar_wait(&d1_full, d1_ph, kWaitNs)) { fail(28); ok = false; break; }
+        d1_ph ^= 1;
+        tc_fence_after();
+        float zr[16], zi[16], g[16];
+        tmem_ld16(tbase + lane_off + 0 + half * 16, zr);
+        tmem_ld16(tbase + lane_off + 32 + half * 16, zi);
+        tmem_ld16(tbase + lane_off + 64 + half * 16, g);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&d1_free);
+        uint32_t pr[8], pi[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float v[2][2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int k = 2 * i + e;
+            const float m = sqrtf(zr[k] * zr[k] + zi[k] * zi[k]);
+            const float f = m > 0.f ? g[k] / m : 0.f;
+            v[0][e] = zr[k] * f;
+            v[1][e] = zi[k] * f;
+          }
+          __nv_bfloat162 hr = __floats2bfloat162_rn(v[0][0], v[0][1]);
+          __nv_bfloat162 hi = __floats2bfloat162_rn(v[1][0], v[1][1]);
+          pr[i] = *reinterpret_cast<uint32_t*>(&hr);
+          pi[i] = *reinterpret_cast<uint32_t*>(&hi);
+        }
+        const int q = j & 1;
+        if (!mbar_wait(&a2_free[q], a2f_ph[q] ^ 1, kWaitNs)) { fail(29); ok = false; break; }
+        a2f_ph[q] ^= 1;
+        // K-major rows of 64 bytes (32 r), 64-byte swizzle: 16-byte chunk c -> c ^ ((row >> 1) & 3)
+        uint8_t* base = sA2 + q * kA2Bytes + row * 64;
+        const int sw = (row >> 1) & 3;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int chunk = half * 2 + c;
+          uint4 vr = make_uint4(pr[4 * c], pr[4 * c + 1], pr[4 * c + 2], pr[4 * c + 3]);
+          uint4 vi = make_uint4(pi[4 * c], pi[4 * c + 1], pi[4 * c + 2], pi[4 * c + 3]);
+          *reinterpret_cast<uint4*>(base + ((chunk ^ sw) * 16)) = vr;
+          *reinterpret_cast<uint4*>(base + 128 * 64 + ((chunk ^ sw) * 16)) = vi;
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a2_full[q]);
+      }
+      if (!ok) break;
+      // gY^T for this tile: columns lambda' = start + c, written as gY[lambda' - lam_min][n]
+      if (!mbar_wait(&d2_full, d2_ph, kWaitNs)) { fail(30); break; }
+      d2_ph ^= 1;
+      tc_fence_after();
+      const Rate2 A = P.rates2[a];
+      const int n = n0 + row;
+      float2* go = args.gy + (size_t)b * P.y_len + A.off_y;
+      const int N2 = K1, hw = N2 / 2;
+      for (int c0 = half * hw; c0 < (half + 1) * hw; c0 += 16) {
+        float vr[16], vi[16];
+        tmem_ld16(tbase + lane_off + 128 + c0, vr);
+        tmem_ld16(tbase + lane_off + 288 + c0, vi);
+        tmem_wait_ld();
+        if (n < A.L) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int lp = start + c0 + i;
+            if (lp >= A.lam_min && lp < P.n1)
+              go[(size_t)(lp - A.lam_min) * A.L + n] = make_float2(vr[i], vi[i]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d2_free);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
+// Three-pass variant (each product split x = hi + lo: hi*hi + hi*lo + lo*hi), for FP32-level
+// gradients.  Shared memory cannot hold a resident hi/lo Y^T tile, so the Y^T tile is
+// streamed in 32-lambda' blocks for every W chunk through a two-stage pipeline.
+struct Tb3Maps {
+  CUtensorMap w[4];      // Wr_hi, Wi_hi, Wr_lo, Wi_lo, box {64 lambda', 32 r}
+  CUtensorMap y[2][16];  // [hi/lo][alpha], box {64 n, 32 lambda', 1}
+  CUtensorMap g1[2];     // hi, lo: box {NT, 32}
+  CUtensorMap wt[2];     // hi, lo: box {NT, 128}
+};
+
+template <int NT, int WB>
+__global__ void __launch_bounds__(kThreads, 1)
+k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr uint32_t kSw = NT * 2;
+  constexpr uint32_t kLayNT = kSw == 128 ? kSw128 : (kSw == 64 ? kSw64 : kSw32);
+  constexpr uint32_t kYStage = 4 * 8192;                      // 4 planes x [32 x 128] bf16
+  constexpr uint32_t kWBuf = 4 * 3 * 4096;                    // 4 planes x 3 blocks
+  constexpr uint32_t kG1Plane = ((kRC * NT * 2 + 1023) / 1024) * 1024;
+  constexpr uint32_t kA4Plane = ((128 * NT * 2 + 1023) / 1024) * 1024;
+  constexpr uint32_t kA2Plane = 128 * 64;                     // [128 n x 32 r] bf16
+  uint8_t* sY = sm;                                           // 2 stages
+  uint8_t* sW = sY + 2 * kYStage;                             // WB buffers
+  uint8_t* sG1 = sW + WB * kWBuf;                             // WB buffers x 2 planes
+  uint8_t* sA4 = sG1 + WB * 2 * kG1Plane;                     // 2 planes
+  uint8_t* sA2 = sA4 + 2 * kA4Plane;                          // 4 planes
+
+  __shared__ uint64_t y_full[2], y_empty[2], w_full[2], w_empty[2], a4_full, a4_free, d1_full,
+      d1_free, a2_full, a2_free, d2_full, d2_free, mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&y_full[i], 1);
+      mbar_init(&y_empty[i], 1);
+      mbar_init(&w_full[i], 1);
+      mbar_init(&w_empty[i], 1);
+    }
+    mbar_init(&a4_full, 1);
+    mbar_init(&a4_free, 1);
+    mbar_init(&d1_full, 1);
+    mbar_init(&d1_free, 8);
+    mbar_init(&a2_full, 8);
+    mbar_init(&a2_free, 1);
+    mbar_init(&d2_full, 1);
+    mbar_init(&d2_free, 8);
+    mbar_init(&mma_done, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  auto fail = [&](int code) {
+    if (!abort_flag) {
+      abort_flag = 1;
+      atomicCAS(args.err, 0, code);
+    }
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      uint32_t a4_ph = 0, yph = 0, wph = 0;
+      int ys = 0, wst = 0;
+      int armed_y[2] = {-1, -1}, armed_w[2] = {-1, -1}, armed_a4 = -1;
+      for (int it = blockIdx.x; it < args.n_items && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it / args.B];
+        const int a = item.x, b = it % args.B, n0 = item.y, start = item.z, K1 = item.w;
+        const Rate2 A = P.rates2[a];
+        if (!mbar_wait(&a4_free, a4_ph ^ 1, kWaitNs)) { fail(41); break; }
+        mbar_arrive_expect_tx(&a4_full, 2 * 128 * NT * 2);
+        armed_a4 = (int)a4_ph;
+        for (int h = 0; h < 2; ++h)
+          tma_load_2d(sA4 + h * kA4Plane, &maps.wt[h], 0, args.wt_row0[a] + n0, &a4_full);
+        a4_ph ^= 1;
+        const int nblk = (K1 + 63) / 64;
+        const int g1row = (b * P.n2 + a) * args.g1_rows;
+        bool ok = true;
+        for (int j = 0; j < args.n_chunks && ok; ++j) {
+          if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(42); ok = false; break; }
+          mbar_arrive_expect_tx(&w_full[wst], 4 * nblk * 4096 + 2 * kRC * NT * 2);
+          armed_w[wst] = (int)wph;
+          uint8_t* wb = sW + wst * kWBuf;
+          for (int p = 0; p < 4; ++p)
+            for (int kb = 0; kb < nblk; ++kb)
+              tma_load_2d(wb + (p * 3 + kb) * 4096, &maps.w[p], start + kb * 64, j * kRC,
+                          &w_full[wst]);
+          for (int h = 0; h < 2; ++h)
+            tma_load_2d(sG1 + (wst * 2 + h) * kG1Plane, &maps.g1[h], 0, g1row + j * kRC,
+                        &w_full[wst]);
+          if (++wst == WB) { wst = 0; wph ^= 1; }
+          for (int kb = 0; kb < K1 / 32; ++kb) {
+            if (!mbar_wait(&y_empty[ys], yph ^ 1, kWaitNs)) { fail(43); ok = false; break; }
+            mbar_arrive_expect_tx(&y_full[ys], kYStage);
+            armed_y[ys] = (int)yph;
+            uint8_t* yb = sY + ys * kYStage;
+            for (int h = 0; h < 2; ++h)        // hi, lo
+              for (int part = 0; part < 2; ++part)
+                for (int nh = 0; nh < 2; ++nh)
+                  tma_load_3d(yb + (h * 2 + part) * 8192 + nh * 4096, &maps.y[h][a],
+                              n0 + nh * 64, start - A.lam_min + kb * 32, 2 * b + part,
+                              &y_full[ys]);
+            if (++ys == 2) { ys = 0; yph ^= 1; }
+          }
+        }
+        if (!ok) break;
+      }
+      for (int i = 0; i < 2; ++i) {
+        if (armed_y[i] >= 0) mbar_wait(&y_full[i], (uint32_t)armed_y[i], kWaitNs);
+        if (armed_w[i] >= 0) mbar_wait(&w_full[i], (uint32_t)armed_w[i], kWaitNs);
+      }
+      if (armed_a4 >= 0) mbar_wait(&a4_full, (uint32_t)armed_a4, kWaitNs);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint32_t t_d1r = tbase, t_d1i = tbase + 32, t_d4 = tbase + 64;
+      const uint32_t t_d2r = tbase + 128, t_d2i = tbase + 288;
+      uint32_t a4_ph = 0, d1f_ph = 0, d2f_ph = 0, a2_ph = 0, yph = 0, wph = 0;
+      int ys = 0, wst = 0;
+      const int pa_[3] = {0, 0, 1}, pb_[3] = {0, 1, 0};
+      for (int it = blockIdx.x; it < args.n_items && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it / args.B];
+        const int K1 = item.w, N2 = K1;
+        const uint32_t id1 = instr_desc(128, kRC, 1, 1, 1, 0, 0);
+        const uint32_t id1n = instr_desc(128, kRC, 1, 1, 1, 0, 1);
+        const uint32_t id4 = instr_desc(128, kRC, 1, 1, 0, 0, 0);
+        const uint32_t id2 = instr_desc(128, N2, 1, 1, 0, 1, 0);
+        const uint32_t id2n = instr_desc(128, N2, 1, 1, 0, 1, 1);
+        if (!mbar_wait(&a4_full, a4_ph, kWaitNs)) { fail(44); break; }
+        a4_ph ^= 1;
+        const uint32_t a4 = smem_u32(sA4);
+        bool first_d2 = true, ok = true;
+        for (int j = 0; j <= args.n_chunks && ok; ++j) {
+          if (j < args.n_chunks) {
+            if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(45); ok = false; break; }
+            if (!mbar_wait(&d1_free, d1f_ph ^ 1, kWaitNs)) { fail(46); ok = false; break; }
+            d1f_ph ^= 1;
+            tc_fence_after();
+            const uint32_t wb = smem_u32(sW + wst * kWBuf);
+            for (int kb = 0; kb < K1 / 32; ++kb) {
+              if (!mbar_wait(&y_full[ys], yph, kWaitNs)) { fail(47); ok = false; break; }
+              tc_fence_after();
+              const uint32_t yb = smem_u32(sY + ys * kYStage);
+              for (int ks = 0; ks < 2; ++ks) {
+                const uint32_t woff = (kb >> 1) * 4096 + ((kb & 1) * 2 + ks) * 32;
+                for (int q = 0; q < 3; ++q) {
+                  const int pa = pa_[q], pb = pb_[q];
+                  const uint64_t ayr = smem_desc(yb + (pa * 2 + 0) * 8192 + ks * 2048, 4096, 1024, kSw128);
+                  const uint64_t ayi = smem_desc(yb + (pa * 2 + 1) * 8192 + ks * 2048, 4096, 1024, kSw128);
+                  const uint64_t bwr = smem_desc(wb + (pb * 2 + 0) * 3 * 4096 + woff, 16, 1024, kSw128);
+                  const uint64_t bwi = smem_desc(wb + (pb * 2 + 1) * 3 * 4096 + woff, 16, 1024, kSw128);
+                  const uint32_t f = (kb == 0 && ks == 0 && q == 0) ? 0u : 1u;
+                  mma_f16(t_d1r, ayr, bwr, id1, f);
+                  mma_f16(t_d1r, ayi, bwi, id1n, 1u);
+                  mma_f16(t_d1i, ayr, bwi, id1, f);
+                  mma_f16(t_d1i, ayi, bwr, id1, 1u);
+                }
+              }
+              mma_commit(&y_empty[ys]);
+              if (++ys == 2) { ys = 0; yph ^= 1; }
+            }
+            if (!ok) break;
+            const uint32_t g1 = smem_u32(sG1 + wst * 2 * kG1Plane);
+            for (int ks = 0; ks < NT / 16; ++ks)
+              for (int q = 0; q < 3; ++q)
+                mma_f16(t_d4, smem_desc(a4 + pa_[q] * kA4Plane + ks * 32, 16, 8 * kSw, kLayNT),
+                        smem_desc(g1 + pb_[q] * kG1Plane + ks * 32, 16, 8 * kSw, kLayNT), id4,
+                        (ks == 0 && q == 0) ? 0u : 1u);
+            mma_commit(&d1_full);
+          }
+          // gY^T += gZ^T conj(W) for chunk g2: the previous chunk when two W buffers let the
+          // next Z product run first, else this chunk (its W buffer is the only one)
+          const int g2 = WB == 1 ? j : j - 1;
+          if (g2 >= 0 && g2 < args.n_chunks) {
+            if (!mbar_wait(&a2_full, a2_ph, kWaitNs)) { fail(48); ok = false; break; }
+            a2_ph ^= 1;
+            if (first_d2) {
+              if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(49); ok = false; break; }
+              d2f_ph ^= 1;
+            }
+            tc_fence_after();
+            const int gw = g2 % WB;
+            const uint32_t wb = smem_u32(sW + gw * kWBuf);
+            const uint32_t a2 = smem_u32(sA2);
+            for (int ks = 0; ks < kRC / 16; ++ks) {
+              for (int q = 0; q < 3; ++q) {
+                const int pa = pa_[q], pb = pb_[q];
+                const uint64_t agr = smem_desc(a2 + (pa * 2 + 0) * kA2Plane + ks * 32, 16, 512, kSw64);
+                const uint64_t agi = smem_desc(a2 + (pa * 2 + 1) * kA2Plane + ks * 32, 16, 512, kSw64);
+                const uint64_t bwr = smem_desc(wb + (pb * 2 + 0) * 3 * 4096 + ks * 2048, 4096, 1024, kSw128);
+                const uint64_t bwi = smem_desc(wb + (pb * 2 + 1) * 3 * 4096 + ks * 2048, 4096, 1024, kSw128);
+                const uint32_t f = (first_d2 && ks == 0 && q == 0) ? 0u : 1u;
+                mma_f16(t_d2r, agr, bwr, id2, f);
+                mma_f16(t_d2r, agi, bwi, id2, 1u);
+                mma_f16(t_d2i, agi, bwr, id2, f);
+                mma_f16(t_d2i, agr, bwi, id2n, 1u);
+              }
+            }
+            first_d2 = false;
+            mma_commit(&a2_free);
+            mma_commit(&w_empty[gw]);
+          }
+          if (j < args.n_chunks) {
+            if (++wst == WB) { wst = 0; wph ^= 1; }
+          }
+        }
+        if (!ok) break;
+        mma_commit(&a4_free);
+        mma_commit(&d2_full);
+      }
+      mma_commit(&mma_done);
+      mbar_wait(&mma_done, 0, kWaitNs);
+    }
+  } else if (warp >= kEpiWarp0) {
+    const int ew = warp - kEpiWarp0;
+    const int quarter = warp & 3;
+    const int half = ew >> 2;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    uint32_t d1_ph = 0, d2_ph = 0, a2f_ph = 0;
+    for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+      const int4 item = args.items[it / args.B];
+      const int a = item.x, b = it % args.B, n0 = item.y, start = item.z, K1 = item.w;
+      bool ok = !abort_flag;
+      for (int j = 0; j < args.n_chunks && ok; ++j) {
+        if (!mbar_wait(&d1_full, d1_ph, kWaitNs)) { fail(50); ok = false; break; }
+        d1_ph ^= 1;
+        tc_fence_after();
+        float zr[16], zi[16], g[16];
+        tmem_ld16(tbase + lane_off + 0 + half * 16, zr);
+        tmem_ld16(tbase + lane_off + 32 + half * 16, zi);
+        tmem_ld16(tbase + lane_off + 64 + half * 16, g);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&d1_free);
+        uint32_t hr[8], hi[8], lr[8], li[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          float vr[2], vi[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int k = 2 * i + e;
+            const float m = sqrtf(zr[k] * zr[k] + zi[k] * zi[k]);
+            const float f = m > 0.f ? g[k] / m : 0.f;
+            vr[e] = zr[k] * f;
+            vi[e] = zi[k] * f;
+          }
+          __nv_bfloat162 a0 = __floats2bfloat162_rn(vr[0], vr[1]);
+          __nv_bfloat162 a1 = __floats2bfloat162_rn(vi[0], vi[1]);
+          const float2 fa0 = __bfloat1622float2(a0), fa1 = __bfloat1622float2(a1);
+          __nv_bfloat162 b0 = __floats2bfloat162_rn(vr[0] - fa0.x, vr[1] - fa0.y);
+          __nv_bfloat162 b1 = __floats2bfloat162_rn(vi[0] - fa1.x, vi[1] - fa1.y);
+          hr[i] = *reinterpret_cast<uint32_t*>(&a0);
+          hi[i] = *reinterpret_cast<uint32_t*>(&a1);
+          lr[i] = *reinterpret_cast<uint32_t*>(&b0);
+          li[i] = *reinterpret_cast<uint32_t*>(&b1);
+        }
+        if (!mbar_wait(&a2_free, a2f_ph ^ 1, kWaitNs)) { fail(51); ok = false; break; }
+        a2f_ph ^= 1;
+        uint8_t* base = sA2 + row * 64;
+        const int sw = (row >> 1) & 3;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int pos = ((half * 2 + c) ^ sw) * 16;
+          *reinterpret_cast<uint4*>(base + 0 * kA2Plane + pos) = make_uint4(hr[4 * c], hr[4 * c + 1], hr[4 * c + 2], hr[4 * c + 3]);
+          *reinterpret_cast<uint4*>(base + 1 * kA2Plane + pos) = make_uint4(hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
+          *reinterpret_cast<uint4*>(base + 2 * kA2Plane + pos) = make_uint4(lr[4 * c], lr[4 * c + 1], lr[4 * c + 2], lr[4 * c + 3]);
+          *reinterpret_cast<uint4*>(base + 3 * kA2Plane + pos) = make_uint4(li[4 * c], li[4 * c + 1], li[4 * c + 2], li[4 * c + 3]);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a2_full);
+      }
+      if (!ok) break;
+      if (!mbar_wait(&d2_full, d2_ph, kWaitNs)) { fail(52); break; }
+      d2_ph ^= 1;
+      tc_fence_after();
+      const Rate2 A = P.rates2[a];
+      const int n = n0 + row;
+      float2* go = args.gy + (size_t)b * P.y_len + A.off_y;
+      const int hw = K1 / 2;
+      for (int c0 = half * hw; c0 < (half + 1) * hw; c0 += 16) {
+        float vr[16], vi[16];
+        tmem_ld16(tbase + lane_off + 128 + c0, vr);
+        tmem_ld16(tbase + lane_off + 288 + c0, vi);
+        tmem_wait_ld();
+        if (n < A.L) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int lp = start + c0 + i;
+            if (lp >= A.lam_min && lp < P.n1)
+              go[(size_t)(lp - A.lam_min) * A.L + n] = make_float2(vr[i], vi[i]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d2_free);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
+// G1[(b n2 + a) g1_rows + c n1 + lambda][t] = sum_lo phi_F[(lo s_F - lambda) mod N_fr] gS2[b,a,c,lo,t]
+// (or gS2 itself for Eq. 4), as BF16, zero for t >= n_t and in the row padding.
+__global__ void k_g1(DevPlan Pd, const float* __restrict__ gs2, int NT, int g1_rows,
+                     __nv_bfloat16* __restrict__ g1, __nv_bfloat16* __restrict__ g1lo) {
+  const int c = blockIdx.x, a = blockIdx.y, b = blockIdx.z;
+  const int n1 = Pd.n1, nt = Pd.n_t, nfm = Pd.N_fr - 1;
+  const float* g = gs2 + (((size_t)b * Pd.n2 + a) * Pd.C + c) * (size_t)Pd.n_lo * nt;
+  const size_t o0 = ((size_t)(b * Pd.n2 + a) * g1_rows + (size_t)c * n1) * NT;
+  __nv_bfloat16* out = g1 + o0;
+  for (int i = threadIdx.x; i < n1 * NT; i += blockDim.x) {
+    const int r = i / NT, t = i % NT;
+    float s = 0.f;
+    if (t < nt) {
+      if (Pd.average_fr) {
+        for (int lo = 0; lo < Pd.n_lo; ++lo)
+          s += __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]) * g[lo * nt + t];
+      } else {
+        s = g[r * nt + t];
+      }
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(s);
+    out[i] = h;
+    if (g1lo) g1lo[o0 + i] = __float2bfloat16_rn(s - __bfloat162float(h));
+  }
+}
+
+// Weight table of the backward, [rows = sum_a Lpad_a][NT] BF16: w[n][t] = s_a phi_T[(tT - n s_a) mod N].
+__global__ void k_build_wtb(DevPlan Pd, int a, int NT, int Lpad, __nv_bfloat16* out,
+                            __nv_bfloat16* outlo) {
+  const Rate2 A = Pd.rates2[a];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Lpad * NT; i += gridDim.x * blockDim.x) {
+    const int n = i / NT, t = i % NT;
+    float v = 0.f;
+    if (A.s > 0 && n < A.L && t < Pd.n_t) v = Pd.phiT[(t * Pd.T - n * A.s) & (Pd.N - 1)] * (float)A.s;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    out[i] = h;
+    outlo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+}  // namespace
+
+int tc_nt(int n_t);
+
+size_t tcb_smem_bytes(int NT) {
+  const size_t g1 = ((kRC * NT * 2 + 1023) / 1024) * 1024;
+  const size_t a4 = ((128 * NT * 2 + 1023) / 1024) * 1024;
+  return 1024 + kA1Bytes + 2 * kWBufBytes + 2 * g1 + a4 + 2 * kA2Bytes;
+}
+
+bool tcb_supported(const jtfs_plan* p) {
+  // the resident Y^T tile holds at most 160 lambda' rows from a 64-aligned start
+  for (int a = 0; a < p->n2; ++a) {
+    const Rate2& A = p->rates2[a];
+    if (A.s == 0) continue;
+    const int start = A.lam_min / 64 * 64;
+    if (p->n1 - start > kK1Max) return false;
+  }
+  return tc_nt(p->n_t) <= 64;
+}
+
+jtfs_status build_tcb_tables(jtfs_plan* p) {
+  const int NT = tc_nt(p->n_t);
+  std::vector<int> row0(p->n2);
+  int rows = 0;
+  for (int a = 0; a < p->n2; ++a) {
+    row0[a] = rows;
+    const int L = p->rates2[a].s ? p->rates2[a].L : 0;
+    rows += (L + 127) / 128 * 128;
+  }
+  struct It { int a, n0, start, K1; long long cost; };
+  std::vector<It> its;
+  for (int a = 0; a < p->n2; ++a) {
+    const Rate2& A = p->rates2[a];
+    if (A.s == 0) continue;
+    const int start = A.lam_min / 64 * 64;
+    const int K1 = (p->n1 - start + 31) / 32 * 32;
+    for (int n0 = 0; n0 < A.L; n0 += 128) its.push_back({a, n0, start, K1, (long long)K1});
+  }
+  std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+  p->tcb_items.clear();
+  for (auto& i : its) { p->tcb_items.push_back(i.a); p->tcb_items.push_back(i.n0); p->tcb_items.push_back(i.start); p->tcb_items.push_back(i.K1); }
+  p->tcb_wt_rows = std::max(rows, 128);
+  size_t off = 0;
+  auto place = [&](size_t bytes) { size_t at = off; off += (bytes + 1023) & ~(size_t)1023; return at; };
+  const size_t o_wt = place((size_t)p->tcb_wt_rows * NT * 2 * 2);   // hi then lo
+  const size_t o_row0 = place((size_t)p->n2 * 4);
+  const size_t o_items = place(std::max<size_t>(16, p->tcb_items.size() * 4));
+  jtfs_status st;
+  if ((st = cuda_check(cudaMalloc(&p->d_tcb_mem, off), "tc backward tables")) != JTFS_OK) return st;
+  char* base = (char*)p->d_tcb_mem;
+  p->d_wtb = base + o_wt;
+  p->d_wtb_row0 = (int*)(base + o_row0);
+  p->d_tcb_items = (int*)(base + o_items);
+  if ((st = cuda_check(cudaMemset(p->d_wtb, 0, (size_t)p->tcb_wt_rows * NT * 2 * 2), "memset")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaMemcpy(p->d_wtb_row0, row0.data(), p->n2 * 4, cudaMemcpyHostToDevice), "upload")) != JTFS_OK) return st;
+  if (!p->tcb_items.empty() &&
+      (st = cuda_check(cudaMemcpy(p->d_tcb_items, p->tcb_items.data(), p->tcb_items.size() * 4, cudaMemcpyHostToDevice), "upload")) != JTFS_OK)
+    return st;
+  for (int a = 0; a < p->n2; ++a) {
+    const int L = p->rates2[a].s ? p->rates2[a].L : 0;
+    const int Lpad = (L + 127) / 128 * 128;
+    if (!Lpad) continue;
+    __nv_bfloat16* hi = (__nv_bfloat16*)p->d_wtb + (size_t)row0[a] * NT;
+    k_build_wtb<<<(Lpad * NT + 255) / 256, 256>>>(p->dp, a, NT, Lpad, hi,
+                                                  hi + (size_t)p->tcb_wt_rows * NT);
+  }
+  return cuda_check(cudaDeviceSynchronize(), "build tc backward tables");
+}
+
+size_t tcb_g1_bytes(const jtfs_plan* p, int64_t B) {   // hi and lo planes
+  const int NT = tc_nt(p->n_t);
+  const int n_chunks = (p->C * p->n1 + kRC - 1) / kRC;
+  return 2 * (size_t)B * p->n2 * (size_t)n_chunks * kRC * NT * 2;
+}
+
+int tcb3_wbufs(int NT) { return NT <= 32 ? 2 : 1; }
+
+size_t tcb3_smem_bytes(int NT) {
+  const size_t g1 = ((kRC * NT * 2 + 1023) / 1024) * 1024;
+  const size_t a4 = ((128 * NT * 2 + 1023) / 1024) * 1024;
+  const int wb = tcb3_wbufs(NT);
+  return 1024 + 2 * 4 * 8192 + (size_t)wb * 4 * 3 * 4096 + (size_t)wb * 2 * g1 + 2 * a4 + 4 * 128 * 64;
+}
+
+jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, const void* ylo_v,
+                                const float* gs2, void* g1buf, float2* gy, cudaStream_t st) {
+  const DevPlan& d = p->dp;
+  const int NT = tc_nt(p->n_t);
+  const int rows = p->C * p->n1;
+  const int n_chunks = (rows + kRC - 1) / kRC;
+  const int g1_rows = n_chunks * kRC;
+  jtfs_status rc;
+  const bool three = p->cfg.precision == JTFS_PREC_FP32;
+  const size_t g1_plane = tcb_g1_bytes(p, B) / 2;
+  __nv_bfloat16* g1hi = (__nv_bfloat16*)g1buf;
+  __nv_bfloat16* g1lo = (__nv_bfloat16*)((char*)g1buf + g1_plane);
+  // G1 (phi_F adjoint of g_S2), zero padded
+  if ((rc = cuda_check(cudaMemsetAsync(g1buf, 0, tcb_g1_bytes(p, B), st), "memset g1")) != JTFS_OK) return rc;
+  k_g1<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, gs2, NT, g1_rows, g1hi, three ? g1lo : nullptr);
+  if ((rc = cuda_check(cudaGetLastError(), "k_g1")) != JTFS_OK) return rc;
+  std::string err;
+  CUtensorMap mw[4], my[2][16], mg1[2], mwt[2];
+  for (int pl = 0; pl < 4; ++pl) {
+    cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)rows};
+    cuuint64_t str[1] = {(cuuint64_t)p->n1_pad * 2};
+    cuuint32_t box[2] = {64, kRC};
+    if (!make_tmap(&mw[pl], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p->d_wplanes[pl], dims, str, box, 128, &err)) {
+      set_error(err);
+      return JTFS_ERR_CUDA;
+    }
+  }
+  for (int h = 0; h < 2; ++h) {
+    const __nv_bfloat16* yb = (const __nv_bfloat16*)(h == 0 ? yhi_v : ylo_v);
+    for (int a = 0; a < 16; ++a) {
+      if (a >= p->n2 || p->rates2[a].s == 0 || (h == 1 && !three)) { my[h][a] = mw[0]; continue; }
+      const Rate2& A = p->rates2[a];
+      cuuint64_t dims[3] = {(cuuint64_t)A.L, (cuuint64_t)A.K, (cuuint64_t)(2 * B)};
+      cuuint64_t str[2] = {(cuuint64_t)A.L * 2, (cuuint64_t)A.K * A.L * 2};
+      cuuint32_t box[3] = {64, 32, 1};
+      if (!make_tmap(&my[h][a], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, yb + (size_t)B * 2 * A.off_y, dims, str, box, 128, &err)) {
+        set_error(err);
+        return JTFS_ERR_CUDA;
+      }
+    }
+  }
+  for (int h = 0; h < 2; ++h) {
+    {
+      cuuint64_t dims[2] = {(cuuint64_t)NT, (cuuint64_t)B * p->n2 * g1_rows};
+      cuuint64_t str[1] = {(cuuint64_t)NT * 2};
+      cuuint32_t box[2] = {(cuuint32_t)NT, kRC};
+      if (!make_tmap(&mg1[h], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h ? g1lo : g1hi, dims, str, box, NT * 2, &err)) {
+        set_error(err);
+        return JTFS_ERR_CUDA;
+      }
+    }
+    {
+      cuuint64_t dims[2] = {(cuuint64_t)NT, (cuuint64_t)p->tcb_wt_rows};
+      cuuint64_t str[1] = {(cuuint64_t)NT * 2};
+      cuuint32_t box[2] = {(cuuint32_t)NT, 128};
+      const __nv_bfloat16* wt = (const __nv_bfloat16*)p->d_wtb + (h ? (size_t)p->tcb_wt_rows * NT : 0);
+      if (!make_tmap(&mwt[h], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, wt, dims, str, box, NT * 2, &err)) {
+        set_error(err);
+        return JTFS_ERR_CUDA;
+      }
+    }
+  }
+  TbArgs args;
+  args.items = reinterpret_cast<const int4*>(p->d_tcb_items);
+  args.n_items = (int)(p->tcb_items.size() / 4) * B;
+  args.B = B;
+  args.n_rows = rows;
+  args.n_chunks = n_chunks;
+  args.g1_rows = g1_rows;
+  args.wt_row0 = p->d_wtb_row0;
+  args.gy = gy;
+  args.err = p->d_err;
+  if (args.n_items == 0) return JTFS_OK;
+  int n_sm = 148;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
+  const int grid = std::min(args.n_items, n_sm);
+  if (three) {
+    Tb3Maps maps;
+    for (int i = 0; i < 4; ++i) maps.w[i] = mw[i];
+    for (int h = 0; h < 2; ++h) {
+      for (int a = 0; a < 16; ++a) maps.y[h][a] = my[h][a];
+      maps.g1[h] = mg1[h];
+      maps.wt[h] = mwt[h];
+    }
+    const size_t smem = tcb3_smem_bytes(NT);
+#define JTFS_LAUNCH_TCB3(NTV, WBV)                                                              \
+  do {                                                                                          \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_tc3<NTV, WBV>,                      \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                              (int)smem), "attr tcb3")) != JTFS_OK)             \
+      return rc;                                                                                \
+    k_joint_bwd_tc3<NTV, WBV><<<grid, kThreads, smem, st>>>(maps, args, d);                    \
+  } while (0)
+    if (NT == 16) JTFS_LAUNCH_TCB3(16, 2);
+    else if (NT == 32) JTFS_LAUNCH_TCB3(32, 2);
+    else JTFS_LAUNCH_TCB3(64, 1);
+#undef JTFS_LAUNCH_TCB3
+    return cuda_check(cudaGetLastError(), "k_joint_bwd_tc3");
+  }
+  TbMaps maps;
+  maps.w[0] = mw[0];
+  maps.w[1] = mw[1];
+  for (int a = 0; a < 16; ++a) maps.y[a] = my[0][a];
+  maps.g1 = mg1[0];
+  maps.wt = mwt[0];
+  const size_t smem = tcb_smem_bytes(NT);
+#define JTFS_LAUNCH_TCB(NTV)                                                                    \
+  do {                                                                                          \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_tc<NTV>,                            \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                              (int)smem), "attr tcb")) != JTFS_OK)              \
+      return rc;                                                                                \
+    k_joint_bwd_tc<NTV><<<grid, kThreads, smem, st>>>(maps, args, d);                          \
+  } while (0)
+  if (NT == 16) JTFS_LAUNCH_TCB(16);
+  else if (NT == 32) JTFS_LAUNCH_TCB(32);
+  else JTFS_LAUNCH_TCB(64);
+#undef JTFS_LAUNCH_TCB
+  return cuda_check(cudaGetLastError(), "k_joint_bwd_tc");
+}
+
+}  // namespace jtfs

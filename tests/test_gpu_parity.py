@@ -21,6 +21,7 @@ SMALL_CFGS = [
     dict(N=256, J=4, Q=3, J_fr=2, Q_fr=2, T=16, F=3),
     dict(N=1024, J=6, Q=2, J_fr=2, Q_fr=1, T=1024, F=1),      # T = N: one frame
     dict(N=2048, J=7, Q=12, J_fr=3, Q_fr=2, T=128, F=12, oversampling=1),
+    dict(N=1024, J=6, Q=16, J_fr=3, Q_fr=2, T=64, F=16),      # the gradient-check slice
 ]
 
 
@@ -144,7 +145,7 @@ def _check_backward(plan, x, op, sc, gtol, idx=None, seed=0):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("ci", [0, 1, 2, 4])
+@pytest.mark.parametrize("ci", [0, 1, 2, 4, 5])
 def test_backward_small_configs(ci, prec):
     cfg = SMALL_CFGS[ci]
     plan = _plans(cfg, prec)
