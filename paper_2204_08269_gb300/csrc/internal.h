@@ -94,8 +94,8 @@ struct jtfs_plan {
   bool use_tc;
   int n1_pad;                  // lambda' columns of the W planes (multiple of 32)
   void* d_wplanes[4];          // Wr_hi, Wi_hi, Wr_lo, Wi_lo: [C * n1][n1_pad] bf16
-  float* d_wt;                 // per alpha: [L_alpha rounded up to 128][NT] pooling weights
-  long long* d_wt_off;         // [n2]
+  void* d_wtf;                 // pooling weights hi / lo: [n2 * NT][tc_wt_cols] bf16
+  int tc_wt_cols;
   std::vector<int> tc_items;   // (alpha, m0, n_tiles, 0) per signal, longest first
   int* d_tc_items;
   int* d_err;                  // device status word of the bounded waits

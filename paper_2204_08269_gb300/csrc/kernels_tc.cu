@@ -33,14 +33,15 @@ using namespace umma;
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 32;
+constexpr int kBM = 128, kBN = 64, kBK = 32;
 constexpr int kThreads = 384;
 constexpr int kEpiWarp0 = 4;
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
 
 struct TcMaps {
-  CUtensorMap w[4];        // Wr_hi, Wi_hi, Wr_lo, Wi_lo : [C*n1 rows][n1_pad] bf16
-  CUtensorMap y[2][16];    // [hi/lo][alpha] : [2B][K_alpha][L_alpha] bf16 (plane 2b+part)
+  CUtensorMap w[4];        // Wr_hi, Wi_hi, Wr_lo, Wi_lo : [C*n1 rows][n1_pad] bf16, box {32, 128}
+  CUtensorMap y[2][16];    // [hi/lo][alpha] : [2B][K_alpha][L_alpha] bf16, box {64, 32, 1}
+  CUtensorMap wt[2];       // pooling weights hi/lo : [n2 * NT rows (t)][Lmax (n)], box {64, NT}
 };
 
 struct TcArgs {
@@ -48,31 +49,36 @@ struct TcArgs {
   int n_items;             // n_base * B
   int B;
   int passes;              // 1 or 3
+  int stages;              // pipeline depth (2..4)
   int n_rows;              // C * n1
   int nt;                  // frames
-  const float* wt;         // per alpha: [L_alpha padded to 128][NT] pooling weights
-  const long long* wt_off; // [n2]
   float* P;                // [B][n2][C*n1][nt]
   int n2;
   int* err;                // device status word (0 = ok)
 };
 
+// Main product per 64-column tile into a double-buffered TMEM accumulator (Re at columns
+// [128 a, 128 a + 64), Im at [128 a + 64, 128 a + 128)); the epilogue writes |Z| of the tile
+// as BF16 (hi, and lo for the split) into shared memory, and a second, small MMA pools it
+// with the tile's phi_T weights into a per-row accumulator at TMEM columns [256, 256 + NT).
 template <int NT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int planes = args.passes == 3 ? 2 : 1;          // hi (+ lo)
-  const int S = args.passes == 3 ? 3 : 4;               // pipeline stages
-  const uint32_t a_plane_bytes = kBM * kBK * 2;         // 8 KB
-  const uint32_t b_plane_bytes = kBK * kBN * 2;         // 8 KB
-  const uint32_t stage_bytes = (a_plane_bytes + b_plane_bytes) * 2 * planes;
-  __shared__ uint64_t full_bar[4], empty_bar[4], tfull[2], tempty[2];
+  const int S = args.stages;
+  constexpr uint32_t kAPlane = kBM * kBK * 2;           // 8 KB, 64-byte swizzle
+  constexpr uint32_t kBPlane = kBK * kBN * 2;           // 4 KB, 128-byte swizzle
+  constexpr uint32_t kZPlane = kBM * kBN * 2;           // 16 KB, 128-byte swizzle
+  constexpr uint32_t kWPlane = NT * kBN * 2;            // NT rows of 128 bytes
+  const uint32_t stage_bytes = (kAPlane + kBPlane) * 2 * planes;
+  uint8_t* sZ = sm + S * stage_bytes;                   // 2 buffers x planes
+  uint8_t* sWt = sZ + 2 * planes * kZPlane;             // 2 buffers x planes
+  __shared__ uint64_t full_bar[4], empty_bar[4], tfull[2], tempty[2], zfull[2], zempty[2],
+      wfull[2], wempty[2], d3full, d3free, mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
-  __shared__ volatile int stop_item;
-  __shared__ uint64_t mma_done;
-  __shared__ float red[kBM][NT + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -83,10 +89,15 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 8);   // one arrive per epilogue warp
+      mbar_init(&tempty[a], 8);
+      mbar_init(&zfull[a], 8);
+      mbar_init(&zempty[a], 1);
+      mbar_init(&wfull[a], 1);
+      mbar_init(&wempty[a], 1);
     }
+    mbar_init(&d3full, 1);
+    mbar_init(&d3free, 8);
     mbar_init(&mma_done, 1);
-    stop_item = 0;
     fence_barrier_init();
   }
   if (warp == 1) {
@@ -107,95 +118,120 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      for (int i = 0; i < 4; ++i) prefetch_tmap(&maps.w[i]);
-      int stage = 0;
-      uint32_t phase = 0;
-      int armed[4] = {-1, -1, -1, -1};   // parity of the last load issued into each stage
-      for (int it = blockIdx.x; it < args.n_items && !abort_flag; it += gridDim.x) {
+      int stage = 0, ws = 0;
+      uint32_t phase = 0, wph = 0;
+      int armed[4] = {-1, -1, -1, -1}, armed_w[2] = {-1, -1};
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it / args.B];
         const int a = item.x, b = it % args.B, m0 = item.y, ntiles = item.z;
         const Rate2 A = P.rates2[a];
         const int kb0 = A.lam_min / kBK, kb1 = (P.n1 + kBK - 1) / kBK;
-        for (int j = 0; j < ntiles && !abort_flag; ++j) {
+        for (int j = 0; j < ntiles && ok; ++j) {
+          if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
+          mbar_arrive_expect_tx(&wfull[ws], planes * kWPlane);
+          armed_w[ws] = (int)wph;
+          for (int pl = 0; pl < planes; ++pl)
+            tma_load_2d(sWt + (ws * planes + pl) * kWPlane, &maps.wt[pl], j * kBN, a * NT,
+                        &wfull[ws]);
+          if (++ws == 2) { ws = 0; wph ^= 1; }
           for (int kb = kb0; kb < kb1; ++kb) {
-            if (!mbar_wait(&empty_bar[stage], phase ^ 1, kWaitNs)) { fail(11); break; }
+            if (!mbar_wait(&empty_bar[stage], phase ^ 1, kWaitNs)) { fail(11); ok = false; break; }
             uint8_t* st = sm + stage * stage_bytes;
             mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
             armed[stage] = (int)phase;
             for (int pl = 0; pl < planes; ++pl) {
               for (int part = 0; part < 2; ++part) {
-                uint8_t* dA = st + (pl * 2 + part) * a_plane_bytes;
-                tma_load_2d(dA, &maps.w[pl * 2 + part], kb * kBK, m0, &full_bar[stage]);
-                uint8_t* dB = st + 2 * planes * a_plane_bytes + (pl * 2 + part) * b_plane_bytes;
-                const int krow = kb * kBK - A.lam_min;
-                for (int h = 0; h < 2; ++h)
-                  tma_load_3d(dB + h * (kBK * 128), &maps.y[pl][a], j * kBN + h * 64, krow,
-                              2 * b + part, &full_bar[stage]);
+                tma_load_2d(st + (pl * 2 + part) * kAPlane, &maps.w[pl * 2 + part], kb * kBK, m0,
+                            &full_bar[stage]);
+                tma_load_3d(st + 2 * planes * kAPlane + (pl * 2 + part) * kBPlane, &maps.y[pl][a],
+                            j * kBN, kb * kBK - A.lam_min, 2 * b + part, &full_bar[stage]);
               }
             }
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
         }
       }
-      // every load issued has landed before the CTA may exit (bounded; immediate when the
-      // MMA warp consumed them)
       for (int s2 = 0; s2 < S; ++s2)
         if (armed[s2] >= 0) mbar_wait(&full_bar[s2], (uint32_t)armed[s2], kWaitNs);
+      for (int s2 = 0; s2 < 2; ++s2)
+        if (armed_w[s2] >= 0) mbar_wait(&wfull[s2], (uint32_t)armed_w[s2], kWaitNs);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       const uint32_t id_pos = instr_desc(kBM, kBN, 1, 1, 0, 1, 0);
       const uint32_t id_neg = instr_desc(kBM, kBN, 1, 1, 0, 1, 1);
-      int stage = 0;
-      uint32_t phase = 0;
-      int acc = 0;
-      uint32_t acc_phase = 0;
-      for (int it = blockIdx.x; it < args.n_items && !abort_flag; it += gridDim.x) {
+      const uint32_t id_pool = instr_desc(kBM, NT, 1, 1, 0, 0, 0);
+      const int npair = args.passes == 3 ? 3 : 1;
+      const int pa_[3] = {0, 0, 1}, pb_[3] = {0, 1, 0};
+      int stage = 0, acc = 0, zq = 0, wq = 0;
+      uint32_t phase = 0, acc_phase = 0, zph = 0, wph = 0, d3ph = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it / args.B];
         const Rate2 A = P.rates2[item.x];
         const int kb0 = A.lam_min / kBK, kb1 = (P.n1 + kBK - 1) / kBK;
-        for (int j = 0; j < item.z && !abort_flag; ++j) {
-          if (!mbar_wait(&tempty[acc], acc_phase ^ 1, kWaitNs)) { fail(12); break; }
-          tc_fence_after();
-          const uint32_t d_re = tbase + acc * 256, d_im = d_re + 128;
-          bool first = true;
-          for (int kb = kb0; kb < kb1; ++kb) {
-            if (!mbar_wait(&full_bar[stage], phase, kWaitNs)) { fail(13); break; }
+        const int ntiles = item.z;
+        for (int j = 0; j <= ntiles && ok; ++j) {
+          if (j < ntiles) {
+            if (!mbar_wait(&tempty[acc], acc_phase ^ 1, kWaitNs)) { fail(12); ok = false; break; }
             tc_fence_after();
-            uint8_t* st = sm + stage * stage_bytes;
-            const uint32_t sa = smem_u32(st);
-            const uint32_t sb = sa + (planes == 2 ? 4 : 2) * a_plane_bytes;
-            for (int ks = 0; ks < kBK / 16; ++ks) {
-              // plane p (0 = hi, 1 = lo), part (0 = re, 1 = im)
-              auto ad = [&](int p, int part) {
-                return smem_desc(sa + (p * 2 + part) * a_plane_bytes + ks * 32, 16, 512, kSw64);
-              };
-              auto bd = [&](int p, int part) {
-                return smem_desc(sb + (p * 2 + part) * b_plane_bytes + ks * 16 * 128, kBK * 128,
-                                 1024, kSw128);
-              };
-              // (pa, pb) plane pairs: hi*hi, then hi*lo and lo*hi for the split
-              const int npair = args.passes == 3 ? 3 : 1;
-              const int pa_[3] = {0, 0, 1}, pb_[3] = {0, 1, 0};
-              for (int q = 0; q < npair; ++q) {
-                const int pa = pa_[q], pb = pb_[q];
-                const uint32_t f = first ? 0u : 1u;
-                mma_f16(d_re, ad(pa, 0), bd(pb, 0), id_pos, f);   // Wr Yr
-                mma_f16(d_re, ad(pa, 1), bd(pb, 1), id_neg, 1u);  // -Wi Yi
-                mma_f16(d_im, ad(pa, 0), bd(pb, 1), id_pos, f);   // Wr Yi
-                mma_f16(d_im, ad(pa, 1), bd(pb, 0), id_pos, 1u);  // Wi Yr
-                first = false;
+            const uint32_t d_re = tbase + acc * 128, d_im = d_re + 64;
+            bool first = true;
+            for (int kb = kb0; kb < kb1; ++kb) {
+              if (!mbar_wait(&full_bar[stage], phase, kWaitNs)) { fail(13); ok = false; break; }
+              tc_fence_after();
+              const uint32_t sa = smem_u32(sm + stage * stage_bytes);
+              const uint32_t sb = sa + 2 * planes * kAPlane;
+              for (int ks = 0; ks < kBK / 16; ++ks) {
+                for (int q = 0; q < npair; ++q) {
+                  const int pa = pa_[q], pb = pb_[q];
+                  const uint64_t ar = smem_desc(sa + (pa * 2 + 0) * kAPlane + ks * 32, 16, 512, kSw64);
+                  const uint64_t ai = smem_desc(sa + (pa * 2 + 1) * kAPlane + ks * 32, 16, 512, kSw64);
+                  const uint64_t br = smem_desc(sb + (pb * 2 + 0) * kBPlane + ks * 2048, kBPlane, 1024, kSw128);
+                  const uint64_t bi = smem_desc(sb + (pb * 2 + 1) * kBPlane + ks * 2048, kBPlane, 1024, kSw128);
+                  const uint32_t f = first ? 0u : 1u;
+                  mma_f16(d_re, ar, br, id_pos, f);    // Wr Yr
+                  mma_f16(d_re, ai, bi, id_neg, 1u);   // -Wi Yi
+                  mma_f16(d_im, ar, bi, id_pos, f);    // Wr Yi
+                  mma_f16(d_im, ai, br, id_pos, 1u);   // Wi Yr
+                  first = false;
+                }
               }
+              mma_commit(&empty_bar[stage]);
+              if (++stage == S) { stage = 0; phase ^= 1; }
             }
-            mma_commit(&empty_bar[stage]);
-            if (++stage == S) { stage = 0; phase ^= 1; }
+            if (!ok) break;
+            mma_commit(&tfull[acc]);
+            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
           }
-          mma_commit(&tfull[acc]);
-          if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+          if (j >= 1) {
+            // pool the previous tile: D3 += |Z| (128 x 64) . w^T (64 x NT)
+            if (!mbar_wait(&zfull[zq], zph, kWaitNs)) { fail(16); ok = false; break; }
+            if (!mbar_wait(&wfull[wq], wph, kWaitNs)) { fail(17); ok = false; break; }
+            if (j == 1) {
+              if (!mbar_wait(&d3free, d3ph ^ 1, kWaitNs)) { fail(18); ok = false; break; }
+              d3ph ^= 1;
+            }
+            tc_fence_after();
+            const uint32_t za = smem_u32(sZ + zq * planes * kZPlane);
+            const uint32_t wa = smem_u32(sWt + wq * planes * kWPlane);
+            for (int ks = 0; ks < kBN / 16; ++ks)
+              for (int q = 0; q < npair; ++q)
+                mma_f16(tbase + 256,
+                        smem_desc(za + pa_[q] * kZPlane + ks * 32, 16, 1024, kSw128),
+                        smem_desc(wa + pb_[q] * kWPlane + ks * 32, 16, 1024, kSw128), id_pool,
+                        (j == 1 && ks == 0 && q == 0) ? 0u : 1u);
+            mma_commit(&zempty[zq]);
+            mma_commit(&wempty[wq]);
+            if (++zq == 2) { zq = 0; zph ^= 1; }
+            if (++wq == 2) { wq = 0; wph ^= 1; }
+          }
         }
+        if (!ok) break;
+        mma_commit(&d3full);
       }
-      // all MMAs issued by this thread have completed before TMEM is released
       mma_commit(&mma_done);
       mbar_wait(&mma_done, 0, kWaitNs);
     }
@@ -205,65 +241,82 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     const int quarter = warp & 3;             // TMEM lane quarter this warp may access
     const int half = ew >> 2;                 // column half
     const int row = quarter * 32 + lane;      // tile row
-    int acc = 0;
-    uint32_t acc_phase = 0;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    int acc = 0, zq = 0;
+    uint32_t acc_phase = 0, zph = 0, d3ph = 0;
     for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
       const int4 item = args.items[it / args.B];
       const int a = item.x, b = it % args.B, m0 = item.y;
-      const float* wt = args.wt + args.wt_off[a];
-      float pacc[NT];
-#pragma unroll
-      for (int t = 0; t < NT; ++t) pacc[t] = 0.f;
-      bool ok = true;
-      for (int j = 0; j < item.z; ++j) {
-        if (abort_flag || !mbar_wait(&tfull[acc], acc_phase, kWaitNs)) { fail(14); ok = false; break; }
+      bool ok = !abort_flag;
+      for (int j = 0; j < item.z && ok; ++j) {
+        if (!mbar_wait(&tfull[acc], acc_phase, kWaitNs)) { fail(14); ok = false; break; }
         tc_fence_after();
-        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const uint32_t c_re = tbase + acc * 256 + half * 64, c_im = c_re + 128;
-#pragma unroll 1
-        for (int c0 = 0; c0 < 64; c0 += 16) {
+        float m[32];
+        {
           float re[16], im[16];
-          tmem_ld16(c_re + lane_off + c0, re);
-          tmem_ld16(c_im + lane_off + c0, im);
-          tmem_wait_ld();
-          const float* wrow = wt + (size_t)(j * kBN + half * 64 + c0) * NT;
+          const uint32_t c_re = tbase + acc * 128 + half * 32;
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float m = sqrtf(re[i] * re[i] + im[i] * im[i]);
-            const float4* w4 = reinterpret_cast<const float4*>(wrow + i * NT);
+          for (int c = 0; c < 2; ++c) {
+            tmem_ld16(c_re + lane_off + c * 16, re);
+            tmem_ld16(c_re + 64 + lane_off + c * 16, im);
+            tmem_wait_ld();
 #pragma unroll
-            for (int t4 = 0; t4 < NT / 4; ++t4) {
-              const float4 w = __ldg(&w4[t4]);
-              pacc[4 * t4 + 0] += w.x * m;
-              pacc[4 * t4 + 1] += w.y * m;
-              pacc[4 * t4 + 2] += w.z * m;
-              pacc[4 * t4 + 3] += w.w * m;
-            }
+            for (int i = 0; i < 16; ++i) m[c * 16 + i] = sqrtf(re[i] * re[i] + im[i] * im[i]);
           }
         }
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[acc]);
         if (++acc == 2) { acc = 0; acc_phase ^= 1; }
-      }
-      // combine the two column halves, then write this row's pooled frames; the decision to
-      // stop is sampled once between the two barriers so every epilogue warp agrees on it
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (half == 1)
+        uint32_t hv[16], lv[16];
 #pragma unroll
-        for (int t = 0; t < NT; ++t) red[row][t] = pacc[t];
-      if (ew == 0 && lane == 0) stop_item = abort_flag;
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      const bool stop = stop_item != 0;
-      if (half == 0 && ok && !stop) {
-        const int r = m0 + row;
-        if (r < args.n_rows) {
-          float* out = args.P + (((size_t)b * args.n2 + a) * args.n_rows + r) * args.nt;
-          for (int t = 0; t < args.nt; ++t) out[t] = pacc[t] + red[row][t];
+        for (int i = 0; i < 16; ++i) {
+          __nv_bfloat162 h = __floats2bfloat162_rn(m[2 * i], m[2 * i + 1]);
+          const float2 hf = __bfloat1622float2(h);
+          __nv_bfloat162 l = __floats2bfloat162_rn(m[2 * i] - hf.x, m[2 * i + 1] - hf.y);
+          hv[i] = *reinterpret_cast<uint32_t*>(&h);
+          lv[i] = *reinterpret_cast<uint32_t*>(&l);
         }
+        if (!mbar_wait(&zempty[zq], zph ^ 1, kWaitNs)) { fail(19); ok = false; break; }
+        uint8_t* zb = sZ + zq * planes * kZPlane + row * 128;
+        const int sw = row & 7;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int pos = ((half * 4 + c) ^ sw) * 16;
+          *reinterpret_cast<uint4*>(zb + pos) =
+              make_uint4(hv[4 * c], hv[4 * c + 1], hv[4 * c + 2], hv[4 * c + 3]);
+          if (planes == 2)
+            *reinterpret_cast<uint4*>(zb + kZPlane + pos) =
+                make_uint4(lv[4 * c], lv[4 * c + 1], lv[4 * c + 2], lv[4 * c + 3]);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&zfull[zq]);
+        if (++zq == 2) { zq = 0; zph ^= 1; }
       }
-      if (stop) break;
-      asm volatile("bar.sync 1, 256;" ::: "memory");   // red[] is reused by the next item
+      if (!ok) break;
+      if (!mbar_wait(&d3full, d3ph, kWaitNs)) { fail(20); break; }
+      d3ph ^= 1;
+      tc_fence_after();
+      float pv[NT];
+#pragma unroll
+      for (int c = 0; c < NT; c += 16) {
+        float v[16];
+        tmem_ld16(tbase + 256 + lane_off + c, v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) pv[c + i] = v[i];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d3free);
+      const int r = m0 + row;
+      if (half == 0 && r < args.n_rows) {
+        float* out = args.P + (((size_t)b * args.n2 + a) * args.n_rows + r) * args.nt;
+#pragma unroll
+        for (int t = 0; t < NT; ++t)
+          if (t < args.nt) out[t] = pv[t];
+      }
     }
   }
   __syncthreads();
@@ -312,16 +365,21 @@ __global__ void k_build_wplanes(DevPlan Pd, int n1_pad, __nv_bfloat16* wr_hi, __
   }
 }
 
-// Pooling weights of rate alpha: w[n][t] = s_alpha phi_T[(t T - n s_alpha) mod N] for n < L_alpha,
-// t < n_t; zero in the padding.
-__global__ void k_build_wt(DevPlan Pd, int a, int NT, int Lpad, float* out) {
-  const Rate2 A = Pd.rates2[a];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Lpad * NT; i += gridDim.x * blockDim.x) {
-    const int n = i / NT, t = i % NT;
+// Pooling weights, t-major: w[a * NT + t][n] = s_a phi_T[(t T - n s_a) mod N] for n < L_a and
+// t < n_t, zero elsewhere; stored as hi = bf16(w) and lo = bf16(w - hi).
+__global__ void k_build_wt(DevPlan Pd, int NT, int Lmax, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  const long long total = (long long)Pd.n2 * NT * Lmax;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int n = (int)(i % Lmax);
+    const int row = (int)(i / Lmax);
+    const int a = row / NT, t = row % NT;
+    const Rate2 A = Pd.rates2[a];
     float v = 0.f;
-    if (A.s > 0 && n < A.L && t < Pd.n_t)
-      v = Pd.phiT[(t * Pd.T - n * A.s) & (Pd.N - 1)] * (float)A.s;
-    out[i] = v;
+    if (A.s > 0 && n < A.L && t < Pd.n_t) v = Pd.phiT[(t * Pd.T - n * A.s) & (Pd.N - 1)] * (float)A.s;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
   }
 }
 
@@ -341,13 +399,10 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   const int NT = tc_nt(p->n_t);
   p->n1_pad = (p->n1 + 63) / 64 * 64;   // W plane rows hold whole 64-column boxes
   const size_t wplane = (size_t)p->C * p->n1 * p->n1_pad;
-  std::vector<long long> wt_off(p->n2);
-  long long wt_len = 0;
-  for (int a = 0; a < p->n2; ++a) {
-    wt_off[a] = wt_len;
-    const int L = p->rates2[a].s ? p->rates2[a].L : 0;
-    wt_len += (long long)((L + kBN - 1) / kBN * kBN) * NT;
-  }
+  int Lmax = 64;
+  for (int a = 0; a < p->n2; ++a)
+    if (p->rates2[a].s) Lmax = std::max(Lmax, (p->rates2[a].L + 63) / 64 * 64);
+  p->tc_wt_cols = Lmax;
   // items: (alpha, m0, n_tiles), longest first (cost ~ n_tiles * k-blocks)
   struct It { int a, m0, nt; long long cost; };
   std::vector<It> its;
@@ -366,19 +421,17 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   auto place = [&](size_t bytes) { size_t at = off; off += (bytes + 1023) & ~(size_t)1023; return at; };
   size_t o_w[4];
   for (int i = 0; i < 4; ++i) o_w[i] = place(wplane * 2);
-  const size_t o_wt = place((size_t)std::max<long long>(1, wt_len) * 4);
-  const size_t o_wto = place((size_t)p->n2 * 8);
+  const size_t wt_elems = (size_t)p->n2 * NT * Lmax;
+  const size_t o_wt = place(wt_elems * 2 * 2);
   const size_t o_items = place(std::max<size_t>(16, p->tc_items.size() * 4));
   const size_t o_err = place(16);
   jtfs_status st;
   if ((st = cuda_check(cudaMalloc(&p->d_tc_mem, off), "tc tables")) != JTFS_OK) return st;
   char* base = (char*)p->d_tc_mem;
   for (int i = 0; i < 4; ++i) p->d_wplanes[i] = base + o_w[i];
-  p->d_wt = (float*)(base + o_wt);
-  p->d_wt_off = (long long*)(base + o_wto);
+  p->d_wtf = base + o_wt;
   p->d_tc_items = (int*)(base + o_items);
   p->d_err = (int*)(base + o_err);
-  if ((st = cuda_check(cudaMemcpy(p->d_wt_off, wt_off.data(), p->n2 * 8, cudaMemcpyHostToDevice), "upload")) != JTFS_OK) return st;
   if (!p->tc_items.empty() &&
       (st = cuda_check(cudaMemcpy(p->d_tc_items, p->tc_items.data(), p->tc_items.size() * 4, cudaMemcpyHostToDevice), "upload")) != JTFS_OK)
     return st;
@@ -386,20 +439,29 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   k_build_wplanes<<<1024, 256>>>(p->dp, p->n1_pad, (__nv_bfloat16*)p->d_wplanes[0],
                                  (__nv_bfloat16*)p->d_wplanes[1], (__nv_bfloat16*)p->d_wplanes[2],
                                  (__nv_bfloat16*)p->d_wplanes[3]);
-  for (int a = 0; a < p->n2; ++a) {
-    const int L = p->rates2[a].s ? p->rates2[a].L : 0;
-    const int Lpad = (L + kBN - 1) / kBN * kBN;
-    if (Lpad == 0) continue;
-    k_build_wt<<<(Lpad * NT + 255) / 256, 256>>>(p->dp, a, NT, Lpad, p->d_wt + wt_off[a]);
-  }
+  k_build_wt<<<1024, 256>>>(p->dp, NT, Lmax, (__nv_bfloat16*)p->d_wtf,
+                            (__nv_bfloat16*)p->d_wtf + wt_elems);
   return cuda_check(cudaDeviceSynchronize(), "build tc tables");
+}
+
+int tc_stages(const jtfs_plan* p) {
+  const int passes = p->cfg.precision == JTFS_PREC_FP32 ? 3 : 1;
+  const int planes = passes == 3 ? 2 : 1;
+  const int NT = tc_nt(p->n_t);
+  const size_t stage = (size_t)(kBM * kBK * 2 + kBK * kBN * 2) * 2 * planes;
+  const size_t fixed = 1024 + 2 * (size_t)planes * kBM * kBN * 2 + 2 * (size_t)planes * NT * kBN * 2;
+  int S = 4;
+  while (S > 2 && fixed + S * stage > 225 * 1024) --S;
+  return S;
 }
 
 size_t tc_smem_bytes(const jtfs_plan* p) {
   const int passes = p->cfg.precision == JTFS_PREC_FP32 ? 3 : 1;
   const int planes = passes == 3 ? 2 : 1;
-  const int S = passes == 3 ? 3 : 4;
-  return 1024 + (size_t)S * (kBM * kBK * 2 + kBK * kBN * 2) * 2 * planes;
+  const int NT = tc_nt(p->n_t);
+  const size_t stage = (size_t)(kBM * kBK * 2 + kBK * kBN * 2) * 2 * planes;
+  return 1024 + tc_stages(p) * stage + 2 * (size_t)planes * kBM * kBN * 2 +
+         2 * (size_t)planes * NT * kBN * 2;
 }
 
 jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, const void* ylo_v,
@@ -411,8 +473,8 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   std::string err;
   const int passes = p->cfg.precision == JTFS_PREC_FP32 ? 3 : 1;
   const int rows = p->C * p->n1;
+  const int NT = tc_nt(p->n_t);
   for (int i = 0; i < 4; ++i) {
-    if (passes == 1 && i >= 2) { maps.w[i] = maps.w[0]; continue; }
     cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)rows};
     cuuint64_t str[1] = {(cuuint64_t)p->n1_pad * 2};
     cuuint32_t box[2] = {kBK, kBM};
@@ -440,25 +502,34 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       }
     }
   }
+  const size_t wt_elems = (size_t)p->n2 * NT * p->tc_wt_cols;
+  for (int h = 0; h < 2; ++h) {
+    cuuint64_t dims[2] = {(cuuint64_t)p->tc_wt_cols, (cuuint64_t)p->n2 * NT};
+    cuuint64_t str[1] = {(cuuint64_t)p->tc_wt_cols * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)NT};
+    if (!make_tmap(&maps.wt[h], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   (const __nv_bfloat16*)p->d_wtf + (h ? wt_elems : 0), dims, str, box, 128, &err)) {
+      set_error(err);
+      return JTFS_ERR_CUDA;
+    }
+  }
   TcArgs args;
   args.items = reinterpret_cast<const int4*>(p->d_tc_items);
   args.n_items = (int)(p->tc_items.size() / 4) * B;
   args.B = B;
   args.passes = passes;
+  args.stages = tc_stages(p);
   args.n_rows = rows;
   args.nt = p->n_t;
-  args.wt = p->d_wt;
-  (void)ylo;
-  args.wt_off = p->d_wt_off;
   args.P = Pbuf;
   args.n2 = p->n2;
   args.err = p->d_err;
-  const size_t smem = tc_smem_bytes(p);
-  int n_sm = 148;
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
-  const int grid = std::min(args.n_items, n_sm);
-  const int nt = tc_nt(p->n_t);
   jtfs_status rc;
+  if (args.n_items > 0) {
+    const size_t smem = tc_smem_bytes(p);
+    int n_sm = 148;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
+    const int grid = std::min(args.n_items, n_sm);
 #define JTFS_LAUNCH_TC(NTV)                                                                     \
   do {                                                                                          \
     if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_tc<NTV>,                            \
@@ -467,11 +538,12 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       return rc;                                                                                \
     k_joint_fwd_tc<NTV><<<grid, kThreads, smem, st>>>(maps, args, d);                          \
   } while (0)
-  if (nt == 16) JTFS_LAUNCH_TC(16);
-  else if (nt == 32) JTFS_LAUNCH_TC(32);
-  else JTFS_LAUNCH_TC(64);
+    if (NT == 16) JTFS_LAUNCH_TC(16);
+    else if (NT == 32) JTFS_LAUNCH_TC(32);
+    else JTFS_LAUNCH_TC(64);
 #undef JTFS_LAUNCH_TC
-  if ((rc = cuda_check(cudaGetLastError(), "k_joint_fwd_tc")) != JTFS_OK) return rc;
+    if ((rc = cuda_check(cudaGetLastError(), "k_joint_fwd_tc")) != JTFS_OK) return rc;
+  }
   k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
   return cuda_check(cudaGetLastError(), "k_pool_lambda");
 }
