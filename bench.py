@@ -109,7 +109,8 @@ def _dist():
 def contraction_flops(plan_shapes, schedule, B):
     """Algorithmic FLOPs of the log-frequency contractions in one forward + backward step:
     the forward Z = W_c Y_alpha, the backward's recomputation of Z and gY = W_c^H gZ; each is
-    C * n1 * K_alpha * L_alpha complex multiply-adds (8 real flops) per signal."""
+    C * n1 * K_alpha * L_alpha complex multiply-adds (8 real flops) per signal.  Extra passes
+    of the split-precision forms are not counted (they are not algorithmic work)."""
     s1, s2, lm = schedule
     n1, C, N = plan_shapes.n1, plan_shapes.C, plan_shapes.N
     per = 0
@@ -117,7 +118,7 @@ def contraction_flops(plan_shapes, schedule, B):
         if s2[a] == 0:
             continue
         per += C * n1 * (n1 - int(lm[a])) * (N // int(s2[a]))
-    return 8 * per * B
+    return 3 * 8 * per * B
 
 
 def run_ours(args):
