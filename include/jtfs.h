@@ -134,6 +134,19 @@ jtfs_status jtfs_profile_enable(const jtfs_plan* plan, int32_t on);
 jtfs_status jtfs_profile_read(const jtfs_plan* plan, double* ms, int32_t n_ms, int64_t* launches);
 const char* jtfs_profile_stage_name(int32_t i);
 
+/* First-order coefficients only (S0 [B, n_t] and S1 [B, n1, n_t], device buffers, same values
+ * as jtfs_forward) computed without allocating any device memory.  The paper has no
+ * counterpart; this entry point serves callers that cannot allocate while they run, such as
+ * a real-time audio callback (an allocation may block for milliseconds and miss the audio
+ * deadline) or a plug-in inside a host application that owns all device memory.  Its scratch
+ * is a fixed 16 MiB array compiled into the library, which every GPU that loads the library
+ * keeps until the process exits; a batch whose scratch would exceed it is rejected with
+ * JTFS_ERR_WORKSPACE (about 2.6 MB per signal at N = 2^16, J = 12, Q = 16).  The first call on
+ * a device looks up the array's device address; make that first call before any stream
+ * capture.  All calls share the array: calls that overlap on the GPU race on it. */
+jtfs_status jtfs_first_order_static(const jtfs_plan* plan, const float* x, int64_t B, float* s0,
+                                    float* s1, void* stream);
+
 /* Waits for the stream and reports any pending device error. */
 jtfs_status jtfs_sync_status(const jtfs_plan* plan, void* stream);
 

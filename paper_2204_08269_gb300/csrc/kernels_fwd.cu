@@ -264,3 +264,106 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
 }
 
 }  // namespace jtfs
+
+// ---------------------------------------------------------------------------------------
+// First-order transform (S0, S1) without any device allocation.
+//
+// Some callers cannot allocate device memory while they run: a real-time audio callback,
+// where cudaMalloc may block for milliseconds and miss the audio deadline, or a plug-in
+// hosted inside an application that owns and budgets all of the device's memory.  For
+// them the scratch of this path (the decimated spectra, x-hat, the scalogram rows and their
+// spectra) lives in one fixed array compiled into the library.  That array is held by every
+// GPU that loads the library until the process exits, and every call shares it: calls that
+// overlap on the GPU (other streams, other host threads) race on it.  Each kernel here
+// writes every scratch element it later reads, so nothing has to be cleared between calls.
+// ---------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace jtfs {
+
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;   // 16 MiB per device
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+namespace {
+std::mutex g_static_mu;
+void* g_static_ptr[256] = {};
+}  // namespace
+
+size_t first_order_static_bytes(const jtfs_plan* p, int64_t B) {
+  auto a = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t Bz = (size_t)B;
+  return a(Bz * p->N * 8) + a(Bz * (p->N / 2) * 8) + a(Bz * p->u1_len * 4) + a(Bz * p->uh_len * 8);
+}
+
+// The array's device address, looked up once per device with that device current (the
+// name of the array is only a host-side stand-in in host code).
+jtfs_status static_scratch(int dev, void** out) {
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (dev < 0 || dev >= 256) {
+    set_error("device ordinal out of range");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  if (!g_static_ptr[dev]) {
+    void* ptr = nullptr;
+    jtfs_status st = cuda_check(cudaGetSymbolAddress(&ptr, g_static_scratch), "cudaGetSymbolAddress");
+    if (st != JTFS_OK) return st;
+    g_static_ptr[dev] = ptr;
+  }
+  *out = g_static_ptr[dev];
+  return JTFS_OK;
+}
+
+jtfs_status launch_first_order_static(const jtfs_plan* p, const float* x, int B, float* s0,
+                                      float* s1, cudaStream_t st) {
+  const size_t need = first_order_static_bytes(p, B);
+  if (need > kStaticScratchBytes) {
+    set_error("jtfs_first_order_static: B = " + std::to_string(B) + " needs " +
+              std::to_string(need) + " bytes of scratch; the fixed array holds " +
+              std::to_string(kStaticScratchBytes) + " (use a smaller batch or jtfs_forward)");
+    return JTFS_ERR_WORKSPACE;
+  }
+  void* base = nullptr;
+  jtfs_status rc = static_scratch(p->device, &base);
+  if (rc != JTFS_OK) return rc;
+  if ((rc = set_attrs(p)) != JTFS_OK) return rc;
+  auto a = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const size_t Bz = (size_t)B;
+  char* c = (char*)base;
+  float2* xsub = (float2*)c;
+  c += a(Bz * p->N * 8);
+  float2* xh = (float2*)c;
+  c += a(Bz * (p->N / 2) * 8);
+  float* u1 = (float*)c;
+  c += a(Bz * p->u1_len * 4);
+  float2* uh = (float2*)c;
+  const DevPlan& d = p->dp;
+  k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 8, st>>>(d, x, xsub);
+  k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, xsub, xh);
+  k_s0<<<dim3(p->n_t, B), 256, 0, st>>>(d, x, s0);
+  k_scalogram<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 12, st>>>(d, xh, u1, uh, s1);
+  return cuda_check(cudaGetLastError(), "first-order static launch");
+}
+
+}  // namespace jtfs
+
+extern "C" jtfs_status jtfs_first_order_static(const jtfs_plan* p, const float* x, int64_t B,
+                                               float* s0, float* s1, void* stream) {
+  using namespace jtfs;
+  if (!p || B < 0 || B > (1 << 20)) {
+    set_error("bad plan or batch size");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  if (B == 0) return JTFS_OK;
+  if (!x || !s0 || !s1) {
+    set_error("NULL input or output");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  int dev = -1;
+  jtfs_status st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+  if (st != JTFS_OK) return st;
+  if (dev != p->device) {
+    set_error("current device differs from the plan's device");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  return launch_first_order_static(p, x, (int)B, s0, s1, (cudaStream_t)stream);
+}

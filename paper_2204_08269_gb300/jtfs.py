@@ -64,6 +64,7 @@ def lib():
         "jtfs_profile_enable": ([_P, _I32], _I32),
         "jtfs_profile_read": ([_P, _P, _I32, ctypes.POINTER(_I64)], _I32),
         "jtfs_profile_stage_name": ([_I32], ctypes.c_char_p),
+        "jtfs_first_order_static": ([_P, _P, _I64, _P, _P, _P], _I32),
         "jtfs_status_string": ([_I32], ctypes.c_char_p),
         "jtfs_last_error": ([], ctypes.c_char_p),
     }
@@ -81,7 +82,7 @@ def exported_symbols():
             "jtfs_workspace_bytes", "jtfs_forward", "jtfs_backward", "jtfs_host_step_bytes",
             "jtfs_forward_backward_host", "jtfs_sync_status", "jtfs_status_string",
             "jtfs_last_error", "jtfs_profile_enable", "jtfs_profile_read",
-            "jtfs_profile_stage_name"]
+            "jtfs_profile_stage_name", "jtfs_first_order_static"]
 
 
 class JTFSError(RuntimeError):
