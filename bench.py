@@ -136,6 +136,8 @@ def run_ours(args):
         build.build()
     if world > 1:
         dist.barrier()
+    global BATCH
+    BATCH = args.batch
     plan = JTFSPlan(**WORKLOAD, precision=args.precision)
     sh = plan.shapes
     x = torch.from_numpy(SS.workload_signals(2, BATCH, WORKLOAD["N"])).cuda()
@@ -179,18 +181,23 @@ def run_ours(args):
     value = BATCH * world / (ms_max / 1e3)
 
     # end to end through the host-buffer entry point (H2D, fwd, bwd, D2H in one call)
-    xh = torch.from_numpy(SS.workload_signals(2, BATCH, WORKLOAD["N"])).pin_memory()
-    gh = [g.cpu().pin_memory() for g in (g0, g1, g2)]
-    for _ in range(max(1, min(args.warmup, 2))):
-        plan.forward_backward_host(xh, *gh)
-    torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 10))
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        o = plan.forward_backward_host(xh, *gh)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    h2d = xh.numel() * 4 + sum(g.numel() * 4 for g in gh)
-    d2h = sum(t.numel() * 4 for t in o)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(SS.workload_signals(2, BATCH, WORKLOAD["N"])).pin_memory()
+        gh = [g.cpu().pin_memory() for g in (g0, g1, g2)]
+        for _ in range(max(1, min(args.warmup, 2))):
+            plan.forward_backward_host(xh, *gh)
+        torch.cuda.synchronize()
+        e2e_steps = max(1, min(args.steps, 10))
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            o = plan.forward_backward_host(xh, *gh)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        h2d = xh.numel() * 4 + sum(g.numel() * 4 for g in gh)
+        d2h = sum(t.numel() * 4 for t in o)
+        e2e = {"value": BATCH / e2e_s, "unit": "signals/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h,
+               "how": "jtfs_forward_backward_host on pinned host buffers, wall clock"}
 
     peaks, peaks_kind = _peaks()
     sched = plan.schedule()
@@ -231,9 +238,7 @@ def run_ours(args):
             "roofline": roof,
             "stage_ms_per_step": {k: v / args.steps for k, v in stages.items()},
             "cpu_baseline": cpu,
-            "e2e": {"value": BATCH / e2e_s, "unit": "signals/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h,
-                    "how": "jtfs_forward_backward_host on pinned host buffers, wall clock"},
+            "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clocks,
             "peaks": peaks_kind,
@@ -305,6 +310,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "fp32_simt"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--batch", type=int, default=BATCH,
+                    help="signals per GPU (the workload is 64; smaller values for profiling)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

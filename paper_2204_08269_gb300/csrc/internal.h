@@ -102,7 +102,8 @@ struct jtfs_plan {
   void* d_tc_mem;
   // tensor-core backward of the joint stage
   bool use_tcb;
-  std::vector<int> tcb_items;  // (alpha, n0, lambda' start, K1) per signal, longest first
+  std::vector<int> tcb_items;  // (alpha, n0, lambda' start, K1) per signal; K1 <= 96 first
+  int tcb_n_res;               // items with K1 <= 96
   int* d_tcb_items;
   void* d_wtb;                 // [rows][NT] bf16 pooling weights (time-major)
   int* d_wtb_row0;             // [n2]

@@ -128,13 +128,9 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         const Rate2 A = P.rates2[a];
         const int kb0 = A.lam_min / kBK, kb1 = (P.n1 + kBK - 1) / kBK;
         for (int j = 0; j < ntiles && ok; ++j) {
-          if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
-          mbar_arrive_expect_tx(&wfull[ws], planes * kWPlane);
-          armed_w[ws] = (int)wph;
-          for (int pl = 0; pl < planes; ++pl)
-            tma_load_2d(sWt + (ws * planes + pl) * kWPlane, &maps.wt[pl], j * kBN, a * NT,
-                        &wfull[ws]);
-          if (++ws == 2) { ws = 0; wph ^= 1; }
+          // operand k-blocks of the tile first, then its pooling weights: the weight buffer
+          // is released only after the previous tile's pooling, which must not hold back the
+          // prefetch of the next tile's operands
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(&empty_bar[stage], phase ^ 1, kWaitNs)) { fail(11); ok = false; break; }
             uint8_t* st = sm + stage * stage_bytes;
@@ -150,6 +146,14 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
             }
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
+          if (!ok) break;
+          if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
+          mbar_arrive_expect_tx(&wfull[ws], planes * kWPlane);
+          armed_w[ws] = (int)wph;
+          for (int pl = 0; pl < planes; ++pl)
+            tma_load_2d(sWt + (ws * planes + pl) * kWPlane, &maps.wt[pl], j * kBN, a * NT,
+                        &wfull[ws]);
+          if (++ws == 2) { ws = 0; wph ^= 1; }
         }
       }
       for (int s2 = 0; s2 < S; ++s2)

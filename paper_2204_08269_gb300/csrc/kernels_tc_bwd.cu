@@ -30,20 +30,17 @@ using namespace umma;
 namespace {
 
 constexpr int kRC = 32;          // W rows per chunk
-constexpr int kK1Max = 160;      // lambda' rows of the resident Y^T tile
+constexpr int kK1Max = 160;      // lambda' rows of a W chunk / gY^T accumulator
 constexpr int kThreads = 384;
 constexpr int kEpiWarp0 = 4;
 constexpr uint64_t kWaitNs = 2000000000ull;
 
-constexpr uint32_t kA1Bytes = 2 * 2 * kK1Max * 128;       // Re/Im x two 64-sample halves
-constexpr uint32_t kWBufBytes = 2 * 3 * kRC * 128;        // Re/Im x three 64-lambda' blocks
-constexpr uint32_t kA2Bytes = 2 * 128 * kRC * 2;          // Re/Im x 128 n x 32 r bf16
 
 struct TbMaps {
-  CUtensorMap w[2];     // Wr, Wi hi planes [C*n1][n1_pad], box {64 lambda', 32 r}, 128-byte swizzle
-  CUtensorMap y[16];    // per alpha: Y hi planes [2B][K][L], box {64 n, 32 lambda', 1}
-  CUtensorMap g1;       // [rows][NT] bf16, box {NT, 32}
-  CUtensorMap wt;       // [rows][NT] bf16, box {NT, 128}
+  CUtensorMap w[4];      // Wr_hi, Wi_hi, Wr_lo, Wi_lo [C*n1][n1_pad], box {64 lambda', 32 r}
+  CUtensorMap y[2][16];  // [hi/lo][alpha]: Y planes [2B][K][L], box {64 n, 32 lambda', 1}
+  CUtensorMap g1[2];     // hi, lo: [rows][NT] bf16, box {NT, 32}
+  CUtensorMap wt[2];     // hi, lo: [rows][NT] bf16, box {NT, 128}
 };
 
 struct TbArgs {
@@ -58,20 +55,31 @@ struct TbArgs {
   int* err;
 };
 
-template <int NT>
+// Resident-Y form: the Y^T tile of the item (PL planes: hi, and lo for the three-pass
+// split) stays in shared memory while the W chunks stream past it.  PL = 1 holds up to 160
+// lambda' rows with two gZ staging buffers; PL = 2 holds up to 96 rows with one.
+template <int NT, int PL>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int kK1M = PL == 1 ? 160 : 96;               // lambda' rows of the resident tile
+  constexpr int kWBlk = (kK1M + 63) / 64;                // 64-lambda' blocks of a W chunk
+  constexpr int kNA2 = PL == 1 ? 2 : 1;                  // gZ staging buffers
   constexpr uint32_t kSw = NT * 2;                       // bytes per row of the NT-wide tiles
   constexpr uint32_t kLayNT = kSw == 128 ? kSw128 : (kSw == 64 ? kSw64 : kSw32);
-  constexpr uint32_t kG1Bytes = ((kRC * NT * 2 + 1023) / 1024) * 1024;
-  constexpr uint32_t kA4Bytes = ((128 * NT * 2 + 1023) / 1024) * 1024;
-  uint8_t* sA1 = sm;
-  uint8_t* sW = sA1 + kA1Bytes;                          // 2 buffers
-  uint8_t* sG1 = sW + 2 * kWBufBytes;                    // 2 buffers
-  uint8_t* sA4 = sG1 + 2 * kG1Bytes;
-  uint8_t* sA2 = sA4 + kA4Bytes;                         // 2 buffers
+  constexpr uint32_t kA1Plane = 2 * kK1M * 128;          // two 64-sample halves
+  constexpr uint32_t kWPart = kWBlk * 4096;              // one (plane, part) of a W chunk
+  constexpr uint32_t kWBuf = PL * 2 * kWPart;
+  constexpr uint32_t kG1Plane = ((kRC * NT * 2 + 1023) / 1024) * 1024;
+  constexpr uint32_t kA4Plane = ((128 * NT * 2 + 1023) / 1024) * 1024;
+  constexpr uint32_t kA2Part = 128 * 64;                 // [128 n x 32 r] bf16
+  constexpr uint32_t kA2Buf = PL * 2 * kA2Part;
+  uint8_t* sA1 = sm;                                     // PL x 2 parts
+  uint8_t* sW = sA1 + PL * 2 * kA1Plane;                 // 2 buffers
+  uint8_t* sG1 = sW + 2 * kWBuf;                         // 2 buffers x PL planes
+  uint8_t* sA4 = sG1 + 2 * PL * kG1Plane;                // PL planes
+  uint8_t* sA2 = sA4 + PL * kA4Plane;                    // kNA2 buffers
 
   __shared__ uint64_t a1_full, a1_free, w_full[2], w_empty[2], d1_full, d1_free, a2_full[2],
       a2_free[2], d2_full, d2_free, mma_done;
@@ -109,6 +117,8 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
       atomicCAS(args.err, 0, code);
     }
   };
+  const int pa_[3] = {0, 0, 1}, pb_[3] = {0, 1, 0};
+  constexpr int kPairs = PL == 2 ? 3 : 1;
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
@@ -117,33 +127,39 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
       int wst = 0;
       uint32_t wph = 0;
       int armed_w[2] = {-1, -1}, armed_a1 = -1;
-      for (int it = blockIdx.x; it < args.n_items && !abort_flag; it += gridDim.x) {
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it / args.B];
         const int a = item.x, b = it % args.B, n0 = item.y, start = item.z, K1 = item.w;
         const Rate2 A = P.rates2[a];
         if (!mbar_wait(&a1_free, a1_ph ^ 1, kWaitNs)) { fail(21); break; }
-        const uint32_t a1_bytes = 2 * 2 * (K1 / 32) * 4096 + 128 * NT * 2;
-        mbar_arrive_expect_tx(&a1_full, a1_bytes);
+        mbar_arrive_expect_tx(&a1_full, PL * 2 * 2 * (K1 / 32) * 4096 + PL * 128 * NT * 2);
         armed_a1 = (int)a1_ph;
-        for (int p = 0; p < 2; ++p)
-          for (int h = 0; h < 2; ++h)
-            for (int kb = 0; kb < K1 / 32; ++kb)
-              tma_load_3d(sA1 + (p * 2 + h) * kK1Max * 128 + kb * 32 * 128, &maps.y[a],
-                          n0 + h * 64, start - A.lam_min + kb * 32, 2 * b + p, &a1_full);
-        tma_load_2d(sA4, &maps.wt, 0, args.wt_row0[a] + n0, &a1_full);
+        for (int pl = 0; pl < PL; ++pl) {
+          for (int part = 0; part < 2; ++part)
+            for (int h = 0; h < 2; ++h)
+              for (int kb = 0; kb < K1 / 32; ++kb)
+                tma_load_3d(sA1 + (pl * 2 + part) * kA1Plane + h * kK1M * 128 + kb * 32 * 128,
+                            &maps.y[pl][a], n0 + h * 64, start - A.lam_min + kb * 32,
+                            2 * b + part, &a1_full);
+          tma_load_2d(sA4 + pl * kA4Plane, &maps.wt[pl], 0, args.wt_row0[a] + n0, &a1_full);
+        }
         a1_ph ^= 1;
         const int nblk = (K1 + 63) / 64;
         const int g1row = (b * P.n2 + a) * args.g1_rows;
         for (int j = 0; j < args.n_chunks; ++j) {
-          if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(22); break; }
-          mbar_arrive_expect_tx(&w_full[wst], 2 * nblk * 4096 + kRC * NT * 2);
+          if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(22); ok = false; break; }
+          mbar_arrive_expect_tx(&w_full[wst], PL * 2 * nblk * 4096 + PL * kRC * NT * 2);
           armed_w[wst] = (int)wph;
-          uint8_t* wb = sW + wst * kWBufBytes;
-          for (int p = 0; p < 2; ++p)
-            for (int kb = 0; kb < nblk; ++kb)
-              tma_load_2d(wb + (p * 3 + kb) * 4096, &maps.w[p], start + kb * 64, j * kRC,
-                          &w_full[wst]);
-          tma_load_2d(sG1 + wst * kG1Bytes, &maps.g1, 0, g1row + j * kRC, &w_full[wst]);
+          uint8_t* wb = sW + wst * kWBuf;
+          for (int pl = 0; pl < PL; ++pl) {
+            for (int part = 0; part < 2; ++part)
+              for (int kb = 0; kb < nblk; ++kb)
+                tma_load_2d(wb + (pl * 2 + part) * kWPart + kb * 4096, &maps.w[pl * 2 + part],
+                            start + kb * 64, j * kRC, &w_full[wst]);
+            tma_load_2d(sG1 + (wst * PL + pl) * kG1Plane, &maps.g1[pl], 0, g1row + j * kRC,
+                        &w_full[wst]);
+          }
           if (++wst == 2) { wst = 0; wph ^= 1; }
         }
       }
@@ -181,51 +197,59 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
             if (!mbar_wait(&d1_free, d1f_ph ^ 1, kWaitNs)) { fail(25); ok = false; break; }
             d1f_ph ^= 1;
             tc_fence_after();
-            const uint32_t wb = smem_u32(sW + wst * kWBufBytes);
+            const uint32_t wb = smem_u32(sW + wst * kWBuf);
             for (int ks = 0; ks < K1 / 16; ++ks) {
               const int kb = ks >> 2, ko = (ks & 3) * 32;
-              // A: Y^T (MN-major, n contiguous); B: W chunk (K-major)
-              const uint64_t ayr = smem_desc(a1 + 0 * 2 * kK1Max * 128 + ks * 2048, kK1Max * 128, 1024, kSw128);
-              const uint64_t ayi = smem_desc(a1 + 1 * 2 * kK1Max * 128 + ks * 2048, kK1Max * 128, 1024, kSw128);
-              const uint64_t bwr = smem_desc(wb + (0 * 3 + kb) * 4096 + ko, 16, 1024, kSw128);
-              const uint64_t bwi = smem_desc(wb + (1 * 3 + kb) * 4096 + ko, 16, 1024, kSw128);
-              const uint32_t f = ks > 0 ? 1u : 0u;
-              mma_f16(t_d1r, ayr, bwr, id1, f);      // Yr Wr
-              mma_f16(t_d1r, ayi, bwi, id1n, 1u);    // -Yi Wi
-              mma_f16(t_d1i, ayr, bwi, id1, f);      // Yr Wi
-              mma_f16(t_d1i, ayi, bwr, id1, 1u);     // Yi Wr
+              for (int q = 0; q < kPairs; ++q) {
+                const int pa = pa_[q], pb = pb_[q];
+                // A: Y^T (MN-major, n contiguous); B: W chunk (K-major)
+                const uint64_t ayr = smem_desc(a1 + (pa * 2 + 0) * kA1Plane + ks * 2048, kK1M * 128, 1024, kSw128);
+                const uint64_t ayi = smem_desc(a1 + (pa * 2 + 1) * kA1Plane + ks * 2048, kK1M * 128, 1024, kSw128);
+                const uint64_t bwr = smem_desc(wb + (pb * 2 + 0) * kWPart + kb * 4096 + ko, 16, 1024, kSw128);
+                const uint64_t bwi = smem_desc(wb + (pb * 2 + 1) * kWPart + kb * 4096 + ko, 16, 1024, kSw128);
+                const uint32_t f = (ks > 0 || q > 0) ? 1u : 0u;
+                mma_f16(t_d1r, ayr, bwr, id1, f);      // Yr Wr
+                mma_f16(t_d1r, ayi, bwi, id1n, 1u);    // -Yi Wi
+                mma_f16(t_d1i, ayr, bwi, id1, f);      // Yr Wi
+                mma_f16(t_d1i, ayi, bwr, id1, 1u);     // Yi Wr
+              }
             }
-            const uint32_t g1 = smem_u32(sG1 + wst * kG1Bytes);
+            const uint32_t g1 = smem_u32(sG1 + wst * PL * kG1Plane);
             for (int ks = 0; ks < NT / 16; ++ks)
-              mma_f16(t_d4, smem_desc(a4 + ks * 32, 16, 8 * kSw, kLayNT),
-                      smem_desc(g1 + ks * 32, 16, 8 * kSw, kLayNT), id4, ks > 0 ? 1u : 0u);
+              for (int q = 0; q < kPairs; ++q)
+                mma_f16(t_d4, smem_desc(a4 + pa_[q] * kA4Plane + ks * 32, 16, 8 * kSw, kLayNT),
+                        smem_desc(g1 + pb_[q] * kG1Plane + ks * 32, 16, 8 * kSw, kLayNT), id4,
+                        (ks > 0 || q > 0) ? 1u : 0u);
             mma_commit(&d1_full);
           }
           if (j >= 1) {
             // gY^T += gZ^T(chunk j-1) conj(W chunk j-1)
-            const int q = (j - 1) & 1;
-            if (!mbar_wait(&a2_full[q], a2_ph[q], kWaitNs)) { fail(26); ok = false; break; }
-            a2_ph[q] ^= 1;
+            const int q2 = kNA2 == 2 ? ((j - 1) & 1) : 0;
+            if (!mbar_wait(&a2_full[q2], a2_ph[q2], kWaitNs)) { fail(26); ok = false; break; }
+            a2_ph[q2] ^= 1;
             if (first_d2) {
               if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(27); ok = false; break; }
               d2f_ph ^= 1;
             }
             tc_fence_after();
-            const uint32_t wb = smem_u32(sW + prev_wst * kWBufBytes);
-            const uint32_t a2 = smem_u32(sA2 + q * kA2Bytes);
+            const uint32_t wb = smem_u32(sW + prev_wst * kWBuf);
+            const uint32_t a2 = smem_u32(sA2 + q2 * kA2Buf);
             for (int ks = 0; ks < kRC / 16; ++ks) {
-              const uint64_t agr = smem_desc(a2 + 0 * 128 * 64 + ks * 32, 16, 512, kSw64);
-              const uint64_t agi = smem_desc(a2 + 1 * 128 * 64 + ks * 32, 16, 512, kSw64);
-              const uint64_t bwr = smem_desc(wb + 0 * 3 * 4096 + ks * 2048, 4096, 1024, kSw128);
-              const uint64_t bwi = smem_desc(wb + 1 * 3 * 4096 + ks * 2048, 4096, 1024, kSw128);
-              const uint32_t f = (first_d2 && ks == 0) ? 0u : 1u;
-              mma_f16(t_d2r, agr, bwr, id2, f);      // gZr Wr
-              mma_f16(t_d2r, agi, bwi, id2, 1u);     // gZi Wi
-              mma_f16(t_d2i, agi, bwr, id2, f);      // gZi Wr
-              mma_f16(t_d2i, agr, bwi, id2n, 1u);    // -gZr Wi
+              for (int q = 0; q < kPairs; ++q) {
+                const int pa = pa_[q], pb = pb_[q];
+                const uint64_t agr = smem_desc(a2 + (pa * 2 + 0) * kA2Part + ks * 32, 16, 512, kSw64);
+                const uint64_t agi = smem_desc(a2 + (pa * 2 + 1) * kA2Part + ks * 32, 16, 512, kSw64);
+                const uint64_t bwr = smem_desc(wb + (pb * 2 + 0) * kWPart + ks * 2048, 4096, 1024, kSw128);
+                const uint64_t bwi = smem_desc(wb + (pb * 2 + 1) * kWPart + ks * 2048, 4096, 1024, kSw128);
+                const uint32_t f = (first_d2 && ks == 0 && q == 0) ? 0u : 1u;
+                mma_f16(t_d2r, agr, bwr, id2, f);      // gZr Wr
+                mma_f16(t_d2r, agi, bwi, id2, 1u);     // gZi Wi
+                mma_f16(t_d2i, agi, bwr, id2, f);      // gZi Wr
+                mma_f16(t_d2i, agr, bwi, id2n, 1u);    // -gZr Wi
+              }
             }
             first_d2 = false;
-            mma_commit(&a2_free[q]);
+            mma_commit(&a2_free[q2]);
             mma_commit(&w_empty[prev_wst]);
           }
           if (j < args.n_chunks) {
@@ -265,40 +289,49 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&d1_free);
-        uint32_t pr[8], pi[8];
+        uint32_t hr[8], hi[8], lr[8], li[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-          float v[2][2];
+          float vr[2], vi[2];
 #pragma unroll
           for (int e = 0; e < 2; ++e) {
             const int k = 2 * i + e;
             const float m = sqrtf(zr[k] * zr[k] + zi[k] * zi[k]);
             const float f = m > 0.f ? g[k] / m : 0.f;
-            v[0][e] = zr[k] * f;
-            v[1][e] = zi[k] * f;
+            vr[e] = zr[k] * f;
+            vi[e] = zi[k] * f;
           }
-          __nv_bfloat162 hr = __floats2bfloat162_rn(v[0][0], v[0][1]);
-          __nv_bfloat162 hi = __floats2bfloat162_rn(v[1][0], v[1][1]);
-          pr[i] = *reinterpret_cast<uint32_t*>(&hr);
-          pi[i] = *reinterpret_cast<uint32_t*>(&hi);
+          __nv_bfloat162 a0 = __floats2bfloat162_rn(vr[0], vr[1]);
+          __nv_bfloat162 a1v = __floats2bfloat162_rn(vi[0], vi[1]);
+          hr[i] = *reinterpret_cast<uint32_t*>(&a0);
+          hi[i] = *reinterpret_cast<uint32_t*>(&a1v);
+          if (PL == 2) {
+            const float2 fa0 = __bfloat1622float2(a0), fa1 = __bfloat1622float2(a1v);
+            __nv_bfloat162 b0 = __floats2bfloat162_rn(vr[0] - fa0.x, vr[1] - fa0.y);
+            __nv_bfloat162 b1 = __floats2bfloat162_rn(vi[0] - fa1.x, vi[1] - fa1.y);
+            lr[i] = *reinterpret_cast<uint32_t*>(&b0);
+            li[i] = *reinterpret_cast<uint32_t*>(&b1);
+          }
         }
-        const int q = j & 1;
-        if (!mbar_wait(&a2_free[q], a2f_ph[q] ^ 1, kWaitNs)) { fail(29); ok = false; break; }
-        a2f_ph[q] ^= 1;
+        const int q2 = kNA2 == 2 ? (j & 1) : 0;
+        if (!mbar_wait(&a2_free[q2], a2f_ph[q2] ^ 1, kWaitNs)) { fail(29); ok = false; break; }
+        a2f_ph[q2] ^= 1;
         // K-major rows of 64 bytes (32 r), 64-byte swizzle: 16-byte chunk c -> c ^ ((row >> 1) & 3)
-        uint8_t* base = sA2 + q * kA2Bytes + row * 64;
+        uint8_t* base = sA2 + q2 * kA2Buf + row * 64;
         const int sw = (row >> 1) & 3;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-          const int chunk = half * 2 + c;
-          uint4 vr = make_uint4(pr[4 * c], pr[4 * c + 1], pr[4 * c + 2], pr[4 * c + 3]);
-          uint4 vi = make_uint4(pi[4 * c], pi[4 * c + 1], pi[4 * c + 2], pi[4 * c + 3]);
-          *reinterpret_cast<uint4*>(base + ((chunk ^ sw) * 16)) = vr;
-          *reinterpret_cast<uint4*>(base + 128 * 64 + ((chunk ^ sw) * 16)) = vi;
+          const int pos = ((half * 2 + c) ^ sw) * 16;
+          *reinterpret_cast<uint4*>(base + 0 * kA2Part + pos) = make_uint4(hr[4 * c], hr[4 * c + 1], hr[4 * c + 2], hr[4 * c + 3]);
+          *reinterpret_cast<uint4*>(base + 1 * kA2Part + pos) = make_uint4(hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
+          if (PL == 2) {
+            *reinterpret_cast<uint4*>(base + 2 * kA2Part + pos) = make_uint4(lr[4 * c], lr[4 * c + 1], lr[4 * c + 2], lr[4 * c + 3]);
+            *reinterpret_cast<uint4*>(base + 3 * kA2Part + pos) = make_uint4(li[4 * c], li[4 * c + 1], li[4 * c + 2], li[4 * c + 3]);
+          }
         }
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&a2_full[q]);
+        if (lane == 0) mbar_arrive(&a2_full[q2]);
       }
       if (!ok) break;
       // gY^T for this tile: columns lambda' = start + c, written as gY[lambda' - lam_min][n]
@@ -693,10 +726,12 @@ __global__ void k_build_wtb(DevPlan Pd, int a, int NT, int Lpad, __nv_bfloat16* 
 
 int tc_nt(int n_t);
 
-size_t tcb_smem_bytes(int NT) {
+size_t tcb_smem_bytes(int NT, int PL) {
+  const int k1m = PL == 1 ? 160 : 96, wblk = (k1m + 63) / 64, na2 = PL == 1 ? 2 : 1;
   const size_t g1 = ((kRC * NT * 2 + 1023) / 1024) * 1024;
   const size_t a4 = ((128 * NT * 2 + 1023) / 1024) * 1024;
-  return 1024 + kA1Bytes + 2 * kWBufBytes + 2 * g1 + a4 + 2 * kA2Bytes;
+  return 1024 + (size_t)PL * 2 * (2 * k1m * 128) + 2 * (size_t)PL * 2 * wblk * 4096 +
+         2 * (size_t)PL * g1 + (size_t)PL * a4 + (size_t)na2 * PL * 2 * 128 * 64;
 }
 
 bool tcb_supported(const jtfs_plan* p) {
@@ -728,9 +763,18 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
     const int K1 = (p->n1 - start + 31) / 32 * 32;
     for (int n0 = 0; n0 < A.L; n0 += 128) its.push_back({a, n0, start, K1, (long long)K1});
   }
-  std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+  // items whose Y^T tile fits the resident three-pass form (K1 <= 96) first, longest first
+  std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) {
+    const bool rx = x.K1 <= 96, ry = y.K1 <= 96;
+    if (rx != ry) return rx;
+    return x.cost > y.cost;
+  });
   p->tcb_items.clear();
-  for (auto& i : its) { p->tcb_items.push_back(i.a); p->tcb_items.push_back(i.n0); p->tcb_items.push_back(i.start); p->tcb_items.push_back(i.K1); }
+  p->tcb_n_res = 0;
+  for (auto& i : its) {
+    p->tcb_items.push_back(i.a); p->tcb_items.push_back(i.n0); p->tcb_items.push_back(i.start); p->tcb_items.push_back(i.K1);
+    if (i.K1 <= 96) ++p->tcb_n_res;
+  }
   p->tcb_wt_rows = std::max(rows, 128);
   size_t off = 0;
   auto place = [&](size_t bytes) { size_t at = off; off += (bytes + 1023) & ~(size_t)1023; return at; };
@@ -836,9 +880,8 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       }
     }
   }
+  const int n_all = (int)(p->tcb_items.size() / 4);
   TbArgs args;
-  args.items = reinterpret_cast<const int4*>(p->d_tcb_items);
-  args.n_items = (int)(p->tcb_items.size() / 4) * B;
   args.B = B;
   args.n_rows = rows;
   args.n_chunks = n_chunks;
@@ -846,53 +889,68 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   args.wt_row0 = p->d_wtb_row0;
   args.gy = gy;
   args.err = p->d_err;
-  if (args.n_items == 0) return JTFS_OK;
   int n_sm = 148;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
-  const int grid = std::min(args.n_items, n_sm);
-  if (three) {
-    Tb3Maps maps;
-    for (int i = 0; i < 4; ++i) maps.w[i] = mw[i];
-    for (int h = 0; h < 2; ++h) {
-      for (int a = 0; a < 16; ++a) maps.y[h][a] = my[h][a];
-      maps.g1[h] = mg1[h];
-      maps.wt[h] = mwt[h];
+  TbMaps maps;
+  for (int i = 0; i < 4; ++i) maps.w[i] = mw[i];
+  for (int h = 0; h < 2; ++h) {
+    for (int a = 0; a < 16; ++a) maps.y[h][a] = my[h][a];
+    maps.g1[h] = mg1[h];
+    maps.wt[h] = mwt[h];
+  }
+  // resident-Y launches: every item for one BF16 pass; the K1 <= 96 items for three passes
+  const int PL = three ? 2 : 1;
+  int n_res = three ? (NT <= 32 ? p->tcb_n_res : 0) : n_all;
+  if (n_res > 0) {
+    args.items = reinterpret_cast<const int4*>(p->d_tcb_items);
+    args.n_items = n_res * B;
+    const int grid = std::min(args.n_items, n_sm);
+    const size_t smem = tcb_smem_bytes(NT, PL);
+#define JTFS_LAUNCH_TCB(NTV, PLV)                                                               \
+  do {                                                                                          \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_tc<NTV, PLV>,                       \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                              (int)smem), "attr tcb")) != JTFS_OK)              \
+      return rc;                                                                                \
+    k_joint_bwd_tc<NTV, PLV><<<grid, kThreads, smem, st>>>(maps, args, d);                     \
+  } while (0)
+    if (PL == 1) {
+      if (NT == 16) JTFS_LAUNCH_TCB(16, 1);
+      else if (NT == 32) JTFS_LAUNCH_TCB(32, 1);
+      else JTFS_LAUNCH_TCB(64, 1);
+    } else {
+      if (NT == 16) JTFS_LAUNCH_TCB(16, 2);
+      else JTFS_LAUNCH_TCB(32, 2);
     }
-    const size_t smem = tcb3_smem_bytes(NT);
+#undef JTFS_LAUNCH_TCB
+    if ((rc = cuda_check(cudaGetLastError(), "k_joint_bwd_tc")) != JTFS_OK) return rc;
+  }
+  if (!three || n_res == n_all) return JTFS_OK;
+  // streamed-Y three-pass launch for the remaining items
+  args.items = reinterpret_cast<const int4*>(p->d_tcb_items) + n_res;
+  args.n_items = (n_all - n_res) * B;
+  const int grid = std::min(args.n_items, n_sm);
+  Tb3Maps maps3;
+  for (int i = 0; i < 4; ++i) maps3.w[i] = mw[i];
+  for (int h = 0; h < 2; ++h) {
+    for (int a = 0; a < 16; ++a) maps3.y[h][a] = my[h][a];
+    maps3.g1[h] = mg1[h];
+    maps3.wt[h] = mwt[h];
+  }
+  const size_t smem = tcb3_smem_bytes(NT);
 #define JTFS_LAUNCH_TCB3(NTV, WBV)                                                              \
   do {                                                                                          \
     if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_tc3<NTV, WBV>,                      \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr tcb3")) != JTFS_OK)             \
       return rc;                                                                                \
-    k_joint_bwd_tc3<NTV, WBV><<<grid, kThreads, smem, st>>>(maps, args, d);                    \
+    k_joint_bwd_tc3<NTV, WBV><<<grid, kThreads, smem, st>>>(maps3, args, d);                   \
   } while (0)
-    if (NT == 16) JTFS_LAUNCH_TCB3(16, 2);
-    else if (NT == 32) JTFS_LAUNCH_TCB3(32, 2);
-    else JTFS_LAUNCH_TCB3(64, 1);
+  if (NT == 16) JTFS_LAUNCH_TCB3(16, 2);
+  else if (NT == 32) JTFS_LAUNCH_TCB3(32, 2);
+  else JTFS_LAUNCH_TCB3(64, 1);
 #undef JTFS_LAUNCH_TCB3
-    return cuda_check(cudaGetLastError(), "k_joint_bwd_tc3");
-  }
-  TbMaps maps;
-  maps.w[0] = mw[0];
-  maps.w[1] = mw[1];
-  for (int a = 0; a < 16; ++a) maps.y[a] = my[0][a];
-  maps.g1 = mg1[0];
-  maps.wt = mwt[0];
-  const size_t smem = tcb_smem_bytes(NT);
-#define JTFS_LAUNCH_TCB(NTV)                                                                    \
-  do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_tc<NTV>,                            \
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                                              (int)smem), "attr tcb")) != JTFS_OK)              \
-      return rc;                                                                                \
-    k_joint_bwd_tc<NTV><<<grid, kThreads, smem, st>>>(maps, args, d);                          \
-  } while (0)
-  if (NT == 16) JTFS_LAUNCH_TCB(16);
-  else if (NT == 32) JTFS_LAUNCH_TCB(32);
-  else JTFS_LAUNCH_TCB(64);
-#undef JTFS_LAUNCH_TCB
-  return cuda_check(cudaGetLastError(), "k_joint_bwd_tc");
+  return cuda_check(cudaGetLastError(), "k_joint_bwd_tc3");
 }
 
 }  // namespace jtfs
