@@ -96,7 +96,8 @@ struct jtfs_plan {
   void* d_wplanes[4];          // Wr_hi, Wi_hi, Wr_lo, Wi_lo: [C * n1][n1_pad] bf16
   void* d_wtf;                 // pooling weights hi / lo: [n2 * NT][tc_wt_cols] bf16
   int tc_wt_cols;
-  std::vector<int> tc_items;   // (alpha, m0, n_tiles, 0) per signal, longest first
+  std::vector<int> tc_items;   // (alpha, m0, n_tiles, 0) per signal; resident-W items first
+  int tc_n_res;                // items whose W tile fits the resident form
   int* d_tc_items;
   int* d_err;                  // device status word of the bounded waits
   void* d_tc_mem;
@@ -151,6 +152,7 @@ struct StageScope {
 // tensor-core contraction (kernels_tc.cu)
 bool tc_supported(const jtfs_plan* p);
 int tc_nt(int n_t);
+int tc_res_kb(const jtfs_plan* p);
 jtfs_status build_tc_tables(jtfs_plan* p);
 jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi, const void* ylo,
                                 float* Pbuf, float* s2, cudaStream_t st);

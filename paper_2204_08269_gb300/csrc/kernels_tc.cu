@@ -13,8 +13,8 @@
 // Complex product from real MMAs into two TMEM accumulators, using the descriptor's
 // negate-A bit:  Re += Wr Yr + (-Wi) Yi,  Im += Wr Yi + Wi Yr.
 //
-// Roles (384 threads): warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM owner),
-// warps 4..11 = epilogue (two warps per TMEM lane quarter, each on half of the columns).
+// Roles (640 threads): warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM owner),
+// warps 4..19 = epilogue (four warps per TMEM lane quarter, 16 columns each).
 // Every wait is bounded; on timeout the CTA records an error code and unwinds.
 #include <cuda_bf16.h>
 
@@ -34,8 +34,8 @@ using namespace umma;
 namespace {
 
 constexpr int kBM = 128, kBN = 64, kBK = 32;
-constexpr int kThreads = 384;
-constexpr int kEpiWarp0 = 4;
+constexpr int kEpiWarp0 = 4, kEpiWarps = 16;
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
 
 struct TcMaps {
@@ -49,7 +49,8 @@ struct TcArgs {
   int n_items;             // n_base * B
   int B;
   int passes;              // 1 or 3
-  int stages;              // pipeline depth (2..4)
+  int stages;              // pipeline depth (2..8)
+  int res_kb;              // k-blocks of the resident W tile (RES form)
   int n_rows;              // C * n1
   int nt;                  // frames
   float* P;                // [B][n2][C*n1][nt]
@@ -61,7 +62,15 @@ struct TcArgs {
 // [128 a, 128 a + 64), Im at [128 a + 64, 128 a + 128)); the epilogue writes |Z| of the tile
 // as BF16 (hi, and lo for the split) into shared memory, and a second, small MMA pools it
 // with the tile's phi_T weights into a per-row accumulator at TMEM columns [256, 256 + NT).
-template <int NT>
+// RES = true keeps the item's W tile (every k-block, hi and lo) resident in shared memory for
+// all of its tiles and streams only the Y blocks; RES = false streams both.
+//
+// The lambda' range of rate alpha starts at lam_min rounded down to a multiple of 8 (the TMA
+// alignment of the W planes) and the MMAs cover it in steps of 16, so a rate with 12 rows
+// costs one K = 16 step, not a 32-wide block.  Sixteen epilogue warps (four per TMEM lane
+// quarter, 16 columns each) keep enough independent work in flight to hide the TMEM-load and
+// square-root latencies of the modulus, which costs as much as the product for small K.
+template <int NT, bool RES>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   extern __shared__ uint8_t smem_raw[];
@@ -72,11 +81,15 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   constexpr uint32_t kBPlane = kBK * kBN * 2;           // 4 KB, 128-byte swizzle
   constexpr uint32_t kZPlane = kBM * kBN * 2;           // 16 KB, 128-byte swizzle
   constexpr uint32_t kWPlane = NT * kBN * 2;            // NT rows of 128 bytes
-  const uint32_t stage_bytes = (kAPlane + kBPlane) * 2 * planes;
-  uint8_t* sZ = sm + S * stage_bytes;                   // 2 buffers x planes
-  uint8_t* sWt = sZ + 2 * planes * kZPlane;             // 2 buffers x planes
-  __shared__ uint64_t full_bar[4], empty_bar[4], tfull[2], tempty[2], zfull[2], zempty[2],
-      wfull[2], wempty[2], d3full, d3free, mma_done;
+  const int max_kb = args.res_kb;                       // k-blocks the resident W tile holds
+  const uint32_t stage_bytes = RES ? kBPlane * 2 * planes : (kAPlane + kBPlane) * 2 * planes;
+  const int NZ = (RES && planes == 2) ? 1 : 2;          // |Z| staging buffers
+  uint8_t* sA = sm;                                     // resident W tile (RES)
+  uint8_t* sStage = sm + (RES ? planes * 2 * max_kb * kAPlane : 0);
+  uint8_t* sZ = sStage + S * stage_bytes;               // NZ buffers x planes
+  uint8_t* sWt = sZ + NZ * planes * kZPlane;            // 2 buffers x planes
+  __shared__ uint64_t full_bar[8], empty_bar[8], tfull[2], tempty[2], zfull[2], zempty[2],
+      wfull[2], wempty[2], d3full, d3free, a_full, a_free, mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -89,14 +102,16 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], 8);
-      mbar_init(&zfull[a], 8);
+      mbar_init(&tempty[a], kEpiWarps);
+      mbar_init(&zfull[a], kEpiWarps);
       mbar_init(&zempty[a], 1);
       mbar_init(&wfull[a], 1);
       mbar_init(&wempty[a], 1);
     }
     mbar_init(&d3full, 1);
-    mbar_init(&d3free, 8);
+    mbar_init(&d3free, 4);
+    mbar_init(&a_full, 1);
+    mbar_init(&a_free, 1);
     mbar_init(&mma_done, 1);
     fence_barrier_init();
   }
@@ -119,29 +134,46 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       int stage = 0, ws = 0;
-      uint32_t phase = 0, wph = 0;
-      int armed[4] = {-1, -1, -1, -1}, armed_w[2] = {-1, -1};
+      uint32_t phase = 0, wph = 0, aph = 0;
+      // stages / weight buffers with a load in flight, and the parity each one completes
+      uint32_t armed = 0, armed_par = 0, armed_w = 0, armed_w_par = 0;
+      int armed_a = -1;
       bool ok = true;
       for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it / args.B];
         const int a = item.x, b = it % args.B, m0 = item.y, ntiles = item.z;
         const Rate2 A = P.rates2[a];
-        const int kb0 = A.lam_min / kBK, kb1 = (P.n1 + kBK - 1) / kBK;
+        const int lm8 = A.lam_min & ~7;
+        const int nkb = (((P.n1 - lm8 + 15) >> 4) + 1) >> 1;
+        if (RES) {
+          if (!mbar_wait(&a_free, aph ^ 1, kWaitNs)) { fail(10); ok = false; break; }
+          mbar_arrive_expect_tx(&a_full, planes * 2 * nkb * kAPlane);
+          armed_a = (int)aph;
+          for (int pl = 0; pl < planes; ++pl)
+            for (int part = 0; part < 2; ++part)
+              for (int kb = 0; kb < nkb; ++kb)
+                tma_load_2d(sA + ((pl * 2 + part) * max_kb + kb) * kAPlane,
+                            &maps.w[pl * 2 + part], lm8 + kb * kBK, m0, &a_full);
+          aph ^= 1;
+        }
         for (int j = 0; j < ntiles && ok; ++j) {
           // operand k-blocks of the tile first, then its pooling weights: the weight buffer
           // is released only after the previous tile's pooling, which must not hold back the
           // prefetch of the next tile's operands
-          for (int kb = kb0; kb < kb1; ++kb) {
+          for (int kb = 0; kb < nkb; ++kb) {
             if (!mbar_wait(&empty_bar[stage], phase ^ 1, kWaitNs)) { fail(11); ok = false; break; }
-            uint8_t* st = sm + stage * stage_bytes;
+            uint8_t* st = sStage + stage * stage_bytes;
             mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
-            armed[stage] = (int)phase;
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+            uint8_t* sb = RES ? st : st + 2 * planes * kAPlane;
             for (int pl = 0; pl < planes; ++pl) {
               for (int part = 0; part < 2; ++part) {
-                tma_load_2d(st + (pl * 2 + part) * kAPlane, &maps.w[pl * 2 + part], kb * kBK, m0,
-                            &full_bar[stage]);
-                tma_load_3d(st + 2 * planes * kAPlane + (pl * 2 + part) * kBPlane, &maps.y[pl][a],
-                            j * kBN, kb * kBK - A.lam_min, 2 * b + part, &full_bar[stage]);
+                if (!RES)
+                  tma_load_2d(st + (pl * 2 + part) * kAPlane, &maps.w[pl * 2 + part],
+                              lm8 + kb * kBK, m0, &full_bar[stage]);
+                tma_load_3d(sb + (pl * 2 + part) * kBPlane, &maps.y[pl][a], j * kBN,
+                            lm8 + kb * kBK - A.lam_min, 2 * b + part, &full_bar[stage]);
               }
             }
             if (++stage == S) { stage = 0; phase ^= 1; }
@@ -149,17 +181,20 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           if (!ok) break;
           if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
           mbar_arrive_expect_tx(&wfull[ws], planes * kWPlane);
-          armed_w[ws] = (int)wph;
+          armed_w |= 1u << ws;
+          armed_w_par = (armed_w_par & ~(1u << ws)) | (wph << ws);
           for (int pl = 0; pl < planes; ++pl)
             tma_load_2d(sWt + (ws * planes + pl) * kWPlane, &maps.wt[pl], j * kBN, a * NT,
                         &wfull[ws]);
           if (++ws == 2) { ws = 0; wph ^= 1; }
         }
       }
+      // never leave the CTA with a copy in flight
       for (int s2 = 0; s2 < S; ++s2)
-        if (armed[s2] >= 0) mbar_wait(&full_bar[s2], (uint32_t)armed[s2], kWaitNs);
+        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, kWaitNs);
       for (int s2 = 0; s2 < 2; ++s2)
-        if (armed_w[s2] >= 0) mbar_wait(&wfull[s2], (uint32_t)armed_w[s2], kWaitNs);
+        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, kWaitNs);
+      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, kWaitNs);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -170,29 +205,39 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       const int npair = args.passes == 3 ? 3 : 1;
       const int pa_[3] = {0, 0, 1}, pb_[3] = {0, 1, 0};
       int stage = 0, acc = 0, zq = 0, wq = 0;
-      uint32_t phase = 0, acc_phase = 0, zph = 0, wph = 0, d3ph = 0;
+      uint32_t phase = 0, acc_phase = 0, zph = 0, wph = 0, d3ph = 0, aph = 0;
       bool ok = true;
       for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it / args.B];
         const Rate2 A = P.rates2[item.x];
-        const int kb0 = A.lam_min / kBK, kb1 = (P.n1 + kBK - 1) / kBK;
+        const int lm8 = A.lam_min & ~7;
+        const int nks = (P.n1 - lm8 + 15) >> 4;           // K = 16 steps of the item
+        const int nkb = (nks + 1) >> 1;
         const int ntiles = item.z;
+        if (RES) {
+          if (!mbar_wait(&a_full, aph, kWaitNs)) { fail(9); ok = false; break; }
+          aph ^= 1;
+        }
         for (int j = 0; j <= ntiles && ok; ++j) {
           if (j < ntiles) {
             if (!mbar_wait(&tempty[acc], acc_phase ^ 1, kWaitNs)) { fail(12); ok = false; break; }
             tc_fence_after();
             const uint32_t d_re = tbase + acc * 128, d_im = d_re + 64;
             bool first = true;
-            for (int kb = kb0; kb < kb1; ++kb) {
+            for (int kb = 0; kb < nkb; ++kb) {
               if (!mbar_wait(&full_bar[stage], phase, kWaitNs)) { fail(13); ok = false; break; }
               tc_fence_after();
-              const uint32_t sa = smem_u32(sm + stage * stage_bytes);
-              const uint32_t sb = sa + 2 * planes * kAPlane;
-              for (int ks = 0; ks < kBK / 16; ++ks) {
+              const uint32_t st = smem_u32(sStage + stage * stage_bytes);
+              const uint32_t sb = RES ? st : st + 2 * planes * kAPlane;
+              const uint32_t sa = RES ? smem_u32(sA) + kb * kAPlane : st;
+              const uint32_t a_stride = RES ? max_kb * kAPlane : kAPlane;   // between planes
+              const int kss = min(2, nks - 2 * kb);
+              for (int ks = 0; ks < kss; ++ks) {
                 for (int q = 0; q < npair; ++q) {
                   const int pa = pa_[q], pb = pb_[q];
-                  const uint64_t ar = smem_desc(sa + (pa * 2 + 0) * kAPlane + ks * 32, 16, 512, kSw64);
-                  const uint64_t ai = smem_desc(sa + (pa * 2 + 1) * kAPlane + ks * 32, 16, 512, kSw64);
+                  const uint32_t ar_a = sa + (pa * 2 + 0) * a_stride + ks * 32;
+                  const uint64_t ar = smem_desc(ar_a, 16, 512, kSw64);
+                  const uint64_t ai = smem_desc(ar_a + a_stride, 16, 512, kSw64);
                   const uint64_t br = smem_desc(sb + (pb * 2 + 0) * kBPlane + ks * 2048, kBPlane, 1024, kSw128);
                   const uint64_t bi = smem_desc(sb + (pb * 2 + 1) * kBPlane + ks * 2048, kBPlane, 1024, kSw128);
                   const uint32_t f = first ? 0u : 1u;
@@ -229,11 +274,12 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
                         (j == 1 && ks == 0 && q == 0) ? 0u : 1u);
             mma_commit(&zempty[zq]);
             mma_commit(&wempty[wq]);
-            if (++zq == 2) { zq = 0; zph ^= 1; }
+            if (++zq == NZ) { zq = 0; zph ^= 1; }
             if (++wq == 2) { wq = 0; wph ^= 1; }
           }
         }
         if (!ok) break;
+        if (RES) mma_commit(&a_free);
         mma_commit(&d3full);
       }
       mma_commit(&mma_done);
@@ -241,9 +287,9 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     }
   } else if (warp >= kEpiWarp0) {
     // ------------------------------------------------------------ epilogue
-    const int ew = warp - kEpiWarp0;          // 0..7
+    const int ew = warp - kEpiWarp0;          // 0..15
     const int quarter = warp & 3;             // TMEM lane quarter this warp may access
-    const int half = ew >> 2;                 // column half
+    const int colq = ew >> 2;                 // 16-column group of the tile
     const int row = quarter * 32 + lane;      // tile row
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     int acc = 0, zq = 0;
@@ -255,29 +301,23 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       for (int j = 0; j < item.z && ok; ++j) {
         if (!mbar_wait(&tfull[acc], acc_phase, kWaitNs)) { fail(14); ok = false; break; }
         tc_fence_after();
-        float m[32];
-        {
-          float re[16], im[16];
-          const uint32_t c_re = tbase + acc * 128 + half * 32;
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            tmem_ld16(c_re + lane_off + c * 16, re);
-            tmem_ld16(c_re + 64 + lane_off + c * 16, im);
-            tmem_wait_ld();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) m[c * 16 + i] = sqrtf(re[i] * re[i] + im[i] * im[i]);
-          }
-        }
+        float re[16], im[16];
+        const uint32_t c_re = tbase + acc * 128 + lane_off + colq * 16;
+        tmem_ld16(c_re, re);
+        tmem_ld16(c_re + 64, im);
+        tmem_wait_ld();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[acc]);
         if (++acc == 2) { acc = 0; acc_phase ^= 1; }
-        uint32_t hv[16], lv[16];
+        uint32_t hv[8], lv[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          __nv_bfloat162 h = __floats2bfloat162_rn(m[2 * i], m[2 * i + 1]);
+        for (int i = 0; i < 8; ++i) {
+          const float m0v = sqrt_approx(fmaf(re[2 * i], re[2 * i], im[2 * i] * im[2 * i]));
+          const float m1v = sqrt_approx(fmaf(re[2 * i + 1], re[2 * i + 1], im[2 * i + 1] * im[2 * i + 1]));
+          __nv_bfloat162 h = __floats2bfloat162_rn(m0v, m1v);
           const float2 hf = __bfloat1622float2(h);
-          __nv_bfloat162 l = __floats2bfloat162_rn(m[2 * i] - hf.x, m[2 * i + 1] - hf.y);
+          __nv_bfloat162 l = __floats2bfloat162_rn(m0v - hf.x, m1v - hf.y);
           hv[i] = *reinterpret_cast<uint32_t*>(&h);
           lv[i] = *reinterpret_cast<uint32_t*>(&l);
         }
@@ -285,8 +325,8 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         uint8_t* zb = sZ + zq * planes * kZPlane + row * 128;
         const int sw = row & 7;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int pos = ((half * 4 + c) ^ sw) * 16;
+        for (int c = 0; c < 2; ++c) {
+          const int pos = ((colq * 2 + c) ^ sw) * 16;
           *reinterpret_cast<uint4*>(zb + pos) =
               make_uint4(hv[4 * c], hv[4 * c + 1], hv[4 * c + 2], hv[4 * c + 3]);
           if (planes == 2)
@@ -296,31 +336,36 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&zfull[zq]);
-        if (++zq == 2) { zq = 0; zph ^= 1; }
+        if (++zq == NZ) { zq = 0; zph ^= 1; }
       }
       if (!ok) break;
+      if (colq != 0) continue;                // one warp per lane quarter reads the pooled rows
       if (!mbar_wait(&d3full, d3ph, kWaitNs)) { fail(20); break; }
       d3ph ^= 1;
       tc_fence_after();
-      float pv[NT];
+      const int r = m0 + row;
+      float* out = args.P + (((size_t)b * args.n2 + a) * args.n_rows + r) * args.nt;
 #pragma unroll
       for (int c = 0; c < NT; c += 16) {
         float v[16];
         tmem_ld16(tbase + 256 + lane_off + c, v);
         tmem_wait_ld();
+        if (r < args.n_rows) {
+          if ((args.nt & 3) == 0) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) pv[c + i] = v[i];
+            for (int t = 0; t < 16; t += 4)
+              if (c + t < args.nt)
+                *reinterpret_cast<float4*>(out + c + t) = make_float4(v[t], v[t + 1], v[t + 2], v[t + 3]);
+          } else {
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+              if (c + t < args.nt) out[c + t] = v[t];
+          }
+        }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&d3free);
-      const int r = m0 + row;
-      if (half == 0 && r < args.n_rows) {
-        float* out = args.P + (((size_t)b * args.n2 + a) * args.n_rows + r) * args.nt;
-#pragma unroll
-        for (int t = 0; t < NT; ++t)
-          if (t < args.nt) out[t] = pv[t];
-      }
     }
   }
   __syncthreads();
@@ -388,6 +433,12 @@ __global__ void k_build_wt(DevPlan Pd, int NT, int Lmax, __nv_bfloat16* hi, __nv
 }
 
 // ----------------------------------------------------------------------------- host side
+// 32-wide k-blocks of rate alpha: lambda' from lam_min rounded down to 8, in K = 16 steps
+static int tc_item_kb(int n1, int lam_min) {
+  const int lm8 = lam_min & ~7;
+  return (((n1 - lm8 + 15) >> 4) + 1) >> 1;
+}
+
 int tc_nt(int n_t) {
   int nt = 16;
   while (nt < n_t) nt <<= 1;
@@ -415,12 +466,23 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
     const Rate2& A = p->rates2[a];
     if (A.s == 0) continue;
     const int ntiles = (A.L + kBN - 1) / kBN;
-    const int kblocks = (p->n1 + kBK - 1) / kBK - A.lam_min / kBK;
+    const int kblocks = tc_item_kb(p->n1, A.lam_min);
     for (int m0 = 0; m0 < rows; m0 += kBM) its.push_back({a, m0, ntiles, (long long)ntiles * (kblocks + 2)});
   }
-  std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+  // items whose W tile fits the resident form first, longest first
+  const int res_kb = tc_res_kb(p);
+  auto nkb = [&](const It& x) { return tc_item_kb(p->n1, p->rates2[x.a].lam_min); };
+  std::stable_sort(its.begin(), its.end(), [&](const It& x, const It& y) {
+    const bool rx = nkb(x) <= res_kb, ry = nkb(y) <= res_kb;
+    if (rx != ry) return rx;
+    return x.cost > y.cost;
+  });
   p->tc_items.clear();
-  for (auto& it : its) { p->tc_items.push_back(it.a); p->tc_items.push_back(it.m0); p->tc_items.push_back(it.nt); p->tc_items.push_back(0); }
+  p->tc_n_res = 0;
+  for (auto& it : its) {
+    p->tc_items.push_back(it.a); p->tc_items.push_back(it.m0); p->tc_items.push_back(it.nt); p->tc_items.push_back(0);
+    if (nkb(it) <= res_kb) ++p->tc_n_res;
+  }
   size_t off = 0;
   auto place = [&](size_t bytes) { size_t at = off; off += (bytes + 1023) & ~(size_t)1023; return at; };
   size_t o_w[4];
@@ -446,6 +508,31 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   k_build_wt<<<1024, 256>>>(p->dp, NT, Lmax, (__nv_bfloat16*)p->d_wtf,
                             (__nv_bfloat16*)p->d_wtf + wt_elems);
   return cuda_check(cudaDeviceSynchronize(), "build tc tables");
+}
+
+int tc_res_kb(const jtfs_plan* p) { return p->cfg.precision == JTFS_PREC_FP32 ? 3 : 6; }
+
+// stages of the resident-W form: the W tile, one |Z| buffer for the split (two otherwise), the
+// weight buffers, and as many 8 KB (16 KB for the split) Y stages as fit, up to 8
+int tc_stages_res(const jtfs_plan* p) {
+  const int planes = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
+  const int NT = tc_nt(p->n_t);
+  const int nz = planes == 2 ? 1 : 2;
+  const size_t fixed = 1024 + (size_t)planes * 2 * tc_res_kb(p) * kBM * kBK * 2 +
+                       (size_t)nz * planes * kBM * kBN * 2 + 2 * (size_t)planes * NT * kBN * 2;
+  const size_t stage = (size_t)planes * 2 * kBK * kBN * 2;
+  const size_t budget = 225 * 1024;
+  if (fixed + 2 * stage > budget) return 0;
+  return (int)std::min<size_t>(8, (budget - fixed) / stage);
+}
+
+size_t tc_smem_res_bytes(const jtfs_plan* p) {
+  const int planes = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
+  const int NT = tc_nt(p->n_t);
+  const int nz = planes == 2 ? 1 : 2;
+  return 1024 + (size_t)planes * 2 * tc_res_kb(p) * kBM * kBK * 2 +
+         (size_t)tc_stages_res(p) * planes * 2 * kBK * kBN * 2 + (size_t)nz * planes * kBM * kBN * 2 +
+         2 * (size_t)planes * NT * kBN * 2;
 }
 
 int tc_stages(const jtfs_plan* p) {
@@ -517,37 +604,51 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       return JTFS_ERR_CUDA;
     }
   }
+  const int n_all = (int)(p->tc_items.size() / 4);
+  const int n_res = tc_stages_res(p) >= 2 ? p->tc_n_res : 0;
   TcArgs args;
-  args.items = reinterpret_cast<const int4*>(p->d_tc_items);
-  args.n_items = (int)(p->tc_items.size() / 4) * B;
   args.B = B;
   args.passes = passes;
-  args.stages = tc_stages(p);
+  args.res_kb = tc_res_kb(p);
   args.n_rows = rows;
   args.nt = p->n_t;
   args.P = Pbuf;
   args.n2 = p->n2;
   args.err = p->d_err;
   jtfs_status rc;
-  if (args.n_items > 0) {
-    const size_t smem = tc_smem_bytes(p);
-    int n_sm = 148;
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
-    const int grid = std::min(args.n_items, n_sm);
-#define JTFS_LAUNCH_TC(NTV)                                                                     \
+  int n_sm = 148;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
+#define JTFS_LAUNCH_TC(NTV, RESV)                                                               \
   do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_tc<NTV>,                            \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_tc<NTV, RESV>,                      \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr tc")) != JTFS_OK)               \
       return rc;                                                                                \
-    k_joint_fwd_tc<NTV><<<grid, kThreads, smem, st>>>(maps, args, d);                          \
+    k_joint_fwd_tc<NTV, RESV><<<grid, kThreads, smem, st>>>(maps, args, d);                    \
   } while (0)
-    if (NT == 16) JTFS_LAUNCH_TC(16);
-    else if (NT == 32) JTFS_LAUNCH_TC(32);
-    else JTFS_LAUNCH_TC(64);
-#undef JTFS_LAUNCH_TC
+  if (n_res > 0) {
+    args.items = reinterpret_cast<const int4*>(p->d_tc_items);
+    args.n_items = n_res * B;
+    args.stages = tc_stages_res(p);
+    const size_t smem = tc_smem_res_bytes(p);
+    const int grid = std::min(args.n_items, n_sm);
+    if (NT == 16) JTFS_LAUNCH_TC(16, true);
+    else if (NT == 32) JTFS_LAUNCH_TC(32, true);
+    else JTFS_LAUNCH_TC(64, true);
+    if ((rc = cuda_check(cudaGetLastError(), "k_joint_fwd_tc resident")) != JTFS_OK) return rc;
+  }
+  if (n_all > n_res) {
+    args.items = reinterpret_cast<const int4*>(p->d_tc_items) + n_res;
+    args.n_items = (n_all - n_res) * B;
+    args.stages = tc_stages(p);
+    const size_t smem = tc_smem_bytes(p);
+    const int grid = std::min(args.n_items, n_sm);
+    if (NT == 16) JTFS_LAUNCH_TC(16, false);
+    else if (NT == 32) JTFS_LAUNCH_TC(32, false);
+    else JTFS_LAUNCH_TC(64, false);
     if ((rc = cuda_check(cudaGetLastError(), "k_joint_fwd_tc")) != JTFS_OK) return rc;
   }
+#undef JTFS_LAUNCH_TC
   k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
   return cuda_check(cudaGetLastError(), "k_pool_lambda");
 }
