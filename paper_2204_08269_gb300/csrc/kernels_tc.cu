@@ -2,7 +2,7 @@
 // and tile of 128 stacked channel rows r = c * n1 + lambda,
 //     Z[r, n] = sum_lambda' W[r, lambda'] Y_alpha[lambda', n]      (complex, K = lambda')
 // with W[c * n1 + lambda, lambda'] = h_c[(lambda - lambda') mod N_fr], then |Z| and the phi_T
-// Riemann sum over n, accumulated per row across every 128-column tile of the signal:
+// Riemann sum over n, accumulated per row across every column tile of the signal:
 //     P[b, alpha, r, t] = sum_n w_alpha[n, t] |Z[r, n]|.
 // A separate small kernel applies the phi_F pooling along lambda (or none, Eq. 4).
 //
@@ -13,8 +13,13 @@
 // Complex product from real MMAs into two TMEM accumulators, using the descriptor's
 // negate-A bit:  Re += Wr Yr + (-Wi) Yi,  Im += Wr Yi + Wi Yr.
 //
-// Roles (640 threads): warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM owner),
-// warps 4..19 = epilogue (four warps per TMEM lane quarter, 16 columns each).
+// Column tiles are BN = 128 samples wide when the pooled frame count is 16 (the MMAs then
+// run at the full tensor rate; an M = 128, K = 16 MMA costs the same ~47 cycles for any
+// N <= 64) and 64 wide otherwise.  One accumulator (Re, Im: 2 BN TMEM columns) is released as
+// soon as the epilogue has loaded it, so the next tile's product overlaps the modulus.
+//
+// Roles (576 threads): warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM owner),
+// warps 2..17 = epilogue (four warps per TMEM lane quarter, BN / 4 columns each).
 // Every wait is bounded; on timeout the CTA records an error code and unwinds.
 #include <cuda_bf16.h>
 
@@ -33,23 +38,25 @@ using namespace umma;
 
 namespace {
 
-constexpr int kBM = 128, kBN = 64, kBK = 32;
-constexpr int kEpiWarp0 = 4, kEpiWarps = 16;
+constexpr int kBM = 128, kBK = 32;
+constexpr int kEpiWarp0 = 2, kEpiWarps = 16;
 constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
+constexpr int kMaxWS = 4;                     // pooling-weight ring depth (at most)
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
 
 struct TcMaps {
   CUtensorMap w[4];        // Wr_hi, Wi_hi, Wr_lo, Wi_lo : [C*n1 rows][n1_pad] bf16, box {32, 128}
   CUtensorMap y[2][16];    // [hi/lo][alpha] : [2B][K_alpha][L_alpha] bf16, box {64, 32, 1}
-  CUtensorMap wt[2];       // pooling weights hi/lo : [n2 * NT rows (t)][Lmax (n)], box {64, NT}
+  CUtensorMap wt[2];       // pooling weights hi/lo : [n2 * NT rows (t)][cols (n)], box {64, NT}
 };
 
 struct TcArgs {
-  const int4* items;       // (alpha, m0, n_tiles, 0), longest first; item it = base it / B, b = it % B
+  const int4* items;       // (alpha, m0, n_tiles, 0); item it = base it / B, b = it % B
   int n_items;             // n_base * B
   int B;
   int passes;              // 1 or 3
-  int stages;              // pipeline depth (2..8)
+  int stages;              // operand pipeline depth (2..8)
+  int wstages;             // pooling-weight ring depth (2..kMaxWS)
   int res_kb;              // k-blocks of the resident W tile (RES form)
   int n_rows;              // C * n1
   int nt;                  // frames
@@ -58,38 +65,58 @@ struct TcArgs {
   int* err;                // device status word (0 = ok)
 };
 
-// Main product per 64-column tile into a double-buffered TMEM accumulator (Re at columns
-// [128 a, 128 a + 64), Im at [128 a + 64, 128 a + 128)); the epilogue writes |Z| of the tile
-// as BF16 (hi, and lo for the split) into shared memory, and a second, small MMA pools it
-// with the tile's phi_T weights into a per-row accumulator at TMEM columns [256, 256 + NT).
-// RES = true keeps the item's W tile (every k-block, hi and lo) resident in shared memory for
-// all of its tiles and streams only the Y blocks; RES = false streams both.
-//
+// 32 lanes x 32 bits, 32 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int CW>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[CW]) {
+  if constexpr (CW == 32) {
+    tmem_ld32(taddr, v);
+  } else {
+    tmem_ld16(taddr, v);
+  }
+}
+
 // The lambda' range of rate alpha starts at lam_min rounded down to a multiple of 8 (the TMA
-// alignment of the W planes) and the MMAs cover it in steps of 16, so a rate with 12 rows
-// costs one K = 16 step, not a 32-wide block.  Sixteen epilogue warps (four per TMEM lane
-// quarter, 16 columns each) keep enough independent work in flight to hide the TMEM-load and
-// square-root latencies of the modulus, which costs as much as the product for small K.
-template <int NT, bool RES>
+// alignment of the W planes) and the MMAs cover it in K = 16 steps, so a rate with 12 rows
+// costs one step, not a 32-wide block.  RES = true keeps the item's W tile (every k-block,
+// hi and lo) resident in shared memory for all of its column tiles and streams only Y.
+template <int NT, int BN, bool RES>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int NH = BN / 64;                           // 64-column halves of a tile
+  constexpr int CW = BN / 4;                            // columns per epilogue warp
   const int planes = args.passes == 3 ? 2 : 1;          // hi (+ lo)
-  const int S = args.stages;
+  const int S = args.stages, WS = args.wstages;
   constexpr uint32_t kAPlane = kBM * kBK * 2;           // 8 KB, 64-byte swizzle
-  constexpr uint32_t kBPlane = kBK * kBN * 2;           // 4 KB, 128-byte swizzle
-  constexpr uint32_t kZPlane = kBM * kBN * 2;           // 16 KB, 128-byte swizzle
-  constexpr uint32_t kWPlane = NT * kBN * 2;            // NT rows of 128 bytes
-  const int max_kb = args.res_kb;                       // k-blocks the resident W tile holds
-  const uint32_t stage_bytes = RES ? kBPlane * 2 * planes : (kAPlane + kBPlane) * 2 * planes;
-  const int NZ = (RES && planes == 2) ? 1 : 2;          // |Z| staging buffers
+  constexpr uint32_t kBHalf = kBK * 64 * 2;             // 4 KB: 32 lambda' x 64 samples
+  constexpr uint32_t kZHalf = kBM * 64 * 2;             // 16 KB: 128 rows x 64 samples
+  constexpr uint32_t kWHalf = NT * 64 * 2;              // NT rows x 64 samples
+  const int max_kb = args.res_kb;
+  const uint32_t y_bytes = planes * 2 * NH * kBHalf;
+  const uint32_t stage_bytes = RES ? y_bytes : planes * 2 * kAPlane + y_bytes;
   uint8_t* sA = sm;                                     // resident W tile (RES)
   uint8_t* sStage = sm + (RES ? planes * 2 * max_kb * kAPlane : 0);
-  uint8_t* sZ = sStage + S * stage_bytes;               // NZ buffers x planes
-  uint8_t* sWt = sZ + NZ * planes * kZPlane;            // 2 buffers x planes
-  __shared__ uint64_t full_bar[8], empty_bar[8], tfull[2], tempty[2], zfull[2], zempty[2],
-      wfull[2], wempty[2], d3full, d3free, a_full, a_free, mma_done;
+  uint8_t* sZ = sStage + S * stage_bytes;               // planes x NH halves
+  uint8_t* sWt = sZ + planes * NH * kZHalf;             // WS buffers x planes x NH halves
+  __shared__ uint64_t full_bar[8], empty_bar[8], wfull[kMaxWS], wempty[kMaxWS], tfull, tempty,
+      zfull, zempty, d3full, d3free, a_full, a_free, mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -100,14 +127,14 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    for (int a = 0; a < 2; ++a) {
-      mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], kEpiWarps);
-      mbar_init(&zfull[a], kEpiWarps);
-      mbar_init(&zempty[a], 1);
-      mbar_init(&wfull[a], 1);
-      mbar_init(&wempty[a], 1);
+    for (int s = 0; s < WS; ++s) {
+      mbar_init(&wfull[s], 1);
+      mbar_init(&wempty[s], 1);
     }
+    mbar_init(&tfull, 1);
+    mbar_init(&tempty, kEpiWarps);
+    mbar_init(&zfull, kEpiWarps);
+    mbar_init(&zempty, 1);
     mbar_init(&d3full, 1);
     mbar_init(&d3free, 4);
     mbar_init(&a_full, 1);
@@ -122,6 +149,7 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
+  const uint32_t t_re = tbase, t_im = tbase + BN, t_pool = tbase + 2 * BN;
 
   auto fail = [&](int code) {
     if (!abort_flag) {
@@ -157,55 +185,55 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           aph ^= 1;
         }
         for (int j = 0; j < ntiles && ok; ++j) {
-          // operand k-blocks of the tile first, then its pooling weights: the weight buffer
-          // is released only after the previous tile's pooling, which must not hold back the
-          // prefetch of the next tile's operands
+          // operand k-blocks of the tile first, then its pooling weights
           for (int kb = 0; kb < nkb; ++kb) {
             if (!mbar_wait(&empty_bar[stage], phase ^ 1, kWaitNs)) { fail(11); ok = false; break; }
             uint8_t* st = sStage + stage * stage_bytes;
             mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
             armed |= 1u << stage;
             armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-            uint8_t* sb = RES ? st : st + 2 * planes * kAPlane;
+            uint8_t* sb = RES ? st : st + planes * 2 * kAPlane;
             for (int pl = 0; pl < planes; ++pl) {
               for (int part = 0; part < 2; ++part) {
                 if (!RES)
                   tma_load_2d(st + (pl * 2 + part) * kAPlane, &maps.w[pl * 2 + part],
                               lm8 + kb * kBK, m0, &full_bar[stage]);
-                tma_load_3d(sb + (pl * 2 + part) * kBPlane, &maps.y[pl][a], j * kBN,
-                            lm8 + kb * kBK - A.lam_min, 2 * b + part, &full_bar[stage]);
+                for (int h = 0; h < NH; ++h)
+                  tma_load_3d(sb + ((pl * 2 + part) * NH + h) * kBHalf, &maps.y[pl][a],
+                              j * BN + h * 64, lm8 + kb * kBK - A.lam_min, 2 * b + part,
+                              &full_bar[stage]);
               }
             }
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
           if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
-          mbar_arrive_expect_tx(&wfull[ws], planes * kWPlane);
+          mbar_arrive_expect_tx(&wfull[ws], planes * NH * kWHalf);
           armed_w |= 1u << ws;
           armed_w_par = (armed_w_par & ~(1u << ws)) | (wph << ws);
           for (int pl = 0; pl < planes; ++pl)
-            tma_load_2d(sWt + (ws * planes + pl) * kWPlane, &maps.wt[pl], j * kBN, a * NT,
-                        &wfull[ws]);
-          if (++ws == 2) { ws = 0; wph ^= 1; }
+            for (int h = 0; h < NH; ++h)
+              tma_load_2d(sWt + ((ws * planes + pl) * NH + h) * kWHalf, &maps.wt[pl],
+                          j * BN + h * 64, a * NT, &wfull[ws]);
+          if (++ws == WS) { ws = 0; wph ^= 1; }
         }
       }
       // never leave the CTA with a copy in flight
       for (int s2 = 0; s2 < S; ++s2)
         if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, kWaitNs);
-      for (int s2 = 0; s2 < 2; ++s2)
+      for (int s2 = 0; s2 < WS; ++s2)
         if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, kWaitNs);
       if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, kWaitNs);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t id_pos = instr_desc(kBM, kBN, 1, 1, 0, 1, 0);
-      const uint32_t id_neg = instr_desc(kBM, kBN, 1, 1, 0, 1, 1);
+      const uint32_t id_pos = instr_desc(kBM, BN, 1, 1, 0, 1, 0);
+      const uint32_t id_neg = instr_desc(kBM, BN, 1, 1, 0, 1, 1);
       const uint32_t id_pool = instr_desc(kBM, NT, 1, 1, 0, 0, 0);
       const int npair = args.passes == 3 ? 3 : 1;
-      const int pa_[3] = {0, 0, 1}, pb_[3] = {0, 1, 0};
-      int stage = 0, acc = 0, zq = 0, wq = 0;
-      uint32_t phase = 0, acc_phase = 0, zph = 0, wph = 0, d3ph = 0, aph = 0;
+      int stage = 0, wq = 0;
+      uint32_t phase = 0, tph = 0, zph = 0, wph = 0, d3ph = 0, aph = 0;
       bool ok = true;
       for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it / args.B];
@@ -220,62 +248,65 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         }
         for (int j = 0; j <= ntiles && ok; ++j) {
           if (j < ntiles) {
-            if (!mbar_wait(&tempty[acc], acc_phase ^ 1, kWaitNs)) { fail(12); ok = false; break; }
+            // the epilogue has loaded the previous tile out of the accumulator
+            if (!mbar_wait(&tempty, tph ^ 1, kWaitNs)) { fail(12); ok = false; break; }
             tc_fence_after();
-            const uint32_t d_re = tbase + acc * 128, d_im = d_re + 64;
-            bool first = true;
             for (int kb = 0; kb < nkb; ++kb) {
               if (!mbar_wait(&full_bar[stage], phase, kWaitNs)) { fail(13); ok = false; break; }
               tc_fence_after();
               const uint32_t st = smem_u32(sStage + stage * stage_bytes);
-              const uint32_t sb = RES ? st : st + 2 * planes * kAPlane;
+              const uint32_t sb = RES ? st : st + planes * 2 * kAPlane;
               const uint32_t sa = RES ? smem_u32(sA) + kb * kAPlane : st;
-              const uint32_t a_stride = RES ? max_kb * kAPlane : kAPlane;   // between planes
+              const uint32_t a_stride = RES ? max_kb * kAPlane : kAPlane;   // Re -> Im plane
               const int kss = min(2, nks - 2 * kb);
               for (int ks = 0; ks < kss; ++ks) {
                 for (int q = 0; q < npair; ++q) {
-                  const int pa = pa_[q], pb = pb_[q];
-                  const uint32_t ar_a = sa + (pa * 2 + 0) * a_stride + ks * 32;
+                  const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;    // hi.hi, hi.lo, lo.hi
+                  const uint32_t ar_a = sa + pa * 2 * a_stride + ks * 32;
                   const uint64_t ar = smem_desc(ar_a, 16, 512, kSw64);
                   const uint64_t ai = smem_desc(ar_a + a_stride, 16, 512, kSw64);
-                  const uint64_t br = smem_desc(sb + (pb * 2 + 0) * kBPlane + ks * 2048, kBPlane, 1024, kSw128);
-                  const uint64_t bi = smem_desc(sb + (pb * 2 + 1) * kBPlane + ks * 2048, kBPlane, 1024, kSw128);
-                  const uint32_t f = first ? 0u : 1u;
-                  mma_f16(d_re, ar, br, id_pos, f);    // Wr Yr
-                  mma_f16(d_re, ai, bi, id_neg, 1u);   // -Wi Yi
-                  mma_f16(d_im, ar, bi, id_pos, f);    // Wr Yi
-                  mma_f16(d_im, ai, br, id_pos, 1u);   // Wi Yr
-                  first = false;
+                  const uint32_t br_a = sb + pb * 2 * NH * kBHalf + ks * 2048;
+                  const uint64_t br = smem_desc(br_a, kBHalf, 1024, kSw128);
+                  const uint64_t bi = smem_desc(br_a + NH * kBHalf, kBHalf, 1024, kSw128);
+                  const uint32_t f = (kb | ks | q) ? 1u : 0u;
+                  mma_f16(t_re, ar, br, id_pos, f);    // Wr Yr
+                  mma_f16(t_re, ai, bi, id_neg, 1u);   // -Wi Yi
+                  mma_f16(t_im, ar, bi, id_pos, f);    // Wr Yi
+                  mma_f16(t_im, ai, br, id_pos, 1u);   // Wi Yr
                 }
               }
               mma_commit(&empty_bar[stage]);
               if (++stage == S) { stage = 0; phase ^= 1; }
             }
             if (!ok) break;
-            mma_commit(&tfull[acc]);
-            if (++acc == 2) { acc = 0; acc_phase ^= 1; }
+            mma_commit(&tfull);
+            tph ^= 1;
           }
           if (j >= 1) {
-            // pool the previous tile: D3 += |Z| (128 x 64) . w^T (64 x NT)
-            if (!mbar_wait(&zfull[zq], zph, kWaitNs)) { fail(16); ok = false; break; }
+            // pool the previous tile: D3 += |Z| (128 x BN) . w^T (BN x NT)
+            if (!mbar_wait(&zfull, zph, kWaitNs)) { fail(16); ok = false; break; }
             if (!mbar_wait(&wfull[wq], wph, kWaitNs)) { fail(17); ok = false; break; }
             if (j == 1) {
               if (!mbar_wait(&d3free, d3ph ^ 1, kWaitNs)) { fail(18); ok = false; break; }
               d3ph ^= 1;
             }
             tc_fence_after();
-            const uint32_t za = smem_u32(sZ + zq * planes * kZPlane);
-            const uint32_t wa = smem_u32(sWt + wq * planes * kWPlane);
-            for (int ks = 0; ks < kBN / 16; ++ks)
-              for (int q = 0; q < npair; ++q)
-                mma_f16(tbase + 256,
-                        smem_desc(za + pa_[q] * kZPlane + ks * 32, 16, 1024, kSw128),
-                        smem_desc(wa + pb_[q] * kWPlane + ks * 32, 16, 1024, kSw128), id_pool,
+            const uint32_t za = smem_u32(sZ);
+            const uint32_t wa = smem_u32(sWt + wq * planes * NH * kWHalf);
+            for (int ks = 0; ks < BN / 16; ++ks) {
+              const uint32_t zo = (ks >> 2) * kZHalf + (ks & 3) * 32;
+              const uint32_t wo = (ks >> 2) * kWHalf + (ks & 3) * 32;
+              for (int q = 0; q < npair; ++q) {
+                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                mma_f16(t_pool, smem_desc(za + pa * NH * kZHalf + zo, 16, 1024, kSw128),
+                        smem_desc(wa + pb * NH * kWHalf + wo, 16, 1024, kSw128), id_pool,
                         (j == 1 && ks == 0 && q == 0) ? 0u : 1u);
-            mma_commit(&zempty[zq]);
+              }
+            }
+            mma_commit(&zempty);
             mma_commit(&wempty[wq]);
-            if (++zq == NZ) { zq = 0; zph ^= 1; }
-            if (++wq == 2) { wq = 0; wph ^= 1; }
+            zph ^= 1;
+            if (++wq == WS) { wq = 0; wph ^= 1; }
           }
         }
         if (!ok) break;
@@ -285,61 +316,63 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       mma_commit(&mma_done);
       mbar_wait(&mma_done, 0, kWaitNs);
     }
-  } else if (warp >= kEpiWarp0) {
+  } else {
     // ------------------------------------------------------------ epilogue
     const int ew = warp - kEpiWarp0;          // 0..15
     const int quarter = warp & 3;             // TMEM lane quarter this warp may access
-    const int colq = ew >> 2;                 // 16-column group of the tile
+    const int cg = ew >> 2;                   // column group: columns [cg CW, cg CW + CW)
     const int row = quarter * 32 + lane;      // tile row
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    int acc = 0, zq = 0;
-    uint32_t acc_phase = 0, zph = 0, d3ph = 0;
+    // |Z| staging (K-major, 128-byte swizzle): half h = (cg CW) / 64, 16-byte chunk
+    // index (cg CW % 64) / 8 + c, swizzled with row & 7
+    uint8_t* zrow = sZ + ((cg * CW) >> 6) * kZHalf + row * 128;
+    const int chunk0 = ((cg * CW) & 63) >> 3;
+    const int sw = row & 7;
+    uint32_t tph = 0, zph = 0, d3ph = 0;
     for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
       const int4 item = args.items[it / args.B];
       const int a = item.x, b = it % args.B, m0 = item.y;
       bool ok = !abort_flag;
       for (int j = 0; j < item.z && ok; ++j) {
-        if (!mbar_wait(&tfull[acc], acc_phase, kWaitNs)) { fail(14); ok = false; break; }
+        if (!mbar_wait(&tfull, tph, kWaitNs)) { fail(14); ok = false; break; }
+        tph ^= 1;
         tc_fence_after();
-        float re[16], im[16];
-        const uint32_t c_re = tbase + acc * 128 + lane_off + colq * 16;
-        tmem_ld16(c_re, re);
-        tmem_ld16(c_re + 64, im);
+        float re[CW], im[CW];
+        tmem_ld_cols<CW>(t_re + lane_off + cg * CW, re);
+        tmem_ld_cols<CW>(t_im + lane_off + cg * CW, im);
         tmem_wait_ld();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&tempty[acc]);
-        if (++acc == 2) { acc = 0; acc_phase ^= 1; }
-        uint32_t hv[8], lv[8];
+        if (lane == 0) mbar_arrive(&tempty);
+        uint32_t hv[CW / 2], lv[CW / 2];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
+        for (int i = 0; i < CW / 2; ++i) {
           const float m0v = sqrt_approx(fmaf(re[2 * i], re[2 * i], im[2 * i] * im[2 * i]));
-          const float m1v = sqrt_approx(fmaf(re[2 * i + 1], re[2 * i + 1], im[2 * i + 1] * im[2 * i + 1]));
+          const float m1v =
+              sqrt_approx(fmaf(re[2 * i + 1], re[2 * i + 1], im[2 * i + 1] * im[2 * i + 1]));
           __nv_bfloat162 h = __floats2bfloat162_rn(m0v, m1v);
           const float2 hf = __bfloat1622float2(h);
           __nv_bfloat162 l = __floats2bfloat162_rn(m0v - hf.x, m1v - hf.y);
           hv[i] = *reinterpret_cast<uint32_t*>(&h);
           lv[i] = *reinterpret_cast<uint32_t*>(&l);
         }
-        if (!mbar_wait(&zempty[zq], zph ^ 1, kWaitNs)) { fail(19); ok = false; break; }
-        uint8_t* zb = sZ + zq * planes * kZPlane + row * 128;
-        const int sw = row & 7;
+        if (!mbar_wait(&zempty, zph ^ 1, kWaitNs)) { fail(19); ok = false; break; }
+        zph ^= 1;
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const int pos = ((colq * 2 + c) ^ sw) * 16;
-          *reinterpret_cast<uint4*>(zb + pos) =
+        for (int c = 0; c < CW / 8; ++c) {
+          const int pos = ((chunk0 + c) ^ sw) * 16;
+          *reinterpret_cast<uint4*>(zrow + pos) =
               make_uint4(hv[4 * c], hv[4 * c + 1], hv[4 * c + 2], hv[4 * c + 3]);
           if (planes == 2)
-            *reinterpret_cast<uint4*>(zb + kZPlane + pos) =
+            *reinterpret_cast<uint4*>(zrow + NH * kZHalf + pos) =
                 make_uint4(lv[4 * c], lv[4 * c + 1], lv[4 * c + 2], lv[4 * c + 3]);
         }
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&zfull[zq]);
-        if (++zq == NZ) { zq = 0; zph ^= 1; }
+        if (lane == 0) mbar_arrive(&zfull);
       }
       if (!ok) break;
-      if (colq != 0) continue;                // one warp per lane quarter reads the pooled rows
+      if (cg != 0) continue;                  // one warp per lane quarter reads the pooled rows
       if (!mbar_wait(&d3full, d3ph, kWaitNs)) { fail(20); break; }
       d3ph ^= 1;
       tc_fence_after();
@@ -348,7 +381,7 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
 #pragma unroll
       for (int c = 0; c < NT; c += 16) {
         float v[16];
-        tmem_ld16(tbase + 256 + lane_off + c, v);
+        tmem_ld16(t_pool + lane_off + c, v);
         tmem_wait_ld();
         if (r < args.n_rows) {
           if ((args.nt & 3) == 0) {
@@ -445,27 +478,80 @@ int tc_nt(int n_t) {
   return nt;
 }
 
+// column-tile width: 128 where the 16-frame pooling leaves the shared memory for it
+static int tc_bn(const jtfs_plan* p) { return tc_nt(p->n_t) == 16 ? 128 : 64; }
+
 bool tc_supported(const jtfs_plan* p) {
   return p->n2 <= 16 && tc_nt(p->n_t) <= 64 && p->cfg.precision != JTFS_PREC_FP32_SIMT &&
          p->cfg.precision != JTFS_PREC_TF32;
 }
 
+int tc_res_kb(const jtfs_plan* p) { return p->cfg.precision == JTFS_PREC_FP32 ? 2 : 4; }
+
+namespace {
+constexpr size_t kSmemBudget = 225 * 1024;
+
+struct TcShape {
+  int planes, NT, BN, NH, WS;
+  size_t fixed(bool res, int res_kb) const {
+    return 1024 + (res ? (size_t)planes * 2 * res_kb * kBM * kBK * 2 : 0) +
+           (size_t)planes * NH * kBM * 64 * 2 + (size_t)WS * planes * NH * NT * 64 * 2;
+  }
+  size_t stage(bool res) const {
+    return (res ? 0 : (size_t)planes * 2 * kBM * kBK * 2) + (size_t)planes * 2 * NH * kBK * 64 * 2;
+  }
+};
+
+TcShape tc_shape(const jtfs_plan* p) {
+  TcShape s;
+  s.planes = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
+  s.NT = tc_nt(p->n_t);
+  s.BN = tc_bn(p);
+  s.NH = s.BN / 64;
+  s.WS = 2;
+  // deepest weight ring (up to 4) that still leaves two operand stages in both forms
+  for (int ws = kMaxWS; ws > 2; --ws) {
+    TcShape t = s;
+    t.WS = ws;
+    if (t.fixed(true, tc_res_kb(p)) + 2 * t.stage(true) <= kSmemBudget &&
+        t.fixed(false, 0) + 2 * t.stage(false) <= kSmemBudget) {
+      s.WS = ws;
+      break;
+    }
+  }
+  return s;
+}
+
+int tc_stages_for(const jtfs_plan* p, bool res) {
+  const TcShape s = tc_shape(p);
+  const size_t fixed = s.fixed(res, tc_res_kb(p)), stage = s.stage(res);
+  if (fixed + 2 * stage > kSmemBudget) return 0;
+  return (int)std::min<size_t>(8, (kSmemBudget - fixed) / stage);
+}
+
+size_t tc_smem_for(const jtfs_plan* p, bool res) {
+  const TcShape s = tc_shape(p);
+  return s.fixed(res, tc_res_kb(p)) + (size_t)tc_stages_for(p, res) * s.stage(res);
+}
+}  // namespace
+
 jtfs_status build_tc_tables(jtfs_plan* p) {
   const int NT = tc_nt(p->n_t);
+  const int BN = tc_bn(p);
   p->n1_pad = (p->n1 + 63) / 64 * 64;   // W plane rows hold whole 64-column boxes
   const size_t wplane = (size_t)p->C * p->n1 * p->n1_pad;
-  int Lmax = 64;
+  int Lmax = BN;
   for (int a = 0; a < p->n2; ++a)
-    if (p->rates2[a].s) Lmax = std::max(Lmax, (p->rates2[a].L + 63) / 64 * 64);
+    if (p->rates2[a].s) Lmax = std::max(Lmax, (p->rates2[a].L + BN - 1) / BN * BN);
   p->tc_wt_cols = Lmax;
-  // items: (alpha, m0, n_tiles), longest first (cost ~ n_tiles * k-blocks)
+  // items: (alpha, m0, n_tiles)
   struct It { int a, m0, nt; long long cost; };
   std::vector<It> its;
   const int rows = p->C * p->n1;
   for (int a = 0; a < p->n2; ++a) {
     const Rate2& A = p->rates2[a];
     if (A.s == 0) continue;
-    const int ntiles = (A.L + kBN - 1) / kBN;
+    const int ntiles = (A.L + BN - 1) / BN;
     const int kblocks = tc_item_kb(p->n1, A.lam_min);
     for (int m0 = 0; m0 < rows; m0 += kBM) its.push_back({a, m0, ntiles, (long long)ntiles * (kblocks + 2)});
   }
@@ -510,51 +596,6 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   return cuda_check(cudaDeviceSynchronize(), "build tc tables");
 }
 
-int tc_res_kb(const jtfs_plan* p) { return p->cfg.precision == JTFS_PREC_FP32 ? 3 : 6; }
-
-// stages of the resident-W form: the W tile, one |Z| buffer for the split (two otherwise), the
-// weight buffers, and as many 8 KB (16 KB for the split) Y stages as fit, up to 8
-int tc_stages_res(const jtfs_plan* p) {
-  const int planes = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
-  const int NT = tc_nt(p->n_t);
-  const int nz = planes == 2 ? 1 : 2;
-  const size_t fixed = 1024 + (size_t)planes * 2 * tc_res_kb(p) * kBM * kBK * 2 +
-                       (size_t)nz * planes * kBM * kBN * 2 + 2 * (size_t)planes * NT * kBN * 2;
-  const size_t stage = (size_t)planes * 2 * kBK * kBN * 2;
-  const size_t budget = 225 * 1024;
-  if (fixed + 2 * stage > budget) return 0;
-  return (int)std::min<size_t>(8, (budget - fixed) / stage);
-}
-
-size_t tc_smem_res_bytes(const jtfs_plan* p) {
-  const int planes = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
-  const int NT = tc_nt(p->n_t);
-  const int nz = planes == 2 ? 1 : 2;
-  return 1024 + (size_t)planes * 2 * tc_res_kb(p) * kBM * kBK * 2 +
-         (size_t)tc_stages_res(p) * planes * 2 * kBK * kBN * 2 + (size_t)nz * planes * kBM * kBN * 2 +
-         2 * (size_t)planes * NT * kBN * 2;
-}
-
-int tc_stages(const jtfs_plan* p) {
-  const int passes = p->cfg.precision == JTFS_PREC_FP32 ? 3 : 1;
-  const int planes = passes == 3 ? 2 : 1;
-  const int NT = tc_nt(p->n_t);
-  const size_t stage = (size_t)(kBM * kBK * 2 + kBK * kBN * 2) * 2 * planes;
-  const size_t fixed = 1024 + 2 * (size_t)planes * kBM * kBN * 2 + 2 * (size_t)planes * NT * kBN * 2;
-  int S = 4;
-  while (S > 2 && fixed + S * stage > 225 * 1024) --S;
-  return S;
-}
-
-size_t tc_smem_bytes(const jtfs_plan* p) {
-  const int passes = p->cfg.precision == JTFS_PREC_FP32 ? 3 : 1;
-  const int planes = passes == 3 ? 2 : 1;
-  const int NT = tc_nt(p->n_t);
-  const size_t stage = (size_t)(kBM * kBK * 2 + kBK * kBN * 2) * 2 * planes;
-  return 1024 + tc_stages(p) * stage + 2 * (size_t)planes * kBM * kBN * 2 +
-         2 * (size_t)planes * NT * kBN * 2;
-}
-
 jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, const void* ylo_v,
                                 float* Pbuf, float* s2, cudaStream_t st) {
   const __nv_bfloat16* yhi = (const __nv_bfloat16*)yhi_v;
@@ -565,6 +606,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   const int passes = p->cfg.precision == JTFS_PREC_FP32 ? 3 : 1;
   const int rows = p->C * p->n1;
   const int NT = tc_nt(p->n_t);
+  const int BN = tc_bn(p);
   for (int i = 0; i < 4; ++i) {
     cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)rows};
     cuuint64_t str[1] = {(cuuint64_t)p->n1_pad * 2};
@@ -605,11 +647,16 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     }
   }
   const int n_all = (int)(p->tc_items.size() / 4);
-  const int n_res = tc_stages_res(p) >= 2 ? p->tc_n_res : 0;
+  const int n_res = tc_stages_for(p, true) >= 2 ? p->tc_n_res : 0;
+  if (n_all > n_res && tc_stages_for(p, false) < 2) {
+    set_error("tensor-core forward: no shared-memory layout for this configuration");
+    return JTFS_ERR_UNSUPPORTED;
+  }
   TcArgs args;
   args.B = B;
   args.passes = passes;
   args.res_kb = tc_res_kb(p);
+  args.wstages = tc_shape(p).WS;
   args.n_rows = rows;
   args.nt = p->n_t;
   args.P = Pbuf;
@@ -618,34 +665,30 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   jtfs_status rc;
   int n_sm = 148;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
-#define JTFS_LAUNCH_TC(NTV, RESV)                                                               \
+#define JTFS_LAUNCH_TC(NTV, BNV, RESV)                                                          \
   do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_tc<NTV, RESV>,                      \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_tc<NTV, BNV, RESV>,                 \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr tc")) != JTFS_OK)               \
       return rc;                                                                                \
-    k_joint_fwd_tc<NTV, RESV><<<grid, kThreads, smem, st>>>(maps, args, d);                    \
+    k_joint_fwd_tc<NTV, BNV, RESV><<<grid, kThreads, smem, st>>>(maps, args, d);               \
   } while (0)
-  if (n_res > 0) {
-    args.items = reinterpret_cast<const int4*>(p->d_tc_items);
-    args.n_items = n_res * B;
-    args.stages = tc_stages_res(p);
-    const size_t smem = tc_smem_res_bytes(p);
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool res = pass == 0;
+    const int first = res ? 0 : n_res, count = res ? n_res : n_all - n_res;
+    if (count <= 0) continue;
+    args.items = reinterpret_cast<const int4*>(p->d_tc_items) + first;
+    args.n_items = count * B;
+    args.stages = tc_stages_for(p, res);
+    const size_t smem = tc_smem_for(p, res);
     const int grid = std::min(args.n_items, n_sm);
-    if (NT == 16) JTFS_LAUNCH_TC(16, true);
-    else if (NT == 32) JTFS_LAUNCH_TC(32, true);
-    else JTFS_LAUNCH_TC(64, true);
-    if ((rc = cuda_check(cudaGetLastError(), "k_joint_fwd_tc resident")) != JTFS_OK) return rc;
-  }
-  if (n_all > n_res) {
-    args.items = reinterpret_cast<const int4*>(p->d_tc_items) + n_res;
-    args.n_items = (n_all - n_res) * B;
-    args.stages = tc_stages(p);
-    const size_t smem = tc_smem_bytes(p);
-    const int grid = std::min(args.n_items, n_sm);
-    if (NT == 16) JTFS_LAUNCH_TC(16, false);
-    else if (NT == 32) JTFS_LAUNCH_TC(32, false);
-    else JTFS_LAUNCH_TC(64, false);
+    if (BN == 128) {
+      if (res) JTFS_LAUNCH_TC(16, 128, true); else JTFS_LAUNCH_TC(16, 128, false);
+    } else if (NT == 32) {
+      if (res) JTFS_LAUNCH_TC(32, 64, true); else JTFS_LAUNCH_TC(32, 64, false);
+    } else {
+      if (res) JTFS_LAUNCH_TC(64, 64, true); else JTFS_LAUNCH_TC(64, 64, false);
+    }
     if ((rc = cuda_check(cudaGetLastError(), "k_joint_fwd_tc")) != JTFS_OK) return rc;
   }
 #undef JTFS_LAUNCH_TC

@@ -22,6 +22,7 @@ SMALL_CFGS = [
     dict(N=1024, J=6, Q=2, J_fr=2, Q_fr=1, T=1024, F=1),      # T = N: one frame
     dict(N=2048, J=7, Q=12, J_fr=3, Q_fr=2, T=128, F=12, oversampling=1),
     dict(N=1024, J=6, Q=16, J_fr=3, Q_fr=2, T=64, F=16),      # the gradient-check slice
+    dict(N=1024, J=6, Q=8, J_fr=3, Q_fr=1, T=32, F=8),        # 32 frames
 ]
 
 
