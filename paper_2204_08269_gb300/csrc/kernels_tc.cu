@@ -51,7 +51,9 @@ struct TcMaps {
 };
 
 struct TcArgs {
-  const int4* items;       // (alpha, m0, n_tiles, 0); item it = base it / B, b = it % B
+  const int4* items;       // (alpha, m0, n_tiles, 0) per base, longest first
+  int n_base;              // bases; item it = base it % n_base of signal it / n_base, so the
+                           // row tiles of one signal's Y run together and share it in L2
   int n_items;             // n_base * B
   int B;
   int passes;              // 1 or 3
@@ -168,8 +170,8 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       int armed_a = -1;
       bool ok = true;
       for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
-        const int4 item = args.items[it / args.B];
-        const int a = item.x, b = it % args.B, m0 = item.y, ntiles = item.z;
+        const int4 item = args.items[it % args.n_base];
+        const int a = item.x, b = it / args.n_base, m0 = item.y, ntiles = item.z;
         const Rate2 A = P.rates2[a];
         const int lm8 = A.lam_min & ~7;
         const int nkb = (((P.n1 - lm8 + 15) >> 4) + 1) >> 1;
@@ -236,7 +238,7 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       uint32_t phase = 0, tph = 0, zph = 0, wph = 0, d3ph = 0, aph = 0;
       bool ok = true;
       for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
-        const int4 item = args.items[it / args.B];
+        const int4 item = args.items[it % args.n_base];
         const Rate2 A = P.rates2[item.x];
         const int lm8 = A.lam_min & ~7;
         const int nks = (P.n1 - lm8 + 15) >> 4;           // K = 16 steps of the item
@@ -330,8 +332,8 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     const int sw = row & 7;
     uint32_t tph = 0, zph = 0, d3ph = 0;
     for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
-      const int4 item = args.items[it / args.B];
-      const int a = item.x, b = it % args.B, m0 = item.y;
+      const int4 item = args.items[it % args.n_base];
+      const int a = item.x, b = it / args.n_base, m0 = item.y;
       bool ok = !abort_flag;
       for (int j = 0; j < item.z && ok; ++j) {
         if (!mbar_wait(&tfull, tph, kWaitNs)) { fail(14); ok = false; break; }
@@ -399,6 +401,383 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&d3free);
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
+// ------------------------------------------------------------------ 16-frame form
+// With 16 pooled frames the phi_T pooling runs in the epilogue warps on the warp-level
+// tensor-core path (mma.sync m16n8k16, BF16 in, FP32 accumulate), which leaves all 512 TMEM
+// columns to two 128 x 128 complex accumulators: the next tile's product is issued while the
+// epilogue drains the previous one, and no pooling MMA sits between them.
+//
+// Each epilogue warp owns 32 rows (its TMEM lane quarter) x 32 columns of a tile.  Per
+// 16-column step it stages |Z| (hi, and lo for the split) in a private 32 x 16 BF16 block,
+// loads mma.sync fragments with ldmatrix and accumulates P[row, t] = sum_n |Z| w[n, t] in
+// registers over every tile of the item; at the end the four column groups of a quarter
+// are summed through shared memory in a fixed order.
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr));
+}
+__device__ __forceinline__ void hmma16816(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                          uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, "
+      "{%4, %5, %6, %7}, {%8, %9}, {%0, %1, %2, %3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <bool RES>
+__global__ void __launch_bounds__(kThreads, 1)
+k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int NT = 16, BN = 128, NH = 2;
+  const int planes = args.passes == 3 ? 2 : 1;
+  const int S = args.stages, WS = args.wstages;
+  constexpr uint32_t kAPlane = kBM * kBK * 2;           // 8 KB, 64-byte swizzle
+  constexpr uint32_t kBHalf = kBK * 64 * 2;             // 4 KB: 32 lambda' x 64 samples
+  constexpr uint32_t kWHalf = NT * 64 * 2;              // 2 KB: 16 frames x 64 samples
+  constexpr uint32_t kStg = 32 * 16 * 2;                // 1 KB: a warp's 32 x 16 |Z| block
+  const int max_kb = args.res_kb;
+  const uint32_t y_bytes = planes * 2 * NH * kBHalf;
+  const uint32_t stage_bytes = RES ? y_bytes : planes * 2 * kAPlane + y_bytes;
+  uint8_t* sA = sm;
+  uint8_t* sStage = sm + (RES ? planes * 2 * max_kb * kAPlane : 0);
+  uint8_t* sWt = sStage + S * stage_bytes;              // WS x NH halves x planes (hi, lo adjacent)
+  uint8_t* sStg = sWt + WS * NH * planes * kWHalf;      // 16 warps x planes x 1 KB
+  float* sRed = (float*)(sStg + kEpiWarps * planes * kStg);   // [4 groups][128 rows][16]
+  __shared__ uint64_t full_bar[8], empty_bar[8], wfull[kMaxWS], wempty[kMaxWS], tfull[2],
+      tempty[2], red_full[4], red_free[4], a_full, a_free, mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int s = 0; s < WS; ++s) {
+      mbar_init(&wfull[s], 1);
+      mbar_init(&wempty[s], kEpiWarps);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], kEpiWarps);
+    }
+    for (int q = 0; q < 4; ++q) {
+      mbar_init(&red_full[q], 4);
+      mbar_init(&red_free[q], 1);
+    }
+    mbar_init(&a_full, 1);
+    mbar_init(&a_free, 1);
+    mbar_init(&mma_done, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+
+  auto fail = [&](int code) {
+    if (!abort_flag) {
+      abort_flag = 1;
+      atomicCAS(args.err, 0, code);
+    }
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0, ws = 0;
+      uint32_t phase = 0, wph = 0, aph = 0;
+      uint32_t armed = 0, armed_par = 0, armed_w = 0, armed_w_par = 0;
+      int armed_a = -1;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        const int a = item.x, b = it / args.n_base, m0 = item.y, ntiles = item.z;
+        const Rate2 A = P.rates2[a];
+        const int lm8 = A.lam_min & ~7;
+        const int nkb = (((P.n1 - lm8 + 15) >> 4) + 1) >> 1;
+        if (RES) {
+          if (!mbar_wait(&a_free, aph ^ 1, kWaitNs)) { fail(10); ok = false; break; }
+          mbar_arrive_expect_tx(&a_full, planes * 2 * nkb * kAPlane);
+          armed_a = (int)aph;
+          for (int pl = 0; pl < planes; ++pl)
+            for (int part = 0; part < 2; ++part)
+              for (int kb = 0; kb < nkb; ++kb)
+                tma_load_2d(sA + ((pl * 2 + part) * max_kb + kb) * kAPlane,
+                            &maps.w[pl * 2 + part], lm8 + kb * kBK, m0, &a_full);
+          aph ^= 1;
+        }
+        for (int j = 0; j < ntiles && ok; ++j) {
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!mbar_wait(&empty_bar[stage], phase ^ 1, kWaitNs)) { fail(11); ok = false; break; }
+            uint8_t* st = sStage + stage * stage_bytes;
+            mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+            uint8_t* sb = RES ? st : st + planes * 2 * kAPlane;
+            for (int pl = 0; pl < planes; ++pl) {
+              for (int part = 0; part < 2; ++part) {
+                if (!RES)
+                  tma_load_2d(st + (pl * 2 + part) * kAPlane, &maps.w[pl * 2 + part],
+                              lm8 + kb * kBK, m0, &full_bar[stage]);
+                for (int h = 0; h < NH; ++h)
+                  tma_load_3d(sb + ((pl * 2 + part) * NH + h) * kBHalf, &maps.y[pl][a],
+                              j * BN + h * 64, lm8 + kb * kBK - A.lam_min, 2 * b + part,
+                              &full_bar[stage]);
+              }
+            }
+            if (++stage == S) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
+          mbar_arrive_expect_tx(&wfull[ws], planes * NH * kWHalf);
+          armed_w |= 1u << ws;
+          armed_w_par = (armed_w_par & ~(1u << ws)) | (wph << ws);
+          for (int h = 0; h < NH; ++h)
+            for (int pl = 0; pl < planes; ++pl)
+              tma_load_2d(sWt + ((ws * NH + h) * planes + pl) * kWHalf, &maps.wt[pl],
+                          j * BN + h * 64, a * NT, &wfull[ws]);
+          if (++ws == WS) { ws = 0; wph ^= 1; }
+        }
+      }
+      for (int s2 = 0; s2 < S; ++s2)
+        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, kWaitNs);
+      for (int s2 = 0; s2 < WS; ++s2)
+        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, kWaitNs);
+      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, kWaitNs);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id_pos = instr_desc(kBM, BN, 1, 1, 0, 1, 0);
+      const uint32_t id_neg = instr_desc(kBM, BN, 1, 1, 0, 1, 1);
+      const int npair = args.passes == 3 ? 3 : 1;
+      int stage = 0, acc = 0;
+      uint32_t phase = 0, acc_ph = 0, aph = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        const Rate2 A = P.rates2[item.x];
+        const int lm8 = A.lam_min & ~7;
+        const int nks = (P.n1 - lm8 + 15) >> 4;
+        const int nkb = (nks + 1) >> 1;
+        if (RES) {
+          if (!mbar_wait(&a_full, aph, kWaitNs)) { fail(9); ok = false; break; }
+          aph ^= 1;
+        }
+        for (int j = 0; j < item.z && ok; ++j) {
+          if (!mbar_wait(&tempty[acc], acc_ph ^ 1, kWaitNs)) { fail(12); ok = false; break; }
+          tc_fence_after();
+          const uint32_t t_re = tbase + acc * 256, t_im = t_re + 128;
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!mbar_wait(&full_bar[stage], phase, kWaitNs)) { fail(13); ok = false; break; }
+            tc_fence_after();
+            const uint32_t st = smem_u32(sStage + stage * stage_bytes);
+            const uint32_t sb = RES ? st : st + planes * 2 * kAPlane;
+            const uint32_t sa = RES ? smem_u32(sA) + kb * kAPlane : st;
+            const uint32_t a_stride = RES ? max_kb * kAPlane : kAPlane;
+            const int kss = min(2, nks - 2 * kb);
+            for (int ks = 0; ks < kss; ++ks) {
+              for (int q = 0; q < npair; ++q) {
+                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                const uint32_t ar_a = sa + pa * 2 * a_stride + ks * 32;
+                const uint64_t ar = smem_desc(ar_a, 16, 512, kSw64);
+                const uint64_t ai = smem_desc(ar_a + a_stride, 16, 512, kSw64);
+                const uint32_t br_a = sb + pb * 2 * NH * kBHalf + ks * 2048;
+                const uint64_t br = smem_desc(br_a, kBHalf, 1024, kSw128);
+                const uint64_t bi = smem_desc(br_a + NH * kBHalf, kBHalf, 1024, kSw128);
+                const uint32_t f = (kb | ks | q) ? 1u : 0u;
+                mma_f16(t_re, ar, br, id_pos, f);    // Wr Yr
+                mma_f16(t_re, ai, bi, id_neg, 1u);   // -Wi Yi
+                mma_f16(t_im, ar, bi, id_pos, f);    // Wr Yi
+                mma_f16(t_im, ai, br, id_pos, 1u);   // Wi Yr
+              }
+            }
+            mma_commit(&empty_bar[stage]);
+            if (++stage == S) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit(&tfull[acc]);
+          if (++acc == 2) { acc = 0; acc_ph ^= 1; }
+        }
+        if (!ok) break;
+        if (RES) mma_commit(&a_free);
+      }
+      mma_commit(&mma_done);
+      mbar_wait(&mma_done, 0, kWaitNs);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue + pooling
+    const int ew = warp - kEpiWarp0;          // 0..15
+    const int quarter = warp & 3;
+    const int cg = ew >> 2;                   // columns [32 cg, 32 cg + 32) of a tile
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const int g = lane >> 2, t4 = lane & 3;
+    // staging block: row = lane, two 16-byte chunks, chunk ^= (row >> 2) & 1
+    uint8_t* stg = sStg + ew * planes * kStg;
+    const uint32_t stg_u = smem_u32(stg);
+    uint8_t* my_row = stg + lane * 32;
+    const int my_sw = (lane >> 2) & 1;
+    // ldmatrix row addresses: A (16 x 16 block mt): row 16 mt + (lane & 15), chunk lane >> 4
+    uint32_t a_addr[2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r = 16 * mt + (lane & 15);
+      a_addr[mt] = stg_u + r * 32 + (((lane >> 4) ^ ((r >> 2) & 1)) << 4);
+    }
+    // B (w tile, [t][n] rows of 128 bytes, 128-byte swizzle): t = 8 (m >> 1) + (lane & 7),
+    // 8-sample chunk of the step + (m & 1), with m = lane >> 3
+    const int bt = 8 * (lane >> 4) + (lane & 7);
+    const int bk = (lane >> 3) & 1;
+    int acc = 0, ws = 0;
+    uint32_t acc_ph = 0, wph = 0, rf_ph = 0, rfree_ph = 0;
+    for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+      const int4 item = args.items[it % args.n_base];
+      const int a = item.x, b = it / args.n_base, m0 = item.y;
+      bool ok = !abort_flag;
+      float c[2][2][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) c[i][k][e] = 0.f;
+      for (int j = 0; j < item.z && ok; ++j) {
+        if (!mbar_wait(&tfull[acc], acc_ph, kWaitNs)) { fail(14); ok = false; break; }
+        tc_fence_after();
+        if (!mbar_wait(&wfull[ws], wph, kWaitNs)) { fail(19); ok = false; break; }
+        const uint32_t t_col = tbase + acc * 256 + lane_off + cg * 32;
+        const uint32_t w_u = smem_u32(sWt + (ws * NH + (cg >> 1)) * planes * kWHalf);
+#pragma unroll
+        for (int sub = 0; sub < 2; ++sub) {
+          float re[16], im[16];
+          tmem_ld16(t_col + sub * 16, re);
+          tmem_ld16(t_col + 128 + sub * 16, im);
+          tmem_wait_ld();
+          if (sub == 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+          }
+          uint32_t hv[8], lv[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float m0v = sqrt_approx(fmaf(re[2 * i], re[2 * i], im[2 * i] * im[2 * i]));
+            const float m1v =
+                sqrt_approx(fmaf(re[2 * i + 1], re[2 * i + 1], im[2 * i + 1] * im[2 * i + 1]));
+            __nv_bfloat162 h = __floats2bfloat162_rn(m0v, m1v);
+            const float2 hf = __bfloat1622float2(h);
+            __nv_bfloat162 l = __floats2bfloat162_rn(m0v - hf.x, m1v - hf.y);
+            hv[i] = *reinterpret_cast<uint32_t*>(&h);
+            lv[i] = *reinterpret_cast<uint32_t*>(&l);
+          }
+          __syncwarp();   // the previous step's fragment loads are done
+#pragma unroll
+          for (int ch = 0; ch < 2; ++ch) {
+            const int pos = (ch ^ my_sw) * 16;
+            *reinterpret_cast<uint4*>(my_row + pos) =
+                make_uint4(hv[4 * ch], hv[4 * ch + 1], hv[4 * ch + 2], hv[4 * ch + 3]);
+            if (planes == 2)
+              *reinterpret_cast<uint4*>(my_row + kStg + pos) =
+                  make_uint4(lv[4 * ch], lv[4 * ch + 1], lv[4 * ch + 2], lv[4 * ch + 3]);
+          }
+          __syncwarp();
+          // B fragments: w[t][n] for n in this step's 16 columns of the 64-column half
+          const int chunk = (((cg & 1) * 32 + sub * 16) >> 3) + bk;
+          const uint32_t b_off = bt * 128 + ((chunk ^ (bt & 7)) << 4);
+          uint32_t bh[4], ah[2][4];
+          ldsm_x4(w_u + b_off, bh);
+          ldsm_x4(a_addr[0], ah[0]);
+          ldsm_x4(a_addr[1], ah[1]);
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            hmma16816(c[mt][0], ah[mt], bh[0], bh[1]);
+            hmma16816(c[mt][1], ah[mt], bh[2], bh[3]);
+          }
+          if (planes == 2) {
+            uint32_t bl[4], al[2][4];
+            ldsm_x4(w_u + kWHalf + b_off, bl);
+            ldsm_x4(a_addr[0] + kStg, al[0]);
+            ldsm_x4(a_addr[1] + kStg, al[1]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+              hmma16816(c[mt][0], ah[mt], bl[0], bl[1]);   // hi . lo
+              hmma16816(c[mt][1], ah[mt], bl[2], bl[3]);
+              hmma16816(c[mt][0], al[mt], bh[0], bh[1]);   // lo . hi
+              hmma16816(c[mt][1], al[mt], bh[2], bh[3]);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&wempty[ws]);
+        if (++ws == WS) { ws = 0; wph ^= 1; }
+        if (++acc == 2) { acc = 0; acc_ph ^= 1; }
+      }
+      if (!ok) break;
+      // sum the four column groups of this lane quarter in a fixed order
+      if (cg != 0) {
+        if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, kWaitNs)) { fail(21); break; }
+        rfree_ph ^= 1;
+      }
+      float* red = sRed + (cg * 128 + quarter * 32) * NT;
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int r = 16 * mt + g, t = 8 * nt + 2 * t4;
+          *reinterpret_cast<float2*>(red + r * NT + t) = make_float2(c[mt][nt][0], c[mt][nt][1]);
+          *reinterpret_cast<float2*>(red + (r + 8) * NT + t) = make_float2(c[mt][nt][2], c[mt][nt][3]);
+        }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&red_full[quarter]);
+      if (cg == 0) {
+        if (!mbar_wait(&red_full[quarter], rf_ph, kWaitNs)) { fail(20); break; }
+        rf_ph ^= 1;
+        const int r = m0 + quarter * 32 + lane;
+        float s[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) s[t] = 0.f;
+#pragma unroll
+        for (int gq = 0; gq < 4; ++gq) {
+          const float* src = sRed + (gq * 128 + quarter * 32 + lane) * NT;
+#pragma unroll
+          for (int t = 0; t < NT; t += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(src + t);
+            s[t] += v.x; s[t + 1] += v.y; s[t + 2] += v.z; s[t + 3] += v.w;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&red_free[quarter]);
+        if (r < args.n_rows) {
+          float* out = args.P + (((size_t)b * args.n2 + a) * args.n_rows + r) * args.nt;
+          if (args.nt == NT) {
+#pragma unroll
+            for (int t = 0; t < NT; t += 4)
+              *reinterpret_cast<float4*>(out + t) = make_float4(s[t], s[t + 1], s[t + 2], s[t + 3]);
+          } else {
+#pragma unroll
+            for (int t = 0; t < NT; ++t)
+              if (t < args.nt) out[t] = s[t];
+          }
+        }
+      }
     }
   }
   __syncthreads();
@@ -533,6 +912,39 @@ size_t tc_smem_for(const jtfs_plan* p, bool res) {
   const TcShape s = tc_shape(p);
   return s.fixed(res, tc_res_kb(p)) + (size_t)tc_stages_for(p, res) * s.stage(res);
 }
+
+// 16-frame form: resident W tile, operand stages, the weight ring, sixteen 1 KB |Z| staging
+// blocks per plane and the 32 KB column-group reduction buffer
+struct Tc16Shape {
+  int planes, WS;
+  size_t fixed(bool res, int res_kb) const {
+    return 1024 + (res ? (size_t)planes * 2 * res_kb * kBM * kBK * 2 : 0) +
+           (size_t)WS * 2 * planes * 16 * 64 * 2 + (size_t)kEpiWarps * planes * 1024 +
+           4 * 128 * 16 * 4;
+  }
+  size_t stage(bool res) const {
+    return (res ? 0 : (size_t)planes * 2 * kBM * kBK * 2) + (size_t)planes * 2 * 2 * kBK * 64 * 2;
+  }
+};
+
+Tc16Shape tc16_shape(const jtfs_plan* p) {
+  Tc16Shape s;
+  s.planes = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
+  s.WS = kMaxWS;
+  return s;
+}
+
+int tc16_stages_for(const jtfs_plan* p, bool res) {
+  const Tc16Shape s = tc16_shape(p);
+  const size_t fixed = s.fixed(res, tc_res_kb(p)), stage = s.stage(res);
+  if (fixed + 2 * stage > kSmemBudget) return 0;
+  return (int)std::min<size_t>(8, (kSmemBudget - fixed) / stage);
+}
+
+size_t tc16_smem_for(const jtfs_plan* p, bool res) {
+  const Tc16Shape s = tc16_shape(p);
+  return s.fixed(res, tc_res_kb(p)) + (size_t)tc16_stages_for(p, res) * s.stage(res);
+}
 }  // namespace
 
 jtfs_status build_tc_tables(jtfs_plan* p) {
@@ -647,8 +1059,9 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     }
   }
   const int n_all = (int)(p->tc_items.size() / 4);
-  const int n_res = tc_stages_for(p, true) >= 2 ? p->tc_n_res : 0;
-  if (n_all > n_res && tc_stages_for(p, false) < 2) {
+  const bool f16 = NT == 16;
+  const int n_res = (f16 ? tc16_stages_for(p, true) : tc_stages_for(p, true)) >= 2 ? p->tc_n_res : 0;
+  if (n_all > n_res && (f16 ? tc16_stages_for(p, false) : tc_stages_for(p, false)) < 2) {
     set_error("tensor-core forward: no shared-memory layout for this configuration");
     return JTFS_ERR_UNSUPPORTED;
   }
@@ -656,7 +1069,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   args.B = B;
   args.passes = passes;
   args.res_kb = tc_res_kb(p);
-  args.wstages = tc_shape(p).WS;
+  args.wstages = f16 ? tc16_shape(p).WS : tc_shape(p).WS;
   args.n_rows = rows;
   args.nt = p->n_t;
   args.P = Pbuf;
@@ -673,17 +1086,26 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       return rc;                                                                                \
     k_joint_fwd_tc<NTV, BNV, RESV><<<grid, kThreads, smem, st>>>(maps, args, d);               \
   } while (0)
+#define JTFS_LAUNCH_TC16(RESV)                                                                  \
+  do {                                                                                          \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_tc16<RESV>,                         \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                              (int)smem), "attr tc16")) != JTFS_OK)             \
+      return rc;                                                                                \
+    k_joint_fwd_tc16<RESV><<<grid, kThreads, smem, st>>>(maps, args, d);                       \
+  } while (0)
   for (int pass = 0; pass < 2; ++pass) {
     const bool res = pass == 0;
     const int first = res ? 0 : n_res, count = res ? n_res : n_all - n_res;
     if (count <= 0) continue;
     args.items = reinterpret_cast<const int4*>(p->d_tc_items) + first;
+    args.n_base = count;
     args.n_items = count * B;
-    args.stages = tc_stages_for(p, res);
-    const size_t smem = tc_smem_for(p, res);
+    args.stages = f16 ? tc16_stages_for(p, res) : tc_stages_for(p, res);
+    const size_t smem = f16 ? tc16_smem_for(p, res) : tc_smem_for(p, res);
     const int grid = std::min(args.n_items, n_sm);
-    if (BN == 128) {
-      if (res) JTFS_LAUNCH_TC(16, 128, true); else JTFS_LAUNCH_TC(16, 128, false);
+    if (f16) {
+      if (res) JTFS_LAUNCH_TC16(true); else JTFS_LAUNCH_TC16(false);
     } else if (NT == 32) {
       if (res) JTFS_LAUNCH_TC(32, 64, true); else JTFS_LAUNCH_TC(32, 64, false);
     } else {
@@ -692,6 +1114,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     if ((rc = cuda_check(cudaGetLastError(), "k_joint_fwd_tc")) != JTFS_OK) return rc;
   }
 #undef JTFS_LAUNCH_TC
+#undef JTFS_LAUNCH_TC16
   k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
   return cuda_check(cudaGetLastError(), "k_pool_lambda");
 }
