@@ -115,3 +115,94 @@ __device__ void fft_dif(float2* buf, int logL, const float2* __restrict__ tw, in
 }
 
 }  // namespace jtfs
+
+namespace jtfs {
+
+// Batched forms: G independent rows of length L = 2^logL stored back to back in buf, every
+// thread of the block working on butterflies of all rows.  Same decimation as above.
+template <int SIGN>
+__device__ void fft_dit_rows(float2* buf, int logL, int G, const float2* __restrict__ tw,
+                             int logTW) {
+  const int L = 1 << logL;
+  int s = 1;
+  if (logL & 1) {
+    const int per = L >> 1;
+    for (int b = threadIdx.x; b < G * per; b += blockDim.x) {
+      const int i0 = (b / per) * L + ((b % per) << 1);
+      const float2 a = buf[i0], c = buf[i0 + 1];
+      buf[i0] = make_float2(a.x + c.x, a.y + c.y);
+      buf[i0 + 1] = make_float2(a.x - c.x, a.y - c.y);
+    }
+    __syncthreads();
+    s = 2;
+  }
+  const int per = L >> 2;
+  for (; s + 1 <= logL; s += 2) {
+    const int q = 1 << (s - 1);
+    const int sh1 = logTW - s;
+    const int sh2 = logTW - s - 1;
+    for (int bb = threadIdx.x; bb < G * per; bb += blockDim.x) {
+      const int row = bb / per, b = bb % per;
+      const int j = b & (q - 1);
+      const int base = row * L + (((b >> (s - 1)) << (s + 1)) | j);
+      float2 x0 = buf[base], x1 = buf[base + q], x2 = buf[base + 2 * q], x3 = buf[base + 3 * q];
+      const float2 w1 = twiddle<SIGN>(tw, j << sh1);
+      float2 t = cmul(x1, w1);
+      float2 a0 = make_float2(x0.x + t.x, x0.y + t.y), a1 = make_float2(x0.x - t.x, x0.y - t.y);
+      t = cmul(x3, w1);
+      float2 a2 = make_float2(x2.x + t.x, x2.y + t.y), a3 = make_float2(x2.x - t.x, x2.y - t.y);
+      const float2 w2 = twiddle<SIGN>(tw, j << sh2);
+      const float2 w3 = twiddle<SIGN>(tw, (j + q) << sh2);
+      t = cmul(a2, w2);
+      buf[base] = make_float2(a0.x + t.x, a0.y + t.y);
+      buf[base + 2 * q] = make_float2(a0.x - t.x, a0.y - t.y);
+      t = cmul(a3, w3);
+      buf[base + q] = make_float2(a1.x + t.x, a1.y + t.y);
+      buf[base + 3 * q] = make_float2(a1.x - t.x, a1.y - t.y);
+    }
+    __syncthreads();
+  }
+}
+
+template <int SIGN>
+__device__ void fft_dif_rows(float2* buf, int logL, int G, const float2* __restrict__ tw,
+                             int logTW) {
+  const int L = 1 << logL;
+  int s = logL;
+  const int per = L >> 2;
+  for (; s - 1 >= 1; s -= 2) {
+    const int q = 1 << (s - 2);
+    const int sh1 = logTW - s;
+    const int sh2 = logTW - s + 1;
+    for (int bb = threadIdx.x; bb < G * per; bb += blockDim.x) {
+      const int row = bb / per, b = bb % per;
+      const int j = b & (q - 1);
+      const int base = row * L + (((b >> (s - 2)) << s) | j);
+      float2 x0 = buf[base], x1 = buf[base + q], x2 = buf[base + 2 * q], x3 = buf[base + 3 * q];
+      const float2 w1 = twiddle<SIGN>(tw, j << sh1);
+      const float2 w1b = twiddle<SIGN>(tw, (j + q) << sh1);
+      float2 a0 = make_float2(x0.x + x2.x, x0.y + x2.y);
+      float2 a2 = cmul(make_float2(x0.x - x2.x, x0.y - x2.y), w1);
+      float2 a1 = make_float2(x1.x + x3.x, x1.y + x3.y);
+      float2 a3 = cmul(make_float2(x1.x - x3.x, x1.y - x3.y), w1b);
+      const float2 w2 = twiddle<SIGN>(tw, j << sh2);
+      buf[base] = make_float2(a0.x + a1.x, a0.y + a1.y);
+      buf[base + q] = cmul(make_float2(a0.x - a1.x, a0.y - a1.y), w2);
+      buf[base + 2 * q] = make_float2(a2.x + a3.x, a2.y + a3.y);
+      buf[base + 3 * q] = cmul(make_float2(a2.x - a3.x, a2.y - a3.y), w2);
+    }
+    __syncthreads();
+  }
+  if (s == 1) {
+    const int per2 = L >> 1;
+    for (int b = threadIdx.x; b < G * per2; b += blockDim.x) {
+      const int i0 = (b / per2) * L + ((b % per2) << 1);
+      const float2 a = buf[i0], c = buf[i0 + 1];
+      buf[i0] = make_float2(a.x + c.x, a.y + c.y);
+      buf[i0 + 1] = make_float2(a.x - c.x, a.y - c.y);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace jtfs

@@ -93,7 +93,7 @@ struct jtfs_plan {
   // tensor-core contraction (precisions FP32 / BF16)
   bool use_tc;
   int n1_pad;                  // lambda' columns of the W planes (multiple of 32)
-  void* d_wplanes[4];          // Wr_hi, Wi_hi, Wr_lo, Wi_lo: [C * n1][n1_pad] bf16
+  void* d_wplanes[6];          // Wr_hi, Wi_hi, Wr_lo, Wi_lo, -Wi_hi, -Wi_lo: [C * n1][n1_pad] bf16
   void* d_wtf;                 // pooling weights hi / lo: [n2 * NT][tc_wt_cols] bf16
   int tc_wt_cols;
   std::vector<int> tc_items;   // (alpha, m0, n_tiles, 0) per signal; resident-W items first
@@ -105,6 +105,8 @@ struct jtfs_plan {
   bool use_tcb;
   std::vector<int> tcb_items;  // (alpha, n0, lambda' start, K1) per signal; K1 <= 96 first
   int tcb_n_res;               // items with K1 <= 96
+  std::vector<int> tcbf_items; // (alpha, n0, lam_min & ~7, K1 <= 64): the fast backward form
+  int* d_tcbf_items;
   int* d_tcb_items;
   void* d_wtb;                 // [rows][NT] bf16 pooling weights (time-major)
   int* d_wtb_row0;             // [n2]

@@ -807,9 +807,10 @@ __global__ void k_pool_lambda(DevPlan Pd, const float* __restrict__ P, float* __
 }  // namespace
 
 // W planes: W[c * n1 + lambda][lambda'] = h_c[(lambda - lambda') mod N_fr] for lambda' < n1, else 0;
-// hi = bf16(v), lo = bf16(v - hi), separately for Re and Im.
+// hi = bf16(v), lo = bf16(v - hi), separately for Re and Im, and the negated Im planes.
 __global__ void k_build_wplanes(DevPlan Pd, int n1_pad, __nv_bfloat16* wr_hi, __nv_bfloat16* wi_hi,
-                                __nv_bfloat16* wr_lo, __nv_bfloat16* wi_lo) {
+                                __nv_bfloat16* wr_lo, __nv_bfloat16* wi_lo, __nv_bfloat16* nwi_hi,
+                                __nv_bfloat16* nwi_lo) {
   const int rows = Pd.C * Pd.n1;
   const long long total = (long long)rows * n1_pad;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -821,8 +822,11 @@ __global__ void k_build_wplanes(DevPlan Pd, int n1_pad, __nv_bfloat16* wr_hi, __
     const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
     wr_hi[i] = hr;
     wi_hi[i] = hi;
+    const __nv_bfloat16 wl = __float2bfloat16_rn(v.y - __bfloat162float(hi));
     wr_lo[i] = __float2bfloat16_rn(v.x - __bfloat162float(hr));
-    wi_lo[i] = __float2bfloat16_rn(v.y - __bfloat162float(hi));
+    wi_lo[i] = wl;
+    nwi_hi[i] = __hneg(hi);
+    nwi_lo[i] = __hneg(wl);
   }
 }
 
@@ -983,8 +987,8 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   }
   size_t off = 0;
   auto place = [&](size_t bytes) { size_t at = off; off += (bytes + 1023) & ~(size_t)1023; return at; };
-  size_t o_w[4];
-  for (int i = 0; i < 4; ++i) o_w[i] = place(wplane * 2);
+  size_t o_w[6];
+  for (int i = 0; i < 6; ++i) o_w[i] = place(wplane * 2);
   const size_t wt_elems = (size_t)p->n2 * NT * Lmax;
   const size_t o_wt = place(wt_elems * 2 * 2);
   const size_t o_items = place(std::max<size_t>(16, p->tc_items.size() * 4));
@@ -992,7 +996,7 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   jtfs_status st;
   if ((st = cuda_check(cudaMalloc(&p->d_tc_mem, off), "tc tables")) != JTFS_OK) return st;
   char* base = (char*)p->d_tc_mem;
-  for (int i = 0; i < 4; ++i) p->d_wplanes[i] = base + o_w[i];
+  for (int i = 0; i < 6; ++i) p->d_wplanes[i] = base + o_w[i];
   p->d_wtf = base + o_wt;
   p->d_tc_items = (int*)(base + o_items);
   p->d_err = (int*)(base + o_err);
@@ -1002,7 +1006,8 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   if ((st = cuda_check(cudaMemset(p->d_err, 0, 16), "memset")) != JTFS_OK) return st;
   k_build_wplanes<<<1024, 256>>>(p->dp, p->n1_pad, (__nv_bfloat16*)p->d_wplanes[0],
                                  (__nv_bfloat16*)p->d_wplanes[1], (__nv_bfloat16*)p->d_wplanes[2],
-                                 (__nv_bfloat16*)p->d_wplanes[3]);
+                                 (__nv_bfloat16*)p->d_wplanes[3], (__nv_bfloat16*)p->d_wplanes[4],
+                                 (__nv_bfloat16*)p->d_wplanes[5]);
   k_build_wt<<<1024, 256>>>(p->dp, NT, Lmax, (__nv_bfloat16*)p->d_wtf,
                             (__nv_bfloat16*)p->d_wtf + wt_elems);
   return cuda_check(cudaDeviceSynchronize(), "build tc tables");

@@ -682,6 +682,358 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
   }
 }
 
+// ------------------------------------------------------------------ fast form (K1 <= 64)
+// For rates whose lambda' range (from lam_min rounded down to 8) spans at most 64 rows.
+// The complex products are stacked so every MMA is 128 wide:
+//   Z^T [Re | Im]   = Yr [Wr ; Wi]^T + Yi [-Wi ; Wr]^T          (N = 2 RC rows of the chunk)
+//   gY^T [Im | Re] += gZi [Wr | Wi] + gZr [-Wi | Wr]            (N = 2 x 64 lambda')
+// from one W chunk held as three blocks [-Wi][Wr][Wi] (each RC rows x 64 lambda', 128-byte
+// swizzle), read K-major by the first product and MN-major by the second.  The Z^T / g|Z|^T
+// accumulators are double-buffered in TMEM so the next chunk's product overlaps the epilogue;
+// sixteen epilogue warps (four per lane quarter, RC / 4 rows each) form gZ.
+struct TfMaps {
+  CUtensorMap w[6];      // Wr_hi, Wi_hi, Wr_lo, Wi_lo, -Wi_hi, -Wi_lo; box {64 lambda', RC r}
+  CUtensorMap y[2][16];  // [hi/lo][alpha]: Y planes [2B][K][L], box {64 n, 32 lambda', 1}
+  CUtensorMap g1[2];     // hi, lo: [rows][NT] bf16, box {NT, RC}
+  CUtensorMap wt[2];     // hi, lo: [rows][NT] bf16, box {NT, 128}
+};
+
+struct TfArgs {
+  const int4* items;    // (alpha, n0, lambda' start = lam_min & ~7, K1 <= 64) per base
+  int n_base;           // item it = base it % n_base of signal it / n_base
+  int n_items;
+  int n_chunks;         // ceil(C n1 / RC)
+  int g1_rows;          // rows per (b, alpha) block of G1
+  int wbufs;            // W chunk ring depth (2..3)
+  int a2bufs;           // gZ staging buffers (1..2)
+  const int* wt_row0;
+  float2* gy;
+  int* err;
+};
+
+constexpr int kFThreads = 32 * 18;   // warp 0 TMA, warp 1 MMA, warps 2..17 epilogue
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+template <int CW>
+__device__ __forceinline__ void tmem_ldc(uint32_t taddr, float (&v)[CW]) {
+  if constexpr (CW == 16) tmem_ld16(taddr, v); else tmem_ld8(taddr, v);
+}
+
+template <int NT, int RC, int PL>
+__global__ void __launch_bounds__(kFThreads, 1)
+k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int CW = RC / 4;                              // chunk rows per epilogue warp
+  constexpr uint32_t kSw = NT * 2;
+  constexpr uint32_t kLayNT = kSw == 128 ? kSw128 : (kSw == 64 ? kSw64 : kSw32);
+  constexpr uint32_t kA1Plane = 2 * 64 * 128;             // two 64-sample halves x 64 lambda'
+  constexpr uint32_t kA4Plane = ((128 * NT * 2 + 1023) / 1024) * 1024;
+  constexpr uint32_t kWBlk = RC * 128;                    // RC rows x 64 lambda'
+  constexpr uint32_t kG1Plane = ((RC * NT * 2 + 1023) / 1024) * 1024;
+  constexpr uint32_t kWBuf = PL * 3 * kWBlk + PL * kG1Plane;
+  constexpr uint32_t kA2Part = 128 * RC * 2;              // [128 n][RC r] bf16
+  constexpr uint32_t kA2Buf = PL * 2 * kA2Part;
+  constexpr uint32_t kA2Lay = RC == 64 ? kSw128 : kSw64;
+  constexpr uint32_t kA2Sbo = RC == 64 ? 1024 : 512;
+  const int WB = args.wbufs, NA2 = args.a2bufs;
+  uint8_t* sA1 = sm;                                       // PL x 2 parts
+  uint8_t* sA4 = sA1 + PL * 2 * kA1Plane;                  // PL planes
+  uint8_t* sW = sA4 + PL * kA4Plane;                       // WB buffers (W blocks, then G1)
+  uint8_t* sA2 = sW + WB * kWBuf;                          // NA2 buffers
+
+  __shared__ uint64_t a1_full, a1_free, w_full[3], w_empty[3], d1_full[2], d1_free[2],
+      a2_full[2], a2_free[2], d2_full, d2_free, mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(&a1_full, 1);
+    mbar_init(&a1_free, 1);
+    for (int i = 0; i < 3; ++i) {
+      mbar_init(&w_full[i], 1);
+      mbar_init(&w_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&d1_full[i], 1);
+      mbar_init(&d1_free[i], 16);
+      mbar_init(&a2_full[i], 16);
+      mbar_init(&a2_free[i], 1);
+    }
+    mbar_init(&d2_full, 1);
+    mbar_init(&d2_free, 16);
+    mbar_init(&mma_done, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t t_d2 = tbase + 6 * RC;                    // [Im 64 | Re 64]
+  auto fail = [&](int code) {
+    if (!abort_flag) {
+      abort_flag = 1;
+      atomicCAS(args.err, 0, code);
+    }
+  };
+  const int npair = PL == 2 ? 3 : 1;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t a1_ph = 0, wph = 0;
+      int wst = 0;
+      uint32_t armed_w = 0, armed_w_par = 0;
+      int armed_a1 = -1;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        const int a = item.x, b = it / args.n_base, n0 = item.y, start = item.z, K1 = item.w;
+        const Rate2 A = P.rates2[a];
+        const int nkb1 = (K1 + 31) / 32;
+        if (!mbar_wait(&a1_free, a1_ph ^ 1, kWaitNs)) { fail(61); break; }
+        mbar_arrive_expect_tx(&a1_full, PL * 2 * 2 * nkb1 * 4096 + PL * 128 * NT * 2);
+        armed_a1 = (int)a1_ph;
+        for (int pl = 0; pl < PL; ++pl) {
+          for (int part = 0; part < 2; ++part)
+            for (int h = 0; h < 2; ++h)
+              for (int kb = 0; kb < nkb1; ++kb)
+                tma_load_3d(sA1 + (pl * 2 + part) * kA1Plane + h * 64 * 128 + kb * 32 * 128,
+                            &maps.y[pl][a], n0 + h * 64, start - A.lam_min + kb * 32,
+                            2 * b + part, &a1_full);
+          tma_load_2d(sA4 + pl * kA4Plane, &maps.wt[pl], 0, args.wt_row0[a] + n0, &a1_full);
+        }
+        a1_ph ^= 1;
+        const int g1row = (b * P.n2 + a) * args.g1_rows;
+        for (int j = 0; j < args.n_chunks; ++j) {
+          if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(62); ok = false; break; }
+          mbar_arrive_expect_tx(&w_full[wst], PL * 3 * RC * 64 * 2 + PL * RC * NT * 2);
+          armed_w |= 1u << wst;
+          armed_w_par = (armed_w_par & ~(1u << wst)) | (wph << wst);
+          uint8_t* wb = sW + wst * kWBuf;
+          for (int pl = 0; pl < PL; ++pl) {
+            tma_load_2d(wb + (pl * 3 + 0) * kWBlk, &maps.w[4 + pl], start, j * RC, &w_full[wst]);
+            tma_load_2d(wb + (pl * 3 + 1) * kWBlk, &maps.w[pl * 2], start, j * RC, &w_full[wst]);
+            tma_load_2d(wb + (pl * 3 + 2) * kWBlk, &maps.w[pl * 2 + 1], start, j * RC, &w_full[wst]);
+            tma_load_2d(wb + PL * 3 * kWBlk + pl * kG1Plane, &maps.g1[pl], 0, g1row + j * RC,
+                        &w_full[wst]);
+          }
+          if (++wst == WB) { wst = 0; wph ^= 1; }
+        }
+      }
+      for (int i = 0; i < WB; ++i)
+        if (armed_w >> i & 1) mbar_wait(&w_full[i], armed_w_par >> i & 1, kWaitNs);
+      if (armed_a1 >= 0) mbar_wait(&a1_full, (uint32_t)armed_a1, kWaitNs);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id1 = instr_desc(128, 2 * RC, 1, 1, 1, 0, 0);
+      const uint32_t id4 = instr_desc(128, RC, 1, 1, 0, 0, 0);
+      const uint32_t id2 = instr_desc(128, 128, 1, 1, 0, 1, 0);
+      uint32_t a1_ph = 0, d2f_ph = 0, wph = 0;
+      uint32_t d1f_ph = 0, a2_ph = 0;   // bit i: phase of buffer i
+      int wst = 0, buf = 0, q2 = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        const int nks1 = item.w / 16;
+        if (!mbar_wait(&a1_full, a1_ph, kWaitNs)) { fail(63); break; }
+        a1_ph ^= 1;
+        const uint32_t a1 = smem_u32(sA1), a4 = smem_u32(sA4);
+        int prev_wst = 0, prev_q2 = 0;
+        bool first_d2 = true;
+        for (int j = 0; j <= args.n_chunks && ok; ++j) {
+          if (j < args.n_chunks) {
+            if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(64); ok = false; break; }
+            if (!mbar_wait(&d1_free[buf], ((d1f_ph >> buf) & 1) ^ 1, kWaitNs)) { fail(65); ok = false; break; }
+            d1f_ph ^= 1u << buf;
+            tc_fence_after();
+            const uint32_t wb = smem_u32(sW + wst * kWBuf);
+            const uint32_t t_d1 = tbase + buf * 3 * RC, t_d4 = t_d1 + 2 * RC;
+            for (int ks = 0; ks < nks1; ++ks) {
+              for (int q = 0; q < npair; ++q) {
+                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                const uint64_t ayr = smem_desc(a1 + (pa * 2 + 0) * kA1Plane + ks * 2048, 64 * 128, 1024, kSw128);
+                const uint64_t ayi = smem_desc(a1 + (pa * 2 + 1) * kA1Plane + ks * 2048, 64 * 128, 1024, kSw128);
+                const uint32_t wpl = wb + pb * 3 * kWBlk + ks * 32;
+                const uint32_t f = (ks | q) ? 1u : 0u;
+                mma_f16(t_d1, ayr, smem_desc(wpl + kWBlk, 16, 1024, kSw128), id1, f);   // Yr [Wr; Wi]
+                mma_f16(t_d1, ayi, smem_desc(wpl, 16, 1024, kSw128), id1, 1u);          // Yi [-Wi; Wr]
+              }
+            }
+            const uint32_t g1 = wb + PL * 3 * kWBlk;
+            for (int ks = 0; ks < NT / 16; ++ks)
+              for (int q = 0; q < npair; ++q) {
+                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                mma_f16(t_d4, smem_desc(a4 + pa * kA4Plane + ks * 32, 16, 8 * kSw, kLayNT),
+                        smem_desc(g1 + pb * kG1Plane + ks * 32, 16, 8 * kSw, kLayNT), id4,
+                        (ks | q) ? 1u : 0u);
+              }
+            mma_commit(&d1_full[buf]);
+          }
+          if (j >= 1) {
+            // gY^T [Im | Re] += gZi [Wr | Wi] + gZr [-Wi | Wr] for chunk j - 1
+            if (!mbar_wait(&a2_full[prev_q2], (a2_ph >> prev_q2) & 1, kWaitNs)) { fail(66); ok = false; break; }
+            a2_ph ^= 1u << prev_q2;
+            if (first_d2) {
+              if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(67); ok = false; break; }
+              d2f_ph ^= 1;
+            }
+            tc_fence_after();
+            const uint32_t wb = smem_u32(sW + prev_wst * kWBuf);
+            const uint32_t a2 = smem_u32(sA2 + prev_q2 * kA2Buf);
+            for (int ks = 0; ks < RC / 16; ++ks) {
+              for (int q = 0; q < npair; ++q) {
+                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                const uint64_t agr = smem_desc(a2 + (pa * 2 + 0) * kA2Part + ks * 32, 16, kA2Sbo, kA2Lay);
+                const uint64_t agi = smem_desc(a2 + (pa * 2 + 1) * kA2Part + ks * 32, 16, kA2Sbo, kA2Lay);
+                const uint32_t wpl = wb + pb * 3 * kWBlk + ks * 2048;
+                const uint32_t f = (first_d2 && ks == 0 && q == 0) ? 0u : 1u;
+                mma_f16(t_d2, agi, smem_desc(wpl + kWBlk, kWBlk, 1024, kSw128), id2, f);   // gZi [Wr | Wi]
+                mma_f16(t_d2, agr, smem_desc(wpl, kWBlk, 1024, kSw128), id2, 1u);          // gZr [-Wi | Wr]
+              }
+            }
+            first_d2 = false;
+            mma_commit(&a2_free[prev_q2]);
+            mma_commit(&w_empty[prev_wst]);
+          }
+          if (j < args.n_chunks) {
+            prev_wst = wst;
+            prev_q2 = q2;
+            if (++wst == WB) { wst = 0; wph ^= 1; }
+            buf ^= 1;
+            if (++q2 == NA2) q2 = 0;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&a1_free);
+        mma_commit(&d2_full);
+      }
+      mma_commit(&mma_done);
+      mbar_wait(&mma_done, 0, kWaitNs);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - 2;                   // 0..15
+    const int quarter = warp & 3;
+    const int cg = ew >> 2;                    // chunk rows [cg CW, cg CW + CW)
+    const int row = quarter * 32 + lane;       // time sample within the tile
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    uint32_t d2_ph = 0;
+    uint32_t d1_ph = 0, a2f_ph = 0;   // bit i: phase of buffer i
+    int buf = 0, q2 = 0;
+    for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+      const int4 item = args.items[it % args.n_base];
+      const int a = item.x, b = it / args.n_base, n0 = item.y, start = item.z;
+      bool ok = !abort_flag;
+      for (int j = 0; j < args.n_chunks && ok; ++j) {
+        if (!mbar_wait(&d1_full[buf], (d1_ph >> buf) & 1, kWaitNs)) { fail(68); ok = false; break; }
+        d1_ph ^= 1u << buf;
+        tc_fence_after();
+        float zr[CW], zi[CW], g[CW];
+        const uint32_t t_d1 = tbase + buf * 3 * RC + lane_off + cg * CW;
+        tmem_ldc<CW>(t_d1, zr);
+        tmem_ldc<CW>(t_d1 + RC, zi);
+        tmem_ldc<CW>(t_d1 + 2 * RC, g);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&d1_free[buf]);
+        uint32_t hr[CW / 2], hi[CW / 2], lr[CW / 2], li[CW / 2];
+#pragma unroll
+        for (int i = 0; i < CW / 2; ++i) {
+          float vr[2], vi[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int k = 2 * i + e;
+            const float m2 = fmaf(zr[k], zr[k], zi[k] * zi[k]);
+            const float f = m2 > 0.f ? g[k] * rsqrt_approx(m2) : 0.f;
+            vr[e] = zr[k] * f;
+            vi[e] = zi[k] * f;
+          }
+          __nv_bfloat162 a0 = __floats2bfloat162_rn(vr[0], vr[1]);
+          __nv_bfloat162 a1v = __floats2bfloat162_rn(vi[0], vi[1]);
+          hr[i] = *reinterpret_cast<uint32_t*>(&a0);
+          hi[i] = *reinterpret_cast<uint32_t*>(&a1v);
+          if (PL == 2) {
+            const float2 fa0 = __bfloat1622float2(a0), fa1 = __bfloat1622float2(a1v);
+            __nv_bfloat162 b0 = __floats2bfloat162_rn(vr[0] - fa0.x, vr[1] - fa0.y);
+            __nv_bfloat162 b1 = __floats2bfloat162_rn(vi[0] - fa1.x, vi[1] - fa1.y);
+            lr[i] = *reinterpret_cast<uint32_t*>(&b0);
+            li[i] = *reinterpret_cast<uint32_t*>(&b1);
+          }
+        }
+        if (!mbar_wait(&a2_free[q2], ((a2f_ph >> q2) & 1) ^ 1, kWaitNs)) { fail(69); ok = false; break; }
+        a2f_ph ^= 1u << q2;
+        uint8_t* base = sA2 + q2 * kA2Buf + row * (RC * 2);
+#pragma unroll
+        for (int c = 0; c < CW / 8; ++c) {
+          const int ch = cg * (CW / 8) + c;
+          const int pos = (RC == 64 ? (ch ^ (row & 7)) : (ch ^ ((row >> 1) & 3))) * 16;
+          *reinterpret_cast<uint4*>(base + 0 * kA2Part + pos) = make_uint4(hr[4 * c], hr[4 * c + 1], hr[4 * c + 2], hr[4 * c + 3]);
+          *reinterpret_cast<uint4*>(base + 1 * kA2Part + pos) = make_uint4(hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
+          if (PL == 2) {
+            *reinterpret_cast<uint4*>(base + 2 * kA2Part + pos) = make_uint4(lr[4 * c], lr[4 * c + 1], lr[4 * c + 2], lr[4 * c + 3]);
+            *reinterpret_cast<uint4*>(base + 3 * kA2Part + pos) = make_uint4(li[4 * c], li[4 * c + 1], li[4 * c + 2], li[4 * c + 3]);
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a2_full[q2]);
+        buf ^= 1;
+        if (++q2 == NA2) q2 = 0;
+      }
+      if (!ok) break;
+      // gY^T of this tile: lambda' = start + c for c in [16 cg, 16 cg + 16)
+      if (!mbar_wait(&d2_full, d2_ph, kWaitNs)) { fail(70); break; }
+      d2_ph ^= 1;
+      tc_fence_after();
+      const Rate2 A = P.rates2[a];
+      const int n = n0 + row;
+      float2* go = args.gy + (size_t)b * P.y_len + A.off_y;
+      float vi[16], vr[16];
+      tmem_ld16(t_d2 + lane_off + cg * 16, vi);
+      tmem_ld16(t_d2 + lane_off + 64 + cg * 16, vr);
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d2_free);
+      if (n < A.L) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int lp = start + cg * 16 + i;
+          if (lp >= A.lam_min && lp < P.n1)
+            go[(size_t)(lp - A.lam_min) * A.L + n] = make_float2(vr[i], vi[i]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
 // G1[(b n2 + a) g1_rows + c n1 + lambda][t] = sum_lo phi_F[(lo s_F - lambda) mod N_fr] gS2[b,a,c,lo,t]
 // (or gS2 itself for Eq. 4), as BF16, zero for t >= n_t and in the row padding.
 __global__ void k_g1(DevPlan Pd, const float* __restrict__ gs2, int NT, int g1_rows,
@@ -755,13 +1107,23 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
     rows += (L + 127) / 128 * 128;
   }
   struct It { int a, n0, start, K1; long long cost; };
-  std::vector<It> its;
+  std::vector<It> its, fast;
   for (int a = 0; a < p->n2; ++a) {
     const Rate2& A = p->rates2[a];
     if (A.s == 0) continue;
+    const int lm8 = A.lam_min & ~7;
+    const int K1f = (p->n1 - lm8 + 15) / 16 * 16;
     const int start = A.lam_min / 64 * 64;
     const int K1 = (p->n1 - start + 31) / 32 * 32;
-    for (int n0 = 0; n0 < A.L; n0 += 128) its.push_back({a, n0, start, K1, (long long)K1});
+    for (int n0 = 0; n0 < A.L; n0 += 128) {
+      if (K1f <= 64) fast.push_back({a, n0, lm8, K1f, (long long)K1f});
+      else its.push_back({a, n0, start, K1, (long long)K1});
+    }
+  }
+  std::stable_sort(fast.begin(), fast.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+  p->tcbf_items.clear();
+  for (auto& i : fast) {
+    p->tcbf_items.push_back(i.a); p->tcbf_items.push_back(i.n0); p->tcbf_items.push_back(i.start); p->tcbf_items.push_back(i.K1);
   }
   // items whose Y^T tile fits the resident three-pass form (K1 <= 96) first, longest first
   std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) {
@@ -781,12 +1143,17 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   const size_t o_wt = place((size_t)p->tcb_wt_rows * NT * 2 * 2);   // hi then lo
   const size_t o_row0 = place((size_t)p->n2 * 4);
   const size_t o_items = place(std::max<size_t>(16, p->tcb_items.size() * 4));
+  const size_t o_fitems = place(std::max<size_t>(16, p->tcbf_items.size() * 4));
   jtfs_status st;
   if ((st = cuda_check(cudaMalloc(&p->d_tcb_mem, off), "tc backward tables")) != JTFS_OK) return st;
   char* base = (char*)p->d_tcb_mem;
   p->d_wtb = base + o_wt;
   p->d_wtb_row0 = (int*)(base + o_row0);
   p->d_tcb_items = (int*)(base + o_items);
+  p->d_tcbf_items = (int*)(base + o_fitems);
+  if (!p->tcbf_items.empty() &&
+      (st = cuda_check(cudaMemcpy(p->d_tcbf_items, p->tcbf_items.data(), p->tcbf_items.size() * 4, cudaMemcpyHostToDevice), "upload")) != JTFS_OK)
+    return st;
   if ((st = cuda_check(cudaMemset(p->d_wtb, 0, (size_t)p->tcb_wt_rows * NT * 2 * 2), "memset")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaMemcpy(p->d_wtb_row0, row0.data(), p->n2 * 4, cudaMemcpyHostToDevice), "upload")) != JTFS_OK) return st;
   if (!p->tcb_items.empty() &&
@@ -803,10 +1170,11 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   return cuda_check(cudaDeviceSynchronize(), "build tc backward tables");
 }
 
+static int tcb_g1_rows(const jtfs_plan* p) { return (p->C * p->n1 + 63) / 64 * 64; }
+
 size_t tcb_g1_bytes(const jtfs_plan* p, int64_t B) {   // hi and lo planes
   const int NT = tc_nt(p->n_t);
-  const int n_chunks = (p->C * p->n1 + kRC - 1) / kRC;
-  return 2 * (size_t)B * p->n2 * (size_t)n_chunks * kRC * NT * 2;
+  return 2 * (size_t)B * p->n2 * (size_t)tcb_g1_rows(p) * NT * 2;
 }
 
 int tcb3_wbufs(int NT) { return NT <= 32 ? 2 : 1; }
@@ -824,7 +1192,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   const int NT = tc_nt(p->n_t);
   const int rows = p->C * p->n1;
   const int n_chunks = (rows + kRC - 1) / kRC;
-  const int g1_rows = n_chunks * kRC;
+  const int g1_rows = tcb_g1_rows(p);
   jtfs_status rc;
   const bool three = p->cfg.precision == JTFS_PREC_FP32;
   const size_t g1_plane = tcb_g1_bytes(p, B) / 2;
@@ -898,6 +1266,79 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     maps.g1[h] = mg1[h];
     maps.wt[h] = mwt[h];
   }
+  // fast form for the rates with K1 <= 64: RC = 64 chunk rows for one BF16 pass, 32 for three
+  if (!p->tcbf_items.empty()) {
+    const int PLf = three ? 2 : 1, RCf = three ? 32 : 64;
+    TfMaps fm;
+    for (int pl = 0; pl < 6; ++pl) {
+      cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)rows};
+      cuuint64_t str[1] = {(cuuint64_t)p->n1_pad * 2};
+      cuuint32_t box[2] = {64, (cuuint32_t)RCf};
+      if (!make_tmap(&fm.w[pl], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p->d_wplanes[pl], dims, str, box, 128, &err)) {
+        set_error(err);
+        return JTFS_ERR_CUDA;
+      }
+    }
+    for (int h = 0; h < 2; ++h) {
+      for (int a = 0; a < 16; ++a) fm.y[h][a] = my[h][a];
+      fm.wt[h] = mwt[h];
+      cuuint64_t dims[2] = {(cuuint64_t)NT, (cuuint64_t)B * p->n2 * g1_rows};
+      cuuint64_t str[1] = {(cuuint64_t)NT * 2};
+      cuuint32_t box[2] = {(cuuint32_t)NT, (cuuint32_t)RCf};
+      if (!make_tmap(&fm.g1[h], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h ? g1lo : g1hi, dims, str, box, NT * 2, &err)) {
+        set_error(err);
+        return JTFS_ERR_CUDA;
+      }
+    }
+    // shared memory: resident Y^T and weight tiles, then the W ring and the gZ staging
+    const size_t a4 = ((128 * NT * 2 + 1023) / 1024) * 1024;
+    const size_t g1p = ((RCf * NT * 2 + 1023) / 1024) * 1024;
+    const size_t fixed = 1024 + (size_t)PLf * 2 * (2 * 64 * 128) + PLf * a4;
+    const size_t wbuf = (size_t)PLf * 3 * RCf * 128 + PLf * g1p;
+    const size_t a2buf = (size_t)PLf * 2 * 128 * RCf * 2;
+    const size_t budget = 225 * 1024;
+    int wb = 3, na2 = 2;
+    while (fixed + wb * wbuf + na2 * a2buf > budget && (wb > 2 || na2 > 1)) {
+      if (na2 > 1 && wb == 2) na2 = 1; else --wb;
+    }
+    if (fixed + wb * wbuf + na2 * a2buf > budget) {
+      set_error("tensor-core backward: no shared-memory layout for the fast form");
+      return JTFS_ERR_UNSUPPORTED;
+    }
+    const size_t smem = fixed + wb * wbuf + na2 * a2buf;
+    TfArgs fa;
+    fa.items = reinterpret_cast<const int4*>(p->d_tcbf_items);
+    fa.n_base = (int)(p->tcbf_items.size() / 4);
+    fa.n_items = fa.n_base * B;
+    fa.n_chunks = (rows + RCf - 1) / RCf;
+    fa.g1_rows = g1_rows;
+    fa.wbufs = wb;
+    fa.a2bufs = na2;
+    fa.wt_row0 = p->d_wtb_row0;
+    fa.gy = gy;
+    fa.err = p->d_err;
+    const int grid = std::min(fa.n_items, n_sm);
+#define JTFS_LAUNCH_TCBF(NTV, RCV, PLV)                                                         \
+  do {                                                                                          \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_fast<NTV, RCV, PLV>,                \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                              (int)smem), "attr tcbf")) != JTFS_OK)             \
+      return rc;                                                                                \
+    k_joint_bwd_fast<NTV, RCV, PLV><<<grid, kFThreads, smem, st>>>(fm, fa, d);                 \
+  } while (0)
+    if (three) {
+      if (NT == 16) JTFS_LAUNCH_TCBF(16, 32, 2);
+      else if (NT == 32) JTFS_LAUNCH_TCBF(32, 32, 2);
+      else JTFS_LAUNCH_TCBF(64, 32, 2);
+    } else {
+      if (NT == 16) JTFS_LAUNCH_TCBF(16, 64, 1);
+      else if (NT == 32) JTFS_LAUNCH_TCBF(32, 64, 1);
+      else JTFS_LAUNCH_TCBF(64, 64, 1);
+    }
+#undef JTFS_LAUNCH_TCBF
+    if ((rc = cuda_check(cudaGetLastError(), "k_joint_bwd_fast")) != JTFS_OK) return rc;
+  }
+  if (n_all == 0) return JTFS_OK;
   // resident-Y launches: every item for one BF16 pass; the K1 <= 96 items for three passes
   const int PL = three ? 2 : 1;
   int n_res = three ? (NT <= 32 ? p->tcb_n_res : 0) : n_all;

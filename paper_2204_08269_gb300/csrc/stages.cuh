@@ -122,5 +122,66 @@ k_second_order(DevPlan P, const int2* __restrict__ pairs, const float2* __restri
   }
 }
 
+// Batched Y producer: one CTA takes G consecutive rows lambda'_0 .. lambda'_0 + G - 1 of one rate
+// (G L_alpha <= 8192 samples), folds them into shared memory, runs one batched inverse FFT and
+// writes BF16 planes (hi, and lo when ylo is given) or complex FP32 rows.
+constexpr int kRowThreads = 256;
+
+template <int OUT_BF16>
+__global__ void __launch_bounds__(kRowThreads)
+k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __restrict__ uh,
+                    float2* __restrict__ y, __nv_bfloat16* __restrict__ yhi,
+                    __nv_bfloat16* __restrict__ ylo, int B) {
+  extern __shared__ float2 sm[];
+  const int4 it = items[blockIdx.x];
+  const int a = it.x, lam0 = it.y, G = it.z, b = blockIdx.y;
+  const Rate2 A = P.rates2[a];
+  const float* psi = P.psi2 + (size_t)a * P.K2max;
+  const int L = A.L, logL = A.logL;
+  for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
+    const int row = idx >> logL, kp = idx & (L - 1);
+    const Row1 R = P.rows1[lam0 + row];
+    const float2* ur = uh + (size_t)b * P.uh_len + R.off_uh;
+    const int kmax = R.L >> 1;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int k = kp; k < kmax; k += L) {
+      const float2 u = ur[k];
+      const float f = __ldg(&psi[k]);
+      acc.x += u.x * f;
+      acc.y += u.y * f;
+    }
+    sm[(row << logL) + bitrev(kp, logL)] = acc;
+  }
+  __syncthreads();
+  fft_dit_rows<+1>(sm, logL, G, P.tw, P.logTW);
+  if (!OUT_BF16) {
+    for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
+      const int row = idx >> logL, m = idx & (L - 1);
+      const float inv = 1.f / (float)P.rows1[lam0 + row].L;
+      const float2 v = sm[idx];
+      y[(size_t)b * P.y_len + A.off_y + (size_t)(lam0 + row - A.lam_min) * L + m] =
+          make_float2(v.x * inv, v.y * inv);
+    }
+  } else {
+    const size_t region = (size_t)B * 2 * A.off_y;
+    const size_t plane = (size_t)A.K * L;
+    for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
+      const int row = idx >> logL, m = idx & (L - 1);
+      const float inv = 1.f / (float)P.rows1[lam0 + row].L;
+      const size_t off_re = region + (size_t)(2 * b) * plane + (size_t)(lam0 + row - A.lam_min) * L + m;
+      const size_t off_im = off_re + plane;
+      const float2 v = sm[idx];
+      const float re = v.x * inv, im = v.y * inv;
+      const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi_ = __float2bfloat16_rn(im);
+      yhi[off_re] = hr;
+      yhi[off_im] = hi_;
+      if (ylo) {
+        ylo[off_re] = __float2bfloat16_rn(re - __bfloat162float(hr));
+        ylo[off_im] = __float2bfloat16_rn(im - __bfloat162float(hi_));
+      }
+    }
+  }
+}
+
 }  // namespace
 }  // namespace jtfs
