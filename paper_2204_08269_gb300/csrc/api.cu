@@ -301,6 +301,20 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   d.M = (int)std::min<int64_t>(N, 8192); d.logM = ilog2(d.M); d.D = (int)(N / d.M);
   d.K2max = std::max(1, p->L1max / 2);
   d.u1_len = p->u1_len; d.uh_len = p->uh_len; d.y_len = p->y_len;
+  // psi-hat_alpha support end (xi + 8 sigma; both Morlet terms are below e^-32 past it) and the
+  // row items of the batched second-order producer: G rows of one rate per CTA
+  p->rows_cap = std::max(p->L2max, 8192);
+  p->rowitems.clear();
+  for (int a = 0; a < p->n2; ++a) {
+    Rate2& A = p->rates2[a];
+    A.k2e = (int)std::min<double>(d.K2max, std::floor((p->xi2[a] + kSupportSigmas * p->sg2[a]) * (double)N) + 1.0);
+    if (A.s == 0) continue;
+    const int G = std::max(1, p->rows_cap / A.L);
+    for (int l0 = A.lam_min; l0 < p->n1; l0 += G) {
+      p->rowitems.push_back(a); p->rowitems.push_back(l0);
+      p->rowitems.push_back(std::min(G, p->n1 - l0)); p->rowitems.push_back(0);
+    }
+  }
   // lambda range per 256-bin block of x-hat (for the gradient gather)
   const int nblk = (int)((N / 2 + 255) / 256);
   std::vector<int2> gxl(nblk);
@@ -332,6 +346,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   const size_t o_gx = place(sizeof(int2) * nblk);
   const size_t o_pairs = place(sizeof(int) * std::max<size_t>(2, p->pairs.size()));
   const size_t o_items = place(sizeof(int) * std::max<size_t>(2, p->items.size()));
+  const size_t o_ritems = place(sizeof(int) * std::max<size_t>(4, p->rowitems.size()));
   p->d_bytes = off;
   if ((st = cuda_check(cudaMalloc(&p->d_mem, off), "plan tables")) != JTFS_OK) return fail(st, "");
   char* base = (char*)p->d_mem;
@@ -346,6 +361,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   d.gx_lam = (const int2*)(base + o_gx);
   p->d_pairs = (int*)(base + o_pairs);
   p->d_items = (int*)(base + o_items);
+  p->d_rowitems = (int*)(base + o_ritems);
   struct Up { size_t at; const void* src; size_t bytes; } ups[] = {
       {o_rows, p->rows1.data(), sizeof(Row1) * p->n1},
       {o_rates, p->rates2.data(), sizeof(Rate2) * p->n2},
@@ -353,6 +369,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
       {o_gx, gxl.data(), sizeof(int2) * nblk},
       {o_pairs, p->pairs.data(), sizeof(int) * p->pairs.size()},
       {o_items, p->items.data(), sizeof(int) * p->items.size()},
+      {o_ritems, p->rowitems.data(), sizeof(int) * p->rowitems.size()},
   };
   for (const Up& u : ups)
     if (u.bytes && (st = cuda_check(cudaMemcpy(base + u.at, u.src, u.bytes, cudaMemcpyHostToDevice),

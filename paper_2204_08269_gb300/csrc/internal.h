@@ -33,6 +33,7 @@ struct Rate2 {
   int logL;
   int lam_min;  // first lambda' row with a non-zero Y_alpha row
   int K;        // n1 - lam_min rows of Y_alpha
+  int k2e;      // end of psi-hat_alpha's support on the N grid (bins >= k2e hold < e^-32)
   long long off_y;  // offset of Y_alpha (K x L complex) in a packed per-signal array
 };
 
@@ -81,6 +82,9 @@ struct jtfs_plan {
   std::vector<jtfs::Row1> rows1;
   std::vector<jtfs::Rate2> rates2;
   std::vector<int> pairs;  // (alpha, lambda') work items of the second-order kernels
+  std::vector<int> rowitems;  // (alpha, lambda'_0, G, 0): G rows of one rate per CTA
+  int rows_cap;               // samples one row item holds (G L_alpha <= rows_cap)
+  int* d_rowitems;
   std::vector<int> items;  // (alpha, first column) work items of the joint backward
   long long u1_len, uh_len, y_len;
   int L1max, L2max;

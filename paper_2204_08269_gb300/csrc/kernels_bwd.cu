@@ -179,7 +179,8 @@ k_second_order_bwd(DevPlan P, const float2* __restrict__ gy, const float* __rest
     __syncthreads();
     fft_dif<-1>(tmp, A.logL, P.tw, P.logTW);
     const float* psi = P.psi2 + (size_t)a * P.K2max;
-    for (int k = 1 + threadIdx.x; k < half; k += blockDim.x) {
+    const int kend = min(half, A.k2e);
+    for (int k = 1 + threadIdx.x; k < kend; k += blockDim.x) {
       const float2 v = tmp[bitrev(k & (A.L - 1), A.logL)];
       const float f = __ldg(&psi[k]) * invLr;
       guh[k].x += v.x * f;
@@ -293,8 +294,8 @@ jtfs_status set_attrs() {
   const int big = 227 * 1024;
   const void* fns[] = {(const void*)k_uh_from_u1, (const void*)k_joint_bwd_simt,
                        (const void*)k_second_order_bwd, (const void*)k_stage1_bwd,
-                       (const void*)k_gx, (const void*)k_xfft_sub, (const void*)k_second_order<0>,
-                       (const void*)k_second_order<1>};
+                       (const void*)k_gx, (const void*)k_xfft_sub, (const void*)k_second_order_rows<0>,
+                       (const void*)k_second_order_rows<1>};
   for (const void* f : fns) {
     jtfs_status st = cuda_check(
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr");
@@ -331,10 +332,10 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
   if (gs2 && n_items > 0 && p->use_tcb) {
     {
       StageScope sc(p, kStSecondOrder, st, 1);
-      k_second_order<1><<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
-                         (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
-                                                     w.uh, nullptr, (__nv_bfloat16*)w.ybh,
-                                                     (__nv_bfloat16*)w.ybl, B);
+      k_second_order_rows<1><<<dim3((unsigned)(p->rowitems.size() / 4), B), kRowThreads,
+                              (size_t)p->rows_cap * 8, st>>>(
+          d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, nullptr,
+          (__nv_bfloat16*)w.ybh, (__nv_bfloat16*)w.ybl, B);
     }
     StageScope sc(p, kStJointBwd, st, 2);
     jtfs_status r2 = launch_joint_bwd_tc(p, B, w.ybh, w.ybl, gs2, w.g1, w.gy, st);
@@ -342,9 +343,9 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
   } else if (gs2 && n_items > 0) {
     {
       StageScope sc(p, kStSecondOrder, st, 1);
-      k_second_order<0><<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
-                         (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
-                                                     w.uh, w.y, nullptr, nullptr, B);
+      k_second_order_rows<0><<<dim3((unsigned)(p->rowitems.size() / 4), B), kRowThreads,
+                              (size_t)p->rows_cap * 8, st>>>(
+          d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, w.y, nullptr, nullptr, B);
     }
     StageScope sc(p, kStJointBwd, st, 1);
     k_joint_bwd_simt<<<dim3((unsigned)n_items, B), kJT, joint_bwd_smem(p), st>>>(

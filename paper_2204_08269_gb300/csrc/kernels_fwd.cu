@@ -5,8 +5,9 @@
 //   k_scalogram                 : per (lambda, signal): periodise x-hat * psi-hat_lambda to
 //                                 L_lambda bins, inverse FFT, modulus -> U1 row (checkpoint),
 //                                 S1 row (Riemann sum of phi_T), FFT of the row -> U1-hat
-//   k_second_order              : per (alpha, lambda', signal): U1-hat * psi-hat_alpha folded to
-//                                 L_alpha bins, inverse FFT -> Y_alpha row
+//   k_second_order_rows         : per (alpha, block of lambda' rows, signal): U1-hat *
+//                                 psi-hat_alpha folded to L_alpha bins, batched inverse FFT
+//                                 -> Y_alpha rows
 //   k_joint_fwd_simt            : per (c, alpha, signal): Z = W_c Y_alpha (zero-padded
 //                                 convolution along lambda), |Z|, phi_T then phi_F pooling -> S2
 #include "stages.cuh"
@@ -201,8 +202,8 @@ jtfs_status set_attrs(const jtfs_plan* p) {
   jtfs_status st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_xfft_sub, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_scalogram, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
-  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
-  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_joint_fwd_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
   g_attrs_set = true;
   return JTFS_OK;
@@ -242,10 +243,10 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   if (p->use_tc) {
     if (!p->pairs.empty()) {
       StageScope sc(p, kStSecondOrder, st, 1);
-      k_second_order<1><<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
-                         (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
-                                                     w.uh, nullptr, (__nv_bfloat16*)w.ybh,
-                                                     (__nv_bfloat16*)w.ybl, B);
+      k_second_order_rows<1><<<dim3((unsigned)(p->rowitems.size() / 4), B), kRowThreads,
+                              (size_t)p->rows_cap * 8, st>>>(
+          d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, nullptr,
+          (__nv_bfloat16*)w.ybh, (__nv_bfloat16*)w.ybl, B);
     }
     StageScope sc(p, kStJointFwd, st, 2);
     jtfs_status r2 = launch_joint_fwd_tc(p, B, w.ybh, w.ybl, w.pbuf, s2, st);
@@ -253,9 +254,9 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   } else {
     if (!p->pairs.empty()) {
       StageScope sc(p, kStSecondOrder, st, 1);
-      k_second_order<0><<<dim3((unsigned)(p->pairs.size() / 2), B), kFftThreads,
-                         (size_t)p->L2max * 8, st>>>(d, reinterpret_cast<const int2*>(p->d_pairs),
-                                                     w.uh, w.y, nullptr, nullptr, B);
+      k_second_order_rows<0><<<dim3((unsigned)(p->rowitems.size() / 4), B), kRowThreads,
+                              (size_t)p->rows_cap * 8, st>>>(
+          d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, w.y, nullptr, nullptr, B);
     }
     StageScope sc(p, kStJointFwd, st, 1);
     k_joint_fwd_simt<<<dim3(p->C, p->n2, B), kJT, joint_fwd_smem(p), st>>>(d, w.y, s2);

@@ -65,66 +65,12 @@ __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R
   }
 }
 
-// Y_alpha row of lambda': the row spectrum U1-hat[k] (positive bins below the row's Nyquist)
-// times psi-hat_alpha(k / N), folded modulo L_alpha, inverse FFT, scaled by 1 / L_lambda'.
-// OUT_BF16 = 0: Y row written as complex FP32 at the per-signal offset of the rate.
-// OUT_BF16 = 1: Y row written as BF16 planes for the tensor-core contraction, layout
-// [alpha][2 b + part][lambda' - lam_min][n] (part 0 = Re, 1 = Im), value = hi + lo with
-// hi = bf16(v) and lo = bf16(v - hi).
-template <int OUT_BF16>
-__global__ void __launch_bounds__(kFftThreads)
-k_second_order(DevPlan P, const int2* __restrict__ pairs, const float2* __restrict__ uh,
-               float2* __restrict__ y, __nv_bfloat16* __restrict__ yhi,
-               __nv_bfloat16* __restrict__ ylo, int B) {
-  extern __shared__ float2 sm[];
-  const int2 pr = pairs[blockIdx.x];
-  const int a = pr.x, lam = pr.y, b = blockIdx.y;
-  const Row1 R = P.rows1[lam];
-  const Rate2 A = P.rates2[a];
-  const float2* ur = uh + (size_t)b * P.uh_len + R.off_uh;
-  const float* psi = P.psi2 + (size_t)a * P.K2max;
-  const int kmax = R.L >> 1;  // positive frequencies strictly below the row's Nyquist
-  for (int kp = threadIdx.x; kp < A.L; kp += blockDim.x) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int k = kp; k < kmax; k += A.L) {
-      const float2 u = ur[k];
-      const float f = __ldg(&psi[k]);
-      acc.x += u.x * f;
-      acc.y += u.y * f;
-    }
-    sm[bitrev(kp, A.logL)] = acc;
-  }
-  __syncthreads();
-  fft_dit<+1>(sm, A.logL, P.tw, P.logTW);
-  const float inv = 1.f / (float)R.L;
-  if (!OUT_BF16) {
-    float2* yr = y + (size_t)b * P.y_len + A.off_y + (size_t)(lam - A.lam_min) * A.L;
-    for (int m = threadIdx.x; m < A.L; m += blockDim.x) {
-      const float2 v = sm[m];
-      yr[m] = make_float2(v.x * inv, v.y * inv);
-    }
-  } else {
-    const size_t region = (size_t)B * 2 * A.off_y;
-    const size_t plane = (size_t)A.K * A.L;
-    const size_t off_re = region + (size_t)(2 * b) * plane + (size_t)(lam - A.lam_min) * A.L;
-    const size_t off_im = off_re + plane;
-    for (int m = threadIdx.x; m < A.L; m += blockDim.x) {
-      const float2 v = sm[m];
-      const float re = v.x * inv, im = v.y * inv;
-      const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi_ = __float2bfloat16_rn(im);
-      yhi[off_re + m] = hr;
-      yhi[off_im + m] = hi_;
-      if (ylo) {
-        ylo[off_re + m] = __float2bfloat16_rn(re - __bfloat162float(hr));
-        ylo[off_im + m] = __float2bfloat16_rn(im - __bfloat162float(hi_));
-      }
-    }
-  }
-}
-
-// Batched Y producer: one CTA takes G consecutive rows lambda'_0 .. lambda'_0 + G - 1 of one rate
-// (G L_alpha <= 8192 samples), folds them into shared memory, runs one batched inverse FFT and
-// writes BF16 planes (hi, and lo when ylo is given) or complex FP32 rows.
+// Batched Y producer: one CTA takes G consecutive rows lambda'_0 .. lambda'_0 + G - 1 of one
+// rate (G L_alpha samples fit the launch's shared memory), folds them into shared memory in
+// bit-reversed order, runs one batched inverse FFT and writes the rows: complex FP32
+// (OUT_BF16 = 0) or BF16 planes hi (and lo when ylo is given) in the contraction layout
+// [alpha][2 b + part][lambda' - lam_min][n].  The fold only visits bins below the rate's
+// psi-hat support end.
 constexpr int kRowThreads = 256;
 
 template <int OUT_BF16>
@@ -138,13 +84,14 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
   const Rate2 A = P.rates2[a];
   const float* psi = P.psi2 + (size_t)a * P.K2max;
   const int L = A.L, logL = A.logL;
+  const float2* ub = uh + (size_t)b * P.uh_len;
   for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
     const int row = idx >> logL, kp = idx & (L - 1);
     const Row1 R = P.rows1[lam0 + row];
-    const float2* ur = uh + (size_t)b * P.uh_len + R.off_uh;
-    const int kmax = R.L >> 1;
+    const float2* ur = ub + R.off_uh;
+    const int kend = min(R.L >> 1, A.k2e);
     float2 acc = make_float2(0.f, 0.f);
-    for (int k = kp; k < kmax; k += L) {
+    for (int k = kp; k < kend; k += L) {
       const float2 u = ur[k];
       const float f = __ldg(&psi[k]);
       acc.x += u.x * f;
@@ -155,29 +102,29 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
   __syncthreads();
   fft_dit_rows<+1>(sm, logL, G, P.tw, P.logTW);
   if (!OUT_BF16) {
+    float2* ya = y + (size_t)b * P.y_len + A.off_y + (size_t)(lam0 - A.lam_min) * L;
     for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
-      const int row = idx >> logL, m = idx & (L - 1);
-      const float inv = 1.f / (float)P.rows1[lam0 + row].L;
+      const float inv = 1.f / (float)P.rows1[lam0 + (idx >> logL)].L;
       const float2 v = sm[idx];
-      y[(size_t)b * P.y_len + A.off_y + (size_t)(lam0 + row - A.lam_min) * L + m] =
-          make_float2(v.x * inv, v.y * inv);
+      ya[idx] = make_float2(v.x * inv, v.y * inv);
     }
   } else {
-    const size_t region = (size_t)B * 2 * A.off_y;
+    // rows of one rate are contiguous in each plane: element idx of the block sits at
+    // (lam0 - lam_min) L + idx; two samples per thread
     const size_t plane = (size_t)A.K * L;
-    for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
-      const int row = idx >> logL, m = idx & (L - 1);
-      const float inv = 1.f / (float)P.rows1[lam0 + row].L;
-      const size_t off_re = region + (size_t)(2 * b) * plane + (size_t)(lam0 + row - A.lam_min) * L + m;
-      const size_t off_im = off_re + plane;
-      const float2 v = sm[idx];
-      const float re = v.x * inv, im = v.y * inv;
-      const __nv_bfloat16 hr = __float2bfloat16_rn(re), hi_ = __float2bfloat16_rn(im);
-      yhi[off_re] = hr;
-      yhi[off_im] = hi_;
+    const size_t base = (size_t)B * 2 * A.off_y + (size_t)(2 * b) * plane + (size_t)(lam0 - A.lam_min) * L;
+    for (int i2 = threadIdx.x; i2 < (G * L) >> 1; i2 += blockDim.x) {
+      const int idx = 2 * i2;
+      const float inv = 1.f / (float)P.rows1[lam0 + (idx >> logL)].L;
+      const float2 v0 = sm[idx], v1 = sm[idx + 1];
+      const float r0 = v0.x * inv, r1 = v1.x * inv, i0 = v0.y * inv, i1 = v1.y * inv;
+      const __nv_bfloat162 hr = __floats2bfloat162_rn(r0, r1), hi_ = __floats2bfloat162_rn(i0, i1);
+      *reinterpret_cast<__nv_bfloat162*>(yhi + base + idx) = hr;
+      *reinterpret_cast<__nv_bfloat162*>(yhi + base + plane + idx) = hi_;
       if (ylo) {
-        ylo[off_re] = __float2bfloat16_rn(re - __bfloat162float(hr));
-        ylo[off_im] = __float2bfloat16_rn(im - __bfloat162float(hi_));
+        const float2 fr = __bfloat1622float2(hr), fi = __bfloat1622float2(hi_);
+        *reinterpret_cast<__nv_bfloat162*>(ylo + base + idx) = __floats2bfloat162_rn(r0 - fr.x, r1 - fr.y);
+        *reinterpret_cast<__nv_bfloat162*>(ylo + base + plane + idx) = __floats2bfloat162_rn(i0 - fi.x, i1 - fi.y);
       }
     }
   }
