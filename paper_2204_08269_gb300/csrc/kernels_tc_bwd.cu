@@ -691,6 +691,10 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
 // swizzle), read K-major by the first product and MN-major by the second.  The Z^T / g|Z|^T
 // accumulators are double-buffered in TMEM so the next chunk's product overlaps the epilogue;
 // sixteen epilogue warps (four per lane quarter, RC / 4 rows each) form gZ.
+// With the FP32-grade split (PL = 2) the first product and the pooling adjoint take three
+// passes (hi hi + hi lo + lo hi) and the last takes two, gZ_hi (W_hi + W_lo): a model of
+// every split in FP64 puts the gradient error of this choice at <= 3e-4 on the Eq. 4 case
+// (1e-3 tolerance), where one pass of the last product alone reaches 6.5e-4.
 struct TfMaps {
   CUtensorMap w[6];      // Wr_hi, Wi_hi, Wr_lo, Wi_lo, -Wi_hi, -Wi_lo; box {64 lambda', RC r}
   CUtensorMap y[2][16];  // [hi/lo][alpha]: Y planes [2B][K][L], box {64 n, 32 lambda', 1}
@@ -747,7 +751,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
   constexpr uint32_t kG1Plane = ((RC * NT * 2 + 1023) / 1024) * 1024;
   constexpr uint32_t kWBuf = PL * 3 * kWBlk + PL * kG1Plane;
   constexpr uint32_t kA2Part = 128 * RC * 2;              // [128 n][RC r] bf16
-  constexpr uint32_t kA2Buf = PL * 2 * kA2Part;
+  constexpr uint32_t kA2Buf = 2 * kA2Part;                // gZr, gZi (BF16 hi)
   constexpr uint32_t kA2Lay = RC == 64 ? kSw128 : kSw64;
   constexpr uint32_t kA2Sbo = RC == 64 ? 1024 : 512;
   const int WB = args.wbufs, NA2 = args.a2bufs;
@@ -902,11 +906,10 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
             const uint32_t wb = smem_u32(sW + prev_wst * kWBuf);
             const uint32_t a2 = smem_u32(sA2 + prev_q2 * kA2Buf);
             for (int ks = 0; ks < RC / 16; ++ks) {
-              for (int q = 0; q < npair; ++q) {
-                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-                const uint64_t agr = smem_desc(a2 + (pa * 2 + 0) * kA2Part + ks * 32, 16, kA2Sbo, kA2Lay);
-                const uint64_t agi = smem_desc(a2 + (pa * 2 + 1) * kA2Part + ks * 32, 16, kA2Sbo, kA2Lay);
-                const uint32_t wpl = wb + pb * 3 * kWBlk + ks * 2048;
+              const uint64_t agr = smem_desc(a2 + ks * 32, 16, kA2Sbo, kA2Lay);
+              const uint64_t agi = smem_desc(a2 + kA2Part + ks * 32, 16, kA2Sbo, kA2Lay);
+              for (int q = 0; q < PL; ++q) {                      // W_hi, then W_lo
+                const uint32_t wpl = wb + q * 3 * kWBlk + ks * 2048;
                 const uint32_t f = (first_d2 && ks == 0 && q == 0) ? 0u : 1u;
                 mma_f16(t_d2, agi, smem_desc(wpl + kWBlk, kWBlk, 1024, kSw128), id2, f);   // gZi [Wr | Wi]
                 mma_f16(t_d2, agr, smem_desc(wpl, kWBlk, 1024, kSw128), id2, 1u);          // gZr [-Wi | Wr]
@@ -958,7 +961,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&d1_free[buf]);
-        uint32_t hr[CW / 2], hi[CW / 2], lr[CW / 2], li[CW / 2];
+        uint32_t hr[CW / 2], hi[CW / 2];
 #pragma unroll
         for (int i = 0; i < CW / 2; ++i) {
           float vr[2], vi[2];
@@ -974,13 +977,6 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
           __nv_bfloat162 a1v = __floats2bfloat162_rn(vi[0], vi[1]);
           hr[i] = *reinterpret_cast<uint32_t*>(&a0);
           hi[i] = *reinterpret_cast<uint32_t*>(&a1v);
-          if (PL == 2) {
-            const float2 fa0 = __bfloat1622float2(a0), fa1 = __bfloat1622float2(a1v);
-            __nv_bfloat162 b0 = __floats2bfloat162_rn(vr[0] - fa0.x, vr[1] - fa0.y);
-            __nv_bfloat162 b1 = __floats2bfloat162_rn(vi[0] - fa1.x, vi[1] - fa1.y);
-            lr[i] = *reinterpret_cast<uint32_t*>(&b0);
-            li[i] = *reinterpret_cast<uint32_t*>(&b1);
-          }
         }
         if (!mbar_wait(&a2_free[q2], ((a2f_ph >> q2) & 1) ^ 1, kWaitNs)) { fail(69); ok = false; break; }
         a2f_ph ^= 1u << q2;
@@ -991,10 +987,6 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
           const int pos = (RC == 64 ? (ch ^ (row & 7)) : (ch ^ ((row >> 1) & 3))) * 16;
           *reinterpret_cast<uint4*>(base + 0 * kA2Part + pos) = make_uint4(hr[4 * c], hr[4 * c + 1], hr[4 * c + 2], hr[4 * c + 3]);
           *reinterpret_cast<uint4*>(base + 1 * kA2Part + pos) = make_uint4(hi[4 * c], hi[4 * c + 1], hi[4 * c + 2], hi[4 * c + 3]);
-          if (PL == 2) {
-            *reinterpret_cast<uint4*>(base + 2 * kA2Part + pos) = make_uint4(lr[4 * c], lr[4 * c + 1], lr[4 * c + 2], lr[4 * c + 3]);
-            *reinterpret_cast<uint4*>(base + 3 * kA2Part + pos) = make_uint4(li[4 * c], li[4 * c + 1], li[4 * c + 2], li[4 * c + 3]);
-          }
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -1078,6 +1070,29 @@ __global__ void k_build_wtb(DevPlan Pd, int a, int NT, int Lpad, __nv_bfloat16* 
 
 int tc_nt(int n_t);
 
+// Shared memory of the fast form (64-row chunks): resident Y^T and weight tiles, then the W
+// ring (2..3 chunks) and the gZ staging (1..2 buffers), deepest first.  False if even the
+// shallowest layout does not fit.
+static bool tcbf_layout(const jtfs_plan* p, int* wb_out, int* na2_out, size_t* smem_out) {
+  const int NT = tc_nt(p->n_t);
+  const int PL = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1, RC = 64;
+  const size_t a4 = ((128 * NT * 2 + 1023) / 1024) * 1024;
+  const size_t g1p = ((RC * NT * 2 + 1023) / 1024) * 1024;
+  const size_t fixed = 1024 + (size_t)PL * 2 * (2 * 64 * 128) + PL * a4;
+  const size_t wbuf = (size_t)PL * 3 * RC * 128 + PL * g1p;
+  const size_t a2buf = (size_t)2 * 128 * RC * 2;
+  const size_t budget = 225 * 1024;
+  int wb = 3, na2 = 2;
+  while (fixed + wb * wbuf + na2 * a2buf > budget && (wb > 2 || na2 > 1)) {
+    if (na2 > 1 && wb == 2) na2 = 1; else --wb;
+  }
+  if (fixed + wb * wbuf + na2 * a2buf > budget) return false;
+  *wb_out = wb;
+  *na2_out = na2;
+  *smem_out = fixed + wb * wbuf + na2 * a2buf;
+  return true;
+}
+
 size_t tcb_smem_bytes(int NT, int PL) {
   const int k1m = PL == 1 ? 160 : 96, wblk = (k1m + 63) / 64, na2 = PL == 1 ? 2 : 1;
   const size_t g1 = ((kRC * NT * 2 + 1023) / 1024) * 1024;
@@ -1108,6 +1123,9 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   }
   struct It { int a, n0, start, K1; long long cost; };
   std::vector<It> its, fast;
+  int wb_, na2_;
+  size_t smem_;
+  const bool use_fast = tcbf_layout(p, &wb_, &na2_, &smem_);
   for (int a = 0; a < p->n2; ++a) {
     const Rate2& A = p->rates2[a];
     if (A.s == 0) continue;
@@ -1116,7 +1134,7 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
     const int start = A.lam_min / 64 * 64;
     const int K1 = (p->n1 - start + 31) / 32 * 32;
     for (int n0 = 0; n0 < A.L; n0 += 128) {
-      if (K1f <= 64) fast.push_back({a, n0, lm8, K1f, (long long)K1f});
+      if (K1f <= 64 && use_fast) fast.push_back({a, n0, lm8, K1f, (long long)K1f});
       else its.push_back({a, n0, start, K1, (long long)K1});
     }
   }
@@ -1266,9 +1284,9 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     maps.g1[h] = mg1[h];
     maps.wt[h] = mwt[h];
   }
-  // fast form for the rates with K1 <= 64: RC = 64 chunk rows for one BF16 pass, 32 for three
+  // fast form for the rates with K1 <= 64, 64-row chunks
   if (!p->tcbf_items.empty()) {
-    const int PLf = three ? 2 : 1, RCf = three ? 32 : 64;
+    const int PLf = three ? 2 : 1, RCf = 64;
     TfMaps fm;
     for (int pl = 0; pl < 6; ++pl) {
       cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)rows};
@@ -1290,22 +1308,12 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
         return JTFS_ERR_CUDA;
       }
     }
-    // shared memory: resident Y^T and weight tiles, then the W ring and the gZ staging
-    const size_t a4 = ((128 * NT * 2 + 1023) / 1024) * 1024;
-    const size_t g1p = ((RCf * NT * 2 + 1023) / 1024) * 1024;
-    const size_t fixed = 1024 + (size_t)PLf * 2 * (2 * 64 * 128) + PLf * a4;
-    const size_t wbuf = (size_t)PLf * 3 * RCf * 128 + PLf * g1p;
-    const size_t a2buf = (size_t)PLf * 2 * 128 * RCf * 2;
-    const size_t budget = 225 * 1024;
-    int wb = 3, na2 = 2;
-    while (fixed + wb * wbuf + na2 * a2buf > budget && (wb > 2 || na2 > 1)) {
-      if (na2 > 1 && wb == 2) na2 = 1; else --wb;
-    }
-    if (fixed + wb * wbuf + na2 * a2buf > budget) {
+    int wb = 0, na2 = 0;
+    size_t smem = 0;
+    if (!tcbf_layout(p, &wb, &na2, &smem)) {
       set_error("tensor-core backward: no shared-memory layout for the fast form");
       return JTFS_ERR_UNSUPPORTED;
     }
-    const size_t smem = fixed + wb * wbuf + na2 * a2buf;
     TfArgs fa;
     fa.items = reinterpret_cast<const int4*>(p->d_tcbf_items);
     fa.n_base = (int)(p->tcbf_items.size() / 4);
@@ -1327,9 +1335,9 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     k_joint_bwd_fast<NTV, RCV, PLV><<<grid, kFThreads, smem, st>>>(fm, fa, d);                 \
   } while (0)
     if (three) {
-      if (NT == 16) JTFS_LAUNCH_TCBF(16, 32, 2);
-      else if (NT == 32) JTFS_LAUNCH_TCBF(32, 32, 2);
-      else JTFS_LAUNCH_TCBF(64, 32, 2);
+      if (NT == 16) JTFS_LAUNCH_TCBF(16, 64, 2);
+      else if (NT == 32) JTFS_LAUNCH_TCBF(32, 64, 2);
+      else JTFS_LAUNCH_TCBF(64, 64, 2);
     } else {
       if (NT == 16) JTFS_LAUNCH_TCBF(16, 64, 1);
       else if (NT == 32) JTFS_LAUNCH_TCBF(32, 64, 1);
