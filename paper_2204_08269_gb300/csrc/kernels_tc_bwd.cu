@@ -682,8 +682,10 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
   }
 }
 
-// ------------------------------------------------------------------ fast form (K1 <= 64)
-// For rates whose lambda' range (from lam_min rounded down to 8) spans at most 64 rows.
+// ------------------------------------------------------------------ fast form
+// For rates whose lambda' range (from lam_min rounded down to 8) spans at most KM rows, held
+// as NAT atoms of 64 lambda' (NAT = 1: K1 <= 64 with 64-row chunks; NAT = 2: K1 <= KM with
+// 32-row chunks, the TMEM then holding two 128-column gY^T atoms).
 // The complex products are stacked so every MMA is 128 wide:
 //   Z^T [Re | Im]   = Yr [Wr ; Wi]^T + Yi [-Wi ; Wr]^T          (N = 2 RC rows of the chunk)
 //   gY^T [Im | Re] += gZi [Wr | Wi] + gZr [-Wi | Wr]            (N = 2 x 64 lambda')
@@ -703,7 +705,7 @@ struct TfMaps {
 };
 
 struct TfArgs {
-  const int4* items;    // (alpha, n0, lambda' start = lam_min & ~7, K1 <= 64) per base
+  const int4* items;    // (alpha, n0, lambda' start = lam_min & ~7, K1 <= KM) per base
   int n_base;           // item it = base it % n_base of signal it / n_base
   int n_items;
   int n_chunks;         // ceil(C n1 / RC)
@@ -737,7 +739,7 @@ __device__ __forceinline__ void tmem_ldc(uint32_t taddr, float (&v)[CW]) {
   if constexpr (CW == 16) tmem_ld16(taddr, v); else tmem_ld8(taddr, v);
 }
 
-template <int NT, int RC, int PL>
+template <int NT, int RC, int PL, int NAT, int KM>
 __global__ void __launch_bounds__(kFThreads, 1)
 k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
   extern __shared__ uint8_t smem_raw[];
@@ -745,11 +747,11 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
   constexpr int CW = RC / 4;                              // chunk rows per epilogue warp
   constexpr uint32_t kSw = NT * 2;
   constexpr uint32_t kLayNT = kSw == 128 ? kSw128 : (kSw == 64 ? kSw64 : kSw32);
-  constexpr uint32_t kA1Plane = 2 * 64 * 128;             // two 64-sample halves x 64 lambda'
+  constexpr uint32_t kA1Plane = 2 * KM * 128;             // two 64-sample halves x KM lambda'
   constexpr uint32_t kA4Plane = ((128 * NT * 2 + 1023) / 1024) * 1024;
   constexpr uint32_t kWBlk = RC * 128;                    // RC rows x 64 lambda'
   constexpr uint32_t kG1Plane = ((RC * NT * 2 + 1023) / 1024) * 1024;
-  constexpr uint32_t kWBuf = PL * 3 * kWBlk + PL * kG1Plane;
+  constexpr uint32_t kWBuf = PL * NAT * 3 * kWBlk + PL * kG1Plane;
   constexpr uint32_t kA2Part = 128 * RC * 2;              // [128 n][RC r] bf16
   constexpr uint32_t kA2Buf = 2 * kA2Part;                // gZr, gZi (BF16 hi)
   constexpr uint32_t kA2Lay = RC == 64 ? kSw128 : kSw64;
@@ -791,7 +793,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
-  const uint32_t t_d2 = tbase + 6 * RC;                    // [Im 64 | Re 64]
+  const uint32_t t_d2 = tbase + 6 * RC;                    // NAT x [Im 64 | Re 64]
   auto fail = [&](int code) {
     if (!abort_flag) {
       abort_flag = 1;
@@ -820,7 +822,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
           for (int part = 0; part < 2; ++part)
             for (int h = 0; h < 2; ++h)
               for (int kb = 0; kb < nkb1; ++kb)
-                tma_load_3d(sA1 + (pl * 2 + part) * kA1Plane + h * 64 * 128 + kb * 32 * 128,
+                tma_load_3d(sA1 + (pl * 2 + part) * kA1Plane + h * KM * 128 + kb * 32 * 128,
                             &maps.y[pl][a], n0 + h * 64, start - A.lam_min + kb * 32,
                             2 * b + part, &a1_full);
           tma_load_2d(sA4 + pl * kA4Plane, &maps.wt[pl], 0, args.wt_row0[a] + n0, &a1_full);
@@ -829,15 +831,18 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
         const int g1row = (b * P.n2 + a) * args.g1_rows;
         for (int j = 0; j < args.n_chunks; ++j) {
           if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(62); ok = false; break; }
-          mbar_arrive_expect_tx(&w_full[wst], PL * 3 * RC * 64 * 2 + PL * RC * NT * 2);
+          mbar_arrive_expect_tx(&w_full[wst], PL * NAT * 3 * RC * 64 * 2 + PL * RC * NT * 2);
           armed_w |= 1u << wst;
           armed_w_par = (armed_w_par & ~(1u << wst)) | (wph << wst);
           uint8_t* wb = sW + wst * kWBuf;
           for (int pl = 0; pl < PL; ++pl) {
-            tma_load_2d(wb + (pl * 3 + 0) * kWBlk, &maps.w[4 + pl], start, j * RC, &w_full[wst]);
-            tma_load_2d(wb + (pl * 3 + 1) * kWBlk, &maps.w[pl * 2], start, j * RC, &w_full[wst]);
-            tma_load_2d(wb + (pl * 3 + 2) * kWBlk, &maps.w[pl * 2 + 1], start, j * RC, &w_full[wst]);
-            tma_load_2d(wb + PL * 3 * kWBlk + pl * kG1Plane, &maps.g1[pl], 0, g1row + j * RC,
+            for (int k = 0; k < NAT; ++k) {
+              uint8_t* blk = wb + (pl * NAT + k) * 3 * kWBlk;
+              tma_load_2d(blk, &maps.w[4 + pl], start + 64 * k, j * RC, &w_full[wst]);
+              tma_load_2d(blk + kWBlk, &maps.w[pl * 2], start + 64 * k, j * RC, &w_full[wst]);
+              tma_load_2d(blk + 2 * kWBlk, &maps.w[pl * 2 + 1], start + 64 * k, j * RC, &w_full[wst]);
+            }
+            tma_load_2d(wb + PL * NAT * 3 * kWBlk + pl * kG1Plane, &maps.g1[pl], 0, g1row + j * RC,
                         &w_full[wst]);
           }
           if (++wst == WB) { wst = 0; wph ^= 1; }
@@ -876,15 +881,15 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
             for (int ks = 0; ks < nks1; ++ks) {
               for (int q = 0; q < npair; ++q) {
                 const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-                const uint64_t ayr = smem_desc(a1 + (pa * 2 + 0) * kA1Plane + ks * 2048, 64 * 128, 1024, kSw128);
-                const uint64_t ayi = smem_desc(a1 + (pa * 2 + 1) * kA1Plane + ks * 2048, 64 * 128, 1024, kSw128);
-                const uint32_t wpl = wb + pb * 3 * kWBlk + ks * 32;
+                const uint64_t ayr = smem_desc(a1 + (pa * 2 + 0) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
+                const uint64_t ayi = smem_desc(a1 + (pa * 2 + 1) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
+                const uint32_t wpl = wb + (pb * NAT + (ks >> 2)) * 3 * kWBlk + (ks & 3) * 32;
                 const uint32_t f = (ks | q) ? 1u : 0u;
                 mma_f16(t_d1, ayr, smem_desc(wpl + kWBlk, 16, 1024, kSw128), id1, f);   // Yr [Wr; Wi]
                 mma_f16(t_d1, ayi, smem_desc(wpl, 16, 1024, kSw128), id1, 1u);          // Yi [-Wi; Wr]
               }
             }
-            const uint32_t g1 = wb + PL * 3 * kWBlk;
+            const uint32_t g1 = wb + PL * NAT * 3 * kWBlk;
             for (int ks = 0; ks < NT / 16; ++ks)
               for (int q = 0; q < npair; ++q) {
                 const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
@@ -909,10 +914,12 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
               const uint64_t agr = smem_desc(a2 + ks * 32, 16, kA2Sbo, kA2Lay);
               const uint64_t agi = smem_desc(a2 + kA2Part + ks * 32, 16, kA2Sbo, kA2Lay);
               for (int q = 0; q < PL; ++q) {                      // W_hi, then W_lo
-                const uint32_t wpl = wb + q * 3 * kWBlk + ks * 2048;
                 const uint32_t f = (first_d2 && ks == 0 && q == 0) ? 0u : 1u;
-                mma_f16(t_d2, agi, smem_desc(wpl + kWBlk, kWBlk, 1024, kSw128), id2, f);   // gZi [Wr | Wi]
-                mma_f16(t_d2, agr, smem_desc(wpl, kWBlk, 1024, kSw128), id2, 1u);          // gZr [-Wi | Wr]
+                for (int k = 0; k < NAT; ++k) {
+                  const uint32_t wpl = wb + (q * NAT + k) * 3 * kWBlk + ks * 2048;
+                  mma_f16(t_d2 + 128 * k, agi, smem_desc(wpl + kWBlk, kWBlk, 1024, kSw128), id2, f);   // gZi [Wr | Wi]
+                  mma_f16(t_d2 + 128 * k, agr, smem_desc(wpl, kWBlk, 1024, kSw128), id2, 1u);          // gZr [-Wi | Wr]
+                }
               }
             }
             first_d2 = false;
@@ -995,27 +1002,32 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
         if (++q2 == NA2) q2 = 0;
       }
       if (!ok) break;
-      // gY^T of this tile: lambda' = start + c for c in [16 cg, 16 cg + 16)
+      // gY^T of this tile: lambda' = start + 64 k + c for c in [16 cg, 16 cg + 16)
       if (!mbar_wait(&d2_full, d2_ph, kWaitNs)) { fail(70); break; }
       d2_ph ^= 1;
       tc_fence_after();
       const Rate2 A = P.rates2[a];
       const int n = n0 + row;
       float2* go = args.gy + (size_t)b * P.y_len + A.off_y;
-      float vi[16], vr[16];
-      tmem_ld16(t_d2 + lane_off + cg * 16, vi);
-      tmem_ld16(t_d2 + lane_off + 64 + cg * 16, vr);
+      float vi[NAT][16], vr[NAT][16];
+#pragma unroll
+      for (int k = 0; k < NAT; ++k) {
+        tmem_ld16(t_d2 + 128 * k + lane_off + cg * 16, vi[k]);
+        tmem_ld16(t_d2 + 128 * k + lane_off + 64 + cg * 16, vr[k]);
+      }
       tmem_wait_ld();
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&d2_free);
       if (n < A.L) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int lp = start + cg * 16 + i;
-          if (lp >= A.lam_min && lp < P.n1)
-            go[(size_t)(lp - A.lam_min) * A.L + n] = make_float2(vr[i], vi[i]);
-        }
+        for (int k = 0; k < NAT; ++k)
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int lp = start + 64 * k + cg * 16 + i;
+            if (lp >= A.lam_min && lp < P.n1)
+              go[(size_t)(lp - A.lam_min) * A.L + n] = make_float2(vr[k][i], vi[k][i]);
+          }
       }
     }
   }
@@ -1070,16 +1082,24 @@ __global__ void k_build_wtb(DevPlan Pd, int a, int NT, int Lpad, __nv_bfloat16* 
 
 int tc_nt(int n_t);
 
-// Shared memory of the fast form (64-row chunks): resident Y^T and weight tiles, then the W
-// ring (2..3 chunks) and the gZ staging (1..2 buffers), deepest first.  False if even the
-// shallowest layout does not fit.
-static bool tcbf_layout(const jtfs_plan* p, int* wb_out, int* na2_out, size_t* smem_out) {
+// Fast-form geometry: NAT = 1 (K1 <= 64) uses 64-row chunks; NAT = 2 uses 32-row chunks and
+// holds up to KM = 128 lambda' rows (96 for the FP32-grade split, whose hi / lo Y^T tile
+// is twice as large).
+static int tcbf_km(const jtfs_plan* p, int nat) {
+  return nat == 1 ? 64 : (p->cfg.precision == JTFS_PREC_FP32 ? 96 : 128);
+}
+
+// Shared memory of the fast form: resident Y^T and weight tiles, then the W ring (2..3
+// chunks) and the gZ staging (1..2 buffers), deepest first.  False if even the shallowest
+// layout does not fit.
+static bool tcbf_layout(const jtfs_plan* p, int nat, int* wb_out, int* na2_out, size_t* smem_out) {
   const int NT = tc_nt(p->n_t);
-  const int PL = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1, RC = 64;
+  const int PL = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1, RC = nat == 1 ? 64 : 32;
+  const int KM = tcbf_km(p, nat);
   const size_t a4 = ((128 * NT * 2 + 1023) / 1024) * 1024;
   const size_t g1p = ((RC * NT * 2 + 1023) / 1024) * 1024;
-  const size_t fixed = 1024 + (size_t)PL * 2 * (2 * 64 * 128) + PL * a4;
-  const size_t wbuf = (size_t)PL * 3 * RC * 128 + PL * g1p;
+  const size_t fixed = 1024 + (size_t)PL * 2 * (2 * KM * 128) + PL * a4;
+  const size_t wbuf = (size_t)PL * nat * 3 * RC * 128 + PL * g1p;
   const size_t a2buf = (size_t)2 * 128 * RC * 2;
   const size_t budget = 225 * 1024;
   int wb = 3, na2 = 2;
@@ -1122,10 +1142,12 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
     rows += (L + 127) / 128 * 128;
   }
   struct It { int a, n0, start, K1; long long cost; };
-  std::vector<It> its, fast;
+  std::vector<It> its, fast1, fast2;
   int wb_, na2_;
   size_t smem_;
-  const bool use_fast = tcbf_layout(p, &wb_, &na2_, &smem_);
+  const bool use_f1 = tcbf_layout(p, 1, &wb_, &na2_, &smem_);
+  const bool use_f2 = tcbf_layout(p, 2, &wb_, &na2_, &smem_);
+  const int km2 = tcbf_km(p, 2);
   for (int a = 0; a < p->n2; ++a) {
     const Rate2& A = p->rates2[a];
     if (A.s == 0) continue;
@@ -1134,15 +1156,20 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
     const int start = A.lam_min / 64 * 64;
     const int K1 = (p->n1 - start + 31) / 32 * 32;
     for (int n0 = 0; n0 < A.L; n0 += 128) {
-      if (K1f <= 64 && use_fast) fast.push_back({a, n0, lm8, K1f, (long long)K1f});
+      if (K1f <= 64 && use_f1) fast1.push_back({a, n0, lm8, K1f, (long long)K1f});
+      else if (K1f <= km2 && use_f2) fast2.push_back({a, n0, lm8, K1f, (long long)K1f});
       else its.push_back({a, n0, start, K1, (long long)K1});
     }
   }
-  std::stable_sort(fast.begin(), fast.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+  auto by_cost = [](const It& x, const It& y) { return x.cost > y.cost; };
+  std::stable_sort(fast1.begin(), fast1.end(), by_cost);
+  std::stable_sort(fast2.begin(), fast2.end(), by_cost);
   p->tcbf_items.clear();
-  for (auto& i : fast) {
-    p->tcbf_items.push_back(i.a); p->tcbf_items.push_back(i.n0); p->tcbf_items.push_back(i.start); p->tcbf_items.push_back(i.K1);
-  }
+  for (auto* v : {&fast1, &fast2})
+    for (auto& i : *v) {
+      p->tcbf_items.push_back(i.a); p->tcbf_items.push_back(i.n0); p->tcbf_items.push_back(i.start); p->tcbf_items.push_back(i.K1);
+    }
+  p->tcbf_n1 = (int)fast1.size();
   // items whose Y^T tile fits the resident three-pass form (K1 <= 96) first, longest first
   std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) {
     const bool rx = x.K1 <= 96, ry = y.K1 <= 96;
@@ -1284,9 +1311,13 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     maps.g1[h] = mg1[h];
     maps.wt[h] = mwt[h];
   }
-  // fast form for the rates with K1 <= 64, 64-row chunks
-  if (!p->tcbf_items.empty()) {
-    const int PLf = three ? 2 : 1, RCf = 64;
+  // fast form: the K1 <= 64 items (one lambda' atom, 64-row chunks), then the K1 <= KM items
+  // (two atoms, 32-row chunks)
+  for (int nat = 1; nat <= 2; ++nat) {
+    const int first = nat == 1 ? 0 : p->tcbf_n1;
+    const int count = nat == 1 ? p->tcbf_n1 : (int)(p->tcbf_items.size() / 4) - p->tcbf_n1;
+    if (count <= 0) continue;
+    const int PLf = three ? 2 : 1, RCf = nat == 1 ? 64 : 32;
     TfMaps fm;
     for (int pl = 0; pl < 6; ++pl) {
       cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)rows};
@@ -1310,14 +1341,14 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     }
     int wb = 0, na2 = 0;
     size_t smem = 0;
-    if (!tcbf_layout(p, &wb, &na2, &smem)) {
+    if (!tcbf_layout(p, nat, &wb, &na2, &smem)) {
       set_error("tensor-core backward: no shared-memory layout for the fast form");
       return JTFS_ERR_UNSUPPORTED;
     }
     TfArgs fa;
-    fa.items = reinterpret_cast<const int4*>(p->d_tcbf_items);
-    fa.n_base = (int)(p->tcbf_items.size() / 4);
-    fa.n_items = fa.n_base * B;
+    fa.items = reinterpret_cast<const int4*>(p->d_tcbf_items) + first;
+    fa.n_base = count;
+    fa.n_items = count * B;
     fa.n_chunks = (rows + RCf - 1) / RCf;
     fa.g1_rows = g1_rows;
     fa.wbufs = wb;
@@ -1326,23 +1357,26 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     fa.gy = gy;
     fa.err = p->d_err;
     const int grid = std::min(fa.n_items, n_sm);
-#define JTFS_LAUNCH_TCBF(NTV, RCV, PLV)                                                         \
+#define JTFS_LAUNCH_TCBF(NTV, RCV, PLV, NATV, KMV)                                              \
   do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_fast<NTV, RCV, PLV>,                \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_fast<NTV, RCV, PLV, NATV, KMV>,     \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr tcbf")) != JTFS_OK)             \
       return rc;                                                                                \
-    k_joint_bwd_fast<NTV, RCV, PLV><<<grid, kFThreads, smem, st>>>(fm, fa, d);                 \
+    k_joint_bwd_fast<NTV, RCV, PLV, NATV, KMV><<<grid, kFThreads, smem, st>>>(fm, fa, d);      \
   } while (0)
-    if (three) {
-      if (NT == 16) JTFS_LAUNCH_TCBF(16, 64, 2);
-      else if (NT == 32) JTFS_LAUNCH_TCBF(32, 64, 2);
-      else JTFS_LAUNCH_TCBF(64, 64, 2);
+#define JTFS_LAUNCH_TCBF_NT(RCV, PLV, NATV, KMV)                                                \
+  do {                                                                                          \
+    if (NT == 16) JTFS_LAUNCH_TCBF(16, RCV, PLV, NATV, KMV);                                    \
+    else if (NT == 32) JTFS_LAUNCH_TCBF(32, RCV, PLV, NATV, KMV);                               \
+    else JTFS_LAUNCH_TCBF(64, RCV, PLV, NATV, KMV);                                             \
+  } while (0)
+    if (nat == 1) {
+      if (three) JTFS_LAUNCH_TCBF_NT(64, 2, 1, 64); else JTFS_LAUNCH_TCBF_NT(64, 1, 1, 64);
     } else {
-      if (NT == 16) JTFS_LAUNCH_TCBF(16, 64, 1);
-      else if (NT == 32) JTFS_LAUNCH_TCBF(32, 64, 1);
-      else JTFS_LAUNCH_TCBF(64, 64, 1);
+      if (three) JTFS_LAUNCH_TCBF_NT(32, 2, 2, 96); else JTFS_LAUNCH_TCBF_NT(32, 1, 2, 128);
     }
+#undef JTFS_LAUNCH_TCBF_NT
 #undef JTFS_LAUNCH_TCBF
     if ((rc = cuda_check(cudaGetLastError(), "k_joint_bwd_fast")) != JTFS_OK) return rc;
   }
