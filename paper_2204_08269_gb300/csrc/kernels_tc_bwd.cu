@@ -717,7 +717,10 @@ struct TfArgs {
   int* err;
 };
 
-constexpr int kFThreads = 32 * 18;   // warp 0 TMA, warp 1 MMA, warps 2..17 epilogue
+// warp 0 TMA, warp 1 first-product MMAs (TMEM owner), warps 2..17 epilogue, warp 18
+// last-product MMAs
+constexpr int kFWarpG2 = 18;
+constexpr int kFThreads = 32 * 19;
 
 __device__ __forceinline__ float rsqrt_approx(float x) {
   float r;
@@ -763,7 +766,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
   uint8_t* sA2 = sW + WB * kWBuf;                          // NA2 buffers
 
   __shared__ uint64_t a1_full, a1_free, w_full[3], w_empty[3], d1_full[2], d1_free[2],
-      a2_full[2], a2_free[2], d2_full, d2_free, mma_done;
+      a2_full[2], a2_free[2], d2_full, d2_free, mma_done, mma_done2;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -784,6 +787,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
     mbar_init(&d2_full, 1);
     mbar_init(&d2_free, 16);
     mbar_init(&mma_done, 1);
+    mbar_init(&mma_done2, 1);
     fence_barrier_init();
   }
   if (warp == 1) {
@@ -853,14 +857,14 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
       if (armed_a1 >= 0) mbar_wait(&a1_full, (uint32_t)armed_a1, kWaitNs);
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+    // ------------------------------------------------------------ first-product issuer
+    // Z^T and g|Z|^T of every chunk, up to two chunks ahead of the epilogue
     if (lane == 0) {
       const uint32_t id1 = instr_desc(128, 2 * RC, 1, 1, 1, 0, 0);
       const uint32_t id4 = instr_desc(128, RC, 1, 1, 0, 0, 0);
-      const uint32_t id2 = instr_desc(128, 128, 1, 1, 0, 1, 0);
-      uint32_t a1_ph = 0, d2f_ph = 0, wph = 0;
-      uint32_t d1f_ph = 0, a2_ph = 0;   // bit i: phase of buffer i
-      int wst = 0, buf = 0, q2 = 0;
+      uint32_t a1_ph = 0, wph = 0;
+      uint32_t d1f_ph = 0;   // bit i: phase of buffer i
+      int wst = 0, buf = 0;
       bool ok = true;
       for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it % args.n_base];
@@ -868,80 +872,87 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
         if (!mbar_wait(&a1_full, a1_ph, kWaitNs)) { fail(63); break; }
         a1_ph ^= 1;
         const uint32_t a1 = smem_u32(sA1), a4 = smem_u32(sA4);
-        int prev_wst = 0, prev_q2 = 0;
-        bool first_d2 = true;
-        for (int j = 0; j <= args.n_chunks && ok; ++j) {
-          if (j < args.n_chunks) {
-            if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(64); ok = false; break; }
-            if (!mbar_wait(&d1_free[buf], ((d1f_ph >> buf) & 1) ^ 1, kWaitNs)) { fail(65); ok = false; break; }
-            d1f_ph ^= 1u << buf;
-            tc_fence_after();
-            const uint32_t wb = smem_u32(sW + wst * kWBuf);
-            const uint32_t t_d1 = tbase + buf * 3 * RC, t_d4 = t_d1 + 2 * RC;
-            for (int ks = 0; ks < nks1; ++ks) {
-              for (int q = 0; q < npair; ++q) {
-                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-                const uint64_t ayr = smem_desc(a1 + (pa * 2 + 0) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
-                const uint64_t ayi = smem_desc(a1 + (pa * 2 + 1) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
-                const uint32_t wpl = wb + (pb * NAT + (ks >> 2)) * 3 * kWBlk + (ks & 3) * 32;
-                const uint32_t f = (ks | q) ? 1u : 0u;
-                mma_f16(t_d1, ayr, smem_desc(wpl + kWBlk, 16, 1024, kSw128), id1, f);   // Yr [Wr; Wi]
-                mma_f16(t_d1, ayi, smem_desc(wpl, 16, 1024, kSw128), id1, 1u);          // Yi [-Wi; Wr]
-              }
+        for (int j = 0; j < args.n_chunks && ok; ++j) {
+          if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(64); ok = false; break; }
+          if (!mbar_wait(&d1_free[buf], ((d1f_ph >> buf) & 1) ^ 1, kWaitNs)) { fail(65); ok = false; break; }
+          d1f_ph ^= 1u << buf;
+          tc_fence_after();
+          const uint32_t wb = smem_u32(sW + wst * kWBuf);
+          const uint32_t t_d1 = tbase + buf * 3 * RC, t_d4 = t_d1 + 2 * RC;
+          for (int ks = 0; ks < nks1; ++ks) {
+            for (int q = 0; q < npair; ++q) {
+              const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+              const uint64_t ayr = smem_desc(a1 + (pa * 2 + 0) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
+              const uint64_t ayi = smem_desc(a1 + (pa * 2 + 1) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
+              const uint32_t wpl = wb + (pb * NAT + (ks >> 2)) * 3 * kWBlk + (ks & 3) * 32;
+              const uint32_t f = (ks | q) ? 1u : 0u;
+              mma_f16(t_d1, ayr, smem_desc(wpl + kWBlk, 16, 1024, kSw128), id1, f);   // Yr [Wr; Wi]
+              mma_f16(t_d1, ayi, smem_desc(wpl, 16, 1024, kSw128), id1, 1u);          // Yi [-Wi; Wr]
             }
-            const uint32_t g1 = wb + PL * NAT * 3 * kWBlk;
-            for (int ks = 0; ks < NT / 16; ++ks)
-              for (int q = 0; q < npair; ++q) {
-                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-                mma_f16(t_d4, smem_desc(a4 + pa * kA4Plane + ks * 32, 16, 8 * kSw, kLayNT),
-                        smem_desc(g1 + pb * kG1Plane + ks * 32, 16, 8 * kSw, kLayNT), id4,
-                        (ks | q) ? 1u : 0u);
-              }
-            mma_commit(&d1_full[buf]);
           }
-          if (j >= 1) {
-            // gY^T [Im | Re] += gZi [Wr | Wi] + gZr [-Wi | Wr] for chunk j - 1
-            if (!mbar_wait(&a2_full[prev_q2], (a2_ph >> prev_q2) & 1, kWaitNs)) { fail(66); ok = false; break; }
-            a2_ph ^= 1u << prev_q2;
-            if (first_d2) {
-              if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(67); ok = false; break; }
-              d2f_ph ^= 1;
+          const uint32_t g1 = wb + PL * NAT * 3 * kWBlk;
+          for (int ks = 0; ks < NT / 16; ++ks)
+            for (int q = 0; q < npair; ++q) {
+              const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+              mma_f16(t_d4, smem_desc(a4 + pa * kA4Plane + ks * 32, 16, 8 * kSw, kLayNT),
+                      smem_desc(g1 + pb * kG1Plane + ks * 32, 16, 8 * kSw, kLayNT), id4,
+                      (ks | q) ? 1u : 0u);
             }
-            tc_fence_after();
-            const uint32_t wb = smem_u32(sW + prev_wst * kWBuf);
-            const uint32_t a2 = smem_u32(sA2 + prev_q2 * kA2Buf);
-            for (int ks = 0; ks < RC / 16; ++ks) {
-              const uint64_t agr = smem_desc(a2 + ks * 32, 16, kA2Sbo, kA2Lay);
-              const uint64_t agi = smem_desc(a2 + kA2Part + ks * 32, 16, kA2Sbo, kA2Lay);
-              for (int q = 0; q < PL; ++q) {                      // W_hi, then W_lo
-                const uint32_t f = (first_d2 && ks == 0 && q == 0) ? 0u : 1u;
-                for (int k = 0; k < NAT; ++k) {
-                  const uint32_t wpl = wb + (q * NAT + k) * 3 * kWBlk + ks * 2048;
-                  mma_f16(t_d2 + 128 * k, agi, smem_desc(wpl + kWBlk, kWBlk, 1024, kSw128), id2, f);   // gZi [Wr | Wi]
-                  mma_f16(t_d2 + 128 * k, agr, smem_desc(wpl, kWBlk, 1024, kSw128), id2, 1u);          // gZr [-Wi | Wr]
-                }
-              }
-            }
-            first_d2 = false;
-            mma_commit(&a2_free[prev_q2]);
-            mma_commit(&w_empty[prev_wst]);
-          }
-          if (j < args.n_chunks) {
-            prev_wst = wst;
-            prev_q2 = q2;
-            if (++wst == WB) { wst = 0; wph ^= 1; }
-            buf ^= 1;
-            if (++q2 == NA2) q2 = 0;
-          }
+          mma_commit(&d1_full[buf]);
+          if (++wst == WB) { wst = 0; wph ^= 1; }
+          buf ^= 1;
         }
         if (!ok) break;
         mma_commit(&a1_free);
-        mma_commit(&d2_full);
       }
       mma_commit(&mma_done);
       mbar_wait(&mma_done, 0, kWaitNs);
     }
-  } else {
+  } else if (warp == kFWarpG2) {
+    // ------------------------------------------------------------ last-product issuer
+    // gY^T [Im | Re] += gZi [Wr | Wi] + gZr [-Wi | Wr], chunk by chunk behind the epilogue;
+    // releases each W chunk (its first product completed before the epilogue ran)
+    if (lane == 0) {
+      const uint32_t id2 = instr_desc(128, 128, 1, 1, 0, 1, 0);
+      uint32_t d2f_ph = 0, wph = 0, a2_ph = 0;   // a2_ph bit i: phase of buffer i
+      int wst = 0, q2 = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        for (int j = 0; j < args.n_chunks && ok; ++j) {
+          if (!mbar_wait(&a2_full[q2], (a2_ph >> q2) & 1, kWaitNs)) { fail(66); ok = false; break; }
+          a2_ph ^= 1u << q2;
+          if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(71); ok = false; break; }
+          if (j == 0) {
+            if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(67); ok = false; break; }
+            d2f_ph ^= 1;
+          }
+          tc_fence_after();
+          const uint32_t wb = smem_u32(sW + wst * kWBuf);
+          const uint32_t a2 = smem_u32(sA2 + q2 * kA2Buf);
+          for (int ks = 0; ks < RC / 16; ++ks) {
+            const uint64_t agr = smem_desc(a2 + ks * 32, 16, kA2Sbo, kA2Lay);
+            const uint64_t agi = smem_desc(a2 + kA2Part + ks * 32, 16, kA2Sbo, kA2Lay);
+            for (int q = 0; q < PL; ++q) {                      // W_hi, then W_lo
+              const uint32_t f = (j == 0 && ks == 0 && q == 0) ? 0u : 1u;
+              for (int k = 0; k < NAT; ++k) {
+                const uint32_t wpl = wb + (q * NAT + k) * 3 * kWBlk + ks * 2048;
+                mma_f16(t_d2 + 128 * k, agi, smem_desc(wpl + kWBlk, kWBlk, 1024, kSw128), id2, f);   // gZi [Wr | Wi]
+                mma_f16(t_d2 + 128 * k, agr, smem_desc(wpl, kWBlk, 1024, kSw128), id2, 1u);          // gZr [-Wi | Wr]
+              }
+            }
+          }
+          mma_commit(&a2_free[q2]);
+          mma_commit(&w_empty[wst]);
+          if (++wst == WB) { wst = 0; wph ^= 1; }
+          if (++q2 == NA2) q2 = 0;
+        }
+        if (!ok) break;
+        mma_commit(&d2_full);
+      }
+      mma_commit(&mma_done2);
+      mbar_wait(&mma_done2, 0, kWaitNs);
+    }
+  } else if (warp >= 2 && warp < 2 + 16) {
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;                   // 0..15
     const int quarter = warp & 3;
