@@ -332,6 +332,15 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
     const double ang = 2.0 * M_PI * (double)j / (double)N;
     tw[j] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
   }
+  // per-length half tables, L = 2^l for 1 <= l <= log2 N, packed back to back
+  std::vector<float2> twl(std::max<long long>(1, N - 1));
+  for (int l = 1; (1LL << l) <= N; ++l) {
+    const long long L = 1LL << l, o = (L >> 1) - 1;
+    for (long long m = 0; m < (L >> 1); ++m) {
+      const double ang = 2.0 * M_PI * (double)m / (double)L;
+      twl[o + m] = make_float2((float)std::cos(ang), (float)-std::sin(ang));
+    }
+  }
   // layout of one device allocation
   size_t off = 0;
   auto place = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
@@ -343,6 +352,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   const size_t o_phiF = place(sizeof(float) * p->N_fr);
   const size_t o_h = place(sizeof(float2) * (size_t)p->C * p->N_fr);
   const size_t o_tw = place(sizeof(float2) * N);
+  const size_t o_twl = place(sizeof(float2) * twl.size());
   const size_t o_gx = place(sizeof(int2) * nblk);
   const size_t o_pairs = place(sizeof(int) * std::max<size_t>(2, p->pairs.size()));
   const size_t o_items = place(sizeof(int) * std::max<size_t>(2, p->items.size()));
@@ -358,6 +368,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   d.phiF = (const float*)(base + o_phiF);
   d.h = (const float2*)(base + o_h);
   d.tw = (const float2*)(base + o_tw);
+  d.twl = (const float2*)(base + o_twl);
   d.gx_lam = (const int2*)(base + o_gx);
   p->d_pairs = (int*)(base + o_pairs);
   p->d_items = (int*)(base + o_items);
@@ -366,6 +377,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
       {o_rows, p->rows1.data(), sizeof(Row1) * p->n1},
       {o_rates, p->rates2.data(), sizeof(Rate2) * p->n2},
       {o_tw, tw.data(), sizeof(float2) * N},
+      {o_twl, twl.data(), sizeof(float2) * twl.size()},
       {o_gx, gxl.data(), sizeof(int2) * nblk},
       {o_pairs, p->pairs.data(), sizeof(int) * p->pairs.size()},
       {o_items, p->items.data(), sizeof(int) * p->items.size()},

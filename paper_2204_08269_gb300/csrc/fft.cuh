@@ -128,7 +128,7 @@ __device__ void fft_dit_rows(float2* buf, int logL, int G, const float2* __restr
   if (logL & 1) {
     const int per = L >> 1;
     for (int b = threadIdx.x; b < G * per; b += blockDim.x) {
-      const int i0 = (b / per) * L + ((b % per) << 1);
+      const int i0 = ((b >> (logL - 1)) << logL) + ((b & (per - 1)) << 1);
       const float2 a = buf[i0], c = buf[i0 + 1];
       buf[i0] = make_float2(a.x + c.x, a.y + c.y);
       buf[i0 + 1] = make_float2(a.x - c.x, a.y - c.y);
@@ -142,9 +142,9 @@ __device__ void fft_dit_rows(float2* buf, int logL, int G, const float2* __restr
     const int sh1 = logTW - s;
     const int sh2 = logTW - s - 1;
     for (int bb = threadIdx.x; bb < G * per; bb += blockDim.x) {
-      const int row = bb / per, b = bb % per;
+      const int row = bb >> (logL - 2), b = bb & (per - 1);
       const int j = b & (q - 1);
-      const int base = row * L + (((b >> (s - 1)) << (s + 1)) | j);
+      const int base = (row << logL) + (((b >> (s - 1)) << (s + 1)) | j);
       float2 x0 = buf[base], x1 = buf[base + q], x2 = buf[base + 2 * q], x3 = buf[base + 3 * q];
       const float2 w1 = twiddle<SIGN>(tw, j << sh1);
       float2 t = cmul(x1, w1);
@@ -175,9 +175,9 @@ __device__ void fft_dif_rows(float2* buf, int logL, int G, const float2* __restr
     const int sh1 = logTW - s;
     const int sh2 = logTW - s + 1;
     for (int bb = threadIdx.x; bb < G * per; bb += blockDim.x) {
-      const int row = bb / per, b = bb % per;
+      const int row = bb >> (logL - 2), b = bb & (per - 1);
       const int j = b & (q - 1);
-      const int base = row * L + (((b >> (s - 2)) << s) | j);
+      const int base = (row << logL) + (((b >> (s - 2)) << s) | j);
       float2 x0 = buf[base], x1 = buf[base + q], x2 = buf[base + 2 * q], x3 = buf[base + 3 * q];
       const float2 w1 = twiddle<SIGN>(tw, j << sh1);
       const float2 w1b = twiddle<SIGN>(tw, (j + q) << sh1);
@@ -196,7 +196,7 @@ __device__ void fft_dif_rows(float2* buf, int logL, int G, const float2* __restr
   if (s == 1) {
     const int per2 = L >> 1;
     for (int b = threadIdx.x; b < G * per2; b += blockDim.x) {
-      const int i0 = (b / per2) * L + ((b % per2) << 1);
+      const int i0 = ((b >> (logL - 1)) << logL) + ((b & (per2 - 1)) << 1);
       const float2 a = buf[i0], c = buf[i0 + 1];
       buf[i0] = make_float2(a.x + c.x, a.y + c.y);
       buf[i0 + 1] = make_float2(a.x - c.x, a.y - c.y);

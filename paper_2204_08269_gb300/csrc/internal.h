@@ -52,8 +52,15 @@ struct DevPlan {
   const float* phiF;      // [N_fr] phi_F[m]
   const float2* h;        // [C][N_fr] log-frequency filters h_c[m]
   const float2* tw;       // [TW] exp(-2 pi i j / TW)
+  const float2* twl;      // per-length tables: for L = 2^l, entries [2^(l-1) - 1, 2^l - 1) hold
+                          // exp(-2 pi i m / L), m < L / 2 (contiguous reads in every stage)
   const int2* gx_lam;     // [N/2 / 256] lambda range touching each 256-bin block of x-hat
 };
+
+// Twiddles of the length-2^logL FFT (half table, exp(-2 pi i m / L) for m < L / 2).
+__host__ __device__ inline const float2* twl_for(const DevPlan& P, int logL) {
+  return P.twl + ((logL > 0 ? (1 << (logL - 1)) : 1) - 1);
+}
 
 }  // namespace jtfs
 

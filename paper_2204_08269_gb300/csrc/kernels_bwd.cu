@@ -25,7 +25,7 @@ k_uh_from_u1(DevPlan P, const float* __restrict__ u1, float2* __restrict__ uh) {
   const float* ub = u1 + (size_t)b * P.u1_len + R.off_u;
   for (int m = threadIdx.x; m < R.L; m += blockDim.x) sm[m] = make_float2(ub[m], 0.f);
   __syncthreads();
-  fft_dif<-1>(sm, R.logL, P.tw, P.logTW);
+  fft_dif<-1>(sm, R.logL, twl_for(P, R.logL), R.logL);
   float2* hb = uh + (size_t)b * P.uh_len + R.off_uh;
   for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[bitrev(k, R.logL)];
 }
@@ -177,7 +177,7 @@ k_second_order_bwd(DevPlan P, const float2* __restrict__ gy, const float* __rest
     const float2* g = gy + (size_t)b * P.y_len + A.off_y + (size_t)(lam - A.lam_min) * A.L;
     for (int m = threadIdx.x; m < A.L; m += blockDim.x) tmp[m] = g[m];
     __syncthreads();
-    fft_dif<-1>(tmp, A.logL, P.tw, P.logTW);
+    fft_dif<-1>(tmp, A.logL, twl_for(P, A.logL), A.logL);
     const float* psi = P.psi2 + (size_t)a * P.K2max;
     const int kend = min(half, A.k2e);
     for (int k = 1 + threadIdx.x; k < kend; k += blockDim.x) {
@@ -191,7 +191,7 @@ k_second_order_bwd(DevPlan P, const float2* __restrict__ gy, const float* __rest
   for (int k = threadIdx.x; k < R.L; k += blockDim.x)
     tmp[bitrev(k, R.logL)] = (k < half) ? guh[k] : make_float2(0.f, 0.f);
   __syncthreads();
-  fft_dit<+1>(tmp, R.logL, P.tw, P.logTW);
+  fft_dit<+1>(tmp, R.logL, twl_for(P, R.logL), R.logL);
   const float* g1 = gs1 ? gs1 + ((size_t)b * P.n1 + lam) * P.n_t : nullptr;
   float* out = gu1 + (size_t)b * P.u1_len + R.off_u;
   for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
@@ -213,7 +213,7 @@ k_stage1_bwd(DevPlan P, const float2* __restrict__ xh, const float* __restrict__
   const Row1 R = P.rows1[lam];
   fold_first_order(P, R, xh + (size_t)b * (P.N >> 1), sm);
   __syncthreads();
-  fft_dit<+1>(sm, R.logL, P.tw, P.logTW);
+  fft_dit<+1>(sm, R.logL, twl_for(P, R.logL), R.logL);
   const float* g = gu1 + (size_t)b * P.u1_len + R.off_u;
   for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
     const float2 z = sm[m];  // N * z
@@ -222,7 +222,7 @@ k_stage1_bwd(DevPlan P, const float2* __restrict__ xh, const float* __restrict__
     sm[m] = make_float2(z.x * f, z.y * f);
   }
   __syncthreads();
-  fft_dif<-1>(sm, R.logL, P.tw, P.logTW);
+  fft_dif<-1>(sm, R.logL, twl_for(P, R.logL), R.logL);
   const float invN = 1.f / (float)P.N;
   float2* out = gf + (size_t)b * P.u1_len + R.off_u;
   for (int k = threadIdx.x; k < R.L; k += blockDim.x) {
@@ -275,7 +275,7 @@ k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, f
     sm[bitrev(kp, P.logM)] = acc;
   }
   __syncthreads();
-  fft_dit<+1>(sm, P.logM, P.tw, P.logTW);
+  fft_dit<+1>(sm, P.logM, twl_for(P, P.logM), P.logM);
   const float* g0 = gs0 ? gs0 + (size_t)b * P.n_t : nullptr;
   float* out = gx + (size_t)b * P.N;
   for (int m = threadIdx.x; m < P.M; m += blockDim.x) {
@@ -294,11 +294,16 @@ jtfs_status set_attrs() {
   const int big = 227 * 1024;
   const void* fns[] = {(const void*)k_uh_from_u1, (const void*)k_joint_bwd_simt,
                        (const void*)k_second_order_bwd, (const void*)k_stage1_bwd,
-                       (const void*)k_gx, (const void*)k_xfft_sub, (const void*)k_second_order_rows<0>,
-                       (const void*)k_second_order_rows<1>};
+                       (const void*)k_gx, (const void*)k_xfft_sub};
   for (const void* f : fns) {
     jtfs_status st = cuda_check(
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr");
+    if (st != JTFS_OK) return st;
+  }
+  // the row producer holds at most 2^14 complex samples next to its static row tables
+  for (const void* f : {(const void*)k_second_order_rows<0>, (const void*)k_second_order_rows<1>}) {
+    jtfs_status st = cuda_check(
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024), "attr");
     if (st != JTFS_OK) return st;
   }
   g_attrs_set = true;

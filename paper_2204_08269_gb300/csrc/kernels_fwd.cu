@@ -48,7 +48,7 @@ k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
   float* su = reinterpret_cast<float*>(sm + R.L);
   fold_first_order(P, R, xh + (size_t)b * (P.N >> 1), sm);
   __syncthreads();
-  fft_dit<+1>(sm, R.logL, P.tw, P.logTW);
+  fft_dit<+1>(sm, R.logL, twl_for(P, R.logL), R.logL);
   const float invN = 1.f / (float)P.N;
   float* ub = u1 + (size_t)b * P.u1_len + R.off_u;
   for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
@@ -70,7 +70,7 @@ k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
       if (l == 0) s1[((size_t)b * P.n1 + lam) * P.n_t + t] = acc * (float)R.s;
     }
   }
-  fft_dif<-1>(sm, R.logL, P.tw, P.logTW);
+  fft_dif<-1>(sm, R.logL, twl_for(P, R.logL), R.logL);
   float2* hb = uh + (size_t)b * P.uh_len + R.off_uh;
   for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[bitrev(k, R.logL)];
 }
@@ -202,8 +202,10 @@ jtfs_status set_attrs(const jtfs_plan* p) {
   jtfs_status st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_xfft_sub, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_scalogram, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
-  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
-  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
+  // the row producer holds at most 2^14 complex samples next to its static row tables
+  const int rows_smem = 128 * 1024;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_joint_fwd_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
   g_attrs_set = true;
   return JTFS_OK;

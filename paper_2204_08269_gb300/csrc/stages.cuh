@@ -22,7 +22,7 @@ k_xfft_sub(DevPlan P, const float* __restrict__ x, float2* __restrict__ xsub) {
   for (int m = threadIdx.x; m < P.M; m += blockDim.x)
     sm[m] = make_float2(__ldg(&xb[r + (size_t)P.D * m]), 0.f);
   __syncthreads();
-  fft_dif<-1>(sm, P.logM, P.tw, P.logTW);
+  fft_dif<-1>(sm, P.logM, twl_for(P, P.logM), P.logM);
   float2* out = xsub + ((size_t)b * P.D + r) * P.M;
   for (int k = threadIdx.x; k < P.M; k += blockDim.x) out[k] = sm[bitrev(k, P.logM)];
 }
@@ -72,6 +72,7 @@ __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R
 // [alpha][2 b + part][lambda' - lam_min][n].  The fold only visits bins below the rate's
 // psi-hat support end.
 constexpr int kRowThreads = 256;
+constexpr int kMaxRowsPerItem = 512;   // G <= rows_cap / 32
 
 template <int OUT_BF16>
 __global__ void __launch_bounds__(kRowThreads)
@@ -79,17 +80,25 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
                     float2* __restrict__ y, __nv_bfloat16* __restrict__ yhi,
                     __nv_bfloat16* __restrict__ ylo, int B) {
   extern __shared__ float2 sm[];
+  __shared__ int s_off[kMaxRowsPerItem], s_kend[kMaxRowsPerItem];
+  __shared__ float s_inv[kMaxRowsPerItem];
   const int4 it = items[blockIdx.x];
   const int a = it.x, lam0 = it.y, G = it.z, b = blockIdx.y;
   const Rate2 A = P.rates2[a];
   const float* psi = P.psi2 + (size_t)a * P.K2max;
   const int L = A.L, logL = A.logL;
   const float2* ub = uh + (size_t)b * P.uh_len;
+  for (int r = threadIdx.x; r < G; r += blockDim.x) {
+    const Row1 R = P.rows1[lam0 + r];
+    s_off[r] = R.off_uh;
+    s_kend[r] = min(R.L >> 1, A.k2e);
+    s_inv[r] = 1.f / (float)R.L;
+  }
+  __syncthreads();
   for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
     const int row = idx >> logL, kp = idx & (L - 1);
-    const Row1 R = P.rows1[lam0 + row];
-    const float2* ur = ub + R.off_uh;
-    const int kend = min(R.L >> 1, A.k2e);
+    const float2* ur = ub + s_off[row];
+    const int kend = s_kend[row];
     float2 acc = make_float2(0.f, 0.f);
     for (int k = kp; k < kend; k += L) {
       const float2 u = ur[k];
@@ -100,11 +109,11 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
     sm[(row << logL) + bitrev(kp, logL)] = acc;
   }
   __syncthreads();
-  fft_dit_rows<+1>(sm, logL, G, P.tw, P.logTW);
+  fft_dit_rows<+1>(sm, logL, G, twl_for(P, logL), logL);
   if (!OUT_BF16) {
     float2* ya = y + (size_t)b * P.y_len + A.off_y + (size_t)(lam0 - A.lam_min) * L;
     for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
-      const float inv = 1.f / (float)P.rows1[lam0 + (idx >> logL)].L;
+      const float inv = s_inv[idx >> logL];
       const float2 v = sm[idx];
       ya[idx] = make_float2(v.x * inv, v.y * inv);
     }
@@ -115,7 +124,7 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
     const size_t base = (size_t)B * 2 * A.off_y + (size_t)(2 * b) * plane + (size_t)(lam0 - A.lam_min) * L;
     for (int i2 = threadIdx.x; i2 < (G * L) >> 1; i2 += blockDim.x) {
       const int idx = 2 * i2;
-      const float inv = 1.f / (float)P.rows1[lam0 + (idx >> logL)].L;
+      const float inv = s_inv[idx >> logL];
       const float2 v0 = sm[idx], v1 = sm[idx + 1];
       const float r0 = v0.x * inv, r1 = v1.x * inv, i0 = v0.y * inv, i1 = v1.y * inv;
       const __nv_bfloat162 hr = __floats2bfloat162_rn(r0, r1), hi_ = __floats2bfloat162_rn(i0, i1);
