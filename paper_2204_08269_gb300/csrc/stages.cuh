@@ -71,7 +71,7 @@ __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R
 // (OUT_BF16 = 0) or BF16 planes hi (and lo when ylo is given) in the contraction layout
 // [alpha][2 b + part][lambda' - lam_min][n].  The fold only visits bins below the rate's
 // psi-hat support end.
-constexpr int kRowThreads = 256;
+constexpr int kRowThreads = 512;
 constexpr int kMaxRowsPerItem = 512;   // G <= rows_cap / 32
 
 template <int OUT_BF16>
