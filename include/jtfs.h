@@ -147,6 +147,53 @@ const char* jtfs_profile_stage_name(int32_t i);
 jtfs_status jtfs_first_order_static(const jtfs_plan* plan, const float* x, int64_t B, float* s0,
                                     float* s1, void* stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Uneven-length batches.  The paper transforms one signal length at a time; these calls take
+ * B signals of lengths len[i] packed back to back (x_packed[x_off[i] .. x_off[i] + len[i])).
+ * Signal i is zero-padded to N_i = jtfs_varlen_padded_length(cfg, len[i]) =
+ * max(2^ceil(log2 len[i]), 2^(J+3)) and transformed with the plan of length N_i (built by
+ * jtfs_varlen_create, periodic in time on N_i like every fixed-length transform); its outputs
+ * keep the first frames_i = ceil(len[i] / T) frames:
+ *   S0 packed [s0_off[i] ..) as [frames_i], S1 as [n1(N_i), frames_i],
+ *   S2 as [n2(N_i), C, n_lam_out, frames_i]  (n1, n2, C, n_lam_out of the plan of N_i).
+ * Cotangents use the same packed layouts; g_x the layout of x (first len[i] samples). */
+typedef struct jtfs_varlen jtfs_varlen;
+
+/* N_i for one length (0 for an invalid argument).  Host only. */
+int64_t jtfs_varlen_padded_length(const jtfs_config* cfg, int64_t len);
+
+/* Groups the signals by N_i, builds one plan per distinct N_i (synchronous, current device)
+ * and splits each group into sub-batches of at most `chunk` signals (0: 64).  len is a host
+ * array of B lengths in [1, 2^24].  Errors as jtfs_plan_create, INVALID_ARG. */
+jtfs_status jtfs_varlen_create(const jtfs_config* cfg, const int64_t* len, int64_t B,
+                               int32_t chunk, jtfs_varlen** out);
+void jtfs_varlen_destroy(jtfs_varlen* v);
+
+/* Packed offsets (host arrays of B + 1 entries; any may be NULL): x / g_x, S0, S1, S2.  The
+ * last entry of each is the total length in floats. */
+jtfs_status jtfs_varlen_layout(const jtfs_varlen* v, int64_t* x_off, int64_t* s0_off,
+                               int64_t* s1_off, int64_t* s2_off);
+
+/* Device workspace for jtfs_varlen_forward_backward / jtfs_varlen_capture (the largest
+ * sub-batch's padded buffers plus its plan workspace; sub-batches run one after another). */
+jtfs_status jtfs_varlen_workspace_bytes(const jtfs_varlen* v, size_t* out);
+
+/* Forward and backward of every signal (device buffers, packed layouts above; cotangents may
+ * be NULL for zero).  Per signal the results equal jtfs_forward / jtfs_backward of its
+ * zero-padded copy, restricted to the kept frames and to its first len[i] samples. */
+jtfs_status jtfs_varlen_forward_backward(const jtfs_varlen* v, const float* x_packed,
+                                         const float* g_s0, const float* g_s1, const float* g_s2,
+                                         float* s0, float* s1, float* s2, float* g_x, void* ws,
+                                         size_t ws_bytes, void* stream);
+
+/* Runs jtfs_varlen_forward_backward once on `stream` (a non-default stream), then captures it
+ * into a CUDA graph owned by v (replacing an earlier one).  The graph keeps these buffer
+ * addresses: jtfs_varlen_replay recomputes the step from whatever the buffers then hold. */
+jtfs_status jtfs_varlen_capture(jtfs_varlen* v, const float* x_packed, const float* g_s0,
+                                const float* g_s1, const float* g_s2, float* s0, float* s1,
+                                float* s2, float* g_x, void* ws, size_t ws_bytes, void* stream);
+jtfs_status jtfs_varlen_replay(const jtfs_varlen* v, void* stream);
+
 /* Waits for the stream and reports any pending device error. */
 jtfs_status jtfs_sync_status(const jtfs_plan* plan, void* stream);
 

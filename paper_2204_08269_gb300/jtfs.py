@@ -65,6 +65,14 @@ def lib():
         "jtfs_profile_read": ([_P, _P, _I32, ctypes.POINTER(_I64)], _I32),
         "jtfs_profile_stage_name": ([_I32], ctypes.c_char_p),
         "jtfs_first_order_static": ([_P, _P, _I64, _P, _P, _P], _I32),
+        "jtfs_varlen_padded_length": ([ctypes.POINTER(_Config), _I64], _I64),
+        "jtfs_varlen_create": ([ctypes.POINTER(_Config), _P, _I64, _I32, ctypes.POINTER(_P)], _I32),
+        "jtfs_varlen_destroy": ([_P], None),
+        "jtfs_varlen_layout": ([_P, _P, _P, _P, _P], _I32),
+        "jtfs_varlen_workspace_bytes": ([_P, ctypes.POINTER(_SZ)], _I32),
+        "jtfs_varlen_forward_backward": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P], _I32),
+        "jtfs_varlen_capture": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P], _I32),
+        "jtfs_varlen_replay": ([_P, _P], _I32),
         "jtfs_status_string": ([_I32], ctypes.c_char_p),
         "jtfs_last_error": ([], ctypes.c_char_p),
     }
@@ -82,7 +90,10 @@ def exported_symbols():
             "jtfs_workspace_bytes", "jtfs_forward", "jtfs_backward", "jtfs_host_step_bytes",
             "jtfs_forward_backward_host", "jtfs_sync_status", "jtfs_status_string",
             "jtfs_last_error", "jtfs_profile_enable", "jtfs_profile_read",
-            "jtfs_profile_stage_name", "jtfs_first_order_static"]
+            "jtfs_profile_stage_name", "jtfs_first_order_static", "jtfs_varlen_padded_length",
+            "jtfs_varlen_create", "jtfs_varlen_destroy", "jtfs_varlen_layout",
+            "jtfs_varlen_workspace_bytes", "jtfs_varlen_forward_backward", "jtfs_varlen_capture",
+            "jtfs_varlen_replay"]
 
 
 class JTFSError(RuntimeError):
@@ -290,3 +301,76 @@ class JTFS(torch.nn.Module):
 
     def forward(self, x):
         return JTFSFunction.apply(x, self.plan)
+
+
+def _config(J, Q, J_fr, Q_fr, T, F, Q2=1, average_fr=True, oversampling=0, precision="fp32"):
+    return _Config(J=J, Q=Q, Q2=Q2, J_fr=J_fr, Q_fr=Q_fr, T=T, F=F,
+                   average_fr=1 if average_fr else 0, oversampling=oversampling,
+                   precision=PRECISIONS[precision])
+
+
+def varlen_padded_length(length, J, **kw):
+    """Padded length of one signal of an uneven-length batch (host only)."""
+    cfg = _config(J=J, Q=kw.pop("Q", 1), J_fr=kw.pop("J_fr", 1), Q_fr=kw.pop("Q_fr", 1),
+                  T=kw.pop("T", 1), F=kw.pop("F", 1), **kw)
+    return int(lib().jtfs_varlen_padded_length(ctypes.byref(cfg), int(length)))
+
+
+class JTFSVarlen:
+    """Uneven-length batch: signals of lengths ``lengths`` packed back to back, each
+    zero-padded to its power-of-two length and keeping ceil(len / T) frames (see jtfs.h)."""
+
+    def __init__(self, lengths, J, Q, J_fr, Q_fr, T, F, chunk=0, **kw):
+        import numpy as np
+        L = lib()
+        self._cfg = _config(J, Q, J_fr, Q_fr, T, F, **kw)
+        self.lengths = np.ascontiguousarray(np.asarray(lengths, dtype=np.int64))
+        B = len(self.lengths)
+        h = ctypes.c_void_p()
+        _check("jtfs_varlen_create", L.jtfs_varlen_create(
+            ctypes.byref(self._cfg), self.lengths.ctypes.data_as(_P), B, int(chunk),
+            ctypes.byref(h)))
+        self._h = h
+        self.B = B
+        offs = [np.zeros(B + 1, dtype=np.int64) for _ in range(4)]
+        _check("jtfs_varlen_layout", L.jtfs_varlen_layout(h, *[o.ctypes.data_as(_P) for o in offs]))
+        self.x_off, self.s0_off, self.s1_off, self.s2_off = offs
+        n = ctypes.c_size_t()
+        _check("jtfs_varlen_workspace_bytes", L.jtfs_varlen_workspace_bytes(h, ctypes.byref(n)))
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self._ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.jtfs_varlen_destroy(h)
+            self._h = None
+
+    def outputs(self):
+        dev = self.device
+        return [torch.empty(int(o[-1]), dtype=torch.float32, device=dev)
+                for o in (self.s0_off, self.s1_off, self.s2_off, self.x_off)]
+
+    def _args(self, x, g, outs):
+        g = list(g) + [None] * (3 - len(g))
+        return [_ptr(x), _ptr(g[0]), _ptr(g[1]), _ptr(g[2]), _ptr(outs[0]), _ptr(outs[1]),
+                _ptr(outs[2]), _ptr(outs[3]), _ptr(self._ws), self._ws.numel()]
+
+    def forward_backward(self, x_packed, g=(), outs=None):
+        """(S0, S1, S2, g_x) packed; g = (g_s0, g_s1, g_s2) packed cotangents (None = 0)."""
+        outs = outs or self.outputs()
+        _check("jtfs_varlen_forward_backward",
+               lib().jtfs_varlen_forward_backward(self._h, *self._args(x_packed, g, outs), _stream()))
+        return outs
+
+    def capture(self, x_packed, g=(), outs=None):
+        """Captures the step on the current (non-default) stream into a CUDA graph bound to
+        these buffers; returns the output buffers the graph writes."""
+        outs = outs or self.outputs()
+        self._bound = (x_packed, tuple(g), outs)   # keep the buffers alive
+        _check("jtfs_varlen_capture",
+               lib().jtfs_varlen_capture(self._h, *self._args(x_packed, g, outs), _stream()))
+        return outs
+
+    def replay(self):
+        _check("jtfs_varlen_replay", lib().jtfs_varlen_replay(self._h, _stream()))

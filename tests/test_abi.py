@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -65,3 +66,13 @@ def test_null_plan_calls(L):
     assert L.jtfs_workspace_bytes(None, 1, 0, ctypes.byref(n)) == 1
     assert L.jtfs_forward(None, None, 1, None, None, None, None, None, 0, None) == 1
     assert L.jtfs_backward(None, None, None, 1, None, None, None, None, None, 0, None) == 1
+
+
+def test_varlen_padded_length_rule():
+    """max(2^ceil(log2 len), 2^(J+3)), computed on the host without a GPU."""
+    from paper_2204_08269_gb300 import jtfs
+    for J in (4, 6, 12):
+        for n in (1, 2, 3, 100, 511, 512, 513, 4096, 70000):
+            want = max(1 << int(np.ceil(np.log2(n))) if n > 1 else 1, 1 << (J + 3))
+            assert jtfs.varlen_padded_length(n, J=J) == want
+    assert jtfs.varlen_padded_length(0, J=4) == 0
