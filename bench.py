@@ -7,6 +7,8 @@ cotangents.  Prints one JSON line.  Under torchrun each rank runs the same per-G
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|tf32|bf16|fp32_simt]
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
+  python bench.py --workload varlen ...  # uneven-length batch (1024 signals of 2^13-2^17
+                                         # samples) in one graph launch vs per-signal launches
 """
 from __future__ import annotations
 
@@ -302,6 +304,76 @@ def run_reference(args):
     return out
 
 
+def run_varlen(args):
+    """Uneven-length batch: J=12, Q=16, J_fr=4, Q_fr=2, T=2^12, F=16, lengths log-uniform in
+    2^13..2^17, half AM/FM tones and half click trains; forward + backward with ones as
+    cotangents.  The step is one replay of the captured graph (autotuned launch shapes); the
+    comparison is one library call per signal (B = 1) on a sample of the batch."""
+    import torch
+    from paper_2204_08269_gb300 import jtfs
+    import synth_signals as SS
+    torch.cuda.set_device(0)
+    count = args.batch if args.batch != BATCH else 1024
+    cfg = dict(J=12, Q=16, J_fr=4, Q_fr=2, T=2 ** 12, F=16)
+    xh, lengths = SS.varlen_batch(count, SS.BASE_SEED + 5)
+    v = jtfs.JTFSVarlen(lengths, **cfg, precision=args.precision, chunk=64)
+    x = torch.from_numpy(xh).cuda()
+    g = [torch.ones(int(o[-1]), device="cuda") for o in (v.s0_off, v.s1_off, v.s2_off)]
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        v.autotune()
+        v.capture(x, g)
+        for _ in range(args.warmup):
+            v.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        side.synchronize()
+        e0.record(side)
+        for _ in range(args.steps):
+            v.replay()
+        e1.record(side)
+    side.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-signal launches on a sample (every 8th signal), one plan per padded length
+    sample = list(range(0, count, 8))
+    plans = {}
+    for i in sample:
+        Np = jtfs.varlen_padded_length(int(lengths[i]), J=cfg["J"])
+        if Np not in plans:
+            plans[Np] = jtfs.JTFSPlan(N=Np, **cfg, precision=args.precision)
+    xs = []
+    for i in sample:
+        Np = jtfs.varlen_padded_length(int(lengths[i]), J=cfg["J"])
+        xi = torch.zeros((1, Np), device="cuda")
+        xi[0, :int(lengths[i])] = x[int(v.x_off[i]):int(v.x_off[i]) + int(lengths[i])]
+        xs.append((plans[Np], xi))
+
+    def per_signal():
+        for p, xi in xs:
+            s0, s1, s2, u1 = p.forward(xi)
+            p.backward(xi, u1, torch.ones_like(s0), torch.ones_like(s1), torch.ones_like(s2))
+
+    per_signal()
+    torch.cuda.synchronize()
+    e0.record()
+    per_signal()
+    e1.record()
+    torch.cuda.synchronize()
+    ms_ps = e0.elapsed_time(e1)
+    out = {"metric": "JTFS fwd+bwd signals/sec, uneven lengths 2^13-2^17 in one graph launch",
+           "value": count / (ms / 1e3), "unit": "signals/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision != "bf16" else "bf16",
+           "data": "synthetic (seeded AM/FM tones and click trains)",
+           "config": {"workload": f"varlen, {count} signals, len log-uniform 2^13..2^17, J=12, Q=16, "
+                                  "J_fr=4, Q_fr=2, T=2^12, F=16", "precision": args.precision,
+                      "padded_lengths": {str(k): int(sum(1 for n in lengths if jtfs.varlen_padded_length(int(n), J=12) == k))
+                                         for k in sorted(set(jtfs.varlen_padded_length(int(n), J=12) for n in lengths))}},
+           "per_signal_launches": {"value": len(sample) / (ms_ps / 1e3), "unit": "signals/s",
+                                   "sample": f"{len(sample)} of the {count} signals, one call per signal"}}
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,11 +385,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="signals per GPU (the workload is 64; smaller values for profiling)")
+    ap.add_argument("--workload", default="fixed", choices=["fixed", "varlen"],
+                    help="varlen: the uneven-length batch (not the headline metric)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "varlen":
+        run_varlen(args)
     else:
         run_ours(args)
 

@@ -125,6 +125,16 @@ jtfs_status jtfs_forward_backward_host(const jtfs_plan* plan, const float* x_hos
                                        size_t dev_buf_bytes, void* ws, size_t ws_bytes,
                                        void* stream);
 
+/* Autotuner of the launch shape of the largest FFT stage (the second-order time wavelets):
+ * times every candidate (256 or 512 threads per CTA; 4096, 8192 or 16384 samples per CTA) on
+ * the plan's work for B signals on `stream` and keeps the fastest in the plan; the results of
+ * later calls do not change (the same arithmetic per row).  ws as for jtfs_forward.  choice
+ * (host, 3 entries, may be NULL) receives threads, samples per CTA and the winner's time per
+ * launch in microseconds.  Synchronous.  Not thread-safe against concurrent calls on the plan.
+ * The paper has no counterpart. */
+jtfs_status jtfs_plan_autotune(jtfs_plan* plan, int64_t B, void* ws, size_t ws_bytes, void* stream,
+                               int32_t* choice);
+
 /* Tracing: when enabled, forward/backward record a CUDA event pair around each stage on
  * the launching stream.  jtfs_profile_read waits for the recorded events, writes the
  * milliseconds accumulated per stage into ms[0..n_ms) (stage i is named by
@@ -193,6 +203,11 @@ jtfs_status jtfs_varlen_capture(jtfs_varlen* v, const float* x_packed, const flo
                                 const float* g_s1, const float* g_s2, float* s0, float* s1,
                                 float* s2, float* g_x, void* ws, size_t ws_bytes, void* stream);
 jtfs_status jtfs_varlen_replay(const jtfs_varlen* v, void* stream);
+
+/* jtfs_plan_autotune for every plan of v at its largest sub-batch (ws: the varlen
+ * workspace).  Call before jtfs_varlen_capture: a captured graph keeps the launch shapes it
+ * was recorded with. */
+jtfs_status jtfs_varlen_autotune(jtfs_varlen* v, void* ws, size_t ws_bytes, void* stream);
 
 /* Waits for the stream and reports any pending device error. */
 jtfs_status jtfs_sync_status(const jtfs_plan* plan, void* stream);

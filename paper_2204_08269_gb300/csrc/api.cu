@@ -124,6 +124,20 @@ StageScope::~StageScope() {
   p->prof.recs.push_back(ProfRec{stage, a, b});
 }
 
+std::vector<int> build_rowitems(const jtfs_plan* p, int cap) {
+  std::vector<int> items;
+  for (int a = 0; a < p->n2; ++a) {
+    const Rate2& A = p->rates2[a];
+    if (A.s == 0) continue;
+    const int G = std::max(1, cap / A.L);
+    for (int l0 = A.lam_min; l0 < p->n1; l0 += G) {
+      items.push_back(a); items.push_back(l0);
+      items.push_back(std::min(G, p->n1 - l0)); items.push_back(0);
+    }
+  }
+  return items;
+}
+
 size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* base, Workspace* w) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -188,6 +202,7 @@ void jtfs_plan_destroy(jtfs_plan* p) {
   for (auto e : p->prof.pool) cudaEventDestroy(e);
   if (p->d_mem) cudaFree(p->d_mem);
   if (p->d_tc_mem) cudaFree(p->d_tc_mem);
+  if (p->d_rowitems_own) cudaFree(p->d_rowitems_own);
   if (p->d_tcb_mem) cudaFree(p->d_tcb_mem);
   delete p;
 }
@@ -303,18 +318,12 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   d.u1_len = p->u1_len; d.uh_len = p->uh_len; d.y_len = p->y_len;
   // psi-hat_alpha support end (xi + 8 sigma; both Morlet terms are below e^-32 past it) and the
   // row items of the batched second-order producer: G rows of one rate per CTA
-  p->rows_cap = std::max(p->L2max, 8192);
-  p->rowitems.clear();
   for (int a = 0; a < p->n2; ++a) {
     Rate2& A = p->rates2[a];
     A.k2e = (int)std::min<double>(d.K2max, std::floor((p->xi2[a] + kSupportSigmas * p->sg2[a]) * (double)N) + 1.0);
-    if (A.s == 0) continue;
-    const int G = std::max(1, p->rows_cap / A.L);
-    for (int l0 = A.lam_min; l0 < p->n1; l0 += G) {
-      p->rowitems.push_back(a); p->rowitems.push_back(l0);
-      p->rowitems.push_back(std::min(G, p->n1 - l0)); p->rowitems.push_back(0);
-    }
   }
+  p->rows_cap = std::max(p->L2max, 8192);
+  p->rowitems = build_rowitems(p, p->rows_cap);
   // lambda range per 256-bin block of x-hat (for the gradient gather)
   const int nblk = (int)((N / 2 + 255) / 256);
   std::vector<int2> gxl(nblk);
@@ -472,6 +481,29 @@ jtfs_status jtfs_backward(const jtfs_plan* p, const float* x, const float* u1_ck
   Workspace w;
   workspace_layout(p, B, true, (char*)ws, &w);
   return launch_backward(p, x, u1_ckpt, (int)B, g_s0, g_s1, g_s2, g_x, w, (cudaStream_t)stream);
+}
+
+jtfs_status jtfs_plan_autotune(jtfs_plan* p, int64_t B, void* ws, size_t ws_bytes, void* stream,
+                               int32_t* choice) {
+  if (!p || B < 1 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
+  jtfs_status st = check_device(p);
+  if (st != JTFS_OK) return st;
+  const size_t need = workspace_layout(p, B, false, nullptr, nullptr);
+  if (!ws || ws_bytes < need) {
+    set_error("workspace needs " + std::to_string(need) + " bytes");
+    return JTFS_ERR_WORKSPACE;
+  }
+  Workspace w;
+  workspace_layout(p, B, false, (char*)ws, &w);
+  int threads = 0, cap = 0;
+  float ms = 0.f;
+  if ((st = autotune_rows(p, (int)B, w, (cudaStream_t)stream, &threads, &cap, &ms)) != JTFS_OK) return st;
+  if (choice) {
+    choice[0] = threads;
+    choice[1] = cap;
+    choice[2] = (int32_t)(ms * 1000.f);
+  }
+  return JTFS_OK;
 }
 
 jtfs_status jtfs_host_step_bytes(const jtfs_plan* p, int64_t B, size_t* out) {

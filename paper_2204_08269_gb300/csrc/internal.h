@@ -91,7 +91,9 @@ struct jtfs_plan {
   std::vector<int> pairs;  // (alpha, lambda') work items of the second-order kernels
   std::vector<int> rowitems;  // (alpha, lambda'_0, G, 0): G rows of one rate per CTA
   int rows_cap;               // samples one row item holds (G L_alpha <= rows_cap)
+  int row_threads = 512;      // threads per CTA of the row producer (autotuned)
   int* d_rowitems;
+  void* d_rowitems_own = nullptr;   // the autotuner's item table, when it replaced the default
   std::vector<int> items;  // (alpha, first column) work items of the joint backward
   long long u1_len, uh_len, y_len;
   int L1max, L2max;
@@ -162,6 +164,11 @@ struct StageScope {
   StageScope(const jtfs_plan* p_, int stage_, cudaStream_t st_, int n_launch);
   ~StageScope();
 };
+
+// row items of the batched second-order producer for a capacity of `cap` samples per CTA
+std::vector<int> build_rowitems(const jtfs_plan* p, int cap);
+jtfs_status autotune_rows(jtfs_plan* p, int B, const Workspace& w, cudaStream_t st,
+                          int* best_threads, int* best_cap, float* best_ms);
 
 // tensor-core contraction (kernels_tc.cu)
 bool tc_supported(const jtfs_plan* p);

@@ -337,7 +337,7 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
   if (gs2 && n_items > 0 && p->use_tcb) {
     {
       StageScope sc(p, kStSecondOrder, st, 1);
-      k_second_order_rows<1><<<dim3((unsigned)(p->rowitems.size() / 4), B), kRowThreads,
+      k_second_order_rows<1><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
                               (size_t)p->rows_cap * 8, st>>>(
           d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, nullptr,
           (__nv_bfloat16*)w.ybh, (__nv_bfloat16*)w.ybl, B);
@@ -348,7 +348,7 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
   } else if (gs2 && n_items > 0) {
     {
       StageScope sc(p, kStSecondOrder, st, 1);
-      k_second_order_rows<0><<<dim3((unsigned)(p->rowitems.size() / 4), B), kRowThreads,
+      k_second_order_rows<0><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
                               (size_t)p->rows_cap * 8, st>>>(
           d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, w.y, nullptr, nullptr, B);
     }

@@ -10,6 +10,9 @@
 //                                 -> Y_alpha rows
 //   k_joint_fwd_simt            : per (c, alpha, signal): Z = W_c Y_alpha (zero-padded
 //                                 convolution along lambda), |Z|, phi_T then phi_F pooling -> S2
+#include <algorithm>
+#include <vector>
+
 #include "stages.cuh"
 
 namespace jtfs {
@@ -224,6 +227,82 @@ bool joint_simt_supported(const jtfs_plan* p) {
          joint_fwd_smem(p) <= 227 * 1024;
 }
 
+// Autotuner of the Y producer (the largest FFT stage): times every (threads per CTA, samples
+// per CTA) candidate on the plan's own work items for a batch of B signals, three launches
+// each after one warm-up, with CUDA events on the stream, and keeps the fastest.  Candidates:
+// 256 or 512 threads; 4096, 8192 or 16384 samples (at least the longest row).
+jtfs_status autotune_rows(jtfs_plan* p, int B, const Workspace& w, cudaStream_t st,
+                          int* best_threads, int* best_cap, float* best_ms) {
+  jtfs_status rc = set_attrs(p);
+  if (rc != JTFS_OK) return rc;
+  const DevPlan& d = p->dp;
+  std::vector<int> caps;
+  for (int c : {4096, 8192, 16384}) {
+    const int cap = std::max(c, p->L2max);
+    if (cap <= 16384 && std::find(caps.begin(), caps.end(), cap) == caps.end()) caps.push_back(cap);
+  }
+  size_t most = 4;
+  std::vector<std::vector<int>> tables;
+  for (int cap : caps) {
+    tables.push_back(build_rowitems(p, cap));
+    most = std::max(most, tables.back().size());
+  }
+  int* d_items = nullptr;
+  if ((rc = cuda_check(cudaMalloc(&d_items, most * sizeof(int)), "autotune items")) != JTFS_OK) return rc;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bt = p->row_threads, bc = p->rows_cap;
+  for (size_t ci = 0; ci < caps.size() && rc == JTFS_OK; ++ci) {
+    const std::vector<int>& items = tables[ci];
+    if (items.empty()) continue;
+    rc = cuda_check(cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(int),
+                                    cudaMemcpyHostToDevice, st), "autotune upload");
+    for (int threads : {256, 512}) {
+      if (rc != JTFS_OK) break;
+      auto launch = [&]() {
+        const dim3 grid((unsigned)(items.size() / 4), B);
+        const size_t smem = (size_t)caps[ci] * 8;
+        if (p->use_tc)
+          k_second_order_rows<1><<<grid, threads, smem, st>>>(
+              d, reinterpret_cast<const int4*>(d_items), w.uh, nullptr, (__nv_bfloat16*)w.ybh,
+              (__nv_bfloat16*)w.ybl, B);
+        else
+          k_second_order_rows<0><<<grid, threads, smem, st>>>(
+              d, reinterpret_cast<const int4*>(d_items), w.uh, w.y, nullptr, nullptr, B);
+      };
+      launch();
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 3; ++r) launch();
+      cudaEventRecord(e1, st);
+      if ((rc = cuda_check(cudaEventSynchronize(e1), "autotune timing")) != JTFS_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bt = threads; bc = caps[ci]; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d_items);
+  if (rc != JTFS_OK) return rc;
+  // install the winner's item table
+  std::vector<int> items = build_rowitems(p, bc);
+  if (p->d_rowitems_own) { cudaFree(p->d_rowitems_own); p->d_rowitems_own = nullptr; }
+  if ((rc = cuda_check(cudaMalloc(&p->d_rowitems_own, std::max<size_t>(16, items.size() * sizeof(int))), "tuned items")) != JTFS_OK)
+    return rc;
+  if ((rc = cuda_check(cudaMemcpy(p->d_rowitems_own, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice), "tuned items")) != JTFS_OK)
+    return rc;
+  p->rowitems = items;
+  p->d_rowitems = (int*)p->d_rowitems_own;
+  p->rows_cap = bc;
+  p->row_threads = bt;
+  *best_threads = bt;
+  *best_cap = bc;
+  *best_ms = best / 3.f;
+  return JTFS_OK;
+}
+
 jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0, float* s1,
                            float* s2, float* u1, const Workspace& w, cudaStream_t st) {
   jtfs_status rc = set_attrs(p);
@@ -245,7 +324,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   if (p->use_tc) {
     if (!p->pairs.empty()) {
       StageScope sc(p, kStSecondOrder, st, 1);
-      k_second_order_rows<1><<<dim3((unsigned)(p->rowitems.size() / 4), B), kRowThreads,
+      k_second_order_rows<1><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
                               (size_t)p->rows_cap * 8, st>>>(
           d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, nullptr,
           (__nv_bfloat16*)w.ybh, (__nv_bfloat16*)w.ybl, B);
@@ -256,7 +335,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   } else {
     if (!p->pairs.empty()) {
       StageScope sc(p, kStSecondOrder, st, 1);
-      k_second_order_rows<0><<<dim3((unsigned)(p->rowitems.size() / 4), B), kRowThreads,
+      k_second_order_rows<0><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
                               (size_t)p->rows_cap * 8, st>>>(
           d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, w.y, nullptr, nullptr, B);
     }

@@ -332,6 +332,23 @@ jtfs_status jtfs_varlen_capture(jtfs_varlen* v, const float* x, const float* g_s
   return cuda_check(cudaGraphInstantiate(&v->exec, g, 0), "graph instantiate");
 }
 
+jtfs_status jtfs_varlen_autotune(jtfs_varlen* v, void* ws, size_t ws_bytes, void* stream) {
+  if (!v) { set_error("NULL varlen"); return JTFS_ERR_INVALID_ARG; }
+  if (!ws || ws_bytes < v->ws_bytes) {
+    set_error("varlen workspace needs " + std::to_string(v->ws_bytes) + " bytes");
+    return JTFS_ERR_WORKSPACE;
+  }
+  for (jtfs_plan* p : v->plans) {
+    int most = 0;
+    for (const auto& ch : v->chunks)
+      if (ch.plan == p) most = std::max(most, ch.count);
+    if (most == 0) continue;
+    jtfs_status rc = jtfs_plan_autotune(p, most, ws, ws_bytes, stream, nullptr);
+    if (rc != JTFS_OK) return rc;
+  }
+  return JTFS_OK;
+}
+
 jtfs_status jtfs_varlen_replay(const jtfs_varlen* v, void* stream) {
   if (!v || !v->exec) { set_error("no captured graph"); return JTFS_ERR_INVALID_ARG; }
   return cuda_check(cudaGraphLaunch(v->exec, (cudaStream_t)stream), "graph launch");

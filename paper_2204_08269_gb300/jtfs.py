@@ -65,6 +65,7 @@ def lib():
         "jtfs_profile_read": ([_P, _P, _I32, ctypes.POINTER(_I64)], _I32),
         "jtfs_profile_stage_name": ([_I32], ctypes.c_char_p),
         "jtfs_first_order_static": ([_P, _P, _I64, _P, _P, _P], _I32),
+        "jtfs_plan_autotune": ([_P, _I64, _P, _SZ, _P, _P], _I32),
         "jtfs_varlen_padded_length": ([ctypes.POINTER(_Config), _I64], _I64),
         "jtfs_varlen_create": ([ctypes.POINTER(_Config), _P, _I64, _I32, ctypes.POINTER(_P)], _I32),
         "jtfs_varlen_destroy": ([_P], None),
@@ -73,6 +74,7 @@ def lib():
         "jtfs_varlen_forward_backward": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P], _I32),
         "jtfs_varlen_capture": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P], _I32),
         "jtfs_varlen_replay": ([_P, _P], _I32),
+        "jtfs_varlen_autotune": ([_P, _P, _SZ, _P], _I32),
         "jtfs_status_string": ([_I32], ctypes.c_char_p),
         "jtfs_last_error": ([], ctypes.c_char_p),
     }
@@ -90,10 +92,11 @@ def exported_symbols():
             "jtfs_workspace_bytes", "jtfs_forward", "jtfs_backward", "jtfs_host_step_bytes",
             "jtfs_forward_backward_host", "jtfs_sync_status", "jtfs_status_string",
             "jtfs_last_error", "jtfs_profile_enable", "jtfs_profile_read",
-            "jtfs_profile_stage_name", "jtfs_first_order_static", "jtfs_varlen_padded_length",
+            "jtfs_profile_stage_name", "jtfs_first_order_static", "jtfs_plan_autotune",
+            "jtfs_varlen_padded_length",
             "jtfs_varlen_create", "jtfs_varlen_destroy", "jtfs_varlen_layout",
             "jtfs_varlen_workspace_bytes", "jtfs_varlen_forward_backward", "jtfs_varlen_capture",
-            "jtfs_varlen_replay"]
+            "jtfs_varlen_replay", "jtfs_varlen_autotune"]
 
 
 class JTFSError(RuntimeError):
@@ -250,6 +253,16 @@ class JTFSPlan:
             ws.numel(), _stream()))
         return outs[0], outs[1], outs[2], gx
 
+    def autotune(self, B):
+        """Tunes the launch shape of the second-order FFT stage for batches of B signals;
+        returns {threads, samples_per_cta, us_per_launch}."""
+        import numpy as np
+        ws = self.workspace(B, True)
+        c = np.zeros(3, dtype=np.int32)
+        _check("jtfs_plan_autotune", lib().jtfs_plan_autotune(
+            self._h, B, _ptr(ws), ws.numel(), _stream(), c.ctypes.data_as(_P)))
+        return dict(threads=int(c[0]), samples_per_cta=int(c[1]), us_per_launch=int(c[2]))
+
     def profile(self, on=True):
         _check("jtfs_profile_enable", lib().jtfs_profile_enable(self._h, 1 if on else 0))
 
@@ -374,3 +387,7 @@ class JTFSVarlen:
 
     def replay(self):
         _check("jtfs_varlen_replay", lib().jtfs_varlen_replay(self._h, _stream()))
+
+    def autotune(self):
+        _check("jtfs_varlen_autotune", lib().jtfs_varlen_autotune(
+            self._h, _ptr(self._ws), self._ws.numel(), _stream()))

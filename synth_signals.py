@@ -109,6 +109,17 @@ def varlen_lengths(count: int, seed: int, lo_log2: float = 13.0, hi_log2: float 
     return np.floor(2.0 ** rng.uniform(lo_log2, hi_log2, size=count)).astype(np.int64)
 
 
+def varlen_batch(count: int, seed: int, lo_log2: float = 13.0, hi_log2: float = 17.0):
+    """Uneven-length batch: lengths log-uniform in [2^lo, 2^hi], even-numbered signals AM/FM
+    tones and odd-numbered ones click trains.  Returns (x packed back to back, lengths)."""
+    lengths = varlen_lengths(count, seed, lo_log2, hi_log2)
+    parts = []
+    for i, n in enumerate(lengths):
+        gen = amfm_batch if i % 2 == 0 else click_train_batch
+        parts.append(gen(1, int(n), seed + 7919 * (i + 1))[0])
+    return np.concatenate(parts).astype(np.float32), lengths
+
+
 def workload_signals(config: int, B: int, N: int):
     """Inputs for the named workloads (1: noise + chirp, 2/4: AM/FM, 3: click trains)."""
     seed = BASE_SEED + config

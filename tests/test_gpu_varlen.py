@@ -111,3 +111,34 @@ def test_varlen_signal_matches_oracle(L):
     assert _rel(s0.cpu().view(fr), ref["S0"][:fr]) <= 1e-4
     assert _rel(s1.cpu().view(plan.n1, fr), ref["S1"][:, :fr]) <= 1e-4
     assert _rel(s2.cpu().view(plan.n2, plan.C, plan.n_lam_out, fr), ref["S2"][..., :fr]) <= 1e-4
+
+
+def test_autotune_keeps_results(L):
+    cfg = dict(N=2048, J=7, Q=12, J_fr=3, Q_fr=2, T=128, F=12)
+    for prec in ("fp32", "fp32_simt"):
+        plan = L.JTFSPlan(**cfg, precision=prec)
+        x = torch.from_numpy(SS.white_noise_batch(3, cfg["N"], 31)).cuda()
+        before = plan.forward(x)
+        g = [torch.ones_like(t) for t in before[:3]]
+        gx0 = plan.backward(x, before[3], *g)
+        choice = plan.autotune(3)
+        assert choice["threads"] in (256, 512)
+        assert choice["samples_per_cta"] in (4096, 8192, 16384)
+        after = plan.forward(x)
+        for a, b in zip(before, after):
+            assert torch.equal(a, b)
+        assert torch.equal(gx0, plan.backward(x, after[3], *g))
+
+
+def test_varlen_autotune_then_graph(L):
+    v = L.JTFSVarlen(LENGTHS, **CFG, precision="bf16")
+    x, g = _packed_inputs(v, 13)
+    direct = [t.clone() for t in v.forward_backward(x, g)]
+    v.autotune()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        outs = v.capture(x, g)
+        v.replay()
+    side.synchronize()
+    for a, b in zip(direct, outs):
+        assert torch.equal(a, b)
