@@ -9,6 +9,7 @@ cotangents.  Prints one JSON line.  Under torchrun each rank runs the same per-G
   python bench.py --impl reference ...   # the FP64 oracle on the host cores
   python bench.py --workload varlen ...  # uneven-length batch (1024 signals of 2^13-2^17
                                          # samples) in one graph launch vs per-signal launches
+  python bench.py --workload mixed ...   # forward by contraction precision with oracle errors
 """
 from __future__ import annotations
 
@@ -374,6 +375,54 @@ def run_varlen(args):
     return out
 
 
+def run_mixed(args):
+    """Mixed-precision forward: B = 256, N = 2^15, J = 11, Q = 12, J_fr = 4, Q_fr = 1 (AM/FM
+    tones).  Forward signals/s of the FP32-grade, TF32 and BF16 contractions, and their
+    per-order relative L2 error against the FP64 oracle on two sampled signals."""
+    import torch
+    from paper_2204_08269_gb300 import jtfs
+    import synth_signals as SS
+    from oracle import jtfs_oracle as O
+    torch.cuda.set_device(0)
+    B = args.batch if args.batch != BATCH else 256
+    oc = O.WORKLOADS[4]
+    cfg = dict(N=oc.N, J=oc.J, Q=oc.Q, J_fr=oc.J_fr, Q_fr=oc.Q_fr, T=oc.T, F=oc.F)
+    xh = SS.workload_signals(4, B, cfg["N"])
+    x = torch.from_numpy(xh).cuda()
+    plan_o = O.Plan(oc)
+    sched_o = O.Schedule(plan_o, 0)
+    sample = [0, B // 2]
+    refs = [O.forward_one(xh[b].astype(np.float64), plan_o, sched_o) for b in sample]
+    res = {}
+    for prec in ("fp32", "tf32", "bf16"):
+        p = jtfs.JTFSPlan(**cfg, precision=prec)
+        for _ in range(args.warmup):
+            out = p.forward(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            out = p.forward(x)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        errs = {}
+        for name, k in (("S0", 0), ("S1", 1), ("S2", 2)):
+            got = out[k].cpu().numpy().astype(np.float64)
+            errs[name] = max(float(np.linalg.norm(got[b] - r[name]) / np.linalg.norm(r[name]))
+                             for b, r in zip(sample, refs))
+        res[prec] = {"signals_per_s": B / (ms / 1e3), "ms_per_forward": ms, "rel_err": errs}
+    out = {"metric": "JTFS forward signals/sec by contraction precision (B=256, N=2^15, J=11, Q=12)",
+           "value": res["tf32"]["signals_per_s"], "unit": "signals/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+           "vs_baseline": None, "dtype": "tf32", "data": "synthetic (seeded AM/FM tones + -30 dB noise)",
+           "config": {"workload": "mixed precision forward, B=256 AM/FM tones, N=2^15, J=11, Q=12, "
+                                  "J_fr=4, Q_fr=1, T=2^11, F=12"},
+           "precisions": res, "oracle_sample": f"signals {sample} of {B}"}
+    print(json.dumps(out), flush=True)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,8 +434,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="signals per GPU (the workload is 64; smaller values for profiling)")
-    ap.add_argument("--workload", default="fixed", choices=["fixed", "varlen"],
-                    help="varlen: the uneven-length batch (not the headline metric)")
+    ap.add_argument("--workload", default="fixed", choices=["fixed", "varlen", "mixed"],
+                    help="varlen: the uneven-length batch; mixed: forward by contraction "
+                         "precision (neither is the headline metric)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -394,6 +444,8 @@ def main():
         run_reference(args)
     elif args.workload == "varlen":
         run_varlen(args)
+    elif args.workload == "mixed":
+        run_mixed(args)
     else:
         run_ours(args)
 

@@ -158,11 +158,13 @@ size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* bas
   W.gf = nullptr;
   W.gxh = nullptr;
   W.ybh = W.ybl = nullptr;
+  W.yt = nullptr;
   W.pbuf = nullptr;
   W.g1 = nullptr;
   if (p->use_tc) {
     W.ybh = take(Bz * p->y_len * 2 * 2);
-    if (p->cfg.precision == JTFS_PREC_FP32) W.ybl = take(Bz * p->y_len * 2 * 2);
+    if (p->split) W.ybl = take(Bz * p->y_len * 2 * 2);
+    if (p->cfg.precision == JTFS_PREC_TF32) W.yt = (float*)take(Bz * p->yt_len * 2 * 4);
     W.pbuf = (float*)take(Bz * p->n2 * (size_t)p->C * p->n1 * p->n_t * 4);
   }
   if (with_grad && p->use_tcb) W.g1 = take(tcb_g1_bytes(p, B));
@@ -318,10 +320,16 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   d.u1_len = p->u1_len; d.uh_len = p->uh_len; d.y_len = p->y_len;
   // psi-hat_alpha support end (xi + 8 sigma; both Morlet terms are below e^-32 past it) and the
   // row items of the batched second-order producer: G rows of one rate per CTA
+  long long off_yt = 0;
   for (int a = 0; a < p->n2; ++a) {
     Rate2& A = p->rates2[a];
     A.k2e = (int)std::min<double>(d.K2max, std::floor((p->xi2[a] + kSupportSigmas * p->sg2[a]) * (double)N) + 1.0);
+    A.kt = A.s ? (p->n1 - (A.lam_min & ~7) + 3) / 4 * 4 : 0;
+    A.off_yt = off_yt;
+    off_yt += (long long)A.L * A.kt;
   }
+  p->yt_len = off_yt;
+  d.yt_len = off_yt;
   p->rows_cap = std::max(p->L2max, 8192);
   p->rowitems = build_rowitems(p, p->rows_cap);
   // lambda range per 256-bin block of x-hat (for the gradient gather)
@@ -397,9 +405,9 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
                                     "plan upload")) != JTFS_OK)
       return fail(st, "");
   if ((st = build_tables(p)) != JTFS_OK) return fail(st, "");
-  if (cfg->precision == JTFS_PREC_TF32)
-    return fail(JTFS_ERR_UNSUPPORTED, "TF32 contraction is not built; use FP32, BF16 or FP32_SIMT");
-  if (cfg->precision == JTFS_PREC_FP32 || cfg->precision == JTFS_PREC_BF16) {
+  p->split = cfg->precision == JTFS_PREC_FP32 || cfg->precision == JTFS_PREC_TF32;
+  if (cfg->precision == JTFS_PREC_FP32 || cfg->precision == JTFS_PREC_BF16 ||
+      cfg->precision == JTFS_PREC_TF32) {
     if (!tc_supported(p)) return fail(JTFS_ERR_UNSUPPORTED, "configuration outside the tensor-core kernel");
     p->use_tc = true;
     if ((st = build_tc_tables(p)) != JTFS_OK) return fail(st, "");

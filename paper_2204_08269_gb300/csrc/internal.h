@@ -34,7 +34,9 @@ struct Rate2 {
   int lam_min;  // first lambda' row with a non-zero Y_alpha row
   int K;        // n1 - lam_min rows of Y_alpha
   int k2e;      // end of psi-hat_alpha's support on the N grid (bins >= k2e hold < e^-32)
+  int kt;       // lambda' columns of the transposed TF32 planes: from lam_min & ~7, padded to 4
   long long off_y;  // offset of Y_alpha (K x L complex) in a packed per-signal array
+  long long off_yt; // offset of the transposed plane (L x kt) in a packed per-signal array
 };
 
 // Device-side constants of a plan (passed by value to kernels).
@@ -43,7 +45,7 @@ struct DevPlan {
   int TW, logTW;          // twiddle table length (>= every FFT length and N)
   int D, M, logM;         // decimation of the length-N FFT: N = D * M, M <= 2^kMaxLogL
   int K2max;              // width of the psi2 table (bins 0..K2max-1 on the N grid)
-  long long u1_len, uh_len, y_len;
+  long long u1_len, uh_len, y_len, yt_len;
   const Row1* rows1;      // [n1]
   const Rate2* rates2;    // [n2]
   const float* psi1;      // packed support values of psi1
@@ -92,10 +94,12 @@ struct jtfs_plan {
   std::vector<int> rowitems;  // (alpha, lambda'_0, G, 0): G rows of one rate per CTA
   int rows_cap;               // samples one row item holds (G L_alpha <= rows_cap)
   int row_threads = 512;      // threads per CTA of the row producer (autotuned)
+  bool split = false;         // BF16 hi / lo split (FP32-grade products; TF32 plans' backward)
+  void* d_wplanes32[2] = {nullptr, nullptr};   // Wr, Wi FP32 [C * n1][n1_pad] (TF32 forward)
   int* d_rowitems;
   void* d_rowitems_own = nullptr;   // the autotuner's item table, when it replaced the default
   std::vector<int> items;  // (alpha, first column) work items of the joint backward
-  long long u1_len, uh_len, y_len;
+  long long u1_len, uh_len, y_len, yt_len;
   int L1max, L2max;
   jtfs::DevPlan dp;
   // device allocations
@@ -150,6 +154,7 @@ struct Workspace {
   float2* gxh;     // [B][N/2]
   void* ybh;       // [B * y_len * 2] bf16 (tensor-core path)
   void* ybl;       // [B * y_len * 2] bf16 (three-pass split only)
+  float* yt;       // [B * yt_len * 2] FP32 transposed Y planes (TF32 contraction only)
   float* pbuf;     // [B][n2][C * n1][n_t] time-pooled rows
   void* g1;        // phi_F adjoint of g_S2 (tensor-core backward), bf16
 };

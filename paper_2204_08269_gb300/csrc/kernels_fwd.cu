@@ -196,6 +196,33 @@ k_joint_fwd_simt(DevPlan P, const float2* __restrict__ y, float* __restrict__ s2
   }
 }
 
+// Transposed FP32 Y planes for the TF32 contraction (its MMAs take K-major operands only):
+// yt[alpha][2 b + part][n][lambda' - (lam_min & ~7)] = y[alpha][2 b + part][lambda' - lam_min][n],
+// zero for lam_min & ~7 <= lambda' < lam_min and in the padding up to kt.  32 x 32 tiles
+// through shared memory; grid (ceil(L / 32), ceil(kt / 32), 2 B) for one rate.
+__global__ void k_transpose_yt(DevPlan P, int a, const float* __restrict__ y,
+                               float* __restrict__ yt, int B) {
+  __shared__ float tile[32][33];
+  const Rate2 A = P.rates2[a];
+  const int lm8 = A.lam_min & ~7;
+  const int n0 = blockIdx.x * 32, c0 = blockIdx.y * 32, bp = blockIdx.z;
+  const size_t plane = (size_t)A.K * A.L, tplane = (size_t)A.L * A.kt;
+  const float* src = y + (size_t)B * 2 * A.off_y + (size_t)bp * plane;
+  float* dst = yt + (size_t)B * 2 * A.off_yt + (size_t)bp * tplane;
+  const int tx = threadIdx.x;
+  for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
+    const int lp = lm8 + c0 + ty, n = n0 + tx;          // lambda' row, sample column
+    float v = 0.f;
+    if (lp >= A.lam_min && lp < P.n1 && n < A.L) v = src[(size_t)(lp - A.lam_min) * A.L + n];
+    tile[ty][tx] = v;
+  }
+  __syncthreads();
+  for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
+    const int n = n0 + ty, c = c0 + tx;
+    if (n < A.L && c < A.kt) dst[(size_t)n * A.kt + c] = tile[tx][ty];
+  }
+}
+
 bool g_attrs_set = false;
 
 jtfs_status set_attrs(const jtfs_plan* p) {
@@ -209,6 +236,7 @@ jtfs_status set_attrs(const jtfs_plan* p) {
   const int rows_smem = 128 * 1024;
   if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_joint_fwd_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
   g_attrs_set = true;
   return JTFS_OK;
@@ -321,7 +349,27 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
     StageScope sc(p, kStScalogram, st, 1);
     k_scalogram<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 12, st>>>(d, w.xh, u1, w.uh, s1);
   }
-  if (p->use_tc) {
+  if (p->use_tc && p->cfg.precision == JTFS_PREC_TF32) {
+    // TF32 operands: Y as FP32 planes (in the complex FP32 buffer, same size)
+    if (!p->pairs.empty()) {
+      StageScope sc(p, kStSecondOrder, st, 1);
+      k_second_order_rows<2><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
+                              (size_t)p->rows_cap * 8, st>>>(
+          d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, w.y, nullptr, nullptr, B);
+    }
+    {
+      StageScope sc(p, kStSecondOrder, st, p->n2);
+      for (int a = 0; a < p->n2; ++a) {
+        const Rate2& A = p->rates2[a];
+        if (A.s == 0 || A.kt == 0) continue;
+        k_transpose_yt<<<dim3((A.L + 31) / 32, (A.kt + 31) / 32, 2 * B), dim3(32, 8), 0, st>>>(
+            d, a, reinterpret_cast<const float*>(w.y), w.yt, B);
+      }
+    }
+    StageScope sc(p, kStJointFwd, st, 2);
+    jtfs_status r2 = launch_joint_fwd_tc(p, B, w.yt, nullptr, w.pbuf, s2, st);
+    if (r2 != JTFS_OK) return r2;
+  } else if (p->use_tc) {
     if (!p->pairs.empty()) {
       StageScope sc(p, kStSecondOrder, st, 1);
       k_second_order_rows<1><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,

@@ -60,6 +60,7 @@ struct TcArgs {
   int stages;              // operand pipeline depth (2..8)
   int wstages;             // pooling-weight ring depth (2..kMaxWS)
   int res_kb;              // k-blocks of the resident W tile (RES form)
+  int pool_split;          // 1: the 16-frame pooling uses the BF16 hi / lo split
   int n_rows;              // C * n1
   int nt;                  // frames
   float* P;                // [B][n2][C*n1][nt]
@@ -435,26 +436,32 @@ __device__ __forceinline__ void hmma16816(float (&c)[4], const uint32_t (&a)[4],
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-template <bool RES>
+// TF = true: TF32 operands (FP32 W and Y planes, kind::tf32 MMAs of K = 8, one pass); the
+// pooling then keeps the BF16 hi / lo split.
+template <bool RES, bool TF>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int NT = 16, BN = 128, NH = 2;
-  const int planes = args.passes == 3 ? 2 : 1;
+  // contraction planes (hi, + lo for the BF16 split) and pooling planes (|Z| and w: hi, + lo)
+  const int planes = TF ? 1 : (args.passes == 3 ? 2 : 1);
+  const int pplanes = args.pool_split ? 2 : 1;
   const int S = args.stages, WS = args.wstages;
-  constexpr uint32_t kAPlane = kBM * kBK * 2;           // 8 KB, 64-byte swizzle
-  constexpr uint32_t kBHalf = kBK * 64 * 2;             // 4 KB: 32 lambda' x 64 samples
+  constexpr uint32_t kAPlane = TF ? kBM * kBK * 4 : kBM * kBK * 2;   // 16 KB SW128 / 8 KB SW64
+  constexpr int NYA = TF ? 4 : 2;                       // Y atoms per part: 32 / 64 samples wide
+  constexpr int kYAW = BN / NYA;
+  constexpr uint32_t kBHalf = 4096;                     // one Y atom: 32 lambda' x 128 bytes
   constexpr uint32_t kWHalf = NT * 64 * 2;              // 2 KB: 16 frames x 64 samples
   constexpr uint32_t kStg = 32 * 16 * 2;                // 1 KB: a warp's 32 x 16 |Z| block
   const int max_kb = args.res_kb;
-  const uint32_t y_bytes = planes * 2 * NH * kBHalf;
+  const uint32_t y_bytes = planes * 2 * NYA * kBHalf;
   const uint32_t stage_bytes = RES ? y_bytes : planes * 2 * kAPlane + y_bytes;
   uint8_t* sA = sm;
   uint8_t* sStage = sm + (RES ? planes * 2 * max_kb * kAPlane : 0);
-  uint8_t* sWt = sStage + S * stage_bytes;              // WS x NH halves x planes (hi, lo adjacent)
-  uint8_t* sStg = sWt + WS * NH * planes * kWHalf;      // 16 warps x planes x 1 KB
-  float* sRed = (float*)(sStg + kEpiWarps * planes * kStg);   // [4 groups][128 rows][16]
+  uint8_t* sWt = sStage + S * stage_bytes;              // WS x NH halves x pplanes (hi, lo adjacent)
+  uint8_t* sStg = sWt + WS * NH * pplanes * kWHalf;     // 16 warps x pplanes x 1 KB
+  float* sRed = (float*)(sStg + kEpiWarps * pplanes * kStg);   // [4 groups][128 rows][16]
   __shared__ uint64_t full_bar[8], empty_bar[8], wfull[kMaxWS], wempty[kMaxWS], tfull[2],
       tempty[2], red_full[4], red_free[4], a_full, a_free, mma_done;
   __shared__ uint32_t tmem_base;
@@ -537,22 +544,28 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
                 if (!RES)
                   tma_load_2d(st + (pl * 2 + part) * kAPlane, &maps.w[pl * 2 + part],
                               lm8 + kb * kBK, m0, &full_bar[stage]);
-                for (int h = 0; h < NH; ++h)
-                  tma_load_3d(sb + ((pl * 2 + part) * NH + h) * kBHalf, &maps.y[pl][a],
-                              j * BN + h * 64, lm8 + kb * kBK - A.lam_min, 2 * b + part,
-                              &full_bar[stage]);
+                if (TF) {
+                  // Y^T [n][lambda' - lm8]: one 128-sample x 32-lambda' K-major box per part
+                  tma_load_3d(sb + (pl * 2 + part) * NYA * kBHalf, &maps.y[pl][a], kb * kBK,
+                              j * BN, 2 * b + part, &full_bar[stage]);
+                } else {
+                  for (int h = 0; h < NYA; ++h)
+                    tma_load_3d(sb + ((pl * 2 + part) * NYA + h) * kBHalf, &maps.y[pl][a],
+                                j * BN + h * kYAW, lm8 + kb * kBK - A.lam_min, 2 * b + part,
+                                &full_bar[stage]);
+                }
               }
             }
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
           if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
-          mbar_arrive_expect_tx(&wfull[ws], planes * NH * kWHalf);
+          mbar_arrive_expect_tx(&wfull[ws], pplanes * NH * kWHalf);
           armed_w |= 1u << ws;
           armed_w_par = (armed_w_par & ~(1u << ws)) | (wph << ws);
           for (int h = 0; h < NH; ++h)
-            for (int pl = 0; pl < planes; ++pl)
-              tma_load_2d(sWt + ((ws * NH + h) * planes + pl) * kWHalf, &maps.wt[pl],
+            for (int pl = 0; pl < pplanes; ++pl)
+              tma_load_2d(sWt + ((ws * NH + h) * pplanes + pl) * kWHalf, &maps.wt[pl],
                           j * BN + h * 64, a * NT, &wfull[ws]);
           if (++ws == WS) { ws = 0; wph ^= 1; }
         }
@@ -566,9 +579,10 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t id_pos = instr_desc(kBM, BN, 1, 1, 0, 1, 0);
-      const uint32_t id_neg = instr_desc(kBM, BN, 1, 1, 0, 1, 1);
-      const int npair = args.passes == 3 ? 3 : 1;
+      constexpr uint32_t kFmt = TF ? 2 : 1;
+      const uint32_t id_pos = instr_desc(kBM, BN, kFmt, kFmt, 0, TF ? 0 : 1, 0);
+      const uint32_t id_neg = instr_desc(kBM, BN, kFmt, kFmt, 0, TF ? 0 : 1, 1);
+      const int npair = (!TF && args.passes == 3) ? 3 : 1;
       int stage = 0, acc = 0;
       uint32_t phase = 0, acc_ph = 0, aph = 0;
       bool ok = true;
@@ -576,8 +590,10 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         const int4 item = args.items[it % args.n_base];
         const Rate2 A = P.rates2[item.x];
         const int lm8 = A.lam_min & ~7;
-        const int nks = (P.n1 - lm8 + 15) >> 4;
-        const int nkb = (nks + 1) >> 1;
+        // K steps of the item: 16 lambda' (BF16) or 8 (TF32); 32 lambda' per k-block
+        constexpr int kKS = TF ? 8 : 16, kSPB = kBK / kKS;
+        const int nks = (P.n1 - lm8 + kKS - 1) / kKS;
+        const int nkb = (nks + kSPB - 1) / kSPB;
         if (RES) {
           if (!mbar_wait(&a_full, aph, kWaitNs)) { fail(9); ok = false; break; }
           aph ^= 1;
@@ -593,21 +609,31 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
             const uint32_t sb = RES ? st : st + planes * 2 * kAPlane;
             const uint32_t sa = RES ? smem_u32(sA) + kb * kAPlane : st;
             const uint32_t a_stride = RES ? max_kb * kAPlane : kAPlane;
-            const int kss = min(2, nks - 2 * kb);
+            const int kss = min(kSPB, nks - kSPB * kb);
             for (int ks = 0; ks < kss; ++ks) {
               for (int q = 0; q < npair; ++q) {
                 const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                // A: K-major rows of 32 lambda' (64-byte swizzle for BF16, 128 for FP32);
+                // B: MN-major atoms of 128 bytes, K step = 16 (BF16) or 8 (TF32) rows
                 const uint32_t ar_a = sa + pa * 2 * a_stride + ks * 32;
-                const uint64_t ar = smem_desc(ar_a, 16, 512, kSw64);
-                const uint64_t ai = smem_desc(ar_a + a_stride, 16, 512, kSw64);
-                const uint32_t br_a = sb + pb * 2 * NH * kBHalf + ks * 2048;
-                const uint64_t br = smem_desc(br_a, kBHalf, 1024, kSw128);
-                const uint64_t bi = smem_desc(br_a + NH * kBHalf, kBHalf, 1024, kSw128);
+                const uint64_t ar = smem_desc(ar_a, 16, TF ? 1024 : 512, TF ? kSw128 : kSw64);
+                const uint64_t ai = smem_desc(ar_a + a_stride, 16, TF ? 1024 : 512, TF ? kSw128 : kSw64);
+                // B for TF32: K-major [128 samples][32 lambda'], +32 bytes per K = 8 step
+                const uint32_t br_a = sb + pb * 2 * NYA * kBHalf + (TF ? ks * 32 : ks * kKS * 128);
+                const uint64_t br = smem_desc(br_a, TF ? 16 : kBHalf, 1024, kSw128);
+                const uint64_t bi = smem_desc(br_a + NYA * kBHalf, TF ? 16 : kBHalf, 1024, kSw128);
                 const uint32_t f = (kb | ks | q) ? 1u : 0u;
-                mma_f16(t_re, ar, br, id_pos, f);    // Wr Yr
-                mma_f16(t_re, ai, bi, id_neg, 1u);   // -Wi Yi
-                mma_f16(t_im, ar, bi, id_pos, f);    // Wr Yi
-                mma_f16(t_im, ai, br, id_pos, 1u);   // Wi Yr
+                if (TF) {
+                  mma_tf32(t_re, ar, br, id_pos, f);    // Wr Yr
+                  mma_tf32(t_re, ai, bi, id_neg, 1u);   // -Wi Yi
+                  mma_tf32(t_im, ar, bi, id_pos, f);    // Wr Yi
+                  mma_tf32(t_im, ai, br, id_pos, 1u);   // Wi Yr
+                } else {
+                  mma_f16(t_re, ar, br, id_pos, f);
+                  mma_f16(t_re, ai, bi, id_neg, 1u);
+                  mma_f16(t_im, ar, bi, id_pos, f);
+                  mma_f16(t_im, ai, br, id_pos, 1u);
+                }
               }
             }
             mma_commit(&empty_bar[stage]);
@@ -631,7 +657,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const int g = lane >> 2, t4 = lane & 3;
     // staging block: row = lane, two 16-byte chunks, chunk ^= (row >> 2) & 1
-    uint8_t* stg = sStg + ew * planes * kStg;
+    uint8_t* stg = sStg + ew * pplanes * kStg;
     const uint32_t stg_u = smem_u32(stg);
     uint8_t* my_row = stg + lane * 32;
     const int my_sw = (lane >> 2) & 1;
@@ -664,7 +690,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         tc_fence_after();
         if (!mbar_wait(&wfull[ws], wph, kWaitNs)) { fail(19); ok = false; break; }
         const uint32_t t_col = tbase + acc * 256 + lane_off + cg * 32;
-        const uint32_t w_u = smem_u32(sWt + (ws * NH + (cg >> 1)) * planes * kWHalf);
+        const uint32_t w_u = smem_u32(sWt + (ws * NH + (cg >> 1)) * pplanes * kWHalf);
 #pragma unroll
         for (int sub = 0; sub < 2; ++sub) {
           float re[16], im[16];
@@ -694,7 +720,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
             const int pos = (ch ^ my_sw) * 16;
             *reinterpret_cast<uint4*>(my_row + pos) =
                 make_uint4(hv[4 * ch], hv[4 * ch + 1], hv[4 * ch + 2], hv[4 * ch + 3]);
-            if (planes == 2)
+            if (pplanes == 2)
               *reinterpret_cast<uint4*>(my_row + kStg + pos) =
                   make_uint4(lv[4 * ch], lv[4 * ch + 1], lv[4 * ch + 2], lv[4 * ch + 3]);
           }
@@ -711,7 +737,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
             hmma16816(c[mt][0], ah[mt], bh[0], bh[1]);
             hmma16816(c[mt][1], ah[mt], bh[2], bh[3]);
           }
-          if (planes == 2) {
+          if (pplanes == 2) {
             uint32_t bl[4], al[2][4];
             ldsm_x4(w_u + kWHalf + b_off, bl);
             ldsm_x4(a_addr[0] + kStg, al[0]);
@@ -830,6 +856,20 @@ __global__ void k_build_wplanes(DevPlan Pd, int n1_pad, __nv_bfloat16* wr_hi, __
   }
 }
 
+// FP32 W planes for the TF32 forward: Wr, Wi [C * n1][n1_pad], zero for lambda' >= n1.
+__global__ void k_build_wplanes32(DevPlan Pd, int n1_pad, float* wr, float* wi) {
+  const long long total = (long long)Pd.C * Pd.n1 * n1_pad;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / n1_pad), lp = (int)(i % n1_pad);
+    const int c = r / Pd.n1, lam = r % Pd.n1;
+    float2 v = make_float2(0.f, 0.f);
+    if (lp < Pd.n1) v = Pd.h[(size_t)c * Pd.N_fr + ((lam - lp) & (Pd.N_fr - 1))];
+    wr[i] = v.x;
+    wi[i] = v.y;
+  }
+}
+
 // Pooling weights, t-major: w[a * NT + t][n] = s_a phi_T[(t T - n s_a) mod N] for n < L_a and
 // t < n_t, zero elsewhere; stored as hi = bf16(w) and lo = bf16(w - hi).
 __global__ void k_build_wt(DevPlan Pd, int NT, int Lmax, __nv_bfloat16* hi, __nv_bfloat16* lo) {
@@ -865,11 +905,11 @@ int tc_nt(int n_t) {
 static int tc_bn(const jtfs_plan* p) { return tc_nt(p->n_t) == 16 ? 128 : 64; }
 
 bool tc_supported(const jtfs_plan* p) {
-  return p->n2 <= 16 && tc_nt(p->n_t) <= 64 && p->cfg.precision != JTFS_PREC_FP32_SIMT &&
-         p->cfg.precision != JTFS_PREC_TF32;
+  if (p->cfg.precision == JTFS_PREC_TF32 && tc_nt(p->n_t) != 16) return false;   // 16-frame form only
+  return p->n2 <= 16 && tc_nt(p->n_t) <= 64 && p->cfg.precision != JTFS_PREC_FP32_SIMT;
 }
 
-int tc_res_kb(const jtfs_plan* p) { return p->cfg.precision == JTFS_PREC_FP32 ? 2 : 4; }
+int tc_res_kb(const jtfs_plan* p) { return p->cfg.precision == JTFS_PREC_BF16 ? 4 : 2; }
 
 namespace {
 constexpr size_t kSmemBudget = 225 * 1024;
@@ -918,22 +958,27 @@ size_t tc_smem_for(const jtfs_plan* p, bool res) {
 }
 
 // 16-frame form: resident W tile, operand stages, the weight ring, sixteen 1 KB |Z| staging
-// blocks per plane and the 32 KB column-group reduction buffer
+// blocks per pooling plane and the 32 KB column-group reduction buffer.  apl: bytes of one
+// 128 x 32 W block (8 KB BF16, 16 KB FP32 for TF32); cpl / ppl: contraction / pooling planes;
+// nya: 4 KB Y atoms per part of a 128-sample tile (2 BF16, 4 FP32).
 struct Tc16Shape {
-  int planes, WS;
+  int apl, cpl, ppl, nya, WS;
   size_t fixed(bool res, int res_kb) const {
-    return 1024 + (res ? (size_t)planes * 2 * res_kb * kBM * kBK * 2 : 0) +
-           (size_t)WS * 2 * planes * 16 * 64 * 2 + (size_t)kEpiWarps * planes * 1024 +
-           4 * 128 * 16 * 4;
+    return 1024 + (res ? (size_t)cpl * 2 * res_kb * apl : 0) + (size_t)WS * 2 * ppl * 16 * 64 * 2 +
+           (size_t)kEpiWarps * ppl * 1024 + 4 * 128 * 16 * 4;
   }
   size_t stage(bool res) const {
-    return (res ? 0 : (size_t)planes * 2 * kBM * kBK * 2) + (size_t)planes * 2 * 2 * kBK * 64 * 2;
+    return (res ? 0 : (size_t)cpl * 2 * apl) + (size_t)cpl * 2 * nya * 4096;
   }
 };
 
 Tc16Shape tc16_shape(const jtfs_plan* p) {
   Tc16Shape s;
-  s.planes = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
+  const bool tf = p->cfg.precision == JTFS_PREC_TF32;
+  s.apl = tf ? kBM * kBK * 4 : kBM * kBK * 2;
+  s.cpl = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
+  s.ppl = p->split ? 2 : 1;
+  s.nya = tf ? 4 : 2;
   s.WS = kMaxWS;
   return s;
 }
@@ -989,6 +1034,10 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   auto place = [&](size_t bytes) { size_t at = off; off += (bytes + 1023) & ~(size_t)1023; return at; };
   size_t o_w[6];
   for (int i = 0; i < 6; ++i) o_w[i] = place(wplane * 2);
+  const bool tf = p->cfg.precision == JTFS_PREC_TF32;
+  size_t o_w32[2] = {0, 0};
+  if (tf)
+    for (int i = 0; i < 2; ++i) o_w32[i] = place(wplane * 4);
   const size_t wt_elems = (size_t)p->n2 * NT * Lmax;
   const size_t o_wt = place(wt_elems * 2 * 2);
   const size_t o_items = place(std::max<size_t>(16, p->tc_items.size() * 4));
@@ -997,6 +1046,8 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   if ((st = cuda_check(cudaMalloc(&p->d_tc_mem, off), "tc tables")) != JTFS_OK) return st;
   char* base = (char*)p->d_tc_mem;
   for (int i = 0; i < 6; ++i) p->d_wplanes[i] = base + o_w[i];
+  if (tf)
+    for (int i = 0; i < 2; ++i) p->d_wplanes32[i] = base + o_w32[i];
   p->d_wtf = base + o_wt;
   p->d_tc_items = (int*)(base + o_items);
   p->d_err = (int*)(base + o_err);
@@ -1010,13 +1061,14 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
                                  (__nv_bfloat16*)p->d_wplanes[5]);
   k_build_wt<<<1024, 256>>>(p->dp, NT, Lmax, (__nv_bfloat16*)p->d_wtf,
                             (__nv_bfloat16*)p->d_wtf + wt_elems);
+  if (tf)
+    k_build_wplanes32<<<1024, 256>>>(p->dp, p->n1_pad, (float*)p->d_wplanes32[0],
+                                     (float*)p->d_wplanes32[1]);
   return cuda_check(cudaDeviceSynchronize(), "build tc tables");
 }
 
 jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, const void* ylo_v,
                                 float* Pbuf, float* s2, cudaStream_t st) {
-  const __nv_bfloat16* yhi = (const __nv_bfloat16*)yhi_v;
-  const __nv_bfloat16* ylo = (const __nv_bfloat16*)ylo_v;
   const DevPlan& d = p->dp;
   TcMaps maps;
   std::string err;
@@ -1024,29 +1076,44 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   const int rows = p->C * p->n1;
   const int NT = tc_nt(p->n_t);
   const int BN = tc_bn(p);
+  // TF32: FP32 W planes (rows of 32 lambda' = 128 bytes) and FP32 Y planes (atoms of 32
+  // samples); otherwise BF16 planes
+  const bool tf = p->cfg.precision == JTFS_PREC_TF32;
+  const size_t esz = tf ? 4 : 2;
+  const CUtensorMapDataType dt = tf ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   for (int i = 0; i < 4; ++i) {
     cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)rows};
-    cuuint64_t str[1] = {(cuuint64_t)p->n1_pad * 2};
+    cuuint64_t str[1] = {(cuuint64_t)p->n1_pad * esz};
     cuuint32_t box[2] = {kBK, kBM};
-    if (!make_tmap(&maps.w[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p->d_wplanes[i], dims, str,
-                   box, 64, &err)) {
+    const void* src = tf ? p->d_wplanes32[i & 1] : p->d_wplanes[i];
+    if (!make_tmap(&maps.w[i], dt, 2, src, dims, str, box, tf ? 128 : 64, &err)) {
       set_error(err);
       return JTFS_ERR_CUDA;
     }
   }
   for (int h = 0; h < 2; ++h) {
-    const __nv_bfloat16* base = h == 0 ? yhi : ylo;
+    const char* base = (const char*)(h == 0 ? yhi_v : ylo_v);
     for (int a = 0; a < 16; ++a) {
       if (a >= p->n2 || p->rates2[a].s == 0 || (passes == 1 && h == 1)) {
         maps.y[h][a] = maps.w[0];
         continue;
       }
       const Rate2& A = p->rates2[a];
-      cuuint64_t dims[3] = {(cuuint64_t)A.L, (cuuint64_t)A.K, (cuuint64_t)(2 * B)};
-      cuuint64_t str[2] = {(cuuint64_t)A.L * 2, (cuuint64_t)A.K * A.L * 2};
-      cuuint32_t box[3] = {64, kBK, 1};
-      if (!make_tmap(&maps.y[h][a], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
-                     base + (size_t)B * 2 * A.off_y, dims, str, box, 128, &err)) {
+      bool okm;
+      if (tf) {   // transposed planes [2B][L][kt]
+        cuuint64_t dims[3] = {(cuuint64_t)A.kt, (cuuint64_t)A.L, (cuuint64_t)(2 * B)};
+        cuuint64_t str[2] = {(cuuint64_t)A.kt * 4, (cuuint64_t)A.L * A.kt * 4};
+        cuuint32_t box[3] = {kBK, 128, 1};
+        okm = make_tmap(&maps.y[h][a], dt, 3, base + (size_t)B * 2 * A.off_yt * 4, dims, str,
+                        box, 128, &err);
+      } else {
+        cuuint64_t dims[3] = {(cuuint64_t)A.L, (cuuint64_t)A.K, (cuuint64_t)(2 * B)};
+        cuuint64_t str[2] = {(cuuint64_t)A.L * esz, (cuuint64_t)A.K * A.L * esz};
+        cuuint32_t box[3] = {64, kBK, 1};
+        okm = make_tmap(&maps.y[h][a], dt, 3, base + (size_t)B * 2 * A.off_y * esz, dims, str,
+                        box, 128, &err);
+      }
+      if (!okm) {
         set_error(err);
         return JTFS_ERR_CUDA;
       }
@@ -1073,6 +1140,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   TcArgs args;
   args.B = B;
   args.passes = passes;
+  args.pool_split = p->split ? 1 : 0;
   args.res_kb = tc_res_kb(p);
   args.wstages = f16 ? tc16_shape(p).WS : tc_shape(p).WS;
   args.n_rows = rows;
@@ -1091,13 +1159,13 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       return rc;                                                                                \
     k_joint_fwd_tc<NTV, BNV, RESV><<<grid, kThreads, smem, st>>>(maps, args, d);               \
   } while (0)
-#define JTFS_LAUNCH_TC16(RESV)                                                                  \
+#define JTFS_LAUNCH_TC16(RESV, TFV)                                                             \
   do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_tc16<RESV>,                         \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_tc16<RESV, TFV>,                    \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr tc16")) != JTFS_OK)             \
       return rc;                                                                                \
-    k_joint_fwd_tc16<RESV><<<grid, kThreads, smem, st>>>(maps, args, d);                       \
+    k_joint_fwd_tc16<RESV, TFV><<<grid, kThreads, smem, st>>>(maps, args, d);                  \
   } while (0)
   for (int pass = 0; pass < 2; ++pass) {
     const bool res = pass == 0;
@@ -1109,8 +1177,10 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     args.stages = f16 ? tc16_stages_for(p, res) : tc_stages_for(p, res);
     const size_t smem = f16 ? tc16_smem_for(p, res) : tc_smem_for(p, res);
     const int grid = std::min(args.n_items, n_sm);
-    if (f16) {
-      if (res) JTFS_LAUNCH_TC16(true); else JTFS_LAUNCH_TC16(false);
+    if (f16 && tf) {
+      if (res) JTFS_LAUNCH_TC16(true, true); else JTFS_LAUNCH_TC16(false, true);
+    } else if (f16) {
+      if (res) JTFS_LAUNCH_TC16(true, false); else JTFS_LAUNCH_TC16(false, false);
     } else if (NT == 32) {
       if (res) JTFS_LAUNCH_TC(32, 64, true); else JTFS_LAUNCH_TC(32, 64, false);
     } else {

@@ -1097,7 +1097,7 @@ int tc_nt(int n_t);
 // holds up to KM = 128 lambda' rows (96 for the FP32-grade split, whose hi / lo Y^T tile
 // is twice as large).
 static int tcbf_km(const jtfs_plan* p, int nat) {
-  return nat == 1 ? 64 : (p->cfg.precision == JTFS_PREC_FP32 ? 96 : 128);
+  return nat == 1 ? 64 : (p->split ? 96 : 128);
 }
 
 // Shared memory of the fast form: resident Y^T and weight tiles, then the W ring (2..3
@@ -1105,7 +1105,7 @@ static int tcbf_km(const jtfs_plan* p, int nat) {
 // layout does not fit.
 static bool tcbf_layout(const jtfs_plan* p, int nat, int* wb_out, int* na2_out, size_t* smem_out) {
   const int NT = tc_nt(p->n_t);
-  const int PL = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1, RC = nat == 1 ? 64 : 32;
+  const int PL = p->split ? 2 : 1, RC = nat == 1 ? 64 : 32;
   const int KM = tcbf_km(p, nat);
   const size_t a4 = ((128 * NT * 2 + 1023) / 1024) * 1024;
   const size_t g1p = ((RC * NT * 2 + 1023) / 1024) * 1024;
@@ -1250,7 +1250,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   const int n_chunks = (rows + kRC - 1) / kRC;
   const int g1_rows = tcb_g1_rows(p);
   jtfs_status rc;
-  const bool three = p->cfg.precision == JTFS_PREC_FP32;
+  const bool three = p->split;
   const size_t g1_plane = tcb_g1_bytes(p, B) / 2;
   __nv_bfloat16* g1hi = (__nv_bfloat16*)g1buf;
   __nv_bfloat16* g1lo = (__nv_bfloat16*)((char*)g1buf + g1_plane);

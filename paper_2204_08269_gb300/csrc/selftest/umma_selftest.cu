@@ -89,7 +89,106 @@ __global__ void k_umma_selftest(const __grid_constant__ CUtensorMap ta,
   if (threadIdx.x == 0) *status = failed;
 }
 
+// TF32 form: A [128 x K] FP32 K-major (rows of 32 values, 128-byte swizzle); B FP32, either
+// MN-major (K rows of 128 values held as four 32-value atoms, 128-byte swizzle) or K-major;
+// kind::tf32 MMAs of K = 8.
+__global__ void k_umma_selftest_tf32(const __grid_constant__ CUtensorMap ta,
+                                     const __grid_constant__ CUtensorMap tb, float* D, int K,
+                                     int b_mn, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = sm;                       // K / 32 atoms of 128 rows x 128 B
+  uint8_t* sB = sA + 128 * K * 4;
+  __shared__ uint64_t bar_tma, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    mbar_init(&bar_tma, 1);
+    mbar_init(&bar_mma, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 128);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar_tma, (uint32_t)(128 * K * 4 * 2));
+    for (int k0 = 0; k0 < K; k0 += 32) tma_load_2d(sA + (k0 / 32) * 128 * 128, &ta, k0, 0, &bar_tma);
+    if (b_mn) {
+      for (int n0 = 0; n0 < 128; n0 += 32) tma_load_2d(sB + (n0 / 32) * K * 128, &tb, n0, 0, &bar_tma);
+    } else {
+      for (int k0 = 0; k0 < K; k0 += 32) tma_load_2d(sB + (k0 / 32) * 128 * 128, &tb, k0, 0, &bar_tma);
+    }
+    if (!mbar_wait(&bar_tma, 0, 2000000000ull)) {
+      failed = 1;
+    } else {
+      const uint32_t idesc = instr_desc(128, 128, 2, 2, 0, (uint32_t)b_mn, 0);
+      for (int j = 0; j < K / 8; ++j) {
+        const int atom = (j * 8) / 32, off = ((j * 8) % 32) * 4;
+        const uint64_t ad = smem_desc(smem_u32(sA + atom * 128 * 128 + off), 16, 1024, kSw128);
+        const uint64_t bd = b_mn
+            ? smem_desc(smem_u32(sB + j * 8 * 128), (uint32_t)(K * 128), 1024, kSw128)
+            : smem_desc(smem_u32(sB + atom * 128 * 128 + off), 16, 1024, kSw128);
+        mma_tf32(tbase, ad, bd, idesc, j > 0 ? 1u : 0u);
+      }
+      mma_commit(&bar_mma);
+    }
+  }
+  __syncthreads();
+  if (!failed) {
+    if (!mbar_wait(&bar_mma, 0, 2000000000ull)) atomicExch(&failed, 1);
+  }
+  tc_fence_after();
+  if (!failed) {
+    const int row = warp * 32 + lane;
+    for (int c0 = 0; c0 < 128; c0 += 16) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) D[row * 128 + c0 + i] = v[i];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 128);
+  if (threadIdx.x == 0) *status = failed;
+}
+
 }  // namespace
+
+extern "C" int jtfs_selftest_umma_tf32(const float* A, const float* B, float* D, int K, int b_mn,
+                                       int* status_dev, void* stream) {
+  if (K < 32 || K > 64 || K % 32) return 1;
+  CUtensorMap ta, tb;
+  std::string err;
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)K, 128};
+    cuuint64_t str[1] = {(cuuint64_t)K * 4};
+    cuuint32_t box[2] = {32, 128};
+    if (!make_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, A, dims, str, box, 128, &err)) return 2;
+  }
+  if (b_mn) {
+    cuuint64_t dims[2] = {128, (cuuint64_t)K};
+    cuuint64_t str[1] = {128 * 4};
+    cuuint32_t box[2] = {32, (cuuint32_t)K};
+    if (!make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, B, dims, str, box, 128, &err)) return 2;
+  } else {
+    cuuint64_t dims[2] = {(cuuint64_t)K, 128};
+    cuuint64_t str[1] = {(cuuint64_t)K * 4};
+    cuuint32_t box[2] = {32, 128};
+    if (!make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, B, dims, str, box, 128, &err)) return 2;
+  }
+  const size_t smem = 1024 + (size_t)128 * K * 4 * 2;
+  cudaFuncSetAttribute(k_umma_selftest_tf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_umma_selftest_tf32<<<1, 128, smem, (cudaStream_t)stream>>>(ta, tb, D, K, b_mn, status_dev);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
 
 extern "C" int jtfs_selftest_umma(const void* A, const void* B, float* D, int K, int a_swz,
                                   int b_mn, int* status_dev, void* stream) {

@@ -68,8 +68,8 @@ __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R
 // Batched Y producer: one CTA takes G consecutive rows lambda'_0 .. lambda'_0 + G - 1 of one
 // rate (G L_alpha samples fit the launch's shared memory), folds them into shared memory in
 // bit-reversed order, runs one batched inverse FFT and writes the rows: complex FP32
-// (OUT_BF16 = 0) or BF16 planes hi (and lo when ylo is given) in the contraction layout
-// [alpha][2 b + part][lambda' - lam_min][n].  The fold only visits bins below the rate's
+// (OUT_BF16 = 0), BF16 planes hi (and lo when ylo is given; OUT_BF16 = 1) or FP32 planes
+// (OUT_BF16 = 2) in the contraction layout [alpha][2 b + part][lambda' - lam_min][n].  The fold only visits bins below the rate's
 // psi-hat support end.
 constexpr int kRowThreads = 512;
 constexpr int kMaxRowsPerItem = 512;   // G <= rows_cap / 32
@@ -110,12 +110,24 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
   }
   __syncthreads();
   fft_dit_rows<+1>(sm, logL, G, twl_for(P, logL), logL);
-  if (!OUT_BF16) {
+  if (OUT_BF16 == 0) {
     float2* ya = y + (size_t)b * P.y_len + A.off_y + (size_t)(lam0 - A.lam_min) * L;
     for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
       const float inv = s_inv[idx >> logL];
       const float2 v = sm[idx];
       ya[idx] = make_float2(v.x * inv, v.y * inv);
+    }
+  } else if (OUT_BF16 == 2) {
+    // FP32 planes in the contraction layout (the TF32 operands)
+    float* yf = reinterpret_cast<float*>(y);
+    const size_t plane = (size_t)A.K * L;
+    const size_t base = (size_t)B * 2 * A.off_y + (size_t)(2 * b) * plane + (size_t)(lam0 - A.lam_min) * L;
+    for (int i2 = threadIdx.x; i2 < (G * L) >> 1; i2 += blockDim.x) {
+      const int idx = 2 * i2;
+      const float inv = s_inv[idx >> logL];
+      const float2 v0 = sm[idx], v1 = sm[idx + 1];
+      *reinterpret_cast<float2*>(yf + base + idx) = make_float2(v0.x * inv, v1.x * inv);
+      *reinterpret_cast<float2*>(yf + base + plane + idx) = make_float2(v0.y * inv, v1.y * inv);
     }
   } else {
     // rows of one rate are contiguous in each plane: element idx of the block sits at

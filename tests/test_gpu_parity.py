@@ -12,8 +12,9 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 TOL = {"fp32": 1e-4, "fp32_simt": 1e-4, "tf32": 1e-3, "bf16": 2e-2}
-GTOL = {"fp32": 1e-3, "fp32_simt": 1e-3, "tf32": 1e-2, "bf16": 5e-2}
-PRECS = ["fp32_simt", "fp32", "bf16"]
+# TF32: unit roundoff 2^-11 on each contraction operand; its backward is the FP32-grade one
+GTOL = {"fp32": 1e-3, "fp32_simt": 1e-3, "tf32": 1e-3, "bf16": 5e-2}
+PRECS = ["fp32_simt", "fp32", "bf16", "tf32"]
 
 SMALL_CFGS = [
     dict(N=512, J=5, Q=4, J_fr=3, Q_fr=1, T=32, F=4),
@@ -37,8 +38,15 @@ def _cuda():
 
 def _plans(cfg, precision):
     from paper_2204_08269_gb300 import JTFSPlan
+    from paper_2204_08269_gb300.jtfs import JTFSError
     kw = dict(cfg)
-    return JTFSPlan(**kw, precision=precision)
+    try:
+        return JTFSPlan(**kw, precision=precision)
+    except JTFSError as e:
+        # the TF32 contraction exists in the 16-frame form only
+        if precision == "tf32" and e.status == 2:
+            pytest.skip("TF32 contraction needs 16 pooled frames")
+        raise
 
 
 def _oracle(cfg):
@@ -173,7 +181,7 @@ def test_backward_workload2_sampled(prec):
     _check_backward(plan, x, op, sc, GTOL[prec], idx=[11])
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
 def test_tensor_core_matches_cuda_core_form(prec):
     """The tcgen05 contraction and the CUDA-core FP32 form agree on the same input."""
     cfg = _workload_cfg(2)

@@ -39,3 +39,30 @@ def test_umma_bf16_gemm(st, K, a_swz, b_mn):
     ref = A.float() @ Bkn.float()
     err = (D - ref).abs().max().item() / ref.abs().max().item()
     assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("K,b_mn", [(32, 0), (64, 0)])
+def test_umma_tf32_gemm(K, b_mn):
+    """kind::tf32 with A and B K-major, against FP64 products of the FP32 operands (TF32
+    keeps 10 mantissa bits).  An MN-major B operand gives zeros for kind::tf32 on this
+    hardware (measured with this kernel), so the TF32 contraction reads Y transposed."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_08269_gb300 import build
+    build.build()
+    L = ctypes.CDLL(build.SELFTEST_LIB)
+    f = L.jtfs_selftest_umma_tf32
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int] * 2 + [ctypes.c_void_p] * 2
+    f.restype = ctypes.c_int
+    g = torch.Generator(device="cuda").manual_seed(7 * K + b_mn)
+    A = torch.randn(128, K, device="cuda", generator=g).contiguous()
+    Bkn = torch.randn(K, 128, device="cuda", generator=g)
+    B = Bkn.contiguous() if b_mn else Bkn.t().contiguous()
+    D = torch.full((128, 128), float("nan"), device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert f(A.data_ptr(), B.data_ptr(), D.data_ptr(), K, b_mn, status.data_ptr(), None) == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = A.double() @ Bkn.double()
+    err = (D.double() - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 2e-3, err
