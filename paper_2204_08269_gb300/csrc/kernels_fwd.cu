@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "stages.cuh"
+#include "umma.cuh"
 
 namespace jtfs {
 namespace {
@@ -198,7 +199,7 @@ k_joint_fwd_simt(DevPlan P, const float2* __restrict__ y, float* __restrict__ s2
 
 // Transposed FP32 Y planes for the TF32 contraction (its MMAs take K-major operands only):
 // yt[alpha][2 b + part][n][lambda' - (lam_min & ~7)] = y[alpha][2 b + part][lambda' - lam_min][n],
-// zero for lam_min & ~7 <= lambda' < lam_min and in the padding up to kt.  32 x 32 tiles
+// rounded to TF32, zero for lam_min & ~7 <= lambda' < lam_min and in the padding up to kt.  32 x 32 tiles
 // through shared memory; grid (ceil(L / 32), ceil(kt / 32), 2 B) for one rate.
 __global__ void k_transpose_yt(DevPlan P, int a, const float* __restrict__ y,
                                float* __restrict__ yt, int B) {
@@ -219,7 +220,7 @@ __global__ void k_transpose_yt(DevPlan P, int a, const float* __restrict__ y,
   __syncthreads();
   for (int ty = threadIdx.y; ty < 32; ty += blockDim.y) {
     const int n = n0 + ty, c = c0 + tx;
-    if (n < A.L && c < A.kt) dst[(size_t)n * A.kt + c] = tile[tx][ty];
+    if (n < A.L && c < A.kt) dst[(size_t)n * A.kt + c] = umma::tf32_rna(tile[tx][ty]);
   }
 }
 

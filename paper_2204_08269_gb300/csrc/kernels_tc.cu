@@ -856,7 +856,8 @@ __global__ void k_build_wplanes(DevPlan Pd, int n1_pad, __nv_bfloat16* wr_hi, __
   }
 }
 
-// FP32 W planes for the TF32 forward: Wr, Wi [C * n1][n1_pad], zero for lambda' >= n1.
+// FP32 W planes for the TF32 forward: Wr, Wi [C * n1][n1_pad] rounded to TF32, zero for
+// lambda' >= n1.
 __global__ void k_build_wplanes32(DevPlan Pd, int n1_pad, float* wr, float* wi) {
   const long long total = (long long)Pd.C * Pd.n1 * n1_pad;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -865,8 +866,8 @@ __global__ void k_build_wplanes32(DevPlan Pd, int n1_pad, float* wr, float* wi) 
     const int c = r / Pd.n1, lam = r % Pd.n1;
     float2 v = make_float2(0.f, 0.f);
     if (lp < Pd.n1) v = Pd.h[(size_t)c * Pd.N_fr + ((lam - lp) & (Pd.N_fr - 1))];
-    wr[i] = v.x;
-    wi[i] = v.y;
+    wr[i] = tf32_rna(v.x);
+    wi[i] = tf32_rna(v.y);
   }
 }
 

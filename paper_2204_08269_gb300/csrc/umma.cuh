@@ -88,6 +88,14 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
+// FP32 -> TF32 (10 mantissa bits) rounded to nearest, ties away; the tensor cores would
+// otherwise drop the low bits of FP32 operands (a biased truncation).
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 // ---------------------------------------------------------------- TMEM
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {  // whole warp
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
