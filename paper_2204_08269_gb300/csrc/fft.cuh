@@ -206,3 +206,64 @@ __device__ void fft_dif_rows(float2* buf, int logL, int G, const float2* __restr
 }
 
 }  // namespace jtfs
+
+namespace jtfs {
+
+// Register-radix forms for a padded layout: element i of a row block lives at
+// fft_pad(i) = i + i / 16 (one float2 of padding per 16), which keeps the strided accesses
+// of the first passes free of bank conflicts.  A pass fuses RB consecutive radix-2 DIT
+// stages s0 .. s0 + RB - 1 in registers: each thread loads 2^RB elements at stride
+// q = 2^(s0-1), applies the stages with the twiddles of the L-point table tw
+// (exp(-2 pi i m / L), m < L / 2) and stores them back.
+__device__ __forceinline__ int fft_pad(int i) { return i + (i >> 4); }
+
+template <int SIGN, int RB>
+__device__ __forceinline__ void fft_dit_pass(float2* buf, int logL, int G,
+                                             const float2* __restrict__ tw, int s0) {
+  constexpr int R = 1 << RB;
+  const int q = 1 << (s0 - 1);
+  const int lgpr = logL - RB;                 // log2 of the groups per row
+  const int groups = G << lgpr;
+  for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+    const int row = g >> lgpr, b = g & ((1 << lgpr) - 1);
+    const int j = b & (q - 1);
+    const int base = (row << logL) + ((b >> (s0 - 1)) << (s0 - 1 + RB)) + j;
+    float2 v[R];
+#pragma unroll
+    for (int m = 0; m < R; ++m) v[m] = buf[fft_pad(base + m * q)];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int sh = logL - s0 - u;
+      float2 w[1 << (RB - 1)];
+#pragma unroll
+      for (int ml = 0; ml < (1 << u); ++ml) w[ml] = twiddle<SIGN>(tw, (j + q * ml) << sh);
+#pragma unroll
+      for (int m = 0; m < R; ++m) {
+        if (m & (1 << u)) continue;
+        const int mp = m + (1 << u);
+        const float2 t = cmul(v[mp], w[m & ((1 << u) - 1)]);
+        v[mp] = make_float2(v[m].x - t.x, v[m].y - t.y);
+        v[m] = make_float2(v[m].x + t.x, v[m].y + t.y);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < R; ++m) buf[fft_pad(base + m * q)] = v[m];
+  }
+  __syncthreads();
+}
+
+// G rows of length 2^logL (padded layout, bit-reversed input, natural output): a first pass
+// of logL mod 4 stages, then radix-16 passes.  Every thread of the block must call it.
+template <int SIGN>
+__device__ void fft_dit_rows_r16(float2* buf, int logL, int G, const float2* __restrict__ tw) {
+  int s0 = 1;
+  switch (logL & 3) {
+    case 1: fft_dit_pass<SIGN, 1>(buf, logL, G, tw, s0); s0 += 1; break;
+    case 2: fft_dit_pass<SIGN, 2>(buf, logL, G, tw, s0); s0 += 2; break;
+    case 3: fft_dit_pass<SIGN, 3>(buf, logL, G, tw, s0); s0 += 3; break;
+    default: break;
+  }
+  for (; s0 + 3 <= logL; s0 += 4) fft_dit_pass<SIGN, 4>(buf, logL, G, tw, s0);
+}
+
+}  // namespace jtfs

@@ -93,7 +93,7 @@ struct jtfs_plan {
   std::vector<int> pairs;  // (alpha, lambda') work items of the second-order kernels
   std::vector<int> rowitems;  // (alpha, lambda'_0, G, 0): G rows of one rate per CTA
   int rows_cap;               // samples one row item holds (G L_alpha <= rows_cap)
-  int row_threads = 512;      // threads per CTA of the row producer (autotuned)
+  int row_threads = 256;      // threads per CTA of the row producer (autotuned)
   bool split = false;         // BF16 hi / lo split (FP32-grade products; TF32 plans' backward)
   void* d_wplanes32[2] = {nullptr, nullptr};   // Wr, Wi FP32 [C * n1][n1_pad] (TF32 forward)
   int* d_rowitems;

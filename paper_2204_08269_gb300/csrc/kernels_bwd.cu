@@ -300,10 +300,11 @@ jtfs_status set_attrs() {
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr");
     if (st != JTFS_OK) return st;
   }
-  // the row producer holds at most 2^14 complex samples next to its static row tables
+  // the row producer holds at most 2^14 complex samples (padded one per 16) next to its
+  // static row tables
   for (const void* f : {(const void*)k_second_order_rows<0>, (const void*)k_second_order_rows<1>}) {
     jtfs_status st = cuda_check(
-        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024), "attr");
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024), "attr");
     if (st != JTFS_OK) return st;
   }
   g_attrs_set = true;
@@ -338,7 +339,7 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
     {
       StageScope sc(p, kStSecondOrder, st, 1);
       k_second_order_rows<1><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
-                              (size_t)p->rows_cap * 8, st>>>(
+                              (size_t)p->rows_cap * 17 / 2, st>>>(
           d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, nullptr,
           (__nv_bfloat16*)w.ybh, (__nv_bfloat16*)w.ybl, B);
     }
@@ -349,7 +350,7 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
     {
       StageScope sc(p, kStSecondOrder, st, 1);
       k_second_order_rows<0><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
-                              (size_t)p->rows_cap * 8, st>>>(
+                              (size_t)p->rows_cap * 17 / 2, st>>>(
           d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, w.y, nullptr, nullptr, B);
     }
     StageScope sc(p, kStJointBwd, st, 1);

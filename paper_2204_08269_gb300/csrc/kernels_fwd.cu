@@ -233,8 +233,9 @@ jtfs_status set_attrs(const jtfs_plan* p) {
   jtfs_status st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_xfft_sub, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_scalogram, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
-  // the row producer holds at most 2^14 complex samples next to its static row tables
-  const int rows_smem = 128 * 1024;
+  // the row producer holds at most 2^14 complex samples (padded one per 16) next to its
+  // static row tables
+  const int rows_smem = 140 * 1024;
   if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
@@ -292,7 +293,7 @@ jtfs_status autotune_rows(jtfs_plan* p, int B, const Workspace& w, cudaStream_t 
       if (rc != JTFS_OK) break;
       auto launch = [&]() {
         const dim3 grid((unsigned)(items.size() / 4), B);
-        const size_t smem = (size_t)caps[ci] * 8;
+        const size_t smem = (size_t)caps[ci] * 17 / 2;   // padded one per 16
         if (p->use_tc)
           k_second_order_rows<1><<<grid, threads, smem, st>>>(
               d, reinterpret_cast<const int4*>(d_items), w.uh, nullptr, (__nv_bfloat16*)w.ybh,
@@ -355,7 +356,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
     if (!p->pairs.empty()) {
       StageScope sc(p, kStSecondOrder, st, 1);
       k_second_order_rows<2><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
-                              (size_t)p->rows_cap * 8, st>>>(
+                              (size_t)p->rows_cap * 17 / 2, st>>>(
           d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, w.y, nullptr, nullptr, B);
     }
     {
@@ -374,7 +375,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
     if (!p->pairs.empty()) {
       StageScope sc(p, kStSecondOrder, st, 1);
       k_second_order_rows<1><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
-                              (size_t)p->rows_cap * 8, st>>>(
+                              (size_t)p->rows_cap * 17 / 2, st>>>(
           d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, nullptr,
           (__nv_bfloat16*)w.ybh, (__nv_bfloat16*)w.ybl, B);
     }
@@ -385,7 +386,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
     if (!p->pairs.empty()) {
       StageScope sc(p, kStSecondOrder, st, 1);
       k_second_order_rows<0><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
-                              (size_t)p->rows_cap * 8, st>>>(
+                              (size_t)p->rows_cap * 17 / 2, st>>>(
           d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, w.y, nullptr, nullptr, B);
     }
     StageScope sc(p, kStJointFwd, st, 1);

@@ -66,8 +66,9 @@ __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R
 }
 
 // Batched Y producer: one CTA takes G consecutive rows lambda'_0 .. lambda'_0 + G - 1 of one
-// rate (G L_alpha samples fit the launch's shared memory), folds them into shared memory in
-// bit-reversed order, runs one batched inverse FFT and writes the rows: complex FP32
+// rate (G L_alpha samples fit the launch's shared memory, padded one per 16), folds them into
+// shared memory in bit-reversed order, runs one batched register-radix inverse FFT and writes
+// the rows: complex FP32
 // (OUT_BF16 = 0), BF16 planes hi (and lo when ylo is given; OUT_BF16 = 1) or FP32 planes
 // (OUT_BF16 = 2) in the contraction layout [alpha][2 b + part][lambda' - lam_min][n].  The fold only visits bins below the rate's
 // psi-hat support end.
@@ -106,15 +107,15 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
       acc.x += u.x * f;
       acc.y += u.y * f;
     }
-    sm[(row << logL) + bitrev(kp, logL)] = acc;
+    sm[fft_pad((row << logL) + bitrev(kp, logL))] = acc;
   }
   __syncthreads();
-  fft_dit_rows<+1>(sm, logL, G, twl_for(P, logL), logL);
+  fft_dit_rows_r16<+1>(sm, logL, G, twl_for(P, logL));
   if (OUT_BF16 == 0) {
     float2* ya = y + (size_t)b * P.y_len + A.off_y + (size_t)(lam0 - A.lam_min) * L;
     for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
       const float inv = s_inv[idx >> logL];
-      const float2 v = sm[idx];
+      const float2 v = sm[fft_pad(idx)];
       ya[idx] = make_float2(v.x * inv, v.y * inv);
     }
   } else if (OUT_BF16 == 2) {
@@ -125,7 +126,7 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
     for (int i2 = threadIdx.x; i2 < (G * L) >> 1; i2 += blockDim.x) {
       const int idx = 2 * i2;
       const float inv = s_inv[idx >> logL];
-      const float2 v0 = sm[idx], v1 = sm[idx + 1];
+      const float2 v0 = sm[fft_pad(idx)], v1 = sm[fft_pad(idx + 1)];
       *reinterpret_cast<float2*>(yf + base + idx) = make_float2(v0.x * inv, v1.x * inv);
       *reinterpret_cast<float2*>(yf + base + plane + idx) = make_float2(v0.y * inv, v1.y * inv);
     }
@@ -137,7 +138,7 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
     for (int i2 = threadIdx.x; i2 < (G * L) >> 1; i2 += blockDim.x) {
       const int idx = 2 * i2;
       const float inv = s_inv[idx >> logL];
-      const float2 v0 = sm[idx], v1 = sm[idx + 1];
+      const float2 v0 = sm[fft_pad(idx)], v1 = sm[fft_pad(idx + 1)];
       const float r0 = v0.x * inv, r1 = v1.x * inv, i0 = v0.y * inv, i1 = v1.y * inv;
       const __nv_bfloat162 hr = __floats2bfloat162_rn(r0, r1), hi_ = __floats2bfloat162_rn(i0, i1);
       *reinterpret_cast<__nv_bfloat162*>(yhi + base + idx) = hr;
