@@ -23,11 +23,12 @@ k_uh_from_u1(DevPlan P, const float* __restrict__ u1, float2* __restrict__ uh) {
   const int lam = blockIdx.x, b = blockIdx.y;
   const Row1 R = P.rows1[lam];
   const float* ub = u1 + (size_t)b * P.u1_len + R.off_u;
-  for (int m = threadIdx.x; m < R.L; m += blockDim.x) sm[m] = make_float2(ub[m], 0.f);
+  for (int m = threadIdx.x; m < R.L; m += blockDim.x)
+    sm[fft_pad(bitrev(m, R.logL))] = make_float2(ub[m], 0.f);
   __syncthreads();
-  fft_dif<-1>(sm, R.logL, twl_for(P, R.logL), R.logL);
+  fft_dit_rows_r16<-1>(sm, R.logL, 1, twl_for(P, R.logL));
   float2* hb = uh + (size_t)b * P.uh_len + R.off_uh;
-  for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[bitrev(k, R.logL)];
+  for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[fft_pad(k)];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -175,13 +176,13 @@ k_second_order_bwd(DevPlan P, const float2* __restrict__ gy, const float* __rest
     if (A.s == 0 || lam < A.lam_min) continue;
     __syncthreads();
     const float2* g = gy + (size_t)b * P.y_len + A.off_y + (size_t)(lam - A.lam_min) * A.L;
-    for (int m = threadIdx.x; m < A.L; m += blockDim.x) tmp[m] = g[m];
+    for (int m = threadIdx.x; m < A.L; m += blockDim.x) tmp[fft_pad(bitrev(m, A.logL))] = g[m];
     __syncthreads();
-    fft_dif<-1>(tmp, A.logL, twl_for(P, A.logL), A.logL);
+    fft_dit_rows_r16<-1>(tmp, A.logL, 1, twl_for(P, A.logL));
     const float* psi = P.psi2 + (size_t)a * P.K2max;
     const int kend = min(half, A.k2e);
     for (int k = 1 + threadIdx.x; k < kend; k += blockDim.x) {
-      const float2 v = tmp[bitrev(k & (A.L - 1), A.logL)];
+      const float2 v = tmp[fft_pad(k & (A.L - 1))];
       const float f = __ldg(&psi[k]) * invLr;
       guh[k].x += v.x * f;
       guh[k].y += v.y * f;
@@ -189,13 +190,13 @@ k_second_order_bwd(DevPlan P, const float2* __restrict__ gy, const float* __rest
   }
   __syncthreads();
   for (int k = threadIdx.x; k < R.L; k += blockDim.x)
-    tmp[bitrev(k, R.logL)] = (k < half) ? guh[k] : make_float2(0.f, 0.f);
+    tmp[fft_pad(bitrev(k, R.logL))] = (k < half) ? guh[k] : make_float2(0.f, 0.f);
   __syncthreads();
-  fft_dit<+1>(tmp, R.logL, twl_for(P, R.logL), R.logL);
+  fft_dit_rows_r16<+1>(tmp, R.logL, 1, twl_for(P, R.logL));
   const float* g1 = gs1 ? gs1 + ((size_t)b * P.n1 + lam) * P.n_t : nullptr;
   float* out = gu1 + (size_t)b * P.u1_len + R.off_u;
   for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
-    float v = tmp[m].x;
+    float v = tmp[fft_pad(m)].x;
     if (g1) {
       float s = 0.f;
       for (int t = 0; t < P.n_t; ++t) s += __ldg(&P.phiT[(t * P.T - m * R.s) & (P.N - 1)]) * g1[t];
@@ -213,20 +214,25 @@ k_stage1_bwd(DevPlan P, const float2* __restrict__ xh, const float* __restrict__
   const Row1 R = P.rows1[lam];
   fold_first_order(P, R, xh + (size_t)b * (P.N >> 1), sm);
   __syncthreads();
-  fft_dit<+1>(sm, R.logL, twl_for(P, R.logL), R.logL);
+  fft_dit_rows_r16<+1>(sm, R.logL, 1, twl_for(P, R.logL));
+  // gz = g_U1 z / |z| (0 at z = 0), stored bit-reversed for the forward FFT: every thread
+  // handles the pairs (m, bitrev(m)) with m <= bitrev(m), so the permutation is in place
   const float* g = gu1 + (size_t)b * P.u1_len + R.off_u;
   for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
-    const float2 z = sm[m];  // N * z
-    const float mag = hypotf(z.x, z.y);
-    const float f = (mag > 0.f) ? g[m] / mag : 0.f;
-    sm[m] = make_float2(z.x * f, z.y * f);
+    const int r = bitrev(m, R.logL);
+    if (m > r) continue;
+    const float2 zm = sm[fft_pad(m)], zr = sm[fft_pad(r)];   // N * z
+    const float am = hypotf(zm.x, zm.y), ar = hypotf(zr.x, zr.y);
+    const float fm = (am > 0.f) ? g[m] / am : 0.f, fr = (ar > 0.f) ? g[r] / ar : 0.f;
+    sm[fft_pad(r)] = make_float2(zm.x * fm, zm.y * fm);
+    sm[fft_pad(m)] = make_float2(zr.x * fr, zr.y * fr);
   }
   __syncthreads();
-  fft_dif<-1>(sm, R.logL, twl_for(P, R.logL), R.logL);
+  fft_dit_rows_r16<-1>(sm, R.logL, 1, twl_for(P, R.logL));
   const float invN = 1.f / (float)P.N;
   float2* out = gf + (size_t)b * P.u1_len + R.off_u;
   for (int k = threadIdx.x; k < R.L; k += blockDim.x) {
-    const float2 v = sm[bitrev(k, R.logL)];
+    const float2 v = sm[fft_pad(k)];
     out[k] = make_float2(v.x * invN, v.y * invN);
   }
 }
@@ -272,15 +278,15 @@ k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, f
       acc.x += v.x * w.x - v.y * w.y;
       acc.y += v.x * w.y + v.y * w.x;
     }
-    sm[bitrev(kp, P.logM)] = acc;
+    sm[fft_pad(bitrev(kp, P.logM))] = acc;
   }
   __syncthreads();
-  fft_dit<+1>(sm, P.logM, twl_for(P, P.logM), P.logM);
+  fft_dit_rows_r16<+1>(sm, P.logM, 1, twl_for(P, P.logM));
   const float* g0 = gs0 ? gs0 + (size_t)b * P.n_t : nullptr;
   float* out = gx + (size_t)b * P.N;
   for (int m = threadIdx.x; m < P.M; m += blockDim.x) {
     const int n = r + P.D * m;
-    float v = sm[m].x;
+    float v = sm[fft_pad(m)].x;
     if (g0)
       for (int t = 0; t < P.n_t; ++t) v += __ldg(&P.phiT[(t * P.T - n) & (P.N - 1)]) * g0[t];
     out[n] = v;
@@ -327,12 +333,12 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
   // recompute x-hat, U1-hat and Y from x and the checkpoint
   {
     StageScope sc(p, kStXfft, st, 2);
-    k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 8, st>>>(d, x, w.xsub);
+    k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, w.xsub);
     k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.xsub, w.xh);
   }
   {
     StageScope sc(p, kStUhFromU1, st, 1);
-    k_uh_from_u1<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 8, st>>>(d, u1, w.uh);
+    k_uh_from_u1<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 17 / 2, st>>>(d, u1, w.uh);
   }
   const size_t n_items = p->items.size() / 2;
   if (gs2 && n_items > 0 && p->use_tcb) {
@@ -359,20 +365,20 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
   } else if (p->y_len > 0) {
     cudaMemsetAsync(w.gy, 0, (size_t)B * p->y_len * sizeof(float2), st);
   }
-  const size_t sob = ((size_t)(p->L1max / 2 > 0 ? p->L1max / 2 : 1) +
-                      (size_t)(p->L2max > p->L1max ? p->L2max : p->L1max)) * 8;
+  const size_t maxL = (size_t)(p->L2max > p->L1max ? p->L2max : p->L1max);
+  const size_t sob = ((size_t)(p->L1max / 2 > 0 ? p->L1max / 2 : 1) + maxL + maxL / 16) * 8;
   {
     StageScope sc(p, kStSecondOrderBwd, st, 1);
     k_second_order_bwd<<<dim3(p->n1, B), kFftThreads, sob, st>>>(d, w.gy, gs1, w.gu1);
   }
   {
     StageScope sc(p, kStStage1Bwd, st, 1);
-    k_stage1_bwd<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 8, st>>>(d, w.xh, w.gu1, w.gf);
+    k_stage1_bwd<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 17 / 2, st>>>(d, w.xh, w.gu1, w.gf);
   }
   {
     StageScope sc(p, kStGx, st, 2);
     k_gxh<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.gf, w.gxh);
-    k_gx<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 8, st>>>(d, w.gxh, gs0, gx);
+    k_gx<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, w.gxh, gs0, gx);
   }
   return cuda_check(cudaGetLastError(), "backward launch");
 }

@@ -49,20 +49,22 @@ k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
   extern __shared__ float2 sm[];
   const int lam = blockIdx.x, b = blockIdx.y;
   const Row1 R = P.rows1[lam];
-  float* su = reinterpret_cast<float*>(sm + R.L);
+  float* su = reinterpret_cast<float*>(sm + R.L + (R.L >> 4));   // after the padded row
   fold_first_order(P, R, xh + (size_t)b * (P.N >> 1), sm);
   __syncthreads();
-  fft_dit<+1>(sm, R.logL, twl_for(P, R.logL), R.logL);
+  fft_dit_rows_r16<+1>(sm, R.logL, 1, twl_for(P, R.logL));
   const float invN = 1.f / (float)P.N;
   float* ub = u1 + (size_t)b * P.u1_len + R.off_u;
   for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
-    const float2 z = sm[m];
+    const float2 z = sm[fft_pad(m)];
     const float a = hypotf(z.x, z.y) * invN;
     ub[m] = a;
     su[m] = a;
-    sm[m] = make_float2(a, 0.f);
   }
   __syncthreads();
+  // the row again, bit-reversed, for the forward FFT
+  for (int m = threadIdx.x; m < R.L; m += blockDim.x)
+    sm[fft_pad(bitrev(m, R.logL))] = make_float2(su[m], 0.f);
   // S1[lambda, t] = sum_m s phi_T[(tT - m s) mod N] U1[m]   (one warp per frame)
   {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -74,9 +76,10 @@ k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
       if (l == 0) s1[((size_t)b * P.n1 + lam) * P.n_t + t] = acc * (float)R.s;
     }
   }
-  fft_dif<-1>(sm, R.logL, twl_for(P, R.logL), R.logL);
+  __syncthreads();
+  fft_dit_rows_r16<-1>(sm, R.logL, 1, twl_for(P, R.logL));
   float2* hb = uh + (size_t)b * P.uh_len + R.off_uh;
-  for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[bitrev(k, R.logL)];
+  for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[fft_pad(k)];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -340,7 +343,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   const DevPlan& d = p->dp;
   {
     StageScope sc(p, kStXfft, st, 2);
-    k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 8, st>>>(d, x, w.xsub);
+    k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, w.xsub);
     k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.xsub, w.xh);
   }
   {
@@ -349,7 +352,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   }
   {
     StageScope sc(p, kStScalogram, st, 1);
-    k_scalogram<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 12, st>>>(d, w.xh, u1, w.uh, s1);
+    k_scalogram<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, w.xh, u1, w.uh, s1);
   }
   if (p->use_tc && p->cfg.precision == JTFS_PREC_TF32) {
     // TF32 operands: Y as FP32 planes (in the complex FP32 buffer, same size)
@@ -469,10 +472,10 @@ jtfs_status launch_first_order_static(const jtfs_plan* p, const float* x, int B,
   c += a(Bz * p->u1_len * 4);
   float2* uh = (float2*)c;
   const DevPlan& d = p->dp;
-  k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 8, st>>>(d, x, xsub);
+  k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, xsub);
   k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, xsub, xh);
   k_s0<<<dim3(p->n_t, B), 256, 0, st>>>(d, x, s0);
-  k_scalogram<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 12, st>>>(d, xh, u1, uh, s1);
+  k_scalogram<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, xh, u1, uh, s1);
   return cuda_check(cudaGetLastError(), "first-order static launch");
 }
 

@@ -20,11 +20,11 @@ k_xfft_sub(DevPlan P, const float* __restrict__ x, float2* __restrict__ xsub) {
   const int r = blockIdx.x, b = blockIdx.y;
   const float* xb = x + (size_t)b * P.N;
   for (int m = threadIdx.x; m < P.M; m += blockDim.x)
-    sm[m] = make_float2(__ldg(&xb[r + (size_t)P.D * m]), 0.f);
+    sm[fft_pad(bitrev(m, P.logM))] = make_float2(__ldg(&xb[r + (size_t)P.D * m]), 0.f);
   __syncthreads();
-  fft_dif<-1>(sm, P.logM, twl_for(P, P.logM), P.logM);
+  fft_dit_rows_r16<-1>(sm, P.logM, 1, twl_for(P, P.logM));
   float2* out = xsub + ((size_t)b * P.D + r) * P.M;
-  for (int k = threadIdx.x; k < P.M; k += blockDim.x) out[k] = sm[bitrev(k, P.logM)];
+  for (int k = threadIdx.x; k < P.M; k += blockDim.x) out[k] = sm[fft_pad(k)];
 }
 
 __global__ void k_xfft_combine(DevPlan P, const float2* __restrict__ xsub, float2* __restrict__ xh) {
@@ -47,7 +47,7 @@ __global__ void k_xfft_combine(DevPlan P, const float2* __restrict__ xsub, float
 }
 
 // Periodisation of x-hat * psi-hat_lambda onto L bins: F[k'] = sum_{k = k' mod L} x-hat[k] psi[k],
-// written to buf in bit-reversed order for the decimation-in-time inverse FFT.
+// written to buf in bit-reversed order (padded layout) for the decimation-in-time inverse FFT.
 __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R,
                                                  const float2* __restrict__ xb, float2* buf) {
   const float* v = P.psi1 + R.off_v;
@@ -61,7 +61,7 @@ __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R
       acc.x += a.x * f;
       acc.y += a.y * f;
     }
-    buf[bitrev(kp, R.logL)] = acc;
+    buf[fft_pad(bitrev(kp, R.logL))] = acc;
   }
 }
 
