@@ -369,7 +369,7 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
   const size_t sob = ((size_t)(p->L1max / 2 > 0 ? p->L1max / 2 : 1) + maxL + maxL / 16) * 8;
   {
     StageScope sc(p, kStSecondOrderBwd, st, 1);
-    k_second_order_bwd<<<dim3(p->n1, B), kFftThreads, sob, st>>>(d, w.gy, gs1, w.gu1);
+    k_second_order_bwd<<<dim3(p->n1, B), 256, sob, st>>>(d, w.gy, gs1, w.gu1);
   }
   {
     StageScope sc(p, kStStage1Bwd, st, 1);
