@@ -1020,26 +1020,24 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
       const Rate2 A = P.rates2[a];
       const int n = n0 + row;
       float2* go = args.gy + (size_t)b * P.y_len + A.off_y;
-      float vi[NAT][16], vr[NAT][16];
 #pragma unroll
-      for (int k = 0; k < NAT; ++k) {
-        tmem_ld16(t_d2 + 128 * k + lane_off + cg * 16, vi[k]);
-        tmem_ld16(t_d2 + 128 * k + lane_off + 64 + cg * 16, vr[k]);
-      }
-      tmem_wait_ld();
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&d2_free);
-      if (n < A.L) {
-#pragma unroll
-        for (int k = 0; k < NAT; ++k)
+      for (int k = 0; k < NAT; ++k) {         // one atom at a time (registers)
+        float vi[16], vr[16];
+        tmem_ld16(t_d2 + 128 * k + lane_off + cg * 16, vi);
+        tmem_ld16(t_d2 + 128 * k + lane_off + 64 + cg * 16, vr);
+        tmem_wait_ld();
+        if (n < A.L) {
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int lp = start + 64 * k + cg * 16 + i;
             if (lp >= A.lam_min && lp < P.n1)
-              go[(size_t)(lp - A.lam_min) * A.L + n] = make_float2(vr[k][i], vi[k][i]);
+              go[(size_t)(lp - A.lam_min) * A.L + n] = make_float2(vr[i], vi[i]);
           }
+        }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d2_free);
     }
   }
   __syncthreads();
