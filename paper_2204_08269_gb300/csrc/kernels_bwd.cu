@@ -6,9 +6,10 @@
 //   k_joint_bwd_simt   : per (alpha, 32-column chunk, signal): for every channel c,
 //                        Z = W_c Y, g|Z| = adjoint of phi_T x phi_F pooling applied to g_S2,
 //                        gZ = g|Z| Z / |Z| (0 at Z = 0), gY += W_c^H gZ
+//   k_gy_spectra       : DFT of every gY row, in place (G rows of one rate per CTA)
 //   k_second_order_bwd : per (lambda', signal): sum over alpha of the adjoint of the
-//                        fold / inverse FFT / psi_alpha product, real part of the inverse of
-//                        the row FFT, plus the adjoint of S1's pooling -> g_U1 row
+//                        fold / psi_alpha product on those spectra, real part of the inverse
+//                        of the row FFT, plus the adjoint of S1's pooling -> g_U1 row
 //   k_stage1_bwd       : per (lambda, signal): recompute z, gz = g_U1 z / |z|, FFT -> gF
 //   k_gxh              : g_x-hat[k] = sum_lambda psi_lambda[k] gF_lambda[k mod L_lambda]
 //   k_gx               : g_x = Re(inverse DFT of g_x-hat) + adjoint of S0's pooling
@@ -158,39 +159,52 @@ k_joint_bwd_simt(DevPlan P, const int2* __restrict__ items, const float2* __rest
   }
 }
 
-// g_U1 row lambda': sum over rates alpha of the adjoint of psi2 (DFT of gY / Lr, times
-// psi-hat_alpha on the row's positive bins), then Re of the inverse row DFT, plus S1's adjoint.
+// Spectra of the gY rows, in place: G rows of one rate per CTA (the Y producer's row items),
+// batched forward FFT (padded radix-16 passes, bit-reversed loads), written back in natural
+// order.
+__global__ void __launch_bounds__(kRowThreads)
+k_gy_spectra(DevPlan P, const int4* __restrict__ items, float2* __restrict__ gy) {
+  extern __shared__ float2 sm[];
+  const int4 it = items[blockIdx.x];
+  const int a = it.x, lam0 = it.y, G = it.z, b = blockIdx.y;
+  const Rate2 A = P.rates2[a];
+  const int L = A.L, logL = A.logL;
+  float2* g = gy + (size_t)b * P.y_len + A.off_y + (size_t)(lam0 - A.lam_min) * L;
+  for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x)
+    sm[fft_pad(((idx >> logL) << logL) + bitrev(idx & (L - 1), logL))] = g[idx];
+  __syncthreads();
+  fft_dit_rows_r16<-1>(sm, logL, G, twl_for(P, logL));
+  for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) g[idx] = sm[fft_pad(idx)];
+}
+
+// g_U1 row lambda': sum over rates alpha of the adjoint of psi2 (the gY row's spectrum / Lr
+// times psi-hat_alpha on the row's positive bins), then Re of the inverse row DFT, plus S1's
+// adjoint.
 __global__ void __launch_bounds__(kFftThreads)
-k_second_order_bwd(DevPlan P, const float2* __restrict__ gy, const float* __restrict__ gs1,
+k_second_order_bwd(DevPlan P, const float2* __restrict__ gys, const float* __restrict__ gs1,
                    float* __restrict__ gu1) {
   extern __shared__ float2 sm[];
   const int lam = blockIdx.x, b = blockIdx.y;
   const Row1 R = P.rows1[lam];
   const int half = R.L >> 1;
-  float2* guh = sm;                // [L/2]
-  float2* tmp = sm + (half > 0 ? half : 1);  // [max(L_alpha, L)]
-  for (int k = threadIdx.x; k < half; k += blockDim.x) guh[k] = make_float2(0.f, 0.f);
+  float2* tmp = sm;                // [L] padded
   const float invLr = 1.f / (float)R.L;
-  for (int a = 0; a < P.n2; ++a) {
-    const Rate2 A = P.rates2[a];
-    if (A.s == 0 || lam < A.lam_min) continue;
-    __syncthreads();
-    const float2* g = gy + (size_t)b * P.y_len + A.off_y + (size_t)(lam - A.lam_min) * A.L;
-    for (int m = threadIdx.x; m < A.L; m += blockDim.x) tmp[fft_pad(bitrev(m, A.logL))] = g[m];
-    __syncthreads();
-    fft_dit_rows_r16<-1>(tmp, A.logL, 1, twl_for(P, A.logL));
-    const float* psi = P.psi2 + (size_t)a * P.K2max;
-    const int kend = min(half, A.k2e);
-    for (int k = 1 + threadIdx.x; k < kend; k += blockDim.x) {
-      const float2 v = tmp[fft_pad(k & (A.L - 1))];
-      const float f = __ldg(&psi[k]) * invLr;
-      guh[k].x += v.x * f;
-      guh[k].y += v.y * f;
+  // guh[k] for k < half, built in registers per bin and stored bit-reversed
+  for (int k = threadIdx.x; k < R.L; k += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    if (k >= 1 && k < half) {
+      for (int a = 0; a < P.n2; ++a) {
+        const Rate2 A = P.rates2[a];
+        if (A.s == 0 || lam < A.lam_min || k >= A.k2e) continue;
+        const float2 v = gys[(size_t)b * P.y_len + A.off_y + (size_t)(lam - A.lam_min) * A.L +
+                             (k & (A.L - 1))];
+        const float f = __ldg(&P.psi2[(size_t)a * P.K2max + k]) * invLr;
+        acc.x += v.x * f;
+        acc.y += v.y * f;
+      }
     }
+    tmp[fft_pad(bitrev(k, R.logL))] = acc;
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < R.L; k += blockDim.x)
-    tmp[fft_pad(bitrev(k, R.logL))] = (k < half) ? guh[k] : make_float2(0.f, 0.f);
   __syncthreads();
   fft_dit_rows_r16<+1>(tmp, R.logL, 1, twl_for(P, R.logL));
   const float* g1 = gs1 ? gs1 + ((size_t)b * P.n1 + lam) * P.n_t : nullptr;
@@ -308,7 +322,8 @@ jtfs_status set_attrs() {
   }
   // the row producer holds at most 2^14 complex samples (padded one per 16) next to its
   // static row tables
-  for (const void* f : {(const void*)k_second_order_rows<0>, (const void*)k_second_order_rows<1>}) {
+  for (const void* f : {(const void*)k_second_order_rows<0>, (const void*)k_second_order_rows<1>,
+                        (const void*)k_gy_spectra}) {
     jtfs_status st = cuda_check(
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024), "attr");
     if (st != JTFS_OK) return st;
@@ -365,11 +380,13 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
   } else if (p->y_len > 0) {
     cudaMemsetAsync(w.gy, 0, (size_t)B * p->y_len * sizeof(float2), st);
   }
-  const size_t maxL = (size_t)(p->L2max > p->L1max ? p->L2max : p->L1max);
-  const size_t sob = ((size_t)(p->L1max / 2 > 0 ? p->L1max / 2 : 1) + maxL + maxL / 16) * 8;
   {
-    StageScope sc(p, kStSecondOrderBwd, st, 1);
-    k_second_order_bwd<<<dim3(p->n1, B), 256, sob, st>>>(d, w.gy, gs1, w.gu1);
+    StageScope sc(p, kStSecondOrderBwd, st, 2);
+    if (!p->rowitems.empty())
+      k_gy_spectra<<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
+                     (size_t)p->rows_cap * 17 / 2, st>>>(
+          d, reinterpret_cast<const int4*>(p->d_rowitems), w.gy);
+    k_second_order_bwd<<<dim3(p->n1, B), 256, (size_t)p->L1max * 17 / 2, st>>>(d, w.gy, gs1, w.gu1);
   }
   {
     StageScope sc(p, kStStage1Bwd, st, 1);
