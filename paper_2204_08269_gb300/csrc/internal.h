@@ -111,6 +111,10 @@ struct jtfs_plan {
   bool use_tc;
   int n1_pad;                  // lambda' columns of the W planes (multiple of 32)
   void* d_wplanes[6];          // Wr_hi, Wi_hi, Wr_lo, Wi_lo, -Wi_hi, -Wi_lo: [C * n1][n1_pad] bf16
+  bool tc_pair = false;        // forward in the spin-pair form (16 frames, BF16 planes)
+  int n_pr = 0;                // pair rows (n_fr + 1) * n1
+  void* d_wpair[4] = {nullptr, nullptr, nullptr, nullptr};   // Wr_hi, Wi_hi, Wr_lo, Wi_lo of
+                               // the spin-up and phi_F rows: [n_pr][n1_pad] bf16
   void* d_wtf;                 // pooling weights hi / lo: [n2 * NT][tc_wt_cols] bf16
   int tc_wt_cols;
   std::vector<int> tc_items;   // (alpha, m0, n_tiles, 0) per signal; resident-W items first

@@ -813,6 +813,408 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   }
 }
 
+// ------------------------------------------------------------------ spin-pair form
+// The spin-down log-frequency filters are the complex conjugates of the spin-up ones
+// (psi_{beta,-1}-hat(omega) = psi_{beta,+1}-hat(-omega) with a real spectrum that vanishes at
+// DC and Nyquist), so for a pair of rows (up c, down c + n_fr) with W_up = Wr + i Wi:
+//   Z_up = (Wr Yr - Wi Yi) + i (Wr Yi + Wi Yr),   Z_down = (Wr Yr + Wi Yi) + i (Wr Yi - Wi Yr).
+// The four real products come from two MMAs per K step over a 64-sample tile with
+// B = [Yr | Yi] (N = 128): [P1 | P3] = Wr [Yr | Yi], [P4 | P2] = Wi [Yr | Yi]; the epilogue
+// forms both channels.  That halves the contraction's MMAs against the channel-row form.
+// Rows are pair rows r = p n1 + lambda: p < n_fr the spin pairs, p = n_fr the phi_F branch
+// (real W, only its "up" output is written).  Sixteen epilogue warps: lane quarter = warp & 3,
+// column group cg = ew >> 2 takes channel cg >> 1 (0 up, 1 down) over samples
+// [32 (cg & 1), +32) of the tile, pooled with mma.sync as in the 16-frame form.
+template <bool RES, int PS>
+__global__ void __launch_bounds__(kThreads, 1)
+k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int NT = 16, BN = 64;
+  const int planes = args.passes == 3 ? 2 : 1;
+  constexpr int pplanes = PS;
+  const int S = args.stages, WS = args.wstages;
+  constexpr uint32_t kAPlane = kBM * kBK * 2;            // 8 KB: 128 rows x 32 lambda', SW64
+  constexpr uint32_t kYAtom = 4096;                      // 32 lambda' x 64 samples, SW128
+  constexpr uint32_t kWHalf = NT * 64 * 2;               // 2 KB: 16 frames x 64 samples
+  constexpr uint32_t kStg = 32 * 16 * 2;                 // 1 KB: a warp's 32 x 16 |Z| block
+  const int max_kb = args.res_kb;
+  const uint32_t y_bytes = planes * 2 * kYAtom;          // per plane [Yr atom | Yi atom]
+  const uint32_t stage_bytes = RES ? y_bytes : planes * 2 * kAPlane + y_bytes;
+  uint8_t* sA = sm;
+  uint8_t* sStage = sm + (RES ? planes * 2 * max_kb * kAPlane : 0);
+  uint8_t* sWt = sStage + S * stage_bytes;               // WS x pplanes (hi, lo adjacent)
+  uint8_t* sStg = sWt + WS * pplanes * kWHalf;           // 16 warps x 2 channels x pplanes x 1 KB
+                                                         // (at an item's end: 32 x 16 partials)
+  __shared__ uint64_t full_bar[8], empty_bar[8], wfull[kMaxWS], wempty[kMaxWS], tfull[2],
+      tempty[2], red_full[4], red_free[4], a_full, a_free, mma_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int s = 0; s < WS; ++s) {
+      mbar_init(&wfull[s], 1);
+      mbar_init(&wempty[s], kEpiWarps);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&tfull[a], 1);
+      mbar_init(&tempty[a], kEpiWarps);
+    }
+    for (int q = 0; q < 4; ++q) {
+      mbar_init(&red_full[q], 4);
+      mbar_init(&red_free[q], 1);
+    }
+    mbar_init(&a_full, 1);
+    mbar_init(&a_free, 1);
+    mbar_init(&mma_done, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+
+  auto fail = [&](int code) {
+    if (!abort_flag) {
+      abort_flag = 1;
+      atomicCAS(args.err, 0, code);
+    }
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0, ws = 0;
+      uint32_t phase = 0, wph = 0, aph = 0;
+      uint32_t armed = 0, armed_par = 0, armed_w = 0, armed_w_par = 0;
+      int armed_a = -1;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        const int a = item.x, b = it / args.n_base, m0 = item.y, ntiles = item.z;
+        const Rate2 A = P.rates2[a];
+        const int lm8 = A.lam_min & ~7;
+        const int nkb = (((P.n1 - lm8 + 15) >> 4) + 1) >> 1;
+        if (RES) {
+          if (!mbar_wait(&a_free, aph ^ 1, kWaitNs)) { fail(10); ok = false; break; }
+          mbar_arrive_expect_tx(&a_full, planes * 2 * nkb * kAPlane);
+          armed_a = (int)aph;
+          for (int pl = 0; pl < planes; ++pl)
+            for (int part = 0; part < 2; ++part)
+              for (int kb = 0; kb < nkb; ++kb)
+                tma_load_2d(sA + ((pl * 2 + part) * max_kb + kb) * kAPlane,
+                            &maps.w[pl * 2 + part], lm8 + kb * kBK, m0, &a_full);
+          aph ^= 1;
+        }
+        for (int j = 0; j < ntiles && ok; ++j) {
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!mbar_wait(&empty_bar[stage], phase ^ 1, kWaitNs)) { fail(11); ok = false; break; }
+            uint8_t* st = sStage + stage * stage_bytes;
+            mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+            uint8_t* sb = RES ? st : st + planes * 2 * kAPlane;
+            for (int pl = 0; pl < planes; ++pl) {
+              for (int part = 0; part < 2; ++part) {
+                if (!RES)
+                  tma_load_2d(st + (pl * 2 + part) * kAPlane, &maps.w[pl * 2 + part],
+                              lm8 + kb * kBK, m0, &full_bar[stage]);
+                tma_load_3d(sb + (pl * 2 + part) * kYAtom, &maps.y[pl][a], j * BN,
+                            lm8 + kb * kBK - A.lam_min, 2 * b + part, &full_bar[stage]);
+              }
+            }
+            if (++stage == S) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
+          mbar_arrive_expect_tx(&wfull[ws], pplanes * kWHalf);
+          armed_w |= 1u << ws;
+          armed_w_par = (armed_w_par & ~(1u << ws)) | (wph << ws);
+          for (int pl = 0; pl < pplanes; ++pl)
+            tma_load_2d(sWt + (ws * pplanes + pl) * kWHalf, &maps.wt[pl], j * BN, a * NT,
+                        &wfull[ws]);
+          if (++ws == WS) { ws = 0; wph ^= 1; }
+        }
+      }
+      for (int s2 = 0; s2 < S; ++s2)
+        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, kWaitNs);
+      for (int s2 = 0; s2 < WS; ++s2)
+        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, kWaitNs);
+      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, kWaitNs);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t id = instr_desc(kBM, 128, 1, 1, 0, 1, 0);
+      const int npair = args.passes == 3 ? 3 : 1;
+      int stage = 0, acc = 0;
+      uint32_t phase = 0, acc_ph = 0, aph = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        const Rate2 A = P.rates2[item.x];
+        const int lm8 = A.lam_min & ~7;
+        const int nks = (P.n1 - lm8 + 15) / 16;
+        const int nkb = (nks + 1) / 2;
+        if (RES) {
+          if (!mbar_wait(&a_full, aph, kWaitNs)) { fail(9); ok = false; break; }
+          aph ^= 1;
+        }
+        for (int j = 0; j < item.z && ok; ++j) {
+          if (!mbar_wait(&tempty[acc], acc_ph ^ 1, kWaitNs)) { fail(12); ok = false; break; }
+          tc_fence_after();
+          const uint32_t t_a = tbase + acc * 256, t_b = t_a + 128;
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!mbar_wait(&full_bar[stage], phase, kWaitNs)) { fail(13); ok = false; break; }
+            tc_fence_after();
+            const uint32_t st = smem_u32(sStage + stage * stage_bytes);
+            const uint32_t sb = RES ? st : st + planes * 2 * kAPlane;
+            const uint32_t sa = RES ? smem_u32(sA) + kb * kAPlane : st;
+            const uint32_t a_stride = RES ? max_kb * kAPlane : kAPlane;
+            const int kss = min(2, nks - 2 * kb);
+            for (int ks = 0; ks < kss; ++ks) {
+              for (int q = 0; q < npair; ++q) {
+                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                // A: K-major rows of 32 lambda' (64-byte swizzle); B: [Yr | Yi] MN-major
+                // atoms of 64 samples, K step = 16 rows of 128 bytes
+                const uint32_t ar_a = sa + pa * 2 * a_stride + ks * 32;
+                const uint64_t ar = smem_desc(ar_a, 16, 512, kSw64);
+                const uint64_t ai = smem_desc(ar_a + a_stride, 16, 512, kSw64);
+                const uint64_t bd = smem_desc(sb + pb * 2 * kYAtom + ks * 16 * 128, kYAtom, 1024, kSw128);
+                const uint32_t f = (kb | ks | q) ? 1u : 0u;
+                mma_f16(t_a, ar, bd, id, f);    // [P1 | P3] = Wr [Yr | Yi]
+                mma_f16(t_b, ai, bd, id, f);    // [P4 | P2] = Wi [Yr | Yi]
+              }
+            }
+            mma_commit(&empty_bar[stage]);
+            if (++stage == S) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit(&tfull[acc]);
+          if (++acc == 2) { acc = 0; acc_ph ^= 1; }
+        }
+        if (!ok) break;
+        if (RES) mma_commit(&a_free);
+      }
+      mma_commit(&mma_done);
+      mbar_wait(&mma_done, 0, kWaitNs);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue + pooling
+    const int ew = warp - kEpiWarp0;          // 0..15
+    const int quarter = warp & 3;
+    const int cg = ew >> 2;                   // samples [16 cg, 16 cg + 16) of the tile
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const int g = lane >> 2, t4 = lane & 3;
+    uint8_t* stg = sStg + ew * 2 * pplanes * kStg;         // [channel][plane] blocks
+    const uint32_t stg_u = smem_u32(stg);
+    uint8_t* my_row = stg + lane * 32;
+    const int my_sw = (lane >> 2) & 1;
+    uint32_t a_addr[2];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int r = 16 * mt + (lane & 15);
+      a_addr[mt] = stg_u + r * 32 + (((lane >> 4) ^ ((r >> 2) & 1)) << 4);
+    }
+    const int bt = 8 * (lane >> 4) + (lane & 7);
+    const int bk = (lane >> 3) & 1;
+    const uint32_t b_off = bt * 128 + ((((cg * 16) >> 3) + bk) ^ (bt & 7)) * 16;
+    int acc = 0, ws = 0;
+    // every wait on red_free follows a completed round of column group 0 (no free first
+    // phase): the first wait is for parity 0
+    uint32_t acc_ph = 0, wph = 0, rf_ph = 0, rfree_ph = 1;
+    bool red_pending = false;
+    for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+      const int4 item = args.items[it % args.n_base];
+      const int a = item.x, b = it / args.n_base, m0 = item.y;
+      bool ok = !abort_flag;
+      float c[2][2][2][4];                     // [channel up / down][mt][nt][4]
+#pragma unroll
+      for (int d = 0; d < 2; ++d)
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int k2 = 0; k2 < 2; ++k2)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) c[d][i][k2][e] = 0.f;
+      if (cg != 0 && red_pending) {
+        // column group 0 has read this warp's partials of the previous item
+        if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, kWaitNs)) { fail(21); break; }
+        rfree_ph ^= 1;
+        red_pending = false;
+      }
+      for (int j = 0; j < item.z && ok; ++j) {
+        if (!mbar_wait(&tfull[acc], acc_ph, kWaitNs)) { fail(14); ok = false; break; }
+        tc_fence_after();
+        if (!mbar_wait(&wfull[ws], wph, kWaitNs)) { fail(19); ok = false; break; }
+        const uint32_t t_col = tbase + acc * 256 + lane_off + cg * 16;
+        const uint32_t w_u = smem_u32(sWt + ws * pplanes * kWHalf);
+        __syncwarp();   // the previous tile's fragment loads are done
+#pragma unroll
+        for (int h8 = 0; h8 < 2; ++h8) {
+          uint32_t p1[8], p3[8], p4[8], p2[8];
+          tmem_ld8u(t_col + h8 * 8, p1);
+          tmem_ld8u(t_col + h8 * 8 + 64, p3);
+          tmem_ld8u(t_col + h8 * 8 + 128, p4);
+          tmem_ld8u(t_col + h8 * 8 + 192, p2);
+          tmem_wait_ld();
+          if (h8 == 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+          }
+          uint32_t hv[2][4], lv[2][4];         // [up / down][8 samples as bf16x2]
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            float mu[2], md[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const int k2 = 2 * i + e;
+              const float x1 = __uint_as_float(p1[k2]), x2 = __uint_as_float(p2[k2]);
+              const float x3 = __uint_as_float(p3[k2]), x4 = __uint_as_float(p4[k2]);
+              const float ru = x1 - x2, iu = x3 + x4, rd = x1 + x2, id = x3 - x4;
+              mu[e] = sqrt_approx(fmaf(ru, ru, iu * iu));
+              md[e] = sqrt_approx(fmaf(rd, rd, id * id));
+            }
+            __nv_bfloat162 hu = __floats2bfloat162_rn(mu[0], mu[1]);
+            __nv_bfloat162 hd = __floats2bfloat162_rn(md[0], md[1]);
+            hv[0][i] = *reinterpret_cast<uint32_t*>(&hu);
+            hv[1][i] = *reinterpret_cast<uint32_t*>(&hd);
+            if (PS == 2) {
+              const float2 fu = __bfloat1622float2(hu), fd = __bfloat1622float2(hd);
+              __nv_bfloat162 lu = __floats2bfloat162_rn(mu[0] - fu.x, mu[1] - fu.y);
+              __nv_bfloat162 ld = __floats2bfloat162_rn(md[0] - fd.x, md[1] - fd.y);
+              lv[0][i] = *reinterpret_cast<uint32_t*>(&lu);
+              lv[1][i] = *reinterpret_cast<uint32_t*>(&ld);
+            }
+          }
+          // samples [8 h8, 8 h8 + 8) of this warp's 16 are 16-byte chunk h8 of its row
+          const int pos = (h8 ^ my_sw) * 16;
+#pragma unroll
+          for (int d = 0; d < 2; ++d) {
+            *reinterpret_cast<uint4*>(my_row + d * pplanes * kStg + pos) =
+                make_uint4(hv[d][0], hv[d][1], hv[d][2], hv[d][3]);
+            if (PS == 2)
+              *reinterpret_cast<uint4*>(my_row + (d * pplanes + 1) * kStg + pos) =
+                  make_uint4(lv[d][0], lv[d][1], lv[d][2], lv[d][3]);
+          }
+        }
+        __syncwarp();
+        // B fragments: w[t][n] for this warp's 16 samples of the 64-sample row
+        uint32_t bh[4], bl[4];
+        ldsm_x4(w_u + b_off, bh);
+        if (PS == 2) ldsm_x4(w_u + kWHalf + b_off, bl);
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          const uint32_t blk = d * pplanes * kStg;
+          uint32_t ah[2][4];
+          ldsm_x4(a_addr[0] + blk, ah[0]);
+          ldsm_x4(a_addr[1] + blk, ah[1]);
+#pragma unroll
+          for (int mt = 0; mt < 2; ++mt) {
+            hmma16816(c[d][mt][0], ah[mt], bh[0], bh[1]);
+            hmma16816(c[d][mt][1], ah[mt], bh[2], bh[3]);
+          }
+          if (PS == 2) {
+            uint32_t al[2][4];
+            ldsm_x4(a_addr[0] + blk + kStg, al[0]);
+            ldsm_x4(a_addr[1] + blk + kStg, al[1]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+              hmma16816(c[d][mt][0], ah[mt], bl[0], bl[1]);   // hi . lo
+              hmma16816(c[d][mt][1], ah[mt], bl[2], bl[3]);
+              hmma16816(c[d][mt][0], al[mt], bh[0], bh[1]);   // lo . hi
+              hmma16816(c[d][mt][1], al[mt], bh[2], bh[3]);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&wempty[ws]);
+        if (++ws == WS) { ws = 0; wph ^= 1; }
+        if (++acc == 2) { acc = 0; acc_ph ^= 1; }
+      }
+      if (!ok) break;
+      // per channel: each warp leaves its 32 x 16 partials in its own staging block and column
+      // group 0 sums the four blocks of its lane quarter in a fixed order
+      const int r = m0 + quarter * 32 + lane;
+      const int p = r / P.n1, lam = r - p * P.n1;
+      float* base = args.P + ((size_t)b * args.n2 + a) * (size_t)P.C * P.n1 * args.nt;
+      bool red_ok = true;
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        if (cg != 0 && d == 1) {
+          if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, kWaitNs)) { fail(21); red_ok = false; break; }
+          rfree_ph ^= 1;
+        }
+        __syncwarp();   // the last tile's fragment loads are done
+        float* red = (float*)stg;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) {
+            const int rr = 16 * mt + g, t = 8 * nt + 2 * t4;
+            *reinterpret_cast<float2*>(red + rr * NT + t) = make_float2(c[d][mt][nt][0], c[d][mt][nt][1]);
+            *reinterpret_cast<float2*>(red + (rr + 8) * NT + t) = make_float2(c[d][mt][nt][2], c[d][mt][nt][3]);
+          }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&red_full[quarter]);
+        if (cg == 0) {
+          if (!mbar_wait(&red_full[quarter], rf_ph, kWaitNs)) { fail(20); red_ok = false; break; }
+          rf_ph ^= 1;
+          float sv[NT];
+#pragma unroll
+          for (int t = 0; t < NT; ++t) sv[t] = 0.f;
+#pragma unroll
+          for (int gq = 0; gq < 4; ++gq) {
+            // the warp of column group gq and this lane quarter: ew = 4 gq + ((quarter + 2) & 3)
+            const float* src =
+                (const float*)(sStg + (gq * 4 + ((quarter + 2) & 3)) * 2 * pplanes * kStg) + lane * NT;
+#pragma unroll
+            for (int t = 0; t < NT; t += 4) {
+              const float4 v = *reinterpret_cast<const float4*>(src + t);
+              sv[t] += v.x; sv[t + 1] += v.y; sv[t + 2] += v.z; sv[t + 3] += v.w;
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&red_free[quarter]);
+          // pair row r: channel p (up) or p + n_fr (down); the phi_F rows (p = n_fr) have no
+          // down channel
+          const bool write = r < args.n_rows && (d == 0 || p < P.n_fr);
+          if (write) {
+            const int row = (d == 0 ? (p < P.n_fr ? p : 2 * P.n_fr) : p + P.n_fr) * P.n1 + lam;
+            float* out = base + (size_t)row * args.nt;
+            if (args.nt == NT) {
+#pragma unroll
+              for (int t = 0; t < NT; t += 4)
+                *reinterpret_cast<float4*>(out + t) = make_float4(sv[t], sv[t + 1], sv[t + 2], sv[t + 3]);
+            } else {
+#pragma unroll
+              for (int t = 0; t < NT; ++t)
+                if (t < args.nt) out[t] = sv[t];
+            }
+          }
+        }
+      }
+      red_pending = true;
+      if (!red_ok) break;
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
 // phi_F pooling along lambda of the time-pooled rows: S2[b, a, c, lo, t].
 __global__ void k_pool_lambda(DevPlan Pd, const float* __restrict__ P, float* __restrict__ s2) {
   const int c = blockIdx.x, a = blockIdx.y, b = blockIdx.z;
@@ -868,6 +1270,26 @@ __global__ void k_build_wplanes32(DevPlan Pd, int n1_pad, float* wr, float* wi) 
     if (lp < Pd.n1) v = Pd.h[(size_t)c * Pd.N_fr + ((lam - lp) & (Pd.N_fr - 1))];
     wr[i] = tf32_rna(v.x);
     wi[i] = tf32_rna(v.y);
+  }
+}
+
+// W planes of the spin-pair forward: row r = p n1 + lambda takes channel p (spin up) for
+// p < n_fr and the phi_F channel 2 n_fr for p = n_fr; BF16 hi / lo of Re and Im.
+__global__ void k_build_wpair(DevPlan Pd, int n1_pad, __nv_bfloat16* wr_hi, __nv_bfloat16* wi_hi,
+                              __nv_bfloat16* wr_lo, __nv_bfloat16* wi_lo) {
+  const long long total = (long long)(Pd.n_fr + 1) * Pd.n1 * n1_pad;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / n1_pad), lp = (int)(i % n1_pad);
+    const int pr = r / Pd.n1, lam = r % Pd.n1;
+    const int c = pr < Pd.n_fr ? pr : 2 * Pd.n_fr;
+    float2 v = make_float2(0.f, 0.f);
+    if (lp < Pd.n1) v = Pd.h[(size_t)c * Pd.N_fr + ((lam - lp) & (Pd.N_fr - 1))];
+    const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
+    wr_hi[i] = hr;
+    wi_hi[i] = hi;
+    wr_lo[i] = __float2bfloat16_rn(v.x - __bfloat162float(hr));
+    wi_lo[i] = __float2bfloat16_rn(v.y - __bfloat162float(hi));
   }
 }
 
@@ -961,12 +1383,15 @@ size_t tc_smem_for(const jtfs_plan* p, bool res) {
 // 16-frame form: resident W tile, operand stages, the weight ring, sixteen 1 KB |Z| staging
 // blocks per pooling plane and the 32 KB column-group reduction buffer.  apl: bytes of one
 // 128 x 32 W block (8 KB BF16, 16 KB FP32 for TF32); cpl / ppl: contraction / pooling planes;
-// nya: 4 KB Y atoms per part of a 128-sample tile (2 BF16, 4 FP32).
+// nya: 4 KB Y atoms per part of a column tile (2 BF16, 4 FP32, 1 for the 64-sample tiles of
+// the spin-pair form); nh: 64-sample halves of a pooling-weight tile (1 in the spin-pair form,
+// whose warps stage both channels, 3 - nh staging blocks per pooling plane, and reduce their
+// partials through those blocks instead of the 32 KB buffer).
 struct Tc16Shape {
-  int apl, cpl, ppl, nya, WS;
+  int apl, cpl, ppl, nya, nh, WS;
   size_t fixed(bool res, int res_kb) const {
-    return 1024 + (res ? (size_t)cpl * 2 * res_kb * apl : 0) + (size_t)WS * 2 * ppl * 16 * 64 * 2 +
-           (size_t)kEpiWarps * ppl * 1024 + 4 * 128 * 16 * 4;
+    return 1024 + (res ? (size_t)cpl * 2 * res_kb * apl : 0) + (size_t)WS * nh * ppl * 16 * 64 * 2 +
+           (size_t)kEpiWarps * (3 - nh) * ppl * 1024 + (nh == 2 ? 4 * 128 * 16 * 4 : 0);
   }
   size_t stage(bool res) const {
     return (res ? 0 : (size_t)cpl * 2 * apl) + (size_t)cpl * 2 * nya * 4096;
@@ -979,7 +1404,8 @@ Tc16Shape tc16_shape(const jtfs_plan* p) {
   s.apl = tf ? kBM * kBK * 4 : kBM * kBK * 2;
   s.cpl = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
   s.ppl = p->split ? 2 : 1;
-  s.nya = tf ? 4 : 2;
+  s.nya = p->tc_pair ? 1 : (tf ? 4 : 2);
+  s.nh = p->tc_pair ? 1 : 2;
   s.WS = kMaxWS;
   return s;
 }
@@ -1006,14 +1432,19 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   for (int a = 0; a < p->n2; ++a)
     if (p->rates2[a].s) Lmax = std::max(Lmax, (p->rates2[a].L + BN - 1) / BN * BN);
   p->tc_wt_cols = Lmax;
-  // items: (alpha, m0, n_tiles)
+  // items: (alpha, m0, n_tiles); the 16-frame BF16-plane forward runs in the spin-pair form
+  // over (n_fr + 1) n1 pair rows and 64-sample tiles
+  const bool tf = p->cfg.precision == JTFS_PREC_TF32;
+  p->tc_pair = NT == 16 && !tf;
+  p->n_pr = (p->n_fr + 1) * p->n1;
+  const int tile_n = p->tc_pair ? 64 : BN;
   struct It { int a, m0, nt; long long cost; };
   std::vector<It> its;
-  const int rows = p->C * p->n1;
+  const int rows = p->tc_pair ? p->n_pr : p->C * p->n1;
   for (int a = 0; a < p->n2; ++a) {
     const Rate2& A = p->rates2[a];
     if (A.s == 0) continue;
-    const int ntiles = (A.L + BN - 1) / BN;
+    const int ntiles = (A.L + tile_n - 1) / tile_n;
     const int kblocks = tc_item_kb(p->n1, A.lam_min);
     for (int m0 = 0; m0 < rows; m0 += kBM) its.push_back({a, m0, ntiles, (long long)ntiles * (kblocks + 2)});
   }
@@ -1035,7 +1466,9 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   auto place = [&](size_t bytes) { size_t at = off; off += (bytes + 1023) & ~(size_t)1023; return at; };
   size_t o_w[6];
   for (int i = 0; i < 6; ++i) o_w[i] = place(wplane * 2);
-  const bool tf = p->cfg.precision == JTFS_PREC_TF32;
+  size_t o_wp[4] = {0, 0, 0, 0};
+  if (p->tc_pair)
+    for (int i = 0; i < 4; ++i) o_wp[i] = place((size_t)p->n_pr * p->n1_pad * 2);
   size_t o_w32[2] = {0, 0};
   if (tf)
     for (int i = 0; i < 2; ++i) o_w32[i] = place(wplane * 4);
@@ -1047,6 +1480,7 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   if ((st = cuda_check(cudaMalloc(&p->d_tc_mem, off), "tc tables")) != JTFS_OK) return st;
   char* base = (char*)p->d_tc_mem;
   for (int i = 0; i < 6; ++i) p->d_wplanes[i] = base + o_w[i];
+  for (int i = 0; i < 4; ++i) p->d_wpair[i] = p->tc_pair ? base + o_wp[i] : nullptr;
   if (tf)
     for (int i = 0; i < 2; ++i) p->d_wplanes32[i] = base + o_w32[i];
   p->d_wtf = base + o_wt;
@@ -1060,6 +1494,10 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
                                  (__nv_bfloat16*)p->d_wplanes[1], (__nv_bfloat16*)p->d_wplanes[2],
                                  (__nv_bfloat16*)p->d_wplanes[3], (__nv_bfloat16*)p->d_wplanes[4],
                                  (__nv_bfloat16*)p->d_wplanes[5]);
+  if (p->tc_pair)
+    k_build_wpair<<<1024, 256>>>(p->dp, p->n1_pad, (__nv_bfloat16*)p->d_wpair[0],
+                                 (__nv_bfloat16*)p->d_wpair[1], (__nv_bfloat16*)p->d_wpair[2],
+                                 (__nv_bfloat16*)p->d_wpair[3]);
   k_build_wt<<<1024, 256>>>(p->dp, NT, Lmax, (__nv_bfloat16*)p->d_wtf,
                             (__nv_bfloat16*)p->d_wtf + wt_elems);
   if (tf)
@@ -1074,7 +1512,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   TcMaps maps;
   std::string err;
   const int passes = p->cfg.precision == JTFS_PREC_FP32 ? 3 : 1;
-  const int rows = p->C * p->n1;
+  const int rows = p->tc_pair ? p->n_pr : p->C * p->n1;
   const int NT = tc_nt(p->n_t);
   const int BN = tc_bn(p);
   // TF32: FP32 W planes (rows of 32 lambda' = 128 bytes) and FP32 Y planes (atoms of 32
@@ -1086,7 +1524,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)rows};
     cuuint64_t str[1] = {(cuuint64_t)p->n1_pad * esz};
     cuuint32_t box[2] = {kBK, kBM};
-    const void* src = tf ? p->d_wplanes32[i & 1] : p->d_wplanes[i];
+    const void* src = tf ? p->d_wplanes32[i & 1] : (p->tc_pair ? p->d_wpair[i] : p->d_wplanes[i]);
     if (!make_tmap(&maps.w[i], dt, 2, src, dims, str, box, tf ? 128 : 64, &err)) {
       set_error(err);
       return JTFS_ERR_CUDA;
@@ -1168,6 +1606,14 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       return rc;                                                                                \
     k_joint_fwd_tc16<RESV, TFV><<<grid, kThreads, smem, st>>>(maps, args, d);                  \
   } while (0)
+#define JTFS_LAUNCH_PAIR(RESV, PSV)                                                             \
+  do {                                                                                          \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_pair<RESV, PSV>,                      \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                              (int)smem), "attr pair")) != JTFS_OK)             \
+      return rc;                                                                                \
+    k_joint_fwd_pair<RESV, PSV><<<grid, kThreads, smem, st>>>(maps, args, d);                   \
+  } while (0)
   for (int pass = 0; pass < 2; ++pass) {
     const bool res = pass == 0;
     const int first = res ? 0 : n_res, count = res ? n_res : n_all - n_res;
@@ -1178,7 +1624,13 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     args.stages = f16 ? tc16_stages_for(p, res) : tc_stages_for(p, res);
     const size_t smem = f16 ? tc16_smem_for(p, res) : tc_smem_for(p, res);
     const int grid = std::min(args.n_items, n_sm);
-    if (f16 && tf) {
+    if (p->tc_pair) {
+      if (args.pool_split) {
+        if (res) JTFS_LAUNCH_PAIR(true, 2); else JTFS_LAUNCH_PAIR(false, 2);
+      } else {
+        if (res) JTFS_LAUNCH_PAIR(true, 1); else JTFS_LAUNCH_PAIR(false, 1);
+      }
+    } else if (f16 && tf) {
       if (res) JTFS_LAUNCH_TC16(true, true); else JTFS_LAUNCH_TC16(false, true);
     } else if (f16) {
       if (res) JTFS_LAUNCH_TC16(true, false); else JTFS_LAUNCH_TC16(false, false);
@@ -1191,6 +1643,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   }
 #undef JTFS_LAUNCH_TC
 #undef JTFS_LAUNCH_TC16
+#undef JTFS_LAUNCH_PAIR
   k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
   return cuda_check(cudaGetLastError(), "k_pool_lambda");
 }
