@@ -61,7 +61,8 @@ struct TcArgs {
   int wstages;             // pooling-weight ring depth (2..kMaxWS)
   int res_kb;              // k-blocks of the resident W tile (RES form)
   int pool_split;          // 1: the 16-frame pooling uses the BF16 hi / lo split
-  int n_rows;              // C * n1
+  int n_rows;              // C * n1 (pair rows n_pr in the spin-pair form)
+  int pr_phi0;             // spin-pair form: first phi_F pair row
   int nt;                  // frames
   float* P;                // [B][n2][C*n1][nt]
   int n2;
@@ -821,8 +822,9 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
 // The four real products come from two MMAs per K step over a 64-sample tile with
 // B = [Yr | Yi] (N = 128): [P1 | P3] = Wr [Yr | Yi], [P4 | P2] = Wi [Yr | Yi]; the epilogue
 // forms both channels.  That halves the contraction's MMAs against the channel-row form.
-// Rows are pair rows r = p n1 + lambda: p < n_fr the spin pairs, p = n_fr the phi_F branch
-// (real W, only its "up" output is written).  Sixteen epilogue warps: lane quarter = warp & 3,
+// Rows are pair rows r = p n1 + lambda for the spin pairs p < n_fr, then zero rows up to the
+// next multiple of 32, then the n1 rows of the phi_F branch (real W, only its "up" output is
+// written).  Sixteen epilogue warps: lane quarter = warp & 3,
 // column group cg = ew >> 2 takes channel cg >> 1 (0 up, 1 down) over samples
 // [32 (cg & 1), +32) of the tile, pooled with mma.sync as in the 16-frame form.
 template <bool RES, int PS>
@@ -1146,7 +1148,9 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       // per channel: each warp leaves its 32 x 16 partials in its own staging block and column
       // group 0 sums the four blocks of its lane quarter in a fixed order
       const int r = m0 + quarter * 32 + lane;
-      const int p = r / P.n1, lam = r - p * P.n1;
+      const bool spin = r < P.n_fr * P.n1;
+      const int p = spin ? r / P.n1 : P.n_fr;
+      const int lam = spin ? r - p * P.n1 : r - args.pr_phi0;
       float* base = args.P + ((size_t)b * args.n2 + a) * (size_t)P.C * P.n1 * args.nt;
       bool red_ok = true;
 #pragma unroll
@@ -1187,8 +1191,8 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           __syncwarp();
           if (lane == 0) mbar_arrive(&red_free[quarter]);
           // pair row r: channel p (up) or p + n_fr (down); the phi_F rows (p = n_fr) have no
-          // down channel
-          const bool write = r < args.n_rows && (d == 0 || p < P.n_fr);
+          // down channel, the zero rows before them no output
+          const bool write = r < args.n_rows && (spin || r >= args.pr_phi0) && (d == 0 || spin);
           if (write) {
             const int row = (d == 0 ? (p < P.n_fr ? p : 2 * P.n_fr) : p + P.n_fr) * P.n1 + lam;
             float* out = base + (size_t)row * args.nt;
@@ -1273,18 +1277,20 @@ __global__ void k_build_wplanes32(DevPlan Pd, int n1_pad, float* wr, float* wi) 
   }
 }
 
-// W planes of the spin-pair forward: row r = p n1 + lambda takes channel p (spin up) for
-// p < n_fr and the phi_F channel 2 n_fr for p = n_fr; BF16 hi / lo of Re and Im.
-__global__ void k_build_wpair(DevPlan Pd, int n1_pad, __nv_bfloat16* wr_hi, __nv_bfloat16* wi_hi,
-                              __nv_bfloat16* wr_lo, __nv_bfloat16* wi_lo) {
-  const long long total = (long long)(Pd.n_fr + 1) * Pd.n1 * n1_pad;
+// W planes of the spin-pair form: row r < n_fr n1 is row lambda = r mod n1 of spin-up channel
+// r / n1, rows [n_fr n1, pr_phi0) are zero and row pr_phi0 + lambda is row lambda of the
+// phi_F channel 2 n_fr; BF16 hi / lo of Re and Im.
+__global__ void k_build_wpair(DevPlan Pd, int n1_pad, int pr_phi0, __nv_bfloat16* wr_hi,
+                              __nv_bfloat16* wi_hi, __nv_bfloat16* wr_lo, __nv_bfloat16* wi_lo) {
+  const long long total = (long long)(pr_phi0 + Pd.n1) * n1_pad;
+  const int spin = Pd.n_fr * Pd.n1;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(i / n1_pad), lp = (int)(i % n1_pad);
-    const int pr = r / Pd.n1, lam = r % Pd.n1;
-    const int c = pr < Pd.n_fr ? pr : 2 * Pd.n_fr;
+    const int c = r < spin ? r / Pd.n1 : (r < pr_phi0 ? -1 : 2 * Pd.n_fr);
+    const int lam = r < spin ? r % Pd.n1 : r - pr_phi0;
     float2 v = make_float2(0.f, 0.f);
-    if (lp < Pd.n1) v = Pd.h[(size_t)c * Pd.N_fr + ((lam - lp) & (Pd.N_fr - 1))];
+    if (lp < Pd.n1 && c >= 0) v = Pd.h[(size_t)c * Pd.N_fr + ((lam - lp) & (Pd.N_fr - 1))];
     const __nv_bfloat16 hr = __float2bfloat16_rn(v.x), hi = __float2bfloat16_rn(v.y);
     wr_hi[i] = hr;
     wi_hi[i] = hi;
@@ -1433,10 +1439,11 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
     if (p->rates2[a].s) Lmax = std::max(Lmax, (p->rates2[a].L + BN - 1) / BN * BN);
   p->tc_wt_cols = Lmax;
   // items: (alpha, m0, n_tiles); the 16-frame BF16-plane forward runs in the spin-pair form
-  // over (n_fr + 1) n1 pair rows and 64-sample tiles
+  // over the pair rows and 64-sample tiles
   const bool tf = p->cfg.precision == JTFS_PREC_TF32;
   p->tc_pair = NT == 16 && !tf;
-  p->n_pr = (p->n_fr + 1) * p->n1;
+  p->pr_phi0 = (p->n_fr * p->n1 + 31) / 32 * 32;
+  p->n_pr = p->pr_phi0 + p->n1;
   const int tile_n = p->tc_pair ? 64 : BN;
   struct It { int a, m0, nt; long long cost; };
   std::vector<It> its;
@@ -1466,8 +1473,10 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   auto place = [&](size_t bytes) { size_t at = off; off += (bytes + 1023) & ~(size_t)1023; return at; };
   size_t o_w[6];
   for (int i = 0; i < 6; ++i) o_w[i] = place(wplane * 2);
+  // the spin-pair planes serve the 16-frame forward and backward
+  const bool pair_planes = NT == 16;
   size_t o_wp[4] = {0, 0, 0, 0};
-  if (p->tc_pair)
+  if (pair_planes)
     for (int i = 0; i < 4; ++i) o_wp[i] = place((size_t)p->n_pr * p->n1_pad * 2);
   size_t o_w32[2] = {0, 0};
   if (tf)
@@ -1480,7 +1489,7 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   if ((st = cuda_check(cudaMalloc(&p->d_tc_mem, off), "tc tables")) != JTFS_OK) return st;
   char* base = (char*)p->d_tc_mem;
   for (int i = 0; i < 6; ++i) p->d_wplanes[i] = base + o_w[i];
-  for (int i = 0; i < 4; ++i) p->d_wpair[i] = p->tc_pair ? base + o_wp[i] : nullptr;
+  for (int i = 0; i < 4; ++i) p->d_wpair[i] = pair_planes ? base + o_wp[i] : nullptr;
   if (tf)
     for (int i = 0; i < 2; ++i) p->d_wplanes32[i] = base + o_w32[i];
   p->d_wtf = base + o_wt;
@@ -1494,8 +1503,8 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
                                  (__nv_bfloat16*)p->d_wplanes[1], (__nv_bfloat16*)p->d_wplanes[2],
                                  (__nv_bfloat16*)p->d_wplanes[3], (__nv_bfloat16*)p->d_wplanes[4],
                                  (__nv_bfloat16*)p->d_wplanes[5]);
-  if (p->tc_pair)
-    k_build_wpair<<<1024, 256>>>(p->dp, p->n1_pad, (__nv_bfloat16*)p->d_wpair[0],
+  if (p->d_wpair[0])
+    k_build_wpair<<<1024, 256>>>(p->dp, p->n1_pad, p->pr_phi0, (__nv_bfloat16*)p->d_wpair[0],
                                  (__nv_bfloat16*)p->d_wpair[1], (__nv_bfloat16*)p->d_wpair[2],
                                  (__nv_bfloat16*)p->d_wpair[3]);
   k_build_wt<<<1024, 256>>>(p->dp, NT, Lmax, (__nv_bfloat16*)p->d_wtf,
@@ -1583,6 +1592,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   args.res_kb = tc_res_kb(p);
   args.wstages = f16 ? tc16_shape(p).WS : tc_shape(p).WS;
   args.n_rows = rows;
+  args.pr_phi0 = p->pr_phi0;
   args.nt = p->n_t;
   args.P = Pbuf;
   args.n2 = p->n2;

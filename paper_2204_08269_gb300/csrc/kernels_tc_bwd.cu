@@ -1047,6 +1047,354 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
   }
 }
 
+// ------------------------------------------------------------------ spin-pair form
+// The backward over pair rows (spin-up rows of the spin-pair W planes, whose spin-down rows
+// are their complex conjugates, then the phi_F rows), for rates whose lambda' range fits one
+// 64-wide atom.  Per 32-row chunk, with A = Y^T and B = [Wr ; Wi] (N = 64 rows):
+//   [P1 | P4] = Yr [Wr ; Wi]^T,  [P3 | P2] = Yi [Wr ; Wi]^T,  [g_up | g_dn] = w [G1_up ; G1_dn]^T
+// Z_up = (P1 - P2, P3 + P4), Z_dn = (P1 + P2, P3 - P4); gZ = g Z / |Z| per channel.  With
+// gZ_up = a + ib and gZ_dn = c + id, W_up^H gZ_up + W_dn^H gZ_dn = Wr^T S + Wi^T T for
+// S = (a + c) + i (b + d) and T = (b - d) + i (c - a), so the last product takes four MMAs:
+//   gY^T_re += S_re Wr + T_re Wi,   gY^T_im += S_im Wr + T_im Wi   (N = 64 lambda').
+// W bytes per channel row are a third of the channel-row form's [-Wi][Wr][Wi] blocks, which
+// leaves room for a four-chunk W ring.  PL = 2: the FP32-grade split as in the fast form.
+struct TpMaps {
+  CUtensorMap w[4];      // pair planes Wr_hi, Wi_hi, Wr_lo, Wi_lo; box {64 lambda', 32 rows}
+  CUtensorMap y[2][16];  // [hi/lo][alpha]: Y planes [2B][K][L], box {64 n, 32 lambda', 1}
+  CUtensorMap g1[2];     // hi, lo: channel-row G1 [rows][16] bf16, box {16, 32}
+  CUtensorMap wt[2];     // hi, lo: [rows][16] bf16, box {16, 128}
+};
+
+struct TpArgs {
+  const int4* items;    // (alpha, n0, lambda' start = lam_min & ~7, K1 <= 64) per base
+  int n_base;
+  int n_items;
+  int n_chunks;         // ceil(n_pr / 32)
+  int g1_rows;          // rows per (b, alpha) block of G1
+  int wbufs;            // W chunk ring depth (2..4)
+  int a2bufs;           // S / T staging buffers (1..2)
+  int pr_phi0;          // first phi_F pair row (multiple of 32)
+  int spin_rows;        // n_fr n1: channel row of the first spin-down row
+  int chan_phi0;        // 2 n_fr n1: channel row of the first phi_F row
+  const int* wt_row0;
+  float2* gy;
+  int* err;
+};
+
+template <int PL>
+__global__ void __launch_bounds__(kFThreads, 1)
+k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int NT = 16, RC = 32, KM = 64, CW = RC / 4;
+  constexpr uint32_t kA1Plane = 2 * KM * 128;             // two 64-sample halves x 64 lambda'
+  constexpr uint32_t kA4Plane = 128 * NT * 2;             // [128 n][16 t], 32-byte swizzle
+  constexpr uint32_t kWBlk = RC * 128;                    // 32 rows x 64 lambda'
+  constexpr uint32_t kG1Blk = RC * NT * 2;                // 32 rows x 16 t
+  constexpr uint32_t kWBuf = PL * 2 * kWBlk + PL * 2 * kG1Blk;
+  constexpr uint32_t kA2Part = 128 * RC * 2;              // [128 n][32 r] bf16, 64-byte swizzle
+  constexpr uint32_t kA2Buf = 4 * kA2Part;                // S_re, S_im, T_re, T_im
+  const int WB = args.wbufs, NA2 = args.a2bufs;
+  uint8_t* sA1 = sm;                                       // PL x 2 parts
+  uint8_t* sA4 = sA1 + PL * 2 * kA1Plane;                  // PL planes
+  uint8_t* sW = sA4 + PL * kA4Plane;                       // WB buffers: W blocks, then G1
+  uint8_t* sA2 = sW + WB * kWBuf;                          // NA2 buffers
+
+  __shared__ uint64_t a1_full, a1_free, w_full[4], w_empty[4], d1_full[2], d1_free[2],
+      a2_full[2], a2_free[2], d2_full, d2_free, mma_done, mma_done2;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    mbar_init(&a1_full, 1);
+    mbar_init(&a1_free, 1);
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&w_full[i], 1);
+      mbar_init(&w_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&d1_full[i], 1);
+      mbar_init(&d1_free[i], 16);
+      mbar_init(&a2_full[i], 16);
+      mbar_init(&a2_free[i], 1);
+    }
+    mbar_init(&d2_full, 1);
+    mbar_init(&d2_free, 16);
+    mbar_init(&mma_done, 1);
+    mbar_init(&mma_done2, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  // TMEM: buffers at 0 and 192, each [P1 | P4] [P3 | P2] [g_up | g_dn] (64 columns apiece);
+  // gY^T_re at 384 and gY^T_im at 448
+  const uint32_t t_re = tbase + 384, t_im = tbase + 448;
+  auto fail = [&](int code) {
+    if (!abort_flag) {
+      abort_flag = 1;
+      atomicCAS(args.err, 0, code);
+    }
+  };
+  const int npair = PL == 2 ? 3 : 1;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      uint32_t a1_ph = 0, wph = 0;
+      int wst = 0;
+      uint32_t armed_w = 0, armed_w_par = 0;
+      int armed_a1 = -1;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        const int a = item.x, b = it / args.n_base, n0 = item.y, start = item.z, K1 = item.w;
+        const Rate2 A = P.rates2[a];
+        const int nkb1 = (K1 + 31) / 32;
+        if (!mbar_wait(&a1_free, a1_ph ^ 1, kWaitNs)) { fail(81); break; }
+        mbar_arrive_expect_tx(&a1_full, PL * 2 * 2 * nkb1 * 4096 + PL * kA4Plane);
+        armed_a1 = (int)a1_ph;
+        for (int pl = 0; pl < PL; ++pl) {
+          for (int part = 0; part < 2; ++part)
+            for (int h = 0; h < 2; ++h)
+              for (int kb = 0; kb < nkb1; ++kb)
+                tma_load_3d(sA1 + (pl * 2 + part) * kA1Plane + h * KM * 128 + kb * 32 * 128,
+                            &maps.y[pl][a], n0 + h * 64, start - A.lam_min + kb * 32,
+                            2 * b + part, &a1_full);
+          tma_load_2d(sA4 + pl * kA4Plane, &maps.wt[pl], 0, args.wt_row0[a] + n0, &a1_full);
+        }
+        a1_ph ^= 1;
+        const int g1row = (b * P.n2 + a) * args.g1_rows;
+        for (int j = 0; j < args.n_chunks; ++j) {
+          if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(82); ok = false; break; }
+          mbar_arrive_expect_tx(&w_full[wst], kWBuf);
+          armed_w |= 1u << wst;
+          armed_w_par = (armed_w_par & ~(1u << wst)) | (wph << wst);
+          uint8_t* wb = sW + wst * kWBuf;
+          // G1 rows of the chunk's up and down channels (the phi_F chunks load their own rows
+          // twice; the epilogue drops the second copy)
+          const int r0 = j * RC;
+          const int up = r0 < args.pr_phi0 ? r0 : args.chan_phi0 + (r0 - args.pr_phi0);
+          const int dn = r0 < args.pr_phi0 ? r0 + args.spin_rows : up;
+          for (int pl = 0; pl < PL; ++pl) {
+            tma_load_2d(wb + pl * 2 * kWBlk, &maps.w[pl * 2], start, r0, &w_full[wst]);
+            tma_load_2d(wb + pl * 2 * kWBlk + kWBlk, &maps.w[pl * 2 + 1], start, r0, &w_full[wst]);
+            uint8_t* gb = wb + PL * 2 * kWBlk + pl * 2 * kG1Blk;
+            tma_load_2d(gb, &maps.g1[pl], 0, g1row + up, &w_full[wst]);
+            tma_load_2d(gb + kG1Blk, &maps.g1[pl], 0, g1row + dn, &w_full[wst]);
+          }
+          if (++wst == WB) { wst = 0; wph ^= 1; }
+        }
+      }
+      for (int i = 0; i < WB; ++i)
+        if (armed_w >> i & 1) mbar_wait(&w_full[i], armed_w_par >> i & 1, kWaitNs);
+      if (armed_a1 >= 0) mbar_wait(&a1_full, (uint32_t)armed_a1, kWaitNs);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ first-product issuer
+    if (lane == 0) {
+      const uint32_t id1 = instr_desc(128, 2 * RC, 1, 1, 1, 0, 0);
+      const uint32_t id4 = instr_desc(128, 2 * RC, 1, 1, 0, 0, 0);
+      uint32_t a1_ph = 0, wph = 0;
+      uint32_t d1f_ph = 0;   // bit i: phase of buffer i
+      int wst = 0, buf = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        const int nks1 = item.w / 16;
+        if (!mbar_wait(&a1_full, a1_ph, kWaitNs)) { fail(83); break; }
+        a1_ph ^= 1;
+        const uint32_t a1 = smem_u32(sA1), a4 = smem_u32(sA4);
+        for (int j = 0; j < args.n_chunks && ok; ++j) {
+          if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(84); ok = false; break; }
+          if (!mbar_wait(&d1_free[buf], ((d1f_ph >> buf) & 1) ^ 1, kWaitNs)) { fail(85); ok = false; break; }
+          d1f_ph ^= 1u << buf;
+          tc_fence_after();
+          const uint32_t wb = smem_u32(sW + wst * kWBuf);
+          const uint32_t t_a = tbase + buf * 192, t_b = t_a + 64, t_g = t_a + 128;
+          for (int ks = 0; ks < nks1; ++ks) {
+            for (int q = 0; q < npair; ++q) {
+              const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+              const uint64_t ayr = smem_desc(a1 + (pa * 2 + 0) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
+              const uint64_t ayi = smem_desc(a1 + (pa * 2 + 1) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
+              const uint64_t bw = smem_desc(wb + pb * 2 * kWBlk + ks * 32, 16, 1024, kSw128);
+              const uint32_t f = (ks | q) ? 1u : 0u;
+              mma_f16(t_a, ayr, bw, id1, f);    // [P1 | P4] = Yr [Wr ; Wi]^T
+              mma_f16(t_b, ayi, bw, id1, f);    // [P3 | P2] = Yi [Wr ; Wi]^T
+            }
+          }
+          const uint32_t g1 = wb + PL * 2 * kWBlk;
+          for (int q = 0; q < npair; ++q) {
+            const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+            mma_f16(t_g, smem_desc(a4 + pa * kA4Plane, 16, 256, kSw32),
+                    smem_desc(g1 + pb * 2 * kG1Blk, 16, 256, kSw32), id4, q ? 1u : 0u);
+          }
+          mma_commit(&d1_full[buf]);
+          if (++wst == WB) { wst = 0; wph ^= 1; }
+          buf ^= 1;
+        }
+        if (!ok) break;
+        mma_commit(&a1_free);
+      }
+      mma_commit(&mma_done);
+      mbar_wait(&mma_done, 0, kWaitNs);
+    }
+  } else if (warp == kFWarpG2) {
+    // ------------------------------------------------------------ last-product issuer
+    if (lane == 0) {
+      const uint32_t id2 = instr_desc(128, 64, 1, 1, 0, 1, 0);
+      uint32_t d2f_ph = 0, wph = 0, a2_ph = 0;   // a2_ph bit i: phase of buffer i
+      int wst = 0, q2 = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        for (int j = 0; j < args.n_chunks && ok; ++j) {
+          if (!mbar_wait(&a2_full[q2], (a2_ph >> q2) & 1, kWaitNs)) { fail(86); ok = false; break; }
+          a2_ph ^= 1u << q2;
+          if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(87); ok = false; break; }
+          if (j == 0) {
+            if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(88); ok = false; break; }
+            d2f_ph ^= 1;
+          }
+          tc_fence_after();
+          const uint32_t wb = smem_u32(sW + wst * kWBuf);
+          const uint32_t a2 = smem_u32(sA2 + q2 * kA2Buf);
+          for (int ks = 0; ks < RC / 16; ++ks) {
+            const uint64_t sre = smem_desc(a2 + 0 * kA2Part + ks * 32, 16, 512, kSw64);
+            const uint64_t sim = smem_desc(a2 + 1 * kA2Part + ks * 32, 16, 512, kSw64);
+            const uint64_t tre = smem_desc(a2 + 2 * kA2Part + ks * 32, 16, 512, kSw64);
+            const uint64_t tim = smem_desc(a2 + 3 * kA2Part + ks * 32, 16, 512, kSw64);
+            for (int q = 0; q < PL; ++q) {                      // W_hi, then W_lo
+              const uint32_t wpl = wb + q * 2 * kWBlk + ks * 2048;
+              const uint64_t wr = smem_desc(wpl, kWBlk, 1024, kSw128);
+              const uint64_t wi = smem_desc(wpl + kWBlk, kWBlk, 1024, kSw128);
+              const uint32_t f = (j == 0 && ks == 0 && q == 0) ? 0u : 1u;
+              mma_f16(t_re, sre, wr, id2, f);
+              mma_f16(t_re, tre, wi, id2, 1u);
+              mma_f16(t_im, sim, wr, id2, f);
+              mma_f16(t_im, tim, wi, id2, 1u);
+            }
+          }
+          mma_commit(&a2_free[q2]);
+          mma_commit(&w_empty[wst]);
+          if (++wst == WB) { wst = 0; wph ^= 1; }
+          if (++q2 == NA2) q2 = 0;
+        }
+        if (!ok) break;
+        mma_commit(&d2_full);
+      }
+      mma_commit(&mma_done2);
+      mbar_wait(&mma_done2, 0, kWaitNs);
+    }
+  } else if (warp >= 2 && warp < 2 + 16) {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - 2;                   // 0..15
+    const int quarter = warp & 3;
+    const int cg = ew >> 2;                    // pair rows [8 cg, 8 cg + 8) of a chunk
+    const int row = quarter * 32 + lane;       // time sample within the tile
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    uint32_t d2_ph = 0;
+    uint32_t d1_ph = 0, a2f_ph = 0;   // bit i: phase of buffer i
+    int buf = 0, q2 = 0;
+    for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+      const int4 item = args.items[it % args.n_base];
+      const int a = item.x, b = it / args.n_base, n0 = item.y, start = item.z;
+      bool ok = !abort_flag;
+      for (int j = 0; j < args.n_chunks && ok; ++j) {
+        if (!mbar_wait(&d1_full[buf], (d1_ph >> buf) & 1, kWaitNs)) { fail(89); ok = false; break; }
+        d1_ph ^= 1u << buf;
+        tc_fence_after();
+        uint32_t p1[CW], p4[CW], p3[CW], p2[CW], gu[CW], gd[CW];
+        const uint32_t t = tbase + buf * 192 + lane_off + cg * CW;
+        tmem_ld8u(t, p1);
+        tmem_ld8u(t + 32, p4);
+        tmem_ld8u(t + 64, p3);
+        tmem_ld8u(t + 96, p2);
+        tmem_ld8u(t + 128, gu);
+        tmem_ld8u(t + 160, gd);
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&d1_free[buf]);
+        const bool phi = j * RC >= args.pr_phi0;   // no spin-down channel
+        uint32_t sre[CW / 2], sim[CW / 2], tre[CW / 2], tim[CW / 2];
+#pragma unroll
+        for (int i = 0; i < CW / 2; ++i) {
+          float vs_re[2], vs_im[2], vt_re[2], vt_im[2];
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int k = 2 * i + e;
+            const float x1 = __uint_as_float(p1[k]), x2 = __uint_as_float(p2[k]);
+            const float x3 = __uint_as_float(p3[k]), x4 = __uint_as_float(p4[k]);
+            const float ru = x1 - x2, iu = x3 + x4, rd = x1 + x2, id = x3 - x4;
+            const float mu = fmaf(ru, ru, iu * iu), md = fmaf(rd, rd, id * id);
+            const float fu = mu > 0.f ? __uint_as_float(gu[k]) * rsqrt_approx(mu) : 0.f;
+            const float fd = (md > 0.f && !phi) ? __uint_as_float(gd[k]) * rsqrt_approx(md) : 0.f;
+            const float ga = ru * fu, gb = iu * fu, gc = rd * fd, gdd = id * fd;
+            vs_re[e] = ga + gc;
+            vs_im[e] = gb + gdd;
+            vt_re[e] = gb - gdd;
+            vt_im[e] = gc - ga;
+          }
+          __nv_bfloat162 h0 = __floats2bfloat162_rn(vs_re[0], vs_re[1]);
+          __nv_bfloat162 h1 = __floats2bfloat162_rn(vs_im[0], vs_im[1]);
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(vt_re[0], vt_re[1]);
+          __nv_bfloat162 h3 = __floats2bfloat162_rn(vt_im[0], vt_im[1]);
+          sre[i] = *reinterpret_cast<uint32_t*>(&h0);
+          sim[i] = *reinterpret_cast<uint32_t*>(&h1);
+          tre[i] = *reinterpret_cast<uint32_t*>(&h2);
+          tim[i] = *reinterpret_cast<uint32_t*>(&h3);
+        }
+        if (!mbar_wait(&a2_free[q2], ((a2f_ph >> q2) & 1) ^ 1, kWaitNs)) { fail(90); ok = false; break; }
+        a2f_ph ^= 1u << q2;
+        uint8_t* base = sA2 + q2 * kA2Buf + row * (RC * 2);
+        const int pos = (cg ^ ((row >> 1) & 3)) * 16;
+        *reinterpret_cast<uint4*>(base + 0 * kA2Part + pos) = make_uint4(sre[0], sre[1], sre[2], sre[3]);
+        *reinterpret_cast<uint4*>(base + 1 * kA2Part + pos) = make_uint4(sim[0], sim[1], sim[2], sim[3]);
+        *reinterpret_cast<uint4*>(base + 2 * kA2Part + pos) = make_uint4(tre[0], tre[1], tre[2], tre[3]);
+        *reinterpret_cast<uint4*>(base + 3 * kA2Part + pos) = make_uint4(tim[0], tim[1], tim[2], tim[3]);
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&a2_full[q2]);
+        buf ^= 1;
+        if (++q2 == NA2) q2 = 0;
+      }
+      if (!ok) break;
+      // gY of this tile: lambda' = start + c for c in [16 cg, 16 cg + 16)
+      if (!mbar_wait(&d2_full, d2_ph, kWaitNs)) { fail(91); break; }
+      d2_ph ^= 1;
+      tc_fence_after();
+      const Rate2 A = P.rates2[a];
+      const int n = n0 + row;
+      float2* go = args.gy + (size_t)b * P.y_len + A.off_y;
+      float vr[16], vi[16];
+      tmem_ld16(t_re + lane_off + cg * 16, vr);
+      tmem_ld16(t_im + lane_off + cg * 16, vi);
+      tmem_wait_ld();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d2_free);
+      if (n < A.L) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int lp = start + cg * 16 + i;
+          if (lp >= A.lam_min && lp < P.n1)
+            go[(size_t)(lp - A.lam_min) * A.L + n] = make_float2(vr[i], vi[i]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
 // G1[(b n2 + a) g1_rows + c n1 + lambda][t] = sum_lo phi_F[(lo s_F - lambda) mod N_fr] gS2[b,a,c,lo,t]
 // (or gS2 itself for Eq. 4), as BF16, zero for t >= n_t and in the row padding.
 __global__ void k_g1(DevPlan Pd, const float* __restrict__ gs2, int NT, int g1_rows,
@@ -1112,6 +1460,25 @@ static bool tcbf_layout(const jtfs_plan* p, int nat, int* wb_out, int* na2_out, 
   const size_t a2buf = (size_t)2 * 128 * RC * 2;
   const size_t budget = 225 * 1024;
   int wb = 3, na2 = 2;
+  while (fixed + wb * wbuf + na2 * a2buf > budget && (wb > 2 || na2 > 1)) {
+    if (na2 > 1 && wb == 2) na2 = 1; else --wb;
+  }
+  if (fixed + wb * wbuf + na2 * a2buf > budget) return false;
+  *wb_out = wb;
+  *na2_out = na2;
+  *smem_out = fixed + wb * wbuf + na2 * a2buf;
+  return true;
+}
+
+// Shared memory of the spin-pair form: resident Y^T and weight tiles, the W ring (2..4 chunks
+// of 32 pair rows) and the S / T staging (1..2 buffers), deepest first.
+static bool tcbp_layout(const jtfs_plan* p, int* wb_out, int* na2_out, size_t* smem_out) {
+  const int PL = p->split ? 2 : 1;
+  const size_t fixed = 1024 + (size_t)PL * 2 * (2 * 64 * 128) + (size_t)PL * 128 * 16 * 2;
+  const size_t wbuf = (size_t)PL * 2 * 32 * 128 + (size_t)PL * 2 * 32 * 16 * 2;
+  const size_t a2buf = (size_t)4 * 128 * 32 * 2;
+  const size_t budget = 225 * 1024;
+  int wb = 4, na2 = 2;
   while (fixed + wb * wbuf + na2 * a2buf > budget && (wb > 2 || na2 > 1)) {
     if (na2 > 1 && wb == 2) na2 = 1; else --wb;
   }
@@ -1326,6 +1693,60 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     const int first = nat == 1 ? 0 : p->tcbf_n1;
     const int count = nat == 1 ? p->tcbf_n1 : (int)(p->tcbf_items.size() / 4) - p->tcbf_n1;
     if (count <= 0) continue;
+    int wbp = 0, na2p = 0;
+    size_t smemp = 0;
+    if (nat == 1 && NT == 16 && three && p->d_wpair[0] && tcbp_layout(p, &wbp, &na2p, &smemp)) {
+      // the K1 <= 64 items of the FP32-grade split in the spin-pair form (with one BF16 pass
+      // the channel-row form's 128-wide products are faster)
+      TpMaps pm;
+      for (int pl = 0; pl < 4; ++pl) {
+        cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)p->n_pr};
+        cuuint64_t str[1] = {(cuuint64_t)p->n1_pad * 2};
+        cuuint32_t box[2] = {64, 32};
+        if (!make_tmap(&pm.w[pl], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p->d_wpair[pl], dims, str, box, 128, &err)) {
+          set_error(err);
+          return JTFS_ERR_CUDA;
+        }
+      }
+      for (int h = 0; h < 2; ++h) {
+        for (int a = 0; a < 16; ++a) pm.y[h][a] = my[h][a];
+        pm.wt[h] = mwt[h];
+        cuuint64_t dims[2] = {(cuuint64_t)NT, (cuuint64_t)B * p->n2 * g1_rows};
+        cuuint64_t str[1] = {(cuuint64_t)NT * 2};
+        cuuint32_t box[2] = {(cuuint32_t)NT, 32};
+        if (!make_tmap(&pm.g1[h], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h ? g1lo : g1hi, dims, str, box, NT * 2, &err)) {
+          set_error(err);
+          return JTFS_ERR_CUDA;
+        }
+      }
+      TpArgs pa;
+      pa.items = reinterpret_cast<const int4*>(p->d_tcbf_items) + first;
+      pa.n_base = count;
+      pa.n_items = count * B;
+      pa.n_chunks = (p->n_pr + 31) / 32;
+      pa.g1_rows = g1_rows;
+      pa.wbufs = wbp;
+      pa.a2bufs = na2p;
+      pa.pr_phi0 = p->pr_phi0;
+      pa.spin_rows = p->n_fr * p->n1;
+      pa.chan_phi0 = 2 * p->n_fr * p->n1;
+      pa.wt_row0 = p->d_wtb_row0;
+      pa.gy = gy;
+      pa.err = p->d_err;
+      const int grid = std::min(pa.n_items, n_sm);
+#define JTFS_LAUNCH_TCBP(PLV)                                                                   \
+  do {                                                                                          \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_pair<PLV>,                            \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                              (int)smemp), "attr tcbp")) != JTFS_OK)            \
+      return rc;                                                                                \
+    k_joint_bwd_pair<PLV><<<grid, kFThreads, smemp, st>>>(pm, pa, d);                           \
+  } while (0)
+      JTFS_LAUNCH_TCBP(2);
+#undef JTFS_LAUNCH_TCBP
+      if ((rc = cuda_check(cudaGetLastError(), "k_joint_bwd_pair")) != JTFS_OK) return rc;
+      continue;
+    }
     const int PLf = three ? 2 : 1, RCf = nat == 1 ? 64 : 32;
     TfMaps fm;
     for (int pl = 0; pl < 6; ++pl) {
