@@ -1081,17 +1081,18 @@ struct TpArgs {
   int* err;
 };
 
-template <int PL>
+template <int PL, int NAT>
 __global__ void __launch_bounds__(kFThreads, 1)
 k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int NT = 16, RC = 32, KM = 64, CW = RC / 4;
+  constexpr int NT = 16, RC = 32, KM = NAT == 1 ? 64 : 96, CW = RC / 4;
+  constexpr int NB1 = NAT == 1 ? 2 : 1;                   // first-product TMEM buffers
   constexpr uint32_t kA1Plane = 2 * KM * 128;             // two 64-sample halves x 64 lambda'
   constexpr uint32_t kA4Plane = 128 * NT * 2;             // [128 n][16 t], 32-byte swizzle
   constexpr uint32_t kWBlk = RC * 128;                    // 32 rows x 64 lambda'
   constexpr uint32_t kG1Blk = RC * NT * 2;                // 32 rows x 16 t
-  constexpr uint32_t kWBuf = PL * 2 * kWBlk + PL * 2 * kG1Blk;
+  constexpr uint32_t kWBuf = PL * NAT * 2 * kWBlk + PL * 2 * kG1Blk;   // [Wr a][Wi a] per atom a
   constexpr uint32_t kA2Part = 128 * RC * 2;              // [128 n][32 r] bf16, 64-byte swizzle
   constexpr uint32_t kA2Buf = 4 * kA2Part;                // S_re, S_im, T_re, T_im
   const int WB = args.wbufs, NA2 = args.a2bufs;
@@ -1132,9 +1133,9 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
-  // TMEM: buffers at 0 and 192, each [P1 | P4] [P3 | P2] [g_up | g_dn] (64 columns apiece);
-  // gY^T_re at 384 and gY^T_im at 448
-  const uint32_t t_re = tbase + 384, t_im = tbase + 448;
+  // TMEM: NB1 buffers of 192 columns, each [P1 | P4] [P3 | P2] [g_up | g_dn] (64 apiece), then
+  // gY^T_re and gY^T_im (64 NAT columns each)
+  const uint32_t t_re = tbase + NB1 * 192, t_im = t_re + 64 * NAT;
   auto fail = [&](int code) {
     if (!abort_flag) {
       abort_flag = 1;
@@ -1182,9 +1183,12 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
           const int up = r0 < args.pr_phi0 ? r0 : args.chan_phi0 + (r0 - args.pr_phi0);
           const int dn = r0 < args.pr_phi0 ? r0 + args.spin_rows : up;
           for (int pl = 0; pl < PL; ++pl) {
-            tma_load_2d(wb + pl * 2 * kWBlk, &maps.w[pl * 2], start, r0, &w_full[wst]);
-            tma_load_2d(wb + pl * 2 * kWBlk + kWBlk, &maps.w[pl * 2 + 1], start, r0, &w_full[wst]);
-            uint8_t* gb = wb + PL * 2 * kWBlk + pl * 2 * kG1Blk;
+            for (int at = 0; at < NAT; ++at) {
+              uint8_t* blk = wb + (pl * NAT + at) * 2 * kWBlk;
+              tma_load_2d(blk, &maps.w[pl * 2], start + 64 * at, r0, &w_full[wst]);
+              tma_load_2d(blk + kWBlk, &maps.w[pl * 2 + 1], start + 64 * at, r0, &w_full[wst]);
+            }
+            uint8_t* gb = wb + PL * NAT * 2 * kWBlk + pl * 2 * kG1Blk;
             tma_load_2d(gb, &maps.g1[pl], 0, g1row + up, &w_full[wst]);
             tma_load_2d(gb + kG1Blk, &maps.g1[pl], 0, g1row + dn, &w_full[wst]);
           }
@@ -1222,13 +1226,14 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
               const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
               const uint64_t ayr = smem_desc(a1 + (pa * 2 + 0) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
               const uint64_t ayi = smem_desc(a1 + (pa * 2 + 1) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
-              const uint64_t bw = smem_desc(wb + pb * 2 * kWBlk + ks * 32, 16, 1024, kSw128);
+              const uint64_t bw = smem_desc(wb + ((pb * NAT + (ks >> 2)) * 2) * kWBlk + (ks & 3) * 32,
+                                            16, 1024, kSw128);
               const uint32_t f = (ks | q) ? 1u : 0u;
               mma_f16(t_a, ayr, bw, id1, f);    // [P1 | P4] = Yr [Wr ; Wi]^T
               mma_f16(t_b, ayi, bw, id1, f);    // [P3 | P2] = Yi [Wr ; Wi]^T
             }
           }
-          const uint32_t g1 = wb + PL * 2 * kWBlk;
+          const uint32_t g1 = wb + PL * NAT * 2 * kWBlk;
           for (int q = 0; q < npair; ++q) {
             const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
             mma_f16(t_g, smem_desc(a4 + pa * kA4Plane, 16, 256, kSw32),
@@ -1236,7 +1241,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
           }
           mma_commit(&d1_full[buf]);
           if (++wst == WB) { wst = 0; wph ^= 1; }
-          buf ^= 1;
+          if (NB1 == 2) buf ^= 1;
         }
         if (!ok) break;
         mma_commit(&a1_free);
@@ -1247,7 +1252,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
   } else if (warp == kFWarpG2) {
     // ------------------------------------------------------------ last-product issuer
     if (lane == 0) {
-      const uint32_t id2 = instr_desc(128, 64, 1, 1, 0, 1, 0);
+      const uint32_t id2 = instr_desc(128, 64 * NAT, 1, 1, 0, 1, 0);
       uint32_t d2f_ph = 0, wph = 0, a2_ph = 0;   // a2_ph bit i: phase of buffer i
       int wst = 0, q2 = 0;
       bool ok = true;
@@ -1269,9 +1274,10 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
             const uint64_t tre = smem_desc(a2 + 2 * kA2Part + ks * 32, 16, 512, kSw64);
             const uint64_t tim = smem_desc(a2 + 3 * kA2Part + ks * 32, 16, 512, kSw64);
             for (int q = 0; q < PL; ++q) {                      // W_hi, then W_lo
-              const uint32_t wpl = wb + q * 2 * kWBlk + ks * 2048;
-              const uint64_t wr = smem_desc(wpl, kWBlk, 1024, kSw128);
-              const uint64_t wi = smem_desc(wpl + kWBlk, kWBlk, 1024, kSw128);
+              // MN-major over lambda': the NAT atoms of Wr (of Wi) are 2 kWBlk apart
+              const uint32_t wpl = wb + q * NAT * 2 * kWBlk + ks * 2048;
+              const uint64_t wr = smem_desc(wpl, 2 * kWBlk, 1024, kSw128);
+              const uint64_t wi = smem_desc(wpl + kWBlk, 2 * kWBlk, 1024, kSw128);
               const uint32_t f = (j == 0 && ks == 0 && q == 0) ? 0u : 1u;
               mma_f16(t_re, sre, wr, id2, f);
               mma_f16(t_re, tre, wi, id2, 1u);
@@ -1360,7 +1366,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
         fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) mbar_arrive(&a2_full[q2]);
-        buf ^= 1;
+        if (NB1 == 2) buf ^= 1;
         if (++q2 == NA2) q2 = 0;
       }
       if (!ok) break;
@@ -1371,21 +1377,24 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
       const Rate2 A = P.rates2[a];
       const int n = n0 + row;
       float2* go = args.gy + (size_t)b * P.y_len + A.off_y;
-      float vr[16], vi[16];
-      tmem_ld16(t_re + lane_off + cg * 16, vr);
-      tmem_ld16(t_im + lane_off + cg * 16, vi);
-      tmem_wait_ld();
+#pragma unroll
+      for (int at = 0; at < NAT; ++at) {      // one atom at a time (registers)
+        float vr[16], vi[16];
+        tmem_ld16(t_re + 64 * at + lane_off + cg * 16, vr);
+        tmem_ld16(t_im + 64 * at + lane_off + cg * 16, vi);
+        tmem_wait_ld();
+        if (n < A.L) {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int lp = start + 64 * at + cg * 16 + i;
+            if (lp >= A.lam_min && lp < P.n1)
+              go[(size_t)(lp - A.lam_min) * A.L + n] = make_float2(vr[i], vi[i]);
+          }
+        }
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&d2_free);
-      if (n < A.L) {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int lp = start + cg * 16 + i;
-          if (lp >= A.lam_min && lp < P.n1)
-            go[(size_t)(lp - A.lam_min) * A.L + n] = make_float2(vr[i], vi[i]);
-        }
-      }
     }
   }
   __syncthreads();
@@ -1472,10 +1481,10 @@ static bool tcbf_layout(const jtfs_plan* p, int nat, int* wb_out, int* na2_out, 
 
 // Shared memory of the spin-pair form: resident Y^T and weight tiles, the W ring (2..4 chunks
 // of 32 pair rows) and the S / T staging (1..2 buffers), deepest first.
-static bool tcbp_layout(const jtfs_plan* p, int* wb_out, int* na2_out, size_t* smem_out) {
-  const int PL = p->split ? 2 : 1;
-  const size_t fixed = 1024 + (size_t)PL * 2 * (2 * 64 * 128) + (size_t)PL * 128 * 16 * 2;
-  const size_t wbuf = (size_t)PL * 2 * 32 * 128 + (size_t)PL * 2 * 32 * 16 * 2;
+static bool tcbp_layout(const jtfs_plan* p, int nat, int* wb_out, int* na2_out, size_t* smem_out) {
+  const int PL = p->split ? 2 : 1, KM = nat == 1 ? 64 : 96;
+  const size_t fixed = 1024 + (size_t)PL * 2 * (2 * KM * 128) + (size_t)PL * 128 * 16 * 2;
+  const size_t wbuf = (size_t)PL * nat * 2 * 32 * 128 + (size_t)PL * 2 * 32 * 16 * 2;
   const size_t a2buf = (size_t)4 * 128 * 32 * 2;
   const size_t budget = 225 * 1024;
   int wb = 4, na2 = 2;
@@ -1695,9 +1704,9 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     if (count <= 0) continue;
     int wbp = 0, na2p = 0;
     size_t smemp = 0;
-    if (nat == 1 && NT == 16 && three && p->d_wpair[0] && tcbp_layout(p, &wbp, &na2p, &smemp)) {
-      // the K1 <= 64 items of the FP32-grade split in the spin-pair form (with one BF16 pass
-      // the channel-row form's 128-wide products are faster)
+    if (NT == 16 && three && p->d_wpair[0] && tcbp_layout(p, nat, &wbp, &na2p, &smemp)) {
+      // the FP32-grade split in the spin-pair form (with one BF16 pass the channel-row form's
+      // 128-wide products are faster)
       TpMaps pm;
       for (int pl = 0; pl < 4; ++pl) {
         cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)p->n_pr};
@@ -1734,15 +1743,15 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       pa.gy = gy;
       pa.err = p->d_err;
       const int grid = std::min(pa.n_items, n_sm);
-#define JTFS_LAUNCH_TCBP(PLV)                                                                   \
+#define JTFS_LAUNCH_TCBP(PLV, NATV)                                                             \
   do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_pair<PLV>,                            \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_pair<PLV, NATV>,                      \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smemp), "attr tcbp")) != JTFS_OK)            \
       return rc;                                                                                \
-    k_joint_bwd_pair<PLV><<<grid, kFThreads, smemp, st>>>(pm, pa, d);                           \
+    k_joint_bwd_pair<PLV, NATV><<<grid, kFThreads, smemp, st>>>(pm, pa, d);                     \
   } while (0)
-      JTFS_LAUNCH_TCBP(2);
+      if (nat == 1) JTFS_LAUNCH_TCBP(2, 1); else JTFS_LAUNCH_TCBP(2, 2);
 #undef JTFS_LAUNCH_TCBP
       if ((rc = cuda_check(cudaGetLastError(), "k_joint_bwd_pair")) != JTFS_OK) return rc;
       continue;
