@@ -196,3 +196,38 @@ def test_lambda_axis_energy_identity():
     frame = p.phi_F_hat ** 2 + np.sum(ps ** 2 + ps[:, (-n) % Nf] ** 2, axis=0)
     rhs = np.sum(np.abs(vh) ** 2 * frame) / Nf
     assert abs(lhs - rhs) / rhs < 1e-12
+
+
+@pytest.mark.parametrize("w", sorted(O.WORKLOADS))
+def test_spin_down_is_conjugate(w):
+    """The spin-down filter is the complex conjugate of the spin-up one (real spectra that
+    vanish at DC and Nyquist), so W_{c + n_fr} = conj(W_c); the contractions build both spins
+    from the four real products of the spin-up rows (Sec. 2, spin pairs)."""
+    p = O.Plan(O.WORKLOADS[w])
+    nf = p.n_fr
+    for b in range(nf):
+        assert p.fr_hat[b][p.N_fr // 2] == 0.0 and p.fr_hat[b][0] == 0.0
+    np.testing.assert_allclose(p.h[nf:2 * nf], np.conj(p.h[:nf]), rtol=0, atol=1e-15)
+    np.testing.assert_allclose(p.W[nf:2 * nf], np.conj(p.W[:nf]), rtol=0, atol=1e-15)
+
+
+def test_spin_pair_products_and_adjoint():
+    """The spin-pair algebra on the oracle's W: with W_up = Wr + i Wi,
+    Z_up = (Wr Yr - Wi Yi) + i (Wr Yi + Wi Yr) and Z_dn = (Wr Yr + Wi Yi) + i (Wr Yi - Wi Yr)
+    equal W_up Y and W_dn Y; and W_up^H gZ_up + W_dn^H gZ_dn = Wr^T S + Wi^T T with
+    S = gZ_up + gZ_dn, T = (Im gZ_up - Im gZ_dn) + i (Re gZ_dn - Re gZ_up)."""
+    p = O.Plan(O.WORKLOADS[2])
+    rng = np.random.default_rng(16)
+    Y = rng.standard_normal((p.n1, 7)) + 1j * rng.standard_normal((p.n1, 7))
+    for b in range(p.n_fr):
+        Wu, Wd = p.W[b], p.W[b + p.n_fr]
+        Wr, Wi = Wu.real, Wu.imag
+        P1, P2, P3, P4 = Wr @ Y.real, Wi @ Y.imag, Wr @ Y.imag, Wi @ Y.real
+        np.testing.assert_allclose(P1 - P2 + 1j * (P3 + P4), Wu @ Y, atol=1e-13)
+        np.testing.assert_allclose(P1 + P2 + 1j * (P3 - P4), Wd @ Y, atol=1e-13)
+        gu = rng.standard_normal((p.n1, 7)) + 1j * rng.standard_normal((p.n1, 7))
+        gd = rng.standard_normal((p.n1, 7)) + 1j * rng.standard_normal((p.n1, 7))
+        S = gu + gd
+        T = (gu.imag - gd.imag) + 1j * (gd.real - gu.real)
+        np.testing.assert_allclose(Wr.T @ S + Wi.T @ T,
+                                   Wu.conj().T @ gu + Wd.conj().T @ gd, atol=1e-13)
