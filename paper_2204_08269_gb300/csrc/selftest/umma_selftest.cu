@@ -15,6 +15,8 @@ using namespace jtfs::umma;
 
 namespace {
 
+using __bf16_raw_t = uint16_t;
+
 __global__ void k_umma_selftest(const __grid_constant__ CUtensorMap ta,
                                 const __grid_constant__ CUtensorMap tb, float* D, int K,
                                 int a_swz, int b_mn, int* status) {
@@ -86,6 +88,76 @@ __global__ void k_umma_selftest(const __grid_constant__ CUtensorMap ta,
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tbase, 128);
+  if (threadIdx.x == 0) *status = failed;
+}
+
+// A from tensor memory: each thread stores its row of A (two BF16 per 32-bit column) with
+// tcgen05.st, then one thread issues D = A B with B MN-major from shared memory (as above).
+__global__ void k_umma_selftest_ta(const __bf16_raw_t* A, const __grid_constant__ CUtensorMap tb,
+                                   float* D, int K, int* status) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sB = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t bar_tma, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    mbar_init(&bar_tma, 1);
+    mbar_init(&bar_mma, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(&tmem_base, 256);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  // A columns start at 128: row r = 32 warp + lane, column c holds A[r][2c], A[r][2c + 1]
+  {
+    const int row = warp * 32 + lane;
+    const uint32_t* arow = reinterpret_cast<const uint32_t*>(A + (size_t)row * K);
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    for (int c = 0; c < K / 2; c += 4)
+      tmem_st4(tbase + lane_off + 128 + c, arow[c], arow[c + 1], arow[c + 2], arow[c + 3]);
+    tmem_wait_st();
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc_fence_after();
+    mbar_arrive_expect_tx(&bar_tma, (uint32_t)(128 * K * 2));
+    for (int n0 = 0; n0 < 128; n0 += 64) tma_load_2d(sB + (n0 / 64) * K * 128, &tb, n0, 0, &bar_tma);
+    if (!mbar_wait(&bar_tma, 0, 2000000000ull)) {
+      failed = 1;
+    } else {
+      const uint32_t idesc = instr_desc(128, 128, 1, 1, 0, 1, 0);
+      for (int j = 0; j < K / 16; ++j) {
+        const uint64_t bd = smem_desc(smem_u32(sB + j * 16 * 128), (uint32_t)(K * 128), 1024, kSw128);
+        mma_f16_ta(tbase, tbase + 128 + j * 8, bd, idesc, j > 0 ? 1u : 0u);
+      }
+      mma_commit(&bar_mma);
+    }
+  }
+  __syncthreads();
+  if (!failed) {
+    if (!mbar_wait(&bar_mma, 0, 2000000000ull)) atomicExch(&failed, 1);
+  }
+  tc_fence_after();
+  if (!failed) {
+    const int row = warp * 32 + lane;
+    for (int c0 = 0; c0 < 128; c0 += 16) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) D[row * 128 + c0 + i] = v[i];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, 256);
   if (threadIdx.x == 0) *status = failed;
 }
 
@@ -218,5 +290,21 @@ extern "C" int jtfs_selftest_umma(const void* A, const void* B, float* D, int K,
   const size_t smem = 1024 + (size_t)128 * K * 2 * 2;
   cudaFuncSetAttribute(k_umma_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_umma_selftest<<<1, 128, smem, (cudaStream_t)stream>>>(ta, tb, D, K, a_swz, b_mn, status_dev);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+extern "C" int jtfs_selftest_umma_ta(const void* A, const void* B, float* D, int K,
+                                     int* status_dev, void* stream) {
+  if (K < 16 || K > 128 || K % 16) return 1;
+  CUtensorMap tb;
+  std::string err;
+  cuuint64_t dims[2] = {128, (cuuint64_t)K};
+  cuuint64_t str[1] = {128 * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)K};
+  if (!make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, dims, str, box, 128, &err)) return 2;
+  const size_t smem = 1024 + (size_t)128 * K * 2;
+  cudaFuncSetAttribute(k_umma_selftest_ta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_umma_selftest_ta<<<1, 128, smem, (cudaStream_t)stream>>>((const __bf16_raw_t*)A, tb, D, K,
+                                                              status_dev);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }

@@ -66,3 +66,29 @@ def test_umma_tf32_gemm(K, b_mn):
     ref = A.double() @ Bkn.double()
     err = (D.double() - ref).abs().max().item() / ref.abs().max().item()
     assert err < 2e-3, err
+
+
+@pytest.mark.parametrize("K", [16, 32, 64])
+def test_umma_bf16_gemm_a_in_tmem(K):
+    """A stored into tensor memory with tcgen05.st (row r in lane r, two BF16 per column),
+    B MN-major in shared memory: D = A B."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_08269_gb300 import build
+    build.build()
+    L = ctypes.CDLL(build.SELFTEST_LIB)
+    f = L.jtfs_selftest_umma_ta
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int] + [ctypes.c_void_p] * 2
+    f.restype = ctypes.c_int
+    g = torch.Generator(device="cuda").manual_seed(100 + K)
+    A = torch.randn(128, K, device="cuda", generator=g).to(torch.bfloat16).contiguous()
+    Bkn = torch.randn(K, 128, device="cuda", generator=g).to(torch.bfloat16).contiguous()
+    D = torch.full((128, 128), float("nan"), device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = f(A.data_ptr(), Bkn.data_ptr(), D.data_ptr(), K, status.data_ptr(), None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    ref = A.float() @ Bkn.float()
+    err = (D - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 1e-5, err
