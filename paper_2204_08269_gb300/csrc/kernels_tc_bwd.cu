@@ -1081,13 +1081,14 @@ struct TpArgs {
   int* err;
 };
 
-template <int PL, int NAT>
+template <int PL, int NAT, int KMV>
 __global__ void __launch_bounds__(kFThreads, 1)
 k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int NT = 16, RC = 32, KM = NAT == 1 ? 64 : 96, CW = RC / 4;
+  constexpr int NT = 16, RC = 32, KM = KMV, CW = RC / 4;
   constexpr int NB1 = NAT == 1 ? 2 : 1;                   // first-product TMEM buffers
+  constexpr bool TA = NAT >= 2;                           // S / T staged in TMEM (A operand)
   constexpr uint32_t kA1Plane = 2 * KM * 128;             // two 64-sample halves x 64 lambda'
   constexpr uint32_t kA4Plane = 128 * NT * 2;             // [128 n][16 t], 32-byte swizzle
   constexpr uint32_t kWBlk = RC * 128;                    // 32 rows x 64 lambda'
@@ -1099,7 +1100,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
   uint8_t* sA1 = sm;                                       // PL x 2 parts
   uint8_t* sA4 = sA1 + PL * 2 * kA1Plane;                  // PL planes
   uint8_t* sW = sA4 + PL * kA4Plane;                       // WB buffers: W blocks, then G1
-  uint8_t* sA2 = sW + WB * kWBuf;                          // NA2 buffers
+  uint8_t* sA2 = sW + WB * kWBuf;                          // NA2 buffers (shared-memory staging)
 
   __shared__ uint64_t a1_full, a1_free, w_full[4], w_empty[4], d1_full[2], d1_free[2],
       a2_full[2], a2_free[2], d2_full, d2_free, mma_done, mma_done2;
@@ -1134,8 +1135,10 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
   tc_fence_after();
   const uint32_t tbase = tmem_base;
   // TMEM: NB1 buffers of 192 columns, each [P1 | P4] [P3 | P2] [g_up | g_dn] (64 apiece), then
-  // gY^T_re and gY^T_im (64 NAT columns each)
+  // gY^T_re and gY^T_im (64 NAT columns each), then (TA) S_re, S_im, T_re, T_im as the last
+  // product's A operand: 32 pair rows of BF16 = 16 columns apiece
   const uint32_t t_re = tbase + NB1 * 192, t_im = t_re + 64 * NAT;
+  const uint32_t t_a2 = t_im + 64 * NAT;
   auto fail = [&](int code) {
     if (!abort_flag) {
       abort_flag = 1;
@@ -1279,10 +1282,18 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
               const uint64_t wr = smem_desc(wpl, 2 * kWBlk, 1024, kSw128);
               const uint64_t wi = smem_desc(wpl + kWBlk, 2 * kWBlk, 1024, kSw128);
               const uint32_t f = (j == 0 && ks == 0 && q == 0) ? 0u : 1u;
-              mma_f16(t_re, sre, wr, id2, f);
-              mma_f16(t_re, tre, wi, id2, 1u);
-              mma_f16(t_im, sim, wr, id2, f);
-              mma_f16(t_im, tim, wi, id2, 1u);
+              if (TA) {
+                const uint32_t ta = t_a2 + ks * 8;
+                mma_f16_ta(t_re, ta, wr, id2, f);
+                mma_f16_ta(t_re, ta + 32, wi, id2, 1u);
+                mma_f16_ta(t_im, ta + 16, wr, id2, f);
+                mma_f16_ta(t_im, ta + 48, wi, id2, 1u);
+              } else {
+                mma_f16(t_re, sre, wr, id2, f);
+                mma_f16(t_re, tre, wi, id2, 1u);
+                mma_f16(t_im, sim, wr, id2, f);
+                mma_f16(t_im, tim, wi, id2, 1u);
+              }
             }
           }
           mma_commit(&a2_free[q2]);
@@ -1357,13 +1368,25 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
         }
         if (!mbar_wait(&a2_free[q2], ((a2f_ph >> q2) & 1) ^ 1, kWaitNs)) { fail(90); ok = false; break; }
         a2f_ph ^= 1u << q2;
-        uint8_t* base = sA2 + q2 * kA2Buf + row * (RC * 2);
-        const int pos = (cg ^ ((row >> 1) & 3)) * 16;
-        *reinterpret_cast<uint4*>(base + 0 * kA2Part + pos) = make_uint4(sre[0], sre[1], sre[2], sre[3]);
-        *reinterpret_cast<uint4*>(base + 1 * kA2Part + pos) = make_uint4(sim[0], sim[1], sim[2], sim[3]);
-        *reinterpret_cast<uint4*>(base + 2 * kA2Part + pos) = make_uint4(tre[0], tre[1], tre[2], tre[3]);
-        *reinterpret_cast<uint4*>(base + 3 * kA2Part + pos) = make_uint4(tim[0], tim[1], tim[2], tim[3]);
-        fence_proxy_async_smem();
+        if (TA) {
+          // this warp's 8 pair rows are columns [4 cg, 4 cg + 4) of each part
+          const uint32_t ta = t_a2 + lane_off + cg * 4;
+          tc_fence_after();
+          tmem_st4(ta, sre[0], sre[1], sre[2], sre[3]);
+          tmem_st4(ta + 16, sim[0], sim[1], sim[2], sim[3]);
+          tmem_st4(ta + 32, tre[0], tre[1], tre[2], tre[3]);
+          tmem_st4(ta + 48, tim[0], tim[1], tim[2], tim[3]);
+          tmem_wait_st();
+          tc_fence_before();
+        } else {
+          uint8_t* base = sA2 + q2 * kA2Buf + row * (RC * 2);
+          const int pos = (cg ^ ((row >> 1) & 3)) * 16;
+          *reinterpret_cast<uint4*>(base + 0 * kA2Part + pos) = make_uint4(sre[0], sre[1], sre[2], sre[3]);
+          *reinterpret_cast<uint4*>(base + 1 * kA2Part + pos) = make_uint4(sim[0], sim[1], sim[2], sim[3]);
+          *reinterpret_cast<uint4*>(base + 2 * kA2Part + pos) = make_uint4(tre[0], tre[1], tre[2], tre[3]);
+          *reinterpret_cast<uint4*>(base + 3 * kA2Part + pos) = make_uint4(tim[0], tim[1], tim[2], tim[3]);
+          fence_proxy_async_smem();
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&a2_full[q2]);
         if (NB1 == 2) buf ^= 1;
@@ -1481,13 +1504,14 @@ static bool tcbf_layout(const jtfs_plan* p, int nat, int* wb_out, int* na2_out, 
 
 // Shared memory of the spin-pair form: resident Y^T and weight tiles, the W ring (2..4 chunks
 // of 32 pair rows) and the S / T staging (1..2 buffers), deepest first.
-static bool tcbp_layout(const jtfs_plan* p, int nat, int* wb_out, int* na2_out, size_t* smem_out) {
-  const int PL = p->split ? 2 : 1, KM = nat == 1 ? 64 : 96;
+static bool tcbp_layout(const jtfs_plan* p, int nat, int KM, int* wb_out, int* na2_out,
+                        size_t* smem_out) {
+  const int PL = p->split ? 2 : 1;
   const size_t fixed = 1024 + (size_t)PL * 2 * (2 * KM * 128) + (size_t)PL * 128 * 16 * 2;
   const size_t wbuf = (size_t)PL * nat * 2 * 32 * 128 + (size_t)PL * 2 * 32 * 16 * 2;
-  const size_t a2buf = (size_t)4 * 128 * 32 * 2;
+  const size_t a2buf = nat >= 2 ? 0 : (size_t)4 * 128 * 32 * 2;   // two atoms: S / T in TMEM
   const size_t budget = 225 * 1024;
-  int wb = 4, na2 = 2;
+  int wb = 4, na2 = nat >= 2 ? 1 : 2;
   while (fixed + wb * wbuf + na2 * a2buf > budget && (wb > 2 || na2 > 1)) {
     if (na2 > 1 && wb == 2) na2 = 1; else --wb;
   }
@@ -1530,9 +1554,13 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   std::vector<It> its, fast1, fast2;
   int wb_, na2_;
   size_t smem_;
-  const bool use_f1 = tcbf_layout(p, 1, &wb_, &na2_, &smem_);
-  const bool use_f2 = tcbf_layout(p, 2, &wb_, &na2_, &smem_);
-  const int km2 = tcbf_km(p, 2);
+  // the FP32-grade split runs the spin-pair form (one atom: K1 <= 64; two atoms: K1 <= 128)
+  const bool pair = p->split && NT == 16 && p->d_wpair[0] != nullptr;
+  const bool use_p1 = pair && tcbp_layout(p, 1, 64, &wb_, &na2_, &smem_);
+  const bool use_p2 = pair && tcbp_layout(p, 2, 128, &wb_, &na2_, &smem_);
+  const bool use_f1 = use_p1 || tcbf_layout(p, 1, &wb_, &na2_, &smem_);
+  const bool use_f2 = use_p2 || tcbf_layout(p, 2, &wb_, &na2_, &smem_);
+  const int km2 = use_p2 ? 128 : tcbf_km(p, 2);
   for (int a = 0; a < p->n2; ++a) {
     const Rate2& A = p->rates2[a];
     if (A.s == 0) continue;
@@ -1548,7 +1576,14 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   }
   auto by_cost = [](const It& x, const It& y) { return x.cost > y.cost; };
   std::stable_sort(fast1.begin(), fast1.end(), by_cost);
-  std::stable_sort(fast2.begin(), fast2.end(), by_cost);
+  // two-atom items with K1 <= 96 first (the spin-pair form runs them with a 96-row Y^T tile)
+  std::stable_sort(fast2.begin(), fast2.end(), [](const It& x, const It& y) {
+    const bool sx = x.K1 <= 96, sy = y.K1 <= 96;
+    if (sx != sy) return sx;
+    return x.cost > y.cost;
+  });
+  p->tcbf_n2a = 0;
+  for (auto& i : fast2) p->tcbf_n2a += i.K1 <= 96 ? 1 : 0;
   p->tcbf_items.clear();
   for (auto* v : {&fast1, &fast2})
     for (auto& i : *v) {
@@ -1704,7 +1739,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     if (count <= 0) continue;
     int wbp = 0, na2p = 0;
     size_t smemp = 0;
-    if (NT == 16 && three && p->d_wpair[0] && tcbp_layout(p, nat, &wbp, &na2p, &smemp)) {
+    if (NT == 16 && three && p->d_wpair[0] && tcbp_layout(p, nat, nat == 1 ? 64 : 128, &wbp, &na2p, &smemp)) {
       // the FP32-grade split in the spin-pair form (with one BF16 pass the channel-row form's
       // 128-wide products are faster)
       TpMaps pm;
@@ -1729,31 +1764,44 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
         }
       }
       TpArgs pa;
-      pa.items = reinterpret_cast<const int4*>(p->d_tcbf_items) + first;
-      pa.n_base = count;
-      pa.n_items = count * B;
       pa.n_chunks = (p->n_pr + 31) / 32;
       pa.g1_rows = g1_rows;
-      pa.wbufs = wbp;
-      pa.a2bufs = na2p;
       pa.pr_phi0 = p->pr_phi0;
       pa.spin_rows = p->n_fr * p->n1;
       pa.chan_phi0 = 2 * p->n_fr * p->n1;
       pa.wt_row0 = p->d_wtb_row0;
       pa.gy = gy;
       pa.err = p->d_err;
-      const int grid = std::min(pa.n_items, n_sm);
-#define JTFS_LAUNCH_TCBP(PLV, NATV)                                                             \
+#define JTFS_LAUNCH_TCBP(PLV, NATV, KMV)                                                        \
   do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_pair<PLV, NATV>,                      \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_pair<PLV, NATV, KMV>,                 \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smemp), "attr tcbp")) != JTFS_OK)            \
       return rc;                                                                                \
-    k_joint_bwd_pair<PLV, NATV><<<grid, kFThreads, smemp, st>>>(pm, pa, d);                     \
+    k_joint_bwd_pair<PLV, NATV, KMV><<<grid, kFThreads, smemp, st>>>(pm, pa, d);                \
   } while (0)
-      if (nat == 1) JTFS_LAUNCH_TCBP(2, 1); else JTFS_LAUNCH_TCBP(2, 2);
+      // one atom; two atoms with K1 <= 96 (a 96-row Y^T tile); two atoms with K1 <= 128
+      for (int part = 0; part < (nat == 1 ? 1 : 2); ++part) {
+        const int f0 = first + (part == 1 ? p->tcbf_n2a : 0);
+        const int cnt = nat == 1 ? count : (part == 0 ? p->tcbf_n2a : count - p->tcbf_n2a);
+        if (cnt <= 0) continue;
+        const int KMp = nat == 1 ? 64 : (part == 0 ? 96 : 128);
+        if (!tcbp_layout(p, nat, KMp, &wbp, &na2p, &smemp)) {
+          set_error("tensor-core backward: no shared-memory layout for the spin-pair form");
+          return JTFS_ERR_UNSUPPORTED;
+        }
+        pa.items = reinterpret_cast<const int4*>(p->d_tcbf_items) + f0;
+        pa.n_base = cnt;
+        pa.n_items = cnt * B;
+        pa.wbufs = wbp;
+        pa.a2bufs = na2p;
+        const int grid = std::min(pa.n_items, n_sm);
+        if (nat == 1) JTFS_LAUNCH_TCBP(2, 1, 64);
+        else if (KMp == 96) JTFS_LAUNCH_TCBP(2, 2, 96);
+        else JTFS_LAUNCH_TCBP(2, 2, 128);
+        if ((rc = cuda_check(cudaGetLastError(), "k_joint_bwd_pair")) != JTFS_OK) return rc;
+      }
 #undef JTFS_LAUNCH_TCBP
-      if ((rc = cuda_check(cudaGetLastError(), "k_joint_bwd_pair")) != JTFS_OK) return rc;
       continue;
     }
     const int PLf = three ? 2 : 1, RCf = nat == 1 ? 64 : 32;
