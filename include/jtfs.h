@@ -112,8 +112,19 @@ jtfs_status jtfs_backward(const jtfs_plan* plan, const float* x, const float* u1
                           int64_t B, const float* g_s0, const float* g_s1, const float* g_s2,
                           float* g_x, void* ws, size_t ws_bytes, void* stream);
 
+/* Forward and backward in one call (Sec. 2 and Sec. 5): s0, s1, s2 as jtfs_forward and
+ * g_x as jtfs_backward, for x and the cotangents on the device.  Between the two halves the
+ * workspace keeps x-hat, the first-order spectra and the BF16 second-order planes, which the
+ * separate calls recompute from the checkpoint; the results match jtfs_forward followed by
+ * jtfs_backward up to rounding order.  u1_ckpt (device, may be NULL) receives the checkpoint.
+ * ws as for with_grad = 1.  Errors as jtfs_forward / jtfs_backward. */
+jtfs_status jtfs_forward_backward(const jtfs_plan* plan, const float* x, int64_t B,
+                                  const float* g_s0, const float* g_s1, const float* g_s2,
+                                  float* s0, float* s1, float* s2, float* u1_ckpt, float* g_x,
+                                  void* ws, size_t ws_bytes, void* stream);
+
 /* End-to-end forward + backward from HOST buffers: copies x (host, [B, N]) and the
- * cotangents (host; NULL = zero) to the device, runs jtfs_forward and jtfs_backward, and
+ * cotangents (host; NULL = zero) to the device, runs jtfs_forward_backward, and
  * copies s0, s1, s2 (host, may be NULL) and g_x (host) back.  dev_buf must hold
  * jtfs_host_step_bytes(plan, B) bytes of device memory; ws as for with_grad = 1.
  * Synchronous on return. */

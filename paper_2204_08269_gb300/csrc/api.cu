@@ -491,6 +491,27 @@ jtfs_status jtfs_backward(const jtfs_plan* p, const float* x, const float* u1_ck
   return launch_backward(p, x, u1_ckpt, (int)B, g_s0, g_s1, g_s2, g_x, w, (cudaStream_t)stream);
 }
 
+jtfs_status jtfs_forward_backward(const jtfs_plan* p, const float* x, int64_t B,
+                                  const float* g_s0, const float* g_s1, const float* g_s2,
+                                  float* s0, float* s1, float* s2, float* u1_ckpt, float* g_x,
+                                  void* ws, size_t ws_bytes, void* stream) {
+  if (!p || B < 0 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
+  if (B == 0) return JTFS_OK;
+  if (!x || !s0 || !s1 || !s2 || !g_x) { set_error("NULL input or output"); return JTFS_ERR_INVALID_ARG; }
+  jtfs_status st = check_device(p);
+  if (st != JTFS_OK) return st;
+  const size_t need = workspace_layout(p, B, true, nullptr, nullptr);
+  if (!ws || ws_bytes < need) {
+    set_error("workspace needs " + std::to_string(need) + " bytes");
+    return JTFS_ERR_WORKSPACE;
+  }
+  Workspace w;
+  workspace_layout(p, B, true, (char*)ws, &w);
+  float* u1 = u1_ckpt ? u1_ckpt : w.u1;
+  if ((st = launch_forward(p, x, (int)B, s0, s1, s2, u1, w, (cudaStream_t)stream)) != JTFS_OK) return st;
+  return launch_backward(p, x, u1, (int)B, g_s0, g_s1, g_s2, g_x, w, (cudaStream_t)stream, true);
+}
+
 jtfs_status jtfs_plan_autotune(jtfs_plan* p, int64_t B, void* ws, size_t ws_bytes, void* stream,
                                int32_t* choice) {
   if (!p || B < 1 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
@@ -560,9 +581,9 @@ jtfs_status jtfs_forward_backward_host(const jtfs_plan* p, const float* x_host, 
   if (g_s0_host && (rc = cuda_check(cudaMemcpyAsync(dg0, g_s0_host, b0, cudaMemcpyHostToDevice, st), "H2D g_s0")) != JTFS_OK) return rc;
   if (g_s1_host && (rc = cuda_check(cudaMemcpyAsync(dg1, g_s1_host, b1, cudaMemcpyHostToDevice, st), "H2D g_s1")) != JTFS_OK) return rc;
   if (g_s2_host && (rc = cuda_check(cudaMemcpyAsync(dg2, g_s2_host, b2, cudaMemcpyHostToDevice, st), "H2D g_s2")) != JTFS_OK) return rc;
-  if ((rc = jtfs_forward(p, dx, B, ds0, ds1, ds2, du1, ws, ws_bytes, stream)) != JTFS_OK) return rc;
-  if ((rc = jtfs_backward(p, dx, du1, B, g_s0_host ? dg0 : nullptr, g_s1_host ? dg1 : nullptr,
-                          g_s2_host ? dg2 : nullptr, dgx, ws, ws_bytes, stream)) != JTFS_OK)
+  if ((rc = jtfs_forward_backward(p, dx, B, g_s0_host ? dg0 : nullptr, g_s1_host ? dg1 : nullptr,
+                                   g_s2_host ? dg2 : nullptr, ds0, ds1, ds2, du1, dgx, ws,
+                                   ws_bytes, stream)) != JTFS_OK)
     return rc;
   if (s0_host && (rc = cuda_check(cudaMemcpyAsync(s0_host, ds0, b0, cudaMemcpyDeviceToHost, st), "D2H s0")) != JTFS_OK) return rc;
   if (s1_host && (rc = cuda_check(cudaMemcpyAsync(s1_host, ds1, b1, cudaMemcpyDeviceToHost, st), "D2H s1")) != JTFS_OK) return rc;

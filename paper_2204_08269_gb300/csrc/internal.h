@@ -200,6 +200,8 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
                            float* s2, float* u1, const Workspace& w, cudaStream_t st);
 jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1, int B,
                             const float* gs0, const float* gs1, const float* gs2, float* gx,
-                            const Workspace& w, cudaStream_t st);
+                            const Workspace& w, cudaStream_t st, bool fused = false);
+// true when a fused step can hand the forward's BF16 Y planes to the backward
+bool backward_reuses_forward(const jtfs_plan* p);
 
 }  // namespace jtfs

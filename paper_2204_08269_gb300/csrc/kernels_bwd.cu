@@ -339,25 +339,35 @@ size_t joint_bwd_smem(const jtfs_plan* p) {
          (size_t)p->n_t * kNC * 4;
 }
 
+bool backward_reuses_forward(const jtfs_plan* p) {
+  // the forward's BF16 Y planes are the backward's operands (not for TF32, whose forward
+  // writes FP32 planes)
+  return p->use_tc && p->use_tcb && p->cfg.precision != JTFS_PREC_TF32;
+}
+
 jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1, int B,
                             const float* gs0, const float* gs1, const float* gs2, float* gx,
-                            const Workspace& w, cudaStream_t st) {
+                            const Workspace& w, cudaStream_t st, bool fused) {
   jtfs_status rc = set_attrs();
   if (rc != JTFS_OK) return rc;
   const DevPlan& d = p->dp;
-  // recompute x-hat, U1-hat and Y from x and the checkpoint
-  {
-    StageScope sc(p, kStXfft, st, 2);
-    k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, w.xsub);
-    k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.xsub, w.xh);
-  }
-  {
-    StageScope sc(p, kStUhFromU1, st, 1);
-    k_uh_from_u1<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 17 / 2, st>>>(d, u1, w.uh);
+  // fused: x-hat, U1-hat (and the BF16 Y planes) are still in the workspace from the forward
+  // of the same call; otherwise recompute them from x and the checkpoint
+  const bool reuse_y = fused && backward_reuses_forward(p);
+  if (!fused) {
+    {
+      StageScope sc(p, kStXfft, st, 2);
+      k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, w.xsub);
+      k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.xsub, w.xh);
+    }
+    {
+      StageScope sc(p, kStUhFromU1, st, 1);
+      k_uh_from_u1<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 17 / 2, st>>>(d, u1, w.uh);
+    }
   }
   const size_t n_items = p->items.size() / 2;
   if (gs2 && n_items > 0 && p->use_tcb) {
-    {
+    if (!reuse_y) {
       StageScope sc(p, kStSecondOrder, st, 1);
       k_second_order_rows<1><<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
                               (size_t)p->rows_cap * 17 / 2, st>>>(

@@ -57,6 +57,8 @@ def lib():
         "jtfs_workspace_bytes": ([_P, _I64, _I32, ctypes.POINTER(_SZ)], _I32),
         "jtfs_forward": ([_P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P], _I32),
         "jtfs_backward": ([_P, _P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P], _I32),
+        "jtfs_forward_backward": ([_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P],
+                                  _I32),
         "jtfs_host_step_bytes": ([_P, _I64, ctypes.POINTER(_SZ)], _I32),
         "jtfs_forward_backward_host": ([_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P,
                                         _SZ, _P], _I32),
@@ -89,7 +91,8 @@ def lib():
 def exported_symbols():
     """Names the binding expects the library to export (one per declaration in jtfs.h)."""
     return ["jtfs_plan_create", "jtfs_plan_destroy", "jtfs_plan_shapes", "jtfs_plan_schedule",
-            "jtfs_workspace_bytes", "jtfs_forward", "jtfs_backward", "jtfs_host_step_bytes",
+            "jtfs_workspace_bytes", "jtfs_forward", "jtfs_backward", "jtfs_forward_backward",
+            "jtfs_host_step_bytes",
             "jtfs_forward_backward_host", "jtfs_sync_status", "jtfs_status_string",
             "jtfs_last_error", "jtfs_profile_enable", "jtfs_profile_read",
             "jtfs_profile_stage_name", "jtfs_first_order_static", "jtfs_plan_autotune",
@@ -229,6 +232,25 @@ class JTFSPlan:
             self._h, _ptr(x), _ptr(u1), B, _ptr(gs[0]), _ptr(gs[1]), _ptr(gs[2]), _ptr(gx),
             _ptr(ws), ws.numel(), _stream()))
         return gx
+
+    def forward_backward(self, x, g_s0=None, g_s1=None, g_s2=None, keep_checkpoint=False):
+        """(S0, S1, S2, g_x[, U1 checkpoint]) in one call on device tensors; the backward half
+        reuses the forward's intermediate spectra instead of recomputing them."""
+        self._check_x(x)
+        B = x.shape[0]
+        sh = self.shapes
+        dev = x.device
+        s0 = torch.empty(sh.s0(B), dtype=torch.float32, device=dev)
+        s1 = torch.empty(sh.s1(B), dtype=torch.float32, device=dev)
+        s2 = torch.empty(sh.s2(B), dtype=torch.float32, device=dev)
+        gx = torch.empty_like(x)
+        u1 = torch.empty((B, sh.u1_len), dtype=torch.float32, device=dev) if keep_checkpoint else None
+        ws = self.workspace(B, True)
+        gs = [None if g is None else g.contiguous() for g in (g_s0, g_s1, g_s2)]
+        _check("jtfs_forward_backward", lib().jtfs_forward_backward(
+            self._h, _ptr(x), B, _ptr(gs[0]), _ptr(gs[1]), _ptr(gs[2]), _ptr(s0), _ptr(s1),
+            _ptr(s2), _ptr(u1), _ptr(gx), _ptr(ws), ws.numel(), _stream()))
+        return (s0, s1, s2, gx, u1) if keep_checkpoint else (s0, s1, s2, gx)
 
     def forward_backward_host(self, x_host, g_s0=None, g_s1=None, g_s2=None, outputs=True):
         """End-to-end step from pinned (or pageable) host tensors: H2D, forward, backward,

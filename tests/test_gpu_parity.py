@@ -269,3 +269,31 @@ def test_autograd_function_and_host_step():
     o0, o1, o2, gxh = m.plan.forward_backward_host(torch.from_numpy(xh), *gh)
     assert torch.allclose(o2, s2.detach().cpu(), rtol=0, atol=1e-6 * float(s2.abs().max()))
     assert torch.allclose(gxh, ref.cpu(), rtol=0, atol=1e-6 * float(ref.abs().max()))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("ci", [0, 5])
+def test_fused_step_matches_separate_calls(ci, prec):
+    """jtfs_forward_backward keeps the forward's spectra for the backward half: its outputs
+    equal jtfs_forward followed by jtfs_backward (the same arithmetic, up to the rounding
+    order of the first-order spectra), and its gradient matches the oracle's."""
+    cfg = SMALL_CFGS[ci]
+    plan = _plans(cfg, prec)
+    sh = plan.shapes
+    x = torch.from_numpy(SS.white_noise_batch(3, cfg["N"], 77 + ci)).cuda()
+    gen = torch.Generator(device="cuda").manual_seed(5 + ci)
+    g = [torch.randn(f(3), device="cuda", generator=gen) for f in (sh.s0, sh.s1, sh.s2)]
+    s0, s1, s2, u1 = plan.forward(x)
+    gx = plan.backward(x, u1, *g)
+    f0, f1, f2, fgx, fu1 = plan.forward_backward(x, *g, keep_checkpoint=True)
+    torch.cuda.synchronize()
+    for a, b in ((s0, f0), (s1, f1), (s2, f2), (u1, fu1)):
+        assert torch.equal(a, b)
+    assert (fgx - gx).norm().item() <= 1e-6 * gx.norm().item()
+    op, sc = _oracle(cfg)
+    xs = x.double().cpu().numpy()
+    gs = [t.double().cpu().numpy() for t in g]
+    got = fgx.double().cpu().numpy()
+    for b in range(3):
+        ref = O.backward_one(xs[b], gs[0][b], gs[1][b], gs[2][b], op, sc)
+        assert _rel(got[b], ref) <= GTOL[prec]
