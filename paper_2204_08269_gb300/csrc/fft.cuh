@@ -37,8 +37,31 @@ namespace jtfs {
 // of the first passes free of bank conflicts.  A pass fuses RB consecutive radix-2 DIT
 // stages s0 .. s0 + RB - 1 in registers: each thread loads 2^RB elements at stride
 // q = 2^(s0-1), applies the stages with the twiddles of the L-point table tw
-// (exp(-2 pi i m / L), m < L / 2) and stores them back.
+// (exp(-2 pi i m / L), m < L / 2; one entry per stage, the others by fixed unit roots) and
+// stores them back.
 __device__ __forceinline__ int fft_pad(int i) { return i + (i >> 4); }
+
+// exp(-i pi m / 2^u) for u = 1..3 and 0 < m < 2^u (conjugated for SIGN = +1): within a
+// pass, the twiddles of stage u are the table entry of the group times these roots.
+template <int SIGN>
+__device__ __forceinline__ float2 unit_root(int u, int m) {
+  constexpr float c1 = 0.92387953251128674f, s1 = 0.38268343236508978f;   // cos, sin(pi/8)
+  constexpr float h = 0.70710678118654752f;                               // cos(pi/4)
+  float2 r = make_float2(1.f, 0.f);
+  const int e = m << (3 - u);                 // angle -pi e / 8, e = 1..7
+  switch (e) {
+    case 1: r = make_float2(c1, -s1); break;
+    case 2: r = make_float2(h, -h); break;
+    case 3: r = make_float2(s1, -c1); break;
+    case 4: r = make_float2(0.f, -1.f); break;
+    case 5: r = make_float2(-s1, -c1); break;
+    case 6: r = make_float2(-h, -h); break;
+    case 7: r = make_float2(-c1, -s1); break;
+    default: break;
+  }
+  if (SIGN > 0) r.y = -r.y;
+  return r;
+}
 
 template <int SIGN, int RB>
 __device__ __forceinline__ void fft_dit_pass(float2* buf, int logL, int G,
@@ -57,9 +80,11 @@ __device__ __forceinline__ void fft_dit_pass(float2* buf, int logL, int G,
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
       const int sh = logL - s0 - u;
+      // w[ml] = tw[(j + q ml) << sh] = tw[j << sh] exp(-i pi ml / 2^u)
       float2 w[1 << (RB - 1)];
+      w[0] = twiddle<SIGN>(tw, j << sh);
 #pragma unroll
-      for (int ml = 0; ml < (1 << u); ++ml) w[ml] = twiddle<SIGN>(tw, (j + q * ml) << sh);
+      for (int ml = 1; ml < (1 << u); ++ml) w[ml] = cmul(w[0], unit_root<SIGN>(u, ml));
 #pragma unroll
       for (int m = 0; m < R; ++m) {
         if (m & (1 << u)) continue;
