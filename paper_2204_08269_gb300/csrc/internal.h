@@ -131,6 +131,7 @@ struct jtfs_plan {
   std::vector<int> tcbf_items; // (alpha, n0, lam_min & ~7, K1): the fast backward form, the
   int tcbf_n1;                 // tcbf_n1 items with K1 <= 64 first
   int tcbf_n2a = 0;            // of the two-atom items, those with K1 <= 96 (first)
+  int tcbf_n3 = 0;             // three-atom items (K1 <= 160, spin-pair form), last
   int* d_tcbf_items;
   int* d_tcb_items;
   void* d_wtb;                 // [rows][NT] bf16 pooling weights (time-major)

@@ -1081,12 +1081,13 @@ struct TpArgs {
   int* err;
 };
 
-template <int PL, int NAT, int KMV>
+template <int PL, int NAT, int KMV, int RCV>
 __global__ void __launch_bounds__(kFThreads, 1)
 k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int NT = 16, RC = 32, KM = KMV, CW = RC / 4;
+  constexpr int NT = 16, RC = RCV, KM = KMV, CW = RC / 4;
+  constexpr int D1C = 6 * RC;                             // first-product columns per buffer
   constexpr int NB1 = NAT == 1 ? 2 : 1;                   // first-product TMEM buffers
   constexpr bool TA = NAT >= 2;                           // S / T staged in TMEM (A operand)
   constexpr uint32_t kA1Plane = 2 * KM * 128;             // two 64-sample halves x 64 lambda'
@@ -1094,7 +1095,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
   constexpr uint32_t kWBlk = RC * 128;                    // 32 rows x 64 lambda'
   constexpr uint32_t kG1Blk = RC * NT * 2;                // 32 rows x 16 t
   constexpr uint32_t kWBuf = PL * NAT * 2 * kWBlk + PL * 2 * kG1Blk;   // [Wr a][Wi a] per atom a
-  constexpr uint32_t kA2Part = 128 * RC * 2;              // [128 n][32 r] bf16, 64-byte swizzle
+  constexpr uint32_t kA2Part = 128 * RC * 2;              // [128 n][RC r] bf16, 64-byte swizzle
   constexpr uint32_t kA2Buf = 4 * kA2Part;                // S_re, S_im, T_re, T_im
   const int WB = args.wbufs, NA2 = args.a2bufs;
   uint8_t* sA1 = sm;                                       // PL x 2 parts
@@ -1134,10 +1135,11 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tmem_base;
-  // TMEM: NB1 buffers of 192 columns, each [P1 | P4] [P3 | P2] [g_up | g_dn] (64 apiece), then
-  // gY^T_re and gY^T_im (64 NAT columns each), then (TA) S_re, S_im, T_re, T_im as the last
-  // product's A operand: 32 pair rows of BF16 = 16 columns apiece
-  const uint32_t t_re = tbase + NB1 * 192, t_im = t_re + 64 * NAT;
+  // TMEM: NB1 buffers of 6 RC columns, each [P1 | P4] [P3 | P2] [g_up | g_dn] (2 RC apiece),
+  // then gY^T_re and gY^T_im (64 NAT columns each), then (TA) S_re, S_im, T_re, T_im as the
+  // last product's A operand: RC pair rows of BF16 = RC / 2 columns apiece
+  static_assert(NB1 * D1C + 128 * NAT + (TA ? 2 * RC : 0) <= 512, "TMEM columns");
+  const uint32_t t_re = tbase + NB1 * D1C, t_im = t_re + 64 * NAT;
   const uint32_t t_a2 = t_im + 64 * NAT;
   auto fail = [&](int code) {
     if (!abort_flag) {
@@ -1223,7 +1225,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
           d1f_ph ^= 1u << buf;
           tc_fence_after();
           const uint32_t wb = smem_u32(sW + wst * kWBuf);
-          const uint32_t t_a = tbase + buf * 192, t_b = t_a + 64, t_g = t_a + 128;
+          const uint32_t t_a = tbase + buf * D1C, t_b = t_a + 2 * RC, t_g = t_a + 4 * RC;
           for (int ks = 0; ks < nks1; ++ks) {
             for (int q = 0; q < npair; ++q) {
               const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
@@ -1285,9 +1287,9 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
               if (TA) {
                 const uint32_t ta = t_a2 + ks * 8;
                 mma_f16_ta(t_re, ta, wr, id2, f);
-                mma_f16_ta(t_re, ta + 32, wi, id2, 1u);
-                mma_f16_ta(t_im, ta + 16, wr, id2, f);
-                mma_f16_ta(t_im, ta + 48, wi, id2, 1u);
+                mma_f16_ta(t_re, ta + RC, wi, id2, 1u);
+                mma_f16_ta(t_im, ta + RC / 2, wr, id2, f);
+                mma_f16_ta(t_im, ta + 3 * RC / 2, wi, id2, 1u);
               } else {
                 mma_f16(t_re, sre, wr, id2, f);
                 mma_f16(t_re, tre, wi, id2, 1u);
@@ -1326,13 +1328,22 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
         d1_ph ^= 1u << buf;
         tc_fence_after();
         uint32_t p1[CW], p4[CW], p3[CW], p2[CW], gu[CW], gd[CW];
-        const uint32_t t = tbase + buf * 192 + lane_off + cg * CW;
-        tmem_ld8u(t, p1);
-        tmem_ld8u(t + 32, p4);
-        tmem_ld8u(t + 64, p3);
-        tmem_ld8u(t + 96, p2);
-        tmem_ld8u(t + 128, gu);
-        tmem_ld8u(t + 160, gd);
+        const uint32_t t = tbase + buf * D1C + lane_off + cg * CW;
+        if constexpr (CW == 8) {
+          tmem_ld8u(t, p1);
+          tmem_ld8u(t + RC, p4);
+          tmem_ld8u(t + 2 * RC, p3);
+          tmem_ld8u(t + 3 * RC, p2);
+          tmem_ld8u(t + 4 * RC, gu);
+          tmem_ld8u(t + 5 * RC, gd);
+        } else {
+          tmem_ld4u(t, p1);
+          tmem_ld4u(t + RC, p4);
+          tmem_ld4u(t + 2 * RC, p3);
+          tmem_ld4u(t + 3 * RC, p2);
+          tmem_ld4u(t + 4 * RC, gu);
+          tmem_ld4u(t + 5 * RC, gd);
+        }
         tmem_wait_ld();
         tc_fence_before();
         __syncwarp();
@@ -1369,16 +1380,23 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
         if (!mbar_wait(&a2_free[q2], ((a2f_ph >> q2) & 1) ^ 1, kWaitNs)) { fail(90); ok = false; break; }
         a2f_ph ^= 1u << q2;
         if (TA) {
-          // this warp's 8 pair rows are columns [4 cg, 4 cg + 4) of each part
-          const uint32_t ta = t_a2 + lane_off + cg * 4;
+          // this warp's CW pair rows are columns [cg CW / 2, +CW / 2) of each part
+          const uint32_t ta = t_a2 + lane_off + cg * (CW / 2);
           tc_fence_after();
-          tmem_st4(ta, sre[0], sre[1], sre[2], sre[3]);
-          tmem_st4(ta + 16, sim[0], sim[1], sim[2], sim[3]);
-          tmem_st4(ta + 32, tre[0], tre[1], tre[2], tre[3]);
-          tmem_st4(ta + 48, tim[0], tim[1], tim[2], tim[3]);
+          if constexpr (CW == 8) {
+            tmem_st4(ta, sre[0], sre[1], sre[2], sre[3]);
+            tmem_st4(ta + RC / 2, sim[0], sim[1], sim[2], sim[3]);
+            tmem_st4(ta + RC, tre[0], tre[1], tre[2], tre[3]);
+            tmem_st4(ta + 3 * RC / 2, tim[0], tim[1], tim[2], tim[3]);
+          } else {
+            tmem_st2(ta, sre[0], sre[1]);
+            tmem_st2(ta + RC / 2, sim[0], sim[1]);
+            tmem_st2(ta + RC, tre[0], tre[1]);
+            tmem_st2(ta + 3 * RC / 2, tim[0], tim[1]);
+          }
           tmem_wait_st();
           tc_fence_before();
-        } else {
+        } else if constexpr (CW == 8) {
           uint8_t* base = sA2 + q2 * kA2Buf + row * (RC * 2);
           const int pos = (cg ^ ((row >> 1) & 3)) * 16;
           *reinterpret_cast<uint4*>(base + 0 * kA2Part + pos) = make_uint4(sre[0], sre[1], sre[2], sre[3]);
@@ -1504,12 +1522,14 @@ static bool tcbf_layout(const jtfs_plan* p, int nat, int* wb_out, int* na2_out, 
 
 // Shared memory of the spin-pair form: resident Y^T and weight tiles, the W ring (2..4 chunks
 // of 32 pair rows) and the S / T staging (1..2 buffers), deepest first.
+static int tcbp_rc(int nat) { return nat >= 3 ? 16 : 32; }
+
 static bool tcbp_layout(const jtfs_plan* p, int nat, int KM, int* wb_out, int* na2_out,
                         size_t* smem_out) {
-  const int PL = p->split ? 2 : 1;
+  const int PL = p->split ? 2 : 1, RC = tcbp_rc(nat);
   const size_t fixed = 1024 + (size_t)PL * 2 * (2 * KM * 128) + (size_t)PL * 128 * 16 * 2;
-  const size_t wbuf = (size_t)PL * nat * 2 * 32 * 128 + (size_t)PL * 2 * 32 * 16 * 2;
-  const size_t a2buf = nat >= 2 ? 0 : (size_t)4 * 128 * 32 * 2;   // two atoms: S / T in TMEM
+  const size_t wbuf = (size_t)PL * nat * 2 * RC * 128 + (size_t)PL * 2 * RC * 16 * 2;
+  const size_t a2buf = nat >= 2 ? 0 : (size_t)4 * 128 * RC * 2;   // two atoms and more: S / T in TMEM
   const size_t budget = 225 * 1024;
   int wb = 4, na2 = nat >= 2 ? 1 : 2;
   while (fixed + wb * wbuf + na2 * a2buf > budget && (wb > 2 || na2 > 1)) {
@@ -1551,13 +1571,14 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
     rows += (L + 127) / 128 * 128;
   }
   struct It { int a, n0, start, K1; long long cost; };
-  std::vector<It> its, fast1, fast2;
+  std::vector<It> its, fast1, fast2, fast3;
   int wb_, na2_;
   size_t smem_;
   // the FP32-grade split runs the spin-pair form (one atom: K1 <= 64; two atoms: K1 <= 128)
   const bool pair = p->split && NT == 16 && p->d_wpair[0] != nullptr;
   const bool use_p1 = pair && tcbp_layout(p, 1, 64, &wb_, &na2_, &smem_);
   const bool use_p2 = pair && tcbp_layout(p, 2, 128, &wb_, &na2_, &smem_);
+  const bool use_p3 = pair && tcbp_layout(p, 3, 160, &wb_, &na2_, &smem_);
   const bool use_f1 = use_p1 || tcbf_layout(p, 1, &wb_, &na2_, &smem_);
   const bool use_f2 = use_p2 || tcbf_layout(p, 2, &wb_, &na2_, &smem_);
   const int km2 = use_p2 ? 128 : tcbf_km(p, 2);
@@ -1571,6 +1592,7 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
     for (int n0 = 0; n0 < A.L; n0 += 128) {
       if (K1f <= 64 && use_f1) fast1.push_back({a, n0, lm8, K1f, (long long)K1f});
       else if (K1f <= km2 && use_f2) fast2.push_back({a, n0, lm8, K1f, (long long)K1f});
+      else if (K1f <= 160 && use_p3) fast3.push_back({a, n0, lm8, K1f, (long long)K1f});
       else its.push_back({a, n0, start, K1, (long long)K1});
     }
   }
@@ -1584,12 +1606,14 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   });
   p->tcbf_n2a = 0;
   for (auto& i : fast2) p->tcbf_n2a += i.K1 <= 96 ? 1 : 0;
+  std::stable_sort(fast3.begin(), fast3.end(), by_cost);
   p->tcbf_items.clear();
-  for (auto* v : {&fast1, &fast2})
+  for (auto* v : {&fast1, &fast2, &fast3})
     for (auto& i : *v) {
       p->tcbf_items.push_back(i.a); p->tcbf_items.push_back(i.n0); p->tcbf_items.push_back(i.start); p->tcbf_items.push_back(i.K1);
     }
   p->tcbf_n1 = (int)fast1.size();
+  p->tcbf_n3 = (int)fast3.size();
   // items whose Y^T tile fits the resident three-pass form (K1 <= 96) first, longest first
   std::stable_sort(its.begin(), its.end(), [](const It& x, const It& y) {
     const bool rx = x.K1 <= 96, ry = y.K1 <= 96;
@@ -1733,20 +1757,24 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   }
   // fast form: the K1 <= 64 items (one lambda' atom, 64-row chunks), then the K1 <= KM items
   // (two atoms, 32-row chunks)
-  for (int nat = 1; nat <= 2; ++nat) {
-    const int first = nat == 1 ? 0 : p->tcbf_n1;
-    const int count = nat == 1 ? p->tcbf_n1 : (int)(p->tcbf_items.size() / 4) - p->tcbf_n1;
+  const int n_fast = (int)(p->tcbf_items.size() / 4);
+  for (int nat = 1; nat <= 3; ++nat) {
+    const int first = nat == 1 ? 0 : (nat == 2 ? p->tcbf_n1 : n_fast - p->tcbf_n3);
+    const int count = nat == 1 ? p->tcbf_n1
+                               : (nat == 2 ? n_fast - p->tcbf_n1 - p->tcbf_n3 : p->tcbf_n3);
     if (count <= 0) continue;
     int wbp = 0, na2p = 0;
     size_t smemp = 0;
-    if (NT == 16 && three && p->d_wpair[0] && tcbp_layout(p, nat, nat == 1 ? 64 : 128, &wbp, &na2p, &smemp)) {
+    if (NT == 16 && three && p->d_wpair[0] &&
+        tcbp_layout(p, nat, nat == 1 ? 64 : (nat == 2 ? 128 : 160), &wbp, &na2p, &smemp)) {
+      const int RCp = tcbp_rc(nat);
       // the FP32-grade split in the spin-pair form (with one BF16 pass the channel-row form's
       // 128-wide products are faster)
       TpMaps pm;
       for (int pl = 0; pl < 4; ++pl) {
         cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)p->n_pr};
         cuuint64_t str[1] = {(cuuint64_t)p->n1_pad * 2};
-        cuuint32_t box[2] = {64, 32};
+        cuuint32_t box[2] = {64, (cuuint32_t)RCp};
         if (!make_tmap(&pm.w[pl], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p->d_wpair[pl], dims, str, box, 128, &err)) {
           set_error(err);
           return JTFS_ERR_CUDA;
@@ -1757,14 +1785,14 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
         pm.wt[h] = mwt[h];
         cuuint64_t dims[2] = {(cuuint64_t)NT, (cuuint64_t)B * p->n2 * g1_rows};
         cuuint64_t str[1] = {(cuuint64_t)NT * 2};
-        cuuint32_t box[2] = {(cuuint32_t)NT, 32};
+        cuuint32_t box[2] = {(cuuint32_t)NT, (cuuint32_t)RCp};
         if (!make_tmap(&pm.g1[h], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, h ? g1lo : g1hi, dims, str, box, NT * 2, &err)) {
           set_error(err);
           return JTFS_ERR_CUDA;
         }
       }
       TpArgs pa;
-      pa.n_chunks = (p->n_pr + 31) / 32;
+      pa.n_chunks = (p->n_pr + RCp - 1) / RCp;
       pa.g1_rows = g1_rows;
       pa.pr_phi0 = p->pr_phi0;
       pa.spin_rows = p->n_fr * p->n1;
@@ -1772,20 +1800,21 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       pa.wt_row0 = p->d_wtb_row0;
       pa.gy = gy;
       pa.err = p->d_err;
-#define JTFS_LAUNCH_TCBP(PLV, NATV, KMV)                                                        \
+#define JTFS_LAUNCH_TCBP(PLV, NATV, KMV, RCV)                                                   \
   do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_pair<PLV, NATV, KMV>,                 \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_pair<PLV, NATV, KMV, RCV>,            \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smemp), "attr tcbp")) != JTFS_OK)            \
       return rc;                                                                                \
-    k_joint_bwd_pair<PLV, NATV, KMV><<<grid, kFThreads, smemp, st>>>(pm, pa, d);                \
+    k_joint_bwd_pair<PLV, NATV, KMV, RCV><<<grid, kFThreads, smemp, st>>>(pm, pa, d);           \
   } while (0)
-      // one atom; two atoms with K1 <= 96 (a 96-row Y^T tile); two atoms with K1 <= 128
-      for (int part = 0; part < (nat == 1 ? 1 : 2); ++part) {
+      // one atom; two atoms with K1 <= 96 (a 96-row Y^T tile); two atoms with K1 <= 128;
+      // three atoms (K1 <= 160, 16-row chunks)
+      for (int part = 0; part < (nat == 2 ? 2 : 1); ++part) {
         const int f0 = first + (part == 1 ? p->tcbf_n2a : 0);
-        const int cnt = nat == 1 ? count : (part == 0 ? p->tcbf_n2a : count - p->tcbf_n2a);
+        const int cnt = nat != 2 ? count : (part == 0 ? p->tcbf_n2a : count - p->tcbf_n2a);
         if (cnt <= 0) continue;
-        const int KMp = nat == 1 ? 64 : (part == 0 ? 96 : 128);
+        const int KMp = nat == 1 ? 64 : (nat == 3 ? 160 : (part == 0 ? 96 : 128));
         if (!tcbp_layout(p, nat, KMp, &wbp, &na2p, &smemp)) {
           set_error("tensor-core backward: no shared-memory layout for the spin-pair form");
           return JTFS_ERR_UNSUPPORTED;
@@ -1796,9 +1825,10 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
         pa.wbufs = wbp;
         pa.a2bufs = na2p;
         const int grid = std::min(pa.n_items, n_sm);
-        if (nat == 1) JTFS_LAUNCH_TCBP(2, 1, 64);
-        else if (KMp == 96) JTFS_LAUNCH_TCBP(2, 2, 96);
-        else JTFS_LAUNCH_TCBP(2, 2, 128);
+        if (nat == 1) JTFS_LAUNCH_TCBP(2, 1, 64, 32);
+        else if (nat == 3) JTFS_LAUNCH_TCBP(2, 3, 160, 16);
+        else if (KMp == 96) JTFS_LAUNCH_TCBP(2, 2, 96, 32);
+        else JTFS_LAUNCH_TCBP(2, 2, 128, 32);
         if ((rc = cuda_check(cudaGetLastError(), "k_joint_bwd_pair")) != JTFS_OK) return rc;
       }
 #undef JTFS_LAUNCH_TCBP

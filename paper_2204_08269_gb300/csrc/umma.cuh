@@ -138,6 +138,18 @@ __device__ __forceinline__ void tmem_ld8u(uint32_t taddr, uint32_t (&r)[8]) {
         "=r"(r[7])
       : "r"(taddr));
 }
+// 32 lanes x 32 bits, 4 consecutive columns per thread (raw words).
+__device__ __forceinline__ void tmem_ld4u(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+}
+// 32 lanes x 32 bits, 2 consecutive columns per thread (store).
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, uint32_t r0, uint32_t r1) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(r0),
+               "r"(r1)
+               : "memory");
+}
 // 32 lanes x 32 bits, 4 consecutive columns per thread (store).
 __device__ __forceinline__ void tmem_st4(uint32_t taddr, uint32_t r0, uint32_t r1, uint32_t r2,
                                          uint32_t r3) {
