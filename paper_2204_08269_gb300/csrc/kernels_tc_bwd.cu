@@ -1574,9 +1574,10 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   std::vector<It> its, fast1, fast2, fast3;
   int wb_, na2_;
   size_t smem_;
-  // the FP32-grade split runs the spin-pair form (one atom: K1 <= 64; two atoms: K1 <= 128)
-  const bool pair = p->split && NT == 16 && p->d_wpair[0] != nullptr;
-  const bool use_p1 = pair && tcbp_layout(p, 1, 64, &wb_, &na2_, &smem_);
+  // spin-pair form: one atom (K1 <= 64) for the FP32-grade split, two (K1 <= 128) and three
+  // (K1 <= 160) atoms for every BF16-plane precision
+  const bool pair = NT == 16 && p->d_wpair[0] != nullptr;
+  const bool use_p1 = pair && p->split && tcbp_layout(p, 1, 64, &wb_, &na2_, &smem_);
   const bool use_p2 = pair && tcbp_layout(p, 2, 128, &wb_, &na2_, &smem_);
   const bool use_p3 = pair && tcbp_layout(p, 3, 160, &wb_, &na2_, &smem_);
   const bool use_f1 = use_p1 || tcbf_layout(p, 1, &wb_, &na2_, &smem_);
@@ -1765,11 +1766,11 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     if (count <= 0) continue;
     int wbp = 0, na2p = 0;
     size_t smemp = 0;
-    if (NT == 16 && three && p->d_wpair[0] &&
+    if (NT == 16 && (three || nat >= 2) && p->d_wpair[0] &&
         tcbp_layout(p, nat, nat == 1 ? 64 : (nat == 2 ? 128 : 160), &wbp, &na2p, &smemp)) {
       const int RCp = tcbp_rc(nat);
-      // the FP32-grade split in the spin-pair form (with one BF16 pass the channel-row form's
-      // 128-wide products are faster)
+      // the spin-pair form: every atom count for the FP32-grade split, two and three atoms for
+      // one BF16 pass (whose one-atom items keep the channel-row form's 128-wide products)
       TpMaps pm;
       for (int pl = 0; pl < 4; ++pl) {
         cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)p->n_pr};
@@ -1825,10 +1826,16 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
         pa.wbufs = wbp;
         pa.a2bufs = na2p;
         const int grid = std::min(pa.n_items, n_sm);
-        if (nat == 1) JTFS_LAUNCH_TCBP(2, 1, 64, 32);
-        else if (nat == 3) JTFS_LAUNCH_TCBP(2, 3, 160, 16);
-        else if (KMp == 96) JTFS_LAUNCH_TCBP(2, 2, 96, 32);
-        else JTFS_LAUNCH_TCBP(2, 2, 128, 32);
+        if (three) {
+          if (nat == 1) JTFS_LAUNCH_TCBP(2, 1, 64, 32);
+          else if (nat == 3) JTFS_LAUNCH_TCBP(2, 3, 160, 16);
+          else if (KMp == 96) JTFS_LAUNCH_TCBP(2, 2, 96, 32);
+          else JTFS_LAUNCH_TCBP(2, 2, 128, 32);
+        } else {
+          if (nat == 3) JTFS_LAUNCH_TCBP(1, 3, 160, 16);
+          else if (KMp == 96) JTFS_LAUNCH_TCBP(1, 2, 96, 32);
+          else JTFS_LAUNCH_TCBP(1, 2, 128, 32);
+        }
         if ((rc = cuda_check(cudaGetLastError(), "k_joint_bwd_pair")) != JTFS_OK) return rc;
       }
 #undef JTFS_LAUNCH_TCBP
