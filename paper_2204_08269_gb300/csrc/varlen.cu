@@ -4,7 +4,7 @@
 // (a power of two, as the periodic transform needs, and long enough for the coarsest
 // first-order filter), transforming it with the plan of that length and keeping the first
 // ceil(len_i / T) frames of S0, S1 and S2.  Signals of the same N_i form one bucket, run in
-// sub-batches through jtfs_forward / jtfs_backward; small kernels gather the packed input and
+// sub-batches through jtfs_forward_backward; small kernels gather the packed input and
 // cotangents into the padded batch and scatter outputs and g_x back.  The whole step can be
 // captured into one CUDA graph and replayed.
 #include <algorithm>
@@ -145,8 +145,9 @@ jtfs_status vl_run(const jtfs_varlen* v, const float* x, const float* gs0, const
     k_vl_frames<0><<<grid_for(rows1), 256, 0, st>>>(gs1, g1b, ch.d_s1off, ch.d_frames, rows1, nt);
     k_vl_frames<0><<<grid_for(rows2), 256, 0, st>>>(gs2, g2b, ch.d_s2off, ch.d_frames, rows2, nt);
     if ((rc = cuda_check(cudaGetLastError(), "varlen gather")) != JTFS_OK) return rc;
-    if ((rc = jtfs_forward(ch.plan, xb, cnt, s0b, s1b, s2b, u1b, pws, pws_bytes, st)) != JTFS_OK) return rc;
-    if ((rc = jtfs_backward(ch.plan, xb, u1b, cnt, g0b, g1b, g2b, gxb, pws, pws_bytes, st)) != JTFS_OK) return rc;
+    if ((rc = jtfs_forward_backward(ch.plan, xb, cnt, g0b, g1b, g2b, s0b, s1b, s2b, u1b, gxb, pws,
+                                    pws_bytes, st)) != JTFS_OK)
+      return rc;
     k_vl_frames<1><<<grid_for(1), 256, 0, st>>>(s0b, s0, ch.d_s0off, ch.d_frames, 1, nt);
     k_vl_frames<1><<<grid_for(rows1), 256, 0, st>>>(s1b, s1, ch.d_s1off, ch.d_frames, rows1, nt);
     k_vl_frames<1><<<grid_for(rows2), 256, 0, st>>>(s2b, s2, ch.d_s2off, ch.d_frames, rows2, nt);
