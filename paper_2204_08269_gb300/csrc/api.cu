@@ -366,6 +366,15 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   const size_t o_psi1 = place(sizeof(float) * std::max<long long>(1, off_v));
   const size_t o_psi2 = place(sizeof(float) * (size_t)p->n2 * d.K2max);
   const size_t o_phiT = place(sizeof(float) * N);
+  // phi_T's spectrum on the bins it is built from (q <= 12 sigma_T N), FP64 then rounded
+  const double sT = 0.1 / (double)p->cfg.T;
+  d.phiT_kmax = std::min((int)std::ceil(12.0 * sT * N), (int)(N / 2));
+  std::vector<float> phat(d.phiT_kmax + 1);
+  for (int q = 0; q <= d.phiT_kmax; ++q) {
+    const double w = (double)q / (double)N;
+    phat[q] = (float)std::exp(-w * w / (2.0 * sT * sT));
+  }
+  const size_t o_phat = place(sizeof(float) * phat.size());
   const size_t o_phiF = place(sizeof(float) * p->N_fr);
   const size_t o_h = place(sizeof(float2) * (size_t)p->C * p->N_fr);
   const size_t o_tw = place(sizeof(float2) * N);
@@ -382,6 +391,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   d.psi1 = (const float*)(base + o_psi1);
   d.psi2 = (const float*)(base + o_psi2);
   d.phiT = (const float*)(base + o_phiT);
+  d.phiThat = (const float*)(base + o_phat);
   d.phiF = (const float*)(base + o_phiF);
   d.h = (const float2*)(base + o_h);
   d.tw = (const float2*)(base + o_tw);
@@ -394,6 +404,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
       {o_rows, p->rows1.data(), sizeof(Row1) * p->n1},
       {o_rates, p->rates2.data(), sizeof(Rate2) * p->n2},
       {o_tw, tw.data(), sizeof(float2) * N},
+      {o_phat, phat.data(), sizeof(float) * phat.size()},
       {o_twl, twl.data(), sizeof(float2) * twl.size()},
       {o_gx, gxl.data(), sizeof(int2) * nblk},
       {o_pairs, p->pairs.data(), sizeof(int) * p->pairs.size()},

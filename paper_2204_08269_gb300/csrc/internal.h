@@ -51,6 +51,9 @@ struct DevPlan {
   const float* psi1;      // packed support values of psi1
   const float* psi2;      // [n2][K2max]
   const float* phiT;      // [N] time-domain lowpass phi_T[n]
+  const float* phiThat;   // [phiT_kmax + 1] its spectrum phi-hat(q / N), q = 0..phiT_kmax (the
+                          // bins phi_T is built from; beyond them phi-hat < e^-72)
+  int phiT_kmax;
   const float* phiF;      // [N_fr] phi_F[m]
   const float2* h;        // [C][N_fr] log-frequency filters h_c[m]
   const float2* tw;       // [TW] exp(-2 pi i j / TW)

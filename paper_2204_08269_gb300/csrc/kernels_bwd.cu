@@ -189,7 +189,14 @@ k_second_order_bwd(DevPlan P, const float2* __restrict__ gys, const float* __res
   const int half = R.L >> 1;
   float2* tmp = sm;                // [L] padded
   const float invLr = 1.f / (float)R.L;
-  // guh[k] for k < half, built in registers per bin and stored bit-reversed
+  const float* g1 = gs1 ? gs1 + ((size_t)b * P.n1 + lam) * P.n_t : nullptr;
+  // guh[k] for k <= half, built in registers per bin and stored bit-reversed; g_U1 is the real
+  // part of its inverse DFT.  Two terms:
+  //  - the rates' adjoint: the gY row spectra / Lr times psi-hat_alpha on bins 0 < k < half;
+  //  - S1's adjoint g[m] = s sum_t phi_T[t T - m s] g_S1[t], whose length-L DFT is
+  //    G[k mod n_t] sum_r phi-hat[k + r L] (the spikes of g_S1 sit tau = T / s apart and
+  //    phi_T at stride s aliases phi-hat): nonzero only where phi-hat is, taken one-sided
+  //    (bins 0 and L / 2 once, the others twice), with phi-hat on the bins phi_T is built from.
   for (int k = threadIdx.x; k < R.L; k += blockDim.x) {
     float2 acc = make_float2(0.f, 0.f);
     if (k >= 1 && k < half) {
@@ -203,21 +210,31 @@ k_second_order_bwd(DevPlan P, const float2* __restrict__ gys, const float* __res
         acc.y += v.y * f;
       }
     }
+    if (g1 && k <= half) {
+      // signed representatives k + r L: r >= 0, then r < 0 (|k + r L| = |r| L - k)
+      float ph = 0.f;
+      for (int q = k; q <= P.phiT_kmax; q += R.L) ph += __ldg(&P.phiThat[q]);
+      for (int q = R.L - k; q <= P.phiT_kmax; q += R.L) ph += __ldg(&P.phiThat[q]);
+      if (ph != 0.f) {
+        const int f = k & (P.n_t - 1);
+        float2 G = make_float2(0.f, 0.f);
+        for (int t = 0; t < P.n_t; ++t) {   // G[f] = sum_t g_S1[t] exp(-2 pi i f t / n_t)
+          float sn, cs;
+          sincospif(2.f * (float)((f * t) & (P.n_t - 1)) / (float)P.n_t, &sn, &cs);
+          G.x += g1[t] * cs;
+          G.y -= g1[t] * sn;
+        }
+        const float c = ((k == 0 || k == half) ? 1.f : 2.f) * invLr * ph;
+        acc.x += c * G.x;
+        acc.y += c * G.y;
+      }
+    }
     tmp[fft_pad(bitrev(k, R.logL))] = acc;
   }
   __syncthreads();
   fft_dit_rows_r16<+1>(tmp, R.logL, 1, twl_for(P, R.logL));
-  const float* g1 = gs1 ? gs1 + ((size_t)b * P.n1 + lam) * P.n_t : nullptr;
   float* out = gu1 + (size_t)b * P.u1_len + R.off_u;
-  for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
-    float v = tmp[fft_pad(m)].x;
-    if (g1) {
-      float s = 0.f;
-      for (int t = 0; t < P.n_t; ++t) s += __ldg(&P.phiT[(t * P.T - m * R.s) & (P.N - 1)]) * g1[t];
-      v += s * (float)R.s;
-    }
-    out[m] = v;
-  }
+  for (int m = threadIdx.x; m < R.L; m += blockDim.x) out[m] = tmp[fft_pad(m)].x;
 }
 
 __global__ void __launch_bounds__(kFftThreads)
