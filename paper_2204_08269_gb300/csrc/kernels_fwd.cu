@@ -4,7 +4,8 @@
 //   k_s0                        : S0[t] = sum_n phi_T[(tT - n) mod N] x[n]
 //   k_scalogram                 : per (lambda, signal): periodise x-hat * psi-hat_lambda to
 //                                 L_lambda bins, inverse FFT, modulus -> U1 row (checkpoint),
-//                                 S1 row (Riemann sum of phi_T), FFT of the row -> U1-hat
+//                                 FFT of the row -> U1-hat, S1 row (the Riemann sum of
+//                                 phi_T, evaluated on the row spectrum)
 //   k_second_order_rows         : per (alpha, block of lambda' rows, signal): U1-hat *
 //                                 psi-hat_alpha folded to L_alpha bins, batched inverse FFT
 //                                 -> Y_alpha rows
@@ -65,21 +66,38 @@ k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
   // the row again, bit-reversed, for the forward FFT
   for (int m = threadIdx.x; m < R.L; m += blockDim.x)
     sm[fft_pad(bitrev(m, R.logL))] = make_float2(su[m], 0.f);
-  // S1[lambda, t] = sum_m s phi_T[(tT - m s) mod N] U1[m]   (one warp per frame)
-  {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int t = w; t < P.n_t; t += nw) {
-      float acc = 0.f;
-      const int tT = t * P.T;
-      for (int m = l; m < R.L; m += 32) acc += __ldg(&P.phiT[(tT - m * R.s) & (P.N - 1)]) * su[m];
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (l == 0) s1[((size_t)b * P.n1 + lam) * P.n_t + t] = acc * (float)R.s;
-    }
-  }
   __syncthreads();
   fft_dit_rows_r16<-1>(sm, R.logL, 1, twl_for(P, R.logL));
   float2* hb = uh + (size_t)b * P.uh_len + R.off_uh;
   for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[fft_pad(k)];
+  // S1[lambda, t] = sum_m s phi_T[(tT - m s) mod N] U1[m] from the row spectrum: with tau =
+  // T / s, it is s (phi_s * U1)[t tau] for phi_s[j] = phi_T[j s], whose length-L DFT is
+  // (1 / s) sum_r phi-hat[k + r L]; so S1[t] = (1 / L) sum_k Phi[k] U1-hat[k] e^{2 pi i k t / n_t}
+  // with Phi[k] = sum_r phi-hat[k + r L], nonzero only near k = 0 (and L).  U1 is real: the
+  // bins 0 < k < L / 2 count twice.  One warp per frame, lanes over the bins.
+  {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int half = R.L >> 1;
+    // bins [0, kA] near 0, and [kB, half] whose alias L - k is within phi-hat's support
+    const int kA = min(half, P.phiT_kmax), kB = max(kA + 1, R.L - P.phiT_kmax);
+    const int nbins = kA + 1 + max(0, half - kB + 1);
+    for (int t = w; t < P.n_t; t += nw) {
+      float acc = 0.f;
+      for (int i = l; i < nbins; i += 32) {
+        const int k = i <= kA ? i : kB + (i - kA - 1);
+        float ph = 0.f;
+        for (int q = k; q <= P.phiT_kmax; q += R.L) ph += __ldg(&P.phiThat[q]);
+        for (int q = R.L - k; q <= P.phiT_kmax; q += R.L) ph += __ldg(&P.phiThat[q]);
+        if (ph == 0.f) continue;
+        const float2 u = sm[fft_pad(k)];
+        float sn, cs;
+        sincospif(2.f * (float)((k * t) & (P.n_t - 1)) / (float)P.n_t, &sn, &cs);
+        acc += ((k == 0 || k == half) ? 1.f : 2.f) * ph * (u.x * cs - u.y * sn);
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (l == 0) s1[((size_t)b * P.n1 + lam) * P.n_t + t] = acc / (float)R.L;
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------
