@@ -11,8 +11,9 @@
 //                        fold / psi_alpha product on those spectra, real part of the inverse
 //                        of the row FFT, plus the adjoint of S1's pooling -> g_U1 row
 //   k_stage1_bwd       : per (lambda, signal): recompute z, gz = g_U1 z / |z|, FFT -> gF
-//   k_gxh              : g_x-hat[k] = sum_lambda psi_lambda[k] gF_lambda[k mod L_lambda]
-//   k_gx               : g_x = Re(inverse DFT of g_x-hat) + adjoint of S0's pooling
+//   k_gxh              : g_x-hat[k] = sum_lambda psi_lambda[k] gF_lambda[k mod L_lambda], plus
+//                        the spectrum of S0's adjoint
+//   k_gx               : g_x = Re(inverse DFT of g_x-hat)
 #include "stages.cuh"
 
 namespace jtfs {
@@ -211,10 +212,12 @@ k_second_order_bwd(DevPlan P, const float2* __restrict__ gys, const float* __res
       }
     }
     if (g1 && k <= half) {
-      // signed representatives k + r L: r >= 0, then r < 0 (|k + r L| = |r| L - k)
+      // signed representatives k + r L of the N-grid bins: r >= 0, then r < 0
+      // (|k + r L| = |r| L - k, below the Nyquist bin, which the first loop holds)
       float ph = 0.f;
+      const int qneg = min(P.phiT_kmax, (P.N >> 1) - 1);
       for (int q = k; q <= P.phiT_kmax; q += R.L) ph += __ldg(&P.phiThat[q]);
-      for (int q = R.L - k; q <= P.phiT_kmax; q += R.L) ph += __ldg(&P.phiThat[q]);
+      for (int q = R.L - k; q <= qneg; q += R.L) ph += __ldg(&P.phiThat[q]);
       if (ph != 0.f) {
         const int f = k & (P.n_t - 1);
         float2 G = make_float2(0.f, 0.f);
@@ -268,7 +271,12 @@ k_stage1_bwd(DevPlan P, const float2* __restrict__ xh, const float* __restrict__
   }
 }
 
-__global__ void k_gxh(DevPlan P, const float2* __restrict__ gf, float2* __restrict__ gxh) {
+// S0's adjoint sum_t phi_T[(tT - n) mod N] g_S0[t] has the length-N DFT
+// DFT(g_S0)[k mod n_t] phi-hat[k] (spikes T apart), nonzero for k <= phiT_kmax: it is added
+// to those bins of the one-sided g_x spectrum (bin 0 once, the others twice, / N).  When
+// phi-hat reaches the Nyquist bin (T <= 2), k_gx adds it in the time domain instead.
+__global__ void k_gxh(DevPlan P, const float2* __restrict__ gf, const float* __restrict__ gs0,
+                      float2* __restrict__ gxh) {
   const int b = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int half = P.N >> 1;
@@ -286,12 +294,26 @@ __global__ void k_gxh(DevPlan P, const float2* __restrict__ gf, float2* __restri
         acc.y += f * v.y;
       }
     }
+    if (gs0 && k <= P.phiT_kmax && P.phiT_kmax < half) {
+      const float* g0 = gs0 + (size_t)b * P.n_t;
+      const int f = k & (P.n_t - 1);
+      float2 G = make_float2(0.f, 0.f);
+      for (int t = 0; t < P.n_t; ++t) {
+        float sn, cs;
+        sincospif(2.f * (float)((f * t) & (P.n_t - 1)) / (float)P.n_t, &sn, &cs);
+        G.x += g0[t] * cs;
+        G.y -= g0[t] * sn;
+      }
+      const float c = (k == 0 ? 1.f : 2.f) * __ldg(&P.phiThat[k]) / (float)P.N;
+      acc.x += c * G.x;
+      acc.y += c * G.y;
+    }
     gxh[(size_t)b * half + k] = acc;
   }
 }
 
 // g_x[r + D m] = Re(sum_k' e^{2 pi i k' m / M} sum_q H[k' + q M] e^{2 pi i (k' + q M) r / N})
-//              + sum_t phi_T[(tT - n) mod N] g_S0[t]
+// (S0's adjoint is already in H unless phi-hat reaches the Nyquist bin)
 __global__ void __launch_bounds__(kFftThreads)
 k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, float* __restrict__ gx) {
   extern __shared__ float2 sm[];
@@ -313,7 +335,7 @@ k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, f
   }
   __syncthreads();
   fft_dit_rows_r16<+1>(sm, P.logM, 1, twl_for(P, P.logM));
-  const float* g0 = gs0 ? gs0 + (size_t)b * P.n_t : nullptr;
+  const float* g0 = (gs0 && P.phiT_kmax >= half) ? gs0 + (size_t)b * P.n_t : nullptr;
   float* out = gx + (size_t)b * P.N;
   for (int m = threadIdx.x; m < P.M; m += blockDim.x) {
     const int n = r + P.D * m;
@@ -421,7 +443,7 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
   }
   {
     StageScope sc(p, kStGx, st, 2);
-    k_gxh<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.gf, w.gxh);
+    k_gxh<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.gf, gs0, w.gxh);
     k_gx<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, w.gxh, gs0, gx);
   }
   return cuda_check(cudaGetLastError(), "backward launch");

@@ -79,15 +79,17 @@ k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int half = R.L >> 1;
     // bins [0, kA] near 0, and [kB, half] whose alias L - k is within phi-hat's support
-    const int kA = min(half, P.phiT_kmax), kB = max(kA + 1, R.L - P.phiT_kmax);
+    const int kA = min(half, P.phiT_kmax), kB = max(kA + 1, R.L - min(P.phiT_kmax, (P.N >> 1) - 1));
     const int nbins = kA + 1 + max(0, half - kB + 1);
     for (int t = w; t < P.n_t; t += nw) {
       float acc = 0.f;
       for (int i = l; i < nbins; i += 32) {
         const int k = i <= kA ? i : kB + (i - kA - 1);
+        // signed representatives k + r L of the N-grid bins (the negative ones below Nyquist)
         float ph = 0.f;
+        const int qneg = min(P.phiT_kmax, (P.N >> 1) - 1);
         for (int q = k; q <= P.phiT_kmax; q += R.L) ph += __ldg(&P.phiThat[q]);
-        for (int q = R.L - k; q <= P.phiT_kmax; q += R.L) ph += __ldg(&P.phiThat[q]);
+        for (int q = R.L - k; q <= qneg; q += R.L) ph += __ldg(&P.phiThat[q]);
         if (ph == 0.f) continue;
         const float2 u = sm[fft_pad(k)];
         float sn, cs;
