@@ -297,3 +297,16 @@ def test_fused_step_matches_separate_calls(ci, prec):
     for b in range(3):
         ref = O.backward_one(xs[b], gs[0][b], gs[1][b], gs[2][b], op, sc)
         assert _rel(got[b], ref) <= GTOL[prec]
+
+
+@pytest.mark.parametrize("T", [1, 2, 4])
+def test_short_pooling_windows_cuda_cores(T):
+    """T <= 2: the lowpass spectrum reaches the Nyquist bin and aliases across the first-order
+    rows, so the frequency-domain S1 / S0 pooling and adjoints take their every-bin forms and
+    the S0 adjoint its time-domain form (CUDA-core contraction, which has no frame limit)."""
+    cfg = dict(N=256, J=4, Q=3, J_fr=2, Q_fr=2, T=T, F=3)
+    plan = _plans(cfg, "fp32_simt")
+    op, sc = _oracle(cfg)
+    x = SS.white_noise_batch(2, cfg["N"], 300 + T)
+    _check_forward(plan, x, op, sc, TOL["fp32_simt"])
+    _check_backward(plan, x, op, sc, GTOL["fp32_simt"], seed=T)
