@@ -1220,18 +1220,44 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
 }
 
 // phi_F pooling along lambda of the time-pooled rows: S2[b, a, c, lo, t].
+// The rows of a (c, alpha, b) block are split over the block's warps (kPoolSplit row ranges);
+// the partial sums meet in shared memory and are added in a fixed order.
+constexpr int kPoolSplit = 8;
+
 __global__ void k_pool_lambda(DevPlan Pd, const float* __restrict__ P, float* __restrict__ s2) {
+  __shared__ float part[kPoolSplit][256];
   const int c = blockIdx.x, a = blockIdx.y, b = blockIdx.z;
   const int n1 = Pd.n1, nt = Pd.n_t, nfm = Pd.N_fr - 1;
   const Rate2 A = Pd.rates2[a];
   float* out = s2 + (((size_t)b * Pd.n2 + a) * Pd.C + c) * (size_t)Pd.n_lo * nt;
   const float* in = P + (((size_t)b * Pd.n2 + a) * (size_t)(Pd.C * n1) + (size_t)c * n1) * nt;
-  for (int i = threadIdx.x; i < Pd.n_lo * nt; i += blockDim.x) {
-    if (A.s == 0) { out[i] = 0.f; continue; }
-    if (!Pd.average_fr) { out[i] = in[i]; continue; }
-    const int lo = i / nt, t = i % nt;
+  const int nout = Pd.n_lo * nt;
+  if (A.s == 0 || !Pd.average_fr || nout > 256 || blockDim.x != 256) {
+    for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+      if (A.s == 0) { out[i] = 0.f; continue; }
+      if (!Pd.average_fr) { out[i] = in[i]; continue; }
+      const int lo = i / nt, t = i % nt;
+      float s = 0.f;
+      for (int r = 0; r < n1; ++r) s += __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]) * in[r * nt + t];
+      out[i] = s;
+    }
+    return;
+  }
+  // element e: output i = e mod nout (lo, t) over the rows [q rq, q rq + rq) of q = e / nout
+  const int rq = (n1 + kPoolSplit - 1) / kPoolSplit;
+  for (int e = threadIdx.x; e < kPoolSplit * nout; e += blockDim.x) {
+    const int q = e / nout, i = e - q * nout;
+    const int lo = i / nt, t = i - lo * nt;
+    const int r0 = q * rq, r1 = min(n1, r0 + rq);
     float s = 0.f;
-    for (int r = 0; r < n1; ++r) s += __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]) * in[r * nt + t];
+    for (int r = r0; r < r1; ++r) s += __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]) * in[r * nt + t];
+    part[q][i] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < kPoolSplit; ++q) s += part[q][i];
     out[i] = s;
   }
 }
