@@ -171,8 +171,21 @@ k_gy_spectra(DevPlan P, const int4* __restrict__ items, float2* __restrict__ gy)
   const Rate2 A = P.rates2[a];
   const int L = A.L, logL = A.logL;
   float2* g = gy + (size_t)b * P.y_len + A.off_y + (size_t)(lam0 - A.lam_min) * L;
-  for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x)
-    sm[fft_pad(((idx >> logL) << logL) + bitrev(idx & (L - 1), logL))] = g[idx];
+  // eight loads in flight per thread before their shared-memory stores
+  const int total = G * L, step = blockDim.x;
+  for (int base = threadIdx.x; base < total; base += 8 * step) {
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = base + q * step;
+      v[q] = idx < total ? g[idx] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = base + q * step;
+      if (idx < total) sm[fft_pad(((idx >> logL) << logL) + bitrev(idx & (L - 1), logL))] = v[q];
+    }
+  }
   __syncthreads();
   fft_dit_rows_r16<-1>(sm, logL, G, twl_for(P, logL));
   for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) g[idx] = sm[fft_pad(idx)];
