@@ -310,3 +310,29 @@ def test_short_pooling_windows_cuda_cores(T):
     x = SS.white_noise_batch(2, cfg["N"], 300 + T)
     _check_forward(plan, x, op, sc, TOL["fp32_simt"])
     _check_backward(plan, x, op, sc, GTOL["fp32_simt"], seed=T)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_fused_step_full_batch_sampled(prec):
+    """The benchmark's call (jtfs_forward_backward, B = 64, N = 2^16): one signal's S and g_x
+    re-computed by the oracle, and the step is bit-for-bit repeatable."""
+    cfg = _workload_cfg(2)
+    plan = _plans(cfg, prec)
+    op, sc = _oracle(cfg)
+    sh = plan.shapes
+    xs = SS.workload_signals(2, 64, cfg["N"])
+    x = torch.from_numpy(xs).cuda()
+    rng = np.random.default_rng(64)
+    g = [rng.standard_normal((64,) + tuple(f(1)[1:])).astype(np.float32) for f in (sh.s0, sh.s1, sh.s2)]
+    gd = [torch.from_numpy(v).cuda() for v in g]
+    s0, s1, s2, gx = plan.forward_backward(x, *gd)
+    r0, r1, r2, rgx = plan.forward_backward(x, *gd)
+    torch.cuda.synchronize()
+    for a, b in ((s0, r0), (s1, r1), (s2, r2), (gx, rgx)):
+        assert torch.equal(a, b)
+    b = 23
+    ref = O.forward_one(xs[b].astype(np.float64), op, sc)
+    for name, got in (("S0", s0), ("S1", s1), ("S2", s2)):
+        assert _rel(got[b].double().cpu().numpy(), ref[name]) <= TOL[prec], name
+    refg = O.backward_one(xs[b].astype(np.float64), g[0][b], g[1][b], g[2][b], op, sc)
+    assert _rel(gx[b].double().cpu().numpy(), refg) <= GTOL[prec]
