@@ -1,8 +1,8 @@
 """Throughput benchmark: JTFS forward + backward signals/sec on the B = 64, N = 2^16, Q = 16
 workload (J = 12, J_fr = 4, Q_fr = 2, T = 2^12, F = 16; seeded synthetic AM/FM tones).
 
-One step = forward of the whole batch (inputs resident in HBM) + backward with fixed
-cotangents.  Prints one JSON line.  Under torchrun each rank runs the same per-GPU batch
+One step = one jtfs_forward_backward call: forward of the whole batch (inputs resident in
+HBM) and backward with fixed cotangents.  Prints one JSON line.  Under torchrun each rank runs the same per-GPU batch
 (weak scaling, no data-path collective); the time is the max over ranks.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|tf32|bf16|fp32_simt]
@@ -109,6 +109,18 @@ def _dist():
     return world, rank, local
 
 
+def job_throughput(ms_local, batch, world, device):
+    """(slowest rank's ms per step, whole-job signals/s): every rank's mean step time is
+    all-reduced with MAX, and the signals of all ranks are divided by it."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, batch * world / (ms_max / 1e3)
+
+
 def contraction_flops(plan_shapes, schedule, B):
     """Algorithmic FLOPs of the log-frequency contractions in one forward + backward step:
     the forward Z = W_c Y_alpha, the backward's recomputation of Z and gY = W_c^H gZ; each is
@@ -180,11 +192,7 @@ def run_ours(args):
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
     stages, launches = plan.profile_read()
     plan.profile(False)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = BATCH * world / (ms_max / 1e3)
+    ms_max, value = job_throughput(ms, BATCH, world, "cuda")
 
     # end to end through the host-buffer entry point (H2D, fwd, bwd, D2H in one call)
     e2e = None
