@@ -121,6 +121,28 @@ def job_throughput(ms_local, batch, world, device):
     return ms_max, batch * world / (ms_max / 1e3)
 
 
+def fft_stage_bytes(plan_shapes, schedule, B, planes):
+    """Algorithmic HBM bytes per step of the FFT-side stages of the fused step (each array
+    read or written once per stage that needs it): the Y producer (U1-hat in, Y planes of
+    `planes` BF16 copies out), the scalogram (x-hat in, U1 and U1-hat out), the gY spectra and
+    second-order backward (gY read, written in place, read again; g_U1 out), the first-order
+    backward (g_U1 and x-hat in, gF out) and g_x (gF in, g_x-hat through, g_x out)."""
+    s1, s2, lm = schedule
+    n1, N = plan_shapes.n1, plan_shapes.N
+    y = sum((n1 - int(lm[a])) * (N // int(s2[a])) for a in range(len(s2)) if s2[a])
+    u1 = plan_shapes.u1_len
+    uh = u1 // 2
+    xh = N // 2
+    per = {
+        "second_order": y * 2 * 2 * planes + uh * 8,
+        "scalogram": xh * 8 + u1 * 4 + uh * 8,
+        "second_order_bwd": y * 8 * 3 + u1 * 4,
+        "stage1_bwd": u1 * 4 + xh * 8 + u1 * 8,
+        "gx": u1 * 8 + xh * 8 * 2 + N * 4,
+    }
+    return {k: v * B for k, v in per.items()}
+
+
 def contraction_flops(plan_shapes, schedule, B):
     """Algorithmic FLOPs of the log-frequency contractions in one forward + backward step:
     the forward Z = W_c Y_alpha, the backward's recomputation of Z and gY = W_c^H gZ; each is
@@ -236,6 +258,16 @@ def run_ours(args):
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["launch_ms"] = joint_ms
     roof["flops_per_step"] = flops
+    # the FFT-side stages (HBM bound by their algorithmic traffic)
+    fft = None
+    if args.precision in ("fp32", "bf16"):
+        fb = fft_stage_bytes(sh, sched, BATCH, 2 if args.precision == "fp32" else 1)
+        fms = sum(stages[k] for k in fb) / args.steps
+        gbs = sum(fb.values()) / (fms / 1e3) / 1e9
+        fft = {"bound": "hbm", "stages": sorted(fb), "achieved": gbs,
+               "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+               "frac": gbs / peaks.get("hbm_gbs"), "bytes_per_step": sum(fb.values()),
+               "ms_per_step": fms}
     out = None
     if rank == 0:
         cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
@@ -251,6 +283,7 @@ def run_ours(args):
                        "l2": "flushed by a 256 MiB write before every timed step",
                        "row_fft_launch": tuned},
             "roofline": roof,
+            "fft_roofline": fft,
             "stage_ms_per_step": {k: v / args.steps for k, v in stages.items()},
             "cpu_baseline": cpu,
             "e2e": e2e,
