@@ -452,7 +452,7 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
   }
   {
     StageScope sc(p, kStStage1Bwd, st, 1);
-    k_stage1_bwd<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 17 / 2, st>>>(d, w.xh, w.gu1, w.gf);
+    k_stage1_bwd<<<dim3(p->n1, B), kRowLaunch, (size_t)p->L1max * 17 / 2, st>>>(d, w.xh, w.gu1, w.gf);
   }
   {
     StageScope sc(p, kStGx, st, 2);

@@ -390,7 +390,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   }
   {
     StageScope sc(p, kStScalogram, st, 1);
-    k_scalogram<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, w.xh, u1, w.uh, s1);
+    k_scalogram<<<dim3(p->n1, B), kRowLaunch, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, w.xh, u1, w.uh, s1);
   }
   if (p->use_tc && p->cfg.precision == JTFS_PREC_TF32) {
     // TF32 operands: Y as FP32 planes (in the complex FP32 buffer, same size)
@@ -513,7 +513,7 @@ jtfs_status launch_first_order_static(const jtfs_plan* p, const float* x, int B,
   k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, xsub);
   k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, xsub, xh);
   k_s0<<<dim3(p->n_t, B), 256, 0, st>>>(d, x, xh, s0);
-  k_scalogram<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, xh, u1, uh, s1);
+  k_scalogram<<<dim3(p->n1, B), kRowLaunch, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, xh, u1, uh, s1);
   return cuda_check(cudaGetLastError(), "first-order static launch");
 }
 

@@ -11,6 +11,9 @@ namespace jtfs {
 namespace {
 
 constexpr int kFftThreads = 512;
+// per-row first-order kernels are launched with 256 threads: with their registers, 512-thread
+// blocks leave one block per SM
+constexpr int kRowLaunch = 256;
 
 // x-hat by decimation: x_r[m] = x[r + D m] (D sub-sequences of length M), FFT each,
 // then x-hat[k] = sum_r exp(-2 pi i r k / N) X_r[k mod M].
