@@ -194,7 +194,7 @@ k_gy_spectra(DevPlan P, const int4* __restrict__ items, float2* __restrict__ gy)
 // g_U1 row lambda': sum over rates alpha of the adjoint of psi2 (the gY row's spectrum / Lr
 // times psi-hat_alpha on the row's positive bins), then Re of the inverse row DFT, plus S1's
 // adjoint.
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(256, 3)   // launched with 256 threads; three blocks per SM
 k_second_order_bwd(DevPlan P, const float2* __restrict__ gys, const float* __restrict__ gs1,
                    float* __restrict__ gu1) {
   extern __shared__ float2 sm[];
