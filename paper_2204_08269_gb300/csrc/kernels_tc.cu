@@ -1666,10 +1666,9 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       } else {
         if (res) JTFS_LAUNCH_PAIR(true, 1); else JTFS_LAUNCH_PAIR(false, 1);
       }
-    } else if (f16 && tf) {
-      if (res) JTFS_LAUNCH_TC16(true, true); else JTFS_LAUNCH_TC16(false, true);
     } else if (f16) {
-      if (res) JTFS_LAUNCH_TC16(true, false); else JTFS_LAUNCH_TC16(false, false);
+      // 16 frames without the spin-pair form: the TF32 operands
+      if (res) JTFS_LAUNCH_TC16(true, true); else JTFS_LAUNCH_TC16(false, true);
     } else if (NT == 32) {
       if (res) JTFS_LAUNCH_TC(32, 64, true); else JTFS_LAUNCH_TC(32, 64, false);
     } else {
