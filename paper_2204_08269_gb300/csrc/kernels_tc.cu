@@ -983,18 +983,28 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
             const uint32_t sa = RES ? smem_u32(sA) + kb * kAPlane : st;
             const uint32_t a_stride = RES ? max_kb * kAPlane : kAPlane;
             const int kss = min(2, nks - 2 * kb);
-            for (int ks = 0; ks < kss; ++ks) {
-              for (int q = 0; q < npair; ++q) {
-                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-                // A: K-major rows of 32 lambda' (64-byte swizzle); B: [Yr | Yi] MN-major
-                // atoms of 64 samples, K step = 16 rows of 128 bytes
-                const uint32_t ar_a = sa + pa * 2 * a_stride + ks * 32;
-                const uint64_t ar = smem_desc(ar_a, 16, 512, kSw64);
-                const uint64_t ai = smem_desc(ar_a + a_stride, 16, 512, kSw64);
-                const uint64_t bd = smem_desc(sb + pb * 2 * kYAtom + ks * 16 * 128, kYAtom, 1024, kSw128);
-                const uint32_t f = (kb | ks | q) ? 1u : 0u;
-                mma_f16(t_a, ar, bd, id, f);    // [P1 | P3] = Wr [Yr | Yi]
-                mma_f16(t_b, ai, bd, id, f);    // [P4 | P2] = Wi [Yr | Yi]
+            // A: K-major rows of 32 lambda' (64-byte swizzle); B: [Yr | Yi] MN-major atoms of
+            // 64 samples, K step = 16 rows of 128 bytes.  The descriptors of one stage differ
+            // only in their start address (16-byte units, below 2^14), so they are the stage's
+            // two base descriptors plus fixed offsets.
+            const uint64_t dA = smem_desc(sa, 16, 512, kSw64);
+            const uint64_t dB = smem_desc(sb, kYAtom, 1024, kSw128);
+            const uint32_t as4 = a_stride >> 4;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              if (ks < kss) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                  if (q < npair) {
+                    const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                    const uint64_t ar = dA + (uint64_t)(pa * 2 * as4 + ks * 2);
+                    const uint64_t ai = ar + as4;
+                    const uint64_t bd = dB + (uint64_t)(pb * 2 * (kYAtom >> 4) + ks * 128);
+                    const uint32_t f = (kb | ks | q) ? 1u : 0u;
+                    mma_f16(t_a, ar, bd, id, f);    // [P1 | P3] = Wr [Yr | Yi]
+                    mma_f16(t_b, ai, bd, id, f);    // [P4 | P2] = Wi [Yr | Yi]
+                  }
+                }
               }
             }
             mma_commit(&empty_bar[stage]);
