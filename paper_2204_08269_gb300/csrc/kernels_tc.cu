@@ -437,8 +437,9 @@ __device__ __forceinline__ void hmma16816(float (&c)[4], const uint32_t (&a)[4],
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// TF = true: TF32 operands (FP32 W and Y planes, kind::tf32 MMAs of K = 8, one pass); the
-// pooling then keeps the BF16 hi / lo split.
+// Launched with TF = true: TF32 operands (FP32 W and Y planes, kind::tf32 MMAs of K = 8, one
+// pass); the pooling then keeps the BF16 hi / lo split.  BF16 planes at 16 frames take the
+// spin-pair form below instead.
 template <bool RES, bool TF>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
