@@ -169,3 +169,37 @@ def test_scheduled_approaches_exact_with_oversampling():
         errs.append((_rel(sc["S1"], ex["S1"]), _rel(sc["S2"], ex["S2"])))
     assert errs[0][1] > errs[1][1] > errs[2][1]
     assert errs[0][1] < 1e-2 and errs[2][1] < 2e-4
+
+
+@pytest.mark.parametrize("cfg", [SMALL, O.WORKLOADS[1]])
+def test_time_pooling_is_a_product_on_the_aliased_lowpass_spectrum(cfg):
+    """The phi_T Riemann sums at stride s (L = N / s samples) and their adjoint, written from
+    the definition phi_T[n] = (1/N) sum_q phi-hat[q] e^{2 pi i q n / N}.  With T / s an
+    integer, the sums fold the spectrum onto L bins:
+      S[t] = (1/L) sum_k Phi[k] U[k] e^{2 pi i k t / n_t},  Phi[k] = sum_r phi-hat[k + r L],
+    and the adjoint is the inverse L-point DFT of Phi[k] G[k mod n_t] (G the n_t-point DFT of
+    the cotangent; phi-hat is real and even).  Keeping only the bins |q| <= ceil(12 sigma_T N)
+    (phi-hat < e^-72 beyond) changes neither.  The oracle keeps the time-domain sums."""
+    p = O.Plan(cfg)
+    rng = np.random.default_rng(7)
+    N, n_t = p.N, p.n_t
+    q = np.where(np.arange(N) <= N // 2, np.arange(N), np.arange(N) - N)
+    kmax = int(np.ceil(12.0 * p.sigma_T * N))
+    ph_trunc = np.where(np.abs(q) <= kmax, p.phi_T_hat, 0.0)
+    assert np.max(np.abs(p.phi_T_hat - ph_trunc)) < np.exp(-72.0)
+    s = 1
+    while s <= p.T:
+        L = N // s
+        Phi = p.pool_T_matrix(s)
+        u = rng.standard_normal(L)
+        g = rng.standard_normal(n_t)
+        for ph in (p.phi_T_hat, ph_trunc):
+            fold = ph.reshape(N // L, L).sum(axis=0)               # Phi[k], k < L
+            k = np.arange(L)
+            S = (fold * np.fft.fft(u)) @ np.exp(2j * np.pi * np.outer(k, np.arange(n_t)) / n_t) / L
+            assert np.max(np.abs(S.imag)) < 1e-12 * np.max(np.abs(S.real))
+            assert _rel(S.real, Phi @ u) < 1e-12, s
+            gu = np.fft.ifft(fold * np.fft.fft(g)[k % n_t])
+            assert np.max(np.abs(gu.imag)) < 1e-12 * np.max(np.abs(gu.real))
+            assert _rel(gu.real, g @ Phi) < 1e-12, s
+        s *= 2
