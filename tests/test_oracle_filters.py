@@ -231,3 +231,23 @@ def test_spin_pair_products_and_adjoint():
         T = (gu.imag - gd.imag) + 1j * (gd.real - gu.real)
         np.testing.assert_allclose(Wr.T @ S + Wi.T @ T,
                                    Wu.conj().T @ gu + Wd.conj().T @ gd, atol=1e-13)
+
+
+@pytest.mark.parametrize("w", [1, 2, 4])
+def test_band_support_bound_of_the_time_wavelets(w):
+    """The GPU keeps each time wavelet psi-hat on |omega - xi| <= 8 sigma (first order) and
+    folds psi_alpha-hat up to xi_alpha + 8 sigma_alpha.  Outside those bands both Morlet terms
+    (the Gaussian at xi and the zero-mean correction kappa e^{-omega^2 / 2 sigma^2}) stay below
+    e^-32 of the filter's peak, on every bin of the N-point grid."""
+    p = O.Plan(O.WORKLOADS[w])
+    om = np.arange(1, p.N // 2) / float(p.N)
+    bound = math.exp(-32.0) * (1.0 + 1e-9)
+    for xi, sig, both in ((p.xi1, p.sigma1, True), (p.xi2, p.sigma2, False)):
+        for x, s in zip(xi, sig):
+            h = np.abs(O.morlet_hat(om, float(x), float(s)))
+            peak = h.max()
+            out = om > x + 8.0 * s
+            if both:
+                out |= om < x - 8.0 * s
+            if out.any():
+                assert h[out].max() <= bound * peak, (w, x, s)
