@@ -38,6 +38,43 @@ def test_counts_closed_form_and_locked(w):
     locked = json.load(open(os.path.join(GOLDEN, "counts.json")))[str(w)]
     for k, v in p.shapes().items():
         assert locked[k] == v, k
+    s = O.Schedule(p, cfg.oversampling)
+    np.testing.assert_array_equal(s.s1, locked["s1"])
+    np.testing.assert_array_equal(s.s2, locked["s2"])
+    np.testing.assert_array_equal(s.lam_min, locked["lam_min"])
+
+
+@pytest.mark.parametrize("w", sorted(O.WORKLOADS))
+def test_locked_schedule_samples_each_band_critically(w):
+    """The stored strides are the sampling rule of the schedule, checked as properties of the
+    sampled bands rather than by re-evaluating its formula: each first-order row's stride s is
+    a power of two whose Nyquist 1/(2s) covers the envelope band |w| <= 8 sigma (no aliasing)
+    while 2s would not (critical), unless s is capped at T; each kept second-order rate's
+    stride covers its band width [xi - 4 sigma, xi + 4 sigma] clipped to the finest
+    first-order Nyquist, critically or capped at T; a rate whose clipped band is empty is
+    skipped; lam_min is the first first-order row whose Nyquist lies above the band's low
+    edge (rows below it are identically zero after the time wavelet)."""
+    cfg = O.WORKLOADS[w]
+    p = O.Plan(cfg)
+    lk = json.load(open(os.path.join(GOLDEN, "counts.json")))[str(w)]
+    s1 = np.array(lk["s1"])
+    for sig, s in zip(p.sigma1, s1):
+        assert s >= 1 and (s & (s - 1)) == 0 and s <= p.T
+        assert 1.0 / (2 * s) >= 8 * sig or s == 1
+        assert s == p.T or 1.0 / (4 * s) < 8 * sig
+    nyq = 0.5 / s1.min()
+    for a, (xi, sig) in enumerate(zip(p.xi2, p.sigma2)):
+        lo, hi = max(0.0, xi - 4 * sig), min(xi + 4 * sig, nyq)
+        s = lk["s2"][a]
+        if lo >= hi:
+            assert lk["lam_min"][a] == p.n1
+            continue
+        assert (s & (s - 1)) == 0 and s <= p.T
+        assert 1.0 / (2 * s) >= hi - lo or s == 1
+        assert s == p.T or 1.0 / (4 * s) < hi - lo
+        above = [lam for lam in range(p.n1) if 0.5 / s1[lam] > lo]
+        assert lk["lam_min"][a] == (above[0] if above else p.n1)
+        assert all(0.5 / s1[lam] <= lo for lam in range(lk["lam_min"][a]))
 
 
 def test_paper_frame_count():
