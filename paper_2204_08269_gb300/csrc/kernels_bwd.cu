@@ -14,6 +14,8 @@
 //   k_gxh              : g_x-hat[k] = sum_lambda psi_lambda[k] gF_lambda[k mod L_lambda], plus
 //                        the spectrum of S0's adjoint
 //   k_gx               : g_x = Re(inverse DFT of g_x-hat)
+#include <mutex>
+
 #include "stages.cuh"
 
 namespace jtfs {
@@ -359,10 +361,18 @@ k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, f
   }
 }
 
-bool g_attrs_set = false;
+// cudaFuncSetAttribute acts on the current device only, so the raised shared-memory limits
+// are recorded per device (the plan's device is current in every call that launches).
+std::mutex g_attrs_mu;
+bool g_attrs_set[256] = {};
 
-jtfs_status set_attrs() {
-  if (g_attrs_set) return JTFS_OK;
+jtfs_status set_attrs(const jtfs_plan* p) {
+  if (p->device < 0 || p->device >= 256) {
+    set_error("device ordinal out of range");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_attrs_mu);
+  if (g_attrs_set[p->device]) return JTFS_OK;
   const int big = 227 * 1024;
   const void* fns[] = {(const void*)k_uh_from_u1, (const void*)k_joint_bwd_simt,
                        (const void*)k_second_order_bwd, (const void*)k_stage1_bwd,
@@ -380,7 +390,7 @@ jtfs_status set_attrs() {
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024), "attr");
     if (st != JTFS_OK) return st;
   }
-  g_attrs_set = true;
+  g_attrs_set[p->device] = true;
   return JTFS_OK;
 }
 
@@ -400,7 +410,7 @@ bool backward_reuses_forward(const jtfs_plan* p) {
 jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1, int B,
                             const float* gs0, const float* gs1, const float* gs2, float* gx,
                             const Workspace& w, cudaStream_t st, bool fused) {
-  jtfs_status rc = set_attrs();
+  jtfs_status rc = set_attrs(p);
   if (rc != JTFS_OK) return rc;
   const DevPlan& d = p->dp;
   // fused: x-hat, U1-hat (and the BF16 Y planes) are still in the workspace from the forward

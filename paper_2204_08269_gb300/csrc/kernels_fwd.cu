@@ -12,6 +12,7 @@
 //   k_joint_fwd_simt            : per (c, alpha, signal): Z = W_c Y_alpha (zero-padded
 //                                 convolution along lambda), |Z|, phi_T then phi_F pooling -> S2
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "stages.cuh"
@@ -265,11 +266,18 @@ __global__ void k_transpose_yt(DevPlan P, int a, const float* __restrict__ y,
   }
 }
 
-bool g_attrs_set = false;
+// cudaFuncSetAttribute acts on the current device only, so the raised shared-memory limits
+// are recorded per device (the plan's device is current in every call that launches).
+std::mutex g_attrs_mu;
+bool g_attrs_set[256] = {};
 
 jtfs_status set_attrs(const jtfs_plan* p) {
-  (void)p;
-  if (g_attrs_set) return JTFS_OK;
+  if (p->device < 0 || p->device >= 256) {
+    set_error("device ordinal out of range");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lk(g_attrs_mu);
+  if (g_attrs_set[p->device]) return JTFS_OK;
   const int big = 227 * 1024;
   jtfs_status st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_xfft_sub, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
@@ -281,7 +289,7 @@ jtfs_status set_attrs(const jtfs_plan* p) {
   if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_joint_fwd_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
-  g_attrs_set = true;
+  g_attrs_set[p->device] = true;
   return JTFS_OK;
 }
 
@@ -450,7 +458,6 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
 // overlap on the GPU (other streams, other host threads) race on it.  Each kernel here
 // writes every scratch element it later reads, so nothing has to be cleared between calls.
 // ---------------------------------------------------------------------------------------
-#include <mutex>
 
 namespace jtfs {
 

@@ -192,8 +192,11 @@ class JTFSPlan:
         return n.value
 
     def workspace(self, B, with_grad):
+        """The plan's cached device workspace for the current stream.  One buffer is kept per
+        stream, so calls issued on different streams (an autograd backward on a side stream,
+        for example) never share scratch; calls on one stream run in order."""
         need = self.workspace_bytes(B, with_grad)
-        key = "ws"
+        key = ("ws", torch.cuda.current_stream(self.device).cuda_stream)
         buf = self._ws.get(key)
         if buf is None or buf.numel() < need:
             buf = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
@@ -259,7 +262,7 @@ class JTFSPlan:
         sh = self.shapes
         n = ctypes.c_size_t()
         _check("jtfs_host_step_bytes", lib().jtfs_host_step_bytes(self._h, B, ctypes.byref(n)))
-        key = "host_dev"
+        key = ("host_dev", torch.cuda.current_stream(self.device).cuda_stream)
         dev_buf = self._ws.get(key)
         if dev_buf is None or dev_buf.numel() < n.value:
             dev_buf = torch.empty(n.value, dtype=torch.uint8, device=self.device)
