@@ -220,8 +220,38 @@ jtfs_status jtfs_varlen_replay(const jtfs_varlen* v, void* stream);
  * was recorded with. */
 jtfs_status jtfs_varlen_autotune(jtfs_varlen* v, void* ws, size_t ws_bytes, void* stream);
 
-/* Waits for the stream and reports any pending device error. */
+/* ---------------------------------------------------------------------------------------
+ * Failure detection.  The paper has no counterpart; these calls report faults instead of
+ * hanging or returning silently wrong numbers.
+ *
+ * Every wait of the tensor-core contraction kernels on a shared-memory barrier is bounded:
+ * after the plan's wait budget of wall time (%globaltimer) the block records a code in the
+ * plan's device status word, stops issuing work and returns, so the CUDA context stays usable.
+ * With check_finite on, forward / backward / forward_backward scan their outputs for NaN or
+ * Inf after the transform and record that in the same word.  The word is read and cleared by
+ * jtfs_sync_status. */
+
+/* Waits for the stream, then reports a pending CUDA error (JTFS_ERR_CUDA), a bounded wait that
+ * gave up (JTFS_ERR_TIMEOUT) or a non-finite output (JTFS_ERR_NUMERIC) of any earlier call on
+ * the plan, and clears the status word.  Synchronous. */
 jtfs_status jtfs_sync_status(const jtfs_plan* plan, void* stream);
+
+/* Sets the budget of every bounded device wait of later calls, in nanoseconds, within
+ * [1 us, 60 s] (default 2 s; INVALID_ARG outside).  Not thread-safe against calls in flight
+ * on other host threads. */
+jtfs_status jtfs_plan_set_wait_budget(jtfs_plan* plan, uint64_t wait_ns);
+
+/* on != 0: later forward / backward calls launch one scan per output (B * its length floats)
+ * and record JTFS_ERR_NUMERIC for the next jtfs_sync_status if any value is NaN or Inf.
+ * Default off. */
+jtfs_status jtfs_plan_set_check_finite(jtfs_plan* plan, int32_t on);
+
+/* Exercises the timeout path on the device: launches one block on `stream` that waits, with
+ * the contraction kernels' bounded wait and a budget of wait_ns in [1 us, 1 s], on a barrier
+ * that nothing ever completes; the wait gives up, the block records its code in the plan's
+ * status word and returns.  The next jtfs_sync_status then returns JTFS_ERR_TIMEOUT.
+ * Asynchronous; INVALID_ARG for a budget outside the range. */
+jtfs_status jtfs_diagnose_wait_timeout(const jtfs_plan* plan, uint64_t wait_ns, void* stream);
 
 const char* jtfs_status_string(jtfs_status s);
 const char* jtfs_last_error(void);

@@ -5,8 +5,10 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <initializer_list>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -175,6 +177,27 @@ size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* bas
     W.gxh = (float2*)take(Bz * (p->N / 2) * 8);
   }
   return off;
+}
+
+// Opt-in output check: any NaN or Inf among n floats records kErrNumeric in the status word.
+__global__ void k_check_finite(const float* __restrict__ v, size_t n, int* err) {
+  bool bad = false;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(v[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicCAS(err, 0, kErrNumeric);
+}
+
+jtfs_status check_finite(const jtfs_plan* p, cudaStream_t st,
+                         std::initializer_list<std::pair<const float*, size_t>> bufs) {
+  if (!p->check_finite) return JTFS_OK;
+  for (const auto& b : bufs) {
+    if (!b.first || b.second == 0) continue;
+    const int grid = (int)std::min<size_t>(1024, (b.second + 255) / 256);
+    k_check_finite<<<grid, 256, 0, st>>>(b.first, b.second, p->d_err);
+    p->prof.launches += 1;
+  }
+  return cuda_check(cudaGetLastError(), "k_check_finite");
 }
 
 }  // namespace jtfs
@@ -383,6 +406,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   const size_t o_pairs = place(sizeof(int) * std::max<size_t>(2, p->pairs.size()));
   const size_t o_items = place(sizeof(int) * std::max<size_t>(2, p->items.size()));
   const size_t o_ritems = place(sizeof(int) * std::max<size_t>(4, p->rowitems.size()));
+  const size_t o_err = place(16);
   p->d_bytes = off;
   if ((st = cuda_check(cudaMalloc(&p->d_mem, off), "plan tables")) != JTFS_OK) return fail(st, "");
   char* base = (char*)p->d_mem;
@@ -400,6 +424,8 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   p->d_pairs = (int*)(base + o_pairs);
   p->d_items = (int*)(base + o_items);
   p->d_rowitems = (int*)(base + o_ritems);
+  p->d_err = (int*)(base + o_err);
+  if ((st = cuda_check(cudaMemset(p->d_err, 0, 16), "status word")) != JTFS_OK) return fail(st, "");
   struct Up { size_t at; const void* src; size_t bytes; } ups[] = {
       {o_rows, p->rows1.data(), sizeof(Row1) * p->n1},
       {o_rates, p->rates2.data(), sizeof(Rate2) * p->n2},
@@ -480,8 +506,13 @@ jtfs_status jtfs_forward(const jtfs_plan* p, const float* x, int64_t B, float* s
   }
   Workspace w;
   workspace_layout(p, B, false, (char*)ws, &w);
-  return launch_forward(p, x, (int)B, s0, s1, s2, u1_ckpt ? u1_ckpt : w.u1, w,
-                        (cudaStream_t)stream);
+  if ((st = launch_forward(p, x, (int)B, s0, s1, s2, u1_ckpt ? u1_ckpt : w.u1, w,
+                           (cudaStream_t)stream)) != JTFS_OK)
+    return st;
+  const size_t Bz = (size_t)B;
+  return check_finite(p, (cudaStream_t)stream,
+                      {{s0, Bz * p->n_t}, {s1, Bz * p->n1 * p->n_t},
+                       {s2, Bz * (size_t)p->n2 * p->C * p->n_lo * p->n_t}});
 }
 
 jtfs_status jtfs_backward(const jtfs_plan* p, const float* x, const float* u1_ckpt, int64_t B,
@@ -499,7 +530,10 @@ jtfs_status jtfs_backward(const jtfs_plan* p, const float* x, const float* u1_ck
   }
   Workspace w;
   workspace_layout(p, B, true, (char*)ws, &w);
-  return launch_backward(p, x, u1_ckpt, (int)B, g_s0, g_s1, g_s2, g_x, w, (cudaStream_t)stream);
+  if ((st = launch_backward(p, x, u1_ckpt, (int)B, g_s0, g_s1, g_s2, g_x, w,
+                            (cudaStream_t)stream)) != JTFS_OK)
+    return st;
+  return check_finite(p, (cudaStream_t)stream, {{g_x, (size_t)B * p->N}});
 }
 
 jtfs_status jtfs_forward_backward(const jtfs_plan* p, const float* x, int64_t B,
@@ -520,7 +554,13 @@ jtfs_status jtfs_forward_backward(const jtfs_plan* p, const float* x, int64_t B,
   workspace_layout(p, B, true, (char*)ws, &w);
   float* u1 = u1_ckpt ? u1_ckpt : w.u1;
   if ((st = launch_forward(p, x, (int)B, s0, s1, s2, u1, w, (cudaStream_t)stream)) != JTFS_OK) return st;
-  return launch_backward(p, x, u1, (int)B, g_s0, g_s1, g_s2, g_x, w, (cudaStream_t)stream, true);
+  if ((st = launch_backward(p, x, u1, (int)B, g_s0, g_s1, g_s2, g_x, w, (cudaStream_t)stream,
+                            true)) != JTFS_OK)
+    return st;
+  const size_t Bz = (size_t)B;
+  return check_finite(p, (cudaStream_t)stream,
+                      {{s0, Bz * p->n_t}, {s1, Bz * p->n1 * p->n_t},
+                       {s2, Bz * (size_t)p->n2 * p->C * p->n_lo * p->n_t}, {g_x, Bz * p->N}});
 }
 
 jtfs_status jtfs_plan_autotune(jtfs_plan* p, int64_t B, void* ws, size_t ws_bytes, void* stream,
@@ -646,12 +686,42 @@ jtfs_status jtfs_sync_status(const jtfs_plan* p, void* stream) {
     if ((st = cuda_check(cudaMemcpy(&code, p->d_err, sizeof(int), cudaMemcpyDeviceToHost), "status word")) != JTFS_OK)
       return st;
     if (code != 0) {
-      cudaMemset(p->d_err, 0, sizeof(int));
+      if ((st = cuda_check(cudaMemset(p->d_err, 0, sizeof(int)), "clear status word")) != JTFS_OK)
+        return st;
+      if (code == kErrNumeric) {
+        set_error("non-finite values (NaN or Inf) in the outputs of an earlier call");
+        return JTFS_ERR_NUMERIC;
+      }
       set_error("a bounded device wait gave up (code " + std::to_string(code) + ")");
       return JTFS_ERR_TIMEOUT;
     }
   }
   return JTFS_OK;
+}
+
+jtfs_status jtfs_plan_set_wait_budget(jtfs_plan* p, uint64_t wait_ns) {
+  if (!p || wait_ns < 1000 || wait_ns > 60000000000ull) {
+    set_error("wait budget must lie in [1 us, 60 s]");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  p->wait_ns = wait_ns;
+  return JTFS_OK;
+}
+
+jtfs_status jtfs_plan_set_check_finite(jtfs_plan* p, int32_t on) {
+  if (!p) { set_error("NULL plan"); return JTFS_ERR_INVALID_ARG; }
+  p->check_finite = on != 0;
+  return JTFS_OK;
+}
+
+jtfs_status jtfs_diagnose_wait_timeout(const jtfs_plan* p, uint64_t wait_ns, void* stream) {
+  if (!p || wait_ns < 1000 || wait_ns > 1000000000ull) {
+    set_error("diagnostic budget must lie in [1 us, 1 s]");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  jtfs_status st = check_device(p);
+  if (st != JTFS_OK) return st;
+  return launch_wait_diagnostic(p, wait_ns, (cudaStream_t)stream);
 }
 
 }  // extern "C"

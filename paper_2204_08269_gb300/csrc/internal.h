@@ -125,7 +125,10 @@ struct jtfs_plan {
   std::vector<int> tc_items;   // (alpha, m0, n_tiles, 0) per signal; resident-W items first
   int tc_n_res;                // items whose W tile fits the resident form
   int* d_tc_items;
-  int* d_err;                  // device status word of the bounded waits
+  int* d_err;                  // device status word: 0 ok, kErrNumeric after a non-finite
+                               // output, any other code from a bounded wait that gave up
+  uint64_t wait_ns = 2000000000ull;   // budget of every bounded device wait (ns)
+  bool check_finite = false;   // scan the outputs for NaN / Inf after each call
   void* d_tc_mem;
   // tensor-core backward of the joint stage
   bool use_tcb;
@@ -145,6 +148,9 @@ struct jtfs_plan {
 };
 
 namespace jtfs {
+
+// status-word code of the opt-in non-finite output check (wait codes are below 100)
+constexpr int kErrNumeric = 1000;
 
 void set_error(const std::string& msg);
 jtfs_status cuda_check(cudaError_t e, const char* what);
@@ -191,6 +197,7 @@ bool tc_supported(const jtfs_plan* p);
 int tc_nt(int n_t);
 int tc_res_kb(const jtfs_plan* p);
 jtfs_status build_tc_tables(jtfs_plan* p);
+jtfs_status launch_wait_diagnostic(const jtfs_plan* p, uint64_t budget_ns, cudaStream_t st);
 jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi, const void* ylo,
                                 float* Pbuf, float* s2, cudaStream_t st);
 

@@ -42,7 +42,6 @@ constexpr int kBM = 128, kBK = 32;
 constexpr int kEpiWarp0 = 2, kEpiWarps = 16;
 constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);
 constexpr int kMaxWS = 4;                     // pooling-weight ring depth (at most)
-constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
 
 struct TcMaps {
   CUtensorMap w[4];        // Wr_hi, Wi_hi, Wr_lo, Wi_lo : [C*n1 rows][n1_pad] bf16, box {32, 128}
@@ -67,6 +66,7 @@ struct TcArgs {
   float* P;                // [B][n2][C*n1][nt]
   int n2;
   int* err;                // device status word (0 = ok)
+  uint64_t wait_ns;        // budget of every barrier wait (the plan's)
 };
 
 // 32 lanes x 32 bits, 32 consecutive columns per thread.
@@ -102,6 +102,7 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[CW]) {
 template <int NT, int BN, bool RES>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
+  const uint64_t wait_budget = args.wait_ns;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int NH = BN / 64;                           // 64-column halves of a tile
@@ -178,7 +179,7 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         const int lm8 = A.lam_min & ~7;
         const int nkb = (((P.n1 - lm8 + 15) >> 4) + 1) >> 1;
         if (RES) {
-          if (!mbar_wait(&a_free, aph ^ 1, kWaitNs)) { fail(10); ok = false; break; }
+          if (!mbar_wait(&a_free, aph ^ 1, wait_budget)) { fail(10); ok = false; break; }
           mbar_arrive_expect_tx(&a_full, planes * 2 * nkb * kAPlane);
           armed_a = (int)aph;
           for (int pl = 0; pl < planes; ++pl)
@@ -191,7 +192,7 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         for (int j = 0; j < ntiles && ok; ++j) {
           // operand k-blocks of the tile first, then its pooling weights
           for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&empty_bar[stage], phase ^ 1, kWaitNs)) { fail(11); ok = false; break; }
+            if (!mbar_wait(&empty_bar[stage], phase ^ 1, wait_budget)) { fail(11); ok = false; break; }
             uint8_t* st = sStage + stage * stage_bytes;
             mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
             armed |= 1u << stage;
@@ -211,7 +212,7 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
-          if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
+          if (!mbar_wait(&wempty[ws], wph ^ 1, wait_budget)) { fail(15); ok = false; break; }
           mbar_arrive_expect_tx(&wfull[ws], planes * NH * kWHalf);
           armed_w |= 1u << ws;
           armed_w_par = (armed_w_par & ~(1u << ws)) | (wph << ws);
@@ -224,10 +225,10 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       }
       // never leave the CTA with a copy in flight
       for (int s2 = 0; s2 < S; ++s2)
-        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, kWaitNs);
+        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, wait_budget);
       for (int s2 = 0; s2 < WS; ++s2)
-        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, kWaitNs);
-      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, kWaitNs);
+        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, wait_budget);
+      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, wait_budget);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -247,16 +248,16 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         const int nkb = (nks + 1) >> 1;
         const int ntiles = item.z;
         if (RES) {
-          if (!mbar_wait(&a_full, aph, kWaitNs)) { fail(9); ok = false; break; }
+          if (!mbar_wait(&a_full, aph, wait_budget)) { fail(9); ok = false; break; }
           aph ^= 1;
         }
         for (int j = 0; j <= ntiles && ok; ++j) {
           if (j < ntiles) {
             // the epilogue has loaded the previous tile out of the accumulator
-            if (!mbar_wait(&tempty, tph ^ 1, kWaitNs)) { fail(12); ok = false; break; }
+            if (!mbar_wait(&tempty, tph ^ 1, wait_budget)) { fail(12); ok = false; break; }
             tc_fence_after();
             for (int kb = 0; kb < nkb; ++kb) {
-              if (!mbar_wait(&full_bar[stage], phase, kWaitNs)) { fail(13); ok = false; break; }
+              if (!mbar_wait(&full_bar[stage], phase, wait_budget)) { fail(13); ok = false; break; }
               tc_fence_after();
               const uint32_t st = smem_u32(sStage + stage * stage_bytes);
               const uint32_t sb = RES ? st : st + planes * 2 * kAPlane;
@@ -288,10 +289,10 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           }
           if (j >= 1) {
             // pool the previous tile: D3 += |Z| (128 x BN) . w^T (BN x NT)
-            if (!mbar_wait(&zfull, zph, kWaitNs)) { fail(16); ok = false; break; }
-            if (!mbar_wait(&wfull[wq], wph, kWaitNs)) { fail(17); ok = false; break; }
+            if (!mbar_wait(&zfull, zph, wait_budget)) { fail(16); ok = false; break; }
+            if (!mbar_wait(&wfull[wq], wph, wait_budget)) { fail(17); ok = false; break; }
             if (j == 1) {
-              if (!mbar_wait(&d3free, d3ph ^ 1, kWaitNs)) { fail(18); ok = false; break; }
+              if (!mbar_wait(&d3free, d3ph ^ 1, wait_budget)) { fail(18); ok = false; break; }
               d3ph ^= 1;
             }
             tc_fence_after();
@@ -318,7 +319,7 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         mma_commit(&d3full);
       }
       mma_commit(&mma_done);
-      mbar_wait(&mma_done, 0, kWaitNs);
+      mbar_wait(&mma_done, 0, wait_budget);
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -338,7 +339,7 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       const int a = item.x, b = it / args.n_base, m0 = item.y;
       bool ok = !abort_flag;
       for (int j = 0; j < item.z && ok; ++j) {
-        if (!mbar_wait(&tfull, tph, kWaitNs)) { fail(14); ok = false; break; }
+        if (!mbar_wait(&tfull, tph, wait_budget)) { fail(14); ok = false; break; }
         tph ^= 1;
         tc_fence_after();
         float re[CW], im[CW];
@@ -360,7 +361,7 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           hv[i] = *reinterpret_cast<uint32_t*>(&h);
           lv[i] = *reinterpret_cast<uint32_t*>(&l);
         }
-        if (!mbar_wait(&zempty, zph ^ 1, kWaitNs)) { fail(19); ok = false; break; }
+        if (!mbar_wait(&zempty, zph ^ 1, wait_budget)) { fail(19); ok = false; break; }
         zph ^= 1;
 #pragma unroll
         for (int c = 0; c < CW / 8; ++c) {
@@ -377,7 +378,7 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       }
       if (!ok) break;
       if (cg != 0) continue;                  // one warp per lane quarter reads the pooled rows
-      if (!mbar_wait(&d3full, d3ph, kWaitNs)) { fail(20); break; }
+      if (!mbar_wait(&d3full, d3ph, wait_budget)) { fail(20); break; }
       d3ph ^= 1;
       tc_fence_after();
       const int r = m0 + row;
@@ -443,6 +444,7 @@ __device__ __forceinline__ void hmma16816(float (&c)[4], const uint32_t (&a)[4],
 template <bool RES, bool TF>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
+  const uint64_t wait_budget = args.wait_ns;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int NT = 16, BN = 128, NH = 2;
@@ -523,7 +525,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         const int lm8 = A.lam_min & ~7;
         const int nkb = (((P.n1 - lm8 + 15) >> 4) + 1) >> 1;
         if (RES) {
-          if (!mbar_wait(&a_free, aph ^ 1, kWaitNs)) { fail(10); ok = false; break; }
+          if (!mbar_wait(&a_free, aph ^ 1, wait_budget)) { fail(10); ok = false; break; }
           mbar_arrive_expect_tx(&a_full, planes * 2 * nkb * kAPlane);
           armed_a = (int)aph;
           for (int pl = 0; pl < planes; ++pl)
@@ -535,7 +537,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         }
         for (int j = 0; j < ntiles && ok; ++j) {
           for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&empty_bar[stage], phase ^ 1, kWaitNs)) { fail(11); ok = false; break; }
+            if (!mbar_wait(&empty_bar[stage], phase ^ 1, wait_budget)) { fail(11); ok = false; break; }
             uint8_t* st = sStage + stage * stage_bytes;
             mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
             armed |= 1u << stage;
@@ -561,7 +563,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
-          if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
+          if (!mbar_wait(&wempty[ws], wph ^ 1, wait_budget)) { fail(15); ok = false; break; }
           mbar_arrive_expect_tx(&wfull[ws], pplanes * NH * kWHalf);
           armed_w |= 1u << ws;
           armed_w_par = (armed_w_par & ~(1u << ws)) | (wph << ws);
@@ -573,10 +575,10 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         }
       }
       for (int s2 = 0; s2 < S; ++s2)
-        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, kWaitNs);
+        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, wait_budget);
       for (int s2 = 0; s2 < WS; ++s2)
-        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, kWaitNs);
-      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, kWaitNs);
+        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, wait_budget);
+      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, wait_budget);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -597,15 +599,15 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         const int nks = (P.n1 - lm8 + kKS - 1) / kKS;
         const int nkb = (nks + kSPB - 1) / kSPB;
         if (RES) {
-          if (!mbar_wait(&a_full, aph, kWaitNs)) { fail(9); ok = false; break; }
+          if (!mbar_wait(&a_full, aph, wait_budget)) { fail(9); ok = false; break; }
           aph ^= 1;
         }
         for (int j = 0; j < item.z && ok; ++j) {
-          if (!mbar_wait(&tempty[acc], acc_ph ^ 1, kWaitNs)) { fail(12); ok = false; break; }
+          if (!mbar_wait(&tempty[acc], acc_ph ^ 1, wait_budget)) { fail(12); ok = false; break; }
           tc_fence_after();
           const uint32_t t_re = tbase + acc * 256, t_im = t_re + 128;
           for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&full_bar[stage], phase, kWaitNs)) { fail(13); ok = false; break; }
+            if (!mbar_wait(&full_bar[stage], phase, wait_budget)) { fail(13); ok = false; break; }
             tc_fence_after();
             const uint32_t st = smem_u32(sStage + stage * stage_bytes);
             const uint32_t sb = RES ? st : st + planes * 2 * kAPlane;
@@ -649,7 +651,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         if (RES) mma_commit(&a_free);
       }
       mma_commit(&mma_done);
-      mbar_wait(&mma_done, 0, kWaitNs);
+      mbar_wait(&mma_done, 0, wait_budget);
     }
   } else {
     // ------------------------------------------------------------ epilogue + pooling
@@ -688,9 +690,9 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
 #pragma unroll
           for (int e = 0; e < 4; ++e) c[i][k][e] = 0.f;
       for (int j = 0; j < item.z && ok; ++j) {
-        if (!mbar_wait(&tfull[acc], acc_ph, kWaitNs)) { fail(14); ok = false; break; }
+        if (!mbar_wait(&tfull[acc], acc_ph, wait_budget)) { fail(14); ok = false; break; }
         tc_fence_after();
-        if (!mbar_wait(&wfull[ws], wph, kWaitNs)) { fail(19); ok = false; break; }
+        if (!mbar_wait(&wfull[ws], wph, wait_budget)) { fail(19); ok = false; break; }
         const uint32_t t_col = tbase + acc * 256 + lane_off + cg * 32;
         const uint32_t w_u = smem_u32(sWt + (ws * NH + (cg >> 1)) * pplanes * kWHalf);
 #pragma unroll
@@ -761,7 +763,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       if (!ok) break;
       // sum the four column groups of this lane quarter in a fixed order
       if (cg != 0) {
-        if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, kWaitNs)) { fail(21); break; }
+        if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, wait_budget)) { fail(21); break; }
         rfree_ph ^= 1;
       }
       float* red = sRed + (cg * 128 + quarter * 32) * NT;
@@ -776,7 +778,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&red_full[quarter]);
       if (cg == 0) {
-        if (!mbar_wait(&red_full[quarter], rf_ph, kWaitNs)) { fail(20); break; }
+        if (!mbar_wait(&red_full[quarter], rf_ph, wait_budget)) { fail(20); break; }
         rf_ph ^= 1;
         const int r = m0 + quarter * 32 + lane;
         float s[NT];
@@ -831,6 +833,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
 template <bool RES, int PS>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
+  const uint64_t wait_budget = args.wait_ns;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int NT = 16, BN = 64;
@@ -908,7 +911,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         const int lm8 = A.lam_min & ~7;
         const int nkb = (((P.n1 - lm8 + 15) >> 4) + 1) >> 1;
         if (RES) {
-          if (!mbar_wait(&a_free, aph ^ 1, kWaitNs)) { fail(10); ok = false; break; }
+          if (!mbar_wait(&a_free, aph ^ 1, wait_budget)) { fail(10); ok = false; break; }
           mbar_arrive_expect_tx(&a_full, planes * 2 * nkb * kAPlane);
           armed_a = (int)aph;
           for (int pl = 0; pl < planes; ++pl)
@@ -920,7 +923,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         }
         for (int j = 0; j < ntiles && ok; ++j) {
           for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&empty_bar[stage], phase ^ 1, kWaitNs)) { fail(11); ok = false; break; }
+            if (!mbar_wait(&empty_bar[stage], phase ^ 1, wait_budget)) { fail(11); ok = false; break; }
             uint8_t* st = sStage + stage * stage_bytes;
             mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
             armed |= 1u << stage;
@@ -938,7 +941,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
-          if (!mbar_wait(&wempty[ws], wph ^ 1, kWaitNs)) { fail(15); ok = false; break; }
+          if (!mbar_wait(&wempty[ws], wph ^ 1, wait_budget)) { fail(15); ok = false; break; }
           mbar_arrive_expect_tx(&wfull[ws], pplanes * kWHalf);
           armed_w |= 1u << ws;
           armed_w_par = (armed_w_par & ~(1u << ws)) | (wph << ws);
@@ -949,10 +952,10 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         }
       }
       for (int s2 = 0; s2 < S; ++s2)
-        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, kWaitNs);
+        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, wait_budget);
       for (int s2 = 0; s2 < WS; ++s2)
-        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, kWaitNs);
-      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, kWaitNs);
+        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, wait_budget);
+      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, wait_budget);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -969,15 +972,15 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         const int nks = (P.n1 - lm8 + 15) / 16;
         const int nkb = (nks + 1) / 2;
         if (RES) {
-          if (!mbar_wait(&a_full, aph, kWaitNs)) { fail(9); ok = false; break; }
+          if (!mbar_wait(&a_full, aph, wait_budget)) { fail(9); ok = false; break; }
           aph ^= 1;
         }
         for (int j = 0; j < item.z && ok; ++j) {
-          if (!mbar_wait(&tempty[acc], acc_ph ^ 1, kWaitNs)) { fail(12); ok = false; break; }
+          if (!mbar_wait(&tempty[acc], acc_ph ^ 1, wait_budget)) { fail(12); ok = false; break; }
           tc_fence_after();
           const uint32_t t_a = tbase + acc * 256, t_b = t_a + 128;
           for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&full_bar[stage], phase, kWaitNs)) { fail(13); ok = false; break; }
+            if (!mbar_wait(&full_bar[stage], phase, wait_budget)) { fail(13); ok = false; break; }
             tc_fence_after();
             const uint32_t st = smem_u32(sStage + stage * stage_bytes);
             const uint32_t sb = RES ? st : st + planes * 2 * kAPlane;
@@ -1019,7 +1022,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         if (RES) mma_commit(&a_free);
       }
       mma_commit(&mma_done);
-      mbar_wait(&mma_done, 0, kWaitNs);
+      mbar_wait(&mma_done, 0, wait_budget);
     }
   } else {
     // ------------------------------------------------------------ epilogue + pooling
@@ -1061,14 +1064,14 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
             for (int e = 0; e < 4; ++e) c[d][i][k2][e] = 0.f;
       if (cg != 0 && red_pending) {
         // column group 0 has read this warp's partials of the previous item
-        if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, kWaitNs)) { fail(21); break; }
+        if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, wait_budget)) { fail(21); break; }
         rfree_ph ^= 1;
         red_pending = false;
       }
       for (int j = 0; j < item.z && ok; ++j) {
-        if (!mbar_wait(&tfull[acc], acc_ph, kWaitNs)) { fail(14); ok = false; break; }
+        if (!mbar_wait(&tfull[acc], acc_ph, wait_budget)) { fail(14); ok = false; break; }
         tc_fence_after();
-        if (!mbar_wait(&wfull[ws], wph, kWaitNs)) { fail(19); ok = false; break; }
+        if (!mbar_wait(&wfull[ws], wph, wait_budget)) { fail(19); ok = false; break; }
         const uint32_t t_col = tbase + acc * 256 + lane_off + cg * 16;
         const uint32_t w_u = smem_u32(sWt + ws * pplanes * kWHalf);
         __syncwarp();   // the previous tile's fragment loads are done
@@ -1167,7 +1170,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
         if (cg != 0 && d == 1) {
-          if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, kWaitNs)) { fail(21); red_ok = false; break; }
+          if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, wait_budget)) { fail(21); red_ok = false; break; }
           rfree_ph ^= 1;
         }
         __syncwarp();   // the last tile's fragment loads are done
@@ -1183,7 +1186,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&red_full[quarter]);
         if (cg == 0) {
-          if (!mbar_wait(&red_full[quarter], rf_ph, kWaitNs)) { fail(20); red_ok = false; break; }
+          if (!mbar_wait(&red_full[quarter], rf_ph, wait_budget)) { fail(20); red_ok = false; break; }
           rf_ph ^= 1;
           float sv[NT];
 #pragma unroll
@@ -1521,7 +1524,6 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   const size_t wt_elems = (size_t)p->n2 * NT * Lmax;
   const size_t o_wt = place(wt_elems * 2 * 2);
   const size_t o_items = place(std::max<size_t>(16, p->tc_items.size() * 4));
-  const size_t o_err = place(16);
   jtfs_status st;
   if ((st = cuda_check(cudaMalloc(&p->d_tc_mem, off), "tc tables")) != JTFS_OK) return st;
   char* base = (char*)p->d_tc_mem;
@@ -1531,11 +1533,9 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
     for (int i = 0; i < 2; ++i) p->d_wplanes32[i] = base + o_w32[i];
   p->d_wtf = base + o_wt;
   p->d_tc_items = (int*)(base + o_items);
-  p->d_err = (int*)(base + o_err);
   if (!p->tc_items.empty() &&
       (st = cuda_check(cudaMemcpy(p->d_tc_items, p->tc_items.data(), p->tc_items.size() * 4, cudaMemcpyHostToDevice), "upload")) != JTFS_OK)
     return st;
-  if ((st = cuda_check(cudaMemset(p->d_err, 0, 16), "memset")) != JTFS_OK) return st;
   k_build_wplanes<<<1024, 256>>>(p->dp, p->n1_pad, (__nv_bfloat16*)p->d_wplanes[0],
                                  (__nv_bfloat16*)p->d_wplanes[1], (__nv_bfloat16*)p->d_wplanes[2],
                                  (__nv_bfloat16*)p->d_wplanes[3], (__nv_bfloat16*)p->d_wplanes[4],
@@ -1634,6 +1634,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   args.P = Pbuf;
   args.n2 = p->n2;
   args.err = p->d_err;
+  args.wait_ns = p->wait_ns;
   jtfs_status rc;
   int n_sm = 148;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
@@ -1692,6 +1693,28 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
 #undef JTFS_LAUNCH_PAIR
   k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
   return cuda_check(cudaGetLastError(), "k_pool_lambda");
+}
+
+namespace {
+// Diagnostic of the bounded waits: one thread initialises a barrier that expects one arrival,
+// which nothing ever makes, and waits for its first phase with the contraction kernels' own
+// bounded wait.  The wait gives up after `budget` ns; the thread records kWaitDiagnosticCode
+// in the status word and the kernel returns (no TMEM, no copies in flight).
+constexpr int kWaitDiagnosticCode = 99;
+__global__ void k_wait_diagnostic(int* err, uint64_t budget) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0, budget)) atomicCAS(err, 0, kWaitDiagnosticCode);
+}
+}  // namespace
+
+jtfs_status launch_wait_diagnostic(const jtfs_plan* p, uint64_t budget_ns, cudaStream_t st) {
+  k_wait_diagnostic<<<1, 32, 0, st>>>(p->d_err, budget_ns);
+  return cuda_check(cudaGetLastError(), "k_wait_diagnostic");
 }
 
 }  // namespace jtfs

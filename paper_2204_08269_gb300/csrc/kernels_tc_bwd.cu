@@ -33,7 +33,6 @@ constexpr int kRC = 32;          // W rows per chunk
 constexpr int kK1Max = 160;      // lambda' rows of a W chunk / gY^T accumulator
 constexpr int kThreads = 384;
 constexpr int kEpiWarp0 = 4;
-constexpr uint64_t kWaitNs = 2000000000ull;
 
 
 struct TbMaps {
@@ -53,6 +52,7 @@ struct TbArgs {
   const int* wt_row0;   // [n2] first row of each rate in the weight table
   float2* gy;           // [B][y_len] complex FP32, rows (lambda' - lam_min) x L_alpha
   int* err;
+  uint64_t wait_ns;     // budget of every barrier wait (the plan's)
 };
 
 // Resident-Y form: the Y^T tile of the item (PL planes: hi, and lo for the three-pass
@@ -61,6 +61,7 @@ struct TbArgs {
 template <int NT, int PL>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
+  const uint64_t wait_budget = args.wait_ns;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int kK1M = PL == 1 ? 160 : 96;               // lambda' rows of the resident tile
@@ -132,7 +133,7 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
         const int4 item = args.items[it / args.B];
         const int a = item.x, b = it % args.B, n0 = item.y, start = item.z, K1 = item.w;
         const Rate2 A = P.rates2[a];
-        if (!mbar_wait(&a1_free, a1_ph ^ 1, kWaitNs)) { fail(21); break; }
+        if (!mbar_wait(&a1_free, a1_ph ^ 1, wait_budget)) { fail(21); break; }
         mbar_arrive_expect_tx(&a1_full, PL * 2 * 2 * (K1 / 32) * 4096 + PL * 128 * NT * 2);
         armed_a1 = (int)a1_ph;
         for (int pl = 0; pl < PL; ++pl) {
@@ -148,7 +149,7 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
         const int nblk = (K1 + 63) / 64;
         const int g1row = (b * P.n2 + a) * args.g1_rows;
         for (int j = 0; j < args.n_chunks; ++j) {
-          if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(22); ok = false; break; }
+          if (!mbar_wait(&w_empty[wst], wph ^ 1, wait_budget)) { fail(22); ok = false; break; }
           mbar_arrive_expect_tx(&w_full[wst], PL * 2 * nblk * 4096 + PL * kRC * NT * 2);
           armed_w[wst] = (int)wph;
           uint8_t* wb = sW + wst * kWBuf;
@@ -164,8 +165,8 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
         }
       }
       for (int i = 0; i < 2; ++i)
-        if (armed_w[i] >= 0) mbar_wait(&w_full[i], (uint32_t)armed_w[i], kWaitNs);
-      if (armed_a1 >= 0) mbar_wait(&a1_full, (uint32_t)armed_a1, kWaitNs);
+        if (armed_w[i] >= 0) mbar_wait(&w_full[i], (uint32_t)armed_w[i], wait_budget);
+      if (armed_a1 >= 0) mbar_wait(&a1_full, (uint32_t)armed_a1, wait_budget);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -185,7 +186,7 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
         const uint32_t id4 = instr_desc(128, kRC, 1, 1, 0, 0, 0);
         const uint32_t id2 = instr_desc(128, N2, 1, 1, 0, 1, 0);
         const uint32_t id2n = instr_desc(128, N2, 1, 1, 0, 1, 1);
-        if (!mbar_wait(&a1_full, a1_ph, kWaitNs)) { fail(23); break; }
+        if (!mbar_wait(&a1_full, a1_ph, wait_budget)) { fail(23); break; }
         a1_ph ^= 1;
         const uint32_t a1 = smem_u32(sA1), a4 = smem_u32(sA4);
         int prev_wst = -1;
@@ -193,8 +194,8 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
         bool ok = true;
         for (int j = 0; j <= args.n_chunks && ok; ++j) {
           if (j < args.n_chunks) {
-            if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(24); ok = false; break; }
-            if (!mbar_wait(&d1_free, d1f_ph ^ 1, kWaitNs)) { fail(25); ok = false; break; }
+            if (!mbar_wait(&w_full[wst], wph, wait_budget)) { fail(24); ok = false; break; }
+            if (!mbar_wait(&d1_free, d1f_ph ^ 1, wait_budget)) { fail(25); ok = false; break; }
             d1f_ph ^= 1;
             tc_fence_after();
             const uint32_t wb = smem_u32(sW + wst * kWBuf);
@@ -225,10 +226,10 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
           if (j >= 1) {
             // gY^T += gZ^T(chunk j-1) conj(W chunk j-1)
             const int q2 = kNA2 == 2 ? ((j - 1) & 1) : 0;
-            if (!mbar_wait(&a2_full[q2], a2_ph[q2], kWaitNs)) { fail(26); ok = false; break; }
+            if (!mbar_wait(&a2_full[q2], a2_ph[q2], wait_budget)) { fail(26); ok = false; break; }
             a2_ph[q2] ^= 1;
             if (first_d2) {
-              if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(27); ok = false; break; }
+              if (!mbar_wait(&d2_free, d2f_ph ^ 1, wait_budget)) { fail(27); ok = false; break; }
               d2f_ph ^= 1;
             }
             tc_fence_after();
@@ -262,7 +263,7 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
         mma_commit(&d2_full);
       }
       mma_commit(&mma_done);
-      mbar_wait(&mma_done, 0, kWaitNs);
+      mbar_wait(&mma_done, 0, wait_budget);
     }
   } else if (warp >= kEpiWarp0) {
     // ------------------------------------------------------------ epilogue
@@ -278,7 +279,7 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
       const int a = item.x, b = it % args.B, n0 = item.y, start = item.z, K1 = item.w;
       bool ok = !abort_flag;
       for (int j = 0; j < args.n_chunks && ok; ++j) {
-        if (!mbar_wait(&d1_full, d1_ph, kWaitNs)) { fail(28); ok = false; break; }
+        if (!mbar_wait(&d1_full, d1_ph, wait_budget)) { fail(28); ok = false; break; }
         d1_ph ^= 1;
         tc_fence_after();
         float zr[16], zi[16], g[16];
@@ -314,7 +315,7 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
           }
         }
         const int q2 = kNA2 == 2 ? (j & 1) : 0;
-        if (!mbar_wait(&a2_free[q2], a2f_ph[q2] ^ 1, kWaitNs)) { fail(29); ok = false; break; }
+        if (!mbar_wait(&a2_free[q2], a2f_ph[q2] ^ 1, wait_budget)) { fail(29); ok = false; break; }
         a2f_ph[q2] ^= 1;
         // K-major rows of 64 bytes (32 r), 64-byte swizzle: 16-byte chunk c -> c ^ ((row >> 1) & 3)
         uint8_t* base = sA2 + q2 * kA2Buf + row * 64;
@@ -335,7 +336,7 @@ k_joint_bwd_tc(const __grid_constant__ TbMaps maps, TbArgs args, DevPlan P) {
       }
       if (!ok) break;
       // gY^T for this tile: columns lambda' = start + c, written as gY[lambda' - lam_min][n]
-      if (!mbar_wait(&d2_full, d2_ph, kWaitNs)) { fail(30); break; }
+      if (!mbar_wait(&d2_full, d2_ph, wait_budget)) { fail(30); break; }
       d2_ph ^= 1;
       tc_fence_after();
       const Rate2 A = P.rates2[a];
@@ -381,6 +382,7 @@ struct Tb3Maps {
 template <int NT, int WB>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
+  const uint64_t wait_budget = args.wait_ns;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr uint32_t kSw = NT * 2;
@@ -443,7 +445,7 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
         const int4 item = args.items[it / args.B];
         const int a = item.x, b = it % args.B, n0 = item.y, start = item.z, K1 = item.w;
         const Rate2 A = P.rates2[a];
-        if (!mbar_wait(&a4_free, a4_ph ^ 1, kWaitNs)) { fail(41); break; }
+        if (!mbar_wait(&a4_free, a4_ph ^ 1, wait_budget)) { fail(41); break; }
         mbar_arrive_expect_tx(&a4_full, 2 * 128 * NT * 2);
         armed_a4 = (int)a4_ph;
         for (int h = 0; h < 2; ++h)
@@ -453,7 +455,7 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
         const int g1row = (b * P.n2 + a) * args.g1_rows;
         bool ok = true;
         for (int j = 0; j < args.n_chunks && ok; ++j) {
-          if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(42); ok = false; break; }
+          if (!mbar_wait(&w_empty[wst], wph ^ 1, wait_budget)) { fail(42); ok = false; break; }
           mbar_arrive_expect_tx(&w_full[wst], 4 * nblk * 4096 + 2 * kRC * NT * 2);
           armed_w[wst] = (int)wph;
           uint8_t* wb = sW + wst * kWBuf;
@@ -466,7 +468,7 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
                         &w_full[wst]);
           if (++wst == WB) { wst = 0; wph ^= 1; }
           for (int kb = 0; kb < K1 / 32; ++kb) {
-            if (!mbar_wait(&y_empty[ys], yph ^ 1, kWaitNs)) { fail(43); ok = false; break; }
+            if (!mbar_wait(&y_empty[ys], yph ^ 1, wait_budget)) { fail(43); ok = false; break; }
             mbar_arrive_expect_tx(&y_full[ys], kYStage);
             armed_y[ys] = (int)yph;
             uint8_t* yb = sY + ys * kYStage;
@@ -482,10 +484,10 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
         if (!ok) break;
       }
       for (int i = 0; i < 2; ++i) {
-        if (armed_y[i] >= 0) mbar_wait(&y_full[i], (uint32_t)armed_y[i], kWaitNs);
-        if (armed_w[i] >= 0) mbar_wait(&w_full[i], (uint32_t)armed_w[i], kWaitNs);
+        if (armed_y[i] >= 0) mbar_wait(&y_full[i], (uint32_t)armed_y[i], wait_budget);
+        if (armed_w[i] >= 0) mbar_wait(&w_full[i], (uint32_t)armed_w[i], wait_budget);
       }
-      if (armed_a4 >= 0) mbar_wait(&a4_full, (uint32_t)armed_a4, kWaitNs);
+      if (armed_a4 >= 0) mbar_wait(&a4_full, (uint32_t)armed_a4, wait_budget);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -502,19 +504,19 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
         const uint32_t id4 = instr_desc(128, kRC, 1, 1, 0, 0, 0);
         const uint32_t id2 = instr_desc(128, N2, 1, 1, 0, 1, 0);
         const uint32_t id2n = instr_desc(128, N2, 1, 1, 0, 1, 1);
-        if (!mbar_wait(&a4_full, a4_ph, kWaitNs)) { fail(44); break; }
+        if (!mbar_wait(&a4_full, a4_ph, wait_budget)) { fail(44); break; }
         a4_ph ^= 1;
         const uint32_t a4 = smem_u32(sA4);
         bool first_d2 = true, ok = true;
         for (int j = 0; j <= args.n_chunks && ok; ++j) {
           if (j < args.n_chunks) {
-            if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(45); ok = false; break; }
-            if (!mbar_wait(&d1_free, d1f_ph ^ 1, kWaitNs)) { fail(46); ok = false; break; }
+            if (!mbar_wait(&w_full[wst], wph, wait_budget)) { fail(45); ok = false; break; }
+            if (!mbar_wait(&d1_free, d1f_ph ^ 1, wait_budget)) { fail(46); ok = false; break; }
             d1f_ph ^= 1;
             tc_fence_after();
             const uint32_t wb = smem_u32(sW + wst * kWBuf);
             for (int kb = 0; kb < K1 / 32; ++kb) {
-              if (!mbar_wait(&y_full[ys], yph, kWaitNs)) { fail(47); ok = false; break; }
+              if (!mbar_wait(&y_full[ys], yph, wait_budget)) { fail(47); ok = false; break; }
               tc_fence_after();
               const uint32_t yb = smem_u32(sY + ys * kYStage);
               for (int ks = 0; ks < 2; ++ks) {
@@ -548,10 +550,10 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
           // next Z product run first, else this chunk (its W buffer is the only one)
           const int g2 = WB == 1 ? j : j - 1;
           if (g2 >= 0 && g2 < args.n_chunks) {
-            if (!mbar_wait(&a2_full, a2_ph, kWaitNs)) { fail(48); ok = false; break; }
+            if (!mbar_wait(&a2_full, a2_ph, wait_budget)) { fail(48); ok = false; break; }
             a2_ph ^= 1;
             if (first_d2) {
-              if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(49); ok = false; break; }
+              if (!mbar_wait(&d2_free, d2f_ph ^ 1, wait_budget)) { fail(49); ok = false; break; }
               d2f_ph ^= 1;
             }
             tc_fence_after();
@@ -585,7 +587,7 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
         mma_commit(&d2_full);
       }
       mma_commit(&mma_done);
-      mbar_wait(&mma_done, 0, kWaitNs);
+      mbar_wait(&mma_done, 0, wait_budget);
     }
   } else if (warp >= kEpiWarp0) {
     const int ew = warp - kEpiWarp0;
@@ -599,7 +601,7 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
       const int a = item.x, b = it % args.B, n0 = item.y, start = item.z, K1 = item.w;
       bool ok = !abort_flag;
       for (int j = 0; j < args.n_chunks && ok; ++j) {
-        if (!mbar_wait(&d1_full, d1_ph, kWaitNs)) { fail(50); ok = false; break; }
+        if (!mbar_wait(&d1_full, d1_ph, wait_budget)) { fail(50); ok = false; break; }
         d1_ph ^= 1;
         tc_fence_after();
         float zr[16], zi[16], g[16];
@@ -632,7 +634,7 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
           lr[i] = *reinterpret_cast<uint32_t*>(&b0);
           li[i] = *reinterpret_cast<uint32_t*>(&b1);
         }
-        if (!mbar_wait(&a2_free, a2f_ph ^ 1, kWaitNs)) { fail(51); ok = false; break; }
+        if (!mbar_wait(&a2_free, a2f_ph ^ 1, wait_budget)) { fail(51); ok = false; break; }
         a2f_ph ^= 1;
         uint8_t* base = sA2 + row * 64;
         const int sw = (row >> 1) & 3;
@@ -649,7 +651,7 @@ k_joint_bwd_tc3(const __grid_constant__ Tb3Maps maps, TbArgs args, DevPlan P) {
         if (lane == 0) mbar_arrive(&a2_full);
       }
       if (!ok) break;
-      if (!mbar_wait(&d2_full, d2_ph, kWaitNs)) { fail(52); break; }
+      if (!mbar_wait(&d2_full, d2_ph, wait_budget)) { fail(52); break; }
       d2_ph ^= 1;
       tc_fence_after();
       const Rate2 A = P.rates2[a];
@@ -715,6 +717,7 @@ struct TfArgs {
   const int* wt_row0;
   float2* gy;
   int* err;
+  uint64_t wait_ns;     // budget of every barrier wait (the plan's)
 };
 
 // warp 0 TMA, warp 1 first-product MMAs (TMEM owner), warps 2..17 epilogue, warp 18
@@ -745,6 +748,7 @@ __device__ __forceinline__ void tmem_ldc(uint32_t taddr, float (&v)[CW]) {
 template <int NT, int RC, int PL, int NAT, int KM>
 __global__ void __launch_bounds__(kFThreads, 1)
 k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
+  const uint64_t wait_budget = args.wait_ns;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int CW = RC / 4;                              // chunk rows per epilogue warp
@@ -819,7 +823,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
         const int a = item.x, b = it / args.n_base, n0 = item.y, start = item.z, K1 = item.w;
         const Rate2 A = P.rates2[a];
         const int nkb1 = (K1 + 31) / 32;
-        if (!mbar_wait(&a1_free, a1_ph ^ 1, kWaitNs)) { fail(61); break; }
+        if (!mbar_wait(&a1_free, a1_ph ^ 1, wait_budget)) { fail(61); break; }
         mbar_arrive_expect_tx(&a1_full, PL * 2 * 2 * nkb1 * 4096 + PL * 128 * NT * 2);
         armed_a1 = (int)a1_ph;
         for (int pl = 0; pl < PL; ++pl) {
@@ -834,7 +838,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
         a1_ph ^= 1;
         const int g1row = (b * P.n2 + a) * args.g1_rows;
         for (int j = 0; j < args.n_chunks; ++j) {
-          if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(62); ok = false; break; }
+          if (!mbar_wait(&w_empty[wst], wph ^ 1, wait_budget)) { fail(62); ok = false; break; }
           mbar_arrive_expect_tx(&w_full[wst], PL * NAT * 3 * RC * 64 * 2 + PL * RC * NT * 2);
           armed_w |= 1u << wst;
           armed_w_par = (armed_w_par & ~(1u << wst)) | (wph << wst);
@@ -853,8 +857,8 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
         }
       }
       for (int i = 0; i < WB; ++i)
-        if (armed_w >> i & 1) mbar_wait(&w_full[i], armed_w_par >> i & 1, kWaitNs);
-      if (armed_a1 >= 0) mbar_wait(&a1_full, (uint32_t)armed_a1, kWaitNs);
+        if (armed_w >> i & 1) mbar_wait(&w_full[i], armed_w_par >> i & 1, wait_budget);
+      if (armed_a1 >= 0) mbar_wait(&a1_full, (uint32_t)armed_a1, wait_budget);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ first-product issuer
@@ -869,12 +873,12 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
       for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it % args.n_base];
         const int nks1 = item.w / 16;
-        if (!mbar_wait(&a1_full, a1_ph, kWaitNs)) { fail(63); break; }
+        if (!mbar_wait(&a1_full, a1_ph, wait_budget)) { fail(63); break; }
         a1_ph ^= 1;
         const uint32_t a1 = smem_u32(sA1), a4 = smem_u32(sA4);
         for (int j = 0; j < args.n_chunks && ok; ++j) {
-          if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(64); ok = false; break; }
-          if (!mbar_wait(&d1_free[buf], ((d1f_ph >> buf) & 1) ^ 1, kWaitNs)) { fail(65); ok = false; break; }
+          if (!mbar_wait(&w_full[wst], wph, wait_budget)) { fail(64); ok = false; break; }
+          if (!mbar_wait(&d1_free[buf], ((d1f_ph >> buf) & 1) ^ 1, wait_budget)) { fail(65); ok = false; break; }
           d1f_ph ^= 1u << buf;
           tc_fence_after();
           const uint32_t wb = smem_u32(sW + wst * kWBuf);
@@ -906,7 +910,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
         mma_commit(&a1_free);
       }
       mma_commit(&mma_done);
-      mbar_wait(&mma_done, 0, kWaitNs);
+      mbar_wait(&mma_done, 0, wait_budget);
     }
   } else if (warp == kFWarpG2) {
     // ------------------------------------------------------------ last-product issuer
@@ -919,11 +923,11 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
       bool ok = true;
       for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         for (int j = 0; j < args.n_chunks && ok; ++j) {
-          if (!mbar_wait(&a2_full[q2], (a2_ph >> q2) & 1, kWaitNs)) { fail(66); ok = false; break; }
+          if (!mbar_wait(&a2_full[q2], (a2_ph >> q2) & 1, wait_budget)) { fail(66); ok = false; break; }
           a2_ph ^= 1u << q2;
-          if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(71); ok = false; break; }
+          if (!mbar_wait(&w_full[wst], wph, wait_budget)) { fail(71); ok = false; break; }
           if (j == 0) {
-            if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(67); ok = false; break; }
+            if (!mbar_wait(&d2_free, d2f_ph ^ 1, wait_budget)) { fail(67); ok = false; break; }
             d2f_ph ^= 1;
           }
           tc_fence_after();
@@ -950,7 +954,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
         mma_commit(&d2_full);
       }
       mma_commit(&mma_done2);
-      mbar_wait(&mma_done2, 0, kWaitNs);
+      mbar_wait(&mma_done2, 0, wait_budget);
     }
   } else if (warp >= 2 && warp < 2 + 16) {
     // ------------------------------------------------------------ epilogue
@@ -967,7 +971,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
       const int a = item.x, b = it / args.n_base, n0 = item.y, start = item.z;
       bool ok = !abort_flag;
       for (int j = 0; j < args.n_chunks && ok; ++j) {
-        if (!mbar_wait(&d1_full[buf], (d1_ph >> buf) & 1, kWaitNs)) { fail(68); ok = false; break; }
+        if (!mbar_wait(&d1_full[buf], (d1_ph >> buf) & 1, wait_budget)) { fail(68); ok = false; break; }
         d1_ph ^= 1u << buf;
         tc_fence_after();
         float zr[CW], zi[CW], g[CW];
@@ -996,7 +1000,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
           hr[i] = *reinterpret_cast<uint32_t*>(&a0);
           hi[i] = *reinterpret_cast<uint32_t*>(&a1v);
         }
-        if (!mbar_wait(&a2_free[q2], ((a2f_ph >> q2) & 1) ^ 1, kWaitNs)) { fail(69); ok = false; break; }
+        if (!mbar_wait(&a2_free[q2], ((a2f_ph >> q2) & 1) ^ 1, wait_budget)) { fail(69); ok = false; break; }
         a2f_ph ^= 1u << q2;
         uint8_t* base = sA2 + q2 * kA2Buf + row * (RC * 2);
 #pragma unroll
@@ -1014,7 +1018,7 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
       }
       if (!ok) break;
       // gY^T of this tile: lambda' = start + 64 k + c for c in [16 cg, 16 cg + 16)
-      if (!mbar_wait(&d2_full, d2_ph, kWaitNs)) { fail(70); break; }
+      if (!mbar_wait(&d2_full, d2_ph, wait_budget)) { fail(70); break; }
       d2_ph ^= 1;
       tc_fence_after();
       const Rate2 A = P.rates2[a];
@@ -1079,11 +1083,13 @@ struct TpArgs {
   const int* wt_row0;
   float2* gy;
   int* err;
+  uint64_t wait_ns;     // budget of every barrier wait (the plan's)
 };
 
 template <int PL, int NAT, int KMV, int RCV>
 __global__ void __launch_bounds__(kFThreads, 1)
 k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
+  const uint64_t wait_budget = args.wait_ns;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   constexpr int NT = 16, RC = RCV, KM = KMV, CW = RC / 4;
@@ -1162,7 +1168,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
         const int a = item.x, b = it / args.n_base, n0 = item.y, start = item.z, K1 = item.w;
         const Rate2 A = P.rates2[a];
         const int nkb1 = (K1 + 31) / 32;
-        if (!mbar_wait(&a1_free, a1_ph ^ 1, kWaitNs)) { fail(81); break; }
+        if (!mbar_wait(&a1_free, a1_ph ^ 1, wait_budget)) { fail(81); break; }
         mbar_arrive_expect_tx(&a1_full, PL * 2 * 2 * nkb1 * 4096 + PL * kA4Plane);
         armed_a1 = (int)a1_ph;
         for (int pl = 0; pl < PL; ++pl) {
@@ -1177,7 +1183,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
         a1_ph ^= 1;
         const int g1row = (b * P.n2 + a) * args.g1_rows;
         for (int j = 0; j < args.n_chunks; ++j) {
-          if (!mbar_wait(&w_empty[wst], wph ^ 1, kWaitNs)) { fail(82); ok = false; break; }
+          if (!mbar_wait(&w_empty[wst], wph ^ 1, wait_budget)) { fail(82); ok = false; break; }
           mbar_arrive_expect_tx(&w_full[wst], kWBuf);
           armed_w |= 1u << wst;
           armed_w_par = (armed_w_par & ~(1u << wst)) | (wph << wst);
@@ -1201,8 +1207,8 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
         }
       }
       for (int i = 0; i < WB; ++i)
-        if (armed_w >> i & 1) mbar_wait(&w_full[i], armed_w_par >> i & 1, kWaitNs);
-      if (armed_a1 >= 0) mbar_wait(&a1_full, (uint32_t)armed_a1, kWaitNs);
+        if (armed_w >> i & 1) mbar_wait(&w_full[i], armed_w_par >> i & 1, wait_budget);
+      if (armed_a1 >= 0) mbar_wait(&a1_full, (uint32_t)armed_a1, wait_budget);
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ first-product issuer
@@ -1216,12 +1222,12 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
       for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it % args.n_base];
         const int nks1 = item.w / 16;
-        if (!mbar_wait(&a1_full, a1_ph, kWaitNs)) { fail(83); break; }
+        if (!mbar_wait(&a1_full, a1_ph, wait_budget)) { fail(83); break; }
         a1_ph ^= 1;
         const uint32_t a1 = smem_u32(sA1), a4 = smem_u32(sA4);
         for (int j = 0; j < args.n_chunks && ok; ++j) {
-          if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(84); ok = false; break; }
-          if (!mbar_wait(&d1_free[buf], ((d1f_ph >> buf) & 1) ^ 1, kWaitNs)) { fail(85); ok = false; break; }
+          if (!mbar_wait(&w_full[wst], wph, wait_budget)) { fail(84); ok = false; break; }
+          if (!mbar_wait(&d1_free[buf], ((d1f_ph >> buf) & 1) ^ 1, wait_budget)) { fail(85); ok = false; break; }
           d1f_ph ^= 1u << buf;
           tc_fence_after();
           const uint32_t wb = smem_u32(sW + wst * kWBuf);
@@ -1252,7 +1258,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
         mma_commit(&a1_free);
       }
       mma_commit(&mma_done);
-      mbar_wait(&mma_done, 0, kWaitNs);
+      mbar_wait(&mma_done, 0, wait_budget);
     }
   } else if (warp == kFWarpG2) {
     // ------------------------------------------------------------ last-product issuer
@@ -1263,11 +1269,11 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
       bool ok = true;
       for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         for (int j = 0; j < args.n_chunks && ok; ++j) {
-          if (!mbar_wait(&a2_full[q2], (a2_ph >> q2) & 1, kWaitNs)) { fail(86); ok = false; break; }
+          if (!mbar_wait(&a2_full[q2], (a2_ph >> q2) & 1, wait_budget)) { fail(86); ok = false; break; }
           a2_ph ^= 1u << q2;
-          if (!mbar_wait(&w_full[wst], wph, kWaitNs)) { fail(87); ok = false; break; }
+          if (!mbar_wait(&w_full[wst], wph, wait_budget)) { fail(87); ok = false; break; }
           if (j == 0) {
-            if (!mbar_wait(&d2_free, d2f_ph ^ 1, kWaitNs)) { fail(88); ok = false; break; }
+            if (!mbar_wait(&d2_free, d2f_ph ^ 1, wait_budget)) { fail(88); ok = false; break; }
             d2f_ph ^= 1;
           }
           tc_fence_after();
@@ -1307,7 +1313,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
         mma_commit(&d2_full);
       }
       mma_commit(&mma_done2);
-      mbar_wait(&mma_done2, 0, kWaitNs);
+      mbar_wait(&mma_done2, 0, wait_budget);
     }
   } else if (warp >= 2 && warp < 2 + 16) {
     // ------------------------------------------------------------ epilogue
@@ -1324,7 +1330,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
       const int a = item.x, b = it / args.n_base, n0 = item.y, start = item.z;
       bool ok = !abort_flag;
       for (int j = 0; j < args.n_chunks && ok; ++j) {
-        if (!mbar_wait(&d1_full[buf], (d1_ph >> buf) & 1, kWaitNs)) { fail(89); ok = false; break; }
+        if (!mbar_wait(&d1_full[buf], (d1_ph >> buf) & 1, wait_budget)) { fail(89); ok = false; break; }
         d1_ph ^= 1u << buf;
         tc_fence_after();
         uint32_t p1[CW], p4[CW], p3[CW], p2[CW], gu[CW], gd[CW];
@@ -1377,7 +1383,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
           tre[i] = *reinterpret_cast<uint32_t*>(&h2);
           tim[i] = *reinterpret_cast<uint32_t*>(&h3);
         }
-        if (!mbar_wait(&a2_free[q2], ((a2f_ph >> q2) & 1) ^ 1, kWaitNs)) { fail(90); ok = false; break; }
+        if (!mbar_wait(&a2_free[q2], ((a2f_ph >> q2) & 1) ^ 1, wait_budget)) { fail(90); ok = false; break; }
         a2f_ph ^= 1u << q2;
         if (TA) {
           // this warp's CW pair rows are columns [cg CW / 2, +CW / 2) of each part
@@ -1412,7 +1418,7 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
       }
       if (!ok) break;
       // gY of this tile: lambda' = start + c for c in [16 cg, 16 cg + 16)
-      if (!mbar_wait(&d2_full, d2_ph, kWaitNs)) { fail(91); break; }
+      if (!mbar_wait(&d2_full, d2_ph, wait_budget)) { fail(91); break; }
       d2_ph ^= 1;
       tc_fence_after();
       const Rate2 A = P.rates2[a];
@@ -1747,6 +1753,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   args.wt_row0 = p->d_wtb_row0;
   args.gy = gy;
   args.err = p->d_err;
+  args.wait_ns = p->wait_ns;
   int n_sm = 148;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device);
   TbMaps maps;
@@ -1801,6 +1808,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       pa.wt_row0 = p->d_wtb_row0;
       pa.gy = gy;
       pa.err = p->d_err;
+      pa.wait_ns = p->wait_ns;
 #define JTFS_LAUNCH_TCBP(PLV, NATV, KMV, RCV)                                                   \
   do {                                                                                          \
     if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_pair<PLV, NATV, KMV, RCV>,            \
@@ -1880,6 +1888,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     fa.wt_row0 = p->d_wtb_row0;
     fa.gy = gy;
     fa.err = p->d_err;
+    fa.wait_ns = p->wait_ns;
     const int grid = std::min(fa.n_items, n_sm);
 #define JTFS_LAUNCH_TCBF(NTV, RCV, PLV, NATV, KMV)                                              \
   do {                                                                                          \

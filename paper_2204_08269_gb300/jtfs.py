@@ -63,6 +63,9 @@ def lib():
         "jtfs_forward_backward_host": ([_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P,
                                         _SZ, _P], _I32),
         "jtfs_sync_status": ([_P, _P], _I32),
+        "jtfs_plan_set_wait_budget": ([_P, ctypes.c_uint64], _I32),
+        "jtfs_plan_set_check_finite": ([_P, _I32], _I32),
+        "jtfs_diagnose_wait_timeout": ([_P, ctypes.c_uint64, _P], _I32),
         "jtfs_profile_enable": ([_P, _I32], _I32),
         "jtfs_profile_read": ([_P, _P, _I32, ctypes.POINTER(_I64)], _I32),
         "jtfs_profile_stage_name": ([_I32], ctypes.c_char_p),
@@ -93,7 +96,8 @@ def exported_symbols():
     return ["jtfs_plan_create", "jtfs_plan_destroy", "jtfs_plan_shapes", "jtfs_plan_schedule",
             "jtfs_workspace_bytes", "jtfs_forward", "jtfs_backward", "jtfs_forward_backward",
             "jtfs_host_step_bytes",
-            "jtfs_forward_backward_host", "jtfs_sync_status", "jtfs_status_string",
+            "jtfs_forward_backward_host", "jtfs_sync_status", "jtfs_plan_set_wait_budget",
+            "jtfs_plan_set_check_finite", "jtfs_diagnose_wait_timeout", "jtfs_status_string",
             "jtfs_last_error", "jtfs_profile_enable", "jtfs_profile_read",
             "jtfs_profile_stage_name", "jtfs_first_order_static", "jtfs_plan_autotune",
             "jtfs_varlen_padded_length",
@@ -308,7 +312,18 @@ class JTFSPlan:
         return dict(zip(names, ms.tolist())), launches.value
 
     def sync(self):
+        """Waits for the current stream; raises JTFSError on a pending device fault, a bounded
+        wait that gave up (status 5) or a non-finite output of an earlier call (status 6)."""
         _check("jtfs_sync_status", lib().jtfs_sync_status(self._h, _stream()))
+
+    def set_wait_budget(self, seconds):
+        """Budget of every bounded device wait of later calls (default 2 s)."""
+        _check("jtfs_plan_set_wait_budget",
+               lib().jtfs_plan_set_wait_budget(self._h, int(seconds * 1e9)))
+
+    def check_finite(self, on=True):
+        """Scan every output for NaN / Inf after each call (reported by sync())."""
+        _check("jtfs_plan_set_check_finite", lib().jtfs_plan_set_check_finite(self._h, int(on)))
 
 
 class JTFSFunction(torch.autograd.Function):

@@ -76,3 +76,11 @@ def test_varlen_padded_length_rule():
             want = max(1 << int(np.ceil(np.log2(n))) if n > 1 else 1, 1 << (J + 3))
             assert jtfs.varlen_padded_length(n, J=J) == want
     assert jtfs.varlen_padded_length(0, J=4) == 0
+
+
+def test_failure_detection_calls_reject_bad_arguments_on_host(L):
+    """NULL plans are refused before any CUDA call."""
+    assert L.jtfs_plan_set_wait_budget(None, 1_000_000) == 1
+    assert L.jtfs_plan_set_check_finite(None, 1) == 1
+    assert L.jtfs_diagnose_wait_timeout(None, 100_000, None) == 1
+    assert L.jtfs_sync_status(None, None) == 1

@@ -6,6 +6,7 @@ import pytest
 
 import synth_signals as SS
 from oracle import jtfs_oracle as O
+from parity_checks import check_orders
 
 pytestmark = pytest.mark.gpu
 
@@ -91,11 +92,9 @@ def _check_forward(plan, x, op, sc, tol, idx=None):
     worst = {}
     for b in idx:
         ref = O.forward_one(x[b].astype(np.float64), op, sc)
-        for name, got in (("S0", s0), ("S1", s1), ("S2", s2)):
-            e = _rel(got[b].cpu().numpy(), ref[name])
+        got = {"S0": s0[b].cpu().numpy(), "S1": s1[b].cpu().numpy(), "S2": s2[b].cpu().numpy()}
+        for name, e in check_orders(got, ref, tol, label=f"signal {b}").items():
             worst[name] = max(worst.get(name, 0.0), e)
-    for name, e in worst.items():
-        assert e <= tol, (name, e)
     return s0, s1, s2, u1, worst
 
 
@@ -332,7 +331,7 @@ def test_fused_step_full_batch_sampled(prec):
         assert torch.equal(a, b)
     b = 23
     ref = O.forward_one(xs[b].astype(np.float64), op, sc)
-    for name, got in (("S0", s0), ("S1", s1), ("S2", s2)):
-        assert _rel(got[b].double().cpu().numpy(), ref[name]) <= TOL[prec], name
+    check_orders({"S0": s0[b].cpu().numpy(), "S1": s1[b].cpu().numpy(),
+                  "S2": s2[b].cpu().numpy()}, ref, TOL[prec], label=f"signal {b}")
     refg = O.backward_one(xs[b].astype(np.float64), g[0][b], g[1][b], g[2][b], op, sc)
     assert _rel(gx[b].double().cpu().numpy(), refg) <= GTOL[prec]
