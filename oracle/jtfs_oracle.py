@@ -54,6 +54,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+PSI_PSI, PSI_PHI, PHI_PSI, PHI_PHI = 1, 2, 4, 8
 FWHM_PER_SIGMA = 2.0 * math.sqrt(2.0 * math.log(2.0))
 XI_CAP = 0.35
 SIGMA0 = 0.1
@@ -68,7 +69,9 @@ class Config:
     """Sec. 4.2 parameters: J octaves, Q filters per octave (first order), Q2 at second
     order, J_fr / Q_fr for the frequential bank, temporal support T, frequential support F,
     signal length N.  ``average_fr`` selects Eq. 3 (True) or Eq. 4 (False).
-    ``oversampling`` o >= 0 divides every schedule stride by 2^o."""
+    ``oversampling`` o >= 0 divides every schedule stride by 2^o.  ``branches`` is a bit mask
+    of the second-order joint wavelets (Eq. 3 with either factor replaced by its lowpass):
+    1 psi_t x psi_f, 2 psi_t x phi_f (both always on), 4 phi_t x psi_f, 8 phi_t x phi_f."""
     J: int
     Q: int
     J_fr: int
@@ -79,6 +82,7 @@ class Config:
     Q2: int = 1
     average_fr: bool = True
     oversampling: int = 0
+    branches: int = 3
 
 
 WORKLOADS = {
@@ -207,6 +211,8 @@ class Plan:
             raise ValueError("N and T must be powers of two with T <= N")
         if cfg.F < 1 or cfg.Q < 1 or cfg.Q2 < 1 or cfg.Q_fr < 1:
             raise ValueError("F, Q, Q2, Q_fr must be >= 1")
+        if cfg.branches & (PSI_PSI | PSI_PHI) != (PSI_PSI | PSI_PHI) or cfg.branches & ~15:
+            raise ValueError("branches must hold psi_t x psi_f and psi_t x phi_f (bits 1, 2)")
         self.cfg = cfg
         N, T = cfg.N, cfg.T
         self.N, self.T = N, T
@@ -255,6 +261,12 @@ class Plan:
         self.W = self.h[:, idx]                               # [C, n1, n1] Toeplitz
         lo = np.arange(self.n_lam_out)
         self.PhiF = self.phi_F[(lo[:, None] * self.s_F - lam[None, :]) % self.N_fr]
+        # phi_t paths (time lowpass phi_T in place of psi_alpha): the spin-up scales beta, then
+        # the phi_F channel.  Their input U1 * phi_T is real, so the spin-down channel gives the
+        # conjugate Z and the same modulus: one spin is kept.
+        self.phi_channels = (list(range(self.n_fr)) if cfg.branches & PHI_PSI else []) + (
+            [2 * self.n_fr] if cfg.branches & PHI_PHI else [])
+        self.n_phi = len(self.phi_channels)
 
     # -- pooling matrices ------------------------------------------------------------
     def pool_T_matrix(self, s: int):
@@ -264,9 +276,19 @@ class Plan:
         m = np.arange(L)
         return s * self.phi_T[(t[:, None] * self.T - m[None, :] * s) % self.N]
 
+    def pool_T_matrix_at(self, s_in: int, s_out: int):
+        """Phi[m, n] = s_in * phi_T[(m s_out - n s_in) mod N]: the Riemann sum of phi_T taking a
+        row at stride s_in to every s_out-th sample (s_out = T gives pool_T_matrix)."""
+        m = np.arange(self.N // s_out)
+        n = np.arange(self.N // s_in)
+        return s_in * self.phi_T[(m[:, None] * s_out - n[None, :] * s_in) % self.N]
+
     def shapes(self):
-        return dict(n1=self.n1, n2=self.n2, n_fr=self.n_fr, C=self.C, n_t=self.n_t,
-                    n_lam_out=self.n_lam_out, N_fr=self.N_fr, s_F=self.s_F)
+        out = dict(n1=self.n1, n2=self.n2, n_fr=self.n_fr, C=self.C, n_t=self.n_t,
+                   n_lam_out=self.n_lam_out, N_fr=self.N_fr, s_F=self.s_F)
+        if self.n_phi:
+            out["n_phi"] = self.n_phi
+        return out
 
 
 # ----------------------------------------------------------------------------------------
@@ -308,6 +330,9 @@ class Schedule:
             self.lam_min[a] = int(np.argmax(keep)) if keep.any() else n1
         self.L1 = N // self.s1
         self.L2 = N // self.s2
+        # phi_t paths: the band [0, 4 sigma_T] of phi_T, sampled like a time wavelet's band
+        self.s_phi = 1 if self.exact else _pow2_stride(
+            1.0 / (2.0 * BAND_SIGMAS * plan.sigma_T), int(oversampling), T)
 
 
 # ----------------------------------------------------------------------------------------
@@ -349,6 +374,17 @@ class Operators:
 
     def pool_T_T(self, g, s):
         return g @ self.PhiT(s)
+
+    # U1 row at stride s_in -> U1 * phi_T at stride s_out (the phi_t paths' time filter)
+    def lowpass_to(self, u, s_in, s_out):
+        key = (s_in, s_out)
+        if key not in self._phiT:
+            self._phiT[key] = self.p.pool_T_matrix_at(s_in, s_out)
+        return u @ self._phiT[key].T
+
+    def lowpass_to_T(self, g, s_in, s_out):
+        self.lowpass_to(np.zeros(self.p.N // s_in), s_in, s_out)
+        return g @ self._phiT[(s_in, s_out)]
 
     # second order, time: U1 row lambda' -> Y_alpha row at stride s_alpha (Eq. 3, t axis)
     def psi2(self, u, lam, a):
@@ -423,27 +459,51 @@ def forward_one(x, plan: Plan, sched: Schedule, engine: str = "fft", keep: bool 
             Z = ops.wfr(Y, c, lm)
             S2[a, c] = ops.pool_F(ops.pool_T(np.abs(Z), sa))
     out = dict(S0=S0, S1=S1, S2=S2)
+    if plan.n_phi:
+        # phi_t x psi_f and phi_t x phi_f: Eq. 3 with the time lowpass as the time filter
+        sp = int(sched.s_phi)
+        Yp = np.stack([ops.lowpass_to(U1[lam], int(sched.s1[lam]), sp) for lam in range(plan.n1)])
+        S2phi = np.zeros((plan.n_phi, plan.n_lam_out, plan.n_t))
+        for q, c in enumerate(plan.phi_channels):
+            S2phi[q] = ops.pool_F(ops.pool_T(np.abs(ops.wfr(Yp, c)), sp))
+        out["S2phi"] = S2phi
+        if keep:
+            out["Yphi"] = Yp
     if keep:
         out.update(z=z, U1=U1, Y=Ys)
     return out
 
 
 def forward(x, plan: Plan, sched: Schedule, engine: str = "fft"):
-    """Batched forward: x [B, N] -> dict of S0 [B, n_t], S1 [B, n1, n_t], S2 [B, n2, C, n_lo, n_t]."""
+    """Batched forward: x [B, N] -> dict of S0 [B, n_t], S1 [B, n1, n_t], S2 [B, n2, C, n_lo, n_t]
+    (and S2phi [B, n_phi, n_lo, n_t] when phi_t paths are selected)."""
     X = np.atleast_2d(np.asarray(x, dtype=np.float64))
     outs = [forward_one(xb, plan, sched, engine) for xb in X]
-    return {k: np.stack([o[k] for o in outs]) for k in ("S0", "S1", "S2")}
+    return {k: np.stack([o[k] for o in outs]) for k in outs[0]}
 
 
-def backward_one(x, gS0, gS1, gS2, plan: Plan, sched: Schedule, engine: str = "fft"):
-    """Gradient w.r.t. x of <gS0, S0> + <gS1, S1> + <gS2, S2> (Sec. 5: reverse-ordered
-    adjoints).  Modulus Jacobian: d|z| = Re(conj(z) dz) / |z|, taken as 0 at z = 0."""
+def backward_one(x, gS0, gS1, gS2, plan: Plan, sched: Schedule, engine: str = "fft",
+                 gS2phi=None):
+    """Gradient w.r.t. x of <gS0, S0> + <gS1, S1> + <gS2, S2> (+ <gS2phi, S2phi>) (Sec. 5:
+    reverse-ordered adjoints).  Modulus Jacobian: d|z| = Re(conj(z) dz) / |z|, taken as 0 at
+    z = 0."""
     ops = Operators(plan, sched, engine)
     x = np.asarray(x, dtype=np.float64)
     xh = ops.x_hat(x)
     z = [ops.psi1(xh, lam) for lam in range(plan.n1)]
     U1 = [np.abs(v) for v in z]
     gU1 = [np.zeros_like(u) for u in U1]
+    if plan.n_phi and gS2phi is not None:
+        # phi_t paths: Y = U1 * phi_T is real, so its cotangent is Re(W^H gZ)
+        sp = int(sched.s_phi)
+        Yp = np.stack([ops.lowpass_to(U1[lam], int(sched.s1[lam]), sp) for lam in range(plan.n1)])
+        gYp = np.zeros_like(Yp)
+        for q, c in enumerate(plan.phi_channels):
+            Z = ops.wfr(Yp, c)
+            g_abs = ops.pool_T_T(ops.pool_F_T(gS2phi[q]), sp)
+            gYp += np.real(ops.wfr_T(g_abs * _safe_phase(Z), c))
+        for lam in range(plan.n1):
+            gU1[lam] += ops.lowpass_to_T(gYp[lam], int(sched.s1[lam]), sp)
     for a in range(plan.n2):
         if sched.skip2[a]:
             continue
@@ -467,9 +527,11 @@ def backward_one(x, gS0, gS1, gS2, plan: Plan, sched: Schedule, engine: str = "f
     return ops.x_hat_T(g_xh) + ops.pool_T_T(gS0, 1)
 
 
-def backward(x, gS0, gS1, gS2, plan: Plan, sched: Schedule, engine: str = "fft"):
+def backward(x, gS0, gS1, gS2, plan: Plan, sched: Schedule, engine: str = "fft",
+             gS2phi=None):
     X = np.atleast_2d(np.asarray(x, dtype=np.float64))
-    return np.stack([backward_one(X[b], gS0[b], gS1[b], gS2[b], plan, sched, engine)
+    return np.stack([backward_one(X[b], gS0[b], gS1[b], gS2[b], plan, sched, engine,
+                                  None if gS2phi is None else gS2phi[b])
                      for b in range(X.shape[0])])
 
 
@@ -507,7 +569,24 @@ def forward_exact_direct(x, plan: Plan):
                     S2[a, c, o] = sum(phiF[(lo[o] - l) % plan.N_fr] * pooled_t[l] for l in lam)
             else:
                 S2[a, c] = pooled_t
-    return dict(S0=S0, S1=S1, S2=S2)
+    out = dict(S0=S0, S1=S1, S2=S2)
+    if plan.n_phi:
+        Y = np.stack([circconv_direct(U1[l], phiT) for l in range(plan.n1)])
+        S2phi = np.zeros((plan.n_phi, plan.n_lam_out, plan.n_t))
+        for q, c in enumerate(plan.phi_channels):
+            Z = np.zeros(Y.shape, dtype=np.complex128)
+            for l in range(plan.n1):
+                for lp in range(plan.n1):
+                    Z[l] += h[c][(l - lp) % plan.N_fr] * Y[lp]
+            pooled_t = np.stack([circconv_direct(np.abs(Z[l]), phiT)[t] for l in range(plan.n1)])
+            if plan.cfg.average_fr:
+                lo = np.arange(plan.n_lam_out) * plan.s_F
+                for o in range(plan.n_lam_out):
+                    S2phi[q, o] = sum(phiF[(lo[o] - l) % plan.N_fr] * pooled_t[l] for l in lam)
+            else:
+                S2phi[q] = pooled_t
+        out["S2phi"] = S2phi
+    return out
 
 
 def stage1_full_rate(x, plan: Plan):

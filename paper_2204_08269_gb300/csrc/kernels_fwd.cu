@@ -1,7 +1,7 @@
 // Forward JTFS kernels (Sec. 2, Eq. 2-4) on CUDA cores, FP32.
 //
 //   k_xfft_sub / k_xfft_combine : x-hat[k] for 0 <= k < N/2 (decimated length-N FFT)
-//   k_s0                        : S0[t] = sum_n phi_T[(tT - n) mod N] x[n] (from x-hat)
+//   k_s0                        : S0[t] = sum_n phi_T[(tT - n) mod N] x[n] (compensated sum)
 //   k_scalogram                 : per (lambda, signal): periodise x-hat * psi-hat_lambda to
 //                                 L_lambda bins, inverse FFT, modulus -> U1 row (checkpoint),
 //                                 FFT of the row -> U1-hat, S1 row (the Riemann sum of
@@ -21,46 +21,35 @@
 namespace jtfs {
 namespace {
 
-__device__ __forceinline__ float block_sum(float v, float* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
-  if (w == 0)
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  return v;
-}
-
-// S0[t] = sum_n phi_T[(tT - n) mod N] x[n].  When phi-hat stays below the Nyquist bin it is
-// (1 / N) sum_k phi-hat[k] x-hat[k] e^{2 pi i k t / n_t} over the bins |k| <= phiT_kmax (x real:
-// bins k > 0 twice), computed from x-hat (one warp per frame); otherwise in the time domain.
-__global__ void k_s0(DevPlan P, const float* __restrict__ x, const float2* __restrict__ xh,
-                     float* __restrict__ s0) {
-  __shared__ float red[32];
+// S0[t] = sum_n phi_T[(tT - n) mod N] x[n], in the time domain from x itself.  For band-pass
+// inputs S0 is a small difference of large terms (x has almost no energy where phi-hat lives),
+// so the sum is compensated: every thread keeps a Neumaier (sum, correction) pair of FP32
+// values, and the pairs are added in FP64.  The spectral form (1 / N) sum_k phi-hat[k] x-hat[k]
+// e^{2 pi i k t / n_t} would inherit the FP32 FFT's rounding of x-hat, which for such inputs is
+// of the size of S0 itself.
+__global__ void k_s0(DevPlan P, const float* __restrict__ x, float* __restrict__ s0) {
+  __shared__ double red[32];
   const int t = blockIdx.x, b = blockIdx.y;
-  if (P.phiT_kmax < (P.N >> 1)) {
-    if (threadIdx.x >= 32) return;
-    const float2* hb = xh + (size_t)b * (P.N >> 1);
-    float acc = 0.f;
-    for (int k = threadIdx.x; k <= P.phiT_kmax; k += 32) {
-      const float2 u = hb[k];
-      float sn, cs;
-      sincospif(2.f * (float)((k * t) & (P.n_t - 1)) / (float)P.n_t, &sn, &cs);
-      acc += (k == 0 ? 1.f : 2.f) * __ldg(&P.phiThat[k]) * (u.x * cs - u.y * sn);
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) s0[(size_t)b * P.n_t + t] = acc / (float)P.N;
-    return;
-  }
   const float* xb = x + (size_t)b * P.N;
   const int tT = t * P.T;
-  float acc = 0.f;
-  for (int n = threadIdx.x; n < P.N; n += blockDim.x)
-    acc += __ldg(&P.phiT[(tT - n) & (P.N - 1)]) * xb[n];
-  acc = block_sum(acc, red);
-  if (threadIdx.x == 0) s0[(size_t)b * P.n_t + t] = acc;
+  float sum = 0.f, cor = 0.f;
+  for (int n = threadIdx.x; n < P.N; n += blockDim.x) {
+    const float v = __fmul_rn(__ldg(&P.phiT[(tT - n) & (P.N - 1)]), xb[n]);
+    const float u = __fadd_rn(sum, v);
+    cor = __fadd_rn(cor, fabsf(sum) >= fabsf(v) ? __fadd_rn(__fsub_rn(sum, u), v)
+                                                : __fadd_rn(__fsub_rn(v, u), sum));
+    sum = u;
+  }
+  double acc = (double)sum + (double)cor;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = acc;
+  __syncthreads();
+  if (w == 0) {
+    acc = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (l == 0) s0[(size_t)b * P.n_t + t] = (float)acc;
+  }
 }
 
 __global__ void __launch_bounds__(kFftThreads)
@@ -394,7 +383,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   }
   {
     StageScope sc(p, kStS0, st, 1);
-    k_s0<<<dim3(p->n_t, B), 256, 0, st>>>(d, x, w.xh, s0);
+    k_s0<<<dim3(p->n_t, B), 256, 0, st>>>(d, x, s0);
   }
   {
     StageScope sc(p, kStScalogram, st, 1);
@@ -519,7 +508,7 @@ jtfs_status launch_first_order_static(const jtfs_plan* p, const float* x, int B,
   const DevPlan& d = p->dp;
   k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, xsub);
   k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, xsub, xh);
-  k_s0<<<dim3(p->n_t, B), 256, 0, st>>>(d, x, xh, s0);
+  k_s0<<<dim3(p->n_t, B), 256, 0, st>>>(d, x, s0);
   k_scalogram<<<dim3(p->n1, B), kRowLaunch, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, xh, u1, uh, s1);
   return cuda_check(cudaGetLastError(), "first-order static launch");
 }

@@ -1,0 +1,121 @@
+"""Texture resynthesis by gradient descent in JTFS space (Sec. 5, "Texture Synthesis").
+
+Starting from white noise y_0, the trial signals are updated so that the normalised error
+E(y) = ||S x - S y|| / ||S x|| (S = the concatenated S0, S1, S2 of one signal) decreases.  The
+gradient of E comes from the library's hand-written adjoint chain (``JTFSFunction``: forward
+with the first-order scalogram as the only checkpoint, then ``jtfs_backward``); the loss
+reduction and the update are a few elementwise PyTorch operations on the device.
+
+Two update rules:
+  * ``"adam"``: Adam on y with learning rate ``lr`` (default 1e-2 times the target's RMS).
+  * ``"bold"``: the bold-driver heuristic the paper uses.  Each signal keeps its own step
+    size mu: a trial y - mu grad E that lowers E is accepted and mu grows by ``inc``; one that
+    does not is rejected and mu shrinks by ``dec``.  The step descends (y - mu grad E), the
+    reading of the paper's garbled update sign.  Every iteration costs one forward and one
+    backward, accepted or not.
+
+Each signal of the batch is an independent problem (the loss is the sum of the per-signal
+E), so a batch resynthesises B textures at once.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from .jtfs import JTFS
+
+
+def _flat(s0, s1, s2):
+    B = s0.shape[0]
+    return torch.cat([s0.reshape(B, -1), s1.reshape(B, -1), s2.reshape(B, -1)], dim=1)
+
+
+def normalised_error(s_y, s_x):
+    """E per signal: ||S x - S y|| / ||S x|| over all orders (tensors [B, paths])."""
+    return (s_y - s_x).norm(dim=1) / s_x.norm(dim=1)
+
+
+class Resynthesis:
+    """Gradient-descent resynthesis of a batch of target signals ``target`` [B, N] (device,
+    float32) from seeded white noise of the targets' RMS.  ``cfg``: the transform's Sec. 4.2
+    parameters (J, Q, J_fr, Q_fr, T, F and optional keywords of ``JTFSPlan``)."""
+
+    def __init__(self, target, method="adam", lr=None, seed=0, inc=1.1, dec=0.5, **cfg):
+        if method not in ("adam", "bold"):
+            raise ValueError("method must be 'adam' or 'bold'")
+        self.B, N = target.shape
+        self.model = JTFS(N, **cfg)
+        self.method = method
+        with torch.no_grad():
+            self.s_x = _flat(*self.model(target.contiguous()))
+        rms = float(target.pow(2).mean().sqrt())
+        gen = torch.Generator(device=target.device).manual_seed(seed)
+        self.y = (torch.randn(target.shape, device=target.device, generator=gen) * rms)
+        self.y.requires_grad_(True)
+        if method == "adam":
+            self.opt = torch.optim.Adam([self.y], lr=lr if lr is not None else 1e-2 * rms)
+        else:
+            self.inc, self.dec = inc, dec
+            self.mu = None
+            self.E, self.g = self._eval(self.y)
+            # first step moves each signal by a tenth of its norm
+            self.mu = 0.1 * self.y.detach().norm(dim=1) / self.g.norm(dim=1).clamp_min(1e-30)
+
+    def _eval(self, y):
+        """(E per signal, dE/dy) at y: one forward and one backward through the library."""
+        y = y.detach().requires_grad_(True)
+        E = normalised_error(_flat(*self.model(y)), self.s_x)
+        (g,) = torch.autograd.grad(E.sum(), y)
+        return E.detach(), g
+
+    def step(self):
+        """One iteration; returns E per signal: for Adam at the iterate the update starts
+        from, for the bold driver at the iterate it keeps."""
+        if self.method == "adam":
+            self.opt.zero_grad(set_to_none=True)
+            E = normalised_error(_flat(*self.model(self.y)), self.s_x)
+            E.sum().backward()
+            self.opt.step()
+            return E.detach()
+        trial = self.y.detach() - self.mu[:, None] * self.g
+        E_t, g_t = self._eval(trial)
+        better = E_t < self.E
+        with torch.no_grad():
+            keep = better[:, None]
+            self.y = torch.where(keep, trial, self.y.detach())
+            self.g = torch.where(keep, g_t, self.g)
+            self.E = torch.where(better, E_t, self.E)
+            self.mu = torch.where(better, self.mu * self.inc, self.mu * self.dec)
+        return self.E
+
+    def run(self, steps, timed=True):
+        """``steps`` iterations.  Returns {"E": mean E per iteration, "E_last": E per signal
+        after the last one, "ms": CUDA-event milliseconds per iteration}."""
+        hist, ms = [], []
+        for _ in range(steps):
+            if timed:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+            E = self.step()
+            if timed:
+                b.record()
+            hist.append(E)
+            if timed:
+                ms.append((a, b))
+        torch.cuda.synchronize()
+        return {"E": [float(e.mean()) for e in hist],
+                "E_last": hist[-1].cpu() if hist else None,
+                "ms": [a.elapsed_time(b) for a, b in ms]}
+
+    def signal(self):
+        return self.y.detach()
+
+
+def converged_fraction(history, fraction):
+    """First iteration (1-based) whose mean E is at most ``fraction``; None if never."""
+    for i, e in enumerate(history):
+        if e <= fraction and not math.isnan(e):
+            return i + 1
+    return None

@@ -62,10 +62,11 @@ def _biquad_bandpass(x, fc, q, sr):
     return lfilter(b, a, x)
 
 
-def click_train_batch(B: int, N: int, seed: int, sr: float = SR):
+def click_train_batch(B: int, N: int, seed: int, sr: float = SR, noise_db=None):
     """Poisson click trains (rate uniform in [5, 40] Hz); every click is an impulse
     through its own random resonator (centre uniform in [200, 6000] Hz, Q log-uniform
-    in [5, 30]).  Normalised to unit RMS."""
+    in [5, 30]).  Normalised to unit RMS.  With ``noise_db`` (e.g. -40), white noise at that
+    level re the unit RMS is added from the signal's own stream (after the clicks)."""
     out = np.empty((B, N), dtype=np.float32)
     for b, rng in enumerate(_streams(seed, B)):
         rate = rng.uniform(5.0, 40.0)
@@ -81,7 +82,10 @@ def click_train_batch(B: int, N: int, seed: int, sr: float = SR):
             imp[0] = rng.uniform(0.5, 1.0) * (1.0 if rng.random() < 0.5 else -1.0)
             y[p:p + span] += _biquad_bandpass(imp, fc, q, sr)
         rms = np.sqrt(np.mean(y * y))
-        out[b] = y / (rms if rms > 0 else 1.0)
+        y = y / (rms if rms > 0 else 1.0)
+        if noise_db is not None:
+            y = y + rng.standard_normal(N) * 10.0 ** (noise_db / 20.0)
+        out[b] = y
     return out
 
 

@@ -3,7 +3,13 @@ parameters (J = 13, Q = 16, J_fr = 4, Q_fr = 2, T = 2^13, F = 16; click-train in
 uneven-length batch with one signal in each padded length of the 2^13..2^17 mix (2^15, 2^16,
 2^17 at J = 12).  The CUDA path runs in the launch configuration of its workload (B = 16 at
 N = 2^17; one uneven-length call) and the FP64 oracle recomputes sampled signals: per-order
-relative L2 and every visible S1 row and S2 (alpha, c) slice, g_x to 1e-3 (5e-2 for BF16)."""
+relative L2 and every visible S1 row and S2 (alpha, c) slice, g_x to 1e-3 (5e-2 for BF16).
+
+Gradients are compared on inputs with a white-noise floor 40 dB down: on bare click trains
+(and in a zero-padded tail) some first-order rows hold no energy, the modulus Jacobian z / |z|
+there is set by rounding, and the FP64 oracle's own gradient moves by order one under a 1e-7
+perturbation of the input (pinned on the CPU by test_gradient_conditioning_needs_a_noise_floor).
+The forward outputs are well conditioned and are compared on the bare inputs."""
 import numpy as np
 import pytest
 
@@ -46,19 +52,22 @@ def test_workload3_fused_step_sampled(L, oracle3, prec):
     assert (sh.n1, sh.n2, sh.C, sh.n_lam_out, sh.n_t) == (op.n1, op.n2, op.C, op.n_lam_out,
                                                           op.n_t)
     B = 16
-    xs = SS.workload_signals(3, B, oc.N)
     rng = np.random.default_rng(2 ** 17)
     g = [rng.standard_normal((B,) + tuple(f(1)[1:])).astype(np.float32)
          for f in (sh.s0, sh.s1, sh.s2)]
-    s0, s1, s2, gx = plan.forward_backward(torch.from_numpy(xs).cuda(),
-                                           *[torch.from_numpy(v).cuda() for v in g])
-    torch.cuda.synchronize()
+    gd = [torch.from_numpy(v).cuda() for v in g]
     b = 9
-    x64 = xs[b].astype(np.float64)
-    ref = O.forward_one(x64, op, sc)
+    # forward on the bare click trains
+    xs = SS.workload_signals(3, B, oc.N)
+    s0, s1, s2, _ = plan.forward_backward(torch.from_numpy(xs).cuda(), *gd)
+    torch.cuda.synchronize()
+    ref = O.forward_one(xs[b].astype(np.float64), op, sc)
     check_orders({"S0": s0[b].cpu().numpy(), "S1": s1[b].cpu().numpy(),
                   "S2": s2[b].cpu().numpy()}, ref, TOL[prec], label=f"N=2^17 signal {b}")
-    gref = O.backward_one(x64, g[0][b], g[1][b], g[2][b], op, sc)
+    # gradient on the click trains with a -40 dB floor
+    xn = SS.click_train_batch(B, oc.N, SS.BASE_SEED + 3, noise_db=-40.0)
+    _, _, _, gx = plan.forward_backward(torch.from_numpy(xn).cuda(), *gd)
+    gref = O.backward_one(xn[b].astype(np.float64), g[0][b], g[1][b], g[2][b], op, sc)
     assert relative_l2(gx[b].cpu().numpy(), gref) <= GTOL[prec]
 
 
@@ -87,15 +96,19 @@ VARLEN_CFG = dict(J=12, Q=16, J_fr=4, Q_fr=2, T=2 ** 12, F=16)
 VARLEN_LENGTHS = [9001, 40000, 100003]
 
 
+def _varlen_parts(lengths, floor):
+    gens = [SS.amfm_batch, lambda B, n, seed: SS.click_train_batch(B, n, seed, noise_db=floor),
+            SS.amfm_batch]
+    return [gen(1, n, SS.BASE_SEED + 500 + i)[0] for i, (gen, n) in
+            enumerate(zip(gens, lengths))]
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_varlen_workload_lengths_match_oracle(L, prec):
     """An uneven-length batch (lengths 9001, 40000, 100003: padded to 2^15, 2^16, 2^17; an
     AM/FM tone, a click train, an AM/FM tone) in one jtfs_varlen_forward_backward call.  Each
-    signal is checked against the oracle on its zero-padded copy: S on the kept frames and
-    g_x on its own samples, for cotangents that vanish outside the kept frames."""
-    gens = [SS.amfm_batch, SS.click_train_batch, SS.amfm_batch]
-    parts = [gen(1, n, SS.BASE_SEED + 500 + i)[0] for i, (gen, n) in
-             enumerate(zip(gens, VARLEN_LENGTHS))]
+    signal's S on the kept frames is checked against the oracle on its zero-padded copy."""
+    parts = _varlen_parts(VARLEN_LENGTHS, None)
     v = L.JTFSVarlen(VARLEN_LENGTHS, **VARLEN_CFG, precision=prec)
     x = torch.from_numpy(np.concatenate(parts).astype(np.float32)).cuda()
     rng = np.random.default_rng(31)
@@ -119,12 +132,34 @@ def test_varlen_workload_lengths_match_oracle(L, prec):
                "S2": s2[v.s2_off[i]:v.s2_off[i + 1]].reshape(op.n2, op.C, op.n_lam_out, fr)}
         kept = {"S0": ref["S0"][:fr], "S1": ref["S1"][:, :fr], "S2": ref["S2"][..., :fr]}
         check_orders(got, kept, TOL[prec], label=f"len {n} (N = {Np})")
+    assert padded == [2 ** 15, 2 ** 16, 2 ** 17]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_varlen_workload_gradients_match_oracle(L, prec):
+    """g_x of an uneven-length batch of one signal per padded length, each filling it (2^15,
+    2^16, 2^17 samples: no zero tail, whose empty rows would leave the gradient set by
+    rounding), the click train with a -40 dB floor; cotangents on every kept frame.  Checked
+    against the oracle per signal.  Zero-padded signals' gradients are compared with the
+    fixed-length transform of the padded copy in the uneven-length tests."""
+    lengths = [2 ** 15, 2 ** 16, 2 ** 17]
+    parts = _varlen_parts(lengths, -40.0)
+    v = L.JTFSVarlen(lengths, **VARLEN_CFG, precision=prec)
+    x = torch.from_numpy(np.concatenate(parts).astype(np.float32)).cuda()
+    rng = np.random.default_rng(37)
+    g = [rng.standard_normal(int(o[-1])).astype(np.float32) for o in (v.s0_off, v.s1_off,
+                                                                       v.s2_off)]
+    gx = v.forward_backward(x, [torch.from_numpy(a).cuda() for a in g])[3].cpu().numpy()
+    T = VARLEN_CFG["T"]
+    for i, n in enumerate(lengths):
+        op = O.Plan(O.Config(N=n, **VARLEN_CFG))
+        sc = O.Schedule(op, 0)
+        fr = n // T
         g0 = np.zeros(op.n_t)
         g1 = np.zeros((op.n1, op.n_t))
         g2 = np.zeros((op.n2, op.C, op.n_lam_out, op.n_t))
         g0[:fr] = g[0][v.s0_off[i]:v.s0_off[i + 1]]
         g1[:, :fr] = g[1][v.s1_off[i]:v.s1_off[i + 1]].reshape(op.n1, fr)
         g2[..., :fr] = g[2][v.s2_off[i]:v.s2_off[i + 1]].reshape(op.n2, op.C, op.n_lam_out, fr)
-        gref = O.backward_one(xp, g0, g1, g2, op, sc)[:n]
-        assert relative_l2(gx[v.x_off[i]:v.x_off[i] + n], gref) <= GTOL[prec], (n, Np)
-    assert padded == [2 ** 15, 2 ** 16, 2 ** 17]
+        gref = O.backward_one(parts[i].astype(np.float64), g0, g1, g2, op, sc)
+        assert relative_l2(gx[v.x_off[i]:v.x_off[i] + n], gref) <= GTOL[prec], n
