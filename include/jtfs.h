@@ -55,6 +55,17 @@ typedef enum {
   JTFS_PREC_FP32_SIMT = 3   /* CUDA cores, plain FP32 (the comparison form) */
 } jtfs_precision;
 
+/* Second-order joint wavelets (Eq. 2-3 with the time wavelet psi_t or the log-frequency
+ * wavelet psi_f replaced by its lowpass phi_T or phi_F).  The psi_t paths (PSI_PSI, PSI_PHI)
+ * are always computed; PHI_PSI and PHI_PHI add the phi_t paths. */
+typedef enum {
+  JTFS_BRANCH_PSI_PSI = 1,   /* psi_alpha(t) psi_{beta,theta}(lambda), both spins */
+  JTFS_BRANCH_PSI_PHI = 2,   /* psi_alpha(t) phi_F(lambda) */
+  JTFS_BRANCH_PHI_PSI = 4,   /* phi_T(t) psi_{beta,+1}(lambda): one spin, the input X * phi_T
+                                being real makes the other spin's modulus the same */
+  JTFS_BRANCH_PHI_PHI = 8    /* phi_T(t) phi_F(lambda) */
+} jtfs_branch;
+
 /* Sec. 4.2 parameters.  T and F must be >= 1; T a power of two <= N.  Q2 is the number of
  * second-order time wavelets per octave (1 in the paper).  oversampling o >= 0 divides every
  * subsampling stride by 2^o. */
@@ -64,17 +75,26 @@ typedef struct {
   int32_t average_fr;    /* 1: Eq. 3 (phi_F pooling, lambda stride 2^floor(log2 F)); 0: Eq. 4 */
   int32_t oversampling;
   int32_t precision;     /* jtfs_precision */
-  int32_t reserved[5];   /* must be 0 */
+  int32_t out_3d;        /* 1: S0, S1 and S2 in their own buffers (S1 2-D, S2 3-D per path);
+                            0: one 2-D buffer per signal, [paths][n_t] with S0, S1 and S2
+                            concatenated along the path axis (Sec. 4.2's two output modes) */
+  int32_t branches;      /* bit mask of jtfs_branch; 0 means PSI_PSI | PSI_PHI.  The phi_t
+                            paths need oversampling 0 (their input is then S1 itself) */
+  int32_t reserved[3];   /* must be 0 */
 } jtfs_config;
 
-/* Output sizes.  S0 [B, n_t]; S1 [B, n1, n_t]; S2 [B, n2, C, n_lam_out, n_t] with channel
- * c < n_fr = (beta = c, theta = +1), n_fr <= c < 2 n_fr = (beta = c - n_fr, theta = -1),
- * c = 2 n_fr = the psi_t x phi_F branch.  lambda increases with frequency (theta = -1 is an
- * upward slope, Sec. 2).  u1_len is the checkpointed scalogram's length per signal (rows
- * packed at their own strides). */
+/* Output sizes.  S0 [B, n_t]; S1 [B, n1, n_t]; S2 [B, s2_paths, n_lam_out, n_t].  The S2 paths
+ * are first the psi_t paths, [n2][C] with channel c < n_fr = (beta = c, theta = +1),
+ * n_fr <= c < 2 n_fr = (beta = c - n_fr, theta = -1), c = 2 n_fr = the psi_t x phi_F branch;
+ * then the n_phi phi_t paths: phi_T x psi_{beta,+1} for beta < n_fr (PHI_PSI) and phi_T x
+ * phi_F (PHI_PHI).  lambda increases with frequency (theta = -1 is an upward slope, Sec. 2).
+ * With out_3d = 0 the single output holds, per signal, out_rows = 1 + n1 + s2_paths * n_lam_out
+ * rows of n_t frames: S0, the n1 rows of S1, then S2 path by path.  u1_len is the checkpointed
+ * scalogram's length per signal (rows packed at their own strides). */
 typedef struct {
   int64_t N, n1, n2, n_fr, C, n_t, n_lam_out, N_fr, s_F;
   int64_t s0_len, s1_len, s2_len, u1_len;
+  int64_t n_phi, s2_paths, out_rows;
 } jtfs_shapes;
 
 typedef struct jtfs_plan jtfs_plan;
@@ -100,13 +120,15 @@ jtfs_status jtfs_workspace_bytes(const jtfs_plan* plan, int64_t B, int32_t with_
                                  size_t* out);
 
 /* Forward transform of x [B, N] (device).  Writes s0, s1, s2 (device, sizes from
- * jtfs_plan_shapes).  u1_ckpt (device, [B, u1_len]) receives the first-order scalogram
+ * jtfs_plan_shapes).  With out_3d = 0, s0 receives the single [B, out_rows, n_t] output and
+ * s1, s2 must be NULL.  u1_ckpt (device, [B, u1_len]) receives the first-order scalogram
  * checkpoint when not NULL; jtfs_backward needs it.  B = 0 is a no-op. */
 jtfs_status jtfs_forward(const jtfs_plan* plan, const float* x, int64_t B, float* s0, float* s1,
                          float* s2, float* u1_ckpt, void* ws, size_t ws_bytes, void* stream);
 
 /* Backward: g_x [B, N] = d<g, S(x)>/dx for cotangents g_s0, g_s1, g_s2 (device, same shapes
- * as the outputs; any may be NULL for zero).  Needs the forward's u1_ckpt for the same x.
+ * as the outputs; any may be NULL for zero; with out_3d = 0, g_s0 holds the single output's
+ * cotangent and g_s1, g_s2 must be NULL).  Needs the forward's u1_ckpt for the same x.
  * The modulus Jacobian d|z| = Re(conj(z) dz) / |z| is taken as 0 at z = 0. */
 jtfs_status jtfs_backward(const jtfs_plan* plan, const float* x, const float* u1_ckpt,
                           int64_t B, const float* g_s0, const float* g_s1, const float* g_s2,

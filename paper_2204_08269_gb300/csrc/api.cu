@@ -87,7 +87,13 @@ jtfs_status validate_cfg(const jtfs_config* c, int64_t N) {
   if (c->average_fr != 0 && c->average_fr != 1) { set_error("average_fr must be 0 or 1"); return JTFS_ERR_INVALID_ARG; }
   if (c->oversampling < 0 || c->oversampling > 16) { set_error("oversampling must be in [0, 16]"); return JTFS_ERR_INVALID_ARG; }
   if (c->precision < 0 || c->precision > 3) { set_error("unknown precision"); return JTFS_ERR_INVALID_ARG; }
-  for (int i = 0; i < 5; ++i)
+  if (c->out_3d != 0 && c->out_3d != 1) { set_error("out_3d must be 0 or 1"); return JTFS_ERR_INVALID_ARG; }
+  const int br = c->branches == 0 ? (JTFS_BRANCH_PSI_PSI | JTFS_BRANCH_PSI_PHI) : c->branches;
+  if ((br & ~15) || (br & 3) != 3) {
+    set_error("branches must hold PSI_PSI and PSI_PHI, plus any of PHI_PSI, PHI_PHI");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < 3; ++i)
     if (c->reserved[i] != 0) { set_error("reserved fields must be 0"); return JTFS_ERR_INVALID_ARG; }
   return JTFS_OK;
 }
@@ -175,6 +181,22 @@ size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* bas
     W.gu1 = (float*)take(Bz * p->u1_len * 4);
     W.gf = (float2*)take(Bz * p->u1_len * 8);
     W.gxh = (float2*)take(Bz * (p->N / 2) * 8);
+  }
+  const size_t n0 = Bz * p->n_t, n1 = Bz * p->n1 * p->n_t, n2 = Bz * (size_t)p->dp.s2_stride;
+  W.s0 = W.s1 = W.s2 = W.gs0 = W.gs1 = W.gs2 = W.s1phi = W.gs1phi = nullptr;
+  if (!p->cfg.out_3d) {
+    W.s0 = (float*)take(n0 * 4);
+    W.s1 = (float*)take(n1 * 4);
+    W.s2 = (float*)take(n2 * 4);
+    if (with_grad) {
+      W.gs0 = (float*)take(n0 * 4);
+      W.gs1 = (float*)take(n1 * 4);
+      W.gs2 = (float*)take(n2 * 4);
+    }
+  }
+  if (with_grad && p->n_phi) {
+    W.s1phi = (float*)take(n1 * 4);
+    W.gs1phi = (float*)take(n1 * 4);
   }
   return off;
 }
@@ -271,6 +293,12 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   p->N_fr = 2 * (1 << ilog2(p->n1));
   p->s_F = 1 << (int)std::floor(std::log2((double)cfg->F));
   p->n_lo = cfg->average_fr ? (p->n1 + p->s_F - 1) / p->s_F : p->n1;
+  {
+    const int br = cfg->branches == 0 ? 3 : cfg->branches;
+    p->phi_psi = (br & JTFS_BRANCH_PHI_PSI) != 0;
+    p->n_phi = (p->phi_psi ? p->n_fr : 0) + ((br & JTFS_BRANCH_PHI_PHI) ? 1 : 0);
+  }
+  p->s2_paths = p->n2 * p->C + p->n_phi;
   // --- schedule (first order: envelope bandwidth 8 sigma per row) ---
   const int o = cfg->oversampling;
   p->rows1.resize(p->n1);
@@ -337,6 +365,10 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   d.N = (int)N; d.logN = ilog2(N); d.T = (int)cfg->T; d.n_t = p->n_t; d.n1 = p->n1; d.n2 = p->n2;
   d.n_fr = p->n_fr; d.C = p->C; d.N_fr = p->N_fr; d.s_F = p->s_F; d.n_lo = p->n_lo;
   d.average_fr = cfg->average_fr;
+  d.n_phi = p->n_phi; d.phi_psi = p->phi_psi;
+  d.s2_stride = p->s2_paths * p->n_lo * p->n_t;
+  if (p->n_phi && !phi_supported(p))
+    return fail(JTFS_ERR_UNSUPPORTED, "the phi_t paths need oversampling 0 and 4 n1 n_t floats of shared memory");
   d.TW = (int)N; d.logTW = d.logN;
   d.M = (int)std::min<int64_t>(N, 8192); d.logM = ilog2(d.M); d.D = (int)(N / d.M);
   d.K2max = std::max(1, p->L1max / 2);
@@ -389,6 +421,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   const size_t o_psi1 = place(sizeof(float) * std::max<long long>(1, off_v));
   const size_t o_psi2 = place(sizeof(float) * (size_t)p->n2 * d.K2max);
   const size_t o_phiT = place(sizeof(float) * N);
+  const size_t o_phiTlo = place(sizeof(float) * N);
   // phi_T's spectrum on the bins it is built from (q <= 12 sigma_T N), FP64 then rounded
   const double sT = 0.1 / (double)p->cfg.T;
   d.phiT_kmax = std::min((int)std::ceil(12.0 * sT * N), (int)(N / 2));
@@ -415,6 +448,7 @@ jtfs_status jtfs_plan_create(const jtfs_config* cfg, int64_t N, jtfs_plan** out)
   d.psi1 = (const float*)(base + o_psi1);
   d.psi2 = (const float*)(base + o_psi2);
   d.phiT = (const float*)(base + o_phiT);
+  d.phiT_lo = (const float*)(base + o_phiTlo);
   d.phiThat = (const float*)(base + o_phat);
   d.phiF = (const float*)(base + o_phiF);
   d.h = (const float2*)(base + o_h);
@@ -463,7 +497,10 @@ jtfs_status jtfs_plan_shapes(const jtfs_plan* p, jtfs_shapes* s) {
   s->n_lam_out = p->n_lo; s->N_fr = p->N_fr; s->s_F = p->s_F;
   s->s0_len = p->n_t;
   s->s1_len = (int64_t)p->n1 * p->n_t;
-  s->s2_len = (int64_t)p->n2 * p->C * p->n_lo * p->n_t;
+  s->s2_len = (int64_t)p->s2_paths * p->n_lo * p->n_t;
+  s->n_phi = p->n_phi;
+  s->s2_paths = p->s2_paths;
+  s->out_rows = 1 + (int64_t)p->n1 + (int64_t)p->s2_paths * p->n_lo;
   s->u1_len = p->u1_len;
   return JTFS_OK;
 }
@@ -484,6 +521,80 @@ jtfs_status jtfs_workspace_bytes(const jtfs_plan* p, int64_t B, int32_t with_gra
   return JTFS_OK;
 }
 
+// Floats per signal of the three outputs as the caller sees them: S0, S1 and S2 in the 3-D
+// mode; one [out_rows][n_t] block (in the s0 slot) and nothing else in the 2-D mode.
+static void out_sizes(const jtfs_plan* p, size_t* n0, size_t* n1, size_t* n2) {
+  if (p->cfg.out_3d) {
+    *n0 = p->n_t;
+    *n1 = (size_t)p->n1 * p->n_t;
+    *n2 = (size_t)p->dp.s2_stride;
+  } else {
+    *n0 = (size_t)(1 + p->n1 + (size_t)p->s2_paths * p->n_lo) * p->n_t;
+    *n1 = *n2 = 0;
+  }
+}
+
+static jtfs_status check_out_args(const jtfs_plan* p, const void* a0, const void* a1,
+                                  const void* a2, bool required, const char* what) {
+  if (p->cfg.out_3d) {
+    if (required && (!a0 || !a1 || !a2)) {
+      set_error(std::string("NULL ") + what);
+      return JTFS_ERR_INVALID_ARG;
+    }
+  } else if ((required && !a0) || a1 || a2) {
+    set_error(std::string("2-D output mode: the first ") + what + " buffer holds all orders; "
+              "the second and third must be NULL");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  return JTFS_OK;
+}
+
+// The forward's outputs, written where the layout wants them: the caller's buffers (3-D) or
+// the workspace's, packed into the caller's single buffer afterwards (2-D).  The phi_t paths
+// are computed from S1 into the tail of each signal's S2.
+static jtfs_status forward_outputs(const jtfs_plan* p, const float* x, int B, float* s0,
+                                   float* s1, float* s2, float* u1, const Workspace& w,
+                                   cudaStream_t st, float** s1_used) {
+  float* o0 = p->cfg.out_3d ? s0 : w.s0;
+  float* o1 = p->cfg.out_3d ? s1 : w.s1;
+  float* o2 = p->cfg.out_3d ? s2 : w.s2;
+  jtfs_status rc = launch_forward(p, x, B, o0, o1, o2, u1, w, st);
+  if (rc == JTFS_OK && p->n_phi) rc = launch_phi_forward(p, B, o1, o2, st);
+  if (rc == JTFS_OK && !p->cfg.out_3d) rc = launch_pack_2d(p, B, o0, o1, o2, s0, false, st);
+  if (s1_used) *s1_used = o1;
+  return rc;
+}
+
+// The cotangents as the backward kernels take them: unpacked from the 2-D layout, and with the
+// phi_t paths' adjoint added to g_S1 (their input is S1: the forward's, or rebuilt from the
+// checkpoint when s1 is NULL).
+static jtfs_status backward_cotangents(const jtfs_plan* p, int B, const float* x,
+                                       const float* u1, const float* s1, const float** g0,
+                                       const float** g1, const float** g2, const Workspace& w,
+                                       cudaStream_t st) {
+  (void)x;
+  jtfs_status rc = JTFS_OK;
+  if (!p->cfg.out_3d) {
+    if (*g0) {
+      rc = launch_pack_2d(p, B, w.gs0, w.gs1, w.gs2, const_cast<float*>(*g0), true, st);
+      *g0 = w.gs0;
+      *g1 = w.gs1;
+      *g2 = w.gs2;
+    } else {
+      *g1 = *g2 = nullptr;
+    }
+  }
+  if (rc == JTFS_OK && p->n_phi && *g2) {
+    if (!s1) {
+      rc = launch_s1_from_u1(p, B, u1, w.s1phi, st);
+      s1 = w.s1phi;
+    }
+    if (rc == JTFS_OK) rc = launch_phi_backward(p, B, s1, *g2, *g1, w.gs1phi, st);
+    *g1 = w.gs1phi;
+  }
+  return rc;
+}
+
 static jtfs_status check_device(const jtfs_plan* p) {
   int dev = -1;
   jtfs_status st = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
@@ -496,8 +607,10 @@ jtfs_status jtfs_forward(const jtfs_plan* p, const float* x, int64_t B, float* s
                          float* s2, float* u1_ckpt, void* ws, size_t ws_bytes, void* stream) {
   if (!p || B < 0 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
   if (B == 0) return JTFS_OK;
-  if (!x || !s0 || !s1 || !s2) { set_error("NULL input or output"); return JTFS_ERR_INVALID_ARG; }
-  jtfs_status st = check_device(p);
+  if (!x) { set_error("NULL input"); return JTFS_ERR_INVALID_ARG; }
+  jtfs_status st = check_out_args(p, s0, s1, s2, true, "output");
+  if (st != JTFS_OK) return st;
+  st = check_device(p);
   if (st != JTFS_OK) return st;
   const size_t need = workspace_layout(p, B, false, nullptr, nullptr);
   if (!ws || ws_bytes < need) {
@@ -506,13 +619,13 @@ jtfs_status jtfs_forward(const jtfs_plan* p, const float* x, int64_t B, float* s
   }
   Workspace w;
   workspace_layout(p, B, false, (char*)ws, &w);
-  if ((st = launch_forward(p, x, (int)B, s0, s1, s2, u1_ckpt ? u1_ckpt : w.u1, w,
-                           (cudaStream_t)stream)) != JTFS_OK)
+  if ((st = forward_outputs(p, x, (int)B, s0, s1, s2, u1_ckpt ? u1_ckpt : w.u1, w,
+                            (cudaStream_t)stream, nullptr)) != JTFS_OK)
     return st;
+  size_t n0, n1, n2;
+  out_sizes(p, &n0, &n1, &n2);
   const size_t Bz = (size_t)B;
-  return check_finite(p, (cudaStream_t)stream,
-                      {{s0, Bz * p->n_t}, {s1, Bz * p->n1 * p->n_t},
-                       {s2, Bz * (size_t)p->n2 * p->C * p->n_lo * p->n_t}});
+  return check_finite(p, (cudaStream_t)stream, {{s0, Bz * n0}, {s1, Bz * n1}, {s2, Bz * n2}});
 }
 
 jtfs_status jtfs_backward(const jtfs_plan* p, const float* x, const float* u1_ckpt, int64_t B,
@@ -521,7 +634,9 @@ jtfs_status jtfs_backward(const jtfs_plan* p, const float* x, const float* u1_ck
   if (!p || B < 0 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
   if (B == 0) return JTFS_OK;
   if (!x || !u1_ckpt || !g_x) { set_error("NULL x, u1_ckpt or g_x"); return JTFS_ERR_INVALID_ARG; }
-  jtfs_status st = check_device(p);
+  jtfs_status st = check_out_args(p, g_s0, g_s1, g_s2, false, "cotangent");
+  if (st != JTFS_OK) return st;
+  st = check_device(p);
   if (st != JTFS_OK) return st;
   const size_t need = workspace_layout(p, B, true, nullptr, nullptr);
   if (!ws || ws_bytes < need) {
@@ -530,6 +645,9 @@ jtfs_status jtfs_backward(const jtfs_plan* p, const float* x, const float* u1_ck
   }
   Workspace w;
   workspace_layout(p, B, true, (char*)ws, &w);
+  if ((st = backward_cotangents(p, (int)B, x, u1_ckpt, nullptr, &g_s0, &g_s1, &g_s2, w,
+                                (cudaStream_t)stream)) != JTFS_OK)
+    return st;
   if ((st = launch_backward(p, x, u1_ckpt, (int)B, g_s0, g_s1, g_s2, g_x, w,
                             (cudaStream_t)stream)) != JTFS_OK)
     return st;
@@ -542,8 +660,11 @@ jtfs_status jtfs_forward_backward(const jtfs_plan* p, const float* x, int64_t B,
                                   void* ws, size_t ws_bytes, void* stream) {
   if (!p || B < 0 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
   if (B == 0) return JTFS_OK;
-  if (!x || !s0 || !s1 || !s2 || !g_x) { set_error("NULL input or output"); return JTFS_ERR_INVALID_ARG; }
-  jtfs_status st = check_device(p);
+  if (!x || !g_x) { set_error("NULL input or output"); return JTFS_ERR_INVALID_ARG; }
+  jtfs_status st = check_out_args(p, s0, s1, s2, true, "output");
+  if (st == JTFS_OK) st = check_out_args(p, g_s0, g_s1, g_s2, false, "cotangent");
+  if (st != JTFS_OK) return st;
+  st = check_device(p);
   if (st != JTFS_OK) return st;
   const size_t need = workspace_layout(p, B, true, nullptr, nullptr);
   if (!ws || ws_bytes < need) {
@@ -553,14 +674,17 @@ jtfs_status jtfs_forward_backward(const jtfs_plan* p, const float* x, int64_t B,
   Workspace w;
   workspace_layout(p, B, true, (char*)ws, &w);
   float* u1 = u1_ckpt ? u1_ckpt : w.u1;
-  if ((st = launch_forward(p, x, (int)B, s0, s1, s2, u1, w, (cudaStream_t)stream)) != JTFS_OK) return st;
-  if ((st = launch_backward(p, x, u1, (int)B, g_s0, g_s1, g_s2, g_x, w, (cudaStream_t)stream,
-                            true)) != JTFS_OK)
+  cudaStream_t cs = (cudaStream_t)stream;
+  float* s1_used = nullptr;
+  if ((st = forward_outputs(p, x, (int)B, s0, s1, s2, u1, w, cs, &s1_used)) != JTFS_OK) return st;
+  if ((st = backward_cotangents(p, (int)B, x, u1, s1_used, &g_s0, &g_s1, &g_s2, w, cs)) != JTFS_OK)
     return st;
+  if ((st = launch_backward(p, x, u1, (int)B, g_s0, g_s1, g_s2, g_x, w, cs, true)) != JTFS_OK)
+    return st;
+  size_t n0, n1, n2;
+  out_sizes(p, &n0, &n1, &n2);
   const size_t Bz = (size_t)B;
-  return check_finite(p, (cudaStream_t)stream,
-                      {{s0, Bz * p->n_t}, {s1, Bz * p->n1 * p->n_t},
-                       {s2, Bz * (size_t)p->n2 * p->C * p->n_lo * p->n_t}, {g_x, Bz * p->N}});
+  return check_finite(p, cs, {{s0, Bz * n0}, {s1, Bz * n1}, {s2, Bz * n2}, {g_x, Bz * p->N}});
 }
 
 jtfs_status jtfs_plan_autotune(jtfs_plan* p, int64_t B, void* ws, size_t ws_bytes, void* stream,
@@ -589,11 +713,13 @@ jtfs_status jtfs_plan_autotune(jtfs_plan* p, int64_t B, void* ws, size_t ws_byte
 jtfs_status jtfs_host_step_bytes(const jtfs_plan* p, int64_t B, size_t* out) {
   if (!p || !out || B < 0) { set_error("bad argument"); return JTFS_ERR_INVALID_ARG; }
   const size_t Bz = (size_t)B;
+  size_t n0, n1, n2;
+  out_sizes(p, &n0, &n1, &n2);
   size_t n = 0;
   n += align256(Bz * p->N * 4) * 2;                             // x, g_x
-  n += align256(Bz * p->n_t * 4) * 2;                           // s0, g_s0
-  n += align256(Bz * (size_t)p->n1 * p->n_t * 4) * 2;           // s1, g_s1
-  n += align256(Bz * (size_t)p->n2 * p->C * p->n_lo * p->n_t * 4) * 2;  // s2, g_s2
+  n += align256(Bz * n0 * 4) * 2;                               // s0, g_s0 (or the 2-D block)
+  n += align256(Bz * n1 * 4) * 2;                               // s1, g_s1
+  n += align256(Bz * n2 * 4) * 2;                               // s2, g_s2
   n += align256(Bz * p->u1_len * 4);                            // checkpoint
   *out = n;
   return JTFS_OK;
@@ -616,8 +742,13 @@ jtfs_status jtfs_forward_backward_host(const jtfs_plan* p, const float* x_host, 
   char* base = (char*)dev_buf;
   size_t off = 0;
   auto take = [&](size_t bytes) { char* q = base + off; off += align256(bytes); return q; };
-  const size_t bx = Bz * p->N * 4, b0 = Bz * p->n_t * 4, b1 = Bz * (size_t)p->n1 * p->n_t * 4;
-  const size_t b2 = Bz * (size_t)p->n2 * p->C * p->n_lo * p->n_t * 4;
+  size_t n0, n1, n2;
+  out_sizes(p, &n0, &n1, &n2);
+  if (!p->cfg.out_3d && (s1_host || s2_host || g_s1_host || g_s2_host)) {
+    set_error("2-D output mode: s0 / g_s0 hold all orders; the others must be NULL");
+    return JTFS_ERR_INVALID_ARG;
+  }
+  const size_t bx = Bz * p->N * 4, b0 = Bz * n0 * 4, b1 = Bz * n1 * 4, b2 = Bz * n2 * 4;
   float* dx = (float*)take(bx);
   float* dgx = (float*)take(bx);
   float* ds0 = (float*)take(b0);
@@ -632,9 +763,10 @@ jtfs_status jtfs_forward_backward_host(const jtfs_plan* p, const float* x_host, 
   if (g_s0_host && (rc = cuda_check(cudaMemcpyAsync(dg0, g_s0_host, b0, cudaMemcpyHostToDevice, st), "H2D g_s0")) != JTFS_OK) return rc;
   if (g_s1_host && (rc = cuda_check(cudaMemcpyAsync(dg1, g_s1_host, b1, cudaMemcpyHostToDevice, st), "H2D g_s1")) != JTFS_OK) return rc;
   if (g_s2_host && (rc = cuda_check(cudaMemcpyAsync(dg2, g_s2_host, b2, cudaMemcpyHostToDevice, st), "H2D g_s2")) != JTFS_OK) return rc;
+  const bool o3 = p->cfg.out_3d != 0;
   if ((rc = jtfs_forward_backward(p, dx, B, g_s0_host ? dg0 : nullptr, g_s1_host ? dg1 : nullptr,
-                                   g_s2_host ? dg2 : nullptr, ds0, ds1, ds2, du1, dgx, ws,
-                                   ws_bytes, stream)) != JTFS_OK)
+                                   g_s2_host ? dg2 : nullptr, ds0, o3 ? ds1 : nullptr,
+                                   o3 ? ds2 : nullptr, du1, dgx, ws, ws_bytes, stream)) != JTFS_OK)
     return rc;
   if (s0_host && (rc = cuda_check(cudaMemcpyAsync(s0_host, ds0, b0, cudaMemcpyDeviceToHost, st), "D2H s0")) != JTFS_OK) return rc;
   if (s1_host && (rc = cuda_check(cudaMemcpyAsync(s1_host, ds1, b1, cudaMemcpyDeviceToHost, st), "D2H s1")) != JTFS_OK) return rc;

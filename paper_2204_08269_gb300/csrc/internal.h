@@ -42,6 +42,9 @@ struct Rate2 {
 // Device-side constants of a plan (passed by value to kernels).
 struct DevPlan {
   int N, logN, T, n_t, n1, n2, n_fr, C, N_fr, s_F, n_lo, average_fr;
+  int n_phi;              // phi_t paths after the psi_t paths of S2 (0, 1, n_fr or n_fr + 1)
+  int phi_psi;            // 1: the first n_fr phi_t paths are phi_T x psi_{beta,+1}
+  int s2_stride;          // floats of S2 per signal: (n2 C + n_phi) n_lo n_t
   int TW, logTW;          // twiddle table length (>= every FFT length and N)
   int D, M, logM;         // decimation of the length-N FFT: N = D * M, M <= 2^kMaxLogL
   int K2max;              // width of the psi2 table (bins 0..K2max-1 on the N grid)
@@ -51,6 +54,7 @@ struct DevPlan {
   const float* psi1;      // packed support values of psi1
   const float* psi2;      // [n2][K2max]
   const float* phiT;      // [N] time-domain lowpass phi_T[n]
+  const float* phiT_lo;   // [N] phi_T[n] - phiT[n] (FP32), for the compensated S0 sums
   const float* phiThat;   // [phiT_kmax + 1] its spectrum phi-hat(q / N), q = 0..phiT_kmax (the
                           // bins phi_T is built from; beyond them phi-hat < e^-72)
   int phiT_kmax;
@@ -89,6 +93,8 @@ struct jtfs_plan {
   int64_t N;
   int device;
   int n1, n2, n_fr, C, n_t, N_fr, s_F, n_lo;
+  int n_phi = 0, phi_psi = 0;  // phi_t paths (see DevPlan)
+  int s2_paths = 0;            // n2 C + n_phi
   std::vector<double> xi1, sg1, xi2, sg2, xi_fr, sg_fr;  // lambda ascending; alpha, beta descending
   double c1, c2, c_fr;
   std::vector<jtfs::Row1> rows1;
@@ -174,6 +180,14 @@ struct Workspace {
   float* yt;       // [B * yt_len * 2] FP32 transposed Y planes (TF32 contraction only)
   float* pbuf;     // [B][n2][C * n1][n_t] time-pooled rows
   void* g1;        // phi_F adjoint of g_S2 (tensor-core backward), bf16
+  float* s0;       // [B][n_t]        S0, S1, S2 of the 2-D output mode (packed at the end)
+  float* s1;       // [B][n1][n_t]
+  float* s2;       // [B][s2_stride]
+  float* gs0;      // cotangents of the 2-D output mode, unpacked
+  float* gs1;
+  float* gs2;
+  float* s1phi;    // [B][n1][n_t] S1 rebuilt from the checkpoint (phi_t paths, backward)
+  float* gs1phi;   // [B][n1][n_t] g_S1 plus the phi_t paths' adjoint
 };
 size_t workspace_layout(const jtfs_plan* p, int64_t B, bool with_grad, char* base, Workspace* w);
 
@@ -197,6 +211,17 @@ bool tc_supported(const jtfs_plan* p);
 int tc_nt(int n_t);
 int tc_res_kb(const jtfs_plan* p);
 jtfs_status build_tc_tables(jtfs_plan* p);
+// phi_t paths (kernels_phi.cu): forward from S1 into the tail of each signal's S2; backward
+// adds their adjoint to g_S1; S1 rebuilt from the checkpoint; the 2-D output packing.
+bool phi_supported(const jtfs_plan* p);
+jtfs_status launch_phi_forward(const jtfs_plan* p, int B, const float* s1, float* s2,
+                               cudaStream_t st);
+jtfs_status launch_s1_from_u1(const jtfs_plan* p, int B, const float* u1, float* s1,
+                              cudaStream_t st);
+jtfs_status launch_phi_backward(const jtfs_plan* p, int B, const float* s1, const float* gs2,
+                                const float* gs1, float* gs1_out, cudaStream_t st);
+jtfs_status launch_pack_2d(const jtfs_plan* p, int B, const float* s0, const float* s1,
+                           const float* s2, float* out, bool unpack, cudaStream_t st);
 jtfs_status launch_wait_diagnostic(const jtfs_plan* p, uint64_t budget_ns, cudaStream_t st);
 jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi, const void* ylo,
                                 float* Pbuf, float* s2, cudaStream_t st);

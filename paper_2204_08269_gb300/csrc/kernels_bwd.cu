@@ -73,7 +73,7 @@ k_joint_bwd_simt(DevPlan P, const int2* __restrict__ items, const float2* __rest
   for (int c = 0; c < P.C; ++c) {
     __syncthreads();
     for (int i = threadIdx.x; i < P.N_fr; i += blockDim.x) sh[i] = P.h[(size_t)c * P.N_fr + i];
-    const float* g = gs2 + (((size_t)b * P.n2 + a) * P.C + c) * (size_t)P.n_lo * nt;
+    const float* g = gs2 + (size_t)b * P.s2_stride + ((size_t)a * P.C + c) * P.n_lo * nt;
     for (int i = threadIdx.x; i < n1 * nt; i += blockDim.x) {
       if (P.average_fr) {
         const int r = i / nt, t = i % nt;

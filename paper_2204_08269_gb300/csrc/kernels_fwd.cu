@@ -21,34 +21,53 @@
 namespace jtfs {
 namespace {
 
-// S0[t] = sum_n phi_T[(tT - n) mod N] x[n], in the time domain from x itself.  For band-pass
-// inputs S0 is a small difference of large terms (x has almost no energy where phi-hat lives),
-// so the sum is compensated: every thread keeps a Neumaier (sum, correction) pair of FP32
-// values, and the pairs are added in FP64.  The spectral form (1 / N) sum_k phi-hat[k] x-hat[k]
-// e^{2 pi i k t / n_t} would inherit the FP32 FFT's rounding of x-hat, which for such inputs is
-// of the size of S0 itself.
-__global__ void k_s0(DevPlan P, const float* __restrict__ x, float* __restrict__ s0) {
-  __shared__ double red[32];
-  const int t = blockIdx.x, b = blockIdx.y;
+// S0[t] = sum_n phi_T[(tT - n) mod N] x[n], in the time domain from x itself, to about FP64
+// accuracy.  For band-pass inputs S0 is a small difference of large terms: for click trains
+// through resonators |S0| is about 2e-6 of sum |phi_T x|, below the rounding of FP32 weights
+// and products.  So every term is formed exactly in two FP32 parts, phi_T = hi + lo and
+// hi x = p + e (e from an FMA), and summed with a Neumaier (sum, correction) pair per frame;
+// the per-thread pairs are added in FP64.  The spectral form from x-hat would inherit the FP32
+// FFT's rounding, which is of the size of S0 itself for such inputs.  One block per
+// (16 frames, signal).
+constexpr int kS0Frames = 16, kS0Threads = 512;
+
+__global__ void __launch_bounds__(kS0Threads)
+k_s0(DevPlan P, const float* __restrict__ x, float* __restrict__ s0) {
+  __shared__ double red[kS0Frames][kS0Threads / 32];
+  const int t0 = blockIdx.x * kS0Frames, b = blockIdx.y;
+  const int nf = min(kS0Frames, P.n_t - t0);
   const float* xb = x + (size_t)b * P.N;
-  const int tT = t * P.T;
-  float sum = 0.f, cor = 0.f;
+  float sum[kS0Frames], cor[kS0Frames];
+#pragma unroll
+  for (int f = 0; f < kS0Frames; ++f) sum[f] = cor[f] = 0.f;
   for (int n = threadIdx.x; n < P.N; n += blockDim.x) {
-    const float v = __fmul_rn(__ldg(&P.phiT[(tT - n) & (P.N - 1)]), xb[n]);
-    const float u = __fadd_rn(sum, v);
-    cor = __fadd_rn(cor, fabsf(sum) >= fabsf(v) ? __fadd_rn(__fsub_rn(sum, u), v)
-                                                : __fadd_rn(__fsub_rn(v, u), sum));
-    sum = u;
+    const float v = xb[n];
+#pragma unroll
+    for (int f = 0; f < kS0Frames; ++f) {
+      if (f >= nf) break;
+      const int k = (int)(((long long)(t0 + f) * P.T - n) & (P.N - 1));
+      const float hi = __ldg(&P.phiT[k]), lo = __ldg(&P.phiT_lo[k]);
+      const float pr = __fmul_rn(hi, v);
+      const float e = fmaf(lo, v, fmaf(hi, v, -pr));
+      const float u = __fadd_rn(sum[f], pr);
+      const float d = fabsf(sum[f]) >= fabsf(pr) ? __fadd_rn(__fsub_rn(sum[f], u), pr)
+                                                 : __fadd_rn(__fsub_rn(pr, u), sum[f]);
+      cor[f] = __fadd_rn(cor[f], __fadd_rn(d, e));
+      sum[f] = u;
+    }
   }
-  double acc = (double)sum + (double)cor;
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red[w] = acc;
-  __syncthreads();
-  if (w == 0) {
-    acc = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+#pragma unroll
+  for (int f = 0; f < kS0Frames; ++f) {
+    double acc = (double)sum[f] + (double)cor[f];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (l == 0) s0[(size_t)b * P.n_t + t] = (float)acc;
+    if (l == 0) red[f][w] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < nf) {
+    double acc = 0.0;
+    for (int i = 0; i < kS0Threads / 32; ++i) acc += red[threadIdx.x][i];
+    s0[(size_t)b * P.n_t + t0 + threadIdx.x] = (float)acc;
   }
 }
 
@@ -131,7 +150,7 @@ k_joint_fwd_simt(DevPlan P, const float2* __restrict__ y, float* __restrict__ s2
   extern __shared__ float4 smraw[];
   const int c = blockIdx.x, a = blockIdx.y, b = blockIdx.z;
   const Rate2 A = P.rates2[a];
-  float* out = s2 + (((size_t)b * P.n2 + a) * P.C + c) * (size_t)P.n_lo * P.n_t;
+  float* out = s2 + (size_t)b * P.s2_stride + ((size_t)a * P.C + c) * P.n_lo * P.n_t;
   if (A.s == 0) {
     for (int i = threadIdx.x; i < P.n_lo * P.n_t; i += blockDim.x) out[i] = 0.f;
     return;
@@ -383,7 +402,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   }
   {
     StageScope sc(p, kStS0, st, 1);
-    k_s0<<<dim3(p->n_t, B), 256, 0, st>>>(d, x, s0);
+    k_s0<<<dim3((p->n_t + kS0Frames - 1) / kS0Frames, B), kS0Threads, 0, st>>>(d, x, s0);
   }
   {
     StageScope sc(p, kStScalogram, st, 1);
@@ -508,7 +527,7 @@ jtfs_status launch_first_order_static(const jtfs_plan* p, const float* x, int B,
   const DevPlan& d = p->dp;
   k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, xsub);
   k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, xsub, xh);
-  k_s0<<<dim3(p->n_t, B), 256, 0, st>>>(d, x, s0);
+  k_s0<<<dim3((p->n_t + kS0Frames - 1) / kS0Frames, B), kS0Threads, 0, st>>>(d, x, s0);
   k_scalogram<<<dim3(p->n1, B), kRowLaunch, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, xh, u1, uh, s1);
   return cuda_check(cudaGetLastError(), "first-order static launch");
 }

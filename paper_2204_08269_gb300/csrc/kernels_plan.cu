@@ -73,8 +73,9 @@ __global__ void k_fill_psi2(int N, int n2, int K2max, const double* __restrict__
 }
 
 // phi_T[n] = (1/N) sum_k phi-hat(k/N) exp(2 pi i k n / N): real and even; bins beyond
-// 12 sigma_T add < e^-72.
-__global__ void k_fill_phiT(int N, int kmax, double sphi, float* out) {
+// 12 sigma_T add < e^-72.  out receives the FP32 rounding of the FP64 value and out_lo the
+// FP32 rounding of the remainder (phi_T = out + out_lo to about 2^-48 relative).
+__global__ void k_fill_phiT(int N, int kmax, double sphi, float* out, float* out_lo) {
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
     double acc = 1.0;
     for (int k = 1; k <= kmax; ++k) {
@@ -84,7 +85,10 @@ __global__ void k_fill_phiT(int N, int kmax, double sphi, float* out) {
       const double cs = cospi(2.0 * (double)kn / (double)N);
       acc += (k == N / 2 ? 1.0 : 2.0) * g * cs;
     }
-    out[n] = (float)(acc / (double)N);
+    const double v = acc / (double)N;
+    const float hi = (float)v;
+    out[n] = hi;
+    out_lo[n] = (float)(v - (double)hi);
   }
 }
 
@@ -195,7 +199,8 @@ jtfs_status build_tables(jtfs_plan* p) {
   {
     int kmax = (int)std::ceil(12.0 * sT * N);
     kmax = std::min(kmax, N / 2);
-    k_fill_phiT<<<(N + 255) / 256, 256>>>(N, kmax, sT, const_cast<float*>(d.phiT));
+    k_fill_phiT<<<(N + 255) / 256, 256>>>(N, kmax, sT, const_cast<float*>(d.phiT),
+                                          const_cast<float*>(d.phiT_lo));
   }
   if ((st = cuda_check(cudaDeviceSynchronize(), "k_fill_phiT")) != JTFS_OK) goto done;
   if ((st = upload(p->xi_fr, p->sg_fr)) != JTFS_OK) goto done;

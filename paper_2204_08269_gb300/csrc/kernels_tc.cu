@@ -1243,7 +1243,7 @@ __global__ void k_pool_lambda(DevPlan Pd, const float* __restrict__ P, float* __
   const int c = blockIdx.x, a = blockIdx.y, b = blockIdx.z;
   const int n1 = Pd.n1, nt = Pd.n_t, nfm = Pd.N_fr - 1;
   const Rate2 A = Pd.rates2[a];
-  float* out = s2 + (((size_t)b * Pd.n2 + a) * Pd.C + c) * (size_t)Pd.n_lo * nt;
+  float* out = s2 + (size_t)b * Pd.s2_stride + ((size_t)a * Pd.C + c) * Pd.n_lo * nt;
   const float* in = P + (((size_t)b * Pd.n2 + a) * (size_t)(Pd.C * n1) + (size_t)c * n1) * nt;
   const int nout = Pd.n_lo * nt;
   if (A.s == 0 || !Pd.average_fr || nout > 256 || blockDim.x != 256) {

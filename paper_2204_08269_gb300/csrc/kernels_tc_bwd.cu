@@ -1457,7 +1457,7 @@ __global__ void k_g1(DevPlan Pd, const float* __restrict__ gs2, int NT, int g1_r
                      __nv_bfloat16* __restrict__ g1, __nv_bfloat16* __restrict__ g1lo) {
   const int c = blockIdx.x, a = blockIdx.y, b = blockIdx.z;
   const int n1 = Pd.n1, nt = Pd.n_t, nfm = Pd.N_fr - 1;
-  const float* g = gs2 + (((size_t)b * Pd.n2 + a) * Pd.C + c) * (size_t)Pd.n_lo * nt;
+  const float* g = gs2 + (size_t)b * Pd.s2_stride + ((size_t)a * Pd.C + c) * Pd.n_lo * nt;
   const size_t o0 = ((size_t)(b * Pd.n2 + a) * g1_rows + (size_t)c * n1) * NT;
   __nv_bfloat16* out = g1 + o0;
   for (int i = threadIdx.x; i < n1 * NT; i += blockDim.x) {

@@ -137,7 +137,7 @@ jtfs_status vl_run(const jtfs_varlen* v, const float* x, const float* gs0, const
     const size_t pws_bytes = ws_bytes - off;
     const dim3 gx_grid((unsigned)std::min<int64_t>((N + 255) / 256, 1024), (unsigned)cnt);
     k_vl_gather_x<<<gx_grid, 256, 0, st>>>(x, ch.d_xoff, ch.d_len, N, xb);
-    const int rows1 = (int)sh.n1, rows2 = (int)(sh.n2 * sh.C * sh.n_lam_out);
+    const int rows1 = (int)sh.n1, rows2 = (int)(sh.s2_paths * sh.n_lam_out);
     auto grid_for = [&](int rows) {
       return dim3((unsigned)std::min<int64_t>(((int64_t)rows * nt + 255) / 256, 1024), (unsigned)cnt);
     };
@@ -173,6 +173,10 @@ jtfs_status jtfs_varlen_create(const jtfs_config* cfg, const int64_t* len, int64
     return JTFS_ERR_INVALID_ARG;
   }
   *out = nullptr;
+  if (cfg->out_3d != 1) {
+    set_error("uneven-length batches keep their own packed layouts: out_3d must be 1");
+    return JTFS_ERR_INVALID_ARG;
+  }
   for (int64_t i = 0; i < B; ++i)
     if (len[i] < 1 || len[i] > ((int64_t)1 << 24)) {
       set_error("signal length out of range [1, 2^24]");
@@ -211,7 +215,7 @@ jtfs_status jtfs_varlen_create(const jtfs_config* cfg, const int64_t* len, int64
     v->x_off[i + 1] = v->x_off[i] + len[i];
     v->s0_off[i + 1] = v->s0_off[i] + frames[i];
     v->s1_off[i + 1] = v->s1_off[i] + sh.n1 * frames[i];
-    v->s2_off[i + 1] = v->s2_off[i] + sh.n2 * sh.C * sh.n_lam_out * frames[i];
+    v->s2_off[i + 1] = v->s2_off[i] + sh.s2_paths * sh.n_lam_out * frames[i];
   }
   // chunks and their device index tables: per chunk [xoff][s0off][s1off][s2off] (int64) then
   // [len][frames] (int32)

@@ -24,13 +24,29 @@ class _Config(ctypes.Structure):
                 ("J_fr", ctypes.c_int32), ("Q_fr", ctypes.c_int32), ("T", ctypes.c_int64),
                 ("F", ctypes.c_int64), ("average_fr", ctypes.c_int32),
                 ("oversampling", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("out_3d", ctypes.c_int32), ("branches", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class _Shapes(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
         "N", "n1", "n2", "n_fr", "C", "n_t", "n_lam_out", "N_fr", "s_F",
-        "s0_len", "s1_len", "s2_len", "u1_len")]
+        "s0_len", "s1_len", "s2_len", "u1_len", "n_phi", "s2_paths", "out_rows")]
+
+
+# second-order joint wavelets (jtfs_branch): psi_t x psi_f and psi_t x phi_f are always on
+BRANCHES = {"psi_psi": 1, "psi_phi": 2, "phi_psi": 4, "phi_phi": 8}
+
+
+def _branch_mask(branches):
+    if branches is None:
+        return 0
+    if isinstance(branches, int):
+        return branches
+    m = 0
+    for b in branches:
+        m |= BRANCHES[b]
+    return m
 
 
 _lib = None
@@ -140,6 +156,9 @@ class Shapes:
     N_fr: int
     s_F: int
     u1_len: int
+    n_phi: int = 0
+    s2_paths: int = 0
+    out_rows: int = 0
 
     def s0(self, B):
         return (B, self.n_t)
@@ -148,7 +167,15 @@ class Shapes:
         return (B, self.n1, self.n_t)
 
     def s2(self, B):
+        """[B, n2, C, n_lam_out, n_t], or [B, s2_paths, n_lam_out, n_t] with the phi_t paths
+        (the n2 C psi_t paths first, then the n_phi phi_t paths)."""
+        if self.n_phi:
+            return (B, self.s2_paths, self.n_lam_out, self.n_t)
         return (B, self.n2, self.C, self.n_lam_out, self.n_t)
+
+    def out_2d(self, B):
+        """The single output of the 2-D layout: [B, 1 + n1 + s2_paths n_lam_out, n_t]."""
+        return (B, self.out_rows, self.n_t)
 
 
 class JTFSPlan:
@@ -157,11 +184,13 @@ class JTFSPlan:
     contraction: 'fp32' (tensor cores, bf16 hi/lo split), 'tf32', 'bf16' or 'fp32_simt'."""
 
     def __init__(self, N, J, Q, J_fr, Q_fr, T, F, Q2=1, average_fr=True, oversampling=0,
-                 precision="fp32"):
+                 precision="fp32", out_3d=True, branches=None):
         L = lib()
         cfg = _Config(J=J, Q=Q, Q2=Q2, J_fr=J_fr, Q_fr=Q_fr, T=T, F=F,
                       average_fr=1 if average_fr else 0, oversampling=oversampling,
-                      precision=PRECISIONS[precision])
+                      precision=PRECISIONS[precision], out_3d=1 if out_3d else 0,
+                      branches=_branch_mask(branches))
+        self.out_3d = bool(out_3d)
         h = ctypes.c_void_p()
         _check("jtfs_plan_create", L.jtfs_plan_create(ctypes.byref(cfg), N, ctypes.byref(h)))
         self._h = h
@@ -169,9 +198,10 @@ class JTFSPlan:
         sh = _Shapes()
         _check("jtfs_plan_shapes", L.jtfs_plan_shapes(h, ctypes.byref(sh)))
         self.shapes = Shapes(sh.N, sh.n1, sh.n2, sh.n_fr, sh.C, sh.n_t, sh.n_lam_out, sh.N_fr,
-                             sh.s_F, sh.u1_len)
+                             sh.s_F, sh.u1_len, sh.n_phi, sh.s2_paths, sh.out_rows)
         self.config = dict(N=N, J=J, Q=Q, Q2=Q2, J_fr=J_fr, Q_fr=Q_fr, T=T, F=F,
-                           average_fr=average_fr, oversampling=oversampling, precision=precision)
+                           average_fr=average_fr, oversampling=oversampling, precision=precision,
+                           out_3d=out_3d, branches=branches)
         self._ws = {}
 
     def __del__(self):
@@ -212,15 +242,21 @@ class JTFSPlan:
                 and x.shape[1] == self.shapes.N and x.is_contiguous()):
             raise ValueError(f"x must be a contiguous float32 CUDA tensor [B, {self.shapes.N}]")
 
+    def _outputs(self, B, dev):
+        sh = self.shapes
+        if not self.out_3d:
+            return torch.empty(sh.out_2d(B), dtype=torch.float32, device=dev), None, None
+        return tuple(torch.empty(f(B), dtype=torch.float32, device=dev)
+                     for f in (sh.s0, sh.s1, sh.s2))
+
     def forward(self, x, keep_checkpoint=True):
-        """S0 [B, n_t], S1 [B, n1, n_t], S2 [B, n2, C, n_lam_out, n_t] and the U1 checkpoint."""
+        """S0 [B, n_t], S1 [B, n1, n_t], S2 (see Shapes.s2) and the U1 checkpoint; in the 2-D
+        layout (out_3d=False) the single [B, out_rows, n_t] output and None, None."""
         self._check_x(x)
         B = x.shape[0]
         sh = self.shapes
         dev = x.device
-        s0 = torch.empty(sh.s0(B), dtype=torch.float32, device=dev)
-        s1 = torch.empty(sh.s1(B), dtype=torch.float32, device=dev)
-        s2 = torch.empty(sh.s2(B), dtype=torch.float32, device=dev)
+        s0, s1, s2 = self._outputs(B, dev)
         u1 = torch.empty((B, sh.u1_len), dtype=torch.float32, device=dev) if keep_checkpoint else None
         ws = self.workspace(B, True)
         _check("jtfs_forward", lib().jtfs_forward(
@@ -247,9 +283,7 @@ class JTFSPlan:
         B = x.shape[0]
         sh = self.shapes
         dev = x.device
-        s0 = torch.empty(sh.s0(B), dtype=torch.float32, device=dev)
-        s1 = torch.empty(sh.s1(B), dtype=torch.float32, device=dev)
-        s2 = torch.empty(sh.s2(B), dtype=torch.float32, device=dev)
+        s0, s1, s2 = self._outputs(B, dev)
         gx = torch.empty_like(x)
         u1 = torch.empty((B, sh.u1_len), dtype=torch.float32, device=dev) if keep_checkpoint else None
         ws = self.workspace(B, True)
@@ -274,8 +308,9 @@ class JTFSPlan:
         ws = self.workspace(B, True)
         pin = x_host.is_pinned()
         gx = torch.empty(x_host.shape, dtype=torch.float32, pin_memory=pin)
-        outs = [torch.empty(s, dtype=torch.float32, pin_memory=pin) if outputs else None
-                for s in (sh.s0(B), sh.s1(B), sh.s2(B))]
+        shapes = (sh.s0(B), sh.s1(B), sh.s2(B)) if self.out_3d else (sh.out_2d(B), None, None)
+        outs = [torch.empty(s, dtype=torch.float32, pin_memory=pin) if (outputs and s) else None
+                for s in shapes]
         _check("jtfs_forward_backward_host", lib().jtfs_forward_backward_host(
             self._h, _ptr(x_host), B, _ptr(g_s0), _ptr(g_s1), _ptr(g_s2), _ptr(outs[0]),
             _ptr(outs[1]), _ptr(outs[2]), _ptr(gx), _ptr(dev_buf), dev_buf.numel(), _ptr(ws),
@@ -336,17 +371,21 @@ class JTFSFunction(torch.autograd.Function):
         s0, s1, s2, u1 = plan.forward(x)
         ctx.plan = plan
         ctx.save_for_backward(x, u1)
+        if not plan.out_3d:
+            return s0
         return s0, s1, s2
 
     @staticmethod
-    def backward(ctx, g0, g1, g2):
+    def backward(ctx, *g):
         x, u1 = ctx.saved_tensors
-        gx = ctx.plan.backward(x, u1, g0, g1, g2)
+        g = list(g) + [None] * (3 - len(g))
+        gx = ctx.plan.backward(x, u1, *g)
         return gx, None
 
 
 class JTFS(torch.nn.Module):
-    """Joint time-frequency scattering as a module: x [B, N] -> (S0, S1, S2)."""
+    """Joint time-frequency scattering as a module: x [B, N] -> (S0, S1, S2), or the single
+    [B, out_rows, n_t] tensor with out_3d=False."""
 
     def __init__(self, N, J, Q, J_fr, Q_fr, T, F, **kw):
         super().__init__()
@@ -356,10 +395,11 @@ class JTFS(torch.nn.Module):
         return JTFSFunction.apply(x, self.plan)
 
 
-def _config(J, Q, J_fr, Q_fr, T, F, Q2=1, average_fr=True, oversampling=0, precision="fp32"):
+def _config(J, Q, J_fr, Q_fr, T, F, Q2=1, average_fr=True, oversampling=0, precision="fp32",
+            branches=None):
     return _Config(J=J, Q=Q, Q2=Q2, J_fr=J_fr, Q_fr=Q_fr, T=T, F=F,
                    average_fr=1 if average_fr else 0, oversampling=oversampling,
-                   precision=PRECISIONS[precision])
+                   precision=PRECISIONS[precision], out_3d=1, branches=_branch_mask(branches))
 
 
 def varlen_padded_length(length, J, **kw):

@@ -41,10 +41,11 @@ def test_status_strings(L):
 
 @pytest.mark.parametrize("field,value", [("J", 0), ("Q", 0), ("T", 3), ("F", 0),
                                          ("average_fr", 2), ("oversampling", -1),
-                                         ("precision", 9)])
+                                         ("precision", 9), ("out_3d", 2), ("branches", 1),
+                                         ("branches", 2), ("branches", 16 | 3)])
 def test_invalid_config_rejected_on_host(L, field, value):
     from paper_2204_08269_gb300 import jtfs
-    cfg = jtfs._Config(J=6, Q=8, Q2=1, J_fr=3, Q_fr=1, T=64, F=8, average_fr=1)
+    cfg = jtfs._Config(J=6, Q=8, Q2=1, J_fr=3, Q_fr=1, T=64, F=8, average_fr=1, out_3d=1)
     setattr(cfg, field, value)
     h = ctypes.c_void_p()
     st = L.jtfs_plan_create(ctypes.byref(cfg), 4096, ctypes.byref(h))
