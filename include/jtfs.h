@@ -145,6 +145,26 @@ jtfs_status jtfs_forward_backward(const jtfs_plan* plan, const float* x, int64_t
                                   float* s0, float* s1, float* s2, float* u1_ckpt, float* g_x,
                                   void* ws, size_t ws_bytes, void* stream);
 
+/* Time scattering (Scattering1D), the baseline of Sec. 4.4, on the plan's filterbanks and
+ * schedule: the first-order scalogram with no log-frequency stage after it.  s0 and s1 as
+ * jtfs_forward; s2t [B, n2, n1, n_t] (device) with
+ *   s2t[alpha][lambda'][t] = (|U1[lambda'] * psi_alpha| * phi_T)(t T)
+ * on the paths (alpha, lambda') of a kept rate with lambda' >= lam_min[alpha]
+ * (jtfs_plan_schedule) and 0 elsewhere.  Runs on CUDA cores in FP32 for every precision;
+ * out_3d and branches do not apply.  u1_ckpt (device, may be NULL) receives the checkpoint.
+ * ws as jtfs_workspace_bytes(with_grad = 0).  Errors as jtfs_forward. */
+jtfs_status jtfs_scattering1d_forward(const jtfs_plan* plan, const float* x, int64_t B,
+                                      float* s0, float* s1, float* s2t, float* u1_ckpt,
+                                      void* ws, size_t ws_bytes, void* stream);
+
+/* Its gradient (Sec. 5 adjoints): g_x [B, N] for cotangents g_s0, g_s1, g_s2t (device, any may
+ * be NULL for zero), given x and the forward's u1_ckpt.  ws as jtfs_workspace_bytes(with_grad
+ * = 1). */
+jtfs_status jtfs_scattering1d_backward(const jtfs_plan* plan, const float* x,
+                                       const float* u1_ckpt, int64_t B, const float* g_s0,
+                                       const float* g_s1, const float* g_s2t, float* g_x,
+                                       void* ws, size_t ws_bytes, void* stream);
+
 /* End-to-end forward + backward from HOST buffers: copies x (host, [B, N]) and the
  * cotangents (host; NULL = zero) to the device, runs jtfs_forward_backward, and
  * copies s0, s1, s2 (host, may be NULL) and g_x (host) back.  dev_buf must hold
@@ -189,6 +209,26 @@ const char* jtfs_profile_stage_name(int32_t i);
  * capture.  All calls share the array: calls that overlap on the GPU race on it. */
 jtfs_status jtfs_first_order_static(const jtfs_plan* plan, const float* x, int64_t B, float* s0,
                                     float* s1, void* stream);
+
+/* ---------------------------------------------------------------------------------------
+ * mu-log compression (Sec. 4.3, Eq. 6-7) of scattering paths, on any device array S
+ * [B, P, M] of B examples, P paths (lambda_2) and M coefficients per path (for the transform's
+ * S2: P = s2_paths, M = n_lam_out n_t; for time scattering's S2t: P = n2 n1, M = n_t).
+ * Asynchronous on `stream`; INVALID_ARG for NULL pointers or non-positive sizes. */
+
+/* Eq. 6: mu [P] (device) = (1 / B) sum over the B examples of each path's sum over its M
+ * coefficients (the integral over lambda and t on the grid).  FP64 sums in a fixed order. */
+jtfs_status jtfs_mulog_mean(const float* s, int64_t B, int64_t P, int64_t M, float* mu,
+                            void* stream);
+
+/* Eq. 7: out = log(1 + S / (eps mu[p])), eps > 0 (0.1 in the paper).  out may alias s. */
+jtfs_status jtfs_mulog(const float* s, int64_t B, int64_t P, int64_t M, const float* mu,
+                       float eps, float* out, void* stream);
+
+/* Its gradient with mu held fixed: g_s = g_out / (eps mu[p] + S). */
+jtfs_status jtfs_mulog_backward(const float* s, int64_t B, int64_t P, int64_t M,
+                                const float* mu, float eps, const float* g_out, float* g_s,
+                                void* stream);
 
 /* ---------------------------------------------------------------------------------------
  * Uneven-length batches.  The paper transforms one signal length at a time; these calls take

@@ -589,6 +589,96 @@ def forward_exact_direct(x, plan: Plan):
     return out
 
 
+# ----------------------------------------------------------------------------------------
+# time scattering (Scattering1D): the baseline of Sec. 4.4, the second order without the
+# log-frequency stage, on the same filterbanks and schedule
+# ----------------------------------------------------------------------------------------
+def scattering1d_one(x, plan: Plan, sched: Schedule, engine: str = "fft"):
+    """S0 [n_t], S1 [n1, n_t] as the transform, and S2t [n2, n1, n_t]:
+    S2t[alpha, lambda] = (|U1[lambda] * psi_alpha| * phi_T) sampled every T, on the paths of a
+    kept rate with lambda >= lam_min[alpha] (the rows whose Y_alpha the schedule computes),
+    0 elsewhere."""
+    ops = Operators(plan, sched, engine)
+    x = np.asarray(x, dtype=np.float64)
+    xh = ops.x_hat(x)
+    U1 = [np.abs(ops.psi1(xh, lam)) for lam in range(plan.n1)]
+    S0 = ops.pool_T(x, 1)
+    S1 = np.stack([ops.pool_T(U1[lam], int(sched.s1[lam])) for lam in range(plan.n1)])
+    S2t = np.zeros((plan.n2, plan.n1, plan.n_t))
+    for a in range(plan.n2):
+        if sched.skip2[a]:
+            continue
+        sa = int(sched.s2[a])
+        for lam in range(int(sched.lam_min[a]), plan.n1):
+            S2t[a, lam] = ops.pool_T(np.abs(ops.psi2(U1[lam], lam, a)), sa)
+    return dict(S0=S0, S1=S1, S2t=S2t)
+
+
+def scattering1d_backward_one(x, gS0, gS1, gS2t, plan: Plan, sched: Schedule,
+                              engine: str = "fft"):
+    """Gradient w.r.t. x of <gS0, S0> + <gS1, S1> + <gS2t, S2t> (reverse-ordered adjoints,
+    d|z| taken as 0 at z = 0)."""
+    ops = Operators(plan, sched, engine)
+    x = np.asarray(x, dtype=np.float64)
+    xh = ops.x_hat(x)
+    z = [ops.psi1(xh, lam) for lam in range(plan.n1)]
+    U1 = [np.abs(v) for v in z]
+    gU1 = [ops.pool_T_T(gS1[lam], int(sched.s1[lam])) for lam in range(plan.n1)]
+    for a in range(plan.n2):
+        if sched.skip2[a]:
+            continue
+        sa = int(sched.s2[a])
+        for lam in range(int(sched.lam_min[a]), plan.n1):
+            Y = ops.psi2(U1[lam], lam, a)
+            gY = ops.pool_T_T(gS2t[a, lam], sa) * _safe_phase(Y)
+            gU1[lam] = gU1[lam] + ops.psi2_T(gY, lam, a)
+    g_xh = np.zeros(plan.N, dtype=np.complex128)
+    for lam in range(plan.n1):
+        g_xh += ops.psi1_T(gU1[lam] * _safe_phase(z[lam]), lam)
+    return ops.x_hat_T(g_xh) + ops.pool_T_T(gS0, 1)
+
+
+def scattering1d_exact_direct(x, plan: Plan):
+    """EXACT time scattering from the definitions: circular sums of the time-domain filters
+    at the full rate, every (alpha, lambda) pair.  O(N^2): tiny inputs only."""
+    N = plan.N
+    x = np.asarray(x, dtype=np.float64)
+    psi1 = idft_sum(plan.psi1_hat, "direct") / N
+    psi2 = idft_sum(plan.psi2_hat, "direct") / N
+    phiT = np.real(idft_sum(plan.phi_T_hat, "direct")) / N
+    t = np.arange(plan.n_t) * plan.T
+    U1 = [np.abs(circconv_direct(x, psi1[lam])) for lam in range(plan.n1)]
+    S2t = np.zeros((plan.n2, plan.n1, plan.n_t))
+    for a in range(plan.n2):
+        for lam in range(plan.n1):
+            S2t[a, lam] = circconv_direct(np.abs(circconv_direct(U1[lam], psi2[a])), phiT)[t]
+    return dict(S0=circconv_direct(x, phiT)[t],
+                S1=np.stack([circconv_direct(u, phiT)[t] for u in U1]), S2t=S2t)
+
+
+def scattering1d_paths(plan: Plan, sched: Schedule) -> int:
+    """Number of second-order (alpha, lambda) paths the schedule computes."""
+    return int(sum(plan.n1 - sched.lam_min[a] for a in range(plan.n2) if not sched.skip2[a]))
+
+
+# ----------------------------------------------------------------------------------------
+# mu-log compression (Sec. 4.3, Eq. 6-7)
+# ----------------------------------------------------------------------------------------
+def mu_log_mean(S):
+    """Eq. 6: mu(lambda_2) = (1/N) sum_n sum_{lambda, t} S x_n(lambda_2, lambda, t), the path's
+    integral over its other axes (a sum on the grid), averaged over the N examples.
+    S: [examples, paths, ...]."""
+    S = np.asarray(S, dtype=np.float64)
+    return S.reshape(S.shape[0], S.shape[1], -1).sum(axis=2).mean(axis=0)
+
+
+def mu_log(S, mu, eps: float = 0.1):
+    """Eq. 7: log(1 + S / (eps mu(lambda_2))), path by path (axis 1)."""
+    S = np.asarray(S, dtype=np.float64)
+    shape = (1, -1) + (1,) * (S.ndim - 2)
+    return np.log1p(S / (eps * np.asarray(mu, dtype=np.float64).reshape(shape)))
+
+
 def stage1_full_rate(x, plan: Plan):
     """x * phi_T and x * psi_lambda at every sample (for the energy identity)."""
     xh = np.fft.fft(np.asarray(x, dtype=np.float64))

@@ -687,6 +687,52 @@ jtfs_status jtfs_forward_backward(const jtfs_plan* p, const float* x, int64_t B,
   return check_finite(p, cs, {{s0, Bz * n0}, {s1, Bz * n1}, {s2, Bz * n2}, {g_x, Bz * p->N}});
 }
 
+jtfs_status jtfs_scattering1d_forward(const jtfs_plan* p, const float* x, int64_t B, float* s0,
+                                      float* s1, float* s2t, float* u1_ckpt, void* ws,
+                                      size_t ws_bytes, void* stream) {
+  if (!p || B < 0 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
+  if (B == 0) return JTFS_OK;
+  if (!x || !s0 || !s1 || !s2t) { set_error("NULL input or output"); return JTFS_ERR_INVALID_ARG; }
+  jtfs_status st = check_device(p);
+  if (st != JTFS_OK) return st;
+  const size_t need = workspace_layout(p, B, false, nullptr, nullptr);
+  if (!ws || ws_bytes < need) {
+    set_error("workspace needs " + std::to_string(need) + " bytes");
+    return JTFS_ERR_WORKSPACE;
+  }
+  Workspace w;
+  workspace_layout(p, B, false, (char*)ws, &w);
+  if ((st = launch_scat1d_forward(p, x, (int)B, s0, s1, s2t, u1_ckpt ? u1_ckpt : w.u1, w,
+                                  (cudaStream_t)stream)) != JTFS_OK)
+    return st;
+  const size_t Bz = (size_t)B;
+  return check_finite(p, (cudaStream_t)stream,
+                      {{s0, Bz * p->n_t}, {s1, Bz * p->n1 * p->n_t},
+                       {s2t, Bz * p->n2 * p->n1 * p->n_t}});
+}
+
+jtfs_status jtfs_scattering1d_backward(const jtfs_plan* p, const float* x, const float* u1_ckpt,
+                                       int64_t B, const float* g_s0, const float* g_s1,
+                                       const float* g_s2t, float* g_x, void* ws, size_t ws_bytes,
+                                       void* stream) {
+  if (!p || B < 0 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }
+  if (B == 0) return JTFS_OK;
+  if (!x || !u1_ckpt || !g_x) { set_error("NULL x, u1_ckpt or g_x"); return JTFS_ERR_INVALID_ARG; }
+  jtfs_status st = check_device(p);
+  if (st != JTFS_OK) return st;
+  const size_t need = workspace_layout(p, B, true, nullptr, nullptr);
+  if (!ws || ws_bytes < need) {
+    set_error("workspace needs " + std::to_string(need) + " bytes");
+    return JTFS_ERR_WORKSPACE;
+  }
+  Workspace w;
+  workspace_layout(p, B, true, (char*)ws, &w);
+  if ((st = launch_scat1d_backward(p, x, u1_ckpt, (int)B, g_s0, g_s1, g_s2t, g_x, w,
+                                   (cudaStream_t)stream)) != JTFS_OK)
+    return st;
+  return check_finite(p, (cudaStream_t)stream, {{g_x, (size_t)B * p->N}});
+}
+
 jtfs_status jtfs_plan_autotune(jtfs_plan* p, int64_t B, void* ws, size_t ws_bytes, void* stream,
                                int32_t* choice) {
   if (!p || B < 1 || B > (1 << 20)) { set_error("bad plan or batch size"); return JTFS_ERR_INVALID_ARG; }

@@ -145,6 +145,11 @@ struct jtfs_plan {
   int tcbf_n2a = 0;            // of the two-atom items, those with K1 <= 96 (first)
   int tcbf_n3 = 0;             // three-atom items (K1 <= 160, spin-pair form), last
   int* d_tcbf_items;
+  std::vector<int> tcb_fb_items;     // (alpha, n0): rates past the tensor-core backward's
+  std::vector<int> tcb_fb_rowitems;  // lambda' capacity, on CUDA cores; their Y row items
+  int* d_tcb_fb_items = nullptr;
+  int* d_tcb_fb_rowitems = nullptr;
+  int tcb_fb_cap = 0;                // samples of the largest of those row items
   int* d_tcb_items;
   void* d_wtb;                 // [rows][NT] bf16 pooling weights (time-major)
   int* d_wtb_row0;             // [n2]
@@ -222,6 +227,11 @@ jtfs_status launch_phi_backward(const jtfs_plan* p, int B, const float* s1, cons
                                 const float* gs1, float* gs1_out, cudaStream_t st);
 jtfs_status launch_pack_2d(const jtfs_plan* p, int B, const float* s0, const float* s1,
                            const float* s2, float* out, bool unpack, cudaStream_t st);
+jtfs_status launch_scat1d_forward(const jtfs_plan* p, const float* x, int B, float* s0, float* s1,
+                                  float* s2t, float* u1, const Workspace& w, cudaStream_t st);
+jtfs_status launch_scat1d_backward(const jtfs_plan* p, const float* x, const float* u1, int B,
+                                   const float* gs0, const float* gs1, const float* gs2t,
+                                   float* gx, const Workspace& w, cudaStream_t st);
 jtfs_status launch_wait_diagnostic(const jtfs_plan* p, uint64_t budget_ns, cudaStream_t st);
 jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi, const void* ylo,
                                 float* Pbuf, float* s2, cudaStream_t st);

@@ -361,6 +361,37 @@ k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, f
   }
 }
 
+// Time scattering (Scattering1D) backward of the second order: Y_alpha rows recomputed in
+// shared memory as in the forward, then gY = g_|Y| Y / |Y| (0 where Y = 0) with
+// g_|Y|[m] = sum_t s_alpha phi_T[(t T - m s_alpha) mod N] g_S2t[t], written in the layout of the
+// transform's gY so that the second-order adjoint that follows is shared.
+__global__ void __launch_bounds__(kRowThreads)
+k_scat1d_bwd_rows(DevPlan P, const int4* __restrict__ items, const float2* __restrict__ uh,
+                  const float* __restrict__ gs2t, float2* __restrict__ gy) {
+  extern __shared__ float2 sm[];
+  __shared__ int s_off[kMaxRowsPerItem], s_kend[kMaxRowsPerItem];
+  __shared__ float s_inv[kMaxRowsPerItem];
+  const int4 it = items[blockIdx.x];
+  const int a = it.x, lam0 = it.y, G = it.z, b = blockIdx.y;
+  const Rate2 A = P.rates2[a];
+  const int L = A.L, logL = A.logL, nt = P.n_t;
+  second_order_rows_ifft(P, A, a, lam0, G, uh + (size_t)b * P.uh_len, sm, s_off, s_kend, s_inv);
+  __syncthreads();
+  const float* g = gs2t + (((size_t)b * P.n2 + a) * P.n1 + lam0) * nt;
+  float2* out = gy + (size_t)b * P.y_len + A.off_y + (size_t)(lam0 - A.lam_min) * L;
+  for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
+    const int r = idx >> logL, m = idx & (L - 1);
+    float ga = 0.f;
+    for (int t = 0; t < nt; ++t)
+      ga = fmaf(__ldg(&P.phiT[((long long)t * P.T - (long long)m * A.s) & (P.N - 1)]),
+                __ldg(&g[r * nt + t]), ga);
+    const float2 v = sm[fft_pad(idx)];
+    const float mag = sqrtf(v.x * v.x + v.y * v.y);
+    const float sc = mag > 0.f ? ga * (float)A.s / mag : 0.f;
+    out[idx] = make_float2(v.x * sc, v.y * sc);
+  }
+}
+
 // cudaFuncSetAttribute acts on the current device only, so the raised shared-memory limits
 // are recorded per device (the plan's device is current in every call that launches).
 std::mutex g_attrs_mu;
@@ -385,7 +416,7 @@ jtfs_status set_attrs(const jtfs_plan* p) {
   // the row producer holds at most 2^14 complex samples (padded one per 16) next to its
   // static row tables
   for (const void* f : {(const void*)k_second_order_rows<0>, (const void*)k_second_order_rows<1>,
-                        (const void*)k_gy_spectra}) {
+                        (const void*)k_gy_spectra, (const void*)k_scat1d_bwd_rows}) {
     jtfs_status st = cuda_check(
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024), "attr");
     if (st != JTFS_OK) return st;
@@ -439,6 +470,18 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
     StageScope sc(p, kStJointBwd, st, 2);
     jtfs_status r2 = launch_joint_bwd_tc(p, B, w.ybh, w.ybl, gs2, w.g1, w.gy, st);
     if (r2 != JTFS_OK) return r2;
+    if (!p->tcb_fb_items.empty()) {
+      // rates beyond the tensor-core backward's lambda' capacity: FP32 Y rows of those rates
+      // only, then the CUDA-core backward on them
+      k_second_order_rows<0><<<dim3((unsigned)(p->tcb_fb_rowitems.size() / 4), B),
+                              p->row_threads, (size_t)p->tcb_fb_cap * 17 / 2, st>>>(
+          d, reinterpret_cast<const int4*>(p->d_tcb_fb_rowitems), w.uh, w.y, nullptr, nullptr,
+          B);
+      k_joint_bwd_simt<<<dim3((unsigned)(p->tcb_fb_items.size() / 2), B), kJT,
+                         joint_bwd_smem(p), st>>>(
+          d, reinterpret_cast<const int2*>(p->d_tcb_fb_items), w.y, gs2, w.gy);
+      p->prof.launches += 2;
+    }
   } else if (gs2 && n_items > 0) {
     {
       StageScope sc(p, kStSecondOrder, st, 1);
@@ -470,6 +513,51 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
     k_gx<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, w.gxh, gs0, gx);
   }
   return cuda_check(cudaGetLastError(), "backward launch");
+}
+
+// Time scattering backward: x-hat and U1-hat rebuilt from x and the checkpoint, the second
+// order's gY from g_S2t, then the transform's own adjoint chain from gY down to g_x.
+jtfs_status launch_scat1d_backward(const jtfs_plan* p, const float* x, const float* u1, int B,
+                                   const float* gs0, const float* gs1, const float* gs2t,
+                                   float* gx, const Workspace& w, cudaStream_t st) {
+  jtfs_status rc = set_attrs(p);
+  if (rc != JTFS_OK) return rc;
+  const DevPlan& d = p->dp;
+  {
+    StageScope sc(p, kStXfft, st, 2);
+    k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, w.xsub);
+    k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.xsub, w.xh);
+  }
+  {
+    StageScope sc(p, kStUhFromU1, st, 1);
+    k_uh_from_u1<<<dim3(p->n1, B), kFftThreads, (size_t)p->L1max * 17 / 2, st>>>(d, u1, w.uh);
+  }
+  if (gs2t && !p->rowitems.empty()) {
+    StageScope sc(p, kStJointBwd, st, 1);
+    k_scat1d_bwd_rows<<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
+                        (size_t)p->rows_cap * 17 / 2, st>>>(
+        d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, gs2t, w.gy);
+  } else if (p->y_len > 0) {
+    cudaMemsetAsync(w.gy, 0, (size_t)B * p->y_len * sizeof(float2), st);
+  }
+  {
+    StageScope sc(p, kStSecondOrderBwd, st, 2);
+    if (!p->rowitems.empty())
+      k_gy_spectra<<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
+                     (size_t)p->rows_cap * 17 / 2, st>>>(
+          d, reinterpret_cast<const int4*>(p->d_rowitems), w.gy);
+    k_second_order_bwd<<<dim3(p->n1, B), 256, (size_t)p->L1max * 17 / 2, st>>>(d, w.gy, gs1, w.gu1);
+  }
+  {
+    StageScope sc(p, kStStage1Bwd, st, 1);
+    k_stage1_bwd<<<dim3(p->n1, B), kRowLaunch, (size_t)p->L1max * 17 / 2, st>>>(d, w.xh, w.gu1, w.gf);
+  }
+  {
+    StageScope sc(p, kStGx, st, 2);
+    k_gxh<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.gf, gs0, w.gxh);
+    k_gx<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, w.gxh, gs0, gx);
+  }
+  return cuda_check(cudaGetLastError(), "time scattering backward");
 }
 
 }  // namespace jtfs

@@ -11,6 +11,8 @@
 //                                 -> Y_alpha rows
 //   k_joint_fwd_simt            : per (c, alpha, signal): Z = W_c Y_alpha (zero-padded
 //                                 convolution along lambda), |Z|, phi_T then phi_F pooling -> S2
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -21,53 +23,56 @@
 namespace jtfs {
 namespace {
 
+namespace cg = cooperative_groups;
+
 // S0[t] = sum_n phi_T[(tT - n) mod N] x[n], in the time domain from x itself, to about FP64
 // accuracy.  For band-pass inputs S0 is a small difference of large terms: for click trains
 // through resonators |S0| is about 2e-6 of sum |phi_T x|, below the rounding of FP32 weights
 // and products.  So every term is formed exactly in two FP32 parts, phi_T = hi + lo and
-// hi x = p + e (e from an FMA), and summed with a Neumaier (sum, correction) pair per frame;
-// the per-thread pairs are added in FP64.  The spectral form from x-hat would inherit the FP32
-// FFT's rounding, which is of the size of S0 itself for such inputs.  One block per
-// (16 frames, signal).
-constexpr int kS0Frames = 16, kS0Threads = 512;
+// hi x = p + e (e from an FMA), and summed with a Neumaier (sum, correction) pair per thread;
+// the pairs are added in FP64.  The spectral form from x-hat would inherit the FP32 FFT's
+// rounding, which is of the size of S0 itself for such inputs.
+// One cluster of kS0Split CTAs per (frame, signal): CTA r sums the r-th slice of the samples
+// (weights and samples both read contiguously) and hands its FP64 partial to CTA 0 through
+// distributed shared memory, which adds them in a fixed order.
+constexpr int kS0Split = 8, kS0Threads = 256;
 
-__global__ void __launch_bounds__(kS0Threads)
+__global__ void __cluster_dims__(kS0Split, 1, 1) __launch_bounds__(kS0Threads)
 k_s0(DevPlan P, const float* __restrict__ x, float* __restrict__ s0) {
-  __shared__ double red[kS0Frames][kS0Threads / 32];
-  const int t0 = blockIdx.x * kS0Frames, b = blockIdx.y;
-  const int nf = min(kS0Frames, P.n_t - t0);
+  __shared__ double red[kS0Threads / 32];
+  __shared__ double parts[kS0Split];
+  cg::cluster_group cl = cg::this_cluster();
+  const int part = (int)cl.block_rank(), t = blockIdx.x / kS0Split, b = blockIdx.y;
+  const int chunk = P.N / kS0Split;
   const float* xb = x + (size_t)b * P.N;
-  float sum[kS0Frames], cor[kS0Frames];
-#pragma unroll
-  for (int f = 0; f < kS0Frames; ++f) sum[f] = cor[f] = 0.f;
-  for (int n = threadIdx.x; n < P.N; n += blockDim.x) {
-    const float v = xb[n];
-#pragma unroll
-    for (int f = 0; f < kS0Frames; ++f) {
-      if (f >= nf) break;
-      const int k = (int)(((long long)(t0 + f) * P.T - n) & (P.N - 1));
-      const float hi = __ldg(&P.phiT[k]), lo = __ldg(&P.phiT_lo[k]);
-      const float pr = __fmul_rn(hi, v);
-      const float e = fmaf(lo, v, fmaf(hi, v, -pr));
-      const float u = __fadd_rn(sum[f], pr);
-      const float d = fabsf(sum[f]) >= fabsf(pr) ? __fadd_rn(__fsub_rn(sum[f], u), pr)
-                                                 : __fadd_rn(__fsub_rn(pr, u), sum[f]);
-      cor[f] = __fadd_rn(cor[f], __fadd_rn(d, e));
-      sum[f] = u;
-    }
+  const long long tT = (long long)t * P.T;
+  float sum = 0.f, cor = 0.f;
+  for (int n = part * chunk + threadIdx.x; n < (part + 1) * chunk; n += blockDim.x) {
+    const int k = (int)((tT - n) & (P.N - 1));
+    const float v = xb[n], hi = __ldg(&P.phiT[k]), lo = __ldg(&P.phiT_lo[k]);
+    const float pr = __fmul_rn(hi, v);
+    const float e = fmaf(lo, v, fmaf(hi, v, -pr));
+    const float u = __fadd_rn(sum, pr);
+    const float d = fabsf(sum) >= fabsf(pr) ? __fadd_rn(__fsub_rn(sum, u), pr)
+                                            : __fadd_rn(__fsub_rn(pr, u), sum);
+    cor = __fadd_rn(cor, __fadd_rn(d, e));
+    sum = u;
   }
+  double acc = (double)sum + (double)cor;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-#pragma unroll
-  for (int f = 0; f < kS0Frames; ++f) {
-    double acc = (double)sum[f] + (double)cor[f];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (l == 0) red[f][w] = acc;
-  }
+  if (l == 0) red[w] = acc;
   __syncthreads();
-  if (threadIdx.x < nf) {
-    double acc = 0.0;
-    for (int i = 0; i < kS0Threads / 32; ++i) acc += red[threadIdx.x][i];
-    s0[(size_t)b * P.n_t + t0 + threadIdx.x] = (float)acc;
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int i = 0; i < kS0Threads / 32; ++i) v += red[i];
+    cl.map_shared_rank(parts, 0)[part] = v;
+  }
+  cl.sync();
+  if (part == 0 && threadIdx.x == 0) {
+    double v = 0.0;
+    for (int r = 0; r < kS0Split; ++r) v += parts[r];
+    s0[(size_t)b * P.n_t + t] = (float)v;
   }
 }
 
@@ -274,6 +279,41 @@ __global__ void k_transpose_yt(DevPlan P, int a, const float* __restrict__ y,
   }
 }
 
+// Time scattering (Scattering1D, the baseline of Sec. 4.4): the second order without the
+// log-frequency stage, S2t[alpha][lambda'][t] = sum_m s_alpha phi_T[(t T - m s_alpha) mod N]
+// |Y_alpha[lambda'][m]|.  One CTA per G rows of one rate: the rows are folded and inverse
+// transformed in shared memory as for the Y producer, their moduli replace them there, and
+// each warp reduces one (row, frame) output at a time; Y never leaves the chip.
+__global__ void __launch_bounds__(kRowThreads)
+k_scat1d_rows(DevPlan P, const int4* __restrict__ items, const float2* __restrict__ uh,
+              float* __restrict__ s2t) {
+  extern __shared__ float2 sm[];
+  __shared__ int s_off[kMaxRowsPerItem], s_kend[kMaxRowsPerItem];
+  __shared__ float s_inv[kMaxRowsPerItem];
+  const int4 it = items[blockIdx.x];
+  const int a = it.x, lam0 = it.y, G = it.z, b = blockIdx.y;
+  const Rate2 A = P.rates2[a];
+  const int L = A.L, logL = A.logL, nt = P.n_t;
+  second_order_rows_ifft(P, A, a, lam0, G, uh + (size_t)b * P.uh_len, sm, s_off, s_kend, s_inv);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
+    const float2 v = sm[fft_pad(idx)];
+    sm[fft_pad(idx)].x = sqrtf(v.x * v.x + v.y * v.y) * s_inv[idx >> logL];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int o = warp; o < G * nt; o += nw) {
+    const int r = o / nt, t = o - r * nt;
+    float acc = 0.f;
+    for (int m = lane; m < L; m += 32)
+      acc = fmaf(__ldg(&P.phiT[((long long)t * P.T - (long long)m * A.s) & (P.N - 1)]),
+                 sm[fft_pad((r << logL) + m)].x, acc);
+    for (int q = 16; q > 0; q >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, q);
+    if (lane == 0)
+      s2t[(((size_t)b * P.n2 + a) * P.n1 + lam0 + r) * nt + t] = acc * (float)A.s;
+  }
+}
+
 // cudaFuncSetAttribute acts on the current device only, so the raised shared-memory limits
 // are recorded per device (the plan's device is current in every call that launches).
 std::mutex g_attrs_mu;
@@ -297,6 +337,7 @@ jtfs_status set_attrs(const jtfs_plan* p) {
   if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_second_order_rows<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
   if ((st = cuda_check(cudaFuncSetAttribute(k_joint_fwd_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, big), "attr")) != JTFS_OK) return st;
+  if ((st = cuda_check(cudaFuncSetAttribute(k_scat1d_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, rows_smem), "attr")) != JTFS_OK) return st;
   g_attrs_set[p->device] = true;
   return JTFS_OK;
 }
@@ -390,6 +431,39 @@ jtfs_status autotune_rows(jtfs_plan* p, int B, const Workspace& w, cudaStream_t 
   return JTFS_OK;
 }
 
+
+// Time scattering forward: the first order as in the transform (S0, S1, the U1 checkpoint and
+// its row spectra), then the second-order moduli pooled per (alpha, lambda') path.  s2t is
+// [B][n2][n1][n_t], zero outside the paths (skipped rates, rows below lam_min).
+jtfs_status launch_scat1d_forward(const jtfs_plan* p, const float* x, int B, float* s0, float* s1,
+                                  float* s2t, float* u1, const Workspace& w, cudaStream_t st) {
+  jtfs_status rc = set_attrs(p);
+  if (rc != JTFS_OK) return rc;
+  const DevPlan& d = p->dp;
+  {
+    StageScope sc(p, kStXfft, st, 2);
+    k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, w.xsub);
+    k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, w.xsub, w.xh);
+  }
+  {
+    StageScope sc(p, kStS0, st, 1);
+    k_s0<<<dim3(kS0Split * p->n_t, B), kS0Threads, 0, st>>>(d, x, s0);
+  }
+  {
+    StageScope sc(p, kStScalogram, st, 1);
+    k_scalogram<<<dim3(p->n1, B), kRowLaunch, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, w.xh, u1, w.uh, s1);
+  }
+  if ((rc = cuda_check(cudaMemsetAsync(s2t, 0, (size_t)B * p->n2 * p->n1 * p->n_t * sizeof(float), st), "memset")) != JTFS_OK)
+    return rc;
+  if (!p->rowitems.empty()) {
+    StageScope sc(p, kStSecondOrder, st, 1);
+    k_scat1d_rows<<<dim3((unsigned)(p->rowitems.size() / 4), B), p->row_threads,
+                    (size_t)p->rows_cap * 17 / 2, st>>>(
+        d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, s2t);
+  }
+  return cuda_check(cudaGetLastError(), "time scattering forward");
+}
+
 jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0, float* s1,
                            float* s2, float* u1, const Workspace& w, cudaStream_t st) {
   jtfs_status rc = set_attrs(p);
@@ -402,7 +476,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   }
   {
     StageScope sc(p, kStS0, st, 1);
-    k_s0<<<dim3((p->n_t + kS0Frames - 1) / kS0Frames, B), kS0Threads, 0, st>>>(d, x, s0);
+    k_s0<<<dim3(kS0Split * p->n_t, B), kS0Threads, 0, st>>>(d, x, s0);
   }
   {
     StageScope sc(p, kStScalogram, st, 1);
@@ -527,7 +601,7 @@ jtfs_status launch_first_order_static(const jtfs_plan* p, const float* x, int B,
   const DevPlan& d = p->dp;
   k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, xsub);
   k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, xsub, xh);
-  k_s0<<<dim3((p->n_t + kS0Frames - 1) / kS0Frames, B), kS0Threads, 0, st>>>(d, x, s0);
+  k_s0<<<dim3(kS0Split * p->n_t, B), kS0Threads, 0, st>>>(d, x, s0);
   k_scalogram<<<dim3(p->n1, B), kRowLaunch, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, xh, u1, uh, s1);
   return cuda_check(cudaGetLastError(), "first-order static launch");
 }

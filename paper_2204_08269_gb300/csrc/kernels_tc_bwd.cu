@@ -1556,16 +1556,16 @@ size_t tcb_smem_bytes(int NT, int PL) {
          2 * (size_t)PL * g1 + (size_t)PL * a4 + (size_t)na2 * PL * 2 * 128 * 64;
 }
 
-bool tcb_supported(const jtfs_plan* p) {
-  // the resident Y^T tile holds at most 160 lambda' rows from a 64-aligned start
-  for (int a = 0; a < p->n2; ++a) {
-    const Rate2& A = p->rates2[a];
-    if (A.s == 0) continue;
-    const int start = A.lam_min / 64 * 64;
-    if (p->n1 - start > kK1Max) return false;
-  }
-  return tc_nt(p->n_t) <= 64;
+// The resident Y^T tile of the tensor-core backward holds at most 160 lambda' rows from a
+// 64-aligned start; a rate with more (lam_min = 0 at n1 > 160, e.g. J = 13, Q = 16) runs on the
+// CUDA-core backward instead, alone (it is a few per cent of the work there: those rates have
+// the shortest rows).
+static bool tcb_rate_fits(const jtfs_plan* p, int a) {
+  const Rate2& A = p->rates2[a];
+  return A.s == 0 || p->n1 - A.lam_min / 64 * 64 <= kK1Max;
 }
+
+bool tcb_supported(const jtfs_plan* p) { return tc_nt(p->n_t) <= 64; }
 
 jtfs_status build_tcb_tables(jtfs_plan* p) {
   const int NT = tc_nt(p->n_t);
@@ -1589,9 +1589,21 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   const bool use_f1 = use_p1 || tcbf_layout(p, 1, &wb_, &na2_, &smem_);
   const bool use_f2 = use_p2 || tcbf_layout(p, 2, &wb_, &na2_, &smem_);
   const int km2 = use_p2 ? 128 : tcbf_km(p, 2);
+  p->tcb_fb_items.clear();
+  p->tcb_fb_rowitems.clear();
+  p->tcb_fb_cap = 0;
   for (int a = 0; a < p->n2; ++a) {
     const Rate2& A = p->rates2[a];
     if (A.s == 0) continue;
+    if (!tcb_rate_fits(p, a)) {
+      for (int n0 = 0; n0 < A.L; n0 += 32) { p->tcb_fb_items.push_back(a); p->tcb_fb_items.push_back(n0); }
+      for (size_t i = 0; i + 3 < p->rowitems.size(); i += 4)
+        if (p->rowitems[i] == a) {
+          for (int q = 0; q < 4; ++q) p->tcb_fb_rowitems.push_back(p->rowitems[i + q]);
+          p->tcb_fb_cap = std::max(p->tcb_fb_cap, p->rowitems[i + 2] * A.L);
+        }
+      continue;
+    }
     const int lm8 = A.lam_min & ~7;
     const int K1f = (p->n1 - lm8 + 15) / 16 * 16;
     const int start = A.lam_min / 64 * 64;
@@ -1640,6 +1652,8 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   const size_t o_row0 = place((size_t)p->n2 * 4);
   const size_t o_items = place(std::max<size_t>(16, p->tcb_items.size() * 4));
   const size_t o_fitems = place(std::max<size_t>(16, p->tcbf_items.size() * 4));
+  const size_t o_fb = place(std::max<size_t>(16, p->tcb_fb_items.size() * 4));
+  const size_t o_fbrow = place(std::max<size_t>(16, p->tcb_fb_rowitems.size() * 4));
   jtfs_status st;
   if ((st = cuda_check(cudaMalloc(&p->d_tcb_mem, off), "tc backward tables")) != JTFS_OK) return st;
   char* base = (char*)p->d_tcb_mem;
@@ -1647,6 +1661,13 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   p->d_wtb_row0 = (int*)(base + o_row0);
   p->d_tcb_items = (int*)(base + o_items);
   p->d_tcbf_items = (int*)(base + o_fitems);
+  p->d_tcb_fb_items = (int*)(base + o_fb);
+  p->d_tcb_fb_rowitems = (int*)(base + o_fbrow);
+  for (auto& v : {std::make_pair(&p->tcb_fb_items, p->d_tcb_fb_items),
+                  std::make_pair(&p->tcb_fb_rowitems, p->d_tcb_fb_rowitems)})
+    if (!v.first->empty() &&
+        (st = cuda_check(cudaMemcpy(v.second, v.first->data(), v.first->size() * 4, cudaMemcpyHostToDevice), "upload")) != JTFS_OK)
+      return st;
   if (!p->tcbf_items.empty() &&
       (st = cuda_check(cudaMemcpy(p->d_tcbf_items, p->tcbf_items.data(), p->tcbf_items.size() * 4, cudaMemcpyHostToDevice), "upload")) != JTFS_OK)
     return st;

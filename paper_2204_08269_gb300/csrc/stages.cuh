@@ -78,20 +78,16 @@ __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R
 constexpr int kRowThreads = 512;
 constexpr int kMaxRowsPerItem = 512;   // G <= rows_cap / 32
 
-template <int OUT_BF16>
-__global__ void __launch_bounds__(kRowThreads)
-k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __restrict__ uh,
-                    float2* __restrict__ y, __nv_bfloat16* __restrict__ yhi,
-                    __nv_bfloat16* __restrict__ ylo, int B) {
-  extern __shared__ float2 sm[];
-  __shared__ int s_off[kMaxRowsPerItem], s_kend[kMaxRowsPerItem];
-  __shared__ float s_inv[kMaxRowsPerItem];
-  const int4 it = items[blockIdx.x];
-  const int a = it.x, lam0 = it.y, G = it.z, b = blockIdx.y;
-  const Rate2 A = P.rates2[a];
+// Folds the G rows lam0 .. lam0 + G - 1 of rate a (U1-hat * psi-hat_alpha onto L_alpha bins)
+// into sm in bit-reversed padded order and runs their batched inverse FFT; s_inv[r] receives
+// the scale 1 / L of first-order row lam0 + r.  The producer of Y_alpha and the time-scattering
+// kernels share it.
+__device__ __forceinline__ void second_order_rows_ifft(const DevPlan& P, const Rate2& A, int a,
+                                                       int lam0, int G, const float2* ub,
+                                                       float2* sm, int* s_off, int* s_kend,
+                                                       float* s_inv) {
   const float* psi = P.psi2 + (size_t)a * P.K2max;
   const int L = A.L, logL = A.logL;
-  const float2* ub = uh + (size_t)b * P.uh_len;
   for (int r = threadIdx.x; r < G; r += blockDim.x) {
     const Row1 R = P.rows1[lam0 + r];
     s_off[r] = R.off_uh;
@@ -114,6 +110,21 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
   }
   __syncthreads();
   fft_dit_rows_r16<+1>(sm, logL, G, twl_for(P, logL));
+}
+
+template <int OUT_BF16>
+__global__ void __launch_bounds__(kRowThreads)
+k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __restrict__ uh,
+                    float2* __restrict__ y, __nv_bfloat16* __restrict__ yhi,
+                    __nv_bfloat16* __restrict__ ylo, int B) {
+  extern __shared__ float2 sm[];
+  __shared__ int s_off[kMaxRowsPerItem], s_kend[kMaxRowsPerItem];
+  __shared__ float s_inv[kMaxRowsPerItem];
+  const int4 it = items[blockIdx.x];
+  const int a = it.x, lam0 = it.y, G = it.z, b = blockIdx.y;
+  const Rate2 A = P.rates2[a];
+  const int L = A.L, logL = A.logL;
+  second_order_rows_ifft(P, A, a, lam0, G, uh + (size_t)b * P.uh_len, sm, s_off, s_kend, s_inv);
   if (OUT_BF16 == 0) {
     float2* ya = y + (size_t)b * P.y_len + A.off_y + (size_t)(lam0 - A.lam_min) * L;
     for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {

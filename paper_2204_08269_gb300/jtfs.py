@@ -39,11 +39,13 @@ BRANCHES = {"psi_psi": 1, "psi_phi": 2, "phi_psi": 4, "phi_phi": 8}
 
 
 def _branch_mask(branches):
+    """jtfs_config.branches from None (the psi_t paths), a bit mask, or names; the psi_t paths
+    (psi_psi, psi_phi) are always included."""
     if branches is None:
         return 0
     if isinstance(branches, int):
         return branches
-    m = 0
+    m = BRANCHES["psi_psi"] | BRANCHES["psi_phi"]
     for b in branches:
         m |= BRANCHES[b]
     return m
@@ -76,6 +78,8 @@ def lib():
         "jtfs_forward_backward": ([_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P],
                                   _I32),
         "jtfs_host_step_bytes": ([_P, _I64, ctypes.POINTER(_SZ)], _I32),
+        "jtfs_scattering1d_forward": ([_P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P], _I32),
+        "jtfs_scattering1d_backward": ([_P, _P, _P, _I64, _P, _P, _P, _P, _P, _SZ, _P], _I32),
         "jtfs_forward_backward_host": ([_P, _P, _I64, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P,
                                         _SZ, _P], _I32),
         "jtfs_sync_status": ([_P, _P], _I32),
@@ -96,6 +100,9 @@ def lib():
         "jtfs_varlen_capture": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P], _I32),
         "jtfs_varlen_replay": ([_P, _P], _I32),
         "jtfs_varlen_autotune": ([_P, _P, _SZ, _P], _I32),
+        "jtfs_mulog_mean": ([_P, _I64, _I64, _I64, _P, _P], _I32),
+        "jtfs_mulog": ([_P, _I64, _I64, _I64, _P, ctypes.c_float, _P, _P], _I32),
+        "jtfs_mulog_backward": ([_P, _I64, _I64, _I64, _P, ctypes.c_float, _P, _P, _P], _I32),
         "jtfs_status_string": ([_I32], ctypes.c_char_p),
         "jtfs_last_error": ([], ctypes.c_char_p),
     }
@@ -111,7 +118,7 @@ def exported_symbols():
     """Names the binding expects the library to export (one per declaration in jtfs.h)."""
     return ["jtfs_plan_create", "jtfs_plan_destroy", "jtfs_plan_shapes", "jtfs_plan_schedule",
             "jtfs_workspace_bytes", "jtfs_forward", "jtfs_backward", "jtfs_forward_backward",
-            "jtfs_host_step_bytes",
+            "jtfs_host_step_bytes", "jtfs_scattering1d_forward", "jtfs_scattering1d_backward",
             "jtfs_forward_backward_host", "jtfs_sync_status", "jtfs_plan_set_wait_budget",
             "jtfs_plan_set_check_finite", "jtfs_diagnose_wait_timeout", "jtfs_status_string",
             "jtfs_last_error", "jtfs_profile_enable", "jtfs_profile_read",
@@ -119,7 +126,8 @@ def exported_symbols():
             "jtfs_varlen_padded_length",
             "jtfs_varlen_create", "jtfs_varlen_destroy", "jtfs_varlen_layout",
             "jtfs_varlen_workspace_bytes", "jtfs_varlen_forward_backward", "jtfs_varlen_capture",
-            "jtfs_varlen_replay", "jtfs_varlen_autotune"]
+            "jtfs_varlen_replay", "jtfs_varlen_autotune", "jtfs_mulog_mean", "jtfs_mulog",
+            "jtfs_mulog_backward"]
 
 
 class JTFSError(RuntimeError):
@@ -293,6 +301,36 @@ class JTFSPlan:
             _ptr(s2), _ptr(u1), _ptr(gx), _ptr(ws), ws.numel(), _stream()))
         return (s0, s1, s2, gx, u1) if keep_checkpoint else (s0, s1, s2, gx)
 
+    def scattering1d(self, x, keep_checkpoint=True):
+        """Time scattering (Sec. 4.4 baseline) on this plan's filterbanks: S0 [B, n_t], S1
+        [B, n1, n_t], S2t [B, n2, n1, n_t] (0 outside the (alpha, lambda') paths) and the U1
+        checkpoint."""
+        self._check_x(x)
+        B = x.shape[0]
+        sh = self.shapes
+        dev = x.device
+        s0 = torch.empty(sh.s0(B), dtype=torch.float32, device=dev)
+        s1 = torch.empty(sh.s1(B), dtype=torch.float32, device=dev)
+        s2t = torch.empty((B, sh.n2, sh.n1, sh.n_t), dtype=torch.float32, device=dev)
+        u1 = torch.empty((B, sh.u1_len), dtype=torch.float32, device=dev) if keep_checkpoint else None
+        ws = self.workspace(B, True)
+        _check("jtfs_scattering1d_forward", lib().jtfs_scattering1d_forward(
+            self._h, _ptr(x), B, _ptr(s0), _ptr(s1), _ptr(s2t), _ptr(u1), _ptr(ws), ws.numel(),
+            _stream()))
+        return s0, s1, s2t, u1
+
+    def scattering1d_backward(self, x, u1, g_s0=None, g_s1=None, g_s2t=None):
+        """g_x of <g, S(x)> for the time scattering outputs (cotangents may be None)."""
+        self._check_x(x)
+        B = x.shape[0]
+        gx = torch.empty_like(x)
+        ws = self.workspace(B, True)
+        gs = [None if g is None else g.contiguous() for g in (g_s0, g_s1, g_s2t)]
+        _check("jtfs_scattering1d_backward", lib().jtfs_scattering1d_backward(
+            self._h, _ptr(x), _ptr(u1), B, _ptr(gs[0]), _ptr(gs[1]), _ptr(gs[2]), _ptr(gx),
+            _ptr(ws), ws.numel(), _stream()))
+        return gx
+
     def forward_backward_host(self, x_host, g_s0=None, g_s1=None, g_s2=None, outputs=True):
         """End-to-end step from pinned (or pageable) host tensors: H2D, forward, backward,
         D2H, all inside one library call.  Returns (s0, s1, s2, g_x) host tensors."""
@@ -359,6 +397,36 @@ class JTFSPlan:
     def check_finite(self, on=True):
         """Scan every output for NaN / Inf after each call (reported by sync())."""
         _check("jtfs_plan_set_check_finite", lib().jtfs_plan_set_check_finite(self._h, int(on)))
+
+
+def mulog_mean(s):
+    """Eq. 6: mu [P] of a device array S [B, P, ...] (mean over examples of each path's sum)."""
+    s = s.contiguous()
+    B, P = s.shape[0], s.shape[1]
+    M = s[0, 0].numel()
+    mu = torch.empty(P, dtype=torch.float32, device=s.device)
+    _check("jtfs_mulog_mean", lib().jtfs_mulog_mean(_ptr(s), B, P, M, _ptr(mu), _stream()))
+    return mu
+
+
+def mulog(s, mu, eps=0.1):
+    """Eq. 7: log(1 + S / (eps mu[path])) for S [B, P, ...] on the device."""
+    s = s.contiguous()
+    out = torch.empty_like(s)
+    B, P = s.shape[0], s.shape[1]
+    _check("jtfs_mulog", lib().jtfs_mulog(_ptr(s), B, P, s[0, 0].numel(), _ptr(mu.contiguous()),
+                                          float(eps), _ptr(out), _stream()))
+    return out
+
+
+def mulog_backward(s, mu, g_out, eps=0.1):
+    s = s.contiguous()
+    gs = torch.empty_like(s)
+    B, P = s.shape[0], s.shape[1]
+    _check("jtfs_mulog_backward", lib().jtfs_mulog_backward(
+        _ptr(s), B, P, s[0, 0].numel(), _ptr(mu.contiguous()), float(eps),
+        _ptr(g_out.contiguous()), _ptr(gs), _stream()))
+    return gs
 
 
 class JTFSFunction(torch.autograd.Function):

@@ -203,3 +203,19 @@ def test_time_pooling_is_a_product_on_the_aliased_lowpass_spectrum(cfg):
             assert np.max(np.abs(gu.imag)) < 1e-12 * np.max(np.abs(gu.real))
             assert _rel(gu.real, g @ Phi) < 1e-12, s
         s *= 2
+
+
+def test_mu_log_definitions():
+    """Eq. 6-7: mu is the mean over examples of each path's sum over (lambda, t) (checked by an
+    explicit loop); the compression is invariant to one scale factor applied to the whole
+    dataset (mu scales with it), increasing in S, and 0 where S = 0."""
+    rng = np.random.default_rng(40)
+    S = rng.gamma(2.0, 1.0, size=(5, 7, 3, 4))
+    mu = O.mu_log_mean(S)
+    for p in range(7):
+        assert abs(mu[p] - sum(S[n, p].sum() for n in range(5)) / 5) < 1e-12 * mu[p]
+    a = O.mu_log(S, mu)
+    b = O.mu_log(3.7 * S, O.mu_log_mean(3.7 * S))
+    assert np.max(np.abs(a - b)) < 1e-14
+    assert np.all(O.mu_log(S + 1.0, mu) > a)
+    assert np.all(O.mu_log(np.zeros_like(S), mu) == 0.0)
