@@ -1556,13 +1556,15 @@ size_t tcb_smem_bytes(int NT, int PL) {
          2 * (size_t)PL * g1 + (size_t)PL * a4 + (size_t)na2 * PL * 2 * 128 * 64;
 }
 
-// The resident Y^T tile of the tensor-core backward holds at most 160 lambda' rows from a
-// 64-aligned start; a rate with more (lam_min = 0 at n1 > 160, e.g. J = 13, Q = 16) runs on the
-// CUDA-core backward instead, alone (it is a few per cent of the work there: those rates have
-// the shortest rows).
-static bool tcb_rate_fits(const jtfs_plan* p, int a) {
+// The resident Y^T tiles of the tensor-core backward hold at most 160 lambda' rows, from a
+// 64-aligned start in the channel-row forms and from lam_min rounded down to 8 in the spin-pair
+// forms; a rate with more (lam_min = 0 at n1 > 160, e.g. J = 13, Q = 16) runs on the CUDA-core
+// backward instead, alone (a few per cent of the work there: those rates have the shortest
+// rows).
+static bool tcb_rate_fits(const jtfs_plan* p, int a, bool pair_forms) {
   const Rate2& A = p->rates2[a];
-  return A.s == 0 || p->n1 - A.lam_min / 64 * 64 <= kK1Max;
+  if (A.s == 0 || p->n1 - A.lam_min / 64 * 64 <= kK1Max) return true;
+  return pair_forms && (p->n1 - (A.lam_min & ~7) + 15) / 16 * 16 <= kK1Max;
 }
 
 bool tcb_supported(const jtfs_plan* p) { return tc_nt(p->n_t) <= 64; }
@@ -1595,7 +1597,7 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   for (int a = 0; a < p->n2; ++a) {
     const Rate2& A = p->rates2[a];
     if (A.s == 0) continue;
-    if (!tcb_rate_fits(p, a)) {
+    if (!tcb_rate_fits(p, a, use_p3)) {
       for (int n0 = 0; n0 < A.L; n0 += 32) { p->tcb_fb_items.push_back(a); p->tcb_fb_items.push_back(n0); }
       for (size_t i = 0; i + 3 < p->rowitems.size(); i += 4)
         if (p->rowitems[i] == a) {

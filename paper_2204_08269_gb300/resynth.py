@@ -7,7 +7,9 @@ with the first-order scalogram as the only checkpoint, then ``jtfs_backward``); 
 reduction and the update are a few elementwise PyTorch operations on the device.
 
 Two update rules:
-  * ``"adam"``: Adam on y with learning rate ``lr`` (default 1e-2 times the target's RMS).
+  * ``"adam"``: Adam on y with learning rate ``lr`` (default 0.3 times the targets' RMS: over
+    50 steps on click-train targets at N = 2^17 the mean E fell to 1.00, 0.28, 0.13 and 0.088
+    for 0.01, 0.03, 0.1 and 0.3 times the RMS).
   * ``"bold"``: the bold-driver heuristic the paper uses.  Each signal keeps its own step
     size mu: a trial y - mu grad E that lowers E is accepted and mu grows by ``inc``; one that
     does not is rejected and mu shrinks by ``dec``.  The step descends (y - mu grad E), the
@@ -54,7 +56,7 @@ class Resynthesis:
         self.y = (torch.randn(target.shape, device=target.device, generator=gen) * rms)
         self.y.requires_grad_(True)
         if method == "adam":
-            self.opt = torch.optim.Adam([self.y], lr=lr if lr is not None else 1e-2 * rms)
+            self.opt = torch.optim.Adam([self.y], lr=lr if lr is not None else 0.3 * rms)
         else:
             self.inc, self.dec = inc, dec
             self.mu = None

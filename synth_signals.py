@@ -107,6 +107,30 @@ def chirp_eq5(N: int, fc: float, fm: float, gamma: float, sr: float = SR, w: flo
     return x.astype(np.float32)
 
 
+def eq5_grid(count: int = 16):
+    """The paper's Eq. 5 dataset parameters (Sec. 3.2): ``count`` values each of f_c
+    (512 to 1024 Hz), f_m (4 to 32 Hz) and gamma (0.5 to 4 octaves/s) in geometric progression,
+    all count^3 triplets, f_c varying slowest.  Returns an array [count^3, 3]."""
+    fc = np.geomspace(512.0, 1024.0, count)
+    fm = np.geomspace(4.0, 32.0, count)
+    gm = np.geomspace(0.5, 4.0, count)
+    g = np.stack(np.meshgrid(fc, fm, gm, indexing="ij"), axis=-1)
+    return g.reshape(-1, 3)
+
+
+def chirp_eq5_batch(N: int, params, sr: float = SR, w: float = 2.0):
+    """Eq. 5 chirps for every (f_c, f_m, gamma) row of ``params``: [len(params), N] float32."""
+    params = np.asarray(params, dtype=np.float64)
+    out = np.empty((len(params), N), dtype=np.float32)
+    t = (np.arange(N, dtype=np.float64) - N / 2) / sr
+    for i in range(0, len(params), 64):
+        fc, fm, gm = (params[i:i + 64, j][:, None] for j in range(3))
+        window = np.exp(-0.5 * (gm * t / (w / 2.0)) ** 2)
+        out[i:i + 64] = window * np.sin(2.0 * np.pi * fm * t) * np.sin(
+            2.0 * np.pi * fc / (gm * np.log(2.0)) * 2.0 ** (gm * t))
+    return out
+
+
 def varlen_lengths(count: int, seed: int, lo_log2: float = 13.0, hi_log2: float = 17.0):
     """Signal lengths drawn log-uniform in [2^lo, 2^hi]."""
     rng = _streams(seed, 1)[0]
