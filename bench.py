@@ -187,7 +187,7 @@ def run_ours(args):
     sh = plan.shapes
     x = torch.from_numpy(SS.workload_signals(2, BATCH, WORKLOAD["N"])).cuda()
     # the plan's launch shape of the row FFT stages, tuned once for this batch (untimed setup)
-    tuned = plan.autotune(BATCH)
+    tuned = None if args.no_autotune else plan.autotune(BATCH)
     gen = torch.Generator(device="cuda").manual_seed(1234 + rank)
     g0 = torch.randn(sh.s0(BATCH), device="cuda", generator=gen)
     g1 = torch.randn(sh.s1(BATCH), device="cuda", generator=gen)
@@ -371,7 +371,7 @@ def run_varlen(args):
     count = args.batch if args.batch != BATCH else 1024
     cfg = dict(J=12, Q=16, J_fr=4, Q_fr=2, T=2 ** 12, F=16)
     xh, lengths = SS.varlen_batch(count, SS.BASE_SEED + 5)
-    v = jtfs.JTFSVarlen(lengths, **cfg, precision=args.precision, chunk=64)
+    v = jtfs.JTFSVarlen(lengths, **cfg, precision=args.precision, chunk=args.chunk)
     x = torch.from_numpy(xh).cuda()
     g = [torch.ones(int(o[-1]), device="cuda") for o in (v.s0_off, v.s1_off, v.s2_off)]
     side = torch.cuda.Stream()
@@ -421,6 +421,7 @@ def run_varlen(args):
            "data": "synthetic (seeded AM/FM tones and click trains)",
            "config": {"workload": f"varlen, {count} signals, len log-uniform 2^13..2^17, J=12, Q=16, "
                                   "J_fr=4, Q_fr=2, T=2^12, F=16", "precision": args.precision,
+                      "signals_per_sub_batch": args.chunk,
                       "padded_lengths": {str(k): int(sum(1 for n in lengths if jtfs.varlen_padded_length(int(n), J=12) == k))
                                          for k in sorted(set(jtfs.varlen_padded_length(int(n), J=12) for n in lengths))}},
            "per_signal_launches": {"value": len(sample) / (ms_ps / 1e3), "unit": "signals/s",
@@ -562,8 +563,12 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "fp32_simt"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default row-FFT launch shape (profiling runs: no tuning launches)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="signals per GPU (the workload is 64; smaller values for profiling)")
+    ap.add_argument("--chunk", type=int, default=64,
+                    help="varlen: signals per sub-batch of one padded length (0: 64)")
     ap.add_argument("--workload", default="fixed", choices=["fixed", "varlen", "mixed", "resynth", "eq5"],
                     help="varlen: the uneven-length batch; mixed: forward by contraction "
                          "precision; resynth: texture resynthesis at N = 2^17 (none of them is "
