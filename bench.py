@@ -36,11 +36,12 @@ WORKLOAD_NAME = ("jtfs fwd+bwd, B=64 AM/FM tones, N=2^16 at 22050 Hz, J=12, Q=16
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                   "sm_max_mhz": 2070.0}
 SMS = 152
-# DRAM bytes (read + write) per step of the two contraction kernels at B = 64, from the ncu
-# capture summarised in profiles/ (captured at a smaller batch and scaled by the signals, the
-# kernels' traffic being proportional to them); None where no capture of the current kernels
+# DRAM bytes (read + write) per step of the contraction stages (forward and backward kernels
+# with their phi_F pooling / adjoint) at B = 64, from the ncu capture summarised in
+# profiles/dram_traffic_B16_N65536_fp32.md: 711.7 MB at B = 16, scaled by the signals (the
+# kernels' traffic is proportional to them); None where no capture of the current kernels
 # exists.
-CONTRACTION_TRAFFIC = {}
+CONTRACTION_TRAFFIC = {"fp32": 4 * 711.7e6}
 
 
 def _peaks():
@@ -263,7 +264,8 @@ def run_ours(args):
         roof = {"bound": "tensor", "kernel": "joint_fwd+joint_bwd (tcgen05 contraction)",
                 "achieved": flops / (joint_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
                 "peak_source": f"{peaks_kind} bf16 burst" + (" / 2 (tf32)" if args.precision == "tf32" else ""),
-                "traffic": CONTRACTION_TRAFFIC.get(args.precision)}
+                "traffic": (CONTRACTION_TRAFFIC.get(args.precision) if BATCH == 64 else None),
+                "traffic_unit": "bytes per step (both contraction launches)"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["launch_ms"] = joint_ms
     roof["flops_per_step"] = flops
