@@ -364,8 +364,9 @@ def run_reference(args):
 def run_varlen(args):
     """Uneven-length batch: J=12, Q=16, J_fr=4, Q_fr=2, T=2^12, F=16, lengths log-uniform in
     2^13..2^17, half AM/FM tones and half click trains; forward + backward with ones as
-    cotangents.  The step is one replay of the captured graph (autotuned launch shapes); the
-    comparison is one library call per signal (B = 1) on a sample of the batch."""
+    cotangents.  The step is one replay of the captured graph (autotuned launch shapes and
+    sub-batch size); the comparison is one library call per signal (B = 1) on a sample of the
+    batch."""
     import torch
     from paper_2204_08269_gb300 import jtfs
     import synth_signals as SS
@@ -379,6 +380,7 @@ def run_varlen(args):
     side = torch.cuda.Stream()
     with torch.cuda.stream(side):
         v.autotune()
+        chosen = v.tune_schedule(x, g)
         v.capture(x, g)
         for _ in range(args.warmup):
             v.replay()
@@ -423,7 +425,7 @@ def run_varlen(args):
            "data": "synthetic (seeded AM/FM tones and click trains)",
            "config": {"workload": f"varlen, {count} signals, len log-uniform 2^13..2^17, J=12, Q=16, "
                                   "J_fr=4, Q_fr=2, T=2^12, F=16", "precision": args.precision,
-                      "signals_per_sub_batch": args.chunk,
+                      "largest_sub_batch_tried": args.chunk, "tuned_sub_batch": chosen,
                       "padded_lengths": {str(k): int(sum(1 for n in lengths if jtfs.varlen_padded_length(int(n), J=12) == k))
                                          for k in sorted(set(jtfs.varlen_padded_length(int(n), J=12) for n in lengths))}},
            "per_signal_launches": {"value": len(sample) / (ms_ps / 1e3), "unit": "signals/s",
@@ -569,8 +571,9 @@ def main():
                     help="keep the default row-FFT launch shape (profiling runs: no tuning launches)")
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="signals per GPU (the workload is 64; smaller values for profiling)")
-    ap.add_argument("--chunk", type=int, default=64,
-                    help="varlen: signals per sub-batch of one padded length (0: 64)")
+    ap.add_argument("--chunk", type=int, default=512,
+                    help="varlen: the largest sub-batch of one padded length the schedule "
+                         "tuner tries (the workspace is sized for it)")
     ap.add_argument("--workload", default="fixed", choices=["fixed", "varlen", "mixed", "resynth", "eq5"],
                     help="varlen: the uneven-length batch; mixed: forward by contraction "
                          "precision; resynth: texture resynthesis at N = 2^17 (none of them is "

@@ -282,6 +282,18 @@ jtfs_status jtfs_varlen_replay(const jtfs_varlen* v, void* stream);
  * was recorded with. */
 jtfs_status jtfs_varlen_autotune(jtfs_varlen* v, void* ws, size_t ws_bytes, void* stream);
 
+/* Schedule autotuner of the uneven-length step (the paper has no counterpart): times the whole
+ * step (jtfs_varlen_forward_backward on these buffers, which it overwrites) with sub-batches of
+ * 16, 32, 64, ... signals up to the `chunk` given at creation (and that size), keeps the
+ * fastest split and writes its size to chosen[0] (host, may be NULL).  The results do not
+ * depend on the split.  Drops a captured graph (capture again afterwards).  ws as
+ * jtfs_varlen_workspace_bytes (sized for the creation's chunk, so every candidate fits).
+ * Synchronous. */
+jtfs_status jtfs_varlen_tune_schedule(jtfs_varlen* v, const float* x_packed, const float* g_s0,
+                                      const float* g_s1, const float* g_s2, float* s0, float* s1,
+                                      float* s2, float* g_x, void* ws, size_t ws_bytes,
+                                      void* stream, int32_t* chosen);
+
 /* ---------------------------------------------------------------------------------------
  * Failure detection.  The paper has no counterpart; these calls report faults instead of
  * hanging or returning silently wrong numbers.

@@ -82,10 +82,14 @@ struct jtfs_varlen {
     int* d_frames;
   };
   std::vector<jtfs_plan*> plans;
+  std::vector<std::pair<jtfs_plan*, std::vector<int>>> buckets;   // plan, signals (in order)
+  std::vector<int> frames;
   std::vector<Chunk> chunks;
   void* d_meta = nullptr;
-  size_t ws_bytes = 0;     // per chunk: plan workspace + padded batch buffers
-  int chunk_max = 64;
+  size_t ws_bytes = 0;     // the current chunks': plan workspace + padded batch buffers
+  size_t ws_cap = 0;       // the workspace the caller sizes: that of chunks of chunk_max
+  int chunk_max = 64;      // sub-batch size given at creation (the largest one tried)
+  int chunk = 64;          // sub-batch size in use
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
 };
@@ -157,6 +161,69 @@ jtfs_status vl_run(const jtfs_varlen* v, const float* x, const float* gs0, const
   return JTFS_OK;
 }
 
+// Splits every bucket into sub-batches of at most `chunk` signals and uploads their index
+// tables (per sub-batch [xoff][s0off][s1off][s2off] as int64, then [len][frames] as int32),
+// replacing earlier ones; sets ws_bytes for them.
+jtfs_status vl_build_chunks(jtfs_varlen* v, int chunk) {
+  if (v->d_meta) { cudaFree(v->d_meta); v->d_meta = nullptr; }
+  v->chunks.clear();
+  v->ws_bytes = 0;
+  v->chunk = chunk;
+  struct Pending { jtfs_plan* plan; std::vector<int> idx; };
+  std::vector<Pending> pend;
+  for (auto& bk : v->buckets) {
+    const auto& ids = bk.second;
+    for (size_t s = 0; s < ids.size(); s += (size_t)chunk) {
+      Pending pc;
+      pc.plan = bk.first;
+      pc.idx.assign(ids.begin() + s, ids.begin() + std::min(ids.size(), s + (size_t)chunk));
+      pend.push_back(pc);
+    }
+  }
+  std::vector<char> host;
+  std::vector<size_t> at;
+  for (auto& pc : pend) {
+    const size_t n = pc.idx.size();
+    at.push_back(host.size());
+    const size_t bytes = ((n * 8 * 4 + n * 4 * 2) + 255) & ~(size_t)255;
+    const size_t o = host.size();
+    host.resize(o + bytes, 0);
+    long long* L64 = (long long*)(host.data() + o);
+    int* L32 = (int*)(host.data() + o + n * 8 * 4);
+    for (size_t k = 0; k < n; ++k) {
+      const int i = pc.idx[k];
+      L64[k] = v->x_off[i];
+      L64[n + k] = v->s0_off[i];
+      L64[2 * n + k] = v->s1_off[i];
+      L64[3 * n + k] = v->s2_off[i];
+      L32[k] = (int)v->len[i];
+      L32[n + k] = v->frames[i];
+    }
+  }
+  jtfs_status rc;
+  if ((rc = cuda_check(cudaMalloc(&v->d_meta, std::max<size_t>(256, host.size())), "varlen tables")) != JTFS_OK ||
+      (rc = cuda_check(cudaMemcpy(v->d_meta, host.data(), host.size(), cudaMemcpyHostToDevice), "varlen upload")) != JTFS_OK)
+    return rc;
+  for (size_t c = 0; c < pend.size(); ++c) {
+    const size_t n = pend[c].idx.size();
+    char* base = (char*)v->d_meta + at[c];
+    jtfs_varlen::Chunk ch;
+    ch.plan = pend[c].plan;
+    ch.count = (int)n;
+    ch.d_xoff = (long long*)base;
+    ch.d_s0off = ch.d_xoff + n;
+    ch.d_s1off = ch.d_xoff + 2 * n;
+    ch.d_s2off = ch.d_xoff + 3 * n;
+    ch.d_len = (int*)(base + n * 8 * 4);
+    ch.d_frames = ch.d_len + n;
+    v->chunks.push_back(ch);
+    size_t pws = 0;
+    jtfs_workspace_bytes(ch.plan, (int64_t)n, 1, &pws);
+    v->ws_bytes = std::max(v->ws_bytes, vl_batch_bytes(ch.plan, (int)n) + pws);
+  }
+  return JTFS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -217,61 +284,13 @@ jtfs_status jtfs_varlen_create(const jtfs_config* cfg, const int64_t* len, int64
     v->s1_off[i + 1] = v->s1_off[i] + sh.n1 * frames[i];
     v->s2_off[i + 1] = v->s2_off[i] + sh.s2_paths * sh.n_lam_out * frames[i];
   }
-  // chunks and their device index tables: per chunk [xoff][s0off][s1off][s2off] (int64) then
-  // [len][frames] (int32)
-  struct Pending { jtfs_plan* plan; std::vector<int> idx; };
-  std::vector<Pending> pend;
-  for (auto& kv : buckets) {
-    const auto& ids = kv.second;
-    for (size_t s = 0; s < ids.size(); s += (size_t)v->chunk_max) {
-      Pending pc;
-      pc.plan = plan_of[kv.first];
-      pc.idx.assign(ids.begin() + s, ids.begin() + std::min(ids.size(), s + (size_t)v->chunk_max));
-      pend.push_back(pc);
-    }
-  }
-  std::vector<char> host;
-  std::vector<size_t> at;
-  for (auto& pc : pend) {
-    const size_t n = pc.idx.size();
-    at.push_back(host.size());
-    const size_t bytes = ((n * 8 * 4 + n * 4 * 2) + 255) & ~(size_t)255;
-    const size_t o = host.size();
-    host.resize(o + bytes, 0);
-    long long* L64 = (long long*)(host.data() + o);
-    int* L32 = (int*)(host.data() + o + n * 8 * 4);
-    for (size_t k = 0; k < n; ++k) {
-      const int i = pc.idx[k];
-      L64[k] = v->x_off[i];
-      L64[n + k] = v->s0_off[i];
-      L64[2 * n + k] = v->s1_off[i];
-      L64[3 * n + k] = v->s2_off[i];
-      L32[k] = (int)len[i];
-      L32[n + k] = frames[i];
-    }
-  }
-  if ((rc = cuda_check(cudaMalloc(&v->d_meta, std::max<size_t>(256, host.size())), "varlen tables")) != JTFS_OK ||
-      (rc = cuda_check(cudaMemcpy(v->d_meta, host.data(), host.size(), cudaMemcpyHostToDevice), "varlen upload")) != JTFS_OK) {
+  v->frames = frames;
+  for (auto& kv : buckets) v->buckets.push_back({plan_of[kv.first], kv.second});
+  if ((rc = vl_build_chunks(v, v->chunk_max)) != JTFS_OK) {
     jtfs_varlen_destroy(v);
     return rc;
   }
-  for (size_t c = 0; c < pend.size(); ++c) {
-    const size_t n = pend[c].idx.size();
-    char* base = (char*)v->d_meta + at[c];
-    jtfs_varlen::Chunk ch;
-    ch.plan = pend[c].plan;
-    ch.count = (int)n;
-    ch.d_xoff = (long long*)base;
-    ch.d_s0off = ch.d_xoff + n;
-    ch.d_s1off = ch.d_xoff + 2 * n;
-    ch.d_s2off = ch.d_xoff + 3 * n;
-    ch.d_len = (int*)(base + n * 8 * 4);
-    ch.d_frames = ch.d_len + n;
-    v->chunks.push_back(ch);
-    size_t pws = 0;
-    jtfs_workspace_bytes(ch.plan, (int64_t)n, 1, &pws);
-    v->ws_bytes = std::max(v->ws_bytes, vl_batch_bytes(ch.plan, (int)n) + pws);
-  }
+  v->ws_cap = v->ws_bytes;
   *out = v;
   return JTFS_OK;
 }
@@ -298,7 +317,50 @@ jtfs_status jtfs_varlen_layout(const jtfs_varlen* v, int64_t* x_off, int64_t* s0
 
 jtfs_status jtfs_varlen_workspace_bytes(const jtfs_varlen* v, size_t* out) {
   if (!v || !out) { set_error("bad argument"); return JTFS_ERR_INVALID_ARG; }
-  *out = v->ws_bytes;
+  *out = v->ws_cap;
+  return JTFS_OK;
+}
+
+jtfs_status jtfs_varlen_tune_schedule(jtfs_varlen* v, const float* x, const float* g_s0,
+                                      const float* g_s1, const float* g_s2, float* s0,
+                                      float* s1, float* s2, float* g_x, void* ws,
+                                      size_t ws_bytes, void* stream, int32_t* chosen) {
+  if (!v || !x || !s0 || !s1 || !s2 || !g_x) { set_error("NULL argument"); return JTFS_ERR_INVALID_ARG; }
+  if (!ws || ws_bytes < v->ws_cap) {
+    set_error("varlen workspace needs " + std::to_string(v->ws_cap) + " bytes");
+    return JTFS_ERR_WORKSPACE;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int> cand;
+  for (int c = 16; c < v->chunk_max; c <<= 1) cand.push_back(c);
+  cand.push_back(v->chunk_max);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  jtfs_status rc = cuda_check(cudaEventCreate(&e0), "event");
+  if (rc == JTFS_OK) rc = cuda_check(cudaEventCreate(&e1), "event");
+  int best = v->chunk;
+  float best_ms = 0.f;
+  for (size_t i = 0; i < cand.size() && rc == JTFS_OK; ++i) {
+    if ((rc = vl_build_chunks(v, cand[i])) != JTFS_OK) break;
+    // one untimed pass (first launches, attributes), then two timed ones
+    if ((rc = vl_run(v, x, g_s0, g_s1, g_s2, s0, s1, s2, g_x, ws, ws_bytes, st)) != JTFS_OK) break;
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 2 && rc == JTFS_OK; ++r)
+      rc = vl_run(v, x, g_s0, g_s1, g_s2, s0, s1, s2, g_x, ws, ws_bytes, st);
+    cudaEventRecord(e1, st);
+    if (rc == JTFS_OK) rc = cuda_check(cudaEventSynchronize(e1), "tune sync");
+    float ms = 0.f;
+    if (rc == JTFS_OK) rc = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "tune time");
+    if (rc == JTFS_OK && (i == 0 || ms < best_ms)) { best_ms = ms; best = cand[i]; }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  // a captured graph holds the old sub-batches: drop it (capture again after tuning)
+  if (v->exec) { cudaGraphExecDestroy(v->exec); v->exec = nullptr; }
+  if (v->graph) { cudaGraphDestroy(v->graph); v->graph = nullptr; }
+  jtfs_status rb = vl_build_chunks(v, best);
+  if (rc != JTFS_OK) return rc;
+  if (rb != JTFS_OK) return rb;
+  if (chosen) chosen[0] = best;
   return JTFS_OK;
 }
 

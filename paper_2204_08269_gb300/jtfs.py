@@ -100,6 +100,8 @@ def lib():
         "jtfs_varlen_capture": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P], _I32),
         "jtfs_varlen_replay": ([_P, _P], _I32),
         "jtfs_varlen_autotune": ([_P, _P, _SZ, _P], _I32),
+        "jtfs_varlen_tune_schedule": ([_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P, _P],
+                                      _I32),
         "jtfs_mulog_mean": ([_P, _I64, _I64, _I64, _P, _P], _I32),
         "jtfs_mulog": ([_P, _I64, _I64, _I64, _P, ctypes.c_float, _P, _P], _I32),
         "jtfs_mulog_backward": ([_P, _I64, _I64, _I64, _P, ctypes.c_float, _P, _P, _P], _I32),
@@ -126,7 +128,8 @@ def exported_symbols():
             "jtfs_varlen_padded_length",
             "jtfs_varlen_create", "jtfs_varlen_destroy", "jtfs_varlen_layout",
             "jtfs_varlen_workspace_bytes", "jtfs_varlen_forward_backward", "jtfs_varlen_capture",
-            "jtfs_varlen_replay", "jtfs_varlen_autotune", "jtfs_mulog_mean", "jtfs_mulog",
+            "jtfs_varlen_replay", "jtfs_varlen_autotune", "jtfs_varlen_tune_schedule",
+            "jtfs_mulog_mean", "jtfs_mulog",
             "jtfs_mulog_backward"]
 
 
@@ -539,3 +542,13 @@ class JTFSVarlen:
     def autotune(self):
         _check("jtfs_varlen_autotune", lib().jtfs_varlen_autotune(
             self._h, _ptr(self._ws), self._ws.numel(), _stream()))
+
+    def tune_schedule(self, x_packed, g=(), outs=None):
+        """Times the step with every sub-batch size up to the creation's ``chunk`` and keeps
+        the fastest; returns that size.  Capture the graph afterwards."""
+        import numpy as np
+        outs = outs or self.outputs()
+        c = np.zeros(1, dtype=np.int32)
+        _check("jtfs_varlen_tune_schedule", lib().jtfs_varlen_tune_schedule(
+            self._h, *self._args(x_packed, g, outs), _stream(), c.ctypes.data_as(_P)))
+        return int(c[0])

@@ -142,3 +142,24 @@ def test_varlen_autotune_then_graph(L):
     side.synchronize()
     for a, b in zip(direct, outs):
         assert torch.equal(a, b)
+
+
+def test_schedule_tuner_keeps_results(L):
+    """jtfs_varlen_tune_schedule times sub-batches of 16, 32, ... up to the creation's size
+    and keeps the fastest; every split gives the same outputs, bit for bit, and the graph
+    captured afterwards replays them."""
+    lengths = LENGTHS * 5
+    v = L.JTFSVarlen(lengths, **CFG, precision="fp32", chunk=64)
+    x, g = _packed_inputs(v, 17)
+    direct = [t.clone() for t in v.forward_backward(x, g)]
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        chosen = v.tune_schedule(x, g)
+        after = [t.clone() for t in v.forward_backward(x, g)]
+        outs = v.capture(x, g)
+        v.replay()
+    side.synchronize()
+    assert chosen in (16, 32, 64)
+    for a, b, c in zip(direct, after, outs):
+        assert torch.equal(a, b)
+        assert torch.equal(a, c)
