@@ -279,6 +279,9 @@ def run_ours(args):
                "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                "frac": gbs / peaks.get("hbm_gbs"), "bytes_per_step": sum(fb.values()),
                "ms_per_step": fms}
+    extras = None
+    if world == 1 and not args.no_extras and BATCH == 64:
+        extras = run_extras(args, plan, x, (g0, g1, g2))
     out = None
     if rank == 0:
         cpu = cpu_baseline(args) if (world == 1 and not args.no_cpu) else None
@@ -301,6 +304,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "peaks": peaks_kind,
+            "comparisons": extras,
         }
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -361,7 +365,50 @@ def run_reference(args):
     return out
 
 
-def run_varlen(args):
+def run_extras(args, plan, x, g):
+    """Short measurements beside the headline, in the same run (one GPU only): the plain FP32
+    CUDA-core form of the same step, and summaries of the uneven-length, mixed-precision,
+    resynthesis and Eq. 5 workloads (each also available alone with --workload).  None of
+    them enters the headline value."""
+    import torch
+    from paper_2204_08269_gb300 import JTFSPlan
+    res = {}
+    try:
+        simt = JTFSPlan(**WORKLOAD, precision="fp32_simt")
+        simt.forward_backward(x[:8], *[t[:8].contiguous() for t in g])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        simt.forward_backward(x, *g)
+        e1.record()
+        torch.cuda.synchronize()
+        res["fp32_cuda_cores"] = {"signals_per_s": BATCH / (e0.elapsed_time(e1) / 1e3),
+                                  "ms_per_step": e0.elapsed_time(e1),
+                                  "how": "the same B=64 step with the contraction on CUDA cores "
+                                         "(plain FP32), one timed step"}
+        del simt
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup, sub.batch = 3, 2, BATCH
+        v = run_varlen(sub, emit=False)
+        res["varlen"] = {k: v[k] for k in ("value", "unit", "ms_per_step", "per_signal_launches")}
+        res["varlen"]["tuned_sub_batch"] = v["config"].get("tuned_sub_batch")
+        m = run_mixed(sub, emit=False)
+        res["mixed_precision_forward"] = m["precisions"]
+        sub.steps = 50
+        r = run_resynth(sub, emit=False)
+        res["resynthesis"] = {k: r[k] for k in ("value", "unit", "ms_per_step", "E_adam",
+                                                "E_bold_driver")}
+        e = run_eq5(sub, emit=False)
+        res["eq5_study"] = {"signals_per_s": e["value"],
+                            "knn_error_ratio": e["study"]["knn_error_ratio"],
+                            "isomap_alignment": e["study"]["isomap_alignment"]}
+    except Exception as exc:   # the headline stands on its own
+        res["error"] = repr(exc)
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_varlen(args, emit=True):
     """Uneven-length batch: J=12, Q=16, J_fr=4, Q_fr=2, T=2^12, F=16, lengths log-uniform in
     2^13..2^17, half AM/FM tones and half click trains; forward + backward with ones as
     cotangents.  The step is one replay of the captured graph (autotuned launch shapes and
@@ -430,11 +477,12 @@ def run_varlen(args):
                                          for k in sorted(set(jtfs.varlen_padded_length(int(n), J=12) for n in lengths))}},
            "per_signal_launches": {"value": len(sample) / (ms_ps / 1e3), "unit": "signals/s",
                                    "sample": f"{len(sample)} of the {count} signals, one call per signal"}}
-    print(json.dumps(out), flush=True)
+    if emit:
+        print(json.dumps(out), flush=True)
     return out
 
 
-def run_mixed(args):
+def run_mixed(args, emit=True):
     """Mixed-precision forward: B = 256, N = 2^15, J = 11, Q = 12, J_fr = 4, Q_fr = 1 (AM/FM
     tones).  Forward signals/s of the FP32-grade, TF32 and BF16 contractions, and their
     per-order relative L2 error against the FP64 oracle on two sampled signals."""
@@ -478,11 +526,12 @@ def run_mixed(args):
            "config": {"workload": "mixed precision forward, B=256 AM/FM tones, N=2^15, J=11, Q=12, "
                                   "J_fr=4, Q_fr=1, T=2^11, F=12"},
            "precisions": res, "oracle_sample": f"signals {sample} of {B}"}
-    print(json.dumps(out), flush=True)
+    if emit:
+        print(json.dumps(out), flush=True)
     return out
 
 
-def run_resynth(args):
+def run_resynth(args, emit=True):
     """Texture resynthesis (Sec. 5): B = 16 click-train targets of N = 2^17 (J = 13, Q = 16,
     J_fr = 4, Q_fr = 2, T = 2^13, F = 16), ``--steps`` Adam iterations (50 by the workload)
     from seeded white noise, each one forward with the U1 checkpoint and one backward through
@@ -531,11 +580,12 @@ def run_resynth(args):
            "paper_context": "about 720 ms per iteration for one signal of N=2^16 (J=12, Q=12) "
                             "on an unnamed GPU; E about 0.10 at 20 and 0.03 at 100 iterations",
            "gpu_launches": int(launches), "clocks": clk.summary()}
-    print(json.dumps(res), flush=True)
+    if emit:
+        print(json.dumps(res), flush=True)
     return res
 
 
-def run_eq5(args):
+def run_eq5(args, emit=True):
     """The Eq. 5 similarity study (Sec. 3.2-3.4) on the 16^3 chirp grid: transform throughput
     on the dataset and the K-NN / Isomap results for this library's features."""
     import torch
@@ -554,7 +604,8 @@ def run_eq5(args):
            "study": res,
            "paper_context": "K-NN error ratios of JTFS: f_m within 0.75-1.5, gamma within "
                             "0.75-1.25, f_c close to 1 (Sec. 3.4)"}
-    print(json.dumps(out), flush=True)
+    if emit:
+        print(json.dumps(out), flush=True)
     return out
 
 
@@ -567,6 +618,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "fp32_simt"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the short comparison measurements after the headline")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default row-FFT launch shape (profiling runs: no tuning launches)")
     ap.add_argument("--batch", type=int, default=BATCH,
