@@ -119,14 +119,17 @@ jtfs_status jtfs_plan_schedule(const jtfs_plan* plan, int32_t* s1, int32_t* s2,
 jtfs_status jtfs_workspace_bytes(const jtfs_plan* plan, int64_t B, int32_t with_grad,
                                  size_t* out);
 
-/* Forward transform of x [B, N] (device).  Writes s0, s1, s2 (device, sizes from
+/* Forward transform (Sec. 2; Eq. 3, or Eq. 4 with average_fr = 0): S0 = x * phi_T and
+ * S1 = |x * psi_lambda| * phi_T sampled every T, and S2 of Eq. 3 for every second-order path.
+ * x [B, N] (device).  Writes s0, s1, s2 (device, sizes from
  * jtfs_plan_shapes).  With out_3d = 0, s0 receives the single [B, out_rows, n_t] output and
  * s1, s2 must be NULL.  u1_ckpt (device, [B, u1_len]) receives the first-order scalogram
  * checkpoint when not NULL; jtfs_backward needs it.  B = 0 is a no-op. */
 jtfs_status jtfs_forward(const jtfs_plan* plan, const float* x, int64_t B, float* s0, float* s1,
                          float* s2, float* u1_ckpt, void* ws, size_t ws_bytes, void* stream);
 
-/* Backward: g_x [B, N] = d<g, S(x)>/dx for cotangents g_s0, g_s1, g_s2 (device, same shapes
+/* Backward (Sec. 5: the reverse-ordered adjoints of the forward's operators):
+ * g_x [B, N] = d<g, S(x)>/dx for cotangents g_s0, g_s1, g_s2 (device, same shapes
  * as the outputs; any may be NULL for zero; with out_3d = 0, g_s0 holds the single output's
  * cotangent and g_s1, g_s2 must be NULL).  Needs the forward's u1_ckpt for the same x.
  * The modulus Jacobian d|z| = Re(conj(z) dz) / |z| is taken as 0 at z = 0. */

@@ -32,58 +32,47 @@ namespace cg = cooperative_groups;
 // hi x = p + e (e from an FMA), and summed with a Neumaier (sum, correction) pair per thread;
 // the pairs are added in FP64.  The spectral form from x-hat would inherit the FP32 FFT's
 // rounding, which is of the size of S0 itself for such inputs.
-// One cluster of kS0Split CTAs per (frame, group of kS0Sig signals): CTA r sums the r-th slice
-// of the samples for every signal of the group, reading each weight once for all of them
-// (weights and samples contiguous), and hands its FP64 partials to CTA 0 through distributed
-// shared memory, which adds them in a fixed order.
-constexpr int kS0Split = 8, kS0Sig = 8, kS0Threads = 256;
+// One cluster of kS0Split CTAs per (frame, signal): CTA r sums the r-th slice of the samples
+// (weights and samples both read contiguously) and hands its FP64 partial to CTA 0 through
+// distributed shared memory, which adds them in a fixed order.
+constexpr int kS0Split = 8, kS0Threads = 256;
 
 __global__ void __cluster_dims__(kS0Split, 1, 1) __launch_bounds__(kS0Threads)
-k_s0(DevPlan P, const float* __restrict__ x, float* __restrict__ s0, int B) {
-  __shared__ double red[kS0Sig][kS0Threads / 32];
-  __shared__ double parts[kS0Split][kS0Sig];
+k_s0(DevPlan P, const float* __restrict__ x, float* __restrict__ s0) {
+  __shared__ double red[kS0Threads / 32];
+  __shared__ double parts[kS0Split];
   cg::cluster_group cl = cg::this_cluster();
-  const int part = (int)cl.block_rank(), t = blockIdx.x / kS0Split, b0 = blockIdx.y * kS0Sig;
+  const int part = (int)cl.block_rank(), t = blockIdx.x / kS0Split, b = blockIdx.y;
   const int chunk = P.N / kS0Split;
-  const int nsig = min(kS0Sig, B - b0);
+  const float* xb = x + (size_t)b * P.N;
   const long long tT = (long long)t * P.T;
-  float sum[kS0Sig], cor[kS0Sig];
-#pragma unroll
-  for (int j = 0; j < kS0Sig; ++j) sum[j] = cor[j] = 0.f;
+  float sum = 0.f, cor = 0.f;
   for (int n = part * chunk + threadIdx.x; n < (part + 1) * chunk; n += blockDim.x) {
     const int k = (int)((tT - n) & (P.N - 1));
-    const float hi = __ldg(&P.phiT[k]), lo = __ldg(&P.phiT_lo[k]);
-#pragma unroll
-    for (int j = 0; j < kS0Sig; ++j) {
-      if (j >= nsig) break;
-      const float v = x[(size_t)(b0 + j) * P.N + n];
-      const float pr = __fmul_rn(hi, v);
-      const float e = fmaf(lo, v, fmaf(hi, v, -pr));
-      const float u = __fadd_rn(sum[j], pr);
-      const float d = fabsf(sum[j]) >= fabsf(pr) ? __fadd_rn(__fsub_rn(sum[j], u), pr)
-                                                  : __fadd_rn(__fsub_rn(pr, u), sum[j]);
-      cor[j] = __fadd_rn(cor[j], __fadd_rn(d, e));
-      sum[j] = u;
-    }
+    const float v = xb[n], hi = __ldg(&P.phiT[k]), lo = __ldg(&P.phiT_lo[k]);
+    const float pr = __fmul_rn(hi, v);
+    const float e = fmaf(lo, v, fmaf(hi, v, -pr));
+    const float u = __fadd_rn(sum, pr);
+    const float d = fabsf(sum) >= fabsf(pr) ? __fadd_rn(__fsub_rn(sum, u), pr)
+                                            : __fadd_rn(__fsub_rn(pr, u), sum);
+    cor = __fadd_rn(cor, __fadd_rn(d, e));
+    sum = u;
   }
+  double acc = (double)sum + (double)cor;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < kS0Sig; ++j) {
-    double acc = (double)sum[j] + (double)cor[j];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (l == 0) red[j][w] = acc;
-  }
+  if (l == 0) red[w] = acc;
   __syncthreads();
-  if (threadIdx.x < kS0Sig) {
+  if (threadIdx.x == 0) {
     double v = 0.0;
-    for (int i = 0; i < kS0Threads / 32; ++i) v += red[threadIdx.x][i];
-    cl.map_shared_rank(&parts[0][0], 0)[part * kS0Sig + threadIdx.x] = v;
+    for (int i = 0; i < kS0Threads / 32; ++i) v += red[i];
+    cl.map_shared_rank(parts, 0)[part] = v;
   }
   cl.sync();
-  if (part == 0 && threadIdx.x < nsig) {
+  if (part == 0 && threadIdx.x == 0) {
     double v = 0.0;
-    for (int r = 0; r < kS0Split; ++r) v += parts[r][threadIdx.x];
-    s0[(size_t)(b0 + threadIdx.x) * P.n_t + t] = (float)v;
+    for (int r = 0; r < kS0Split; ++r) v += parts[r];
+    s0[(size_t)b * P.n_t + t] = (float)v;
   }
 }
 
@@ -458,7 +447,7 @@ jtfs_status launch_scat1d_forward(const jtfs_plan* p, const float* x, int B, flo
   }
   {
     StageScope sc(p, kStS0, st, 1);
-    k_s0<<<dim3(kS0Split * p->n_t, (B + kS0Sig - 1) / kS0Sig), kS0Threads, 0, st>>>(d, x, s0, B);
+    k_s0<<<dim3(kS0Split * p->n_t, B), kS0Threads, 0, st>>>(d, x, s0);
   }
   {
     StageScope sc(p, kStScalogram, st, 1);
@@ -487,7 +476,7 @@ jtfs_status launch_forward(const jtfs_plan* p, const float* x, int B, float* s0,
   }
   {
     StageScope sc(p, kStS0, st, 1);
-    k_s0<<<dim3(kS0Split * p->n_t, (B + kS0Sig - 1) / kS0Sig), kS0Threads, 0, st>>>(d, x, s0, B);
+    k_s0<<<dim3(kS0Split * p->n_t, B), kS0Threads, 0, st>>>(d, x, s0);
   }
   {
     StageScope sc(p, kStScalogram, st, 1);
@@ -612,7 +601,7 @@ jtfs_status launch_first_order_static(const jtfs_plan* p, const float* x, int B,
   const DevPlan& d = p->dp;
   k_xfft_sub<<<dim3(d.D, B), kFftThreads, (size_t)d.M * 17 / 2, st>>>(d, x, xsub);
   k_xfft_combine<<<dim3((p->N / 2 + 255) / 256, B), 256, 0, st>>>(d, xsub, xh);
-  k_s0<<<dim3(kS0Split * p->n_t, (B + kS0Sig - 1) / kS0Sig), kS0Threads, 0, st>>>(d, x, s0, B);
+  k_s0<<<dim3(kS0Split * p->n_t, B), kS0Threads, 0, st>>>(d, x, s0);
   k_scalogram<<<dim3(p->n1, B), kRowLaunch, (size_t)p->L1max * 17 / 2 + (size_t)p->L1max * 4, st>>>(d, xh, u1, uh, s1);
   return cuda_check(cudaGetLastError(), "first-order static launch");
 }

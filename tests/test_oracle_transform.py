@@ -219,3 +219,22 @@ def test_mu_log_definitions():
     assert np.max(np.abs(a - b)) < 1e-14
     assert np.all(O.mu_log(S + 1.0, mu) > a)
     assert np.all(O.mu_log(np.zeros_like(S), mu) == 0.0)
+
+
+def test_schedule_measurement_script():
+    """oracle.measure_schedule reports SCHEDULED against EXACT per order; on a small workload
+    the departure shrinks with the oversampling and vanishes once every stride is 1."""
+    from oracle import measure_schedule as MS
+    O.WORKLOADS[99] = O.Config(J=4, Q=3, J_fr=2, Q_fr=2, T=16, F=3, N=256)
+    try:
+        import synth_signals as SS
+        orig = SS.workload_signals
+        SS.workload_signals = lambda c, B, N: SS.white_noise_batch(B, N, 99)
+        res = MS.measure(99, 2, [0, 1, 50])
+    finally:
+        SS.workload_signals = orig
+        del O.WORKLOADS[99]
+    r = res["oversampling"]
+    assert r[0]["S2"] >= r[1]["S2"] and r[0]["S1"] >= r[1]["S1"]
+    assert r[50]["S1"] < 1e-12 and r[50]["S2"] < 1e-12
+    assert r[50]["L1_max"] == 256
