@@ -467,7 +467,7 @@ jtfs_status launch_backward(const jtfs_plan* p, const float* x, const float* u1,
           d, reinterpret_cast<const int4*>(p->d_rowitems), w.uh, nullptr,
           (__nv_bfloat16*)w.ybh, (__nv_bfloat16*)w.ybl, B);
     }
-    StageScope sc(p, kStJointBwd, st, 2);
+    StageScope sc(p, kStJointBwd, st, 0);   // the launcher counts its kernels
     jtfs_status r2 = launch_joint_bwd_tc(p, B, w.ybh, w.ybl, gs2, w.g1, w.gy, st);
     if (r2 != JTFS_OK) return r2;
     if (!p->tcb_fb_items.empty()) {

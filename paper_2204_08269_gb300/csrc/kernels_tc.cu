@@ -1644,7 +1644,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr tc")) != JTFS_OK)               \
       return rc;                                                                                \
-    k_joint_fwd_tc<NTV, BNV, RESV><<<grid, kThreads, smem, st>>>(maps, args, d);               \
+    k_joint_fwd_tc<NTV, BNV, RESV><<<grid, kThreads, smem, st>>>(maps, args, d); ++p->prof.launches; \
   } while (0)
 #define JTFS_LAUNCH_TC16(RESV, TFV)                                                             \
   do {                                                                                          \
@@ -1652,7 +1652,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr tc16")) != JTFS_OK)             \
       return rc;                                                                                \
-    k_joint_fwd_tc16<RESV, TFV><<<grid, kThreads, smem, st>>>(maps, args, d);                  \
+    k_joint_fwd_tc16<RESV, TFV><<<grid, kThreads, smem, st>>>(maps, args, d); ++p->prof.launches; \
   } while (0)
 #define JTFS_LAUNCH_PAIR(RESV, PSV)                                                             \
   do {                                                                                          \
@@ -1660,7 +1660,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr pair")) != JTFS_OK)             \
       return rc;                                                                                \
-    k_joint_fwd_pair<RESV, PSV><<<grid, kThreads, smem, st>>>(maps, args, d);                   \
+    k_joint_fwd_pair<RESV, PSV><<<grid, kThreads, smem, st>>>(maps, args, d); ++p->prof.launches; \
   } while (0)
   for (int pass = 0; pass < 2; ++pass) {
     const bool res = pass == 0;
@@ -1692,6 +1692,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
 #undef JTFS_LAUNCH_TC16
 #undef JTFS_LAUNCH_PAIR
   k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
+  ++p->prof.launches;
   return cuda_check(cudaGetLastError(), "k_pool_lambda");
 }
 

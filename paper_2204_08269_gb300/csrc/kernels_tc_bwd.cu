@@ -1720,6 +1720,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   // G1 (phi_F adjoint of g_S2), zero padded
   if ((rc = cuda_check(cudaMemsetAsync(g1buf, 0, tcb_g1_bytes(p, B), st), "memset g1")) != JTFS_OK) return rc;
   k_g1<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, gs2, NT, g1_rows, g1hi, three ? g1lo : nullptr);
+  ++p->prof.launches;
   if ((rc = cuda_check(cudaGetLastError(), "k_g1")) != JTFS_OK) return rc;
   std::string err;
   CUtensorMap mw[4], my[2][16], mg1[2], mwt[2];
@@ -1838,7 +1839,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smemp), "attr tcbp")) != JTFS_OK)            \
       return rc;                                                                                \
-    k_joint_bwd_pair<PLV, NATV, KMV, RCV><<<grid, kFThreads, smemp, st>>>(pm, pa, d);           \
+    k_joint_bwd_pair<PLV, NATV, KMV, RCV><<<grid, kFThreads, smemp, st>>>(pm, pa, d); ++p->prof.launches; \
   } while (0)
       // one atom; two atoms with K1 <= 96 (a 96-row Y^T tile); two atoms with K1 <= 128;
       // three atoms (K1 <= 160, 16-row chunks)
@@ -1919,7 +1920,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr tcbf")) != JTFS_OK)             \
       return rc;                                                                                \
-    k_joint_bwd_fast<NTV, RCV, PLV, NATV, KMV><<<grid, kFThreads, smem, st>>>(fm, fa, d);      \
+    k_joint_bwd_fast<NTV, RCV, PLV, NATV, KMV><<<grid, kFThreads, smem, st>>>(fm, fa, d); ++p->prof.launches; \
   } while (0)
 #define JTFS_LAUNCH_TCBF_NT(RCV, PLV, NATV, KMV)                                                \
   do {                                                                                          \
@@ -1951,7 +1952,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr tcb")) != JTFS_OK)              \
       return rc;                                                                                \
-    k_joint_bwd_tc<NTV, PLV><<<grid, kThreads, smem, st>>>(maps, args, d);                     \
+    k_joint_bwd_tc<NTV, PLV><<<grid, kThreads, smem, st>>>(maps, args, d); ++p->prof.launches; \
   } while (0)
     if (PL == 1) {
       if (NT == 16) JTFS_LAUNCH_TCB(16, 1);
@@ -1983,7 +1984,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr tcb3")) != JTFS_OK)             \
       return rc;                                                                                \
-    k_joint_bwd_tc3<NTV, WBV><<<grid, kThreads, smem, st>>>(maps3, args, d);                   \
+    k_joint_bwd_tc3<NTV, WBV><<<grid, kThreads, smem, st>>>(maps3, args, d); ++p->prof.launches; \
   } while (0)
   if (NT == 16) JTFS_LAUNCH_TCB3(16, 2);
   else if (NT == 32) JTFS_LAUNCH_TCB3(32, 2);

@@ -335,3 +335,36 @@ def test_fused_step_full_batch_sampled(prec):
                   "S2": s2[b].cpu().numpy()}, ref, TOL[prec], label=f"signal {b}")
     refg = O.backward_one(xs[b].astype(np.float64), g[0][b], g[1][b], g[2][b], op, sc)
     assert _rel(gx[b].double().cpu().numpy(), refg) <= GTOL[prec]
+
+
+def test_largest_supported_length_and_refusal_beyond():
+    """Q = 16: the top first-order row has stride 8, so N = 2^17 is the longest signal whose
+    rows fit the 2^14-sample shared-memory FFT; N = 2^18 is refused as unsupported (status 2)
+    before any device work, and N = 2^17 plans build (the parity at that size is in
+    test_gpu_parity_large)."""
+    from paper_2204_08269_gb300 import JTFSPlan
+    from paper_2204_08269_gb300.jtfs import JTFSError
+    cfg = dict(J=13, Q=16, J_fr=4, Q_fr=2, T=2 ** 13, F=16)
+    p = JTFSPlan(N=2 ** 17, **cfg, precision="fp32")
+    s1, s2, lm = p.schedule()
+    assert (2 ** 17) // int(s1.min()) == 2 ** 14
+    with pytest.raises(JTFSError) as e:
+        JTFSPlan(N=2 ** 18, **cfg, precision="fp32")
+    assert e.value.status == 2
+
+
+def test_launch_count_of_the_fused_step():
+    """The profiler's launch counter matches the kernels the fused FP32-grade step issues at
+    the benchmark's workload: 8 in the forward (x FFT 2, S0, scalogram, Y producer, two
+    contraction forms, phi_F pooling) and 10 in the backward (G1, four contraction forms,
+    gY spectra, second-order backward, first-order backward, g_x 2)."""
+    cfg = _workload_cfg(2)
+    plan = _plans(cfg, "fp32")
+    sh = plan.shapes
+    x = torch.from_numpy(SS.workload_signals(2, 4, cfg["N"])).cuda()
+    g = [torch.ones(f(4), device="cuda") for f in (sh.s0, sh.s1, sh.s2)]
+    plan.forward_backward(x, *g)
+    plan.profile_read()
+    plan.forward_backward(x, *g)
+    _, launches = plan.profile_read()
+    assert launches == 18
