@@ -467,7 +467,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   uint8_t* sStg = sWt + WS * NH * pplanes * kWHalf;     // 16 warps x pplanes x 1 KB
   float* sRed = (float*)(sStg + kEpiWarps * pplanes * kStg);   // [4 groups][128 rows][16]
   __shared__ uint64_t full_bar[8], empty_bar[8], wfull[kMaxWS], wempty[kMaxWS], tfull[2],
-      tempty[2], red_full[4], red_free[4], a_full, a_free, mma_done;
+      tempty[2], red_full[4], red_free[4], sfull[4], sfree[4], a_full, a_free, mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -489,6 +489,8 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     for (int q = 0; q < 4; ++q) {
       mbar_init(&red_full[q], 4);
       mbar_init(&red_free[q], 1);
+      mbar_init(&sfull[q], 4);
+      mbar_init(&sfree[q], 4);
     }
     mbar_init(&a_full, 1);
     mbar_init(&a_free, 1);
@@ -827,33 +829,40 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
 // forms both channels.  That halves the contraction's MMAs against the channel-row form.
 // Rows are pair rows r = p n1 + lambda for the spin pairs p < n_fr, then zero rows up to the
 // next multiple of 32, then the n1 rows of the phi_F branch (real W, only its "up" output is
-// written).  Sixteen epilogue warps: lane quarter = warp & 3,
-// column group cg = ew >> 2 takes channel cg >> 1 (0 up, 1 down) over samples
-// [32 (cg & 1), +32) of the tile, pooled with mma.sync as in the 16-frame form.
-template <bool RES, int PS>
+// written).  Sixteen epilogue warps: lane quarter = warp & 3, column group cg = ew >> 2 forms
+// |Z| of both channels over samples [16 cg, +16) of the tile and stages it.  16 frames: each
+// warp pools its own samples over all frames with mma.sync, and at an item's end the four
+// column groups' partials are summed.  32 frames (the partials of all frames would not fit the
+// registers): the quarter's four warps exchange their staged |Z| blocks, and warp cg pools
+// channel cg >> 1 over frames [16 (cg & 1), +16) and all 64 samples, so that it owns its
+// outputs and writes them at an item's end.
+template <bool RES, int PS, int NT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
+  static_assert(NT == 16 || NT == 32, "pooled frames");
   const uint64_t wait_budget = args.wait_ns;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int NT = 16, BN = 64;
+  constexpr int BN = 64;
+  constexpr int CD = NT == 16 ? 2 : 1;                   // channels a warp accumulates
   const int planes = args.passes == 3 ? 2 : 1;
   constexpr int pplanes = PS;
   const int S = args.stages, WS = args.wstages;
   constexpr uint32_t kAPlane = kBM * kBK * 2;            // 8 KB: 128 rows x 32 lambda', SW64
   constexpr uint32_t kYAtom = 4096;                      // 32 lambda' x 64 samples, SW128
-  constexpr uint32_t kWHalf = NT * 64 * 2;               // 2 KB: 16 frames x 64 samples
+  constexpr uint32_t kWHalf = NT * 64 * 2;               // NT frames x 64 samples
   constexpr uint32_t kStg = 32 * 16 * 2;                 // 1 KB: a warp's 32 x 16 |Z| block
+  // a warp's staging: its |Z| blocks per channel and plane, at an item's end its 32 x NT partials
+  constexpr uint32_t kStgWarp = 2 * PS * kStg > NT * 32 * 4 ? 2 * PS * kStg : NT * 32 * 4;
   const int max_kb = args.res_kb;
   const uint32_t y_bytes = planes * 2 * kYAtom;          // per plane [Yr atom | Yi atom]
   const uint32_t stage_bytes = RES ? y_bytes : planes * 2 * kAPlane + y_bytes;
   uint8_t* sA = sm;
   uint8_t* sStage = sm + (RES ? planes * 2 * max_kb * kAPlane : 0);
   uint8_t* sWt = sStage + S * stage_bytes;               // WS x pplanes (hi, lo adjacent)
-  uint8_t* sStg = sWt + WS * pplanes * kWHalf;           // 16 warps x 2 channels x pplanes x 1 KB
-                                                         // (at an item's end: 32 x 16 partials)
+  uint8_t* sStg = sWt + WS * pplanes * kWHalf;           // 16 warps x kStgWarp
   __shared__ uint64_t full_bar[8], empty_bar[8], wfull[kMaxWS], wempty[kMaxWS], tfull[2],
-      tempty[2], red_full[4], red_free[4], a_full, a_free, mma_done;
+      tempty[2], red_full[4], red_free[4], sfull[4], sfree[4], a_full, a_free, mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -875,6 +884,8 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     for (int q = 0; q < 4; ++q) {
       mbar_init(&red_full[q], 4);
       mbar_init(&red_free[q], 1);
+      mbar_init(&sfull[q], 4);
+      mbar_init(&sfree[q], 4);
     }
     mbar_init(&a_full, 1);
     mbar_init(&a_free, 1);
@@ -1031,7 +1042,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     const int cg = ew >> 2;                   // samples [16 cg, 16 cg + 16) of the tile
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const int g = lane >> 2, t4 = lane & 3;
-    uint8_t* stg = sStg + ew * 2 * pplanes * kStg;         // [channel][plane] blocks
+    uint8_t* stg = sStg + ew * kStgWarp;                   // [channel][plane] blocks
     const uint32_t stg_u = smem_u32(stg);
     uint8_t* my_row = stg + lane * 32;
     const int my_sw = (lane >> 2) & 1;
@@ -1044,25 +1055,30 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     const int bt = 8 * (lane >> 4) + (lane & 7);
     const int bk = (lane >> 3) & 1;
     const uint32_t b_off = bt * 128 + ((((cg * 16) >> 3) + bk) ^ (bt & 7)) * 16;
+    // 32 frames: this warp's channel and frame half; the quarter's staging blocks of column
+    // groups 0..3 are kQStride apart from the first
+    const int dch = cg >> 1, fh = cg & 1;
+    constexpr uint32_t kQStride = 4 * kStgWarp;
+    const uint32_t q_stg = smem_u32(sStg) + ((quarter + 2) & 3) * kStgWarp + dch * pplanes * kStg;
     int acc = 0, ws = 0;
     // every wait on red_free follows a completed round of column group 0 (no free first
     // phase): the first wait is for parity 0
-    uint32_t acc_ph = 0, wph = 0, rf_ph = 0, rfree_ph = 1;
+    uint32_t acc_ph = 0, wph = 0, rf_ph = 0, rfree_ph = 1, sf_ph = 0, sr_ph = 0;
     bool red_pending = false;
     for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
       const int4 item = args.items[it % args.n_base];
       const int a = item.x, b = it / args.n_base, m0 = item.y;
       bool ok = !abort_flag;
-      float c[2][2][2][4];                     // [channel up / down][mt][nt][4]
+      float c[CD][2][2][4];                    // [channel up / down][mt][nt][4]
 #pragma unroll
-      for (int d = 0; d < 2; ++d)
+      for (int d = 0; d < CD; ++d)
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
           for (int k2 = 0; k2 < 2; ++k2)
 #pragma unroll
             for (int e = 0; e < 4; ++e) c[d][i][k2][e] = 0.f;
-      if (cg != 0 && red_pending) {
+      if (NT == 16 && cg != 0 && red_pending) {
         // column group 0 has read this warp's partials of the previous item
         if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, wait_budget)) { fail(21); break; }
         rfree_ph ^= 1;
@@ -1074,6 +1090,11 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         if (!mbar_wait(&wfull[ws], wph, wait_budget)) { fail(19); ok = false; break; }
         const uint32_t t_col = tbase + acc * 256 + lane_off + cg * 16;
         const uint32_t w_u = smem_u32(sWt + ws * pplanes * kWHalf);
+        if (NT == 32) {
+          // the quarter's four warps have read the previous tile's |Z| blocks
+          if (!mbar_wait(&sfree[quarter], sr_ph ^ 1, wait_budget)) { fail(22); ok = false; break; }
+          sr_ph ^= 1;
+        }
         __syncwarp();   // the previous tile's fragment loads are done
 #pragma unroll
         for (int h8 = 0; h8 < 2; ++h8) {
@@ -1125,33 +1146,71 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           }
         }
         __syncwarp();
-        // B fragments: w[t][n] for this warp's 16 samples of the 64-sample row
-        uint32_t bh[4], bl[4];
-        ldsm_x4(w_u + b_off, bh);
-        if (PS == 2) ldsm_x4(w_u + kWHalf + b_off, bl);
+        if constexpr (NT == 16) {
+          // B fragments: w[t][n] for this warp's 16 samples of the 64-sample row
+          uint32_t bh[4], bl[4];
+          ldsm_x4(w_u + b_off, bh);
+          if (PS == 2) ldsm_x4(w_u + kWHalf + b_off, bl);
 #pragma unroll
-        for (int d = 0; d < 2; ++d) {
-          const uint32_t blk = d * pplanes * kStg;
-          uint32_t ah[2][4];
-          ldsm_x4(a_addr[0] + blk, ah[0]);
-          ldsm_x4(a_addr[1] + blk, ah[1]);
-#pragma unroll
-          for (int mt = 0; mt < 2; ++mt) {
-            hmma16816(c[d][mt][0], ah[mt], bh[0], bh[1]);
-            hmma16816(c[d][mt][1], ah[mt], bh[2], bh[3]);
-          }
-          if (PS == 2) {
-            uint32_t al[2][4];
-            ldsm_x4(a_addr[0] + blk + kStg, al[0]);
-            ldsm_x4(a_addr[1] + blk + kStg, al[1]);
+          for (int d = 0; d < 2; ++d) {
+            const uint32_t blk = d * pplanes * kStg;
+            uint32_t ah[2][4];
+            ldsm_x4(a_addr[0] + blk, ah[0]);
+            ldsm_x4(a_addr[1] + blk, ah[1]);
 #pragma unroll
             for (int mt = 0; mt < 2; ++mt) {
-              hmma16816(c[d][mt][0], ah[mt], bl[0], bl[1]);   // hi . lo
-              hmma16816(c[d][mt][1], ah[mt], bl[2], bl[3]);
-              hmma16816(c[d][mt][0], al[mt], bh[0], bh[1]);   // lo . hi
-              hmma16816(c[d][mt][1], al[mt], bh[2], bh[3]);
+              hmma16816(c[d][mt][0], ah[mt], bh[0], bh[1]);
+              hmma16816(c[d][mt][1], ah[mt], bh[2], bh[3]);
+            }
+            if (PS == 2) {
+              uint32_t al[2][4];
+              ldsm_x4(a_addr[0] + blk + kStg, al[0]);
+              ldsm_x4(a_addr[1] + blk + kStg, al[1]);
+#pragma unroll
+              for (int mt = 0; mt < 2; ++mt) {
+                hmma16816(c[d][mt][0], ah[mt], bl[0], bl[1]);   // hi . lo
+                hmma16816(c[d][mt][1], ah[mt], bl[2], bl[3]);
+                hmma16816(c[d][mt][0], al[mt], bh[0], bh[1]);   // lo . hi
+                hmma16816(c[d][mt][1], al[mt], bh[2], bh[3]);
+              }
             }
           }
+        } else {
+          if (lane == 0) mbar_arrive(&sfull[quarter]);
+          if (!mbar_wait(&sfull[quarter], sf_ph, wait_budget)) { fail(23); ok = false; break; }
+          sf_ph ^= 1;
+          // channel dch, frames [16 fh, +16) (rows 16 fh.. of the 128-byte W rows), samples of
+          // column group q from that warp's staging block
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t bo = fh * 2048 + bt * 128 + (((2 * q) + bk) ^ (bt & 7)) * 16;
+            uint32_t bh[4], bl[4];
+            ldsm_x4(w_u + bo, bh);
+            if (PS == 2) ldsm_x4(w_u + kWHalf + bo, bl);
+            const uint32_t blk = q_stg + q * kQStride - stg_u;
+            uint32_t ah[2][4];
+            ldsm_x4(a_addr[0] + blk, ah[0]);
+            ldsm_x4(a_addr[1] + blk, ah[1]);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt) {
+              hmma16816(c[0][mt][0], ah[mt], bh[0], bh[1]);
+              hmma16816(c[0][mt][1], ah[mt], bh[2], bh[3]);
+            }
+            if (PS == 2) {
+              uint32_t al[2][4];
+              ldsm_x4(a_addr[0] + blk + kStg, al[0]);
+              ldsm_x4(a_addr[1] + blk + kStg, al[1]);
+#pragma unroll
+              for (int mt = 0; mt < 2; ++mt) {
+                hmma16816(c[0][mt][0], ah[mt], bl[0], bl[1]);   // hi . lo
+                hmma16816(c[0][mt][1], ah[mt], bl[2], bl[3]);
+                hmma16816(c[0][mt][0], al[mt], bh[0], bh[1]);   // lo . hi
+                hmma16816(c[0][mt][1], al[mt], bh[2], bh[3]);
+              }
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sfree[quarter]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&wempty[ws]);
@@ -1159,6 +1218,33 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         if (++acc == 2) { acc = 0; acc_ph ^= 1; }
       }
       if (!ok) break;
+      if constexpr (NT == 32) {
+        float* base = args.P + ((size_t)b * args.n2 + a) * (size_t)P.C * P.n1 * args.nt;
+        // rows 16 mt + g + 8 h of the quarter, frames 16 fh + 8 nt + 2 t4 (+1) of channel dch
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = m0 + quarter * 32 + 16 * mt + g + 8 * h;
+            const bool spin = r < P.n_fr * P.n1;
+            const int p = spin ? r / P.n1 : P.n_fr;
+            const int lam = spin ? r - p * P.n1 : r - args.pr_phi0;
+            if (!(r < args.n_rows && (spin || r >= args.pr_phi0) && (dch == 0 || spin))) continue;
+            const int row = (dch == 0 ? (p < P.n_fr ? p : 2 * P.n_fr) : p + P.n_fr) * P.n1 + lam;
+            float* out = base + (size_t)row * args.nt;
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+              const int t = 16 * fh + 8 * nt + 2 * t4;
+              const float v0 = c[0][mt][nt][2 * h], v1 = c[0][mt][nt][2 * h + 1];
+              if (args.nt == NT) {
+                *reinterpret_cast<float2*>(out + t) = make_float2(v0, v1);
+              } else {
+                if (t < args.nt) out[t] = v0;
+                if (t + 1 < args.nt) out[t + 1] = v1;
+              }
+            }
+          }
+      } else {
       // per channel: each warp leaves its 32 x 16 partials in its own staging block and column
       // group 0 sums the four blocks of its lane quarter in a fixed order
       const int r = m0 + quarter * 32 + lane;
@@ -1195,7 +1281,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           for (int gq = 0; gq < 4; ++gq) {
             // the warp of column group gq and this lane quarter: ew = 4 gq + ((quarter + 2) & 3)
             const float* src =
-                (const float*)(sStg + (gq * 4 + ((quarter + 2) & 3)) * 2 * pplanes * kStg) + lane * NT;
+                (const float*)(sStg + (gq * 4 + ((quarter + 2) & 3)) * kStgWarp) + lane * NT;
 #pragma unroll
             for (int t = 0; t < NT; t += 4) {
               const float4 v = *reinterpret_cast<const float4*>(src + t);
@@ -1224,6 +1310,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       }
       red_pending = true;
       if (!red_ok) break;
+      }
     }
   }
   __syncthreads();
@@ -1434,10 +1521,12 @@ size_t tc_smem_for(const jtfs_plan* p, bool res) {
 // whose warps stage both channels, 3 - nh staging blocks per pooling plane, and reduce their
 // partials through those blocks instead of the 32 KB buffer).
 struct Tc16Shape {
-  int apl, cpl, ppl, nya, nh, WS;
+  int apl, cpl, ppl, nya, nh, WS, nt;
   size_t fixed(bool res, int res_kb) const {
-    return 1024 + (res ? (size_t)cpl * 2 * res_kb * apl : 0) + (size_t)WS * nh * ppl * 16 * 64 * 2 +
-           (size_t)kEpiWarps * (3 - nh) * ppl * 1024 + (nh == 2 ? 4 * 128 * 16 * 4 : 0);
+    // a spin-pair warp's staging also holds its 32 x nt FP32 partials at an item's end
+    const size_t stg = nh == 1 ? std::max<size_t>(2 * ppl * 1024, (size_t)nt * 32 * 4) : (size_t)ppl * 1024;
+    return 1024 + (res ? (size_t)cpl * 2 * res_kb * apl : 0) + (size_t)WS * nh * ppl * nt * 64 * 2 +
+           (size_t)kEpiWarps * stg + (nh == 2 ? 4 * 128 * 16 * 4 : 0);
   }
   size_t stage(bool res) const {
     return (res ? 0 : (size_t)cpl * 2 * apl) + (size_t)cpl * 2 * nya * 4096;
@@ -1453,6 +1542,7 @@ Tc16Shape tc16_shape(const jtfs_plan* p) {
   s.nya = p->tc_pair ? 1 : (tf ? 4 : 2);
   s.nh = p->tc_pair ? 1 : 2;
   s.WS = kMaxWS;
+  s.nt = tc_nt(p->n_t);
   return s;
 }
 
@@ -1478,10 +1568,10 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   for (int a = 0; a < p->n2; ++a)
     if (p->rates2[a].s) Lmax = std::max(Lmax, (p->rates2[a].L + BN - 1) / BN * BN);
   p->tc_wt_cols = Lmax;
-  // items: (alpha, m0, n_tiles); the 16-frame BF16-plane forward runs in the spin-pair form
-  // over the pair rows and 64-sample tiles
+  // items: (alpha, m0, n_tiles); the BF16-plane forward with 16 or 32 frames runs in the
+  // spin-pair form over the pair rows and 64-sample tiles
   const bool tf = p->cfg.precision == JTFS_PREC_TF32;
-  p->tc_pair = NT == 16 && !tf;
+  p->tc_pair = NT <= 32 && !tf;
   p->pr_phi0 = (p->n_fr * p->n1 + 31) / 32 * 32;
   p->n_pr = p->pr_phi0 + p->n1;
   const int tile_n = p->tc_pair ? 64 : BN;
@@ -1513,8 +1603,8 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   auto place = [&](size_t bytes) { size_t at = off; off += (bytes + 1023) & ~(size_t)1023; return at; };
   size_t o_w[6];
   for (int i = 0; i < 6; ++i) o_w[i] = place(wplane * 2);
-  // the spin-pair planes serve the 16-frame forward and backward
-  const bool pair_planes = NT == 16;
+  // the spin-pair planes serve the forward and backward with 16 or 32 frames
+  const bool pair_planes = NT <= 32;
   size_t o_wp[4] = {0, 0, 0, 0};
   if (pair_planes)
     for (int i = 0; i < 4; ++i) o_wp[i] = place((size_t)p->n_pr * p->n1_pad * 2);
@@ -1616,7 +1706,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     }
   }
   const int n_all = (int)(p->tc_items.size() / 4);
-  const bool f16 = NT == 16;
+  const bool f16 = NT == 16 || p->tc_pair;   // the 16-frame and spin-pair layouts
   const int n_res = (f16 ? tc16_stages_for(p, true) : tc_stages_for(p, true)) >= 2 ? p->tc_n_res : 0;
   if (n_all > n_res && (f16 ? tc16_stages_for(p, false) : tc_stages_for(p, false)) < 2) {
     set_error("tensor-core forward: no shared-memory layout for this configuration");
@@ -1654,13 +1744,18 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       return rc;                                                                                \
     k_joint_fwd_tc16<RESV, TFV><<<grid, kThreads, smem, st>>>(maps, args, d); ++p->prof.launches; \
   } while (0)
-#define JTFS_LAUNCH_PAIR(RESV, PSV)                                                             \
+#define JTFS_LAUNCH_PAIR1(RESV, PSV, NTV)                                                       \
   do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_pair<RESV, PSV>,                      \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_pair<RESV, PSV, NTV>,                 \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr pair")) != JTFS_OK)             \
       return rc;                                                                                \
-    k_joint_fwd_pair<RESV, PSV><<<grid, kThreads, smem, st>>>(maps, args, d); ++p->prof.launches; \
+    k_joint_fwd_pair<RESV, PSV, NTV><<<grid, kThreads, smem, st>>>(maps, args, d);              \
+    ++p->prof.launches;                                                                         \
+  } while (0)
+#define JTFS_LAUNCH_PAIR(RESV, PSV)                                                             \
+  do {                                                                                          \
+    if (NT == 16) JTFS_LAUNCH_PAIR1(RESV, PSV, 16); else JTFS_LAUNCH_PAIR1(RESV, PSV, 32);      \
   } while (0)
   for (int pass = 0; pass < 2; ++pass) {
     const bool res = pass == 0;
@@ -1691,6 +1786,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
 #undef JTFS_LAUNCH_TC
 #undef JTFS_LAUNCH_TC16
 #undef JTFS_LAUNCH_PAIR
+#undef JTFS_LAUNCH_PAIR1
   k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
   ++p->prof.launches;
   return cuda_check(cudaGetLastError(), "k_pool_lambda");

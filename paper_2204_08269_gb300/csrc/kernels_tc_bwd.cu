@@ -1062,11 +1062,12 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
 //   gY^T_re += S_re Wr + T_re Wi,   gY^T_im += S_im Wr + T_im Wi   (N = 64 lambda').
 // W bytes per channel row are a third of the channel-row form's [-Wi][Wr][Wi] blocks, which
 // leaves room for a four-chunk W ring.  PL = 2: the FP32-grade split as in the fast form.
+// NT = 16 or 32 pooled frames (the K of the g product; rows of NT BF16 = 32 or 64 bytes).
 struct TpMaps {
-  CUtensorMap w[4];      // pair planes Wr_hi, Wi_hi, Wr_lo, Wi_lo; box {64 lambda', 32 rows}
+  CUtensorMap w[4];      // pair planes Wr_hi, Wi_hi, Wr_lo, Wi_lo; box {64 lambda', RC rows}
   CUtensorMap y[2][16];  // [hi/lo][alpha]: Y planes [2B][K][L], box {64 n, 32 lambda', 1}
-  CUtensorMap g1[2];     // hi, lo: channel-row G1 [rows][16] bf16, box {16, 32}
-  CUtensorMap wt[2];     // hi, lo: [rows][16] bf16, box {16, 128}
+  CUtensorMap g1[2];     // hi, lo: channel-row G1 [rows][NT] bf16, box {NT, RC}
+  CUtensorMap wt[2];     // hi, lo: [rows][NT] bf16, box {NT, 128}
 };
 
 struct TpArgs {
@@ -1086,20 +1087,23 @@ struct TpArgs {
   uint64_t wait_ns;     // budget of every barrier wait (the plan's)
 };
 
-template <int PL, int NAT, int KMV, int RCV>
+template <int PL, int NAT, int KMV, int RCV, int NT>
 __global__ void __launch_bounds__(kFThreads, 1)
 k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
+  static_assert(NT == 16 || NT == 32, "pooled frames");
   const uint64_t wait_budget = args.wait_ns;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int NT = 16, RC = RCV, KM = KMV, CW = RC / 4;
+  constexpr int RC = RCV, KM = KMV, CW = RC / 4;
+  constexpr uint32_t kSw = NT * 2;                        // bytes per row of the NT-wide tiles
+  constexpr uint32_t kLayNT = kSw == 64 ? kSw64 : kSw32;
   constexpr int D1C = 6 * RC;                             // first-product columns per buffer
   constexpr int NB1 = NAT == 1 ? 2 : 1;                   // first-product TMEM buffers
   constexpr bool TA = NAT >= 2;                           // S / T staged in TMEM (A operand)
   constexpr uint32_t kA1Plane = 2 * KM * 128;             // two 64-sample halves x 64 lambda'
-  constexpr uint32_t kA4Plane = 128 * NT * 2;             // [128 n][16 t], 32-byte swizzle
-  constexpr uint32_t kWBlk = RC * 128;                    // 32 rows x 64 lambda'
-  constexpr uint32_t kG1Blk = RC * NT * 2;                // 32 rows x 16 t
+  constexpr uint32_t kA4Plane = 128 * NT * 2;             // [128 n][NT t], NT * 2-byte swizzle
+  constexpr uint32_t kWBlk = RC * 128;                    // RC rows x 64 lambda'
+  constexpr uint32_t kG1Blk = RC * NT * 2;                // RC rows x NT t
   constexpr uint32_t kWBuf = PL * NAT * 2 * kWBlk + PL * 2 * kG1Blk;   // [Wr a][Wi a] per atom a
   constexpr uint32_t kA2Part = 128 * RC * 2;              // [128 n][RC r] bf16, 64-byte swizzle
   constexpr uint32_t kA2Buf = 4 * kA2Part;                // S_re, S_im, T_re, T_im
@@ -1247,8 +1251,11 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
           const uint32_t g1 = wb + PL * NAT * 2 * kWBlk;
           for (int q = 0; q < npair; ++q) {
             const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-            mma_f16(t_g, smem_desc(a4 + pa * kA4Plane, 16, 256, kSw32),
-                    smem_desc(g1 + pb * 2 * kG1Blk, 16, 256, kSw32), id4, q ? 1u : 0u);
+#pragma unroll
+            for (int ks = 0; ks < NT / 16; ++ks)
+              mma_f16(t_g, smem_desc(a4 + pa * kA4Plane + ks * 32, 16, 8 * kSw, kLayNT),
+                      smem_desc(g1 + pb * 2 * kG1Blk + ks * 32, 16, 8 * kSw, kLayNT), id4,
+                      (q | ks) ? 1u : 0u);
           }
           mma_commit(&d1_full[buf]);
           if (++wst == WB) { wst = 0; wph ^= 1; }
@@ -1532,9 +1539,9 @@ static int tcbp_rc(int nat) { return nat >= 3 ? 16 : 32; }
 
 static bool tcbp_layout(const jtfs_plan* p, int nat, int KM, int* wb_out, int* na2_out,
                         size_t* smem_out) {
-  const int PL = p->split ? 2 : 1, RC = tcbp_rc(nat);
-  const size_t fixed = 1024 + (size_t)PL * 2 * (2 * KM * 128) + (size_t)PL * 128 * 16 * 2;
-  const size_t wbuf = (size_t)PL * nat * 2 * RC * 128 + (size_t)PL * 2 * RC * 16 * 2;
+  const int PL = p->split ? 2 : 1, RC = tcbp_rc(nat), NT = tc_nt(p->n_t);
+  const size_t fixed = 1024 + (size_t)PL * 2 * (2 * KM * 128) + (size_t)PL * 128 * NT * 2;
+  const size_t wbuf = (size_t)PL * nat * 2 * RC * 128 + (size_t)PL * 2 * RC * NT * 2;
   const size_t a2buf = nat >= 2 ? 0 : (size_t)4 * 128 * RC * 2;   // two atoms and more: S / T in TMEM
   const size_t budget = 225 * 1024;
   int wb = 4, na2 = nat >= 2 ? 1 : 2;
@@ -1582,9 +1589,9 @@ jtfs_status build_tcb_tables(jtfs_plan* p) {
   std::vector<It> its, fast1, fast2, fast3;
   int wb_, na2_;
   size_t smem_;
-  // spin-pair form: one atom (K1 <= 64) for the FP32-grade split, two (K1 <= 128) and three
-  // (K1 <= 160) atoms for every BF16-plane precision
-  const bool pair = NT == 16 && p->d_wpair[0] != nullptr;
+  // spin-pair form (16 or 32 frames): one atom (K1 <= 64) for the FP32-grade split, two
+  // (K1 <= 128) and three (K1 <= 160) atoms for every BF16-plane precision
+  const bool pair = NT <= 32 && p->d_wpair[0] != nullptr;
   const bool use_p1 = pair && p->split && tcbp_layout(p, 1, 64, &wb_, &na2_, &smem_);
   const bool use_p2 = pair && tcbp_layout(p, 2, 128, &wb_, &na2_, &smem_);
   const bool use_p3 = pair && tcbp_layout(p, 3, 160, &wb_, &na2_, &smem_);
@@ -1797,7 +1804,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     if (count <= 0) continue;
     int wbp = 0, na2p = 0;
     size_t smemp = 0;
-    if (NT == 16 && (three || nat >= 2) && p->d_wpair[0] &&
+    if (NT <= 32 && (three || nat >= 2) && p->d_wpair[0] &&
         tcbp_layout(p, nat, nat == 1 ? 64 : (nat == 2 ? 128 : 160), &wbp, &na2p, &smemp)) {
       const int RCp = tcbp_rc(nat);
       // the spin-pair form: every atom count for the FP32-grade split, two and three atoms for
@@ -1833,13 +1840,19 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       pa.gy = gy;
       pa.err = p->d_err;
       pa.wait_ns = p->wait_ns;
-#define JTFS_LAUNCH_TCBP(PLV, NATV, KMV, RCV)                                                   \
+#define JTFS_LAUNCH_TCBP1(PLV, NATV, KMV, RCV, NTV)                                             \
   do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_pair<PLV, NATV, KMV, RCV>,            \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_bwd_pair<PLV, NATV, KMV, RCV, NTV>,       \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smemp), "attr tcbp")) != JTFS_OK)            \
       return rc;                                                                                \
-    k_joint_bwd_pair<PLV, NATV, KMV, RCV><<<grid, kFThreads, smemp, st>>>(pm, pa, d); ++p->prof.launches; \
+    k_joint_bwd_pair<PLV, NATV, KMV, RCV, NTV><<<grid, kFThreads, smemp, st>>>(pm, pa, d);     \
+    ++p->prof.launches;                                                                         \
+  } while (0)
+#define JTFS_LAUNCH_TCBP(PLV, NATV, KMV, RCV)                                                   \
+  do {                                                                                          \
+    if (NT == 16) JTFS_LAUNCH_TCBP1(PLV, NATV, KMV, RCV, 16);                                   \
+    else JTFS_LAUNCH_TCBP1(PLV, NATV, KMV, RCV, 32);                                            \
   } while (0)
       // one atom; two atoms with K1 <= 96 (a 96-row Y^T tile); two atoms with K1 <= 128;
       // three atoms (K1 <= 160, 16-row chunks)
@@ -1871,6 +1884,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
         if ((rc = cuda_check(cudaGetLastError(), "k_joint_bwd_pair")) != JTFS_OK) return rc;
       }
 #undef JTFS_LAUNCH_TCBP
+#undef JTFS_LAUNCH_TCBP1
       continue;
     }
     const int PLf = three ? 2 : 1, RCf = nat == 1 ? 64 : 32;

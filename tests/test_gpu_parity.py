@@ -153,7 +153,7 @@ def _check_backward(plan, x, op, sc, gtol, idx=None, seed=0):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("ci", [0, 1, 2, 4, 5])
+@pytest.mark.parametrize("ci", [0, 1, 2, 4, 5, 6])
 def test_backward_small_configs(ci, prec):
     cfg = SMALL_CFGS[ci]
     plan = _plans(cfg, prec)
@@ -178,6 +178,25 @@ def test_backward_workload2_sampled(prec):
     op, sc = _oracle(cfg)
     x = SS.workload_signals(2, 64, cfg["N"])
     _check_backward(plan, x, op, sc, GTOL[prec], idx=[11])
+
+
+# 32 pooled frames over several 64-sample tiles per rate: the spin-pair contraction with its
+# 32-frame pooling; at J = 11 the rates with lam_min = 0 (K1 = 144) take the three-atom
+# backward (BF16 planes) or the channel-row one (the FP32-grade split)
+FRAMES32 = [dict(N=2 ** 13, J=8, Q=16, J_fr=3, Q_fr=2, T=2 ** 8, F=16),
+            dict(N=2 ** 15, J=11, Q=16, J_fr=4, Q_fr=2, T=2 ** 10, F=16)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("ci", range(len(FRAMES32)))
+def test_thirty_two_frames_forward_and_backward(ci, prec):
+    cfg = FRAMES32[ci]
+    plan = _plans(cfg, prec)
+    assert plan.shapes.n_t == 32
+    op, sc = _oracle(cfg)
+    x = SS.white_noise_batch(3, cfg["N"], 300 + ci)
+    _check_forward(plan, x, op, sc, TOL[prec])
+    _check_backward(plan, x, op, sc, GTOL[prec], idx=[0, 2], seed=ci)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
