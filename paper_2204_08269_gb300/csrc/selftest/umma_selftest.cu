@@ -234,6 +234,96 @@ __global__ void k_umma_selftest_tf32(const __grid_constant__ CUtensorMap ta,
 
 }  // namespace
 
+// A pair of CTAs (cta_group::2, a cluster of two): D[256 x 128] = A[256 x K] B[K x 128] in
+// BF16 with FP32 accumulation.  CTA r holds rows [128 r, +128) of A (K-major, 128-byte
+// swizzle) and columns [64 r, +64) of B, MN-major (rows of 64 samples) or K-major (64 rows of
+// B^T); the even CTA issues the M = 256 MMAs and commits to both CTAs' barriers, and each CTA
+// reads its 128 rows of D from its own TMEM.  info[4 r + 0, 1] = TMEM base, cluster rank.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(128, 1)
+k_umma2_selftest(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                 float* D, int K, int b_mn, int* status, uint32_t* info) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // each region is twice what this CTA loads, so that the operands stay inside the allocation
+  // whatever the split of A and B between the two CTAs
+  uint8_t* sA = sm;                       // K / 64 boxes of 128 rows x 128 B
+  uint8_t* sB = sA + 256 * K * 2;         // MN-major: K rows x 128 B; K-major: K / 64 boxes of 64 rows
+  __shared__ uint64_t bar_tma, bar_peer, bar_mma;
+  __shared__ uint32_t tmem_base;
+  __shared__ int failed;
+  const uint32_t rank = cluster_rank();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    failed = 0;
+    mbar_init(&bar_tma, 1);
+    mbar_init(&bar_peer, 1);
+    mbar_init(&bar_mma, 1);
+    fence_barrier_init();
+  }
+  if (warp == 0) {
+    tmem_alloc2(&tmem_base, 128);
+    tmem_relinquish2();
+  }
+  __syncthreads();
+  cluster_sync_all();   // both CTAs' barriers exist before the peer arrives on them
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  if (threadIdx.x == 0) {
+    info[rank * 4 + 0] = tbase;
+    info[rank * 4 + 1] = rank;
+    mbar_arrive_expect_tx(&bar_tma, (uint32_t)(128 * K * 2 + 64 * K * 2));
+    for (int k0 = 0; k0 < K; k0 += 64) tma_load_2d(sA + k0 * 256, &ta, k0, 128 * (int)rank, &bar_tma);
+    if (b_mn) {
+      tma_load_2d(sB, &tb, 64 * (int)rank, 0, &bar_tma);
+    } else {
+      for (int k0 = 0; k0 < K; k0 += 64) tma_load_2d(sB + k0 * 128, &tb, k0, 64 * (int)rank, &bar_tma);
+    }
+    bool ok = mbar_wait(&bar_tma, 0, 2000000000ull);
+    if (!ok) failed = 1;
+    if (rank == 1) {
+      if (ok) mbar_arrive_cluster(mapa_rank(&bar_peer, 0));
+    } else {
+      if (ok && !mbar_wait_cluster(&bar_peer, 0, 2000000000ull)) {
+        failed = 2;
+        ok = false;
+      }
+      if (ok) {
+        tc_fence_after();
+        const uint32_t idesc = instr_desc(256, 128, 1, 1, 0, (uint32_t)b_mn, 0);
+        for (int j = 0; j < K / 16; ++j) {
+          const int box = j / 4, off = (j % 4) * 32;
+          const uint64_t ad = smem_desc(smem_u32(sA + box * 128 * 128 + off), 16, 1024, kSw128);
+          const uint64_t bd =
+              b_mn ? smem_desc(smem_u32(sB + j * 16 * 128), (uint32_t)(K * 128), 1024, kSw128)
+                   : smem_desc(smem_u32(sB + box * 64 * 128 + off), 16, 1024, kSw128);
+          mma2_f16(tbase, ad, bd, idesc, j > 0 ? 1u : 0u);
+        }
+        mma2_commit_mc(&bar_mma, (uint16_t)3);
+      }
+    }
+  }
+  __syncthreads();
+  if (!failed) {
+    if (!mbar_wait_cluster(&bar_mma, 0, 2000000000ull)) atomicExch(&failed, 3);
+  }
+  tc_fence_after();
+  if (!failed) {
+    const int row = warp * 32 + lane;
+    for (int c0 = 0; c0 < 128; c0 += 16) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      tmem_wait_ld();
+#pragma unroll
+      for (int i = 0; i < 16; ++i) D[(128 * rank + row) * 128 + c0 + i] = v[i];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();   // the peer's MMAs and reads are done before the pair frees its TMEM
+  if (warp == 0) tmem_dealloc2(tbase, 128);
+  if (threadIdx.x == 0) status[rank] = failed;
+}
+
 extern "C" int jtfs_selftest_umma_tf32(const float* A, const float* B, float* D, int K, int b_mn,
                                        int* status_dev, void* stream) {
   if (K < 32 || K > 64 || K % 32) return 1;
@@ -306,5 +396,33 @@ extern "C" int jtfs_selftest_umma_ta(const void* A, const void* B, float* D, int
   cudaFuncSetAttribute(k_umma_selftest_ta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_umma_selftest_ta<<<1, 128, smem, (cudaStream_t)stream>>>((const __bf16_raw_t*)A, tb, D, K,
                                                               status_dev);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+
+extern "C" int jtfs_selftest_umma2(const void* A, const void* B, float* D, int K, int b_mn,
+                                   int* status_dev, uint32_t* info_dev, void* stream) {
+  if (K < 64 || K > 128 || K % 64) return 1;
+  CUtensorMap ta, tb;
+  std::string err;
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)K, 256};
+    cuuint64_t str[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {64, 128};
+    if (!make_tmap(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, A, dims, str, box, 128, &err)) return 2;
+  }
+  if (b_mn) {
+    cuuint64_t dims[2] = {128, (cuuint64_t)K};
+    cuuint64_t str[1] = {128 * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)K};
+    if (!make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, dims, str, box, 128, &err)) return 2;
+  } else {
+    cuuint64_t dims[2] = {(cuuint64_t)K, 128};
+    cuuint64_t str[1] = {(cuuint64_t)K * 2};
+    cuuint32_t box[2] = {64, 64};
+    if (!make_tmap(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, B, dims, str, box, 128, &err)) return 2;
+  }
+  const size_t smem = 1024 + (size_t)256 * K * 2 + (size_t)128 * K * 2;
+  cudaFuncSetAttribute(k_umma2_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_umma2_selftest<<<2, 128, smem, (cudaStream_t)stream>>>(ta, tb, D, K, b_mn, status_dev, info_dev);
   return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }

@@ -92,3 +92,35 @@ def test_umma_bf16_gemm_a_in_tmem(K):
     ref = A.float() @ Bkn.float()
     err = (D - ref).abs().max().item() / ref.abs().max().item()
     assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("K,b_mn", [(64, 1), (128, 1), (64, 0), (128, 0)])
+def test_umma_cta_pair_gemm(K, b_mn):
+    """cta_group::2 on a cluster of two CTAs: D[256 x 128] = A B with A's rows and B's columns
+    split between the two CTAs' shared memories and D's rows between their TMEMs; both CTAs
+    must receive the same TMEM base from the collective allocation."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2204_08269_gb300 import build
+    build.build()
+    L = ctypes.CDLL(build.SELFTEST_LIB)
+    f = L.jtfs_selftest_umma2
+    f.argtypes = [ctypes.c_void_p] * 3 + [ctypes.c_int] * 2 + [ctypes.c_void_p] * 3
+    f.restype = ctypes.c_int
+    g = torch.Generator(device="cuda").manual_seed(11 * K + b_mn)
+    A = torch.randn(256, K, device="cuda", generator=g).to(torch.bfloat16).contiguous()
+    Bkn = torch.randn(K, 128, device="cuda", generator=g).to(torch.bfloat16)
+    B = Bkn.contiguous() if b_mn else Bkn.t().contiguous()
+    D = torch.full((256, 128), float("nan"), device="cuda")
+    status = torch.full((2,), -1, dtype=torch.int32, device="cuda")
+    info = torch.zeros(8, dtype=torch.int32, device="cuda")
+    rc = f(A.data_ptr(), B.data_ptr(), D.data_ptr(), K, b_mn, status.data_ptr(), info.data_ptr(),
+           None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    inf = info.cpu().tolist()
+    assert status.cpu().tolist() == [0, 0], (status.cpu().tolist(), inf)
+    assert inf[1] == 0 and inf[5] == 1 and inf[0] == inf[4], inf
+    ref = A.float() @ Bkn.float()
+    err = (D - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 1e-5, (err, inf)
