@@ -216,14 +216,30 @@ k_second_order_bwd(DevPlan P, const float2* __restrict__ gys, const float* __res
   for (int k = threadIdx.x; k < R.L; k += blockDim.x) {
     float2 acc = make_float2(0.f, 0.f);
     if (k >= 1 && k < half) {
-      for (int a = 0; a < P.n2; ++a) {
-        const Rate2 A = P.rates2[a];
-        if (A.s == 0 || lam < A.lam_min || k >= A.k2e) continue;
-        const float2 v = gys[(size_t)b * P.y_len + A.off_y + (size_t)(lam - A.lam_min) * A.L +
-                             (k & (A.L - 1))];
-        const float f = __ldg(&P.psi2[(size_t)a * P.K2max + k]) * invLr;
-        acc.x += v.x * f;
-        acc.y += v.y * f;
+      // the rates in groups of eight whose loads are in flight together, summed in
+      // increasing alpha (a rate outside its support adds 0 * 0)
+      for (int a0 = 0; a0 < P.n2; a0 += 8) {
+        float2 v[8];
+        float f[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int a = a0 + q;
+          v[q] = make_float2(0.f, 0.f);
+          f[q] = 0.f;
+          if (a < P.n2) {
+            const Rate2 A = P.rates2[a];
+            if (A.s != 0 && lam >= A.lam_min && k < A.k2e) {
+              v[q] = gys[(size_t)b * P.y_len + A.off_y + (size_t)(lam - A.lam_min) * A.L +
+                         (k & (A.L - 1))];
+              f[q] = __ldg(&P.psi2[(size_t)a * P.K2max + k]) * invLr;
+            }
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          acc.x += v[q].x * f[q];
+          acc.y += v[q].y * f[q];
+        }
       }
     }
     if (g1 && k <= half) {

@@ -51,20 +51,40 @@ __global__ void k_xfft_combine(DevPlan P, const float2* __restrict__ xsub, float
 
 // Periodisation of x-hat * psi-hat_lambda onto L bins: F[k'] = sum_{k = k' mod L} x-hat[k] psi[k],
 // written to buf in bit-reversed order (padded layout) for the decimation-in-time inverse FFT.
+// Each thread keeps the first terms of eight bins in flight before it sums them (most bins
+// take one or two terms); the terms of each bin are added in increasing k.
 __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R,
                                                  const float2* __restrict__ xb, float2* buf) {
   const float* v = P.psi1 + R.off_v;
   const int kend = R.ks + R.kl;
-  for (int kp = threadIdx.x; kp < R.L; kp += blockDim.x) {
-    int k = R.ks + ((kp - R.ks) & (R.L - 1));
-    float2 acc = make_float2(0.f, 0.f);
-    for (; k < kend; k += R.L) {
-      const float2 a = xb[k];
-      const float f = __ldg(&v[k - R.ks]);
-      acc.x += a.x * f;
-      acc.y += a.y * f;
+  const int step = blockDim.x;
+  for (int base = threadIdx.x; base < R.L; base += 8 * step) {
+    float2 a[8];
+    float f[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int kp = base + q * step;
+      const int k = R.ks + ((kp - R.ks) & (R.L - 1));
+      a[q] = make_float2(0.f, 0.f);
+      f[q] = 0.f;
+      if (kp < R.L && k < kend) {
+        a[q] = xb[k];
+        f[q] = __ldg(&v[k - R.ks]);
+      }
     }
-    buf[fft_pad(bitrev(kp, R.logL))] = acc;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int kp = base + q * step;
+      if (kp >= R.L) break;
+      float2 acc = make_float2(a[q].x * f[q], a[q].y * f[q]);
+      for (int k = R.ks + ((kp - R.ks) & (R.L - 1)) + R.L; k < kend; k += R.L) {
+        const float2 t = xb[k];
+        const float w = __ldg(&v[k - R.ks]);
+        acc.x += t.x * w;
+        acc.y += t.y * w;
+      }
+      buf[fft_pad(bitrev(kp, R.logL))] = acc;
+    }
   }
 }
 
@@ -95,18 +115,41 @@ __device__ __forceinline__ void second_order_rows_ifft(const DevPlan& P, const R
     s_inv[r] = 1.f / (float)R.L;
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
-    const int row = idx >> logL, kp = idx & (L - 1);
-    const float2* ur = ub + s_off[row];
-    const int kend = s_kend[row];
-    float2 acc = make_float2(0.f, 0.f);
-    for (int k = kp; k < kend; k += L) {
-      const float2 u = ur[k];
-      const float f = __ldg(&psi[k]);
-      acc.x += u.x * f;
-      acc.y += u.y * f;
+  // the first terms of eight bins per thread in flight before they are summed (a bin takes
+  // one term below the filter's support end, further ones only where that end passes L)
+  const int total = G * L, step = blockDim.x;
+  for (int base = threadIdx.x; base < total; base += 8 * step) {
+    float2 u[8];
+    float f[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = base + q * step;
+      u[q] = make_float2(0.f, 0.f);
+      f[q] = 0.f;
+      if (idx < total) {
+        const int row = idx >> logL, kp = idx & (L - 1);
+        if (kp < s_kend[row]) {
+          u[q] = ub[s_off[row] + kp];
+          f[q] = __ldg(&psi[kp]);
+        }
+      }
     }
-    sm[fft_pad((row << logL) + bitrev(kp, logL))] = acc;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int idx = base + q * step;
+      if (idx >= total) break;
+      const int row = idx >> logL, kp = idx & (L - 1);
+      const float2* ur = ub + s_off[row];
+      const int kend = s_kend[row];
+      float2 acc = make_float2(u[q].x * f[q], u[q].y * f[q]);
+      for (int k = kp + L; k < kend; k += L) {
+        const float2 t = ur[k];
+        const float w = __ldg(&psi[k]);
+        acc.x += t.x * w;
+        acc.y += t.y * w;
+      }
+      sm[fft_pad((row << logL) + bitrev(kp, logL))] = acc;
+    }
   }
   __syncthreads();
   fft_dit_rows_r16<+1>(sm, logL, G, twl_for(P, logL));
