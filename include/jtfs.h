@@ -323,13 +323,6 @@ jtfs_status jtfs_plan_set_wait_budget(jtfs_plan* plan, uint64_t wait_ns);
  * Default off. */
 jtfs_status jtfs_plan_set_check_finite(jtfs_plan* plan, int32_t on);
 
-/* on != 0: the spin-pair forward contraction (Eq. 3's |W_c * Y|, 16 or 32 pooled frames, BF16
- * planes) runs on pairs of CTAs (thread-block clusters of two on two SMs) whose M = 256
- * tensor-core products cover two 128-row blocks and read half of each Y tile from either SM;
- * 0 (the default, the faster form on GB300): one CTA per 128-row block.  Both forms compute
- * every output with the same products in the same order.  No effect on other plans. */
-jtfs_status jtfs_plan_set_cta_pairs(jtfs_plan* plan, int32_t on);
-
 /* Exercises the timeout path on the device: launches one block on `stream` that waits, with
  * the contraction kernels' bounded wait and a budget of wait_ns in [1 us, 1 s], on a barrier
  * that nothing ever completes; the wait gives up, the block records its code in the plan's

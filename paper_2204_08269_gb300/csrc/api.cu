@@ -892,12 +892,6 @@ jtfs_status jtfs_plan_set_check_finite(jtfs_plan* p, int32_t on) {
   return JTFS_OK;
 }
 
-jtfs_status jtfs_plan_set_cta_pairs(jtfs_plan* p, int32_t on) {
-  if (!p) { set_error("NULL plan"); return JTFS_ERR_INVALID_ARG; }
-  p->tc_cta_pair = on != 0;
-  return JTFS_OK;
-}
-
 jtfs_status jtfs_diagnose_wait_timeout(const jtfs_plan* p, uint64_t wait_ns, void* stream) {
   if (!p || wait_ns < 1000 || wait_ns > 1000000000ull) {
     set_error("diagnostic budget must lie in [1 us, 1 s]");

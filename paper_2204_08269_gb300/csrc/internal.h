@@ -120,22 +120,17 @@ struct jtfs_plan {
   bool use_tc;
   int n1_pad;                  // lambda' columns of the W planes (multiple of 32)
   void* d_wplanes[6];          // Wr_hi, Wi_hi, Wr_lo, Wi_lo, -Wi_hi, -Wi_lo: [C * n1][n1_pad] bf16
-  bool tc_pair = false;        // forward in the spin-pair form (16 or 32 frames, BF16 planes)
-  bool tc_cta_pair = false;    // spin-pair forward on CTA pairs (cta_group::2, M = 256)
+  bool tc_pair = false;        // forward in the spin-pair form (16 frames, BF16 planes)
   int pr_phi0 = 0;             // first phi_F pair row: n_fr n1 rounded up to 32 (zero rows
                                // between), so 32-row chunks never mix spin and phi_F rows
   int n_pr = 0;                // pair rows pr_phi0 + n1
   void* d_wpair[4] = {nullptr, nullptr, nullptr, nullptr};   // Wr_hi, Wi_hi, Wr_lo, Wi_lo of
-                               // the spin-up and phi_F rows: [n_pr][n1_pad] bf16
+                               // the spin-up and phi_F rows: [n_pr][n1_pad] bf16 (16 frames)
   void* d_wtf;                 // pooling weights hi / lo: [n2 * NT][tc_wt_cols] bf16
   int tc_wt_cols;
   std::vector<int> tc_items;   // (alpha, m0, n_tiles, 0) per signal; resident-W items first
   int tc_n_res;                // items whose W tile fits the resident form
   int* d_tc_items;
-  std::vector<int> tc2_items;  // the same over 256-row pair items (CTA-pair form)
-  int tc2_n_res = 0;
-  int* d_tc2_items = nullptr;
-  mutable int tc2_clusters = 0;   // co-resident CTA pairs of the CTA-pair forward (0: not queried)
   int* d_err;                  // device status word: 0 ok, kErrNumeric after a non-finite
                                // output, any other code from a bounded wait that gave up
   uint64_t wait_ns = 2000000000ull;   // budget of every bounded device wait (ns)

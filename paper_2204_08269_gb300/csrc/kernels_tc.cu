@@ -836,7 +836,7 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
 // registers): the quarter's four warps exchange their staged |Z| blocks, and warp cg pools
 // channel cg >> 1 over frames [16 (cg & 1), +16) and all 64 samples, so that it owns its
 // outputs and writes them at an item's end.
-template <bool RES, int PS, int NT, bool CP>
+template <bool RES, int PS, int NT>
 __global__ void __launch_bounds__(kThreads, 1)
 k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   static_assert(NT == 16 || NT == 32, "pooled frames");
@@ -855,44 +855,31 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   // a warp's staging: its |Z| blocks per channel and plane, at an item's end its 32 x NT partials
   constexpr uint32_t kStgWarp = 2 * PS * kStg > NT * 32 * 4 ? 2 * PS * kStg : NT * 32 * 4;
   const int max_kb = args.res_kb;
-  // per plane [Yr atom | Yi atom]; a CTA of a pair holds one of the two (B's N / 2 columns)
-  const uint32_t y_bytes = planes * (CP ? 1 : 2) * kYAtom;
+  const uint32_t y_bytes = planes * 2 * kYAtom;          // per plane [Yr atom | Yi atom]
   const uint32_t stage_bytes = RES ? y_bytes : planes * 2 * kAPlane + y_bytes;
   uint8_t* sA = sm;
   uint8_t* sStage = sm + (RES ? planes * 2 * max_kb * kAPlane : 0);
   uint8_t* sWt = sStage + S * stage_bytes;               // WS x pplanes (hi, lo adjacent)
   uint8_t* sStg = sWt + WS * pplanes * kWHalf;           // 16 warps x kStgWarp
   __shared__ uint64_t full_bar[8], empty_bar[8], wfull[kMaxWS], wempty[kMaxWS], tfull[2],
-      tempty[2], red_full[4], red_free[4], sfull[4], sfree[4], a_full, a_free, mma_done,
-      peer_full[8], peer_a;
+      tempty[2], red_full[4], red_free[4], sfull[4], sfree[4], a_full, a_free, mma_done;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // CTA pair: both CTAs walk the same items; CTA `rank` takes rows [128 rank, +128) of the
-  // item's 256 and part `rank` (re / im) of every Y atom
-  const uint32_t rank = CP ? cluster_rank() : 0;
-  const int it0 = CP ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-  const int istep = CP ? (int)(gridDim.x >> 1) : (int)gridDim.x;
-  // barriers that the peer CTA or a multicast commit also arrives on
-  auto wait_x = [&](uint64_t* bar, uint32_t parity) {
-    return CP ? mbar_wait_cluster(bar, parity, wait_budget) : mbar_wait(bar, parity, wait_budget);
-  };
 
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < S; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
-      mbar_init(&peer_full[s], 1);
     }
-    mbar_init(&peer_a, 1);
     for (int s = 0; s < WS; ++s) {
       mbar_init(&wfull[s], 1);
       mbar_init(&wempty[s], kEpiWarps);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], CP ? 2 * kEpiWarps : kEpiWarps);
+      mbar_init(&tempty[a], kEpiWarps);
     }
     for (int q = 0; q < 4; ++q) {
       mbar_init(&red_full[q], 4);
@@ -906,16 +893,10 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     fence_barrier_init();
   }
   if (warp == 1) {
-    if (CP) {
-      tmem_alloc2(&tmem_base, 512);
-      tmem_relinquish2();
-    } else {
-      tmem_alloc(&tmem_base, 512);
-      tmem_relinquish();
-    }
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
   }
   __syncthreads();
-  if (CP) cluster_sync_all();   // the peer's barriers exist before any remote arrival
   tc_fence_after();
   const uint32_t tbase = tmem_base;
 
@@ -934,14 +915,14 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
       uint32_t armed = 0, armed_par = 0, armed_w = 0, armed_w_par = 0;
       int armed_a = -1;
       bool ok = true;
-      for (int it = it0; it < args.n_items && ok && !abort_flag; it += istep) {
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it % args.n_base];
-        const int a = item.x, b = it / args.n_base, m0 = item.y + 128 * (int)rank, ntiles = item.z;
+        const int a = item.x, b = it / args.n_base, m0 = item.y, ntiles = item.z;
         const Rate2 A = P.rates2[a];
         const int lm8 = A.lam_min & ~7;
         const int nkb = (((P.n1 - lm8 + 15) >> 4) + 1) >> 1;
         if (RES) {
-          if (!wait_x(&a_free, aph ^ 1)) { fail(10); ok = false; break; }
+          if (!mbar_wait(&a_free, aph ^ 1, wait_budget)) { fail(10); ok = false; break; }
           mbar_arrive_expect_tx(&a_full, planes * 2 * nkb * kAPlane);
           armed_a = (int)aph;
           for (int pl = 0; pl < planes; ++pl)
@@ -953,7 +934,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         }
         for (int j = 0; j < ntiles && ok; ++j) {
           for (int kb = 0; kb < nkb; ++kb) {
-            if (!wait_x(&empty_bar[stage], phase ^ 1)) { fail(11); ok = false; break; }
+            if (!mbar_wait(&empty_bar[stage], phase ^ 1, wait_budget)) { fail(11); ok = false; break; }
             uint8_t* st = sStage + stage * stage_bytes;
             mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
             armed |= 1u << stage;
@@ -964,13 +945,9 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
                 if (!RES)
                   tma_load_2d(st + (pl * 2 + part) * kAPlane, &maps.w[pl * 2 + part],
                               lm8 + kb * kBK, m0, &full_bar[stage]);
-                if (!CP)
-                  tma_load_3d(sb + (pl * 2 + part) * kYAtom, &maps.y[pl][a], j * BN,
-                              lm8 + kb * kBK - A.lam_min, 2 * b + part, &full_bar[stage]);
+                tma_load_3d(sb + (pl * 2 + part) * kYAtom, &maps.y[pl][a], j * BN,
+                            lm8 + kb * kBK - A.lam_min, 2 * b + part, &full_bar[stage]);
               }
-              if (CP)
-                tma_load_3d(sb + pl * kYAtom, &maps.y[pl][a], j * BN, lm8 + kb * kBK - A.lam_min,
-                            2 * b + (int)rank, &full_bar[stage]);
             }
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
@@ -993,38 +970,13 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0 && CP && rank == 1) {
-      // the odd CTA of a pair issues nothing: it tells the even CTA's issuer when its own W
-      // tile and Y stages have landed
-      const uint32_t peer_full0 = mapa_rank(&peer_full[0], 0), peer_a0 = mapa_rank(&peer_a, 0);
-      int stage = 0;
-      uint32_t phase = 0, aph = 0;
-      bool ok = true;
-      for (int it = it0; it < args.n_items && ok && !abort_flag; it += istep) {
-        const int4 item = args.items[it % args.n_base];
-        const Rate2 A = P.rates2[item.x];
-        const int nkb = (((P.n1 - (A.lam_min & ~7) + 15) >> 4) + 1) >> 1;
-        if (RES) {
-          if (!mbar_wait(&a_full, aph, wait_budget)) { fail(24); ok = false; break; }
-          aph ^= 1;
-          mbar_arrive_cluster(peer_a0);
-        }
-        for (int j = 0; j < item.z && ok; ++j)
-          for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&full_bar[stage], phase, wait_budget)) { fail(25); ok = false; break; }
-            mbar_arrive_cluster(peer_full0 + 8 * stage);
-            if (++stage == S) { stage = 0; phase ^= 1; }
-          }
-      }
-      // the even CTA's last MMAs (which read this CTA's shared memory) have completed
-      wait_x(&mma_done, 0);
-    } else if (lane == 0) {
-      const uint32_t id = instr_desc(CP ? 2 * kBM : kBM, 128, 1, 1, 0, 1, 0);
+    if (lane == 0) {
+      const uint32_t id = instr_desc(kBM, 128, 1, 1, 0, 1, 0);
       const int npair = args.passes == 3 ? 3 : 1;
       int stage = 0, acc = 0;
       uint32_t phase = 0, acc_ph = 0, aph = 0;
       bool ok = true;
-      for (int it = it0; it < args.n_items && ok && !abort_flag; it += istep) {
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
         const int4 item = args.items[it % args.n_base];
         const Rate2 A = P.rates2[item.x];
         const int lm8 = A.lam_min & ~7;
@@ -1032,16 +984,14 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         const int nkb = (nks + 1) / 2;
         if (RES) {
           if (!mbar_wait(&a_full, aph, wait_budget)) { fail(9); ok = false; break; }
-          if (CP && !wait_x(&peer_a, aph)) { fail(26); ok = false; break; }
           aph ^= 1;
         }
         for (int j = 0; j < item.z && ok; ++j) {
-          if (!wait_x(&tempty[acc], acc_ph ^ 1)) { fail(12); ok = false; break; }
+          if (!mbar_wait(&tempty[acc], acc_ph ^ 1, wait_budget)) { fail(12); ok = false; break; }
           tc_fence_after();
           const uint32_t t_a = tbase + acc * 256, t_b = t_a + 128;
           for (int kb = 0; kb < nkb; ++kb) {
             if (!mbar_wait(&full_bar[stage], phase, wait_budget)) { fail(13); ok = false; break; }
-            if (CP && !wait_x(&peer_full[stage], phase)) { fail(27); ok = false; break; }
             tc_fence_after();
             const uint32_t st = smem_u32(sStage + stage * stage_bytes);
             const uint32_t sb = RES ? st : st + planes * 2 * kAPlane;
@@ -1064,34 +1014,26 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
                     const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
                     const uint64_t ar = dA + (uint64_t)(pa * 2 * as4 + ks * 2);
                     const uint64_t ai = ar + as4;
-                    const uint64_t bd =
-                        dB + (uint64_t)(pb * (CP ? 1 : 2) * (kYAtom >> 4) + ks * 128);
+                    const uint64_t bd = dB + (uint64_t)(pb * 2 * (kYAtom >> 4) + ks * 128);
                     const uint32_t f = (kb | ks | q) ? 1u : 0u;
-                    if (CP) {
-                      mma2_f16(t_a, ar, bd, id, f);
-                      mma2_f16(t_b, ai, bd, id, f);
-                    } else {
-                      mma_f16(t_a, ar, bd, id, f);    // [P1 | P3] = Wr [Yr | Yi]
-                      mma_f16(t_b, ai, bd, id, f);    // [P4 | P2] = Wi [Yr | Yi]
-                    }
+                    mma_f16(t_a, ar, bd, id, f);    // [P1 | P3] = Wr [Yr | Yi]
+                    mma_f16(t_b, ai, bd, id, f);    // [P4 | P2] = Wi [Yr | Yi]
                   }
                 }
               }
             }
-            if (CP) mma2_commit_mc(&empty_bar[stage], 3); else mma_commit(&empty_bar[stage]);
+            mma_commit(&empty_bar[stage]);
             if (++stage == S) { stage = 0; phase ^= 1; }
           }
           if (!ok) break;
-          if (CP) mma2_commit_mc(&tfull[acc], 3); else mma_commit(&tfull[acc]);
+          mma_commit(&tfull[acc]);
           if (++acc == 2) { acc = 0; acc_ph ^= 1; }
         }
         if (!ok) break;
-        if (RES) {
-          if (CP) mma2_commit_mc(&a_free, 3); else mma_commit(&a_free);
-        }
+        if (RES) mma_commit(&a_free);
       }
-      if (CP) mma2_commit_mc(&mma_done, 3); else mma_commit(&mma_done);
-      wait_x(&mma_done, 0);
+      mma_commit(&mma_done);
+      mbar_wait(&mma_done, 0, wait_budget);
     }
   } else {
     // ------------------------------------------------------------ epilogue + pooling
@@ -1123,9 +1065,9 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     // phase): the first wait is for parity 0
     uint32_t acc_ph = 0, wph = 0, rf_ph = 0, rfree_ph = 1, sf_ph = 0, sr_ph = 0;
     bool red_pending = false;
-    for (int it = it0; it < args.n_items; it += istep) {
+    for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
       const int4 item = args.items[it % args.n_base];
-      const int a = item.x, b = it / args.n_base, m0 = item.y + 128 * (int)rank;
+      const int a = item.x, b = it / args.n_base, m0 = item.y;
       bool ok = !abort_flag;
       float c[CD][2][2][4];                    // [channel up / down][mt][nt][4]
 #pragma unroll
@@ -1143,7 +1085,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         red_pending = false;
       }
       for (int j = 0; j < item.z && ok; ++j) {
-        if (!wait_x(&tfull[acc], acc_ph)) { fail(14); ok = false; break; }
+        if (!mbar_wait(&tfull[acc], acc_ph, wait_budget)) { fail(14); ok = false; break; }
         tc_fence_after();
         if (!mbar_wait(&wfull[ws], wph, wait_budget)) { fail(19); ok = false; break; }
         const uint32_t t_col = tbase + acc * 256 + lane_off + cg * 16;
@@ -1165,10 +1107,7 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           if (h8 == 1) {
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) {
-              // the accumulator is released to the even CTA's issuer
-              if (CP) mbar_arrive_cluster(mapa_rank(&tempty[acc], 0)); else mbar_arrive(&tempty[acc]);
-            }
+            if (lane == 0) mbar_arrive(&tempty[acc]);
           }
           uint32_t hv[2][4], lv[2][4];         // [up / down][8 samples as bf16x2]
 #pragma unroll
@@ -1375,10 +1314,9 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     }
   }
   __syncthreads();
-  if (CP) cluster_sync_all();   // no remote arrival or MMA of the pair is still in flight
   if (warp == 1) {
     tc_fence_after();
-    if (CP) tmem_dealloc2(tbase, 512); else tmem_dealloc(tbase, 512);
+    tmem_dealloc(tbase, 512);
   }
 }
 
@@ -1583,7 +1521,7 @@ size_t tc_smem_for(const jtfs_plan* p, bool res) {
 // whose warps stage both channels, 3 - nh staging blocks per pooling plane, and reduce their
 // partials through those blocks instead of the 32 KB buffer).
 struct Tc16Shape {
-  int apl, cpl, ppl, nya, nh, WS, nt, yparts;
+  int apl, cpl, ppl, nya, nh, WS, nt;
   size_t fixed(bool res, int res_kb) const {
     // a spin-pair warp's staging also holds its 32 x nt FP32 partials at an item's end
     const size_t stg = nh == 1 ? std::max<size_t>(2 * ppl * 1024, (size_t)nt * 32 * 4) : (size_t)ppl * 1024;
@@ -1591,12 +1529,11 @@ struct Tc16Shape {
            (size_t)kEpiWarps * stg + (nh == 2 ? 4 * 128 * 16 * 4 : 0);
   }
   size_t stage(bool res) const {
-    return (res ? 0 : (size_t)cpl * 2 * apl) + (size_t)cpl * yparts * nya * 4096;
+    return (res ? 0 : (size_t)cpl * 2 * apl) + (size_t)cpl * 2 * nya * 4096;
   }
 };
 
-// cp: the CTA-pair form, whose CTAs each hold one part (re or im) of every Y atom
-Tc16Shape tc16_shape(const jtfs_plan* p, bool cp = false) {
+Tc16Shape tc16_shape(const jtfs_plan* p) {
   Tc16Shape s;
   const bool tf = p->cfg.precision == JTFS_PREC_TF32;
   s.apl = tf ? kBM * kBK * 4 : kBM * kBK * 2;
@@ -1606,20 +1543,19 @@ Tc16Shape tc16_shape(const jtfs_plan* p, bool cp = false) {
   s.nh = p->tc_pair ? 1 : 2;
   s.WS = kMaxWS;
   s.nt = tc_nt(p->n_t);
-  s.yparts = cp ? 1 : 2;
   return s;
 }
 
-int tc16_stages_for(const jtfs_plan* p, bool res, bool cp = false) {
-  const Tc16Shape s = tc16_shape(p, cp);
+int tc16_stages_for(const jtfs_plan* p, bool res) {
+  const Tc16Shape s = tc16_shape(p);
   const size_t fixed = s.fixed(res, tc_res_kb(p)), stage = s.stage(res);
   if (fixed + 2 * stage > kSmemBudget) return 0;
   return (int)std::min<size_t>(8, (kSmemBudget - fixed) / stage);
 }
 
-size_t tc16_smem_for(const jtfs_plan* p, bool res, bool cp = false) {
-  const Tc16Shape s = tc16_shape(p, cp);
-  return s.fixed(res, tc_res_kb(p)) + (size_t)tc16_stages_for(p, res, cp) * s.stage(res);
+size_t tc16_smem_for(const jtfs_plan* p, bool res) {
+  const Tc16Shape s = tc16_shape(p);
+  return s.fixed(res, tc_res_kb(p)) + (size_t)tc16_stages_for(p, res) * s.stage(res);
 }
 }  // namespace
 
@@ -1659,17 +1595,9 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   });
   p->tc_items.clear();
   p->tc_n_res = 0;
-  p->tc2_items.clear();
-  p->tc2_n_res = 0;
   for (auto& it : its) {
     p->tc_items.push_back(it.a); p->tc_items.push_back(it.m0); p->tc_items.push_back(it.nt); p->tc_items.push_back(0);
     if (nkb(it) <= res_kb) ++p->tc_n_res;
-    // CTA-pair items: 256 rows from every even 128-row block (the odd CTA's rows past the
-    // last pair row read zero W rows and write nothing)
-    if (p->tc_pair && it.m0 % (2 * kBM) == 0) {
-      p->tc2_items.push_back(it.a); p->tc2_items.push_back(it.m0); p->tc2_items.push_back(it.nt); p->tc2_items.push_back(0);
-      if (nkb(it) <= res_kb) ++p->tc2_n_res;
-    }
   }
   size_t off = 0;
   auto place = [&](size_t bytes) { size_t at = off; off += (bytes + 1023) & ~(size_t)1023; return at; };
@@ -1686,7 +1614,6 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
   const size_t wt_elems = (size_t)p->n2 * NT * Lmax;
   const size_t o_wt = place(wt_elems * 2 * 2);
   const size_t o_items = place(std::max<size_t>(16, p->tc_items.size() * 4));
-  const size_t o_items2 = place(std::max<size_t>(16, p->tc2_items.size() * 4));
   jtfs_status st;
   if ((st = cuda_check(cudaMalloc(&p->d_tc_mem, off), "tc tables")) != JTFS_OK) return st;
   char* base = (char*)p->d_tc_mem;
@@ -1696,12 +1623,8 @@ jtfs_status build_tc_tables(jtfs_plan* p) {
     for (int i = 0; i < 2; ++i) p->d_wplanes32[i] = base + o_w32[i];
   p->d_wtf = base + o_wt;
   p->d_tc_items = (int*)(base + o_items);
-  p->d_tc2_items = (int*)(base + o_items2);
   if (!p->tc_items.empty() &&
       (st = cuda_check(cudaMemcpy(p->d_tc_items, p->tc_items.data(), p->tc_items.size() * 4, cudaMemcpyHostToDevice), "upload")) != JTFS_OK)
-    return st;
-  if (!p->tc2_items.empty() &&
-      (st = cuda_check(cudaMemcpy(p->d_tc2_items, p->tc2_items.data(), p->tc2_items.size() * 4, cudaMemcpyHostToDevice), "upload")) != JTFS_OK)
     return st;
   k_build_wplanes<<<1024, 256>>>(p->dp, p->n1_pad, (__nv_bfloat16*)p->d_wplanes[0],
                                  (__nv_bfloat16*)p->d_wplanes[1], (__nv_bfloat16*)p->d_wplanes[2],
@@ -1782,12 +1705,10 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       return JTFS_ERR_CUDA;
     }
   }
-  const bool cp = p->tc_pair && p->tc_cta_pair;   // CTA pairs: 256-row items
-  const int n_all = (int)((cp ? p->tc2_items.size() : p->tc_items.size()) / 4);
+  const int n_all = (int)(p->tc_items.size() / 4);
   const bool f16 = NT == 16 || p->tc_pair;   // the 16-frame and spin-pair layouts
-  const int n_res = (f16 ? tc16_stages_for(p, true, cp) : tc_stages_for(p, true)) >= 2
-                        ? (cp ? p->tc2_n_res : p->tc_n_res) : 0;
-  if (n_all > n_res && (f16 ? tc16_stages_for(p, false, cp) : tc_stages_for(p, false)) < 2) {
+  const int n_res = (f16 ? tc16_stages_for(p, true) : tc_stages_for(p, true)) >= 2 ? p->tc_n_res : 0;
+  if (n_all > n_res && (f16 ? tc16_stages_for(p, false) : tc_stages_for(p, false)) < 2) {
     set_error("tensor-core forward: no shared-memory layout for this configuration");
     return JTFS_ERR_UNSUPPORTED;
   }
@@ -1823,62 +1744,29 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       return rc;                                                                                \
     k_joint_fwd_tc16<RESV, TFV><<<grid, kThreads, smem, st>>>(maps, args, d); ++p->prof.launches; \
   } while (0)
-#define JTFS_LAUNCH_PAIR1(RESV, PSV, NTV, CPV)                                                  \
+#define JTFS_LAUNCH_PAIR1(RESV, PSV, NTV)                                                       \
   do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_pair<RESV, PSV, NTV, CPV>,            \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_pair<RESV, PSV, NTV>,                 \
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,      \
                                               (int)smem), "attr pair")) != JTFS_OK)             \
       return rc;                                                                                \
-    if (CPV) {                                                                                  \
-      cudaLaunchConfig_t lc = {};                                                               \
-      cudaLaunchAttribute la[1];                                                                \
-      la[0].id = cudaLaunchAttributeClusterDimension;                                           \
-      la[0].val.clusterDim.x = 2;                                                               \
-      la[0].val.clusterDim.y = 1;                                                               \
-      la[0].val.clusterDim.z = 1;                                                               \
-      lc.gridDim = dim3(grid);                                                                  \
-      lc.blockDim = dim3(kThreads);                                                             \
-      lc.dynamicSmemBytes = smem;                                                               \
-      lc.stream = st;                                                                           \
-      lc.attrs = la;                                                                            \
-      lc.numAttrs = 1;                                                                          \
-      if (p->tc2_clusters == 0) {                                                               \
-        int ncl = 0;                                                                            \
-        if (cudaOccupancyMaxActiveClusters(&ncl, k_joint_fwd_pair<RESV, PSV, NTV, CPV>, &lc) !=  \
-                cudaSuccess || ncl < 1) {                                                       \
-          cudaGetLastError();                                                                   \
-          ncl = n_sm / 2;                                                                       \
-        }                                                                                       \
-        p->tc2_clusters = ncl;                                                                  \
-      }                                                                                         \
-      lc.gridDim = dim3(2 * std::min(args.n_items, p->tc2_clusters));                          \
-      if ((rc = cuda_check(cudaLaunchKernelEx(&lc, k_joint_fwd_pair<RESV, PSV, NTV, CPV>, maps, \
-                                              args, d), "k_joint_fwd_pair (CTA pairs)")) != JTFS_OK) \
-        return rc;                                                                              \
-    } else {                                                                                    \
-      k_joint_fwd_pair<RESV, PSV, NTV, CPV><<<grid, kThreads, smem, st>>>(maps, args, d);       \
-    }                                                                                           \
+    k_joint_fwd_pair<RESV, PSV, NTV><<<grid, kThreads, smem, st>>>(maps, args, d);              \
     ++p->prof.launches;                                                                         \
-  } while (0)
-#define JTFS_LAUNCH_PAIR2(RESV, PSV, NTV)                                                       \
-  do {                                                                                          \
-    if (cp) JTFS_LAUNCH_PAIR1(RESV, PSV, NTV, true); else JTFS_LAUNCH_PAIR1(RESV, PSV, NTV, false); \
   } while (0)
 #define JTFS_LAUNCH_PAIR(RESV, PSV)                                                             \
   do {                                                                                          \
-    if (NT == 16) JTFS_LAUNCH_PAIR2(RESV, PSV, 16); else JTFS_LAUNCH_PAIR2(RESV, PSV, 32);      \
+    if (NT == 16) JTFS_LAUNCH_PAIR1(RESV, PSV, 16); else JTFS_LAUNCH_PAIR1(RESV, PSV, 32);      \
   } while (0)
   for (int pass = 0; pass < 2; ++pass) {
     const bool res = pass == 0;
     const int first = res ? 0 : n_res, count = res ? n_res : n_all - n_res;
     if (count <= 0) continue;
-    args.items = reinterpret_cast<const int4*>(cp ? p->d_tc2_items : p->d_tc_items) + first;
+    args.items = reinterpret_cast<const int4*>(p->d_tc_items) + first;
     args.n_base = count;
     args.n_items = count * B;
-    args.stages = f16 ? tc16_stages_for(p, res, cp) : tc_stages_for(p, res);
-    const size_t smem = f16 ? tc16_smem_for(p, res, cp) : tc_smem_for(p, res);
-    // CTA pairs: two CTAs per item, the grid a whole number of pairs
-    const int grid = cp ? 2 * std::min(args.n_items, n_sm / 2) : std::min(args.n_items, n_sm);
+    args.stages = f16 ? tc16_stages_for(p, res) : tc_stages_for(p, res);
+    const size_t smem = f16 ? tc16_smem_for(p, res) : tc_smem_for(p, res);
+    const int grid = std::min(args.n_items, n_sm);
     if (p->tc_pair) {
       if (args.pool_split) {
         if (res) JTFS_LAUNCH_PAIR(true, 2); else JTFS_LAUNCH_PAIR(false, 2);
@@ -1898,7 +1786,6 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
 #undef JTFS_LAUNCH_TC
 #undef JTFS_LAUNCH_TC16
 #undef JTFS_LAUNCH_PAIR
-#undef JTFS_LAUNCH_PAIR2
 #undef JTFS_LAUNCH_PAIR1
   k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
   ++p->prof.launches;

@@ -85,7 +85,6 @@ def lib():
         "jtfs_sync_status": ([_P, _P], _I32),
         "jtfs_plan_set_wait_budget": ([_P, ctypes.c_uint64], _I32),
         "jtfs_plan_set_check_finite": ([_P, _I32], _I32),
-        "jtfs_plan_set_cta_pairs": ([_P, _I32], _I32),
         "jtfs_diagnose_wait_timeout": ([_P, ctypes.c_uint64, _P], _I32),
         "jtfs_profile_enable": ([_P, _I32], _I32),
         "jtfs_profile_read": ([_P, _P, _I32, ctypes.POINTER(_I64)], _I32),
@@ -123,8 +122,7 @@ def exported_symbols():
             "jtfs_workspace_bytes", "jtfs_forward", "jtfs_backward", "jtfs_forward_backward",
             "jtfs_host_step_bytes", "jtfs_scattering1d_forward", "jtfs_scattering1d_backward",
             "jtfs_forward_backward_host", "jtfs_sync_status", "jtfs_plan_set_wait_budget",
-            "jtfs_plan_set_check_finite", "jtfs_plan_set_cta_pairs", "jtfs_diagnose_wait_timeout",
-            "jtfs_status_string",
+            "jtfs_plan_set_check_finite", "jtfs_diagnose_wait_timeout", "jtfs_status_string",
             "jtfs_last_error", "jtfs_profile_enable", "jtfs_profile_read",
             "jtfs_profile_stage_name", "jtfs_first_order_static", "jtfs_plan_autotune",
             "jtfs_varlen_padded_length",
@@ -402,11 +400,6 @@ class JTFSPlan:
     def check_finite(self, on=True):
         """Scan every output for NaN / Inf after each call (reported by sync())."""
         _check("jtfs_plan_set_check_finite", lib().jtfs_plan_set_check_finite(self._h, int(on)))
-
-    def cta_pairs(self, on=True):
-        """Run the spin-pair forward contraction on CTA pairs or (the default) one CTA per
-        row block; both give the same outputs."""
-        _check("jtfs_plan_set_cta_pairs", lib().jtfs_plan_set_cta_pairs(self._h, int(on)))
 
 
 def mulog_mean(s):

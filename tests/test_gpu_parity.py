@@ -199,27 +199,6 @@ def test_thirty_two_frames_forward_and_backward(ci, prec):
     _check_backward(plan, x, op, sc, GTOL[prec], idx=[0, 2], seed=ci)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
-@pytest.mark.parametrize("which", ["workload2", "frames32"])
-def test_cta_pair_form_matches_single_cta_form(which, prec):
-    """The spin-pair forward on CTA pairs (M = 256 products over two SMs) and on single CTAs
-    (the default): every output row comes from the same products in the same order."""
-    cfg = _workload_cfg(2) if which == "workload2" else FRAMES32[1]
-    a = _plans(cfg, prec)
-    a.cta_pairs(True)
-    b = _plans(cfg, prec)
-    b.cta_pairs(False)
-    n = 8 if which == "workload2" else 5
-    x = torch.from_numpy(SS.white_noise_batch(n, cfg["N"], 400)).cuda()
-    ra = a.forward(x)
-    rb = b.forward(x)
-    for u, v in zip(ra[:3], rb[:3]):
-        e = float((u - v).norm() / u.norm())
-        assert e <= 1e-6, e
-    a.sync()
-    b.sync()
-
-
 @pytest.mark.parametrize("prec", ["fp32", "bf16", "tf32"])
 def test_tensor_core_matches_cuda_core_form(prec):
     """The tcgen05 contraction and the CUDA-core FP32 form agree on the same input."""
