@@ -32,14 +32,27 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int idx
 
 namespace jtfs {
 
-// Register-radix forms for a padded layout: element i of a row block lives at
-// fft_pad(i) = i + i / 16 (one float2 of padding per 16), which keeps the strided accesses
-// of the first passes free of bank conflicts.  A pass fuses RB consecutive radix-2 DIT
+// Register-radix forms for a padded layout: element i of a row block lives at fft_pos(i, logL)
+// (below: one float2 of padding per 16, plus an XOR of index bits for long rows), which keeps
+// the strided accesses of the passes free of bank conflicts.  A pass fuses RB consecutive radix-2 DIT
 // stages s0 .. s0 + RB - 1 in registers: each thread loads 2^RB elements at stride
 // q = 2^(s0-1), applies the stages with the twiddles of the L-point table tw
 // (exp(-2 pi i m / L), m < L / 2; one entry per stage, the others by fixed unit roots) and
 // stores them back.
 __device__ __forceinline__ int fft_pad(int i) { return i + (i >> 4); }
+
+// Shared-memory position of element i of a block of rows of 2^logL elements: fft_pad, and for
+// rows of 512 or more the top four bits of i's index within its row XORed into its low four
+// bits first.  The bit-reversed scatters of the inputs send a half-warp's 16 consecutive bins
+// to indices that differ only in their top bits, which fft_pad alone maps to one bank (2- to
+// 16-way conflicts for rows of 1024 to 16384); the XOR spreads them over all banks, and the
+// strided accesses of the passes and the natural-order reads stay conflict-free (a model of
+// the 8-byte bank mapping over logL = 5 .. 15; at logL = 8 the XOR would conflict instead).
+// Within a row it is a bijection onto the same positions as fft_pad.
+__device__ __forceinline__ int fft_pos(int i, int logL) {
+  if (logL >= 9) i ^= (i >> (logL - 4)) & 15;
+  return i + (i >> 4);
+}
 
 // exp(-i pi m / 2^u) for u = 1..3 and 0 < m < 2^u (conjugated for SIGN = +1): within a
 // pass, the twiddles of stage u are the table entry of the group times these roots.
@@ -74,9 +87,32 @@ __device__ __forceinline__ void fft_dit_pass(float2* buf, int logL, int G,
     const int row = g >> lgpr, b = g & ((1 << lgpr) - 1);
     const int j = b & (q - 1);
     const int base = (row << logL) + ((b >> (s0 - 1)) << (s0 - 1 + RB)) + j;
+    // p[m] = fft_pos(base + m q, logL), from fewer operations: below the last pass of a
+    // swizzled row the XOR term t (the top four in-row bits) is the same for the whole group,
+    // and from q = 16 on the positions step by q + q / 16; in the last radix-16 pass of a
+    // swizzled row (base = j < q) the term is m itself
+    int p[R];
+    if (logL >= 9 && RB == 4 && s0 + 3 == logL) {
+      const int c0 = (row << logL) + (row << (logL - 4)) + (j >> 4);
+#pragma unroll
+      for (int m = 0; m < R; ++m) p[m] = c0 + (j ^ m) + m * (q + (q >> 4));
+    } else if (logL < 9 || s0 + RB - 1 <= logL - 4) {
+      const int t = logL >= 9 ? (base >> (logL - 4)) & 15 : 0;
+      if (q >= 16) {
+        const int p0 = fft_pad(base ^ t);
+#pragma unroll
+        for (int m = 0; m < R; ++m) p[m] = p0 + m * (q + (q >> 4));
+      } else {
+#pragma unroll
+        for (int m = 0; m < R; ++m) p[m] = fft_pad((base + m * q) ^ t);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < R; ++m) p[m] = fft_pos(base + m * q, logL);
+    }
     float2 v[R];
 #pragma unroll
-    for (int m = 0; m < R; ++m) v[m] = buf[fft_pad(base + m * q)];
+    for (int m = 0; m < R; ++m) v[m] = buf[p[m]];
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
       const int sh = logL - s0 - u;
@@ -95,7 +131,7 @@ __device__ __forceinline__ void fft_dit_pass(float2* buf, int logL, int G,
       }
     }
 #pragma unroll
-    for (int m = 0; m < R; ++m) buf[fft_pad(base + m * q)] = v[m];
+    for (int m = 0; m < R; ++m) buf[p[m]] = v[m];
   }
   __syncthreads();
 }

@@ -28,11 +28,11 @@ k_uh_from_u1(DevPlan P, const float* __restrict__ u1, float2* __restrict__ uh) {
   const Row1 R = P.rows1[lam];
   const float* ub = u1 + (size_t)b * P.u1_len + R.off_u;
   for (int m = threadIdx.x; m < R.L; m += blockDim.x)
-    sm[fft_pad(bitrev(m, R.logL))] = make_float2(ub[m], 0.f);
+    sm[fft_pos(bitrev(m, R.logL), R.logL)] = make_float2(ub[m], 0.f);
   __syncthreads();
   fft_dit_rows_r16<-1>(sm, R.logL, 1, twl_for(P, R.logL));
   float2* hb = uh + (size_t)b * P.uh_len + R.off_uh;
-  for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[fft_pad(k)];
+  for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[fft_pos(k, R.logL)];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -165,7 +165,7 @@ k_joint_bwd_simt(DevPlan P, const int2* __restrict__ items, const float2* __rest
 // Spectra of the gY rows, in place: G rows of one rate per CTA (the Y producer's row items),
 // batched forward FFT (padded radix-16 passes, bit-reversed loads), written back in natural
 // order.
-__global__ void __launch_bounds__(kRowThreads)
+__global__ void __launch_bounds__(kRowBound)
 k_gy_spectra(DevPlan P, const int4* __restrict__ items, float2* __restrict__ gy) {
   extern __shared__ float2 sm[];
   const int4 it = items[blockIdx.x];
@@ -185,12 +185,12 @@ k_gy_spectra(DevPlan P, const int4* __restrict__ items, float2* __restrict__ gy)
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int idx = base + q * step;
-      if (idx < total) sm[fft_pad(((idx >> logL) << logL) + bitrev(idx & (L - 1), logL))] = v[q];
+      if (idx < total) sm[fft_pos(((idx >> logL) << logL) + bitrev(idx & (L - 1), logL), logL)] = v[q];
     }
   }
   __syncthreads();
   fft_dit_rows_r16<-1>(sm, logL, G, twl_for(P, logL));
-  for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) g[idx] = sm[fft_pad(idx)];
+  for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) g[idx] = sm[fft_pos(idx, logL)];
 }
 
 // g_U1 row lambda': sum over rates alpha of the adjoint of psi2 (the gY row's spectrum / Lr
@@ -263,15 +263,15 @@ k_second_order_bwd(DevPlan P, const float2* __restrict__ gys, const float* __res
         acc.y += c * G.y;
       }
     }
-    tmp[fft_pad(bitrev(k, R.logL))] = acc;
+    tmp[fft_pos(bitrev(k, R.logL), R.logL)] = acc;
   }
   __syncthreads();
   fft_dit_rows_r16<+1>(tmp, R.logL, 1, twl_for(P, R.logL));
   float* out = gu1 + (size_t)b * P.u1_len + R.off_u;
-  for (int m = threadIdx.x; m < R.L; m += blockDim.x) out[m] = tmp[fft_pad(m)].x;
+  for (int m = threadIdx.x; m < R.L; m += blockDim.x) out[m] = tmp[fft_pos(m, R.logL)].x;
 }
 
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kRowLaunch, 3)   // three 256-thread blocks per SM
 k_stage1_bwd(DevPlan P, const float2* __restrict__ xh, const float* __restrict__ gu1,
              float2* __restrict__ gf) {
   extern __shared__ float2 sm[];
@@ -286,18 +286,18 @@ k_stage1_bwd(DevPlan P, const float2* __restrict__ xh, const float* __restrict__
   for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
     const int r = bitrev(m, R.logL);
     if (m > r) continue;
-    const float2 zm = sm[fft_pad(m)], zr = sm[fft_pad(r)];   // N * z
+    const float2 zm = sm[fft_pos(m, R.logL)], zr = sm[fft_pos(r, R.logL)];   // N * z
     const float am = hypotf(zm.x, zm.y), ar = hypotf(zr.x, zr.y);
     const float fm = (am > 0.f) ? g[m] / am : 0.f, fr = (ar > 0.f) ? g[r] / ar : 0.f;
-    sm[fft_pad(r)] = make_float2(zm.x * fm, zm.y * fm);
-    sm[fft_pad(m)] = make_float2(zr.x * fr, zr.y * fr);
+    sm[fft_pos(r, R.logL)] = make_float2(zm.x * fm, zm.y * fm);
+    sm[fft_pos(m, R.logL)] = make_float2(zr.x * fr, zr.y * fr);
   }
   __syncthreads();
   fft_dit_rows_r16<-1>(sm, R.logL, 1, twl_for(P, R.logL));
   const float invN = 1.f / (float)P.N;
   float2* out = gf + (size_t)b * P.u1_len + R.off_u;
   for (int k = threadIdx.x; k < R.L; k += blockDim.x) {
-    const float2 v = sm[fft_pad(k)];
+    const float2 v = sm[fft_pos(k, R.logL)];
     out[k] = make_float2(v.x * invN, v.y * invN);
   }
 }
@@ -345,7 +345,7 @@ __global__ void k_gxh(DevPlan P, const float2* __restrict__ gf, const float* __r
 
 // g_x[r + D m] = Re(sum_k' e^{2 pi i k' m / M} sum_q H[k' + q M] e^{2 pi i (k' + q M) r / N})
 // (S0's adjoint is already in H unless phi-hat reaches the Nyquist bin)
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, 2)   // two 512-thread blocks per SM
 k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, float* __restrict__ gx) {
   extern __shared__ float2 sm[];
   const int r = blockIdx.x, b = blockIdx.y;
@@ -362,7 +362,7 @@ k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, f
       acc.x += v.x * w.x - v.y * w.y;
       acc.y += v.x * w.y + v.y * w.x;
     }
-    sm[fft_pad(bitrev(kp, P.logM))] = acc;
+    sm[fft_pos(bitrev(kp, P.logM), P.logM)] = acc;
   }
   __syncthreads();
   fft_dit_rows_r16<+1>(sm, P.logM, 1, twl_for(P, P.logM));
@@ -370,7 +370,7 @@ k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, f
   float* out = gx + (size_t)b * P.N;
   for (int m = threadIdx.x; m < P.M; m += blockDim.x) {
     const int n = r + P.D * m;
-    float v = sm[fft_pad(m)].x;
+    float v = sm[fft_pos(m, P.logM)].x;
     if (g0)
       for (int t = 0; t < P.n_t; ++t) v += __ldg(&P.phiT[(t * P.T - n) & (P.N - 1)]) * g0[t];
     out[n] = v;
@@ -381,7 +381,7 @@ k_gx(DevPlan P, const float2* __restrict__ gxh, const float* __restrict__ gs0, f
 // shared memory as in the forward, then gY = g_|Y| Y / |Y| (0 where Y = 0) with
 // g_|Y|[m] = sum_t s_alpha phi_T[(t T - m s_alpha) mod N] g_S2t[t], written in the layout of the
 // transform's gY so that the second-order adjoint that follows is shared.
-__global__ void __launch_bounds__(kRowThreads)
+__global__ void __launch_bounds__(kRowBound)
 k_scat1d_bwd_rows(DevPlan P, const int4* __restrict__ items, const float2* __restrict__ uh,
                   const float* __restrict__ gs2t, float2* __restrict__ gy) {
   extern __shared__ float2 sm[];
@@ -401,7 +401,7 @@ k_scat1d_bwd_rows(DevPlan P, const int4* __restrict__ items, const float2* __res
     for (int t = 0; t < nt; ++t)
       ga = fmaf(__ldg(&P.phiT[((long long)t * P.T - (long long)m * A.s) & (P.N - 1)]),
                 __ldg(&g[r * nt + t]), ga);
-    const float2 v = sm[fft_pad(idx)];
+    const float2 v = sm[fft_pos(idx, logL)];
     const float mag = sqrtf(v.x * v.x + v.y * v.y);
     const float sc = mag > 0.f ? ga * (float)A.s / mag : 0.f;
     out[idx] = make_float2(v.x * sc, v.y * sc);

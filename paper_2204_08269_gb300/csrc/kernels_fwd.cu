@@ -76,7 +76,7 @@ k_s0(DevPlan P, const float* __restrict__ x, float* __restrict__ s0) {
   }
 }
 
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kRowLaunch, 3)   // three 256-thread blocks per SM
 k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
             float2* __restrict__ uh, float* __restrict__ s1) {
   extern __shared__ float2 sm[];
@@ -89,7 +89,7 @@ k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
   const float invN = 1.f / (float)P.N;
   float* ub = u1 + (size_t)b * P.u1_len + R.off_u;
   for (int m = threadIdx.x; m < R.L; m += blockDim.x) {
-    const float2 z = sm[fft_pad(m)];
+    const float2 z = sm[fft_pos(m, R.logL)];
     const float a = hypotf(z.x, z.y) * invN;
     ub[m] = a;
     su[m] = a;
@@ -97,11 +97,11 @@ k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
   __syncthreads();
   // the row again, bit-reversed, for the forward FFT
   for (int m = threadIdx.x; m < R.L; m += blockDim.x)
-    sm[fft_pad(bitrev(m, R.logL))] = make_float2(su[m], 0.f);
+    sm[fft_pos(bitrev(m, R.logL), R.logL)] = make_float2(su[m], 0.f);
   __syncthreads();
   fft_dit_rows_r16<-1>(sm, R.logL, 1, twl_for(P, R.logL));
   float2* hb = uh + (size_t)b * P.uh_len + R.off_uh;
-  for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[fft_pad(k)];
+  for (int k = threadIdx.x; k < (R.L >> 1); k += blockDim.x) hb[k] = sm[fft_pos(k, R.logL)];
   // S1[lambda, t] = sum_m s phi_T[(tT - m s) mod N] U1[m] from the row spectrum: with tau =
   // T / s, it is s (phi_s * U1)[t tau] for phi_s[j] = phi_T[j s], whose length-L DFT is
   // (1 / s) sum_r phi-hat[k + r L]; so S1[t] = (1 / L) sum_k Phi[k] U1-hat[k] e^{2 pi i k t / n_t}
@@ -123,7 +123,7 @@ k_scalogram(DevPlan P, const float2* __restrict__ xh, float* __restrict__ u1,
         for (int q = k; q <= P.phiT_kmax; q += R.L) ph += __ldg(&P.phiThat[q]);
         for (int q = R.L - k; q <= qneg; q += R.L) ph += __ldg(&P.phiThat[q]);
         if (ph == 0.f) continue;
-        const float2 u = sm[fft_pad(k)];
+        const float2 u = sm[fft_pos(k, R.logL)];
         float sn, cs;
         sincospif(2.f * (float)((k * t) & (P.n_t - 1)) / (float)P.n_t, &sn, &cs);
         acc += ((k == 0 || k == half) ? 1.f : 2.f) * ph * (u.x * cs - u.y * sn);
@@ -284,7 +284,7 @@ __global__ void k_transpose_yt(DevPlan P, int a, const float* __restrict__ y,
 // |Y_alpha[lambda'][m]|.  One CTA per G rows of one rate: the rows are folded and inverse
 // transformed in shared memory as for the Y producer, their moduli replace them there, and
 // each warp reduces one (row, frame) output at a time; Y never leaves the chip.
-__global__ void __launch_bounds__(kRowThreads)
+__global__ void __launch_bounds__(kRowBound)
 k_scat1d_rows(DevPlan P, const int4* __restrict__ items, const float2* __restrict__ uh,
               float* __restrict__ s2t) {
   extern __shared__ float2 sm[];
@@ -297,8 +297,8 @@ k_scat1d_rows(DevPlan P, const int4* __restrict__ items, const float2* __restric
   second_order_rows_ifft(P, A, a, lam0, G, uh + (size_t)b * P.uh_len, sm, s_off, s_kend, s_inv);
   __syncthreads();
   for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
-    const float2 v = sm[fft_pad(idx)];
-    sm[fft_pad(idx)].x = sqrtf(v.x * v.x + v.y * v.y) * s_inv[idx >> logL];
+    const float2 v = sm[fft_pos(idx, logL)];
+    sm[fft_pos(idx, logL)].x = sqrtf(v.x * v.x + v.y * v.y) * s_inv[idx >> logL];
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -307,7 +307,7 @@ k_scat1d_rows(DevPlan P, const int4* __restrict__ items, const float2* __restric
     float acc = 0.f;
     for (int m = lane; m < L; m += 32)
       acc = fmaf(__ldg(&P.phiT[((long long)t * P.T - (long long)m * A.s) & (P.N - 1)]),
-                 sm[fft_pad((r << logL) + m)].x, acc);
+                 sm[fft_pos((r << logL) + m, logL)].x, acc);
     for (int q = 16; q > 0; q >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, q);
     if (lane == 0)
       s2t[(((size_t)b * P.n2 + a) * P.n1 + lam0 + r) * nt + t] = acc * (float)A.s;

@@ -23,11 +23,11 @@ k_xfft_sub(DevPlan P, const float* __restrict__ x, float2* __restrict__ xsub) {
   const int r = blockIdx.x, b = blockIdx.y;
   const float* xb = x + (size_t)b * P.N;
   for (int m = threadIdx.x; m < P.M; m += blockDim.x)
-    sm[fft_pad(bitrev(m, P.logM))] = make_float2(__ldg(&xb[r + (size_t)P.D * m]), 0.f);
+    sm[fft_pos(bitrev(m, P.logM), P.logM)] = make_float2(__ldg(&xb[r + (size_t)P.D * m]), 0.f);
   __syncthreads();
   fft_dit_rows_r16<-1>(sm, P.logM, 1, twl_for(P, P.logM));
   float2* out = xsub + ((size_t)b * P.D + r) * P.M;
-  for (int k = threadIdx.x; k < P.M; k += blockDim.x) out[k] = sm[fft_pad(k)];
+  for (int k = threadIdx.x; k < P.M; k += blockDim.x) out[k] = sm[fft_pos(k, P.logM)];
 }
 
 __global__ void k_xfft_combine(DevPlan P, const float2* __restrict__ xsub, float2* __restrict__ xh) {
@@ -83,7 +83,7 @@ __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R
         acc.x += t.x * w;
         acc.y += t.y * w;
       }
-      buf[fft_pad(bitrev(kp, R.logL))] = acc;
+      buf[fft_pos(bitrev(kp, R.logL), R.logL)] = acc;
     }
   }
 }
@@ -96,6 +96,10 @@ __device__ __forceinline__ void fold_first_order(const DevPlan& P, const Row1& R
 // (OUT_BF16 = 2) in the contraction layout [alpha][2 b + part][lambda' - lam_min][n].  The fold only visits bins below the rate's
 // psi-hat support end.
 constexpr int kRowThreads = 512;
+// launch bound of the row kernels, which run with 256 or 512 threads: declared for 768 so that
+// the compiler keeps them within 80 registers, where three 256-thread blocks share an SM (at
+// 81 to 96 only two fit)
+constexpr int kRowBound = 768;
 constexpr int kMaxRowsPerItem = 512;   // G <= rows_cap / 32
 
 // Folds the G rows lam0 .. lam0 + G - 1 of rate a (U1-hat * psi-hat_alpha onto L_alpha bins)
@@ -148,7 +152,7 @@ __device__ __forceinline__ void second_order_rows_ifft(const DevPlan& P, const R
         acc.x += t.x * w;
         acc.y += t.y * w;
       }
-      sm[fft_pad((row << logL) + bitrev(kp, logL))] = acc;
+      sm[fft_pos((row << logL) + bitrev(kp, logL), logL)] = acc;
     }
   }
   __syncthreads();
@@ -156,7 +160,7 @@ __device__ __forceinline__ void second_order_rows_ifft(const DevPlan& P, const R
 }
 
 template <int OUT_BF16>
-__global__ void __launch_bounds__(kRowThreads)
+__global__ void __launch_bounds__(kRowBound)
 k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __restrict__ uh,
                     float2* __restrict__ y, __nv_bfloat16* __restrict__ yhi,
                     __nv_bfloat16* __restrict__ ylo, int B) {
@@ -172,7 +176,7 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
     float2* ya = y + (size_t)b * P.y_len + A.off_y + (size_t)(lam0 - A.lam_min) * L;
     for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) {
       const float inv = s_inv[idx >> logL];
-      const float2 v = sm[fft_pad(idx)];
+      const float2 v = sm[fft_pos(idx, logL)];
       ya[idx] = make_float2(v.x * inv, v.y * inv);
     }
   } else if (OUT_BF16 == 2) {
@@ -183,7 +187,7 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
     for (int i2 = threadIdx.x; i2 < (G * L) >> 1; i2 += blockDim.x) {
       const int idx = 2 * i2;
       const float inv = s_inv[idx >> logL];
-      const float2 v0 = sm[fft_pad(idx)], v1 = sm[fft_pad(idx + 1)];
+      const float2 v0 = sm[fft_pos(idx, logL)], v1 = sm[fft_pos(idx + 1, logL)];
       *reinterpret_cast<float2*>(yf + base + idx) = make_float2(v0.x * inv, v1.x * inv);
       *reinterpret_cast<float2*>(yf + base + plane + idx) = make_float2(v0.y * inv, v1.y * inv);
     }
@@ -195,7 +199,7 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
     for (int i2 = threadIdx.x; i2 < (G * L) >> 1; i2 += blockDim.x) {
       const int idx = 2 * i2;
       const float inv = s_inv[idx >> logL];
-      const float2 v0 = sm[fft_pad(idx)], v1 = sm[fft_pad(idx + 1)];
+      const float2 v0 = sm[fft_pos(idx, logL)], v1 = sm[fft_pos(idx + 1, logL)];
       const float r0 = v0.x * inv, r1 = v1.x * inv, i0 = v0.y * inv, i1 = v1.y * inv;
       const __nv_bfloat162 hr = __floats2bfloat162_rn(r0, r1), hi_ = __floats2bfloat162_rn(i0, i1);
       *reinterpret_cast<__nv_bfloat162*>(yhi + base + idx) = hr;
