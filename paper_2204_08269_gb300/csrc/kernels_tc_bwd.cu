@@ -1887,7 +1887,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
 #undef JTFS_LAUNCH_TCBP1
       continue;
     }
-    const int PLf = three ? 2 : 1, RCf = nat == 1 ? 64 : 32;
+    const int RCf = nat == 1 ? 64 : 32;
     TfMaps fm;
     for (int pl = 0; pl < 6; ++pl) {
       cuuint64_t dims[2] = {(cuuint64_t)p->n1_pad, (cuuint64_t)rows};
