@@ -1320,6 +1320,397 @@ k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   }
 }
 
+// ------------------------------------------------------------------ spin-pair form, tensor pooling
+// The spin-pair forward with the phi_T pooling on the tensor cores instead of mma.sync.  The
+// epilogue stages |Z| (BF16 hi, lo for the FP32-grade split) of both spins in the K-major
+// 128-byte-swizzled layout of an MMA operand, [128 rows][64 samples] per spin and plane, and a
+// second issuing thread accumulates D_spin[row][f] += |Z|[row][n] [W_hi | W_lo][f][n] over the
+// item's tiles into TMEM (N = NT per weight plane: frames of W_hi, then of W_lo; both |Z| planes
+// accumulate into the same D, so D[f] + D[NT + f] = (Z_hi + Z_lo)(W_hi + W_lo)).  The TMEM holds
+// one 256-column product accumulator beside the two pooling accumulators, so the product of tile
+// j + 1 starts once the epilogue has loaded tile j.  At an item's end warp (quarter, cg) reads
+// spin cg >> 1, frames [NT / 2 (cg & 1), +NT / 2) of its 32 rows and writes them.
+constexpr int kTpThreads = 32 * 19;   // producer, product issuer, 16 epilogue warps, pooling issuer
+constexpr int kTpWarpPool = 18;
+
+template <bool RES, int PS, int NT>
+__global__ void __launch_bounds__(kTpThreads, 1)
+k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
+  static_assert(NT == 16 || NT == 32, "pooled frames");
+  const uint64_t wait_budget = args.wait_ns;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int BN = 64;
+  constexpr int NP = PS * NT;                            // pooling N (frames of W_hi [, W_lo])
+  const int planes = args.passes == 3 ? 2 : 1;
+  const int S = args.stages, WS = args.wstages;
+  constexpr uint32_t kAPlane = kBM * kBK * 2;            // 8 KB: 128 rows x 32 lambda', SW64
+  constexpr uint32_t kYAtom = 4096;                      // 32 lambda' x 64 samples, SW128
+  constexpr uint32_t kWHalf = NT * 64 * 2;               // one weight plane: NT frames x 64 samples
+  constexpr uint32_t kZPlane = 128 * 64 * 2;             // |Z| of one spin and plane: 16 KB
+  const int max_kb = args.res_kb;
+  const uint32_t y_bytes = planes * 2 * kYAtom;          // per plane [Yr atom | Yi atom]
+  const uint32_t stage_bytes = RES ? y_bytes : planes * 2 * kAPlane + y_bytes;
+  uint8_t* sA = sm;
+  uint8_t* sStage = sm + (RES ? planes * 2 * max_kb * kAPlane : 0);
+  uint8_t* sWt = sStage + S * stage_bytes;               // WS slots of [W_hi plane][W_lo plane]
+  uint8_t* sZ = sWt + WS * PS * kWHalf;                  // [spin][plane] planes of |Z|
+  __shared__ uint64_t full_bar[8], empty_bar[8], wfull[kMaxWS], wempty[kMaxWS], tfull, tempty,
+      sfull, sfree, dfull, dfree, a_full, a_free, mma_done, pool_done;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < S; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int s = 0; s < WS; ++s) {
+      mbar_init(&wfull[s], 1);
+      mbar_init(&wempty[s], 1);
+    }
+    mbar_init(&tfull, 1);
+    mbar_init(&tempty, kEpiWarps);
+    mbar_init(&sfull, kEpiWarps);
+    mbar_init(&sfree, 1);
+    mbar_init(&dfull, 1);
+    mbar_init(&dfree, kEpiWarps);
+    mbar_init(&a_full, 1);
+    mbar_init(&a_free, 1);
+    mbar_init(&mma_done, 1);
+    mbar_init(&pool_done, 1);
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(&tmem_base, 512);
+    tmem_relinquish();
+  }
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base;
+  const uint32_t t_pool = tbase + 256;                   // [spin] NP columns each
+
+  auto fail = [&](int code) {
+    if (!abort_flag) {
+      abort_flag = 1;
+      atomicCAS(args.err, 0, code);
+    }
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0, ws = 0;
+      uint32_t phase = 0, wph = 0, aph = 0;
+      uint32_t armed = 0, armed_par = 0, armed_w = 0, armed_w_par = 0;
+      int armed_a = -1;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        const int a = item.x, b = it / args.n_base, m0 = item.y, ntiles = item.z;
+        const Rate2 A = P.rates2[a];
+        const int lm8 = A.lam_min & ~7;
+        const int nkb = (((P.n1 - lm8 + 15) >> 4) + 1) >> 1;
+        if (RES) {
+          if (!mbar_wait(&a_free, aph ^ 1, wait_budget)) { fail(30); ok = false; break; }
+          mbar_arrive_expect_tx(&a_full, planes * 2 * nkb * kAPlane);
+          armed_a = (int)aph;
+          for (int pl = 0; pl < planes; ++pl)
+            for (int part = 0; part < 2; ++part)
+              for (int kb = 0; kb < nkb; ++kb)
+                tma_load_2d(sA + ((pl * 2 + part) * max_kb + kb) * kAPlane,
+                            &maps.w[pl * 2 + part], lm8 + kb * kBK, m0, &a_full);
+          aph ^= 1;
+        }
+        for (int j = 0; j < ntiles && ok; ++j) {
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!mbar_wait(&empty_bar[stage], phase ^ 1, wait_budget)) { fail(31); ok = false; break; }
+            uint8_t* st = sStage + stage * stage_bytes;
+            mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
+            armed |= 1u << stage;
+            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+            uint8_t* sb = RES ? st : st + planes * 2 * kAPlane;
+            for (int pl = 0; pl < planes; ++pl) {
+              for (int part = 0; part < 2; ++part) {
+                if (!RES)
+                  tma_load_2d(st + (pl * 2 + part) * kAPlane, &maps.w[pl * 2 + part],
+                              lm8 + kb * kBK, m0, &full_bar[stage]);
+                tma_load_3d(sb + (pl * 2 + part) * kYAtom, &maps.y[pl][a], j * BN,
+                            lm8 + kb * kBK - A.lam_min, 2 * b + part, &full_bar[stage]);
+              }
+            }
+            if (++stage == S) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          if (!mbar_wait(&wempty[ws], wph ^ 1, wait_budget)) { fail(32); ok = false; break; }
+          mbar_arrive_expect_tx(&wfull[ws], PS * kWHalf);
+          armed_w |= 1u << ws;
+          armed_w_par = (armed_w_par & ~(1u << ws)) | (wph << ws);
+          for (int pl = 0; pl < PS; ++pl)
+            tma_load_2d(sWt + (ws * PS + pl) * kWHalf, &maps.wt[pl], j * BN, a * NT, &wfull[ws]);
+          if (++ws == WS) { ws = 0; wph ^= 1; }
+        }
+      }
+      for (int s2 = 0; s2 < S; ++s2)
+        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, wait_budget);
+      for (int s2 = 0; s2 < WS; ++s2)
+        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, wait_budget);
+      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, wait_budget);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ product issuer
+    if (lane == 0) {
+      const uint32_t id = instr_desc(kBM, 128, 1, 1, 0, 1, 0);
+      const int npair = args.passes == 3 ? 3 : 1;
+      int stage = 0;
+      uint32_t phase = 0, tph = 0, aph = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        const Rate2 A = P.rates2[item.x];
+        const int lm8 = A.lam_min & ~7;
+        const int nks = (P.n1 - lm8 + 15) / 16;
+        const int nkb = (nks + 1) / 2;
+        if (RES) {
+          if (!mbar_wait(&a_full, aph, wait_budget)) { fail(33); ok = false; break; }
+          aph ^= 1;
+        }
+        for (int j = 0; j < item.z && ok; ++j) {
+          if (!mbar_wait(&tempty, tph ^ 1, wait_budget)) { fail(34); ok = false; break; }
+          tph ^= 1;
+          tc_fence_after();
+          const uint32_t t_a = tbase, t_b = tbase + 128;
+          for (int kb = 0; kb < nkb; ++kb) {
+            if (!mbar_wait(&full_bar[stage], phase, wait_budget)) { fail(35); ok = false; break; }
+            tc_fence_after();
+            const uint32_t st = smem_u32(sStage + stage * stage_bytes);
+            const uint32_t sb = RES ? st : st + planes * 2 * kAPlane;
+            const uint32_t sa = RES ? smem_u32(sA) + kb * kAPlane : st;
+            const uint32_t a_stride = RES ? max_kb * kAPlane : kAPlane;
+            const int kss = min(2, nks - 2 * kb);
+            const uint64_t dA = smem_desc(sa, 16, 512, kSw64);
+            const uint64_t dB = smem_desc(sb, kYAtom, 1024, kSw128);
+            const uint32_t as4 = a_stride >> 4;
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              if (ks < kss) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                  if (q < npair) {
+                    const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                    const uint64_t ar = dA + (uint64_t)(pa * 2 * as4 + ks * 2);
+                    const uint64_t ai = ar + as4;
+                    const uint64_t bd = dB + (uint64_t)(pb * 2 * (kYAtom >> 4) + ks * 128);
+                    const uint32_t f = (kb | ks | q) ? 1u : 0u;
+                    mma_f16(t_a, ar, bd, id, f);    // [P1 | P3] = Wr [Yr | Yi]
+                    mma_f16(t_b, ai, bd, id, f);    // [P4 | P2] = Wi [Yr | Yi]
+                  }
+                }
+              }
+            }
+            mma_commit(&empty_bar[stage]);
+            if (++stage == S) { stage = 0; phase ^= 1; }
+          }
+          if (!ok) break;
+          mma_commit(&tfull);
+        }
+        if (!ok) break;
+        if (RES) mma_commit(&a_free);
+      }
+      mma_commit(&mma_done);
+      mbar_wait(&mma_done, 0, wait_budget);
+    }
+  } else if (warp == kTpWarpPool) {
+    // ------------------------------------------------------------ pooling issuer
+    if (lane == 0) {
+      // A = |Z| [128 rows][64 samples] K-major, B = [W_hi ; W_lo] [NP frames][64 samples]
+      // K-major, both 128-byte rows; a K step is 16 samples (32 bytes)
+      const uint32_t idp = instr_desc(kBM, NP, 1, 1, 0, 0, 0);
+      int ws = 0;
+      uint32_t sph = 0, wph = 0, dph = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
+        const int4 item = args.items[it % args.n_base];
+        // the epilogue has read the previous item's accumulators
+        if (!mbar_wait(&dfree, dph ^ 1, wait_budget)) { fail(36); ok = false; break; }
+        dph ^= 1;
+        for (int j = 0; j < item.z && ok; ++j) {
+          if (!mbar_wait(&sfull, sph, wait_budget)) { fail(37); ok = false; break; }
+          sph ^= 1;
+          if (!mbar_wait(&wfull[ws], wph, wait_budget)) { fail(38); ok = false; break; }
+          tc_fence_after();
+          const uint64_t dW = smem_desc(smem_u32(sWt + ws * PS * kWHalf), 16, 1024, kSw128);
+          const uint64_t dZ = smem_desc(smem_u32(sZ), 16, 1024, kSw128);
+#pragma unroll
+          for (int d = 0; d < 2; ++d)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+              for (int pa = 0; pa < PS; ++pa) {
+                const uint64_t az = dZ + (uint64_t)(((d * PS + pa) * kZPlane + k * 32) >> 4);
+                const uint64_t bw = dW + (uint64_t)((k * 32) >> 4);
+                mma_f16(t_pool + d * NP, az, bw, idp, (j | k | pa) ? 1u : 0u);
+              }
+          mma_commit(&sfree);
+          mma_commit(&wempty[ws]);
+          if (++ws == WS) { ws = 0; wph ^= 1; }
+        }
+        if (!ok) break;
+        mma_commit(&dfull);
+      }
+      mma_commit(&pool_done);
+      mbar_wait(&pool_done, 0, wait_budget);
+    }
+  } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + kEpiWarps) {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - kEpiWarp0;          // 0..15
+    const int quarter = warp & 3;
+    const int cg = ew >> 2;                   // samples [16 cg, 16 cg + 16) of the tile
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const int row = quarter * 32 + lane;      // row of the 128-row block (TMEM lane)
+    // this row's 16-byte chunks 2 cg + h of each |Z| plane (128-byte swizzle)
+    uint8_t* zrow = sZ + row * 128;
+    const int zc0 = ((2 * cg) ^ (row & 7)) * 16, zc1 = ((2 * cg + 1) ^ (row & 7)) * 16;
+    uint32_t tph = 0, sph = 0, dph = 0;
+    for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
+      const int4 item = args.items[it % args.n_base];
+      const int a = item.x, b = it / args.n_base, m0 = item.y;
+      bool ok = !abort_flag;
+      for (int j = 0; j < item.z && ok; ++j) {
+        if (!mbar_wait(&tfull, tph, wait_budget)) { fail(39); ok = false; break; }
+        tph ^= 1;
+        tc_fence_after();
+        const uint32_t t_col = tbase + lane_off + cg * 16;
+        uint32_t hv[2][2][4], lv[2][2][4];     // [h8][spin][4 bf16x2]
+#pragma unroll
+        for (int h8 = 0; h8 < 2; ++h8) {
+          uint32_t p1[8], p3[8], p4[8], p2[8];
+          tmem_ld8u(t_col + h8 * 8, p1);
+          tmem_ld8u(t_col + h8 * 8 + 64, p3);
+          tmem_ld8u(t_col + h8 * 8 + 128, p4);
+          tmem_ld8u(t_col + h8 * 8 + 192, p2);
+          tmem_wait_ld();
+          if (h8 == 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            float mu[2], md[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const int k2 = 2 * i + e;
+              const float x1 = __uint_as_float(p1[k2]), x2 = __uint_as_float(p2[k2]);
+              const float x3 = __uint_as_float(p3[k2]), x4 = __uint_as_float(p4[k2]);
+              const float ru = x1 - x2, iu = x3 + x4, rd = x1 + x2, id = x3 - x4;
+              mu[e] = sqrt_approx(fmaf(ru, ru, iu * iu));
+              md[e] = sqrt_approx(fmaf(rd, rd, id * id));
+            }
+            __nv_bfloat162 hu = __floats2bfloat162_rn(mu[0], mu[1]);
+            __nv_bfloat162 hd = __floats2bfloat162_rn(md[0], md[1]);
+            hv[h8][0][i] = *reinterpret_cast<uint32_t*>(&hu);
+            hv[h8][1][i] = *reinterpret_cast<uint32_t*>(&hd);
+            if (PS == 2) {
+              const float2 fu = __bfloat1622float2(hu), fd = __bfloat1622float2(hd);
+              __nv_bfloat162 lu = __floats2bfloat162_rn(mu[0] - fu.x, mu[1] - fu.y);
+              __nv_bfloat162 ld = __floats2bfloat162_rn(md[0] - fd.x, md[1] - fd.y);
+              lv[h8][0][i] = *reinterpret_cast<uint32_t*>(&lu);
+              lv[h8][1][i] = *reinterpret_cast<uint32_t*>(&ld);
+            }
+          }
+        }
+        // the pooling MMAs of the previous tile have read the staged |Z|
+        if (!mbar_wait(&sfree, sph ^ 1, wait_budget)) { fail(40); ok = false; break; }
+        sph ^= 1;
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          uint8_t* zp = zrow + d * PS * kZPlane;
+          *reinterpret_cast<uint4*>(zp + zc0) = make_uint4(hv[0][d][0], hv[0][d][1], hv[0][d][2], hv[0][d][3]);
+          *reinterpret_cast<uint4*>(zp + zc1) = make_uint4(hv[1][d][0], hv[1][d][1], hv[1][d][2], hv[1][d][3]);
+          if (PS == 2) {
+            *reinterpret_cast<uint4*>(zp + kZPlane + zc0) = make_uint4(lv[0][d][0], lv[0][d][1], lv[0][d][2], lv[0][d][3]);
+            *reinterpret_cast<uint4*>(zp + kZPlane + zc1) = make_uint4(lv[1][d][0], lv[1][d][1], lv[1][d][2], lv[1][d][3]);
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sfull);
+      }
+      if (!ok) break;
+      // the item's pooled rows: spin d = cg >> 1, frames [NT / 2 (cg & 1), +NT / 2)
+      if (!mbar_wait(&dfull, dph, wait_budget)) { fail(41); break; }
+      dph ^= 1;
+      tc_fence_after();
+      constexpr int HF = NT / 2;
+      const int d = cg >> 1, f0 = HF * (cg & 1);
+      float v[HF];
+      {
+        const uint32_t tp = t_pool + lane_off + d * NP + f0;
+        if constexpr (HF == 8) {
+          uint32_t hi[8];
+          tmem_ld8u(tp, hi);
+          if (PS == 2) {
+            uint32_t lo[8];
+            tmem_ld8u(tp + NT, lo);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(hi[i]) + __uint_as_float(lo[i]);
+          } else {
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(hi[i]);
+          }
+        } else {
+          float hi[16];
+          tmem_ld16(tp, hi);
+          if (PS == 2) {
+            float lo[16];
+            tmem_ld16(tp + NT, lo);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = hi[i] + lo[i];
+          } else {
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = hi[i];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&dfree);
+      // pair row r: channel p (up) or p + n_fr (down); the phi_F rows (p = n_fr) have no down
+      // channel, the zero rows before them no output
+      const int r = m0 + row;
+      const bool spin = r < P.n_fr * P.n1;
+      const int p = spin ? r / P.n1 : P.n_fr;
+      const int lam = spin ? r - p * P.n1 : r - args.pr_phi0;
+      if (r < args.n_rows && (spin || r >= args.pr_phi0) && (d == 0 || spin)) {
+        const int crow = (d == 0 ? (p < P.n_fr ? p : 2 * P.n_fr) : p + P.n_fr) * P.n1 + lam;
+        float* out = args.P + ((size_t)b * args.n2 + a) * (size_t)P.C * P.n1 * args.nt +
+                     (size_t)crow * args.nt;
+        if (args.nt == NT) {
+#pragma unroll
+          for (int i = 0; i < HF; i += 4)
+            *reinterpret_cast<float4*>(out + f0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < HF; ++i)
+            if (f0 + i < args.nt) out[f0 + i] = v[i];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, 512);
+  }
+}
+
 // phi_F pooling along lambda of the time-pooled rows: S2[b, a, c, lo, t].
 // The rows of a (c, alpha, b) block are split over the block's warps (kPoolSplit row ranges);
 // the partial sums meet in shared memory and are added in a fixed order.
@@ -1557,6 +1948,40 @@ size_t tc16_smem_for(const jtfs_plan* p, bool res) {
   const Tc16Shape s = tc16_shape(p);
   return s.fixed(res, tc_res_kb(p)) + (size_t)tc16_stages_for(p, res) * s.stage(res);
 }
+
+// Tensor-pooling form (k_joint_fwd_tp): resident W tile, operand stages, the weight ring
+// (kMaxWS slots of ppl planes of NT x 64 BF16) and the staged |Z| (2 spins x ppl planes of
+// 128 x 64 BF16).
+struct TpShape {
+  int cpl, ppl, nt, res_kb;
+  size_t fixed(bool res) const {
+    return 1024 + (res ? (size_t)cpl * 2 * res_kb * kBM * kBK * 2 : 0) +
+           (size_t)kMaxWS * ppl * nt * 64 * 2 + (size_t)2 * ppl * 128 * 64 * 2;
+  }
+  size_t stage(bool res) const {
+    return (res ? 0 : (size_t)cpl * 2 * kBM * kBK * 2) + (size_t)cpl * 2 * 4096;
+  }
+};
+
+TpShape tp_shape(const jtfs_plan* p) {
+  TpShape s;
+  s.cpl = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
+  s.ppl = p->split ? 2 : 1;
+  s.nt = tc_nt(p->n_t);
+  s.res_kb = tc_res_kb(p);
+  return s;
+}
+
+int tp_stages_for(const jtfs_plan* p, bool res) {
+  const TpShape s = tp_shape(p);
+  if (s.fixed(res) + 2 * s.stage(res) > kSmemBudget) return 0;
+  return (int)std::min<size_t>(8, (kSmemBudget - s.fixed(res)) / s.stage(res));
+}
+
+size_t tp_smem_for(const jtfs_plan* p, bool res) {
+  const TpShape s = tp_shape(p);
+  return s.fixed(res) + (size_t)tp_stages_for(p, res) * s.stage(res);
+}
 }  // namespace
 
 jtfs_status build_tc_tables(jtfs_plan* p) {
@@ -1707,8 +2132,12 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   }
   const int n_all = (int)(p->tc_items.size() / 4);
   const bool f16 = NT == 16 || p->tc_pair;   // the 16-frame and spin-pair layouts
-  const int n_res = (f16 ? tc16_stages_for(p, true) : tc_stages_for(p, true)) >= 2 ? p->tc_n_res : 0;
-  if (n_all > n_res && (f16 ? tc16_stages_for(p, false) : tc_stages_for(p, false)) < 2) {
+  const bool tp = p->tc_pair && p->tc_tp;    // pooling on the tensor cores
+  auto stages_for = [&](bool res) {
+    return tp ? tp_stages_for(p, res) : (f16 ? tc16_stages_for(p, res) : tc_stages_for(p, res));
+  };
+  const int n_res = stages_for(true) >= 2 ? p->tc_n_res : 0;
+  if (n_all > n_res && stages_for(false) < 2) {
     set_error("tensor-core forward: no shared-memory layout for this configuration");
     return JTFS_ERR_UNSUPPORTED;
   }
@@ -1753,9 +2182,22 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     k_joint_fwd_pair<RESV, PSV, NTV><<<grid, kThreads, smem, st>>>(maps, args, d);              \
     ++p->prof.launches;                                                                         \
   } while (0)
+#define JTFS_LAUNCH_TP1(RESV, PSV, NTV)                                                         \
+  do {                                                                                          \
+    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_tp<RESV, PSV, NTV>,                   \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                                              (int)smem), "attr tp")) != JTFS_OK)               \
+      return rc;                                                                                \
+    k_joint_fwd_tp<RESV, PSV, NTV><<<grid, kTpThreads, smem, st>>>(maps, args, d);              \
+    ++p->prof.launches;                                                                         \
+  } while (0)
 #define JTFS_LAUNCH_PAIR(RESV, PSV)                                                             \
   do {                                                                                          \
-    if (NT == 16) JTFS_LAUNCH_PAIR1(RESV, PSV, 16); else JTFS_LAUNCH_PAIR1(RESV, PSV, 32);      \
+    if (tp) {                                                                                   \
+      if (NT == 16) JTFS_LAUNCH_TP1(RESV, PSV, 16); else JTFS_LAUNCH_TP1(RESV, PSV, 32);        \
+    } else {                                                                                    \
+      if (NT == 16) JTFS_LAUNCH_PAIR1(RESV, PSV, 16); else JTFS_LAUNCH_PAIR1(RESV, PSV, 32);    \
+    }                                                                                           \
   } while (0)
   for (int pass = 0; pass < 2; ++pass) {
     const bool res = pass == 0;
@@ -1764,8 +2206,8 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     args.items = reinterpret_cast<const int4*>(p->d_tc_items) + first;
     args.n_base = count;
     args.n_items = count * B;
-    args.stages = f16 ? tc16_stages_for(p, res) : tc_stages_for(p, res);
-    const size_t smem = f16 ? tc16_smem_for(p, res) : tc_smem_for(p, res);
+    args.stages = stages_for(res);
+    const size_t smem = tp ? tp_smem_for(p, res) : (f16 ? tc16_smem_for(p, res) : tc_smem_for(p, res));
     const int grid = std::min(args.n_items, n_sm);
     if (p->tc_pair) {
       if (args.pool_split) {
@@ -1787,6 +2229,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
 #undef JTFS_LAUNCH_TC16
 #undef JTFS_LAUNCH_PAIR
 #undef JTFS_LAUNCH_PAIR1
+#undef JTFS_LAUNCH_TP1
   k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
   ++p->prof.launches;
   return cuda_check(cudaGetLastError(), "k_pool_lambda");
