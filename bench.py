@@ -37,11 +37,11 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
                   "sm_max_mhz": 2070.0}
 SMS = 152
 # DRAM bytes (read + write) per step of the contraction stages (forward and backward kernels
-# with their phi_F pooling / adjoint) at B = 64, from the ncu capture summarised in
-# profiles/dram_traffic_B16_N65536_fp32.md: 711.7 MB at B = 16, scaled by the signals (the
+# with their phi_F pooling / adjoint) at B = 64, from an ncu capture of dram__bytes_read.sum +
+# dram__bytes_write.sum of the current kernels: 710.8 MB at B = 16, scaled by the signals (the
 # kernels' traffic is proportional to them); None where no capture of the current kernels
 # exists.
-CONTRACTION_TRAFFIC = {"fp32": 4 * 711.7e6}
+CONTRACTION_TRAFFIC = {"fp32": 4 * 710.8e6}
 
 
 def _peaks():

@@ -121,7 +121,6 @@ struct jtfs_plan {
   int n1_pad;                  // lambda' columns of the W planes (multiple of 32)
   void* d_wplanes[6];          // Wr_hi, Wi_hi, Wr_lo, Wi_lo, -Wi_hi, -Wi_lo: [C * n1][n1_pad] bf16
   bool tc_pair = false;        // forward in the spin-pair form (16 or 32 frames, BF16 planes)
-  bool tc_tp = true;           // spin-pair forward with the phi_T pooling on tcgen05
   int pr_phi0 = 0;             // first phi_F pair row: n_fr n1 rounded up to 32 (zero rows
                                // between), so 32-row chunks never mix spin and phi_F rows
   int n_pr = 0;                // pair rows pr_phi0 + n1

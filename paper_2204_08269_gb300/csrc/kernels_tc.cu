@@ -829,502 +829,11 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
 // forms both channels.  That halves the contraction's MMAs against the channel-row form.
 // Rows are pair rows r = p n1 + lambda for the spin pairs p < n_fr, then zero rows up to the
 // next multiple of 32, then the n1 rows of the phi_F branch (real W, only its "up" output is
-// written).  Sixteen epilogue warps: lane quarter = warp & 3, column group cg = ew >> 2 forms
-// |Z| of both channels over samples [16 cg, +16) of the tile and stages it.  16 frames: each
-// warp pools its own samples over all frames with mma.sync, and at an item's end the four
-// column groups' partials are summed.  32 frames (the partials of all frames would not fit the
-// registers): the quarter's four warps exchange their staged |Z| blocks, and warp cg pools
-// channel cg >> 1 over frames [16 (cg & 1), +16) and all 64 samples, so that it owns its
-// outputs and writes them at an item's end.
-template <bool RES, int PS, int NT>
-__global__ void __launch_bounds__(kThreads, 1)
-k_joint_fwd_pair(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
-  static_assert(NT == 16 || NT == 32, "pooled frames");
-  const uint64_t wait_budget = args.wait_ns;
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  constexpr int BN = 64;
-  constexpr int CD = NT == 16 ? 2 : 1;                   // channels a warp accumulates
-  const int planes = args.passes == 3 ? 2 : 1;
-  constexpr int pplanes = PS;
-  const int S = args.stages, WS = args.wstages;
-  constexpr uint32_t kAPlane = kBM * kBK * 2;            // 8 KB: 128 rows x 32 lambda', SW64
-  constexpr uint32_t kYAtom = 4096;                      // 32 lambda' x 64 samples, SW128
-  constexpr uint32_t kWHalf = NT * 64 * 2;               // NT frames x 64 samples
-  constexpr uint32_t kStg = 32 * 16 * 2;                 // 1 KB: a warp's 32 x 16 |Z| block
-  // a warp's staging: its |Z| blocks per channel and plane, at an item's end its 32 x NT partials
-  constexpr uint32_t kStgWarp = 2 * PS * kStg > NT * 32 * 4 ? 2 * PS * kStg : NT * 32 * 4;
-  const int max_kb = args.res_kb;
-  const uint32_t y_bytes = planes * 2 * kYAtom;          // per plane [Yr atom | Yi atom]
-  const uint32_t stage_bytes = RES ? y_bytes : planes * 2 * kAPlane + y_bytes;
-  uint8_t* sA = sm;
-  uint8_t* sStage = sm + (RES ? planes * 2 * max_kb * kAPlane : 0);
-  uint8_t* sWt = sStage + S * stage_bytes;               // WS x pplanes (hi, lo adjacent)
-  uint8_t* sStg = sWt + WS * pplanes * kWHalf;           // 16 warps x kStgWarp
-  __shared__ uint64_t full_bar[8], empty_bar[8], wfull[kMaxWS], wempty[kMaxWS], tfull[2],
-      tempty[2], red_full[4], red_free[4], sfull[4], sfree[4], a_full, a_free, mma_done;
-  __shared__ uint32_t tmem_base;
-  __shared__ volatile int abort_flag;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  if (threadIdx.x == 0) {
-    abort_flag = 0;
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
-    }
-    for (int s = 0; s < WS; ++s) {
-      mbar_init(&wfull[s], 1);
-      mbar_init(&wempty[s], kEpiWarps);
-    }
-    for (int a = 0; a < 2; ++a) {
-      mbar_init(&tfull[a], 1);
-      mbar_init(&tempty[a], kEpiWarps);
-    }
-    for (int q = 0; q < 4; ++q) {
-      mbar_init(&red_full[q], 4);
-      mbar_init(&red_free[q], 1);
-      mbar_init(&sfull[q], 4);
-      mbar_init(&sfree[q], 4);
-    }
-    mbar_init(&a_full, 1);
-    mbar_init(&a_free, 1);
-    mbar_init(&mma_done, 1);
-    fence_barrier_init();
-  }
-  if (warp == 1) {
-    tmem_alloc(&tmem_base, 512);
-    tmem_relinquish();
-  }
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tbase = tmem_base;
-
-  auto fail = [&](int code) {
-    if (!abort_flag) {
-      abort_flag = 1;
-      atomicCAS(args.err, 0, code);
-    }
-  };
-
-  if (warp == 0) {
-    // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      int stage = 0, ws = 0;
-      uint32_t phase = 0, wph = 0, aph = 0;
-      uint32_t armed = 0, armed_par = 0, armed_w = 0, armed_w_par = 0;
-      int armed_a = -1;
-      bool ok = true;
-      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
-        const int4 item = args.items[it % args.n_base];
-        const int a = item.x, b = it / args.n_base, m0 = item.y, ntiles = item.z;
-        const Rate2 A = P.rates2[a];
-        const int lm8 = A.lam_min & ~7;
-        const int nkb = (((P.n1 - lm8 + 15) >> 4) + 1) >> 1;
-        if (RES) {
-          if (!mbar_wait(&a_free, aph ^ 1, wait_budget)) { fail(10); ok = false; break; }
-          mbar_arrive_expect_tx(&a_full, planes * 2 * nkb * kAPlane);
-          armed_a = (int)aph;
-          for (int pl = 0; pl < planes; ++pl)
-            for (int part = 0; part < 2; ++part)
-              for (int kb = 0; kb < nkb; ++kb)
-                tma_load_2d(sA + ((pl * 2 + part) * max_kb + kb) * kAPlane,
-                            &maps.w[pl * 2 + part], lm8 + kb * kBK, m0, &a_full);
-          aph ^= 1;
-        }
-        for (int j = 0; j < ntiles && ok; ++j) {
-          for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&empty_bar[stage], phase ^ 1, wait_budget)) { fail(11); ok = false; break; }
-            uint8_t* st = sStage + stage * stage_bytes;
-            mbar_arrive_expect_tx(&full_bar[stage], stage_bytes);
-            armed |= 1u << stage;
-            armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
-            uint8_t* sb = RES ? st : st + planes * 2 * kAPlane;
-            for (int pl = 0; pl < planes; ++pl) {
-              for (int part = 0; part < 2; ++part) {
-                if (!RES)
-                  tma_load_2d(st + (pl * 2 + part) * kAPlane, &maps.w[pl * 2 + part],
-                              lm8 + kb * kBK, m0, &full_bar[stage]);
-                tma_load_3d(sb + (pl * 2 + part) * kYAtom, &maps.y[pl][a], j * BN,
-                            lm8 + kb * kBK - A.lam_min, 2 * b + part, &full_bar[stage]);
-              }
-            }
-            if (++stage == S) { stage = 0; phase ^= 1; }
-          }
-          if (!ok) break;
-          if (!mbar_wait(&wempty[ws], wph ^ 1, wait_budget)) { fail(15); ok = false; break; }
-          mbar_arrive_expect_tx(&wfull[ws], pplanes * kWHalf);
-          armed_w |= 1u << ws;
-          armed_w_par = (armed_w_par & ~(1u << ws)) | (wph << ws);
-          for (int pl = 0; pl < pplanes; ++pl)
-            tma_load_2d(sWt + (ws * pplanes + pl) * kWHalf, &maps.wt[pl], j * BN, a * NT,
-                        &wfull[ws]);
-          if (++ws == WS) { ws = 0; wph ^= 1; }
-        }
-      }
-      for (int s2 = 0; s2 < S; ++s2)
-        if (armed >> s2 & 1) mbar_wait(&full_bar[s2], armed_par >> s2 & 1, wait_budget);
-      for (int s2 = 0; s2 < WS; ++s2)
-        if (armed_w >> s2 & 1) mbar_wait(&wfull[s2], armed_w_par >> s2 & 1, wait_budget);
-      if (armed_a >= 0) mbar_wait(&a_full, (uint32_t)armed_a, wait_budget);
-    }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      const uint32_t id = instr_desc(kBM, 128, 1, 1, 0, 1, 0);
-      const int npair = args.passes == 3 ? 3 : 1;
-      int stage = 0, acc = 0;
-      uint32_t phase = 0, acc_ph = 0, aph = 0;
-      bool ok = true;
-      for (int it = blockIdx.x; it < args.n_items && ok && !abort_flag; it += gridDim.x) {
-        const int4 item = args.items[it % args.n_base];
-        const Rate2 A = P.rates2[item.x];
-        const int lm8 = A.lam_min & ~7;
-        const int nks = (P.n1 - lm8 + 15) / 16;
-        const int nkb = (nks + 1) / 2;
-        if (RES) {
-          if (!mbar_wait(&a_full, aph, wait_budget)) { fail(9); ok = false; break; }
-          aph ^= 1;
-        }
-        for (int j = 0; j < item.z && ok; ++j) {
-          if (!mbar_wait(&tempty[acc], acc_ph ^ 1, wait_budget)) { fail(12); ok = false; break; }
-          tc_fence_after();
-          const uint32_t t_a = tbase + acc * 256, t_b = t_a + 128;
-          for (int kb = 0; kb < nkb; ++kb) {
-            if (!mbar_wait(&full_bar[stage], phase, wait_budget)) { fail(13); ok = false; break; }
-            tc_fence_after();
-            const uint32_t st = smem_u32(sStage + stage * stage_bytes);
-            const uint32_t sb = RES ? st : st + planes * 2 * kAPlane;
-            const uint32_t sa = RES ? smem_u32(sA) + kb * kAPlane : st;
-            const uint32_t a_stride = RES ? max_kb * kAPlane : kAPlane;
-            const int kss = min(2, nks - 2 * kb);
-            // A: K-major rows of 32 lambda' (64-byte swizzle); B: [Yr | Yi] MN-major atoms of
-            // 64 samples, K step = 16 rows of 128 bytes.  The descriptors of one stage differ
-            // only in their start address (16-byte units, below 2^14), so they are the stage's
-            // two base descriptors plus fixed offsets.
-            const uint64_t dA = smem_desc(sa, 16, 512, kSw64);
-            const uint64_t dB = smem_desc(sb, kYAtom, 1024, kSw128);
-            const uint32_t as4 = a_stride >> 4;
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-              if (ks < kss) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                  if (q < npair) {
-                    const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-                    const uint64_t ar = dA + (uint64_t)(pa * 2 * as4 + ks * 2);
-                    const uint64_t ai = ar + as4;
-                    const uint64_t bd = dB + (uint64_t)(pb * 2 * (kYAtom >> 4) + ks * 128);
-                    const uint32_t f = (kb | ks | q) ? 1u : 0u;
-                    mma_f16(t_a, ar, bd, id, f);    // [P1 | P3] = Wr [Yr | Yi]
-                    mma_f16(t_b, ai, bd, id, f);    // [P4 | P2] = Wi [Yr | Yi]
-                  }
-                }
-              }
-            }
-            mma_commit(&empty_bar[stage]);
-            if (++stage == S) { stage = 0; phase ^= 1; }
-          }
-          if (!ok) break;
-          mma_commit(&tfull[acc]);
-          if (++acc == 2) { acc = 0; acc_ph ^= 1; }
-        }
-        if (!ok) break;
-        if (RES) mma_commit(&a_free);
-      }
-      mma_commit(&mma_done);
-      mbar_wait(&mma_done, 0, wait_budget);
-    }
-  } else {
-    // ------------------------------------------------------------ epilogue + pooling
-    const int ew = warp - kEpiWarp0;          // 0..15
-    const int quarter = warp & 3;
-    const int cg = ew >> 2;                   // samples [16 cg, 16 cg + 16) of the tile
-    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    const int g = lane >> 2, t4 = lane & 3;
-    uint8_t* stg = sStg + ew * kStgWarp;                   // [channel][plane] blocks
-    const uint32_t stg_u = smem_u32(stg);
-    uint8_t* my_row = stg + lane * 32;
-    const int my_sw = (lane >> 2) & 1;
-    uint32_t a_addr[2];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const int r = 16 * mt + (lane & 15);
-      a_addr[mt] = stg_u + r * 32 + (((lane >> 4) ^ ((r >> 2) & 1)) << 4);
-    }
-    const int bt = 8 * (lane >> 4) + (lane & 7);
-    const int bk = (lane >> 3) & 1;
-    const uint32_t b_off = bt * 128 + ((((cg * 16) >> 3) + bk) ^ (bt & 7)) * 16;
-    // 32 frames: this warp's channel and frame half; the quarter's staging blocks of column
-    // groups 0..3 are kQStride apart from the first
-    const int dch = cg >> 1, fh = cg & 1;
-    constexpr uint32_t kQStride = 4 * kStgWarp;
-    const uint32_t q_stg = smem_u32(sStg) + ((quarter + 2) & 3) * kStgWarp + dch * pplanes * kStg;
-    int acc = 0, ws = 0;
-    // every wait on red_free follows a completed round of column group 0 (no free first
-    // phase): the first wait is for parity 0
-    uint32_t acc_ph = 0, wph = 0, rf_ph = 0, rfree_ph = 1, sf_ph = 0, sr_ph = 0;
-    bool red_pending = false;
-    for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
-      const int4 item = args.items[it % args.n_base];
-      const int a = item.x, b = it / args.n_base, m0 = item.y;
-      bool ok = !abort_flag;
-      float c[CD][2][2][4];                    // [channel up / down][mt][nt][4]
-#pragma unroll
-      for (int d = 0; d < CD; ++d)
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int k2 = 0; k2 < 2; ++k2)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) c[d][i][k2][e] = 0.f;
-      if (NT == 16 && cg != 0 && red_pending) {
-        // column group 0 has read this warp's partials of the previous item
-        if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, wait_budget)) { fail(21); break; }
-        rfree_ph ^= 1;
-        red_pending = false;
-      }
-      for (int j = 0; j < item.z && ok; ++j) {
-        if (!mbar_wait(&tfull[acc], acc_ph, wait_budget)) { fail(14); ok = false; break; }
-        tc_fence_after();
-        if (!mbar_wait(&wfull[ws], wph, wait_budget)) { fail(19); ok = false; break; }
-        const uint32_t t_col = tbase + acc * 256 + lane_off + cg * 16;
-        const uint32_t w_u = smem_u32(sWt + ws * pplanes * kWHalf);
-        if (NT == 32) {
-          // the quarter's four warps have read the previous tile's |Z| blocks
-          if (!mbar_wait(&sfree[quarter], sr_ph ^ 1, wait_budget)) { fail(22); ok = false; break; }
-          sr_ph ^= 1;
-        }
-        __syncwarp();   // the previous tile's fragment loads are done
-#pragma unroll
-        for (int h8 = 0; h8 < 2; ++h8) {
-          uint32_t p1[8], p3[8], p4[8], p2[8];
-          tmem_ld8u(t_col + h8 * 8, p1);
-          tmem_ld8u(t_col + h8 * 8 + 64, p3);
-          tmem_ld8u(t_col + h8 * 8 + 128, p4);
-          tmem_ld8u(t_col + h8 * 8 + 192, p2);
-          tmem_wait_ld();
-          if (h8 == 1) {
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[acc]);
-          }
-          uint32_t hv[2][4], lv[2][4];         // [up / down][8 samples as bf16x2]
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            float mu[2], md[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const int k2 = 2 * i + e;
-              const float x1 = __uint_as_float(p1[k2]), x2 = __uint_as_float(p2[k2]);
-              const float x3 = __uint_as_float(p3[k2]), x4 = __uint_as_float(p4[k2]);
-              const float ru = x1 - x2, iu = x3 + x4, rd = x1 + x2, id = x3 - x4;
-              mu[e] = sqrt_approx(fmaf(ru, ru, iu * iu));
-              md[e] = sqrt_approx(fmaf(rd, rd, id * id));
-            }
-            __nv_bfloat162 hu = __floats2bfloat162_rn(mu[0], mu[1]);
-            __nv_bfloat162 hd = __floats2bfloat162_rn(md[0], md[1]);
-            hv[0][i] = *reinterpret_cast<uint32_t*>(&hu);
-            hv[1][i] = *reinterpret_cast<uint32_t*>(&hd);
-            if (PS == 2) {
-              const float2 fu = __bfloat1622float2(hu), fd = __bfloat1622float2(hd);
-              __nv_bfloat162 lu = __floats2bfloat162_rn(mu[0] - fu.x, mu[1] - fu.y);
-              __nv_bfloat162 ld = __floats2bfloat162_rn(md[0] - fd.x, md[1] - fd.y);
-              lv[0][i] = *reinterpret_cast<uint32_t*>(&lu);
-              lv[1][i] = *reinterpret_cast<uint32_t*>(&ld);
-            }
-          }
-          // samples [8 h8, 8 h8 + 8) of this warp's 16 are 16-byte chunk h8 of its row
-          const int pos = (h8 ^ my_sw) * 16;
-#pragma unroll
-          for (int d = 0; d < 2; ++d) {
-            *reinterpret_cast<uint4*>(my_row + d * pplanes * kStg + pos) =
-                make_uint4(hv[d][0], hv[d][1], hv[d][2], hv[d][3]);
-            if (PS == 2)
-              *reinterpret_cast<uint4*>(my_row + (d * pplanes + 1) * kStg + pos) =
-                  make_uint4(lv[d][0], lv[d][1], lv[d][2], lv[d][3]);
-          }
-        }
-        __syncwarp();
-        if constexpr (NT == 16) {
-          // B fragments: w[t][n] for this warp's 16 samples of the 64-sample row
-          uint32_t bh[4], bl[4];
-          ldsm_x4(w_u + b_off, bh);
-          if (PS == 2) ldsm_x4(w_u + kWHalf + b_off, bl);
-#pragma unroll
-          for (int d = 0; d < 2; ++d) {
-            const uint32_t blk = d * pplanes * kStg;
-            uint32_t ah[2][4];
-            ldsm_x4(a_addr[0] + blk, ah[0]);
-            ldsm_x4(a_addr[1] + blk, ah[1]);
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-              hmma16816(c[d][mt][0], ah[mt], bh[0], bh[1]);
-              hmma16816(c[d][mt][1], ah[mt], bh[2], bh[3]);
-            }
-            if (PS == 2) {
-              uint32_t al[2][4];
-              ldsm_x4(a_addr[0] + blk + kStg, al[0]);
-              ldsm_x4(a_addr[1] + blk + kStg, al[1]);
-#pragma unroll
-              for (int mt = 0; mt < 2; ++mt) {
-                hmma16816(c[d][mt][0], ah[mt], bl[0], bl[1]);   // hi . lo
-                hmma16816(c[d][mt][1], ah[mt], bl[2], bl[3]);
-                hmma16816(c[d][mt][0], al[mt], bh[0], bh[1]);   // lo . hi
-                hmma16816(c[d][mt][1], al[mt], bh[2], bh[3]);
-              }
-            }
-          }
-        } else {
-          if (lane == 0) mbar_arrive(&sfull[quarter]);
-          if (!mbar_wait(&sfull[quarter], sf_ph, wait_budget)) { fail(23); ok = false; break; }
-          sf_ph ^= 1;
-          // channel dch, frames [16 fh, +16) (rows 16 fh.. of the 128-byte W rows), samples of
-          // column group q from that warp's staging block
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint32_t bo = fh * 2048 + bt * 128 + (((2 * q) + bk) ^ (bt & 7)) * 16;
-            uint32_t bh[4], bl[4];
-            ldsm_x4(w_u + bo, bh);
-            if (PS == 2) ldsm_x4(w_u + kWHalf + bo, bl);
-            const uint32_t blk = q_stg + q * kQStride - stg_u;
-            uint32_t ah[2][4];
-            ldsm_x4(a_addr[0] + blk, ah[0]);
-            ldsm_x4(a_addr[1] + blk, ah[1]);
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-              hmma16816(c[0][mt][0], ah[mt], bh[0], bh[1]);
-              hmma16816(c[0][mt][1], ah[mt], bh[2], bh[3]);
-            }
-            if (PS == 2) {
-              uint32_t al[2][4];
-              ldsm_x4(a_addr[0] + blk + kStg, al[0]);
-              ldsm_x4(a_addr[1] + blk + kStg, al[1]);
-#pragma unroll
-              for (int mt = 0; mt < 2; ++mt) {
-                hmma16816(c[0][mt][0], ah[mt], bl[0], bl[1]);   // hi . lo
-                hmma16816(c[0][mt][1], ah[mt], bl[2], bl[3]);
-                hmma16816(c[0][mt][0], al[mt], bh[0], bh[1]);   // lo . hi
-                hmma16816(c[0][mt][1], al[mt], bh[2], bh[3]);
-              }
-            }
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sfree[quarter]);
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&wempty[ws]);
-        if (++ws == WS) { ws = 0; wph ^= 1; }
-        if (++acc == 2) { acc = 0; acc_ph ^= 1; }
-      }
-      if (!ok) break;
-      if constexpr (NT == 32) {
-        float* base = args.P + ((size_t)b * args.n2 + a) * (size_t)P.C * P.n1 * args.nt;
-        // rows 16 mt + g + 8 h of the quarter, frames 16 fh + 8 nt + 2 t4 (+1) of channel dch
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int r = m0 + quarter * 32 + 16 * mt + g + 8 * h;
-            const bool spin = r < P.n_fr * P.n1;
-            const int p = spin ? r / P.n1 : P.n_fr;
-            const int lam = spin ? r - p * P.n1 : r - args.pr_phi0;
-            if (!(r < args.n_rows && (spin || r >= args.pr_phi0) && (dch == 0 || spin))) continue;
-            const int row = (dch == 0 ? (p < P.n_fr ? p : 2 * P.n_fr) : p + P.n_fr) * P.n1 + lam;
-            float* out = base + (size_t)row * args.nt;
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-              const int t = 16 * fh + 8 * nt + 2 * t4;
-              const float v0 = c[0][mt][nt][2 * h], v1 = c[0][mt][nt][2 * h + 1];
-              if (args.nt == NT) {
-                *reinterpret_cast<float2*>(out + t) = make_float2(v0, v1);
-              } else {
-                if (t < args.nt) out[t] = v0;
-                if (t + 1 < args.nt) out[t + 1] = v1;
-              }
-            }
-          }
-      } else {
-      // per channel: each warp leaves its 32 x 16 partials in its own staging block and column
-      // group 0 sums the four blocks of its lane quarter in a fixed order
-      const int r = m0 + quarter * 32 + lane;
-      const bool spin = r < P.n_fr * P.n1;
-      const int p = spin ? r / P.n1 : P.n_fr;
-      const int lam = spin ? r - p * P.n1 : r - args.pr_phi0;
-      float* base = args.P + ((size_t)b * args.n2 + a) * (size_t)P.C * P.n1 * args.nt;
-      bool red_ok = true;
-#pragma unroll
-      for (int d = 0; d < 2; ++d) {
-        if (cg != 0 && d == 1) {
-          if (!mbar_wait(&red_free[quarter], rfree_ph ^ 1, wait_budget)) { fail(21); red_ok = false; break; }
-          rfree_ph ^= 1;
-        }
-        __syncwarp();   // the last tile's fragment loads are done
-        float* red = (float*)stg;
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-          for (int nt = 0; nt < 2; ++nt) {
-            const int rr = 16 * mt + g, t = 8 * nt + 2 * t4;
-            *reinterpret_cast<float2*>(red + rr * NT + t) = make_float2(c[d][mt][nt][0], c[d][mt][nt][1]);
-            *reinterpret_cast<float2*>(red + (rr + 8) * NT + t) = make_float2(c[d][mt][nt][2], c[d][mt][nt][3]);
-          }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&red_full[quarter]);
-        if (cg == 0) {
-          if (!mbar_wait(&red_full[quarter], rf_ph, wait_budget)) { fail(20); red_ok = false; break; }
-          rf_ph ^= 1;
-          float sv[NT];
-#pragma unroll
-          for (int t = 0; t < NT; ++t) sv[t] = 0.f;
-#pragma unroll
-          for (int gq = 0; gq < 4; ++gq) {
-            // the warp of column group gq and this lane quarter: ew = 4 gq + ((quarter + 2) & 3)
-            const float* src =
-                (const float*)(sStg + (gq * 4 + ((quarter + 2) & 3)) * kStgWarp) + lane * NT;
-#pragma unroll
-            for (int t = 0; t < NT; t += 4) {
-              const float4 v = *reinterpret_cast<const float4*>(src + t);
-              sv[t] += v.x; sv[t + 1] += v.y; sv[t + 2] += v.z; sv[t + 3] += v.w;
-            }
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&red_free[quarter]);
-          // pair row r: channel p (up) or p + n_fr (down); the phi_F rows (p = n_fr) have no
-          // down channel, the zero rows before them no output
-          const bool write = r < args.n_rows && (spin || r >= args.pr_phi0) && (d == 0 || spin);
-          if (write) {
-            const int row = (d == 0 ? (p < P.n_fr ? p : 2 * P.n_fr) : p + P.n_fr) * P.n1 + lam;
-            float* out = base + (size_t)row * args.nt;
-            if (args.nt == NT) {
-#pragma unroll
-              for (int t = 0; t < NT; t += 4)
-                *reinterpret_cast<float4*>(out + t) = make_float4(sv[t], sv[t + 1], sv[t + 2], sv[t + 3]);
-            } else {
-#pragma unroll
-              for (int t = 0; t < NT; ++t)
-                if (t < args.nt) out[t] = sv[t];
-            }
-          }
-        }
-      }
-      red_pending = true;
-      if (!red_ok) break;
-      }
-    }
-  }
-  __syncthreads();
-  if (warp == 1) {
-    tc_fence_after();
-    tmem_dealloc(tbase, 512);
-  }
-}
-
-// ------------------------------------------------------------------ spin-pair form, tensor pooling
-// The spin-pair forward with the phi_T pooling on the tensor cores instead of mma.sync.  The
-// epilogue stages |Z| (BF16 hi, lo for the FP32-grade split) of both spins in the K-major
-// 128-byte-swizzled layout of an MMA operand, [128 rows][64 samples] per spin and plane, and a
-// second issuing thread accumulates D_spin[row][f] += |Z|[row][n] [W_hi | W_lo][f][n] over the
+// written).
+// The phi_T pooling runs on the tensor cores too (an earlier form pooled with mma.sync in the
+// epilogue, at a quarter of the tcgen05 rate).  The epilogue stages |Z| (BF16 hi, lo for the
+// FP32-grade split) of both spins in the K-major 128-byte-swizzled layout of an MMA operand,
+// [128 rows][64 samples] per spin and plane, and a second issuing thread accumulates D_spin[row][f] += |Z|[row][n] [W_hi | W_lo][f][n] over the
 // item's tiles into TMEM (N = NT per weight plane: frames of W_hi, then of W_lo; both |Z| planes
 // accumulate into the same D, so D[f] + D[NT + f] = (Z_hi + Z_lo)(W_hi + W_lo)).  The TMEM holds
 // one 256-column product accumulator beside the two pooling accumulators, so the product of tile
@@ -2132,7 +1641,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   }
   const int n_all = (int)(p->tc_items.size() / 4);
   const bool f16 = NT == 16 || p->tc_pair;   // the 16-frame and spin-pair layouts
-  const bool tp = p->tc_pair && p->tc_tp;    // pooling on the tensor cores
+  const bool tp = p->tc_pair;                // the spin-pair form pools on the tensor cores
   auto stages_for = [&](bool res) {
     return tp ? tp_stages_for(p, res) : (f16 ? tc16_stages_for(p, res) : tc_stages_for(p, res));
   };
@@ -2173,15 +1682,6 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
       return rc;                                                                                \
     k_joint_fwd_tc16<RESV, TFV><<<grid, kThreads, smem, st>>>(maps, args, d); ++p->prof.launches; \
   } while (0)
-#define JTFS_LAUNCH_PAIR1(RESV, PSV, NTV)                                                       \
-  do {                                                                                          \
-    if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_pair<RESV, PSV, NTV>,                 \
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                                              (int)smem), "attr pair")) != JTFS_OK)             \
-      return rc;                                                                                \
-    k_joint_fwd_pair<RESV, PSV, NTV><<<grid, kThreads, smem, st>>>(maps, args, d);              \
-    ++p->prof.launches;                                                                         \
-  } while (0)
 #define JTFS_LAUNCH_TP1(RESV, PSV, NTV)                                                         \
   do {                                                                                          \
     if ((rc = cuda_check(cudaFuncSetAttribute(k_joint_fwd_tp<RESV, PSV, NTV>,                   \
@@ -2193,11 +1693,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   } while (0)
 #define JTFS_LAUNCH_PAIR(RESV, PSV)                                                             \
   do {                                                                                          \
-    if (tp) {                                                                                   \
-      if (NT == 16) JTFS_LAUNCH_TP1(RESV, PSV, 16); else JTFS_LAUNCH_TP1(RESV, PSV, 32);        \
-    } else {                                                                                    \
-      if (NT == 16) JTFS_LAUNCH_PAIR1(RESV, PSV, 16); else JTFS_LAUNCH_PAIR1(RESV, PSV, 32);    \
-    }                                                                                           \
+    if (NT == 16) JTFS_LAUNCH_TP1(RESV, PSV, 16); else JTFS_LAUNCH_TP1(RESV, PSV, 32);          \
   } while (0)
   for (int pass = 0; pass < 2; ++pass) {
     const bool res = pass == 0;
@@ -2228,7 +1724,6 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
 #undef JTFS_LAUNCH_TC
 #undef JTFS_LAUNCH_TC16
 #undef JTFS_LAUNCH_PAIR
-#undef JTFS_LAUNCH_PAIR1
 #undef JTFS_LAUNCH_TP1
   k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
   ++p->prof.launches;
