@@ -1220,46 +1220,72 @@ k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   }
 }
 
-// phi_F pooling along lambda of the time-pooled rows: S2[b, a, c, lo, t].
-// The rows of a (c, alpha, b) block are split over the block's warps (kPoolSplit row ranges);
-// the partial sums meet in shared memory and are added in a fixed order.
-constexpr int kPoolSplit = 8;
+// phi_F pooling along lambda of the time-pooled rows: S2[b, a, c, lo, t] =
+// sum_lambda phi_F[(lo s_F - lambda) mod N_fr] P[b, a, c, lambda, t] (or P itself for Eq. 4).
+// One block per (alpha, signal) walks the channels: each channel's n1 x n_t rows (contiguous
+// in P) are staged in shared memory, the next channel's already in flight in registers, and
+// every output adds its n1 terms in increasing lambda.
+constexpr int kPoolThreads = 256;
+constexpr int kPoolRowsMax = 8192;   // n1 * n_t floats staged per channel
 
-__global__ void k_pool_lambda(DevPlan Pd, const float* __restrict__ P, float* __restrict__ s2) {
-  __shared__ float part[kPoolSplit][256];
-  const int c = blockIdx.x, a = blockIdx.y, b = blockIdx.z;
-  const int n1 = Pd.n1, nt = Pd.n_t, nfm = Pd.N_fr - 1;
+__global__ void __launch_bounds__(kPoolThreads)
+k_pool_lambda(DevPlan Pd, const float* __restrict__ P, float* __restrict__ s2) {
+  __shared__ float rows[kPoolRowsMax];
+  __shared__ float phi[1024];
+  const int a = blockIdx.x, b = blockIdx.y;
+  const int n1 = Pd.n1, nt = Pd.n_t, nfm = Pd.N_fr - 1, C = Pd.C;
   const Rate2 A = Pd.rates2[a];
-  float* out = s2 + (size_t)b * Pd.s2_stride + ((size_t)a * Pd.C + c) * Pd.n_lo * nt;
-  const float* in = P + (((size_t)b * Pd.n2 + a) * (size_t)(Pd.C * n1) + (size_t)c * n1) * nt;
-  const int nout = Pd.n_lo * nt;
-  if (A.s == 0 || !Pd.average_fr || nout > 256 || blockDim.x != 256) {
-    for (int i = threadIdx.x; i < nout; i += blockDim.x) {
-      if (A.s == 0) { out[i] = 0.f; continue; }
-      if (!Pd.average_fr) { out[i] = in[i]; continue; }
-      const int lo = i / nt, t = i % nt;
-      float s = 0.f;
-      for (int r = 0; r < n1; ++r) s += __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]) * in[r * nt + t];
-      out[i] = s;
+  const int nout = Pd.n_lo * nt, nrow = n1 * nt;
+  float* out0 = s2 + (size_t)b * Pd.s2_stride + (size_t)a * C * Pd.n_lo * nt;
+  const float* in0 = P + ((size_t)b * Pd.n2 + a) * (size_t)(C * n1) * nt;
+  if (A.s == 0 || !Pd.average_fr || nrow > kPoolRowsMax || Pd.N_fr > 1024) {
+    for (int c = 0; c < C; ++c) {
+      float* out = out0 + (size_t)c * nout;
+      const float* in = in0 + (size_t)c * nrow;
+      for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+        if (A.s == 0) { out[i] = 0.f; continue; }
+        if (!Pd.average_fr) { out[i] = in[i]; continue; }
+        const int lo = i / nt, t = i % nt;
+        float v = 0.f;
+        for (int r = 0; r < n1; ++r) v += __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]) * in[r * nt + t];
+        out[i] = v;
+      }
     }
     return;
   }
-  // element e: output i = e mod nout (lo, t) over the rows [q rq, q rq + rq) of q = e / nout
-  const int rq = (n1 + kPoolSplit - 1) / kPoolSplit;
-  for (int e = threadIdx.x; e < kPoolSplit * nout; e += blockDim.x) {
-    const int q = e / nout, i = e - q * nout;
-    const int lo = i / nt, t = i - lo * nt;
-    const int r0 = q * rq, r1 = min(n1, r0 + rq);
-    float s = 0.f;
-    for (int r = r0; r < r1; ++r) s += __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]) * in[r * nt + t];
-    part[q][i] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < nout; i += blockDim.x) {
-    float s = 0.f;
+  for (int i = threadIdx.x; i < Pd.N_fr; i += blockDim.x) phi[i] = __ldg(&Pd.phiF[i]);
+  constexpr int kPer = kPoolRowsMax / kPoolThreads;   // staged floats per thread
+  float nxt[kPer];
 #pragma unroll
-    for (int q = 0; q < kPoolSplit; ++q) s += part[q][i];
-    out[i] = s;
+  for (int q = 0; q < kPer; ++q) {
+    const int i = threadIdx.x + q * kPoolThreads;
+    nxt[q] = i < nrow ? in0[i] : 0.f;
+  }
+  for (int c = 0; c < C; ++c) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int i = threadIdx.x + q * kPoolThreads;
+      if (i < nrow) rows[i] = nxt[q];
+    }
+    __syncthreads();
+    if (c + 1 < C) {
+      const float* in = in0 + (size_t)(c + 1) * nrow;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int i = threadIdx.x + q * kPoolThreads;
+        if (i < nrow) nxt[q] = in[i];
+      }
+    }
+    float* out = out0 + (size_t)c * nout;
+    for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+      const int lo = i / nt, t = i - (i / nt) * nt;
+      const int base = lo * Pd.s_F;
+      float v = 0.f;
+#pragma unroll 4
+      for (int r = 0; r < n1; ++r) v += phi[(base - r) & nfm] * rows[r * nt + t];
+      out[i] = v;
+    }
+    __syncthreads();
   }
 }
 
@@ -1725,7 +1751,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
 #undef JTFS_LAUNCH_TC16
 #undef JTFS_LAUNCH_PAIR
 #undef JTFS_LAUNCH_TP1
-  k_pool_lambda<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, Pbuf, s2);
+  k_pool_lambda<<<dim3(p->n2, B), kPoolThreads, 0, st>>>(d, Pbuf, s2);
   ++p->prof.launches;
   return cuda_check(cudaGetLastError(), "k_pool_lambda");
 }

@@ -1459,28 +1459,50 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
 }
 
 // G1[(b n2 + a) g1_rows + c n1 + lambda][t] = sum_lo phi_F[(lo s_F - lambda) mod N_fr] gS2[b,a,c,lo,t]
-// (or gS2 itself for Eq. 4), as BF16, zero for t >= n_t and in the row padding.
-__global__ void k_g1(DevPlan Pd, const float* __restrict__ gs2, int NT, int g1_rows,
-                     __nv_bfloat16* __restrict__ g1, __nv_bfloat16* __restrict__ g1lo) {
-  const int c = blockIdx.x, a = blockIdx.y, b = blockIdx.z;
-  const int n1 = Pd.n1, nt = Pd.n_t, nfm = Pd.N_fr - 1;
-  const float* g = gs2 + (size_t)b * Pd.s2_stride + ((size_t)a * Pd.C + c) * Pd.n_lo * nt;
-  const size_t o0 = ((size_t)(b * Pd.n2 + a) * g1_rows + (size_t)c * n1) * NT;
-  __nv_bfloat16* out = g1 + o0;
-  for (int i = threadIdx.x; i < n1 * NT; i += blockDim.x) {
-    const int r = i / NT, t = i % NT;
-    float s = 0.f;
-    if (t < nt) {
-      if (Pd.average_fr) {
-        for (int lo = 0; lo < Pd.n_lo; ++lo)
-          s += __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]) * g[lo * nt + t];
-      } else {
-        s = g[r * nt + t];
-      }
+// (or gS2 itself for Eq. 4), as BF16 (hi, and lo when g1lo is given), zero for t >= n_t.  One
+// block per (alpha, signal) walks the channels with phi_F and each channel's n_lo x n_t
+// cotangents in shared memory; every row adds its n_lo terms in increasing lo.
+constexpr int kG1Threads = 256;
+constexpr int kG1InMax = 4096;       // n_lo * n_t floats of one channel
+
+__global__ void __launch_bounds__(kG1Threads)
+k_g1(DevPlan Pd, const float* __restrict__ gs2, int NT, int g1_rows,
+     __nv_bfloat16* __restrict__ g1, __nv_bfloat16* __restrict__ g1lo) {
+  __shared__ float gin[kG1InMax];
+  __shared__ float phi[1024];
+  const int a = blockIdx.x, b = blockIdx.y;
+  const int n1 = Pd.n1, nt = Pd.n_t, nfm = Pd.N_fr - 1, C = Pd.C;
+  const int nin = Pd.average_fr ? Pd.n_lo * nt : n1 * nt;
+  const bool staged = nin <= kG1InMax && Pd.N_fr <= 1024;
+  if (staged)
+    for (int i = threadIdx.x; i < Pd.N_fr; i += blockDim.x) phi[i] = __ldg(&Pd.phiF[i]);
+  for (int c = 0; c < C; ++c) {
+    const float* g = gs2 + (size_t)b * Pd.s2_stride + ((size_t)a * C + c) * Pd.n_lo * nt;
+    const size_t o0 = ((size_t)(b * Pd.n2 + a) * g1_rows + (size_t)c * n1) * NT;
+    if (staged) {
+      __syncthreads();   // the previous channel's reads are done
+      for (int i = threadIdx.x; i < nin; i += blockDim.x) gin[i] = g[i];
+      __syncthreads();
     }
-    const __nv_bfloat16 h = __float2bfloat16_rn(s);
-    out[i] = h;
-    if (g1lo) g1lo[o0 + i] = __float2bfloat16_rn(s - __bfloat162float(h));
+    for (int i = threadIdx.x; i < n1 * NT; i += blockDim.x) {
+      const int r = i / NT, t = i - r * NT;
+      float s = 0.f;
+      if (t < nt) {
+        if (Pd.average_fr) {
+          if (staged) {
+            for (int lo = 0; lo < Pd.n_lo; ++lo) s += phi[(lo * Pd.s_F - r) & nfm] * gin[lo * nt + t];
+          } else {
+            for (int lo = 0; lo < Pd.n_lo; ++lo)
+              s += __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]) * g[lo * nt + t];
+          }
+        } else {
+          s = staged ? gin[r * nt + t] : g[r * nt + t];
+        }
+      }
+      const __nv_bfloat16 h = __float2bfloat16_rn(s);
+      g1[o0 + i] = h;
+      if (g1lo) g1lo[o0 + i] = __float2bfloat16_rn(s - __bfloat162float(h));
+    }
   }
 }
 
@@ -1726,7 +1748,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   __nv_bfloat16* g1lo = (__nv_bfloat16*)((char*)g1buf + g1_plane);
   // G1 (phi_F adjoint of g_S2), zero padded
   if ((rc = cuda_check(cudaMemsetAsync(g1buf, 0, tcb_g1_bytes(p, B), st), "memset g1")) != JTFS_OK) return rc;
-  k_g1<<<dim3(p->C, p->n2, B), 256, 0, st>>>(d, gs2, NT, g1_rows, g1hi, three ? g1lo : nullptr);
+  k_g1<<<dim3(p->n2, B), kG1Threads, 0, st>>>(d, gs2, NT, g1_rows, g1hi, three ? g1lo : nullptr);
   ++p->prof.launches;
   if ((rc = cuda_check(cudaGetLastError(), "k_g1")) != JTFS_OK) return rc;
   std::string err;
