@@ -1108,24 +1108,24 @@ k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           }
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
-            float mu[2], md[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const int k2 = 2 * i + e;
-              const float x1 = __uint_as_float(p1[k2]), x2 = __uint_as_float(p2[k2]);
-              const float x3 = __uint_as_float(p3[k2]), x4 = __uint_as_float(p4[k2]);
-              const float ru = x1 - x2, iu = x3 + x4, rd = x1 + x2, id = x3 - x4;
-              mu[e] = sqrt_approx(fmaf(ru, ru, iu * iu));
-              md[e] = sqrt_approx(fmaf(rd, rd, id * id));
-            }
-            __nv_bfloat162 hu = __floats2bfloat162_rn(mu[0], mu[1]);
-            __nv_bfloat162 hd = __floats2bfloat162_rn(md[0], md[1]);
+            // samples' element pairs (2i, 2i + 1) in packed FP32 operations
+            const float2 x1 = u2f2(p1[2 * i], p1[2 * i + 1]), x2 = u2f2(p2[2 * i], p2[2 * i + 1]);
+            const float2 x3 = u2f2(p3[2 * i], p3[2 * i + 1]), x4 = u2f2(p4[2 * i], p4[2 * i + 1]);
+            const float2 ru = fsub2(x1, x2), iu = __fadd2_rn(x3, x4);
+            const float2 rd = __fadd2_rn(x1, x2), id = fsub2(x3, x4);
+            const float2 su = __ffma2_rn(ru, ru, __fmul2_rn(iu, iu));
+            const float2 sd = __ffma2_rn(rd, rd, __fmul2_rn(id, id));
+            const float2 mu = make_float2(sqrt_approx(su.x), sqrt_approx(su.y));
+            const float2 md = make_float2(sqrt_approx(sd.x), sqrt_approx(sd.y));
+            __nv_bfloat162 hu = __floats2bfloat162_rn(mu.x, mu.y);
+            __nv_bfloat162 hd = __floats2bfloat162_rn(md.x, md.y);
             hv[h8][0][i] = *reinterpret_cast<uint32_t*>(&hu);
             hv[h8][1][i] = *reinterpret_cast<uint32_t*>(&hd);
             if (PS == 2) {
-              const float2 fu = __bfloat1622float2(hu), fd = __bfloat1622float2(hd);
-              __nv_bfloat162 lu = __floats2bfloat162_rn(mu[0] - fu.x, mu[1] - fu.y);
-              __nv_bfloat162 ld = __floats2bfloat162_rn(md[0] - fd.x, md[1] - fd.y);
+              const float2 fu = fsub2(mu, __bfloat1622float2(hu));
+              const float2 fd = fsub2(md, __bfloat1622float2(hd));
+              __nv_bfloat162 lu = __floats2bfloat162_rn(fu.x, fu.y);
+              __nv_bfloat162 ld = __floats2bfloat162_rn(fd.x, fd.y);
               lv[h8][0][i] = *reinterpret_cast<uint32_t*>(&lu);
               lv[h8][1][i] = *reinterpret_cast<uint32_t*>(&ld);
             }
@@ -1439,20 +1439,16 @@ size_t tc_smem_for(const jtfs_plan* p, bool res) {
   return s.fixed(res, tc_res_kb(p)) + (size_t)tc_stages_for(p, res) * s.stage(res);
 }
 
-// 16-frame form: resident W tile, operand stages, the weight ring, sixteen 1 KB |Z| staging
-// blocks per pooling plane and the 32 KB column-group reduction buffer.  apl: bytes of one
-// 128 x 32 W block (8 KB BF16, 16 KB FP32 for TF32); cpl / ppl: contraction / pooling planes;
-// nya: 4 KB Y atoms per part of a column tile (2 BF16, 4 FP32, 1 for the 64-sample tiles of
-// the spin-pair form); nh: 64-sample halves of a pooling-weight tile (1 in the spin-pair form,
-// whose warps stage both channels, 3 - nh staging blocks per pooling plane, and reduce their
-// partials through those blocks instead of the 32 KB buffer).
+// 16-frame form (TF32 operands): resident W tile, operand stages, the weight ring, sixteen
+// 1 KB |Z| staging blocks per pooling plane and the 32 KB column-group reduction buffer.
+// apl: bytes of one 128 x 32 W block (8 KB BF16, 16 KB FP32 for TF32); cpl / ppl:
+// contraction / pooling planes; nya: 4 KB Y atoms per part of a column tile (2 BF16, 4 FP32).
+// A pooling-weight tile has two 64-sample halves.
 struct Tc16Shape {
-  int apl, cpl, ppl, nya, nh, WS, nt;
+  int apl, cpl, ppl, nya, WS, nt;
   size_t fixed(bool res, int res_kb) const {
-    // a spin-pair warp's staging also holds its 32 x nt FP32 partials at an item's end
-    const size_t stg = nh == 1 ? std::max<size_t>(2 * ppl * 1024, (size_t)nt * 32 * 4) : (size_t)ppl * 1024;
-    return 1024 + (res ? (size_t)cpl * 2 * res_kb * apl : 0) + (size_t)WS * nh * ppl * nt * 64 * 2 +
-           (size_t)kEpiWarps * stg + (nh == 2 ? 4 * 128 * 16 * 4 : 0);
+    return 1024 + (res ? (size_t)cpl * 2 * res_kb * apl : 0) + (size_t)WS * 2 * ppl * nt * 64 * 2 +
+           (size_t)kEpiWarps * ppl * 1024 + 4 * 128 * 16 * 4;
   }
   size_t stage(bool res) const {
     return (res ? 0 : (size_t)cpl * 2 * apl) + (size_t)cpl * 2 * nya * 4096;
@@ -1465,8 +1461,7 @@ Tc16Shape tc16_shape(const jtfs_plan* p) {
   s.apl = tf ? kBM * kBK * 4 : kBM * kBK * 2;
   s.cpl = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
   s.ppl = p->split ? 2 : 1;
-  s.nya = p->tc_pair ? 1 : (tf ? 4 : 2);
-  s.nh = p->tc_pair ? 1 : 2;
+  s.nya = tf ? 4 : 2;
   s.WS = kMaxWS;
   s.nt = tc_nt(p->n_t);
   return s;
@@ -1666,8 +1661,8 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
     }
   }
   const int n_all = (int)(p->tc_items.size() / 4);
-  const bool f16 = NT == 16 || p->tc_pair;   // the 16-frame and spin-pair layouts
   const bool tp = p->tc_pair;                // the spin-pair form pools on the tensor cores
+  const bool f16 = NT == 16 && !tp;          // the 16-frame TF32 form
   auto stages_for = [&](bool res) {
     return tp ? tp_stages_for(p, res) : (f16 ? tc16_stages_for(p, res) : tc_stages_for(p, res));
   };
@@ -1681,7 +1676,7 @@ jtfs_status launch_joint_fwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   args.passes = passes;
   args.pool_split = p->split ? 1 : 0;
   args.res_kb = tc_res_kb(p);
-  args.wstages = f16 ? tc16_shape(p).WS : tc_shape(p).WS;
+  args.wstages = tp || f16 ? kMaxWS : tc_shape(p).WS;
   args.n_rows = rows;
   args.pr_phi0 = p->pr_phi0;
   args.nt = p->n_t;

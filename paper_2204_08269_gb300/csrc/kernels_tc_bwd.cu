@@ -1361,30 +1361,36 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&d1_free[buf]);
-        const bool phi = j * RC >= args.pr_phi0;   // no spin-down channel
+        // phi_F rows have no spin-down channel: their g_dn copy is dropped
+        if (j * RC >= args.pr_phi0) {
+#pragma unroll
+          for (int k = 0; k < CW; ++k) gd[k] = 0u;
+        }
         uint32_t sre[CW / 2], sim[CW / 2], tre[CW / 2], tim[CW / 2];
 #pragma unroll
         for (int i = 0; i < CW / 2; ++i) {
-          float vs_re[2], vs_im[2], vt_re[2], vt_im[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int k = 2 * i + e;
-            const float x1 = __uint_as_float(p1[k]), x2 = __uint_as_float(p2[k]);
-            const float x3 = __uint_as_float(p3[k]), x4 = __uint_as_float(p4[k]);
-            const float ru = x1 - x2, iu = x3 + x4, rd = x1 + x2, id = x3 - x4;
-            const float mu = fmaf(ru, ru, iu * iu), md = fmaf(rd, rd, id * id);
-            const float fu = mu > 0.f ? __uint_as_float(gu[k]) * rsqrt_approx(mu) : 0.f;
-            const float fd = (md > 0.f && !phi) ? __uint_as_float(gd[k]) * rsqrt_approx(md) : 0.f;
-            const float ga = ru * fu, gb = iu * fu, gc = rd * fd, gdd = id * fd;
-            vs_re[e] = ga + gc;
-            vs_im[e] = gb + gdd;
-            vt_re[e] = gb - gdd;
-            vt_im[e] = gc - ga;
-          }
-          __nv_bfloat162 h0 = __floats2bfloat162_rn(vs_re[0], vs_re[1]);
-          __nv_bfloat162 h1 = __floats2bfloat162_rn(vs_im[0], vs_im[1]);
-          __nv_bfloat162 h2 = __floats2bfloat162_rn(vt_re[0], vt_re[1]);
-          __nv_bfloat162 h3 = __floats2bfloat162_rn(vt_im[0], vt_im[1]);
+          // samples' element pairs (2i, 2i + 1) in packed FP32 operations
+          const float2 x1 = u2f2(p1[2 * i], p1[2 * i + 1]), x2 = u2f2(p2[2 * i], p2[2 * i + 1]);
+          const float2 x3 = u2f2(p3[2 * i], p3[2 * i + 1]), x4 = u2f2(p4[2 * i], p4[2 * i + 1]);
+          const float2 ru = fsub2(x1, x2), iu = __fadd2_rn(x3, x4);
+          const float2 rd = __fadd2_rn(x1, x2), id = fsub2(x3, x4);
+          const float2 mu = __ffma2_rn(ru, ru, __fmul2_rn(iu, iu));
+          const float2 md = __ffma2_rn(rd, rd, __fmul2_rn(id, id));
+          // g / |Z|, 0 at Z = 0
+          const float2 su = make_float2(mu.x > 0.f ? rsqrt_approx(mu.x) : 0.f,
+                                        mu.y > 0.f ? rsqrt_approx(mu.y) : 0.f);
+          const float2 sd = make_float2(md.x > 0.f ? rsqrt_approx(md.x) : 0.f,
+                                        md.y > 0.f ? rsqrt_approx(md.y) : 0.f);
+          const float2 fu = __fmul2_rn(u2f2(gu[2 * i], gu[2 * i + 1]), su);
+          const float2 fd = __fmul2_rn(u2f2(gd[2 * i], gd[2 * i + 1]), sd);
+          const float2 ga = __fmul2_rn(ru, fu), gb = __fmul2_rn(iu, fu);
+          const float2 gc = __fmul2_rn(rd, fd), gdd = __fmul2_rn(id, fd);
+          const float2 vs_re = __fadd2_rn(ga, gc), vs_im = __fadd2_rn(gb, gdd);
+          const float2 vt_re = fsub2(gb, gdd), vt_im = fsub2(gc, ga);
+          __nv_bfloat162 h0 = __floats2bfloat162_rn(vs_re.x, vs_re.y);
+          __nv_bfloat162 h1 = __floats2bfloat162_rn(vs_im.x, vs_im.y);
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(vt_re.x, vt_re.y);
+          __nv_bfloat162 h3 = __floats2bfloat162_rn(vt_im.x, vt_im.y);
           sre[i] = *reinterpret_cast<uint32_t*>(&h0);
           sim[i] = *reinterpret_cast<uint32_t*>(&h1);
           tre[i] = *reinterpret_cast<uint32_t*>(&h2);

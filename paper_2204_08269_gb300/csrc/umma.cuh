@@ -90,6 +90,16 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
+// Packed FP32 pairs (one instruction for two IEEE single operations, sm_100 and later): the
+// epilogues take their element pairs (k, k + 1) through these.  fsub2 is a - b as
+// b * (-1) + a, whose product is exact, so it rounds like a - b.
+__device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b) {
+  return make_float2(__uint_as_float(a), __uint_as_float(b));
+}
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
 // FP32 -> TF32 (10 mantissa bits) rounded to nearest, ties away; the tensor cores would
 // otherwise drop the low bits of FP32 operands (a biased truncation).
 __device__ __forceinline__ float tf32_rna(float x) {
