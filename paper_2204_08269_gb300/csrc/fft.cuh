@@ -21,6 +21,13 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
   return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
+// Complex sums as packed FP32 pairs (one instruction each, sm_100 and later); a - b is taken
+// as b * (-1) + a, whose product is exact, so it rounds like a - b.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+
 template <int SIGN>
 __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int idx) {
   float2 w = __ldg(&tw[idx]);
@@ -126,8 +133,8 @@ __device__ __forceinline__ void fft_dit_pass(float2* buf, int logL, int G,
         if (m & (1 << u)) continue;
         const int mp = m + (1 << u);
         const float2 t = cmul(v[mp], w[m & ((1 << u) - 1)]);
-        v[mp] = make_float2(v[m].x - t.x, v[m].y - t.y);
-        v[m] = make_float2(v[m].x + t.x, v[m].y + t.y);
+        v[mp] = csub(v[m], t);
+        v[m] = cadd(v[m], t);
       }
     }
 #pragma unroll

@@ -1374,13 +1374,13 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
           const float2 x3 = u2f2(p3[2 * i], p3[2 * i + 1]), x4 = u2f2(p4[2 * i], p4[2 * i + 1]);
           const float2 ru = fsub2(x1, x2), iu = __fadd2_rn(x3, x4);
           const float2 rd = __fadd2_rn(x1, x2), id = fsub2(x3, x4);
-          const float2 mu = __ffma2_rn(ru, ru, __fmul2_rn(iu, iu));
-          const float2 md = __ffma2_rn(rd, rd, __fmul2_rn(id, id));
-          // g / |Z|, 0 at Z = 0
-          const float2 su = make_float2(mu.x > 0.f ? rsqrt_approx(mu.x) : 0.f,
-                                        mu.y > 0.f ? rsqrt_approx(mu.y) : 0.f);
-          const float2 sd = make_float2(md.x > 0.f ? rsqrt_approx(md.x) : 0.f,
-                                        md.y > 0.f ? rsqrt_approx(md.y) : 0.f);
+          // g / |Z| as g rsqrt(|Z|^2 + 1e-30): gZ is exactly 0 at Z = 0, and the offset moves
+          // 1 / |Z| by less than BF16 rounding (2^-9) wherever |Z| > 1.6e-14
+          const float2 kEps = make_float2(1e-30f, 1e-30f);
+          const float2 mu = __ffma2_rn(ru, ru, __ffma2_rn(iu, iu, kEps));
+          const float2 md = __ffma2_rn(rd, rd, __ffma2_rn(id, id, kEps));
+          const float2 su = make_float2(rsqrt_approx(mu.x), rsqrt_approx(mu.y));
+          const float2 sd = make_float2(rsqrt_approx(md.x), rsqrt_approx(md.y));
           const float2 fu = __fmul2_rn(u2f2(gu[2 * i], gu[2 * i + 1]), su);
           const float2 fd = __fmul2_rn(u2f2(gd[2 * i], gd[2 * i + 1]), sd);
           const float2 ga = __fmul2_rn(ru, fu), gb = __fmul2_rn(iu, fu);
