@@ -832,13 +832,17 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
 // written).
 // The phi_T pooling runs on the tensor cores too (an earlier form pooled with mma.sync in the
 // epilogue, at a quarter of the tcgen05 rate).  The epilogue stages |Z| (BF16 hi, lo for the
-// FP32-grade split) of both spins in the K-major 128-byte-swizzled layout of an MMA operand,
-// [128 rows][64 samples] per spin and plane, and a second issuing thread accumulates D_spin[row][f] += |Z|[row][n] [W_hi | W_lo][f][n] over the
-// item's tiles into TMEM (N = NT per weight plane: frames of W_hi, then of W_lo; both |Z| planes
-// accumulate into the same D, so D[f] + D[NT + f] = (Z_hi + Z_lo)(W_hi + W_lo)).  The TMEM holds
-// one 256-column product accumulator beside the two pooling accumulators, so the product of tile
-// j + 1 starts once the epilogue has loaded tile j.  At an item's end warp (quarter, cg) reads
-// spin cg >> 1, frames [NT / 2 (cg & 1), +NT / 2) of its 32 rows and writes them.
+// FP32-grade split) of both spins in tensor memory as an MMA A operand (row r in lane r, two
+// samples per 32-bit column: 32 columns per spin and plane), and a second issuing thread
+// accumulates D_spin[row][f] += |Z|[row][n] [W_hi | W_lo][f][n] over the item's tiles into TMEM
+// (N = NT per weight plane: frames of W_hi, then of W_lo; both |Z| planes accumulate into the
+// same D, so D[f] + D[NT + f] = (Z_hi + Z_lo)(W_hi + W_lo)).  Staging |Z| in tensor memory
+// keeps its stores and the pooling MMAs' A reads off the shared memory, whose bandwidth the
+// product MMAs (8 KB per M = 128, N = 128, K = 16 step) already fill.  The TMEM holds one
+// 256-column product accumulator, the two pooling accumulators and the staged |Z|, so the
+// product of tile j + 1 starts once the epilogue has loaded tile j.  At an item's end warp
+// (quarter, cg) reads spin cg >> 1, frames [NT / 2 (cg & 1), +NT / 2) of its 32 rows and
+// writes them.
 constexpr int kTpThreads = 32 * 19;   // producer, product issuer, 16 epilogue warps, pooling issuer
 constexpr int kTpWarpPool = 18;
 
@@ -856,14 +860,12 @@ k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   constexpr uint32_t kAPlane = kBM * kBK * 2;            // 8 KB: 128 rows x 32 lambda', SW64
   constexpr uint32_t kYAtom = 4096;                      // 32 lambda' x 64 samples, SW128
   constexpr uint32_t kWHalf = NT * 64 * 2;               // one weight plane: NT frames x 64 samples
-  constexpr uint32_t kZPlane = 128 * 64 * 2;             // |Z| of one spin and plane: 16 KB
   const int max_kb = args.res_kb;
   const uint32_t y_bytes = planes * 2 * kYAtom;          // per plane [Yr atom | Yi atom]
   const uint32_t stage_bytes = RES ? y_bytes : planes * 2 * kAPlane + y_bytes;
   uint8_t* sA = sm;
   uint8_t* sStage = sm + (RES ? planes * 2 * max_kb * kAPlane : 0);
   uint8_t* sWt = sStage + S * stage_bytes;               // WS slots of [W_hi plane][W_lo plane]
-  uint8_t* sZ = sWt + WS * PS * kWHalf;                  // [spin][plane] planes of |Z|
   __shared__ uint64_t full_bar[8], empty_bar[8], wfull[kMaxWS], wempty[kMaxWS], tfull, tempty,
       sfull, sfree, dfull, dfree, a_full, a_free, mma_done, pool_done;
   __shared__ uint32_t tmem_base;
@@ -900,6 +902,8 @@ k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   tc_fence_after();
   const uint32_t tbase = tmem_base;
   const uint32_t t_pool = tbase + 256;                   // [spin] NP columns each
+  const uint32_t t_z = t_pool + 2 * NP;                  // [spin][plane] 32 columns of |Z|
+  static_assert(256 + 2 * NP + 2 * PS * 32 <= 512, "TMEM columns");
 
   auto fail = [&](int code) {
     if (!abort_flag) {
@@ -1034,8 +1038,8 @@ k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
   } else if (warp == kTpWarpPool) {
     // ------------------------------------------------------------ pooling issuer
     if (lane == 0) {
-      // A = |Z| [128 rows][64 samples] K-major, B = [W_hi ; W_lo] [NP frames][64 samples]
-      // K-major, both 128-byte rows; a K step is 16 samples (32 bytes)
+      // A = |Z| [128 rows][64 samples] in tensor memory, B = [W_hi ; W_lo] [NP frames][64
+      // samples] K-major with 128-byte rows; a K step is 16 samples
       const uint32_t idp = instr_desc(kBM, NP, 1, 1, 0, 0, 0);
       int ws = 0;
       uint32_t sph = 0, wph = 0, dph = 0;
@@ -1051,16 +1055,16 @@ k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           if (!mbar_wait(&wfull[ws], wph, wait_budget)) { fail(38); ok = false; break; }
           tc_fence_after();
           const uint64_t dW = smem_desc(smem_u32(sWt + ws * PS * kWHalf), 16, 1024, kSw128);
-          const uint64_t dZ = smem_desc(smem_u32(sZ), 16, 1024, kSw128);
 #pragma unroll
           for (int d = 0; d < 2; ++d)
 #pragma unroll
             for (int k = 0; k < 4; ++k)
 #pragma unroll
               for (int pa = 0; pa < PS; ++pa) {
-                const uint64_t az = dZ + (uint64_t)(((d * PS + pa) * kZPlane + k * 32) >> 4);
+                // A: samples [16 k, 16 k + 16) of |Z| (spin d, plane pa) in tensor memory
                 const uint64_t bw = dW + (uint64_t)((k * 32) >> 4);
-                mma_f16(t_pool + d * NP, az, bw, idp, (j | k | pa) ? 1u : 0u);
+                mma_f16_ta(t_pool + d * NP, t_z + (d * PS + pa) * 32 + k * 8, bw, idp,
+                           (j | k | pa) ? 1u : 0u);
               }
           mma_commit(&sfree);
           mma_commit(&wempty[ws]);
@@ -1079,9 +1083,8 @@ k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
     const int cg = ew >> 2;                   // samples [16 cg, 16 cg + 16) of the tile
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const int row = quarter * 32 + lane;      // row of the 128-row block (TMEM lane)
-    // this row's 16-byte chunks 2 cg + h of each |Z| plane (128-byte swizzle)
-    uint8_t* zrow = sZ + row * 128;
-    const int zc0 = ((2 * cg) ^ (row & 7)) * 16, zc1 = ((2 * cg + 1) ^ (row & 7)) * 16;
+    // this warp's |Z| columns: samples [16 cg, 16 cg + 16) of each (spin, plane) block
+    const uint32_t t_zw = t_z + lane_off + cg * 8;
     uint32_t tph = 0, sph = 0, dph = 0;
     for (int it = blockIdx.x; it < args.n_items; it += gridDim.x) {
       const int4 item = args.items[it % args.n_base];
@@ -1093,19 +1096,24 @@ k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         tc_fence_after();
         const uint32_t t_col = tbase + lane_off + cg * 16;
         uint32_t hv[2][2][4], lv[2][2][4];     // [h8][spin][4 bf16x2]
+        uint32_t q1[2][8], q3[2][8], q4[2][8], q2[2][8];
 #pragma unroll
         for (int h8 = 0; h8 < 2; ++h8) {
-          uint32_t p1[8], p3[8], p4[8], p2[8];
-          tmem_ld8u(t_col + h8 * 8, p1);
-          tmem_ld8u(t_col + h8 * 8 + 64, p3);
-          tmem_ld8u(t_col + h8 * 8 + 128, p4);
-          tmem_ld8u(t_col + h8 * 8 + 192, p2);
-          tmem_wait_ld();
-          if (h8 == 1) {
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty);
-          }
+          tmem_ld8u(t_col + h8 * 8, q1[h8]);
+          tmem_ld8u(t_col + h8 * 8 + 64, q3[h8]);
+          tmem_ld8u(t_col + h8 * 8 + 128, q4[h8]);
+          tmem_ld8u(t_col + h8 * 8 + 192, q2[h8]);
+        }
+        tmem_wait_ld();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty);
+#pragma unroll
+        for (int h8 = 0; h8 < 2; ++h8) {
+          const uint32_t* p1 = q1[h8];
+          const uint32_t* p3 = q3[h8];
+          const uint32_t* p4 = q4[h8];
+          const uint32_t* p2 = q2[h8];
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             // samples' element pairs (2i, 2i + 1) in packed FP32 operations
@@ -1134,17 +1142,20 @@ k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         // the pooling MMAs of the previous tile have read the staged |Z|
         if (!mbar_wait(&sfree, sph ^ 1, wait_budget)) { fail(40); ok = false; break; }
         sph ^= 1;
+        tc_fence_after();
 #pragma unroll
         for (int d = 0; d < 2; ++d) {
-          uint8_t* zp = zrow + d * PS * kZPlane;
-          *reinterpret_cast<uint4*>(zp + zc0) = make_uint4(hv[0][d][0], hv[0][d][1], hv[0][d][2], hv[0][d][3]);
-          *reinterpret_cast<uint4*>(zp + zc1) = make_uint4(hv[1][d][0], hv[1][d][1], hv[1][d][2], hv[1][d][3]);
+          const uint32_t zh[8] = {hv[0][d][0], hv[0][d][1], hv[0][d][2], hv[0][d][3],
+                                  hv[1][d][0], hv[1][d][1], hv[1][d][2], hv[1][d][3]};
+          tmem_st8(t_zw + (d * PS) * 32, zh);
           if (PS == 2) {
-            *reinterpret_cast<uint4*>(zp + kZPlane + zc0) = make_uint4(lv[0][d][0], lv[0][d][1], lv[0][d][2], lv[0][d][3]);
-            *reinterpret_cast<uint4*>(zp + kZPlane + zc1) = make_uint4(lv[1][d][0], lv[1][d][1], lv[1][d][2], lv[1][d][3]);
+            const uint32_t zl[8] = {lv[0][d][0], lv[0][d][1], lv[0][d][2], lv[0][d][3],
+                                    lv[1][d][0], lv[1][d][1], lv[1][d][2], lv[1][d][3]};
+            tmem_st8(t_zw + (d * PS + 1) * 32, zl);
           }
         }
-        fence_proxy_async_smem();
+        tmem_wait_st();
+        tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&sfull);
       }
@@ -1391,7 +1402,15 @@ bool tc_supported(const jtfs_plan* p) {
   return p->n2 <= 16 && tc_nt(p->n_t) <= 64 && p->cfg.precision != JTFS_PREC_FP32_SIMT;
 }
 
-int tc_res_kb(const jtfs_plan* p) { return p->cfg.precision == JTFS_PREC_BF16 ? 4 : 2; }
+namespace {
+int tp_res_kb(const jtfs_plan* p);
+}  // namespace
+
+// 32-lambda' blocks of a W tile held resident in shared memory (items with more stream W)
+int tc_res_kb(const jtfs_plan* p) {
+  if (p->tc_pair) return tp_res_kb(p);
+  return p->cfg.precision == JTFS_PREC_BF16 ? 4 : 2;
+}
 
 namespace {
 constexpr size_t kSmemBudget = 225 * 1024;
@@ -1479,28 +1498,32 @@ size_t tc16_smem_for(const jtfs_plan* p, bool res) {
   return s.fixed(res, tc_res_kb(p)) + (size_t)tc16_stages_for(p, res) * s.stage(res);
 }
 
-// Tensor-pooling form (k_joint_fwd_tp): resident W tile, operand stages, the weight ring
-// (kMaxWS slots of ppl planes of NT x 64 BF16) and the staged |Z| (2 spins x ppl planes of
-// 128 x 64 BF16).
+// Tensor-pooling form (k_joint_fwd_tp): resident W tile, operand stages and the weight ring
+// (kMaxWS slots of ppl planes of NT x 64 BF16); |Z| is staged in tensor memory.
 struct TpShape {
   int cpl, ppl, nt, res_kb;
   size_t fixed(bool res) const {
     return 1024 + (res ? (size_t)cpl * 2 * res_kb * kBM * kBK * 2 : 0) +
-           (size_t)kMaxWS * ppl * nt * 64 * 2 + (size_t)2 * ppl * 128 * 64 * 2;
+           (size_t)kMaxWS * ppl * nt * 64 * 2;
   }
   size_t stage(bool res) const {
     return (res ? 0 : (size_t)cpl * 2 * kBM * kBK * 2) + (size_t)cpl * 2 * 4096;
   }
 };
 
+// The resident W tile holds the most 32-lambda' blocks (up to the 5 of K = 160) that leave
+// room for four operand stages.
 TpShape tp_shape(const jtfs_plan* p) {
   TpShape s;
   s.cpl = p->cfg.precision == JTFS_PREC_FP32 ? 2 : 1;
   s.ppl = p->split ? 2 : 1;
   s.nt = tc_nt(p->n_t);
-  s.res_kb = tc_res_kb(p);
+  for (s.res_kb = 5; s.res_kb > 2; --s.res_kb)
+    if (s.fixed(true) + 4 * s.stage(true) <= kSmemBudget) break;
   return s;
 }
+
+int tp_res_kb(const jtfs_plan* p) { return tp_shape(p).res_kb; }
 
 int tp_stages_for(const jtfs_plan* p, bool res) {
   const TpShape s = tp_shape(p);
