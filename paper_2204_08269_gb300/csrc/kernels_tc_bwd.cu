@@ -1236,16 +1236,25 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
           tc_fence_after();
           const uint32_t wb = smem_u32(sW + wst * kWBuf);
           const uint32_t t_a = tbase + buf * D1C, t_b = t_a + 2 * RC, t_g = t_a + 4 * RC;
-          for (int ks = 0; ks < nks1; ++ks) {
-            for (int q = 0; q < npair; ++q) {
-              const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-              const uint64_t ayr = smem_desc(a1 + (pa * 2 + 0) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
-              const uint64_t ayi = smem_desc(a1 + (pa * 2 + 1) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
-              const uint64_t bw = smem_desc(wb + ((pb * NAT + (ks >> 2)) * 2) * kWBlk + (ks & 3) * 32,
-                                            16, 1024, kSw128);
-              const uint32_t f = (ks | q) ? 1u : 0u;
-              mma_f16(t_a, ayr, bw, id1, f);    // [P1 | P4] = Yr [Wr ; Wi]^T
-              mma_f16(t_b, ayi, bw, id1, f);    // [P3 | P2] = Yi [Wr ; Wi]^T
+          // descriptors from two bases plus constant offsets (16-byte units)
+          const uint64_t dY = smem_desc(a1, KM * 128, 1024, kSw128);
+          const uint64_t dW = smem_desc(wb, 16, 1024, kSw128);
+#pragma unroll
+          for (int ks = 0; ks < 4 * NAT; ++ks) {
+            if (ks < nks1) {
+#pragma unroll
+              for (int q = 0; q < 3; ++q) {
+                if (q < npair) {
+                  const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                  const uint64_t ayr = dY + (uint64_t)(((pa * 2 + 0) * kA1Plane + ks * 2048) >> 4);
+                  const uint64_t ayi = ayr + (uint64_t)(kA1Plane >> 4);
+                  const uint64_t bw =
+                      dW + (uint64_t)((((pb * NAT + (ks >> 2)) * 2) * kWBlk + (ks & 3) * 32) >> 4);
+                  const uint32_t f = (ks | q) ? 1u : 0u;
+                  mma_f16(t_a, ayr, bw, id1, f);    // [P1 | P4] = Yr [Wr ; Wi]^T
+                  mma_f16(t_b, ayi, bw, id1, f);    // [P3 | P2] = Yi [Wr ; Wi]^T
+                }
+              }
             }
           }
           const uint32_t g1 = wb + PL * NAT * 2 * kWBlk;
@@ -1286,16 +1295,21 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
           tc_fence_after();
           const uint32_t wb = smem_u32(sW + wst * kWBuf);
           const uint32_t a2 = smem_u32(sA2 + q2 * kA2Buf);
+          // descriptors from two bases plus constant offsets (16-byte units)
+          const uint64_t dS = smem_desc(a2, 16, 512, kSw64);
+          // MN-major over lambda': the NAT atoms of Wr (of Wi) are 2 kWBlk apart
+          const uint64_t dW = smem_desc(wb, 2 * kWBlk, 1024, kSw128);
+#pragma unroll
           for (int ks = 0; ks < RC / 16; ++ks) {
-            const uint64_t sre = smem_desc(a2 + 0 * kA2Part + ks * 32, 16, 512, kSw64);
-            const uint64_t sim = smem_desc(a2 + 1 * kA2Part + ks * 32, 16, 512, kSw64);
-            const uint64_t tre = smem_desc(a2 + 2 * kA2Part + ks * 32, 16, 512, kSw64);
-            const uint64_t tim = smem_desc(a2 + 3 * kA2Part + ks * 32, 16, 512, kSw64);
+            const uint64_t sre = dS + (uint64_t)((0 * kA2Part + ks * 32) >> 4);
+            const uint64_t sim = dS + (uint64_t)((1 * kA2Part + ks * 32) >> 4);
+            const uint64_t tre = dS + (uint64_t)((2 * kA2Part + ks * 32) >> 4);
+            const uint64_t tim = dS + (uint64_t)((3 * kA2Part + ks * 32) >> 4);
+#pragma unroll
             for (int q = 0; q < PL; ++q) {                      // W_hi, then W_lo
-              // MN-major over lambda': the NAT atoms of Wr (of Wi) are 2 kWBlk apart
-              const uint32_t wpl = wb + q * NAT * 2 * kWBlk + ks * 2048;
-              const uint64_t wr = smem_desc(wpl, 2 * kWBlk, 1024, kSw128);
-              const uint64_t wi = smem_desc(wpl + kWBlk, 2 * kWBlk, 1024, kSw128);
+              const uint32_t wo = q * NAT * 2 * kWBlk + ks * 2048;
+              const uint64_t wr = dW + (uint64_t)(wo >> 4);
+              const uint64_t wi = dW + (uint64_t)((wo + kWBlk) >> 4);
               const uint32_t f = (j == 0 && ks == 0 && q == 0) ? 0u : 1u;
               if (TA) {
                 const uint32_t ta = t_a2 + ks * 8;
