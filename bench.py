@@ -38,10 +38,10 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 SMS = 152
 # DRAM bytes (read + write) per step of the contraction stages (forward and backward kernels
 # with their phi_F pooling / adjoint) at B = 64, from an ncu capture of dram__bytes_read.sum +
-# dram__bytes_write.sum of the current kernels: 710.8 MB at B = 16, scaled by the signals (the
+# dram__bytes_write.sum of the current kernels: 715.7 MB at B = 16, scaled by the signals (the
 # kernels' traffic is proportional to them); None where no capture of the current kernels
 # exists.
-CONTRACTION_TRAFFIC = {"fp32": 4 * 710.8e6}
+CONTRACTION_TRAFFIC = {"fp32": 4 * 715.7e6}
 
 
 def _peaks():
