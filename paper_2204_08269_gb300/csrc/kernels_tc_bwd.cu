@@ -1481,7 +1481,8 @@ k_joint_bwd_pair(const __grid_constant__ TpMaps maps, TpArgs args, DevPlan P) {
 // G1[(b n2 + a) g1_rows + c n1 + lambda][t] = sum_lo phi_F[(lo s_F - lambda) mod N_fr] gS2[b,a,c,lo,t]
 // (or gS2 itself for Eq. 4), as BF16 (hi, and lo when g1lo is given), zero for t >= n_t.  One
 // block per (alpha, signal) walks the channels with phi_F and each channel's n_lo x n_t
-// cotangents in shared memory; every row adds its n_lo terms in increasing lo.
+// cotangents in shared memory; every row adds its n_lo terms in increasing lo.  G1 rows are
+// NT = 16 or 32 BF16 (32 or 64 bytes) from 16-byte aligned plane bases.
 constexpr int kG1Threads = 256;
 constexpr int kG1InMax = 4096;       // n_lo * n_t floats of one channel
 
@@ -1504,25 +1505,46 @@ k_g1(DevPlan Pd, const float* __restrict__ gs2, int NT, int g1_rows,
       for (int i = threadIdx.x; i < nin; i += blockDim.x) gin[i] = g[i];
       __syncthreads();
     }
-    for (int i = threadIdx.x; i < n1 * NT; i += blockDim.x) {
-      const int r = i / NT, t = i - r * NT;
-      float s = 0.f;
-      if (t < nt) {
-        if (Pd.average_fr) {
-          if (staged) {
-            for (int lo = 0; lo < Pd.n_lo; ++lo) s += phi[(lo * Pd.s_F - r) & nfm] * gin[lo * nt + t];
-          } else {
-            for (int lo = 0; lo < Pd.n_lo; ++lo)
-              s += __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]) * g[lo * nt + t];
-          }
-        } else {
-          s = staged ? gin[r * nt + t] : g[r * nt + t];
+    // eight frames per thread: one phi_F value serves eight outputs, and each plane takes one
+    // 16-byte store (NT is 16 or 32, so a group never straddles rows)
+    const int ng = NT / 8;
+    for (int u = threadIdx.x; u < n1 * ng; u += blockDim.x) {
+      const int r = u / ng, t0 = (u - r * ng) * 8;
+      float s[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s[k] = 0.f;
+      if (Pd.average_fr) {
+        for (int lo = 0; lo < Pd.n_lo; ++lo) {
+          const float p = staged ? phi[(lo * Pd.s_F - r) & nfm] : __ldg(&Pd.phiF[(lo * Pd.s_F - r) & nfm]);
+          const float* gl = staged ? gin + lo * nt : g + lo * nt;
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (t0 + k < nt) s[k] += p * gl[t0 + k];
         }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          if (t0 + k < nt) s[k] = staged ? gin[r * nt + t0 + k] : g[r * nt + t0 + k];
       }
-      const __nv_bfloat16 h = __float2bfloat16_rn(s);
-      g1[o0 + i] = h;
-      if (g1lo) g1lo[o0 + i] = __float2bfloat16_rn(s - __bfloat162float(h));
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(s[2 * k], s[2 * k + 1]);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(s[2 * k] - hf.x, s[2 * k + 1] - hf.y);
+        hw[k] = *reinterpret_cast<const uint32_t*>(&h);
+        lw[k] = *reinterpret_cast<const uint32_t*>(&l);
+      }
+      const size_t o = o0 + (size_t)r * NT + t0;
+      *reinterpret_cast<uint4*>(g1 + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      if (g1lo) *reinterpret_cast<uint4*>(g1lo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
     }
+  }
+  // the block's padding rows C n1 .. g1_rows - 1 (read by the last chunks' boxes) are zero
+  const size_t ob = (size_t)(b * Pd.n2 + a) * g1_rows * NT;
+  for (int i = C * n1 * NT + threadIdx.x * 8; i < g1_rows * NT; i += blockDim.x * 8) {
+    *reinterpret_cast<uint4*>(g1 + ob + i) = make_uint4(0u, 0u, 0u, 0u);
+    if (g1lo) *reinterpret_cast<uint4*>(g1lo + ob + i) = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
@@ -1766,8 +1788,7 @@ jtfs_status launch_joint_bwd_tc(const jtfs_plan* p, int B, const void* yhi_v, co
   const size_t g1_plane = tcb_g1_bytes(p, B) / 2;
   __nv_bfloat16* g1hi = (__nv_bfloat16*)g1buf;
   __nv_bfloat16* g1lo = (__nv_bfloat16*)((char*)g1buf + g1_plane);
-  // G1 (phi_F adjoint of g_S2), zero padded
-  if ((rc = cuda_check(cudaMemsetAsync(g1buf, 0, tcb_g1_bytes(p, B), st), "memset g1")) != JTFS_OK) return rc;
+  // G1 (phi_F adjoint of g_S2), zero padded by the kernel
   k_g1<<<dim3(p->n2, B), kG1Threads, 0, st>>>(d, gs2, NT, g1_rows, g1hi, three ? g1lo : nullptr);
   ++p->prof.launches;
   if ((rc = cuda_check(cudaGetLastError(), "k_g1")) != JTFS_OK) return rc;
