@@ -1096,6 +1096,8 @@ k_joint_fwd_tp(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         tc_fence_after();
         const uint32_t t_col = tbase + lane_off + cg * 16;
         uint32_t hv[2][2][4], lv[2][2][4];     // [h8][spin][4 bf16x2]
+        // the whole accumulator share (four products x 16 samples) is loaded before it is
+        // released, so the next tile's product waits for the loads alone
         uint32_t q1[2][8], q3[2][8], q4[2][8], q2[2][8];
 #pragma unroll
         for (int h8 = 0; h8 < 2; ++h8) {
