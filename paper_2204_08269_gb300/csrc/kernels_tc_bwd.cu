@@ -883,24 +883,39 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
           tc_fence_after();
           const uint32_t wb = smem_u32(sW + wst * kWBuf);
           const uint32_t t_d1 = tbase + buf * 3 * RC, t_d4 = t_d1 + 2 * RC;
-          for (int ks = 0; ks < nks1; ++ks) {
-            for (int q = 0; q < npair; ++q) {
-              const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-              const uint64_t ayr = smem_desc(a1 + (pa * 2 + 0) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
-              const uint64_t ayi = smem_desc(a1 + (pa * 2 + 1) * kA1Plane + ks * 2048, KM * 128, 1024, kSw128);
-              const uint32_t wpl = wb + (pb * NAT + (ks >> 2)) * 3 * kWBlk + (ks & 3) * 32;
-              const uint32_t f = (ks | q) ? 1u : 0u;
-              mma_f16(t_d1, ayr, smem_desc(wpl + kWBlk, 16, 1024, kSw128), id1, f);   // Yr [Wr; Wi]
-              mma_f16(t_d1, ayi, smem_desc(wpl, 16, 1024, kSw128), id1, 1u);          // Yi [-Wi; Wr]
+          // descriptors from per-chunk bases plus constant offsets (16-byte units)
+          const uint64_t dY = smem_desc(a1, KM * 128, 1024, kSw128);
+          const uint64_t dW = smem_desc(wb, 16, 1024, kSw128);
+#pragma unroll
+          for (int ks = 0; ks < 4 * NAT; ++ks) {
+            if (ks < nks1) {
+#pragma unroll
+              for (int q = 0; q < 3; ++q) {
+                if (q < npair) {
+                  const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                  const uint64_t ayr = dY + (uint64_t)(((pa * 2 + 0) * kA1Plane + ks * 2048) >> 4);
+                  const uint64_t ayi = ayr + (uint64_t)(kA1Plane >> 4);
+                  const uint64_t bw =
+                      dW + (uint64_t)(((pb * NAT + (ks >> 2)) * 3 * kWBlk + (ks & 3) * 32) >> 4);
+                  const uint32_t f = (ks | q) ? 1u : 0u;
+                  mma_f16(t_d1, ayr, bw + (uint64_t)(kWBlk >> 4), id1, f);   // Yr [Wr; Wi]
+                  mma_f16(t_d1, ayi, bw, id1, 1u);                           // Yi [-Wi; Wr]
+                }
+              }
             }
           }
           const uint32_t g1 = wb + PL * NAT * 3 * kWBlk;
+          const uint64_t dA4 = smem_desc(a4, 16, 8 * kSw, kLayNT);
+          const uint64_t dG1 = smem_desc(g1, 16, 8 * kSw, kLayNT);
+#pragma unroll
           for (int ks = 0; ks < NT / 16; ++ks)
-            for (int q = 0; q < npair; ++q) {
-              const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
-              mma_f16(t_d4, smem_desc(a4 + pa * kA4Plane + ks * 32, 16, 8 * kSw, kLayNT),
-                      smem_desc(g1 + pb * kG1Plane + ks * 32, 16, 8 * kSw, kLayNT), id4,
-                      (ks | q) ? 1u : 0u);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              if (q < npair) {
+                const int pa = q == 2 ? 1 : 0, pb = q == 1 ? 1 : 0;
+                mma_f16(t_d4, dA4 + (uint64_t)((pa * kA4Plane + ks * 32) >> 4),
+                        dG1 + (uint64_t)((pb * kG1Plane + ks * 32) >> 4), id4, (ks | q) ? 1u : 0u);
+              }
             }
           mma_commit(&d1_full[buf]);
           if (++wst == WB) { wst = 0; wph ^= 1; }
@@ -933,15 +948,21 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
           tc_fence_after();
           const uint32_t wb = smem_u32(sW + wst * kWBuf);
           const uint32_t a2 = smem_u32(sA2 + q2 * kA2Buf);
+          // descriptors from per-chunk bases plus constant offsets (16-byte units)
+          const uint64_t dA2 = smem_desc(a2, 16, kA2Sbo, kA2Lay);
+          const uint64_t dW = smem_desc(wb, kWBlk, 1024, kSw128);
+#pragma unroll
           for (int ks = 0; ks < RC / 16; ++ks) {
-            const uint64_t agr = smem_desc(a2 + ks * 32, 16, kA2Sbo, kA2Lay);
-            const uint64_t agi = smem_desc(a2 + kA2Part + ks * 32, 16, kA2Sbo, kA2Lay);
+            const uint64_t agr = dA2 + (uint64_t)((ks * 32) >> 4);
+            const uint64_t agi = dA2 + (uint64_t)((kA2Part + ks * 32) >> 4);
+#pragma unroll
             for (int q = 0; q < PL; ++q) {                      // W_hi, then W_lo
               const uint32_t f = (j == 0 && ks == 0 && q == 0) ? 0u : 1u;
+#pragma unroll
               for (int k = 0; k < NAT; ++k) {
-                const uint32_t wpl = wb + (q * NAT + k) * 3 * kWBlk + ks * 2048;
-                mma_f16(t_d2 + 128 * k, agi, smem_desc(wpl + kWBlk, kWBlk, 1024, kSw128), id2, f);   // gZi [Wr | Wi]
-                mma_f16(t_d2 + 128 * k, agr, smem_desc(wpl, kWBlk, 1024, kSw128), id2, 1u);          // gZr [-Wi | Wr]
+                const uint64_t wd = dW + (uint64_t)(((q * NAT + k) * 3 * kWBlk + ks * 2048) >> 4);
+                mma_f16(t_d2 + 128 * k, agi, wd + (uint64_t)(kWBlk >> 4), id2, f);   // gZi [Wr | Wi]
+                mma_f16(t_d2 + 128 * k, agr, wd, id2, 1u);                           // gZr [-Wi | Wr]
               }
             }
           }
@@ -986,17 +1007,16 @@ k_joint_bwd_fast(const __grid_constant__ TfMaps maps, TfArgs args, DevPlan P) {
         uint32_t hr[CW / 2], hi[CW / 2];
 #pragma unroll
         for (int i = 0; i < CW / 2; ++i) {
-          float vr[2], vi[2];
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int k = 2 * i + e;
-            const float m2 = fmaf(zr[k], zr[k], zi[k] * zi[k]);
-            const float f = m2 > 0.f ? g[k] * rsqrt_approx(m2) : 0.f;
-            vr[e] = zr[k] * f;
-            vi[e] = zi[k] * f;
-          }
-          __nv_bfloat162 a0 = __floats2bfloat162_rn(vr[0], vr[1]);
-          __nv_bfloat162 a1v = __floats2bfloat162_rn(vi[0], vi[1]);
+          // element pairs (2i, 2i + 1) in packed FP32 operations; g / |Z| as
+          // g rsqrt(|Z|^2 + 1e-30), so gZ is exactly 0 at Z = 0
+          const float2 r2 = make_float2(zr[2 * i], zr[2 * i + 1]);
+          const float2 i2 = make_float2(zi[2 * i], zi[2 * i + 1]);
+          const float2 m2 = __ffma2_rn(r2, r2, __ffma2_rn(i2, i2, make_float2(1e-30f, 1e-30f)));
+          const float2 f = __fmul2_rn(make_float2(g[2 * i], g[2 * i + 1]),
+                                      make_float2(rsqrt_approx(m2.x), rsqrt_approx(m2.y)));
+          const float2 vr = __fmul2_rn(r2, f), vi = __fmul2_rn(i2, f);
+          __nv_bfloat162 a0 = __floats2bfloat162_rn(vr.x, vr.y);
+          __nv_bfloat162 a1v = __floats2bfloat162_rn(vi.x, vi.y);
           hr[i] = *reinterpret_cast<uint32_t*>(&a0);
           hi[i] = *reinterpret_cast<uint32_t*>(&a1v);
         }
