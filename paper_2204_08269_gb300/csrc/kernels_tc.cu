@@ -352,12 +352,14 @@ k_joint_fwd_tc(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
         uint32_t hv[CW / 2], lv[CW / 2];
 #pragma unroll
         for (int i = 0; i < CW / 2; ++i) {
-          const float m0v = sqrt_approx(fmaf(re[2 * i], re[2 * i], im[2 * i] * im[2 * i]));
-          const float m1v =
-              sqrt_approx(fmaf(re[2 * i + 1], re[2 * i + 1], im[2 * i + 1] * im[2 * i + 1]));
-          __nv_bfloat162 h = __floats2bfloat162_rn(m0v, m1v);
-          const float2 hf = __bfloat1622float2(h);
-          __nv_bfloat162 l = __floats2bfloat162_rn(m0v - hf.x, m1v - hf.y);
+          // element pairs (2i, 2i + 1) in packed FP32 operations
+          const float2 r2 = make_float2(re[2 * i], re[2 * i + 1]);
+          const float2 i2 = make_float2(im[2 * i], im[2 * i + 1]);
+          const float2 m2 = __ffma2_rn(r2, r2, __fmul2_rn(i2, i2));
+          const float2 mv = make_float2(sqrt_approx(m2.x), sqrt_approx(m2.y));
+          __nv_bfloat162 h = __floats2bfloat162_rn(mv.x, mv.y);
+          const float2 d = fsub2(mv, __bfloat1622float2(h));
+          __nv_bfloat162 l = __floats2bfloat162_rn(d.x, d.y);
           hv[i] = *reinterpret_cast<uint32_t*>(&h);
           lv[i] = *reinterpret_cast<uint32_t*>(&l);
         }
@@ -711,12 +713,14 @@ k_joint_fwd_tc16(const __grid_constant__ TcMaps maps, TcArgs args, DevPlan P) {
           uint32_t hv[8], lv[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const float m0v = sqrt_approx(fmaf(re[2 * i], re[2 * i], im[2 * i] * im[2 * i]));
-            const float m1v =
-                sqrt_approx(fmaf(re[2 * i + 1], re[2 * i + 1], im[2 * i + 1] * im[2 * i + 1]));
-            __nv_bfloat162 h = __floats2bfloat162_rn(m0v, m1v);
-            const float2 hf = __bfloat1622float2(h);
-            __nv_bfloat162 l = __floats2bfloat162_rn(m0v - hf.x, m1v - hf.y);
+            // element pairs (2i, 2i + 1) in packed FP32 operations
+            const float2 r2 = make_float2(re[2 * i], re[2 * i + 1]);
+            const float2 i2 = make_float2(im[2 * i], im[2 * i + 1]);
+            const float2 m2 = __ffma2_rn(r2, r2, __fmul2_rn(i2, i2));
+            const float2 mv = make_float2(sqrt_approx(m2.x), sqrt_approx(m2.y));
+            __nv_bfloat162 h = __floats2bfloat162_rn(mv.x, mv.y);
+            const float2 d = fsub2(mv, __bfloat1622float2(h));
+            __nv_bfloat162 l = __floats2bfloat162_rn(d.x, d.y);
             hv[i] = *reinterpret_cast<uint32_t*>(&h);
             lv[i] = *reinterpret_cast<uint32_t*>(&l);
           }
