@@ -193,10 +193,14 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
     }
   } else {
     // rows of one rate are contiguous in each plane: element idx of the block sits at
-    // (lam0 - lam_min) L + idx; two samples per thread
+    // (lam0 - lam_min) L + idx
     const size_t plane = (size_t)A.K * L;
     const size_t base = (size_t)B * 2 * A.off_y + (size_t)(2 * b) * plane + (size_t)(lam0 - A.lam_min) * L;
-    for (int i2 = threadIdx.x; i2 < (G * L) >> 1; i2 += blockDim.x) {
+    // four samples per thread, one 8-byte store per plane, where rows hold at least four
+    // samples (so a group never straddles rows) and both plane offsets are multiples of four
+    // samples; else two samples per thread
+    const bool quad = L >= 4 && (base & 3) == 0 && (plane & 3) == 0;
+    for (int i2 = threadIdx.x; !quad && i2 < (G * L) >> 1; i2 += blockDim.x) {
       const int idx = 2 * i2;
       const float inv = s_inv[idx >> logL];
       const float2 v0 = sm[fft_pos(idx, logL)], v1 = sm[fft_pos(idx + 1, logL)];
@@ -208,6 +212,30 @@ k_second_order_rows(DevPlan P, const int4* __restrict__ items, const float2* __r
         const float2 fr = __bfloat1622float2(hr), fi = __bfloat1622float2(hi_);
         *reinterpret_cast<__nv_bfloat162*>(ylo + base + idx) = __floats2bfloat162_rn(r0 - fr.x, r1 - fr.y);
         *reinterpret_cast<__nv_bfloat162*>(ylo + base + plane + idx) = __floats2bfloat162_rn(i0 - fi.x, i1 - fi.y);
+      }
+    }
+    for (int i4 = threadIdx.x; quad && i4 < (G * L) >> 2; i4 += blockDim.x) {
+      const int idx = 4 * i4;
+      const float inv = s_inv[idx >> logL];
+      uint32_t hw[2][2], lw[2][2];   // [re / im][sample pair]
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float2 v0 = sm[fft_pos(idx + 2 * e, logL)], v1 = sm[fft_pos(idx + 2 * e + 1, logL)];
+        const float r0 = v0.x * inv, r1 = v1.x * inv, i0 = v0.y * inv, i1 = v1.y * inv;
+        const __nv_bfloat162 hr = __floats2bfloat162_rn(r0, r1), hi_ = __floats2bfloat162_rn(i0, i1);
+        hw[0][e] = *reinterpret_cast<const uint32_t*>(&hr);
+        hw[1][e] = *reinterpret_cast<const uint32_t*>(&hi_);
+        const float2 fr = __bfloat1622float2(hr), fi = __bfloat1622float2(hi_);
+        const __nv_bfloat162 lr = __floats2bfloat162_rn(r0 - fr.x, r1 - fr.y);
+        const __nv_bfloat162 li = __floats2bfloat162_rn(i0 - fi.x, i1 - fi.y);
+        lw[0][e] = *reinterpret_cast<const uint32_t*>(&lr);
+        lw[1][e] = *reinterpret_cast<const uint32_t*>(&li);
+      }
+      *reinterpret_cast<uint2*>(yhi + base + idx) = make_uint2(hw[0][0], hw[0][1]);
+      *reinterpret_cast<uint2*>(yhi + base + plane + idx) = make_uint2(hw[1][0], hw[1][1]);
+      if (ylo) {
+        *reinterpret_cast<uint2*>(ylo + base + idx) = make_uint2(lw[0][0], lw[0][1]);
+        *reinterpret_cast<uint2*>(ylo + base + plane + idx) = make_uint2(lw[1][0], lw[1][1]);
       }
     }
   }
