@@ -173,24 +173,58 @@ k_gy_spectra(DevPlan P, const int4* __restrict__ items, float2* __restrict__ gy)
   const Rate2 A = P.rates2[a];
   const int L = A.L, logL = A.logL;
   float2* g = gy + (size_t)b * P.y_len + A.off_y + (size_t)(lam0 - A.lam_min) * L;
-  // eight loads in flight per thread before their shared-memory stores
   const int total = G * L, step = blockDim.x;
-  for (int base = threadIdx.x; base < total; base += 8 * step) {
-    float2 v[8];
+  // two samples per 16-byte access where the block's rows start 16-byte aligned (rows hold an
+  // even number of samples), else one
+  const bool pair = L >= 2 && ((uintptr_t)g & 15) == 0;
+  if (pair) {
+    // four 16-byte loads in flight per thread before their shared-memory stores
+    const float4* g4 = reinterpret_cast<const float4*>(g);
+    const int total2 = total >> 1;
+    for (int base = threadIdx.x; base < total2; base += 4 * step) {
+      float4 v[4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int idx = base + q * step;
-      v[q] = idx < total ? g[idx] : make_float2(0.f, 0.f);
+      for (int q = 0; q < 4; ++q) {
+        const int i2 = base + q * step;
+        v[q] = i2 < total2 ? g4[i2] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int idx = 2 * (base + q * step);
+        if (idx < total) {
+          const int r0 = (idx >> logL) << logL, k = idx & (L - 1);
+          sm[fft_pos(r0 + bitrev(k, logL), logL)] = make_float2(v[q].x, v[q].y);
+          sm[fft_pos(r0 + bitrev(k + 1, logL), logL)] = make_float2(v[q].z, v[q].w);
+        }
+      }
     }
+  } else {
+    // eight loads in flight per thread before their shared-memory stores
+    for (int base = threadIdx.x; base < total; base += 8 * step) {
+      float2 v[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int idx = base + q * step;
-      if (idx < total) sm[fft_pos(((idx >> logL) << logL) + bitrev(idx & (L - 1), logL), logL)] = v[q];
+      for (int q = 0; q < 8; ++q) {
+        const int idx = base + q * step;
+        v[q] = idx < total ? g[idx] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int idx = base + q * step;
+        if (idx < total) sm[fft_pos(((idx >> logL) << logL) + bitrev(idx & (L - 1), logL), logL)] = v[q];
+      }
     }
   }
   __syncthreads();
   fft_dit_rows_r16<-1>(sm, logL, G, twl_for(P, logL));
-  for (int idx = threadIdx.x; idx < G * L; idx += blockDim.x) g[idx] = sm[fft_pos(idx, logL)];
+  if (pair) {
+    float4* g4 = reinterpret_cast<float4*>(g);
+    for (int i2 = threadIdx.x; i2 < total >> 1; i2 += blockDim.x) {
+      const float2 a = sm[fft_pos(2 * i2, logL)], c = sm[fft_pos(2 * i2 + 1, logL)];
+      g4[i2] = make_float4(a.x, a.y, c.x, c.y);
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) g[idx] = sm[fft_pos(idx, logL)];
+  }
 }
 
 // g_U1 row lambda': sum over rates alpha of the adjoint of psi2 (the gY row's spectrum / Lr
